@@ -1,0 +1,581 @@
+"""CPU float64 oracle for Exp-ParaDiag -- TEST INFRASTRUCTURE, not product code.
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline / reference leg
+may import this module.  It shares no code with the CUDA path and never imports
+the product package; inputs reach it as plain numpy arrays.
+
+It is a plain, slow, obviously-correct numpy restatement (float64 throughout) of
+what Garai & Chamakuri, "Exp-ParaDiag: Time-Parallel Exponential Integrators for
+Parabolic PDEs" (arXiv 2603.04350) computes:
+
+  * the exponential BDF-s schemes u_n = sum_j a_j A^j u_{n-j}, A = exp(dt L_h)
+    (Eq. (4.1), Sec. 5 Eqs. (5.1), (5.3), (5.5), (5.7)), with the
+    integrating-factor nonlinear term of Eq. (6.1) and a source term;
+  * the all-at-once systems Q u = f / R_s v = f_s (Eqs. (3.1), (4.2), Sec. 5)
+    and their alpha-circulant preconditioners (Eqs. (3.2), (4.4), Sec. 5);
+  * the three-step preconditioner solve (Eq. (3.3), Eq. (4.5));
+  * the preconditioned Richardson iteration (Eq. (3.2), (4.4)) and its lagged
+    nonlinear form (Eqs. (7.3)-(7.4));
+  * left-preconditioned GMRES (Sec. 3.2, Theorem 3.3);
+  * dense brute-force versions of all of the above for tiny sizes (explicit
+    L_h, scipy's expm, explicit C_j^alpha matrices, LU solves).
+
+Readings taken where the paper is silent (each is also listed in the design
+notes): the source f enters row n as beta_s*dt*f(t_n) and the nonlinear term as
+beta_s*dt*N(u_n) (implicit, integrating factor); the startup values
+u_1..u_{s-1} come from the IF-BDF_j ramp j = 1..s-1; C_j^alpha = (C_0^alpha)^(j+1)
+(the printed entry lists of Sec. 5 are garbled); the periodic L_h is the
+spectral Laplacian with the Nyquist mode's symbol -a*(pi*n/L)^2.
+
+Parity status: every function here is pinned by tests/test_oracle_pins.py
+against closed forms, the paper's printed coefficients and spectra, and dense
+brute force; nothing is "parity unpinned".
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+from fractions import Fraction
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+import scipy.fft
+import scipy.linalg
+
+PERIODIC = "periodic"
+DIRICHLET = "dirichlet"
+
+
+# ---------------------------------------------------------------------------
+# Problem description (plain data; the oracle does not import the product).
+# ---------------------------------------------------------------------------
+@dataclass(frozen=True)
+class Spec:
+    bc: str                      # "periodic" | "dirichlet"
+    n: Tuple[int, ...]           # grid points per dimension
+    length: Tuple[float, ...]    # domain length per dimension
+    a: float                     # L = a*Lap - c   (Eq. (1.2))
+    c: float
+    nonlin: str                  # "none" | "allen_cahn"
+    dt: float
+    Nt: int
+    alpha: float
+    order: int                   # s in 1..6
+
+    @property
+    def ndim(self):
+        return len(self.n)
+
+    @property
+    def Ns(self):
+        return self.Nt - self.order + 1
+
+
+def spec_of(p) -> Spec:
+    """Build a Spec from any object with the same attribute names."""
+    return Spec(p.bc, tuple(p.n), tuple(p.length), p.a, p.c, p.nonlin, p.dt, p.Nt,
+                p.alpha, p.order)
+
+
+# ---------------------------------------------------------------------------
+# BDF coefficients (Eq. (4.1), Eqs. (5.1), (5.3), (5.5), (5.7)).
+# ---------------------------------------------------------------------------
+def bdf_coefficients(s: int) -> Tuple[List[Fraction], Fraction]:
+    """Exact a_1..a_s and beta_s of BDF-s from its defining difference form
+    sum_{i=1..s} (1/i) nabla^i u_n = dt f_n, i.e. the polynomial
+    sum_i (1/i)(1 - z)^i = c_0 + c_1 z + ... normalised to u_n - sum_j a_j u_{n-j}
+    = beta dt f_n.  The paper prints the resulting a_j for s = 2..6."""
+    if not 1 <= s <= 6:
+        raise ValueError("order must be 1..6")
+    c = [Fraction(0)] * (s + 1)
+    for i in range(1, s + 1):
+        for j in range(i + 1):
+            c[j] += Fraction(1, i) * math.comb(i, j) * (-1) ** j
+    beta = 1 / c[0]
+    a = [-c[j] / c[0] for j in range(1, s + 1)]
+    return a, beta
+
+
+def bdf_float(s: int):
+    a, beta = bdf_coefficients(s)
+    return np.array([float(x) for x in a]), float(beta)
+
+
+# ---------------------------------------------------------------------------
+# Spatial operator L_h = a*Delta_h - c and its eigenbasis (Sec. 2, after Eq. (2.7)).
+# ---------------------------------------------------------------------------
+def spatial_eigenvalues(sp: Spec) -> np.ndarray:
+    """Eigenvalues mu of L_h laid out like the oracle's eigen-coefficients.
+
+    Periodic: spectral Laplacian, mu = -a*sum_d (2*pi*k_d/L_d)^2 - c with k_d in
+    numpy FFT order (the Nyquist index carries (pi*n/L)^2).
+    Dirichlet: 3-point (1D) / 5-point (2D) finite differences on n interior
+    points, h = L/(n+1): mu = -a*sum_d (4/h^2) sin^2(pi k_d h/(2 L_d)) - c,
+    k_d = 1..n, eigenvectors sin(pi k_d x/L_d) (the DST-I basis)."""
+    parts = []
+    for n, L in zip(sp.n, sp.length):
+        if sp.bc == PERIODIC:
+            k = np.fft.fftfreq(n, 1.0 / n)
+            parts.append(-(2.0 * np.pi * k / L) ** 2)
+        else:
+            h = L / (n + 1)
+            k = np.arange(1, n + 1)
+            parts.append(-(4.0 / h**2) * np.sin(np.pi * k * h / (2.0 * L)) ** 2)
+    grids = np.meshgrid(*parts, indexing="ij")
+    return sp.a * sum(grids) - sp.c
+
+
+def _axes(sp: Spec, x: np.ndarray):
+    return tuple(range(x.ndim - sp.ndim, x.ndim))
+
+
+def to_eigen(sp: Spec, u: np.ndarray) -> np.ndarray:
+    """Coefficients of u in L_h's eigenbasis (last ndim axes): unnormalised
+    DFT for periodic grids, orthonormal DST-I for Dirichlet grids."""
+    ax = _axes(sp, u)
+    if sp.bc == PERIODIC:
+        return np.fft.fftn(u, axes=ax)
+    if np.iscomplexobj(u):
+        return (scipy.fft.dstn(u.real, type=1, axes=ax, norm="ortho")
+                + 1j * scipy.fft.dstn(u.imag, type=1, axes=ax, norm="ortho"))
+    return scipy.fft.dstn(u, type=1, axes=ax, norm="ortho")
+
+
+def from_eigen(sp: Spec, uh: np.ndarray) -> np.ndarray:
+    """Inverse of to_eigen (complex in, complex out for periodic grids)."""
+    ax = _axes(sp, uh)
+    if sp.bc == PERIODIC:
+        return np.fft.ifftn(uh, axes=ax)
+    if np.iscomplexobj(uh):
+        return (scipy.fft.idstn(uh.real, type=1, axes=ax, norm="ortho")
+                + 1j * scipy.fft.idstn(uh.imag, type=1, axes=ax, norm="ortho"))
+    return scipy.fft.idstn(uh, type=1, axes=ax, norm="ortho")
+
+
+def apply_A_power(sp: Spec, u: np.ndarray, j: int) -> np.ndarray:
+    """A^j u with A = exp(dt L_h) (Eq. (2.2)), applied in L_h's eigenbasis."""
+    mu = spatial_eigenvalues(sp)
+    out = from_eigen(sp, np.exp(j * sp.dt * mu) * to_eigen(sp, u))
+    return out if np.iscomplexobj(u) else out.real
+
+
+# ---------------------------------------------------------------------------
+# Nonlinearity and the pointwise implicit solve of the IF scheme (Eq. (6.1)).
+# ---------------------------------------------------------------------------
+def nonlinearity(sp: Spec, u: np.ndarray) -> np.ndarray:
+    """N(u): zero for linear problems, u - u^3 for Allen-Cahn."""
+    if sp.nonlin == "none":
+        return np.zeros_like(u)
+    if sp.nonlin == "allen_cahn":
+        return u - u**3
+    raise ValueError(sp.nonlin)
+
+
+def pointwise_implicit_solve(sp: Spec, w: np.ndarray, bdt: float) -> np.ndarray:
+    """Solve u - bdt*N(u) = w pointwise (the implicit IF step of Eq. (6.1)).
+    For Allen-Cahn g(u) = u - bdt(u - u^3) - w is strictly increasing when
+    bdt < 1, so Newton from u = w converges to the unique root."""
+    if sp.nonlin == "none":
+        return w.copy()
+    if not bdt < 1.0:
+        raise ValueError("pointwise solve needs beta*dt < 1")
+    u = w.copy()
+    for _ in range(60):
+        g = u - bdt * (u - u**3) - w
+        dg = 1.0 - bdt + 3.0 * bdt * u**2
+        du = g / dg
+        u = u - du
+        if np.max(np.abs(du)) <= 1e-16 * max(1.0, float(np.max(np.abs(u)))):
+            break
+    return u
+
+
+# ---------------------------------------------------------------------------
+# Sequential time stepping: the exact solution of the all-at-once system.
+# ---------------------------------------------------------------------------
+def step_rhs(sp: Spec, U: np.ndarray, n: int, q: int, f: Optional[np.ndarray]) -> np.ndarray:
+    """w_n = sum_{j=1..q} a_j A^j u_{n-j} + beta_q dt f(t_n) of BDF-q."""
+    a, beta = bdf_float(q)
+    w = np.zeros(sp.n)
+    for j in range(1, q + 1):
+        w += a[j - 1] * apply_A_power(sp, U[n - j], j)
+    if f is not None:
+        w += beta * sp.dt * f[n - 1]
+    return w
+
+
+def sequential_solve(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None,
+                     U_start: Optional[np.ndarray] = None) -> np.ndarray:
+    """u_0..u_Nt by sequential exponential BDF stepping, shape (Nt+1, *n).
+
+    Steps n >= s use BDF-s (Eqs. (2.2), (4.1), (5.1), (5.3), (5.5), (5.7)).
+    The paper treats u_1..u_{s-1} as given (Eqs. (4.2), (5.2)-(5.8)); they are
+    taken from U_start (shape (s, *n), U_start[0] = u0) when supplied, else
+    from the ramp that steps u_n with BDF-n.  Each step solves
+    u_n - beta dt N(u_n) = sum_j a_j A^j u_{n-j} + beta dt f(t_n)."""
+    U = np.zeros((sp.Nt + 1,) + sp.n)
+    U[0] = u0
+    first = 1
+    if U_start is not None:
+        U[: sp.order] = U_start
+        first = sp.order
+    for n in range(first, sp.Nt + 1):
+        q = min(n, sp.order)
+        _, beta = bdf_float(q)
+        w = step_rhs(sp, U, n, q, f)
+        U[n] = pointwise_implicit_solve(sp, w, beta * sp.dt)
+    return U
+
+
+def startup_values(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None,
+                   U_start: Optional[np.ndarray] = None) -> np.ndarray:
+    """u_0..u_{s-1}: the given values, or u0 and the sequential ramp."""
+    if U_start is not None:
+        return np.array(U_start, dtype=float).reshape((sp.order,) + sp.n)
+    short = Spec(sp.bc, sp.n, sp.length, sp.a, sp.c, sp.nonlin, sp.dt, sp.order - 1,
+                 sp.alpha, sp.order)
+    if sp.order == 1:
+        return u0[None].copy()
+    return sequential_solve(short, u0, f)
+
+
+# ---------------------------------------------------------------------------
+# The all-at-once system (Eqs. (3.1), (4.2), (5.2), (5.4), (5.6), (5.8)).
+# Unknowns v = (u_s, ..., u_Nt): Ns = Nt - s + 1 slices; row i is time n = s+i.
+# ---------------------------------------------------------------------------
+def rhs_known(sp: Spec, U_start: np.ndarray, f: Optional[np.ndarray]) -> np.ndarray:
+    """The known right-hand side f_s: the startup terms a_j A^j u_{n-j} with
+    n-j < s (the printed f_2 .. f_6) plus beta_s dt f(t_n)."""
+    s = sp.order
+    a, beta = bdf_float(s)
+    b = np.zeros((sp.Ns,) + sp.n)
+    for i in range(sp.Ns):
+        n = s + i
+        if f is not None:
+            b[i] += beta * sp.dt * f[n - 1]
+        for j in range(1, s + 1):
+            if n - j < s:
+                b[i] += a[j - 1] * apply_A_power(sp, U_start[n - j], j)
+    return b
+
+
+def apply_R(sp: Spec, V: np.ndarray) -> np.ndarray:
+    """R_s v: row i is v_i - sum_{j=1..s, i-j>=0} a_j A^j v_{i-j}
+    (I - sum_j a_j C_{j-1} (x) A^j with the lower shifts C_{j-1})."""
+    a, _ = bdf_float(sp.order)
+    out = V.astype(np.result_type(V, np.float64)).copy()
+    for i in range(sp.Ns):
+        for j in range(1, sp.order + 1):
+            if i - j >= 0:
+                out[i] -= a[j - 1] * apply_A_power(sp, V[i - j], j)
+    return out
+
+
+def residual(sp: Spec, V: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """r = f_s + beta dt N(v) - R_s v (Eq. (3.2); the lagged nonlinear term of
+    Eq. (7.4) enters with the current iterate)."""
+    _, beta = bdf_float(sp.order)
+    return b + beta * sp.dt * nonlinearity(sp, V) - apply_R(sp, V)
+
+
+def time_eigenvalues(sp: Spec) -> np.ndarray:
+    """lambda_{0,n} = alpha^(1/Ns) e^{2 pi i (n-1)/Ns}, n = 1..Ns (Sec. 2)."""
+    Ns = sp.Ns
+    return sp.alpha ** (1.0 / Ns) * np.exp(2j * np.pi * np.arange(Ns) / Ns)
+
+
+def gamma_alpha(sp: Spec) -> np.ndarray:
+    """Diagonal of Gamma_alpha = diag(1, alpha^(1/Ns), ..., alpha^((Ns-1)/Ns))."""
+    return sp.alpha ** (np.arange(sp.Ns) / sp.Ns)
+
+
+def precond_apply(sp: Spec, r: np.ndarray) -> np.ndarray:
+    """s = P_alpha^{-1} r by the three steps of Eq. (3.3) / Eq. (4.5).
+
+    Step (a): S_a = (F (x) I)(Gamma_alpha (x) I) r, F the unitary DFT with
+              omega = e^{+2 pi i/Ns} (F x = sqrt(Ns) * numpy.ifft(x));
+    Step (b): S_b,n = (I - sum_j a_j lambda_n^j A^j)^{-1} S_a,n per slice
+              (lambda_{j-1,n} = lambda_{0,n}^j, Sec. 4 after Eq. (4.4)); the spatial solve
+              is diagonal in L_h's eigenbasis;
+    Step (c): s = (Gamma_alpha^{-1} (x) I)(F^* (x) I) S_b."""
+    Ns = sp.Ns
+    a, _ = bdf_float(sp.order)
+    gam = gamma_alpha(sp).reshape((Ns,) + (1,) * sp.ndim)
+    lam = time_eigenvalues(sp)
+    mu = spatial_eigenvalues(sp)
+    # Step (a)
+    Sa = np.sqrt(Ns) * np.fft.ifft(gam * r, axis=0)
+    # Step (b)
+    Sb = np.empty_like(Sa)
+    for n in range(Ns):
+        d = np.ones(sp.n, dtype=complex)
+        for j in range(1, sp.order + 1):
+            d -= a[j - 1] * lam[n] ** j * np.exp(j * sp.dt * mu)
+        Sb[n] = from_eigen(sp, to_eigen(sp, Sa[n]) / d)
+    # Step (c)
+    s = np.fft.fft(Sb, axis=0) / np.sqrt(Ns) / gam
+    return s.real
+
+
+# ---------------------------------------------------------------------------
+# Solvers.
+# ---------------------------------------------------------------------------
+@dataclass
+class SolveResult:
+    U: np.ndarray                 # (Nt+1, *n): u_0 .. u_Nt
+    iterations: int
+    history: List[float]          # relative update / residual norms per iteration
+    iterates: Optional[List[np.ndarray]] = None
+
+
+def assemble(sp: Spec, U_start: np.ndarray, V: np.ndarray) -> np.ndarray:
+    U = np.zeros((sp.Nt + 1,) + sp.n)
+    U[: sp.order] = U_start
+    U[sp.order:] = V
+    return U
+
+
+def richardson(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None,
+               max_iter: int = 50, tol: float = 0.0, keep_iterates: bool = False,
+               V0: Optional[np.ndarray] = None,
+               U_start: Optional[np.ndarray] = None) -> SolveResult:
+    """Preconditioned fixed-point iteration v^{k+1} = v^k + P_alpha^{-1}(f_s +
+    beta dt N(v^k) - R_s v^k) from v^0 = 0 (Eqs. (3.2), (4.4), (7.3)-(7.4);
+    Sec. 7 starts from zero).  Stops when max_n ||s_n|| <= tol * max_n ||v_n||
+    or after max_iter iterations."""
+    U_start = startup_values(sp, u0, f, U_start)
+    b = rhs_known(sp, U_start, f)
+    V = np.zeros((sp.Ns,) + sp.n) if V0 is None else V0.copy()
+    hist, its = [], []
+    k = 0
+    for k in range(1, max_iter + 1):
+        s = precond_apply(sp, residual(sp, V, b))
+        V = V + s
+        sn = np.sqrt((s.reshape(sp.Ns, -1) ** 2).sum(1)).max()
+        vn = np.sqrt((V.reshape(sp.Ns, -1) ** 2).sum(1)).max()
+        hist.append(sn / vn if vn > 0 else 0.0)
+        if keep_iterates:
+            its.append(V.copy())
+        if hist[-1] <= tol:
+            break
+    return SolveResult(assemble(sp, U_start, V), k, hist, its if keep_iterates else None)
+
+
+def gmres(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None, tol: float = 1e-10,
+          restart: int = 20, max_iter: int = 200,
+          U_start: Optional[np.ndarray] = None) -> SolveResult:
+    """Left-preconditioned restarted GMRES(m) with modified Gram-Schmidt on
+    P_alpha^{-1} R_s v = P_alpha^{-1} f_s (Sec. 3.2, Theorem 3.3), v^0 = 0.
+    Stops when ||P^{-1}(f_s - R_s v)|| <= tol * ||P^{-1} f_s||.
+    history[k] is that relative preconditioned residual after k iterations."""
+    if sp.nonlin != "none":
+        raise ValueError("GMRES is for linear problems")
+    U_start = startup_values(sp, u0, f, U_start)
+    b = rhs_known(sp, U_start, f)
+    shape = (sp.Ns,) + sp.n
+
+    def op(x):
+        return precond_apply(sp, apply_R(sp, x.reshape(shape))).ravel()
+
+    c = precond_apply(sp, b).ravel()
+    cn = np.linalg.norm(c)
+    x = np.zeros_like(c)
+    hist = [1.0]
+    total = 0
+    if cn == 0:
+        return SolveResult(assemble(sp, U_start, x.reshape(shape)), 0, hist)
+    while total < max_iter:
+        r = c - op(x)
+        beta = np.linalg.norm(r)
+        if beta <= tol * cn:
+            break
+        m = restart
+        Vb = np.zeros((m + 1, c.size))
+        H = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        Vb[0] = r / beta
+        j_done = 0
+        for j in range(m):
+            w = op(Vb[j])
+            for i in range(j + 1):                      # modified Gram-Schmidt
+                H[i, j] = np.dot(w, Vb[i])
+                w = w - H[i, j] * Vb[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0:
+                Vb[j + 1] = w / H[j + 1, j]
+            for i in range(j):                          # previous Givens rotations
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = math.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            total += 1
+            j_done = j + 1
+            hist.append(abs(g[j + 1]) / cn)
+            if abs(g[j + 1]) <= tol * cn or total >= max_iter:
+                break
+        y = scipy.linalg.solve_triangular(H[:j_done, :j_done], g[:j_done])
+        x = x + Vb[:j_done].T @ y
+        if hist[-1] <= tol:
+            break
+    return SolveResult(assemble(sp, U_start, x.reshape(shape)), total, hist)
+
+
+# ---------------------------------------------------------------------------
+# Error metric: L^inf(0,T; L^2) relative error (Sec. 7).
+# ---------------------------------------------------------------------------
+def rel_error(U: np.ndarray, Uref: np.ndarray) -> float:
+    """max_n ||u_n - u_n^ref||_2 / max_n ||u_n^ref||_2 over the given slices."""
+    d = (U - Uref).reshape(U.shape[0], -1)
+    r = Uref.reshape(Uref.shape[0], -1)
+    return float(np.sqrt((d**2).sum(1)).max() / np.sqrt((r**2).sum(1)).max())
+
+
+# ---------------------------------------------------------------------------
+# Dense brute force for tiny sizes (independent of the eigen-symbol path).
+# ---------------------------------------------------------------------------
+def dense_laplacian_1d(bc: str, n: int, L: float) -> np.ndarray:
+    """Periodic: the spectral second-derivative matrix of the periodic sinc
+    interpolant (even n): -pi^2/(3h^2) - 1/6 on the diagonal and
+    -(-1)^j / (2 sin^2(j h/2)) off it, for the grid spacing h = 2 pi/n, scaled
+    to length L.  Dirichlet: tridiag(1, -2, 1)/h^2 with h = L/(n+1)."""
+    if bc == PERIODIC:
+        if n % 2:
+            raise ValueError("even n only")
+        h = 2.0 * np.pi / n
+        col = np.empty(n)
+        col[0] = -np.pi**2 / (3.0 * h**2) - 1.0 / 6.0
+        j = np.arange(1, n)
+        col[1:] = -((-1.0) ** j) / (2.0 * np.sin(j * h / 2.0) ** 2)
+        return scipy.linalg.toeplitz(col) * (2.0 * np.pi / L) ** 2
+    h = L / (n + 1)
+    return (np.diag(-2.0 * np.ones(n)) + np.diag(np.ones(n - 1), 1)
+            + np.diag(np.ones(n - 1), -1)) / h**2
+
+
+def dense_Lh(sp: Spec) -> np.ndarray:
+    """L_h = a Delta_h - c I as an explicit matrix (row-major grid ordering)."""
+    mats = [dense_laplacian_1d(sp.bc, n, L) for n, L in zip(sp.n, sp.length)]
+    M = int(np.prod(sp.n))
+    lap = np.zeros((M, M))
+    for d, D in enumerate(mats):
+        term = np.ones((1, 1))
+        for e in range(sp.ndim):
+            term = np.kron(term, D if e == d else np.eye(sp.n[e]))
+        lap += term
+    return sp.a * lap - sp.c * np.eye(M)
+
+
+def dense_A(sp: Spec) -> np.ndarray:
+    """A = exp(dt L_h) by scipy's scaling-and-squaring expm."""
+    return scipy.linalg.expm(sp.dt * dense_Lh(sp))
+
+
+def shift_matrix(N: int, j: int, alpha: float = 0.0) -> np.ndarray:
+    """C_j (alpha = 0) or C_j^alpha: ones where row - col = j+1, and alpha on
+    the wrap-around entries row - col = j+1-N (top-right corner).
+    C_0^alpha is Eq. (2.4); C_1^alpha has alpha at (1, N-1) and (2, N)
+    (Sec. 4 after Eq. (4.4), 1-based); C_j^alpha for j >= 2 is read as
+    (C_0^alpha)^(j+1) (the entry lists printed in Sec. 5 are garbled)."""
+    C = np.zeros((N, N))
+    for r in range(N):
+        cidx = r - (j + 1)
+        if cidx >= 0:
+            C[r, cidx] = 1.0
+        else:
+            C[r, cidx + N] = alpha
+    return C
+
+
+def dense_R(sp: Spec, alpha: float = 0.0) -> np.ndarray:
+    """R_s (alpha = 0) or R_s^alpha = I - sum_j a_j C_{j-1}^alpha (x) A^j."""
+    a, _ = bdf_float(sp.order)
+    A = dense_A(sp)
+    M = A.shape[0]
+    Ns = sp.Ns
+    R = np.eye(Ns * M)
+    Aj = np.eye(M)
+    for j in range(1, sp.order + 1):
+        Aj = Aj @ A
+        R -= a[j - 1] * np.kron(shift_matrix(Ns, j - 1, alpha), Aj)
+    return R
+
+
+def dense_rhs(sp: Spec, U_start: np.ndarray, f: Optional[np.ndarray]) -> np.ndarray:
+    """f_s assembled with the dense A (the printed f_2..f_6 plus the source)."""
+    a, beta = bdf_float(sp.order)
+    A = dense_A(sp)
+    s = sp.order
+    M = A.shape[0]
+    b = np.zeros((sp.Ns, M))
+    for i in range(sp.Ns):
+        n = s + i
+        if f is not None:
+            b[i] += beta * sp.dt * f[n - 1].ravel()
+        for j in range(1, s + 1):
+            if n - j < s:
+                b[i] += a[j - 1] * (np.linalg.matrix_power(A, j) @ U_start[n - j].ravel())
+    return b.ravel()
+
+
+def dense_solve(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None) -> np.ndarray:
+    """u_0..u_Nt from the dense all-at-once system.  Linear: one LU solve of
+    R_s v = f_s.  Allen-Cahn: Newton on R_s v - beta dt N(v) = f_s with the
+    dense Jacobian.  The startup ramp is stepped with the dense A too."""
+    a, _ = bdf_float(sp.order)
+    A = dense_A(sp)
+    M = A.shape[0]
+    # dense startup ramp u_1..u_{s-1}
+    Us = [u0.ravel().copy()]
+    for n in range(1, sp.order):
+        an, bn = bdf_float(n)
+        w = sum(an[j - 1] * (np.linalg.matrix_power(A, j) @ Us[n - j]) for j in range(1, n + 1))
+        if f is not None:
+            w = w + bn * sp.dt * f[n - 1].ravel()
+        Us.append(_dense_pointwise(sp, w, bn * sp.dt))
+    U_start = np.array(Us).reshape((sp.order,) + sp.n)
+    b = dense_rhs(sp, U_start, f)
+    R = dense_R(sp)
+    _, beta = bdf_float(sp.order)
+    if sp.nonlin == "none":
+        v = scipy.linalg.lu_solve(scipy.linalg.lu_factor(R), b)
+    else:
+        v = np.linalg.solve(R, b)
+        for _ in range(50):
+            F = R @ v - beta * sp.dt * (v - v**3) - b
+            J = R - beta * sp.dt * np.diag(1.0 - 3.0 * v**2)
+            dv = np.linalg.solve(J, F)
+            v = v - dv
+            if np.max(np.abs(dv)) < 1e-15:
+                break
+    return assemble(sp, U_start, v.reshape((sp.Ns,) + sp.n))
+
+
+def _dense_pointwise(sp: Spec, w: np.ndarray, bdt: float) -> np.ndarray:
+    if sp.nonlin == "none":
+        return w
+    u = w.copy()
+    for _ in range(60):
+        du = (u - bdt * (u - u**3) - w) / (1.0 - bdt + 3.0 * bdt * u**2)
+        u = u - du
+        if np.max(np.abs(du)) < 1e-16:
+            break
+    return u
+
+
+def dense_precond_apply(sp: Spec, r: np.ndarray) -> np.ndarray:
+    """P_alpha^{-1} r by an LU solve with the explicit dense R_s^alpha."""
+    return np.linalg.solve(dense_R(sp, sp.alpha), r.ravel()).reshape(r.shape)
+
+
+def dense_iteration_matrix(sp: Spec) -> np.ndarray:
+    """I - (R_s^alpha)^{-1} R_s, the Richardson iteration matrix (Eq. (3.4))."""
+    R = dense_R(sp)
+    Ra = dense_R(sp, sp.alpha)
+    return np.eye(R.shape[0]) - np.linalg.solve(Ra, R)

@@ -1,0 +1,329 @@
+"""Pin checks for the CPU oracle, written as functions that return an error
+measure so that tests/test_oracle_pins.py can assert on them and
+tests/test_oracle_planted.py can show that a planted mistake trips them.
+
+Every check compares the oracle with something other than itself: a closed
+form, a value printed in the paper, an independent dense brute force (explicit
+L_h, scipy.linalg.expm, explicit alpha-circulant matrices, LU), or a textbook
+ODE solution.
+"""
+from __future__ import annotations
+
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def spec(bc="periodic", n=(8,), length=None, a=0.3, c=0.1, nonlin="none", dt=0.05, Nt=8,
+         alpha=0.05, order=1):
+    if length is None:
+        length = tuple(2 * math.pi if bc == "periodic" else 1.0 for _ in n)
+    return O.Spec(bc, tuple(n), tuple(length), a, c, nonlin, dt, Nt, alpha, order)
+
+
+def rng_field(sp, seed, lead=()):
+    return np.random.default_rng(seed).standard_normal(tuple(lead) + sp.n)
+
+
+# --- printed coefficients -------------------------------------------------
+def read_golden_bdf():
+    rows = {}
+    with open(os.path.join(GOLDEN, "bdf_coefficients.txt")) as fh:
+        for line in fh:
+            if not line.strip() or line.startswith("#"):
+                continue
+            tok = line.split()
+            s = int(tok[0])
+            rows[s] = [Fraction(t) for t in tok[1:1 + s]]
+    return rows
+
+
+def check_bdf_golden():
+    """Max |a_j(oracle) - a_j(paper)| over s = 1..6 (exact fractions)."""
+    worst = Fraction(0)
+    for s, printed in read_golden_bdf().items():
+        a, _ = O.bdf_coefficients(s)
+        worst = max(worst, max(abs(x - y) for x, y in zip(a, printed)))
+    return float(worst)
+
+
+# --- spatial operator -----------------------------------------------------
+def check_A_vs_dense(sp, seed=0):
+    """Relative difference of the oracle's A^j u (eigen-symbol path) and the
+    dense expm of the explicit L_h, j = 1..3."""
+    A = O.dense_A(sp)
+    u = rng_field(sp, seed)
+    worst = 0.0
+    Aj = np.eye(A.shape[0])
+    for j in range(1, 4):
+        Aj = Aj @ A
+        ref = (Aj @ u.ravel()).reshape(sp.n)
+        got = O.apply_A_power(sp, u, j)
+        worst = max(worst, np.abs(got - ref).max() / np.abs(ref).max())
+    return worst
+
+
+# --- all-at-once pieces ---------------------------------------------------
+def check_apply_R_vs_dense(sp, seed=1):
+    V = rng_field(sp, seed, (sp.Ns,))
+    ref = (O.dense_R(sp) @ V.ravel()).reshape(V.shape)
+    return np.abs(O.apply_R(sp, V) - ref).max() / np.abs(ref).max()
+
+
+def check_precond_vs_dense(sp, seed=2):
+    r = rng_field(sp, seed, (sp.Ns,))
+    ref = O.dense_precond_apply(sp, r)
+    return np.abs(O.precond_apply(sp, r) - ref).max() / np.abs(ref).max()
+
+
+def check_sequential_vs_dense(sp, seed=3, forcing=True):
+    rng = np.random.default_rng(seed)
+    u0 = rng.uniform(-0.8, 0.8, size=sp.n)
+    f = rng.standard_normal((sp.Nt,) + sp.n) if forcing else None
+    U = O.sequential_solve(sp, u0, f)
+    Ud = O.dense_solve(sp, u0, f)
+    return O.rel_error(U[1:], Ud[1:])
+
+
+def check_rhs_vs_dense(sp, seed=4):
+    rng = np.random.default_rng(seed)
+    u0 = rng.standard_normal(sp.n)
+    f = rng.standard_normal((sp.Nt,) + sp.n)
+    Us = O.startup_values(sp, u0, f)
+    ref = O.dense_rhs(sp, Us, f).reshape((sp.Ns,) + sp.n)
+    return np.abs(O.rhs_known(sp, Us, f) - ref).max() / np.abs(ref).max()
+
+
+# --- alpha-circulant structure -------------------------------------------
+def check_alpha_circulant(N=7, alpha=0.3):
+    """C_0^alpha = P_alpha D_0 P_alpha^{-1} with P_alpha = Gamma^{-1} F^* (Sec. 2),
+    lambda_{1,n} = lambda_{0,n}^2 diagonalises C_1^alpha (Sec. 4), C_1^alpha
+    has alpha exactly at (1, N-1), (2, N) (1-based), and C_j^alpha =
+    (C_0^alpha)^(j+1)."""
+    sp = O.Spec("periodic", (4,), (1.0,), 1.0, 0.0, "none", 0.1, N, alpha, 1)
+    gam = O.gamma_alpha(sp)
+    lam = O.time_eigenvalues(sp)
+    w = np.exp(2j * np.pi / N)
+    F = np.array([[w ** (l * k) for k in range(N)] for l in range(N)]) / np.sqrt(N)
+    P = np.diag(1.0 / gam) @ F.conj().T
+    Pinv = np.linalg.inv(P)
+    C0 = O.shift_matrix(N, 0, alpha)
+    C1 = O.shift_matrix(N, 1, alpha)
+    err = np.abs(P @ np.diag(lam) @ Pinv - C0).max()
+    err = max(err, np.abs(P @ np.diag(lam**2) @ Pinv - C1).max())
+    printed = np.zeros((N, N))
+    for r in range(2, N):
+        printed[r, r - 2] = 1.0
+    printed[0, N - 2] = alpha
+    printed[1, N - 1] = alpha
+    err = max(err, np.abs(C1 - printed).max())
+    for j in range(6):
+        err = max(err, np.abs(O.shift_matrix(N, j, alpha)
+                              - np.linalg.matrix_power(C0, j + 1)).max())
+    # the printed lambda_{1,n} formula
+    lam1 = alpha ** (2.0 / N) * np.exp(4j * np.pi * np.arange(N) / N)
+    err = max(err, np.abs(lam1 - lam**2).max())
+    return err
+
+
+# --- spectra of the iteration matrix -------------------------------------
+def predicted_iteration_spectrum(sp):
+    """Non-zero eigenvalues -alpha z^N/(1 - alpha z^N) per spatial mode, z the
+    roots of zeta^s - sum_j a_j E^j zeta^(s-j), N = Ns.  For s = 1 this is
+    Theorem 3.1 (Eq. (3.6)); for s = 2 Theorem 4.1 (z = E, E/3)."""
+    mu = O.spatial_eigenvalues(sp).ravel()
+    a, _ = O.bdf_float(sp.order)
+    out = []
+    for m in mu:
+        E = math.exp(sp.dt * m)
+        coef = [1.0] + [-a[j - 1] * E**j for j in range(1, sp.order + 1)]
+        for z in np.roots(coef):
+            zN = z ** sp.Ns
+            out.append(-sp.alpha * zN / (1 - sp.alpha * zN))
+    return np.array(out)
+
+
+def theorem_spectrum(sp):
+    """The printed closed forms: Theorem 3.1 (s = 1) and Theorem 4.1 (s = 2)."""
+    mu = O.spatial_eigenvalues(sp).ravel()
+    out = []
+    for m in mu:
+        z = sp.dt * m
+        if sp.order == 1:
+            q = sp.alpha * math.exp(z * sp.Nt)
+            out.append(-q / (1 - q))
+        elif sp.order == 2:
+            N1 = sp.Nt - 1
+            q1 = sp.alpha * math.exp(N1 * z)
+            q2 = sp.alpha * (math.exp(z) / 3.0) ** N1
+            out += [-q1 / (1 - q1), -q2 / (1 - q2)]
+        else:
+            raise ValueError
+    return np.array(out)
+
+
+def match_multisets(got, want):
+    """Max distance after greedy matching of two small complex multisets."""
+    got = list(got)
+    worst = 0.0
+    for w in want:
+        i = int(np.argmin([abs(g - w) for g in got]))
+        worst = max(worst, abs(got[i] - w))
+        got.pop(i)
+    return worst
+
+
+def check_iteration_spectrum(sp, closed_form="theorem"):
+    """Distance between the dense iteration matrix's non-zero spectrum and the
+    predicted one; plus the size of the eigenvalues that must be zero."""
+    ev = np.linalg.eigvals(O.dense_iteration_matrix(sp))
+    want = theorem_spectrum(sp) if closed_form == "theorem" else predicted_iteration_spectrum(sp)
+    order = np.argsort(-np.abs(ev))
+    big = ev[order[: len(want)]]
+    rest = ev[order[len(want):]]
+    scale = max(1e-300, np.abs(want).max())
+    return max(match_multisets(big, want) / scale, (np.abs(rest).max() if rest.size else 0.0) / scale)
+
+
+# --- closed-form solutions ----------------------------------------------
+def check_heat_exact(Nx=64, Nt=16, seed=1):
+    """Spectral exponential Euler for u_t = u_xx on [0, 2 pi) is exact in time:
+    u(x, t) = sum_k e^{-k^2 t}(a_k cos kx + b_k sin kx)/k^2, evaluated directly."""
+    sp = O.Spec("periodic", (Nx,), (2 * math.pi,), 1.0, 0.0, "none", 1.0 / Nt, Nt, 1e-2, 1)
+    rng = np.random.default_rng(seed)
+    ak, bk = rng.standard_normal(16), rng.standard_normal(16)
+    x = np.arange(Nx) * 2 * math.pi / Nx
+    def exact(t):
+        return sum(math.exp(-k * k * t) * (ak[k - 1] * np.cos(k * x) + bk[k - 1] * np.sin(k * x)) / k**2
+                   for k in range(1, 17))
+    U = O.sequential_solve(sp, exact(0.0))
+    Ue = np.array([exact(n * sp.dt) for n in range(Nt + 1)])
+    return O.rel_error(U[1:], Ue[1:])
+
+
+def check_richardson_closed_form(k_mode=3, iters=4, Nx=16, Nt=8, alpha=0.2):
+    """First-order Richardson from zero on u0 = cos(k x): the k-th iterate is
+    (1 - (-q)^k) E^n u0 with E = e^{dt mu}, q = alpha E^Nt/(1 - alpha E^Nt)
+    (from the error recursion of Sec. 2, Eqs. (2.5)-(2.6))."""
+    sp = O.Spec("periodic", (Nx,), (2 * math.pi,), 0.05, 0.02, "none", 0.1, Nt, alpha, 1)
+    x = np.arange(Nx) * 2 * math.pi / Nx
+    u0 = np.cos(k_mode * x)
+    res = O.richardson(sp, u0, max_iter=iters, keep_iterates=True)
+    mu = -0.05 * k_mode**2 - 0.02
+    E = math.exp(sp.dt * mu)
+    q = alpha * E**Nt / (1 - alpha * E**Nt)
+    worst = 0.0
+    for k, V in enumerate(res.iterates, start=1):
+        want = np.array([(1 - (-q) ** k) * E**n * u0 for n in range(1, Nt + 1)])
+        worst = max(worst, np.abs(V - want).max())
+    return worst
+
+
+def logistic_exact(u0, t):
+    """Exact solution of u' = u - u^3."""
+    return u0 * math.exp(t) / math.sqrt(1 - u0**2 + u0**2 * math.exp(2 * t))
+
+
+def check_nonlinear_order(order, c0=0.4, T=0.5):
+    """IF-BDF-s on a spatially constant Allen-Cahn state reduces to BDF-s for
+    u' = u - u^3 (A acts as 1 on constants when c = 0).  Returns the observed
+    convergence order from dt = T/40 -> T/80 (must be ~ s)."""
+    errs = []
+    for Nt in (40, 80):
+        sp = O.Spec("periodic", (4,), (1.0,), 1e-3, 0.0, "allen_cahn", T / Nt, Nt, 1e-3, order)
+        start = np.array([np.full(sp.n, logistic_exact(c0, n * sp.dt)) for n in range(order)])
+        U = O.sequential_solve(sp, np.full(sp.n, c0), U_start=start)
+        errs.append(abs(U[-1, 0] - logistic_exact(c0, T)))
+    return math.log2(errs[0] / errs[1])
+
+
+def check_forced_order(order, k=2, T=0.5):
+    """Linear heat with source e^{-t} cos(kx) on [0, 2pi): the exact Fourier
+    coefficient is y(t) = e^{mu t} y0 + (e^{mu t} - e^{-t})/(mu + 1).  Returns
+    the observed convergence order of the scheme (must be ~ s)."""
+    errs = []
+    a = 0.05
+    mu = -a * k * k
+    for Nt in (40, 80):
+        sp = O.Spec("periodic", (8,), (2 * math.pi,), a, 0.0, "none", T / Nt, Nt, 1e-3, order)
+        x = np.arange(8) * 2 * math.pi / 8
+        f = np.array([math.exp(-(n + 1) * sp.dt) * np.cos(k * x) for n in range(Nt)])
+        def y_of(t):
+            return math.exp(mu * t) + (math.exp(mu * t) - math.exp(-t)) / (mu + 1.0)
+        start = np.array([y_of(n * sp.dt) * np.cos(k * x) for n in range(order)])
+        U = O.sequential_solve(sp, np.cos(k * x), f, U_start=start)
+        y = y_of(T)
+        errs.append(abs(U[-1] @ np.cos(k * x) / 4.0 - y))
+    return math.log2(errs[0] / errs[1])
+
+
+def check_dirichlet_single_mode(order=2, n=(6, 5), p=(2, 3), Nt=10):
+    """A grid sine mode is an exact eigenvector of the 5-point Laplacian with
+    eigenvalue -(4a/h^2) sum_d sin^2(p_d pi h_d/2) - c; with the source
+    e^{-t} times that mode the whole solution stays on it.  Compares with the
+    scalar BDF-s recursion for the mode amplitude."""
+    a, c, dt = 0.7, 0.2, 0.01
+    sp = O.Spec("dirichlet", n, (1.0, 1.0), a, c, "none", dt, Nt, 1e-3, order)
+    xs = [np.arange(1, m + 1) / (m + 1) for m in n]
+    X, Y = np.meshgrid(*xs, indexing="ij")
+    mode = np.sin(p[0] * np.pi * X) * np.sin(p[1] * np.pi * Y)
+    lam = -c
+    for m, pd in zip(n, p):
+        h = 1.0 / (m + 1)
+        lam -= a * (4.0 / h**2) * math.sin(pd * math.pi * h / 2) ** 2
+    E = math.exp(dt * lam)
+    f = np.array([math.exp(-(k + 1) * dt) * mode for k in range(Nt)])
+    U = O.sequential_solve(sp, mode, f)
+    y = [1.0]
+    for m in range(1, Nt + 1):
+        q = min(m, order)
+        aa, bb = O.bdf_coefficients(q)
+        y.append(sum(float(aa[j - 1]) * E**j * y[m - j] for j in range(1, q + 1))
+                 + float(bb) * dt * math.exp(-m * dt))
+    want = np.array([yy * mode for yy in y])
+    return np.abs(U - want).max()
+
+
+# --- convergence theory ---------------------------------------------------
+def check_thm21_contraction(Nx=16, Nt=12, alpha=0.05, iters=5):
+    """Ratio of successive errors max_n ||e_n^k|| must not exceed the factor
+    |alpha| e^{lambda_max T}/(1 - |alpha| e^{lambda_max T}) of Theorem 2.1;
+    returns (max observed ratio) / (bound)."""
+    sp = O.Spec("dirichlet", (Nx,), (1.0,), 0.02, 0.5, "none", 0.05, Nt, alpha, 1)
+    u0 = np.random.default_rng(5).standard_normal(sp.n)
+    ref = O.sequential_solve(sp, u0)[1:]
+    res = O.richardson(sp, u0, max_iter=iters, keep_iterates=True)
+    errs = [np.sqrt(((ref) ** 2).reshape(Nt, -1).sum(1)).max()]
+    for V in res.iterates:
+        errs.append(np.sqrt(((V - ref) ** 2).reshape(Nt, -1).sum(1)).max())
+    lam_max = O.spatial_eigenvalues(sp).max()
+    T = sp.dt * Nt
+    bound = alpha * math.exp(lam_max * T) / (1 - alpha * math.exp(lam_max * T))
+    ratios = [errs[k] / errs[k - 1] for k in range(1, len(errs))]
+    return max(ratios) / bound
+
+
+def check_gmres_terminates(sp, seed=6):
+    """Number of GMRES iterations to reach 1e-12 (Theorem 3.3: <= Nx + 1 for
+    s = 1; Theorem 4.3: <= 2 Nx + 1 for s = 2)."""
+    rng = np.random.default_rng(seed)
+    u0 = rng.standard_normal(sp.n)
+    f = rng.standard_normal((sp.Nt,) + sp.n)
+    res = O.gmres(sp, u0, f, tol=1e-12, restart=200, max_iter=200)
+    return res.iterations, res
+
+
+def check_gmres_elman(sp, seed=7):
+    """max_k ||r_k|| / ((4 alpha (1 - alpha))^{k/2} ||r_0||) for the
+    preconditioned GMRES residuals (Theorem 3.14); must be <= 1."""
+    rng = np.random.default_rng(seed)
+    u0 = rng.standard_normal(sp.n)
+    res = O.gmres(sp, u0, None, tol=1e-14, restart=50, max_iter=30)
+    q = 4 * sp.alpha * (1 - sp.alpha)
+    return max(h / q ** (k / 2) for k, h in enumerate(res.history))

@@ -1,0 +1,219 @@
+"""The CPU oracle pinned against things other than itself (runs without a GPU).
+
+Each test names what fixes the expected value: a coefficient the paper prints,
+a closed-form solution, a theorem's spectrum, or an independent dense brute
+force (explicit L_h, scipy.linalg.expm, explicit alpha-circulant matrices, LU).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import oracle_checks as C
+
+SPATIAL_CASES = [
+    C.spec("periodic", (8,)),
+    C.spec("periodic", (4, 6), length=(1.0, 1.5), a=0.02),
+    C.spec("dirichlet", (7,)),
+    C.spec("dirichlet", (4, 5), a=0.01),
+]
+
+
+def test_bdf_coefficients_match_paper():
+    # Eq. (2.2), Eq. (4.1), Eqs. (5.1), (5.3), (5.5), (5.7)
+    assert C.check_bdf_golden() == 0.0
+    # beta_1 = 1 is the coefficient of dt N(u_n) in Eq. (6.1)
+    assert O.bdf_coefficients(1)[1] == 1
+
+
+@pytest.mark.parametrize("sp", SPATIAL_CASES, ids=lambda s: f"{s.bc}{s.n}")
+def test_A_matches_dense_expm(sp):
+    # A = exp(dt L_h) (Eq. (2.2)): eigen-symbol path vs expm of the explicit matrix
+    assert C.check_A_vs_dense(sp) < 1e-12
+
+
+def test_periodic_symbol_includes_nyquist():
+    sp = C.spec("periodic", (8,), length=(2 * math.pi,), a=1.0, c=0.0)
+    ev = np.sort(np.linalg.eigvalsh(O.dense_Lh(sp)))
+    assert np.allclose(ev, np.sort(O.spatial_eigenvalues(sp)), atol=1e-12)
+    assert np.isclose(ev.min(), -16.0)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 6])
+@pytest.mark.parametrize("bc", ["periodic", "dirichlet"])
+def test_apply_R_and_rhs_match_dense(order, bc):
+    sp = C.spec(bc, (6,), Nt=order + 5, order=order)
+    assert C.check_apply_R_vs_dense(sp) < 1e-12
+    assert C.check_rhs_vs_dense(sp) < 1e-12
+
+
+def test_alpha_circulant_structure():
+    # Sec. 2 (P_alpha = Gamma^{-1} F^*), Sec. 4 (C_1^alpha entries, lambda_1 = lambda_0^2)
+    assert C.check_alpha_circulant() < 1e-13
+
+
+@pytest.mark.parametrize("order", [1, 2, 6])
+@pytest.mark.parametrize("sp0", SPATIAL_CASES, ids=lambda s: f"{s.bc}{s.n}")
+def test_precond_three_steps_match_dense_solve(order, sp0):
+    # Eq. (3.3) / Eq. (4.5): the three steps equal an LU solve with R_s^alpha
+    sp = O.Spec(sp0.bc, sp0.n, sp0.length, sp0.a, sp0.c, "none", sp0.dt, order + 6, 0.07, order)
+    assert C.check_precond_vs_dense(sp) < 1e-10
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 6])
+@pytest.mark.parametrize("bc,nonlin", [("periodic", "none"), ("dirichlet", "none"),
+                                       ("periodic", "allen_cahn"), ("dirichlet", "allen_cahn")])
+def test_sequential_equals_dense_all_at_once(order, bc, nonlin):
+    sp = C.spec(bc, (6,), nonlin=nonlin, Nt=order + 5, order=order, dt=0.02)
+    assert C.check_sequential_vs_dense(sp, forcing=True) < 1e-12
+
+
+def test_sequential_equals_dense_2d_nonlinear():
+    sp = C.spec("periodic", (4, 4), length=(1.0, 1.0), a=0.01, c=0.0, nonlin="allen_cahn",
+                Nt=8, order=2, dt=0.01)
+    assert C.check_sequential_vs_dense(sp, forcing=False) < 1e-12
+
+
+def test_heat_exact_in_time():
+    # spectral exponential Euler reproduces e^{-k^2 t} exactly
+    assert C.check_heat_exact() < 1e-13
+
+
+def test_richardson_iterates_closed_form():
+    # u^k_n = (1 - (-q)^k) E^n u0, q = alpha E^Nt / (1 - alpha E^Nt)
+    assert C.check_richardson_closed_form() < 1e-13
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("bc", ["periodic", "dirichlet"])
+def test_iteration_spectrum_theorems(order, bc):
+    # Theorem 3.1 (Eq. (3.6)) and Theorem 4.1
+    sp = C.spec(bc, (5,) if bc == "dirichlet" else (6,), Nt=7, order=order, alpha=0.1, a=0.05)
+    assert C.check_iteration_spectrum(sp, "theorem") < 1e-8
+
+
+@pytest.mark.parametrize("order", [3, 6])
+def test_iteration_spectrum_order_s(order):
+    # generalisation of Theorems 3.1/4.1: roots of zeta^s - sum a_j E^j zeta^{s-j}
+    sp = C.spec("dirichlet", (3,), Nt=order + 6, order=order, alpha=0.2, a=0.02, dt=0.1)
+    assert C.check_iteration_spectrum(sp, "general") < 1e-6
+
+
+def test_iteration_spectrum_general_reduces_to_theorems():
+    for order in (1, 2):
+        sp = C.spec("periodic", (6,), Nt=7, order=order, alpha=0.1)
+        got = np.sort_complex(C.predicted_iteration_spectrum(sp))
+        want = np.sort_complex(C.theorem_spectrum(sp).astype(complex))
+        assert np.abs(got - want).max() < 1e-14
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_forced_convergence_order(order):
+    # IF-BDF-s with beta_s dt f(t_n) is consistent of order s
+    p = C.check_forced_order(order)
+    assert abs(p - order) < 0.25, p
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
+def test_nonlinear_convergence_order(order):
+    # IF-BDF-s with beta_s dt N(u_n) on u' = u - u^3 (exact logistic-type solution)
+    p = C.check_nonlinear_order(order)
+    assert abs(p - order) < 0.3, p
+
+
+@pytest.mark.parametrize("order", [1, 2, 6])
+def test_dirichlet_single_sine_mode(order):
+    assert C.check_dirichlet_single_mode(order) < 1e-13
+
+
+def test_allen_cahn_constant_state_high_precision():
+    # constant state: each grid point follows u_n - dt(u_n - u_n^3) = u_{n-1};
+    # compare with a 40-digit scalar Newton solve.
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    sp = C.spec("periodic", (4, 4), length=(1.0, 1.0), a=0.01, c=0.0, nonlin="allen_cahn",
+                Nt=12, order=1, dt=0.01)
+    U = O.sequential_solve(sp, np.full(sp.n, 0.3))
+    u = mp.mpf("0.3")
+    dt = mp.mpf("0.01")
+    for n in range(1, 13):
+        w = u
+        x = w
+        for _ in range(60):
+            x = x - (x - dt * (x - x**3) - w) / (1 - dt + 3 * dt * x**2)
+        u = x
+        assert abs(U[n, 1, 2] - float(u)) < 1e-16
+
+
+def test_thm21_contraction_bound():
+    r = C.check_thm21_contraction()
+    assert r <= 1.0 + 1e-9, r
+
+
+@pytest.mark.parametrize("bc", ["periodic", "dirichlet"])
+def test_gmres_terminates_thm33(bc):
+    # Theorem 3.3: at most Nx + 1 iterations (first order)
+    sp = C.spec(bc, (5,) if bc == "dirichlet" else (6,), Nt=9, order=1, alpha=0.5, a=0.3)
+    its, res = C.check_gmres_terminates(sp)
+    assert its <= int(np.prod(sp.n)) + 1
+    assert res.history[-1] < 1e-12
+
+
+def test_gmres_terminates_thm43():
+    # Theorem 4.3: at most 2 Nx + 1 iterations (second order)
+    sp = C.spec("dirichlet", (4,), Nt=9, order=2, alpha=0.5, a=0.3)
+    its, res = C.check_gmres_terminates(sp)
+    assert its <= 2 * int(np.prod(sp.n)) + 1
+
+
+def test_gmres_elman_bound_thm314():
+    sp = C.spec("dirichlet", (8,), Nt=10, order=1, alpha=0.2, a=0.01, c=0.0)
+    assert C.check_gmres_elman(sp) <= 1.0 + 1e-12
+
+
+@pytest.mark.parametrize("order", [1, 2, 6])
+def test_gmres_and_richardson_reach_sequential(order):
+    sp = C.spec("periodic", (4, 4), length=(1.0, 1.0), a=0.05, c=0.1, Nt=order + 9,
+                order=order, alpha=1e-3, dt=0.02)
+    rng = np.random.default_rng(order)
+    u0 = rng.standard_normal(sp.n)
+    f = rng.standard_normal((sp.Nt,) + sp.n)
+    ref = O.sequential_solve(sp, u0, f)
+    g = O.gmres(sp, u0, f, tol=1e-13)
+    r = O.richardson(sp, u0, f, max_iter=8)
+    assert O.rel_error(g.U[1:], ref[1:]) < 1e-12
+    assert O.rel_error(r.U[1:], ref[1:]) < 1e-12
+
+
+def test_lagged_nonlinear_richardson_reaches_sequential():
+    # Eqs. (7.3)-(7.4) and their order-s extension
+    for order in (1, 2, 6):
+        sp = C.spec("periodic", (8, 8), length=(1.0, 1.0), a=0.0025, c=0.0,
+                    nonlin="allen_cahn", Nt=order + 15, order=order, alpha=1e-3, dt=1e-3)
+        u0 = np.random.default_rng(10 + order).uniform(-0.9, 0.9, sp.n)
+        ref = O.sequential_solve(sp, u0)
+        r = O.richardson(sp, u0, max_iter=30, tol=1e-15)
+        assert O.rel_error(r.U[1:], ref[1:]) < 1e-12
+
+
+def test_one_iteration_claim_long_window():
+    # Sec. 7.1: T = 64 with dt = h = 1/128, 1,048,576 unknowns, one iteration.
+    claims = {}
+    with open(C.os.path.join(C.GOLDEN, "paper_claims.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()[:2]
+                claims[k] = float(v)
+    dt = claims["one_iteration_dt"]
+    Nt = int(round(claims["one_iteration_T"] / dt))
+    nx = int(claims["one_iteration_unknowns"]) // Nt
+    L = (nx + 1) * dt                          # h = L/(nx+1) = 1/128
+    sp = O.Spec("dirichlet", (nx,), (L,), claims["one_iteration_a"], claims["one_iteration_c"],
+                "none", dt, Nt, claims["alpha_opt"], 1)
+    x = np.arange(1, nx + 1) * L / (nx + 1)
+    u0 = np.exp(-30 * (x - L / 2) ** 2)
+    assert nx * Nt == 1048576
+    ref = O.sequential_solve(sp, u0)
+    r = O.richardson(sp, u0, max_iter=1)
+    assert O.rel_error(r.U[1:], ref[1:]) < claims["one_iteration_tol"]

@@ -1,0 +1,127 @@
+"""Plant plausible mistakes in the CPU oracle and check that a pin catches each.
+
+A mistake is planted by monkeypatching one oracle function for the duration of
+one test (on the CPU only); the matching pin from tests/oracle_checks.py must
+then exceed the tolerance that tests/test_oracle_pins.py asserts.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.expd_oracle as E
+from tests import oracle_checks as C
+
+
+def patch(monkeypatch, name, fn):
+    monkeypatch.setattr(E, name, fn)
+    monkeypatch.setattr(O, name, fn)
+
+
+def precond_variant(conj_omega=False, gamma_den=0, no_power=False, drop_gamma_inverse=False):
+    def precond_apply(sp, r):
+        Ns = sp.Ns
+        a, _ = E.bdf_float(sp.order)
+        gam = (sp.alpha ** (np.arange(Ns) / (Ns + gamma_den))).reshape((Ns,) + (1,) * sp.ndim)
+        lam = E.time_eigenvalues(sp)
+        mu = E.spatial_eigenvalues(sp)
+        fwd = np.fft.fft if conj_omega else np.fft.ifft
+        inv = np.fft.ifft if conj_omega else np.fft.fft
+        scale = (1.0 / Ns) if conj_omega else 1.0
+        Sa = np.sqrt(Ns) * fwd(gam * r, axis=0) * scale
+        Sb = np.empty_like(Sa)
+        for n in range(Ns):
+            d = np.ones(sp.n, dtype=complex)
+            for j in range(1, sp.order + 1):
+                d -= a[j - 1] * (lam[n] if no_power else lam[n] ** j) * np.exp(j * sp.dt * mu)
+            Sb[n] = E.from_eigen(sp, E.to_eigen(sp, Sa[n]) / d)
+        s = inv(Sb, axis=0) / np.sqrt(Ns) / scale
+        if not drop_gamma_inverse:
+            s = s / gam
+        return s.real
+    return precond_apply
+
+
+SP6 = O.Spec("periodic", (4, 6), (1.0, 1.5), 0.02, 0.1, "none", 0.05, 12, 0.07, 6)
+SP2 = O.Spec("dirichlet", (5,), (1.0,), 0.3, 0.1, "none", 0.05, 9, 0.07, 2)
+
+
+@pytest.mark.parametrize("kw", [dict(conj_omega=True), dict(gamma_den=-1), dict(no_power=True),
+                                dict(drop_gamma_inverse=True)],
+                         ids=["omega_sign", "gamma_root", "lambda_power", "gamma_inverse"])
+def test_planted_precond_mistakes_are_caught(monkeypatch, kw):
+    patch(monkeypatch, "precond_apply", precond_variant(**kw))
+    assert max(C.check_precond_vs_dense(SP6), C.check_precond_vs_dense(SP2)) > 1e-6
+
+
+def test_planted_wrong_shift_direction_is_caught(monkeypatch):
+    def apply_R(sp, V):
+        a, _ = E.bdf_float(sp.order)
+        out = V.copy()
+        for i in range(sp.Ns):
+            for j in range(1, sp.order + 1):
+                if i + j < sp.Ns:                      # transposed shift
+                    out[i] -= a[j - 1] * E.apply_A_power(sp, V[i + j], j)
+        return out
+    patch(monkeypatch, "apply_R", apply_R)
+    assert C.check_apply_R_vs_dense(SP2) > 1e-3
+
+
+def test_planted_dropped_startup_term_is_caught(monkeypatch):
+    orig = E.rhs_known
+
+    def rhs_known(sp, U_start, f):
+        return orig(sp, U_start[:1].repeat(sp.order, axis=0) * 0 + U_start[-1:], f)
+    patch(monkeypatch, "rhs_known", rhs_known)
+    sp = C.spec("periodic", (6,), Nt=9, order=3)
+    assert C.check_rhs_vs_dense(sp) > 1e-3
+
+
+def test_planted_wrong_nyquist_symbol_is_caught(monkeypatch):
+    def spatial_eigenvalues(sp):
+        parts = []
+        for n, L in zip(sp.n, sp.length):
+            k = np.arange(n)                            # forgot the negative frequencies
+            parts.append(-(2.0 * np.pi * k / L) ** 2)
+        return sp.a * sum(np.meshgrid(*parts, indexing="ij")) - sp.c
+    patch(monkeypatch, "spatial_eigenvalues", spatial_eigenvalues)
+    assert C.check_A_vs_dense(C.spec("periodic", (8,))) > 1e-3
+
+
+def test_planted_missing_beta_on_source_is_caught(monkeypatch):
+    def step_rhs(sp, U, n, q, f):
+        a, beta = E.bdf_float(q)
+        w = np.zeros(sp.n)
+        for j in range(1, q + 1):
+            w += a[j - 1] * E.apply_A_power(sp, U[n - j], j)
+        if f is not None:
+            w += sp.dt * f[n - 1]                      # beta dropped
+        return w
+    patch(monkeypatch, "step_rhs", step_rhs)
+    assert abs(C.check_forced_order(2) - 2) > 0.5
+
+
+def test_planted_wrong_bdf_coefficient_is_caught(monkeypatch):
+    orig = E.bdf_coefficients
+
+    def bdf_coefficients(s):
+        a, beta = orig(s)
+        if s >= 2:
+            a = list(a)
+            a[1] = -a[1]
+        return a, beta
+    patch(monkeypatch, "bdf_coefficients", bdf_coefficients)
+    assert C.check_bdf_golden() > 0
+
+
+def test_planted_wrong_nonlinear_sign_is_caught(monkeypatch):
+    def nonlinearity(sp, u):
+        return u + u**3 if sp.nonlin == "allen_cahn" else np.zeros_like(u)
+    patch(monkeypatch, "nonlinearity", nonlinearity)
+    sp = C.spec("periodic", (6,), nonlin="allen_cahn", Nt=8, order=1, dt=0.02)
+    # sequential (pointwise Newton) vs dense Newton: both use their own N, so
+    # the Richardson fixed point (which uses nonlinearity) moves off the
+    # sequential solution.
+    u0 = np.random.default_rng(0).uniform(-0.8, 0.8, sp.n)
+    ref = O.sequential_solve(sp, u0)
+    r = O.richardson(sp, u0, max_iter=30)
+    assert O.rel_error(r.U[1:], ref[1:]) > 1e-6
