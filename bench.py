@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Exp-ParaDiag benchmark: space-time unknowns per second to 1e-8 relative error.
+
+Workload (one "step" = one whole solve of one batch of synthetic input): 2D
+periodic Allen-Cahn u_t = eps^2 Lap u + u - u^3, eps = 0.05, 256 x 256 grid,
+Nt = 64, dt = 1e-3, exponential Euler (s = 1), lagged nonlinear Exp-ParaDiag
+fixed point with alpha = 1e-3, u0 ~ U(-0.9, 0.9) seeded, tol 1e-8.  Every step
+runs the whole hot path: the lagged N evaluation through the spatial FFTs, the
+float64 residual, the alpha-scaled time DFT, the shifted solves, the inverse
+time DFT and the update, until the convergence test passes, then the solution
+returns to physical space.
+
+  value      whole-job unknowns/s of the mixed-precision path, inputs resident
+             in HBM, L2 flushed (256 MiB write) between timed steps
+  e2e        the same through the C ABI with pinned host buffers (u0 in, U out)
+  fp64_path  the plain float64 GPU path on the same workload (for the speedup)
+  roofline   the dominant kernel class from CUDA events on its launch stream
+  cpu_baseline  the CPU oracle (tests' reference), one full solve, host cores
+
+Launch: python bench.py [--gpus N --steps K --warmup W] (N > 1 under torchrun:
+every rank solves its own seeded problem, no collective on the data path).
+--impl reference times the CPU oracle on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "space-time unknowns/sec to 1e-8 rel. error, mixed vs FP64 GPU path; p50/p99 latency"
+UNIT = "unknowns/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload(rank: int):
+    from paper_2603_04350_gb300 import inputs as I
+    p = I.ALLEN_CAHN_256
+    return p.with_(seed=p.seed + 1000 * rank) if rank else p
+
+
+def config_dict(p, world):
+    return {"workload": p.name, "grid": list(p.n), "Nt": p.Nt, "Ns": p.Ns, "order": p.order, "alpha": p.alpha,
+            "dt": p.dt, "tol": p.tol, "nonlin": p.nonlin, "unknowns_per_solve": p.unknowns,
+            "parallelism": f"replicas{world}" if world > 1 else "single",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ----------------------------------------------------------------- clocks ---
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------ cpu oracle ---
+def cpu_oracle_solve(p, u0):
+    """One oracle Exp-ParaDiag solve (lagged fixed point to tol): (seconds, iters, U)."""
+    import oracle as O
+    sp = O.spec_of(p)
+    t0 = time.perf_counter()
+    res = O.richardson(sp, u0, None, max_iter=60, tol=p.tol * 0.1)
+    return time.perf_counter() - t0, res.iterations, res.U
+
+
+def cpu_baseline(p, u0):
+    secs, iters, _ = cpu_oracle_solve(p, u0)
+    return {"value": p.unknowns / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full solve of the {p.name} workload ({iters} fixed-point sweeps, numpy float64, "
+                      f"single-threaded pocketfft), {secs:.2f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2603_04350_gb300 import inputs as I
+    p = workload(0)
+    u0 = I.make_u0(p)
+    times = []
+    for k in range(args.warmup + args.steps):
+        secs, iters, _ = cpu_oracle_solve(p, u0)
+        if k >= args.warmup:
+            times.append(secs)
+    # bounded: the reference arm's step is the full solve (~8 s on one core); K and W are
+    # capped so the run ends within minutes
+    total = sum(times)
+    value = p.unknowns * len(times) / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": len(times),
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config_dict(p, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{len(times)} full solves of {p.name} on the host, numpy float64"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm ---
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        args.steps = min(args.steps, 4)
+        args.warmup = min(args.warmup, 1)
+        return run_reference(args)
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_env()
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2603_04350_gb300 import expd, inputs as I
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    p = workload(rank)
+    u0 = I.make_u0(p)
+    u0_d = torch.from_numpy(u0).to(dev)
+    U_d = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    plan = expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, max_iter=100), stream)
+    plan64 = expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_FP64, max_iter=100), stream)
+
+    def timed_steps(pl, K, warm, timing=False):
+        infos = []
+        for k in range(warm):
+            flush.fill_(float(k))
+            pl.solve_fp(u0_d, None, U_d)
+        barrier()
+        pl.timing_read(reset=True)
+        if timing:
+            pl.timing_enable(True)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        barrier()
+        for k in range(K):
+            flush.fill_(float(k + 1))
+            starts[k].record(stream)
+            infos.append(pl.solve_fp(u0_d, None, U_d))
+            ends[k].record(stream)
+        barrier()
+        ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        tm = pl.timing_read(reset=True)
+        pl.timing_enable(False)
+        return ms, infos, tm
+
+    # ---- mixed path: the headline ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, infos, tm = timed_steps(plan, args.steps, args.warmup, timing=True)
+    clk = clocks.stop()
+    U_mixed = U_d.cpu().numpy()
+    total_ms = sum(ms)
+    if pg is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * p.unknowns * args.steps / (total_ms / 1e3)
+
+    # untimed-by-events repeat of the same loop: event records around every launch
+    # add overhead, so report how much (kept as the headline's own check)
+    ms_plain, _, tm_plain = timed_steps(plan, args.steps, 1, timing=False)
+
+    # ---- plain float64 path ----
+    K64 = max(3, args.steps // 2)
+    ms64, infos64, _ = timed_steps(plan64, K64, 3, timing=False)
+    U_fp64 = U_d.cpu().numpy()
+    value64 = p.unknowns / (statistics.mean(ms64) / 1e3)
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    u0_h = torch.from_numpy(u0).pin_memory()
+    U_h = torch.empty((p.Nt,) + p.n, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        plan.solve_fp(u0_h, None, U_h)
+    barrier()
+    e2e_t = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.solve_fp(u0_h, None, U_h)          # copies in and out inside the call
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_value = world * p.unknowns / statistics.mean(e2e_t)
+
+    # ---- roofline of the dominant kernel class ----
+    peak, peak_src = measured_peaks()
+    classes = tm["classes"]
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    c = classes[dom]
+    achieved = (c["bytes"] / c["count"]) / (c["ms"] / c["count"] / 1e3) / 1e9 if c["count"] else 0.0
+    kernels = {k: {"launches": v["count"], "ms_total": round(v["ms"], 4),
+                   "avg_us": round(1e3 * v["ms"] / v["count"], 3) if v["count"] else None,
+                   "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] else None}
+               for k, v in classes.items() if v["count"]}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+           "config": config_dict(p, world),
+           "iterations": infos[-1]["iterations"], "fp32_iterations": infos[-1]["fp32_iterations"],
+           "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+           "ms_per_step_without_event_timing": statistics.mean(ms_plain),
+           "fp64_path": {"value": value64, "ms_per_step": statistics.mean(ms64),
+                         "iterations": infos64[-1]["iterations"]},
+           "speedup_vs_fp64": value / (world * value64),
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(u0.nbytes),
+                   "d2h_bytes_per_step": int(U_h.numel() * 8)},
+           "gpu_launches": int(tm_plain["launches"]),
+           "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                        "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak, "traffic": None},
+           "kernels": kernels}
+    if clk:
+        out["clocks"] = clk
+    if rank == 0 and not args.no_check:
+        import oracle as O
+        ref = O.sequential_solve(O.spec_of(p), u0)[1:]
+        out["rel_err_vs_oracle"] = {"mixed": O.rel_error(U_mixed, ref), "fp64": O.rel_error(U_fp64, ref)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(p, u0)
+    plan.destroy()
+    plan64.destroy()
+    if rank == 0:
+        print(json.dumps(out))
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,225 @@
+/*
+ * expd.h -- C ABI of the GB300 Exp-ParaDiag library (libexpd.so).
+ *
+ * Exp-ParaDiag (Garai & Chamakuri, arXiv 2603.04350) solves the all-at-once
+ * system of an exponential BDF-s time integrator for u_t = L u + N(u),
+ * L = a*Lap - c, on Nt time steps at once:
+ *
+ *     R_s v = f_s,   R_s = I - sum_{j=1..s} a_j C_{j-1} (x) A^j,  A = exp(dt L_h)
+ *
+ * (Sec. 3 Eq. (3.1), Sec. 4 Eq. (4.2), Sec. 5 Eqs. (5.2)-(5.8)), with the
+ * alpha-circulant preconditioner R_s^alpha (Eq. (3.2), Eq. (4.4)) applied by
+ * the three steps of Eq. (3.3) / Eq. (4.5): an alpha-scaled DFT over the time
+ * slices, Ns independent shifted spatial solves, and the inverse scaled DFT.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grids.  1D: n[0] points.  2D: n[0] rows (slow axis) x n[1] columns (fast
+ *    axis).  Periodic grids (spectral Laplacian, x_j = j*L/n) need power-of-two
+ *    sizes 8..4096; Dirichlet grids (3-/5-point Laplacian on n interior
+ *    points, x_j = j*L/(n+1)) accept 2..4096 points per axis.
+ *  - Time.  u_0 is the initial value; u_1..u_Nt are the time slices.  For
+ *    order s the unknowns are v = (u_s, ..., u_Nt): Ns = Nt - s + 1 slices.
+ *    u_1..u_{s-1} are either produced by the ramp (u_j by BDF-j, j < s) or
+ *    supplied by the caller (EXPD_STARTUP_GIVEN).
+ *  - Arrays.  All arrays are float64, C order, slice-major: a space-time
+ *    array is [slices][n0] (1D) or [slices][n0][n1] (2D).  u0 is one slice.
+ *    U arguments hold u_1..u_Nt ([Nt] slices); residual and preconditioner
+ *    arguments hold the Ns unknown rows ([Ns] slices, row i is time s+i).
+ *  - Pointers may be device pointers (cudaMalloc / torch CUDA tensors) or
+ *    host pointers; the library detects which with cudaPointerGetAttributes.
+ *    Host buffers are staged through plan-owned device buffers with the
+ *    copies enqueued on the call's stream, so a call with host buffers
+ *    includes its own host<->device traffic.  The caller owns every buffer it
+ *    passes; the library never keeps a pointer past the call.
+ *  - Streams.  `stream` is a cudaStream_t (NULL = the legacy default
+ *    stream).  Device-pointer calls are asynchronous except that solvers
+ *    synchronise the stream to read convergence norms; host-pointer calls
+ *    return after their results are in host memory.  One call per plan may
+ *    be in flight at a time.
+ *  - Errors.  Every entry point returns an expd_status; nothing is thrown
+ *    across the ABI.  expd_last_error() gives a thread-local message for the
+ *    last failure.  EXPD_ERR_CUDA means a CUDA call failed (the message names
+ *    it); the plan stays valid unless the CUDA context itself is lost.
+ */
+#ifndef EXPD_H
+#define EXPD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EXPD_OK = 0,
+    EXPD_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range        */
+    EXPD_ERR_OOM = 2,           /* device allocation failed                             */
+    EXPD_ERR_NOT_CONVERGED = 3, /* max_iter reached; the last iterate is returned       */
+    EXPD_ERR_DIVERGED = 4,      /* update norm non-finite or growing 1e3-fold           */
+    EXPD_ERR_CUDA = 5,          /* a CUDA runtime call failed                           */
+    EXPD_ERR_UNSUPPORTED = 6    /* valid request that this build does not implement     */
+} expd_status;
+
+enum { EXPD_BC_PERIODIC = 0, EXPD_BC_DIRICHLET = 1 };
+enum { EXPD_NL_NONE = 0, EXPD_NL_ALLEN_CAHN = 1 };      /* N(u) = 0 or u - u^3          */
+enum { EXPD_PREC_FP64 = 0, EXPD_PREC_MIXED = 1 };
+enum { EXPD_STARTUP_RAMP = 0, EXPD_STARTUP_GIVEN = 1 };
+
+/* Spatial grid.  ndim is 1 or 2; n[1]/length[1] are ignored for 1D. */
+typedef struct {
+    int ndim;
+    int n[2];
+    double length[2];
+    int bc;                     /* EXPD_BC_*                                           */
+} expd_grid;
+
+/* L = a*Lap - c (Sec. 1, Eq. (1.2)) and the nonlinearity N. */
+typedef struct {
+    double a;
+    double c;
+    int nonlin;                 /* EXPD_NL_*                                           */
+} expd_operator;
+
+/* Scheme and solver controls.
+ *  order      s in 1..6: exponential BDF-s (Eq. (2.2), Eq. (4.1), Sec. 5)
+ *  precision  EXPD_PREC_FP64: every transform, the preconditioner and the
+ *             residual in float64.  EXPD_PREC_MIXED: the preconditioner's time
+ *             DFT and shifted solves in float32 and, for nonlinear problems,
+ *             the spatial FFTs that evaluate N in float32 until the update
+ *             stalls, then float64 sweeps; the residual is always float64.
+ *  max_iter   iteration cap of expd_solve_fp / expd_solve_gmres
+ *  tol        stop when the estimated L^inf(0,T;L^2) relative error of the
+ *             iterate is <= tol (fixed point) or the relative preconditioned
+ *             residual is <= tol (GMRES)
+ *  gmres_restart  GMRES restart length m (1..64)
+ *  startup    EXPD_STARTUP_RAMP or EXPD_STARTUP_GIVEN (u_1..u_{s-1} read
+ *             from the first s-1 slices of the U argument of the solvers)   */
+typedef struct {
+    int order;
+    int precision;
+    int max_iter;
+    double tol;
+    int gmres_restart;
+    int startup;
+} expd_scheme;
+
+#define EXPD_MAX_HISTORY 128
+
+/* Per-solve report.  history[k] is the convergence measure after iteration
+ * k+1: the estimated relative error (fixed point) or the relative
+ * preconditioned residual (GMRES). */
+typedef struct {
+    int iterations;
+    int fp32_iterations;        /* fixed-point sweeps that evaluated N with float32 FFTs */
+    double final_measure;
+    double contraction;         /* last observed ratio of successive update norms    */
+    double history[EXPD_MAX_HISTORY];
+} expd_info;
+
+typedef struct expd_plan_s* expd_plan;
+
+/* Create a plan: validates the problem, allocates all device workspace for it
+ * (see expd_plan_workspace_bytes) and builds the spectral tables (the
+ * eigenvalues of L_h, exp(dt mu), the alpha-circulant eigenvalues
+ * lambda_n = alpha^(1/Ns) e^{2 pi i n/Ns} and Gamma_alpha of Sec. 2, BDF
+ * coefficients).  Requires 0 < alpha < 1, dt > 0, Nt >= order + 1,
+ * beta_s*dt < 1 for nonlinear problems.  `stream` orders the table uploads.
+ * On failure *out is NULL and nothing stays allocated. */
+expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, double dt, int Nt,
+                             double alpha, const expd_scheme* scheme, void* stream,
+                             expd_plan* out);
+
+/* Device bytes the plan holds (for admission by memory footprint). */
+expd_status expd_plan_workspace_bytes(expd_plan plan, size_t* bytes);
+
+/* Residual of the all-at-once system (Eq. (3.2) right-hand side; for the
+ * lagged nonlinear form Eqs. (7.3)-(7.4)):
+ *     R = f_s + beta_s dt N(v) - R_s v,
+ * where v = U[s-1..Nt-1] (u_s..u_Nt), the startup values are u0 and
+ * U[0..s-2], and f_s holds the startup terms and beta_s dt f(t_n).
+ *   u0  [1 slice]   f  [Nt slices] or NULL (no source)   U  [Nt slices]
+ *   R   [Ns slices] (output)
+ * Everything is evaluated in float64. */
+expd_status expd_residual(expd_plan plan, const double* u0, const double* f, const double* U,
+                          double* R, void* stream);
+
+/* S = (R_s^alpha)^{-1} R by the three steps of Eq. (3.3) / Eq. (4.5):
+ * (a) S_a = (F (x) I)(Gamma_alpha (x) I) R, F the unitary DFT with
+ * omega = e^{2 pi i/Ns}; (b) per slice S_b,n = (I - sum_j a_j lambda_n^j A^j)^{-1} S_a,n
+ * in L_h's eigenbasis; (c) S = (Gamma_alpha^{-1} (x) I)(F^* (x) I) S_b.
+ *   R, S  [Ns slices]; R and S may alias.
+ * Steps (a)-(c) run in the plan's preconditioner precision (float32 for
+ * EXPD_PREC_MIXED); the spatial transforms around them are float64. */
+expd_status expd_precond_apply(expd_plan plan, const double* R, double* S, void* stream);
+
+/* Preconditioned fixed-point (Richardson) iteration v^{k+1} = v^k +
+ * (R_s^alpha)^{-1}(f_s + beta_s dt N(v^k) - R_s v^k) from v^0 = 0
+ * (Eq. (3.2), Eq. (4.4); lagged N as in Eqs. (7.3)-(7.4)).
+ *   u0 [1 slice]; f [Nt slices] or NULL; U [Nt slices] output u_1..u_Nt
+ *   (input for its first s-1 slices when startup = EXPD_STARTUP_GIVEN)
+ *   info may be NULL.
+ * Returns EXPD_ERR_NOT_CONVERGED (U holds the last iterate) when max_iter
+ * sweeps do not reach tol, EXPD_ERR_DIVERGED on a non-finite or exploding
+ * update. */
+expd_status expd_solve_fp(expd_plan plan, const double* u0, const double* f, double* U,
+                          expd_info* info, void* stream);
+
+/* Left-preconditioned restarted GMRES(m) on (R_s^alpha)^{-1} R_s v =
+ * (R_s^alpha)^{-1} f_s (Sec. 3.2, Theorem 3.3), v^0 = 0, classical
+ * Gram-Schmidt with one re-orthogonalisation, float64.  Linear problems
+ * only (EXPD_ERR_INVALID_ARG otherwise).  Arguments as expd_solve_fp. */
+expd_status expd_solve_gmres(expd_plan plan, const double* u0, const double* f, double* U,
+                             expd_info* info, void* stream);
+
+/* ---- per-kernel timing -------------------------------------------------------
+ * With timing enabled, every libexpd kernel launch of the plan is bracketed by
+ * two CUDA events recorded on the stream it is launched on; expd_timing_read
+ * waits for those events and reports, per kernel class, the number of timed
+ * launches, the summed device time, and the summed algorithmic DRAM bytes and
+ * flops the launches are defined to move / perform (the roofline numerators:
+ * one read of every input element and one write of every output element).
+ * `launches` counts all kernels launched by the plan since the last reset,
+ * timed or not.  Timing adds two event records per launch. */
+enum {
+    EXPD_K_TIME = 0,      /* residual + alpha-scaled DFT + shifted solves + inverse DFT + update */
+    EXPD_K_FFT_COL = 1,   /* spatial FFT along the strided axis                              */
+    EXPD_K_FFT_ROW = 2,   /* spatial real FFT along the contiguous axis (incl. fused N(u))   */
+    EXPD_K_DST = 3,       /* Dirichlet DST-I as a dense matrix product                        */
+    EXPD_K_GMRES = 4,     /* GMRES dot products and vector updates                            */
+    EXPD_K_POINTWISE = 5, /* pointwise solves, eigen-space combinations, f_s assembly         */
+    EXPD_K_REDUCE = 6,    /* per-slice norm reduction                                         */
+    EXPD_NUM_KCLASS = 7
+};
+
+typedef struct {
+    long long launches;
+    int count[EXPD_NUM_KCLASS];
+    double ms[EXPD_NUM_KCLASS];
+    double bytes[EXPD_NUM_KCLASS];
+    double flops[EXPD_NUM_KCLASS];
+} expd_timing;
+
+/* Turn per-launch event timing on (1) or off (0) for the plan. */
+expd_status expd_timing_enable(expd_plan plan, int enable);
+
+/* Report the accumulated timing; reset = 1 clears it afterwards. */
+expd_status expd_timing_read(expd_plan plan, expd_timing* out, int reset);
+
+/* Release the plan and all its device memory.  NULL is accepted. */
+expd_status expd_destroy(expd_plan plan);
+
+/* Static text for a status code. */
+const char* expd_status_string(expd_status s);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* expd_last_error(void);
+
+/* Library ABI version (major*10000 + minor*100 + patch). */
+int expd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXPD_H */

@@ -1,0 +1,871 @@
+// C ABI of libexpd: plans, the fixed-point and GMRES solvers, and the residual
+// and preconditioner entry points (declared and documented in include/expd.h).
+//
+// A solve runs entirely in L_h's eigenbasis:
+//   1. u0 (and the source f) go to the eigenbasis; the startup values
+//      u_1..u_{s-1} come from the ramp (BDF-j, j < s) or from the caller;
+//   2. the known right-hand side f_s is assembled (startup terms a_j A^j u_{n-j}
+//      with n-j < s, plus beta_s dt f(t_n));
+//   3. Richardson sweeps (Eq. (3.2) / Eq. (4.4)) or GMRES (Sec. 3.2) run on the
+//      Ns unknown slices; a nonlinear sweep first evaluates N at the iterate
+//      through the spatial FFTs (lagged form, Eqs. (7.3)-(7.4));
+//   4. the unknown slices return to physical space.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "plan.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+const int64_t kMaxSlices = 1 << 20;
+
+struct Rational {
+    int64_t n, d;
+};
+int64_t gcd64(int64_t a, int64_t b) {
+    if (a < 0) a = -a;
+    if (b < 0) b = -b;
+    while (b) {
+        int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a ? a : 1;
+}
+Rational rnorm(int64_t n, int64_t d) {
+    if (d < 0) {
+        n = -n;
+        d = -d;
+    }
+    const int64_t g = gcd64(n, d);
+    return {n / g, d / g};
+}
+Rational radd(Rational a, Rational b) { return rnorm(a.n * b.d + b.n * a.d, a.d * b.d); }
+Rational rdiv(Rational a, Rational b) { return rnorm(a.n * b.d, a.d * b.n); }
+
+// BDF-q: sum_{i=1..q} (1/i) (1 - z)^i = sum_j c_j z^j, normalised to
+// u_n - sum_j a_j u_{n-j} = beta dt f_n (Eq. (4.1), Eqs. (5.1)-(5.7)).
+void bdf(int q, double* a, double* beta) {
+    Rational c[7];
+    for (int j = 0; j < 7; ++j) c[j] = {0, 1};
+    for (int i = 1; i <= q; ++i) {
+        int64_t binom = 1;
+        for (int j = 0; j <= i; ++j) {
+            c[j] = radd(c[j], rnorm((j % 2 ? -1 : 1) * binom, i));
+            binom = binom * (i - j) / (j + 1);
+        }
+    }
+    *beta = (double)c[0].d / (double)c[0].n;
+    a[0] = 0.0;
+    for (int j = 1; j <= q; ++j) {
+        const Rational r = rdiv(c[j], c[0]);
+        a[j] = -(double)r.n / (double)r.d;
+    }
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+bool is_device_ptr(const void* ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+expd_status dalloc(expd_plan p, void** ptr, size_t bytes, const char* what) {
+    *ptr = nullptr;
+    if (bytes == 0) return EXPD_OK;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return expd_fail(EXPD_ERR_OOM, std::string("cudaMalloc failed for ") + what + " (" +
+                                            std::to_string(bytes) + " bytes): " + cudaGetErrorString(e));
+    }
+    p->bytes += bytes;
+    return EXPD_OK;
+}
+
+template <typename T>
+expd_status upload_vec(expd_plan p, T** dptr, const std::vector<T>& h, const char* what, cudaStream_t s) {
+    expd_status st = dalloc(p, reinterpret_cast<void**>(dptr), h.size() * sizeof(T), what);
+    if (st != EXPD_OK) return st;
+    EXPD_CUDA_TRY(cudaMemcpyAsync(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+    return EXPD_OK;
+}
+
+void free_plan(expd_plan p) {
+    if (!p) return;
+    void* bufs[] = {p->E,    p->Wx64, p->Wx32,   p->Wy64,    p->Wy32,    p->Sx,        p->Sy,
+                    p->Uh,   p->Fh,   p->Sh,     p->fh,      p->NL64,    p->NL32,      p->work64,
+                    p->work32, p->startphys, p->partial, p->redout, p->stage, p->gm};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (p->redhost) cudaFreeHost(p->redhost);
+    for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+    time_tables_free(p);
+    delete p;
+}
+
+// ---- staging of host pointers ------------------------------------------------
+struct Staging {
+    const double* u0 = nullptr;
+    const double* f = nullptr;
+    double* U = nullptr;        // device view of the U argument
+    double* U_host = nullptr;   // non-null when U is host memory
+    size_t U_slices = 0;
+};
+
+expd_status ensure_stage(expd_plan p) {
+    if (p->stage) return EXPD_OK;
+    p->stage_elems = (size_t)(2 * p->Nt + 1) * p->M;
+    return dalloc(p, reinterpret_cast<void**>(&p->stage), p->stage_elems * sizeof(double), "staging");
+}
+
+// Resolve u0/f (inputs, [1]/[Nt] slices) and U ([U_slices], in/out) to device memory.
+expd_status stage_in(expd_plan p, const double* u0, const double* f, double* U, size_t U_slices, bool U_is_input,
+                     Staging& st, cudaStream_t s) {
+    const bool hu0 = u0 && !is_device_ptr(u0);
+    const bool hf = f && !is_device_ptr(f);
+    const bool hU = U && !is_device_ptr(U);
+    if (hu0 || hf || hU) {
+        expd_status r = ensure_stage(p);
+        if (r != EXPD_OK) return r;
+    }
+    const size_t M = (size_t)p->M;
+    st.u0 = u0;
+    st.f = f;
+    st.U = U;
+    st.U_slices = U_slices;
+    if (hu0) {
+        EXPD_CUDA_TRY(cudaMemcpyAsync(p->stage, u0, M * sizeof(double), cudaMemcpyHostToDevice, s));
+        st.u0 = p->stage;
+    }
+    if (hf) {
+        EXPD_CUDA_TRY(cudaMemcpyAsync(p->stage + M, f, (size_t)p->Nt * M * sizeof(double), cudaMemcpyHostToDevice, s));
+        st.f = p->stage + M;
+    }
+    if (hU) {
+        st.U_host = U;
+        st.U = p->stage + (size_t)(p->Nt + 1) * M;
+        if (U_is_input)
+            EXPD_CUDA_TRY(cudaMemcpyAsync(st.U, U, U_slices * M * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    return EXPD_OK;
+}
+
+expd_status stage_out(expd_plan p, const Staging& st, cudaStream_t s) {
+    if (st.U_host)
+        EXPD_CUDA_TRY(cudaMemcpyAsync(st.U_host, st.U, st.U_slices * (size_t)p->M * sizeof(double),
+                                      cudaMemcpyDeviceToHost, s));
+    if (st.U_host) EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+    return EXPD_OK;
+}
+
+void* eig_slice(expd_plan p, void* base, long long n) {
+    return static_cast<char*>(base) + (size_t)n * p->Mcol * p->esz;
+}
+
+// ---- startup values and f_s ----------------------------------------------------
+// Sh[n] (eigen) and startphys[n] (physical) for n = 0..s-1, fh (eigen source)
+// when f is given, and the assembled right-hand side Fh.
+expd_status setup_start(expd_plan p, const double* u0, const double* f, const double* Ugiven, cudaStream_t s) {
+    const size_t M = (size_t)p->M;
+    const int so = p->order;
+    EXPD_CUDA_TRY(cudaMemcpyAsync(p->startphys, u0, M * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    expd_status st = spatial_forward64(p, p->startphys, p->Sh, 1, s);
+    if (st != EXPD_OK) return st;
+    if (f) {
+        if (!p->fh) {
+            st = dalloc(p, &p->fh, (size_t)p->Nt * p->Mcol * p->esz, "source (eigen)");
+            if (st != EXPD_OK) return st;
+        }
+        st = spatial_forward64(p, f, p->fh, p->Nt, s);
+        if (st != EXPD_OK) return st;
+    }
+    void* tmp = p->Fh;  // slice 0 of Fh is free until assemble_rhs
+    for (int n = 1; n < so; ++n) {
+        double* phys_n = p->startphys + (size_t)n * M;
+        void* eig_n = eig_slice(p, p->Sh, n);
+        if (p->startup == EXPD_STARTUP_GIVEN) {
+            EXPD_CUDA_TRY(cudaMemcpyAsync(phys_n, Ugiven + (size_t)(n - 1) * M, M * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, s));
+            st = spatial_forward64(p, phys_n, eig_n, 1, s);
+            if (st != EXPD_OK) return st;
+            continue;
+        }
+        // ramp: BDF-n step  w = sum_j a_j A^j u_{n-j} + beta_n dt f(t_n)
+        const void* in[6];
+        double coef[6];
+        for (int j = 1; j <= n; ++j) {
+            in[j - 1] = eig_slice(p, p->Sh, n - j);
+            coef[j - 1] = p->acoef[n][j];
+        }
+        const void* src = f ? eig_slice(p, p->fh, n - 1) : nullptr;
+        const double bdt = p->beta[n] * p->dt;
+        if (p->nonlin == EXPD_NL_NONE) {
+            st = eigen_combine(p, eig_n, in, coef, n, src, bdt, s);
+            if (st == EXPD_OK) st = spatial_inverse64(p, eig_n, phys_n, 1, s);
+        } else {
+            st = eigen_combine(p, tmp, in, coef, n, src, bdt, s);
+            if (st == EXPD_OK) st = spatial_inverse64(p, tmp, phys_n, 1, s);
+            if (st == EXPD_OK) st = pointwise_solve(p, phys_n, phys_n, (long long)M, bdt, s);
+            if (st == EXPD_OK) st = spatial_forward64(p, phys_n, eig_n, 1, s);
+        }
+        if (st != EXPD_OK) return st;
+    }
+    return assemble_rhs(p, f ? p->fh : nullptr, s);
+}
+
+expd_status read_norms(expd_plan p, cudaStream_t s, double out[4]) {
+    expd_status st = time_reduce(p, s);
+    if (st != EXPD_OK) return st;
+    EXPD_CUDA_TRY(cudaMemcpyAsync(p->redhost, p->redout, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < 4; ++i) out[i] = p->redhost[i];
+    return EXPD_OK;
+}
+
+// U output: u_1..u_{s-1} from the startup values, u_s..u_Nt from Uh.
+expd_status write_solution(expd_plan p, double* U, cudaStream_t s) {
+    const size_t M = (size_t)p->M;
+    if (p->order > 1)
+        EXPD_CUDA_TRY(cudaMemcpyAsync(U, p->startphys + M, (size_t)(p->order - 1) * M * sizeof(double),
+                                      cudaMemcpyDeviceToDevice, s));
+    return spatial_inverse64(p, p->Uh, U + (size_t)(p->order - 1) * M, p->Ns, s);
+}
+
+void info_reset(expd_info* info) {
+    if (!info) return;
+    memset(info, 0, sizeof(*info));
+}
+
+}  // namespace
+
+expd_status expd_cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    g_err = buf;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? EXPD_ERR_OOM : EXPD_ERR_CUDA;
+}
+
+expd_status expd_fail(expd_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+KProf::KProf(expd_plan p_, cudaStream_t s_, int cls_, double bytes_, double flops_)
+    : p(p_), s(s_), cls(cls_), bytes(bytes_), flops(flops_) {
+    ++p->launches;
+    if (!p->timing) return;
+    while (p->events.size() < p->ev_used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        p->events.push_back(e);
+    }
+    e0 = (int)p->ev_used;
+    p->ev_used += 2;
+    cudaEventRecord(p->events[e0], s);
+}
+
+KProf::~KProf() {
+    if (e0 < 0) return;
+    cudaEventRecord(p->events[e0 + 1], s);
+    p->recs.push_back({cls, e0, bytes, flops});
+}
+
+extern "C" {
+
+const char* expd_status_string(expd_status s) {
+    switch (s) {
+        case EXPD_OK: return "ok";
+        case EXPD_ERR_INVALID_ARG: return "invalid argument";
+        case EXPD_ERR_OOM: return "out of device memory";
+        case EXPD_ERR_NOT_CONVERGED: return "not converged";
+        case EXPD_ERR_DIVERGED: return "diverged";
+        case EXPD_ERR_CUDA: return "CUDA error";
+        case EXPD_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* expd_last_error(void) { return g_err.c_str(); }
+
+int expd_version(void) { return 10000; }
+
+expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, double dt, int Nt, double alpha,
+                             const expd_scheme* scheme, void* stream, expd_plan* out) {
+    if (!out) return expd_fail(EXPD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    g_err.clear();
+    if (!grid || !op || !scheme) return expd_fail(EXPD_ERR_INVALID_ARG, "grid, operator and scheme are required");
+    if (grid->ndim != 1 && grid->ndim != 2) return expd_fail(EXPD_ERR_INVALID_ARG, "ndim must be 1 or 2");
+    if (grid->bc != EXPD_BC_PERIODIC && grid->bc != EXPD_BC_DIRICHLET)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "bc must be EXPD_BC_PERIODIC or EXPD_BC_DIRICHLET");
+    for (int d = 0; d < grid->ndim; ++d) {
+        const int n = grid->n[d];
+        if (grid->bc == EXPD_BC_PERIODIC && (!is_pow2(n) || n < 8 || n > EXPD_MAX_PERIODIC_N))
+            return expd_fail(EXPD_ERR_INVALID_ARG, "periodic grid sizes must be powers of two in [8, 4096]");
+        if (grid->bc == EXPD_BC_DIRICHLET && (n < 2 || n > EXPD_MAX_DIRICHLET_N))
+            return expd_fail(EXPD_ERR_INVALID_ARG, "Dirichlet grid sizes must be in [2, 4096]");
+        if (!(grid->length[d] > 0) || !isfinite(grid->length[d]))
+            return expd_fail(EXPD_ERR_INVALID_ARG, "domain lengths must be positive");
+    }
+    if (!(dt > 0) || !isfinite(dt)) return expd_fail(EXPD_ERR_INVALID_ARG, "dt must be positive");
+    if (!(alpha > 0 && alpha < 1)) return expd_fail(EXPD_ERR_INVALID_ARG, "alpha must lie in (0, 1)");
+    if (scheme->order < 1 || scheme->order > 6) return expd_fail(EXPD_ERR_INVALID_ARG, "order must be 1..6");
+    if (Nt < scheme->order + 1 || Nt > kMaxSlices)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "Nt must be at least order + 1");
+    if (Nt - scheme->order + 1 > EXPD_MAX_NS)
+        return expd_fail(EXPD_ERR_UNSUPPORTED, "Nt - order + 1 exceeds 2048 unknown slices");
+    if (op->nonlin != EXPD_NL_NONE && op->nonlin != EXPD_NL_ALLEN_CAHN)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "unknown nonlinearity");
+    if (!isfinite(op->a) || !isfinite(op->c)) return expd_fail(EXPD_ERR_INVALID_ARG, "a and c must be finite");
+    if (scheme->precision != EXPD_PREC_FP64 && scheme->precision != EXPD_PREC_MIXED)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "unknown precision");
+    if (scheme->max_iter < 1 || scheme->max_iter > 100000)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "max_iter must be in [1, 100000]");
+    if (!(scheme->tol > 0)) return expd_fail(EXPD_ERR_INVALID_ARG, "tol must be positive");
+    if (scheme->gmres_restart < 1 || scheme->gmres_restart > 64)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "gmres_restart must be in [1, 64]");
+    if (scheme->startup != EXPD_STARTUP_RAMP && scheme->startup != EXPD_STARTUP_GIVEN)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "unknown startup mode");
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    expd_plan p = new expd_plan_s();
+    p->ndim = grid->ndim;
+    if (p->ndim == 1) {
+        p->NX = grid->n[0];
+        p->NY = 1;
+        p->LX = grid->length[0];
+        p->LY = 1.0;
+    } else {
+        p->NY = grid->n[0];
+        p->NX = grid->n[1];
+        p->LY = grid->length[0];
+        p->LX = grid->length[1];
+    }
+    p->bc = grid->bc;
+    p->a = op->a;
+    p->c = op->c;
+    p->nonlin = op->nonlin;
+    p->dt = dt;
+    p->Nt = Nt;
+    p->order = scheme->order;
+    p->Ns = Nt - scheme->order + 1;
+    p->alpha = alpha;
+    p->precision = scheme->precision;
+    p->max_iter = scheme->max_iter;
+    p->tol = scheme->tol;
+    p->restart = scheme->gmres_restart;
+    p->startup = scheme->startup;
+    for (int q = 1; q <= 6; ++q) bdf(q, p->acoef[q], &p->beta[q]);
+    if (p->nonlin != EXPD_NL_NONE) {
+        for (int q = 1; q <= p->order; ++q)
+            if (!(p->beta[q] * dt < 1.0)) {
+                delete p;
+                return expd_fail(EXPD_ERR_INVALID_ARG, "nonlinear problems need beta_s*dt < 1");
+            }
+    }
+    p->M = (long long)p->NX * p->NY;
+    p->realcol = p->bc == EXPD_BC_DIRICHLET;
+    p->KX = p->realcol ? p->NX : p->NX / 2 + 1;
+    p->Mcol = (long long)p->NY * p->KX;
+    p->esz = p->realcol ? sizeof(double) : sizeof(double2);
+
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (ce != cudaSuccess) {
+        delete p;
+        return expd_cuda_fail(ce, "cudaGetDevice/cudaDeviceGetAttribute", __FILE__, __LINE__);
+    }
+
+    expd_status st = EXPD_OK;
+    // ---- eigenvalues of L_h: E_m = exp(dt mu_m) ----
+    {
+        std::vector<double> E(p->Mcol);
+        for (long long m = 0; m < p->Mcol; ++m) {
+            const int kx = (int)(m % p->KX);
+            const int ky = (int)(m / p->KX);
+            double mu = -p->c;
+            if (p->bc == EXPD_BC_PERIODIC) {
+                const double wx = 2.0 * M_PI * kx / p->LX;
+                mu -= p->a * wx * wx;
+                if (p->ndim == 2) {
+                    const int kyf = ky <= p->NY / 2 ? ky : ky - p->NY;
+                    const double wy = 2.0 * M_PI * kyf / p->LY;
+                    mu -= p->a * wy * wy;
+                }
+            } else {
+                const double hx = p->LX / (p->NX + 1);
+                const double sx = sin(M_PI * (kx + 1) * hx / (2.0 * p->LX));
+                mu -= p->a * (4.0 / (hx * hx)) * sx * sx;
+                if (p->ndim == 2) {
+                    const double hy = p->LY / (p->NY + 1);
+                    const double sy = sin(M_PI * (ky + 1) * hy / (2.0 * p->LY));
+                    mu -= p->a * (4.0 / (hy * hy)) * sy * sy;
+                }
+            }
+            E[m] = exp(dt * mu);
+        }
+        st = upload_vec(p, &p->E, E, "E", s);
+    }
+    // ---- spatial transform tables ----
+    if (st == EXPD_OK && p->bc == EXPD_BC_PERIODIC) {
+        std::vector<double2> w64(p->NX / 2 + 1);
+        std::vector<float2> w32(p->NX / 2 + 1);
+        for (int k = 0; k <= p->NX / 2; ++k) {
+            const double ang = -2.0 * M_PI * k / p->NX;
+            w64[k] = make_double2(cos(ang), sin(ang));
+            w32[k] = make_float2((float)cos(ang), (float)sin(ang));
+        }
+        st = upload_vec(p, &p->Wx64, w64, "Wx", s);
+        if (st == EXPD_OK) st = upload_vec(p, &p->Wx32, w32, "Wx32", s);
+        if (st == EXPD_OK && p->ndim == 2) {
+            std::vector<double2> y64(std::max(1, p->NY / 2));
+            std::vector<float2> y32(std::max(1, p->NY / 2));
+            for (int k = 0; k < p->NY / 2; ++k) {
+                const double ang = -2.0 * M_PI * k / p->NY;
+                y64[k] = make_double2(cos(ang), sin(ang));
+                y32[k] = make_float2((float)cos(ang), (float)sin(ang));
+            }
+            st = upload_vec(p, &p->Wy64, y64, "Wy", s);
+            if (st == EXPD_OK) st = upload_vec(p, &p->Wy32, y32, "Wy32", s);
+        }
+    }
+    if (st == EXPD_OK && p->bc == EXPD_BC_DIRICHLET) {
+        for (int d = 0; d < p->ndim && st == EXPD_OK; ++d) {
+            const int n = d == 0 ? p->NX : p->NY;
+            std::vector<double> S((size_t)n * n);
+            const double sc = sqrt(2.0 / (n + 1));
+            for (int j = 0; j < n; ++j)
+                for (int k = 0; k < n; ++k) {
+                    const long long r = ((long long)(j + 1) * (k + 1)) % (2LL * (n + 1));
+                    S[(size_t)j * n + k] = sc * sin(M_PI * (double)r / (n + 1));
+                }
+            st = upload_vec(p, d == 0 ? &p->Sx : &p->Sy, S, "DST matrix", s);
+        }
+    }
+    // ---- state and workspace ----
+    const size_t vec = (size_t)p->Ns * p->Mcol * p->esz;
+    if (st == EXPD_OK) st = dalloc(p, &p->Uh, vec, "iterate");
+    if (st == EXPD_OK) st = dalloc(p, &p->Fh, vec, "right-hand side");
+    if (st == EXPD_OK) st = dalloc(p, &p->Sh, (size_t)p->order * p->Mcol * p->esz, "startup (eigen)");
+    if (st == EXPD_OK)
+        st = dalloc(p, reinterpret_cast<void**>(&p->startphys), (size_t)p->order * p->M * sizeof(double),
+                    "startup (physical)");
+    const size_t work = (size_t)p->Ns * p->NY * p->KX * sizeof(double2);
+    if (st == EXPD_OK) st = dalloc(p, &p->work64, work, "work64");
+    if (st == EXPD_OK && p->nonlin != EXPD_NL_NONE) {
+        st = dalloc(p, &p->NL64, vec, "N (float64)");
+        if (st == EXPD_OK && p->precision == EXPD_PREC_MIXED && p->bc == EXPD_BC_PERIODIC) {
+            st = dalloc(p, &p->NL32, (size_t)p->Ns * p->Mcol * sizeof(float2), "N (float32)");
+            if (st == EXPD_OK) st = dalloc(p, &p->work32, (size_t)p->Ns * p->NY * p->KX * sizeof(float2), "work32");
+        }
+    }
+    if (st == EXPD_OK) st = dalloc(p, reinterpret_cast<void**>(&p->redout), 8 * sizeof(double), "norms");
+    if (st == EXPD_OK) {
+        cudaError_t e = cudaMallocHost(&p->redhost, 8 * sizeof(double));
+        if (e != cudaSuccess) st = expd_cuda_fail(e, "cudaMallocHost(norms)", __FILE__, __LINE__);
+    }
+    if (st == EXPD_OK) st = time_tables_build(p, s);
+    if (st != EXPD_OK) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return EXPD_OK;
+}
+
+expd_status expd_plan_workspace_bytes(expd_plan p, size_t* bytes) {
+    if (!p || !bytes) return expd_fail(EXPD_ERR_INVALID_ARG, "plan and bytes are required");
+    *bytes = p->bytes;
+    return EXPD_OK;
+}
+
+expd_status expd_timing_enable(expd_plan p, int enable) {
+    if (!p) return expd_fail(EXPD_ERR_INVALID_ARG, "plan is NULL");
+    p->timing = enable ? 1 : 0;
+    return EXPD_OK;
+}
+
+expd_status expd_timing_read(expd_plan p, expd_timing* out, int reset) {
+    if (!p || !out) return expd_fail(EXPD_ERR_INVALID_ARG, "plan and out are required");
+    memset(out, 0, sizeof(*out));
+    out->launches = p->launches;
+    for (const auto& r : p->recs) {
+        EXPD_CUDA_TRY(cudaEventSynchronize(p->events[r.e0 + 1]));
+        float ms = 0.f;
+        EXPD_CUDA_TRY(cudaEventElapsedTime(&ms, p->events[r.e0], p->events[r.e0 + 1]));
+        if (r.cls < 0 || r.cls >= EXPD_NUM_KCLASS) continue;
+        out->count[r.cls] += 1;
+        out->ms[r.cls] += ms;
+        out->bytes[r.cls] += r.bytes;
+        out->flops[r.cls] += r.flops;
+    }
+    if (reset) {
+        p->recs.clear();
+        p->ev_used = 0;
+        p->launches = 0;
+    }
+    return EXPD_OK;
+}
+
+expd_status expd_destroy(expd_plan p) {
+    if (!p) return EXPD_OK;
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return EXPD_OK;
+}
+
+expd_status expd_residual(expd_plan p, const double* u0, const double* f, const double* U, double* R,
+                          void* stream) {
+    if (!p || !u0 || !U || !R) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, u0, U and R are required");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t M = (size_t)p->M;
+    Staging sg;
+    expd_status st = stage_in(p, u0, f, const_cast<double*>(U), p->Nt, true, sg, s);
+    if (st != EXPD_OK) return st;
+    // R may be host memory: compute into the staging area or the caller's buffer
+    const bool hR = !is_device_ptr(R);
+    double* Rd = R;
+    if (hR) {
+        st = ensure_stage(p);
+        if (st != EXPD_OK) return st;
+        Rd = p->stage + M;  // the source slot; f has been transformed before it is overwritten
+    }
+    const int saved = p->startup;
+    p->startup = EXPD_STARTUP_GIVEN;
+    st = setup_start(p, sg.u0, sg.f, sg.U, s);
+    p->startup = saved;
+    if (st != EXPD_OK) return st;
+    st = spatial_forward64(p, sg.U + (size_t)(p->order - 1) * M, p->Uh, p->Ns, s);
+    if (st != EXPD_OK) return st;
+    TimeOp op;
+    op.X = p->Uh;
+    op.F = p->Fh;
+    op.sigR = -1.0;
+    op.precond = 0;
+    op.out = p->Fh;  // in-place per tile: each tile is loaded before it is written
+    if (p->nonlin != EXPD_NL_NONE) {
+        st = nonlinear_eval(p, p->Uh, p->NL64, 0, s);
+        if (st != EXPD_OK) return st;
+        op.NL = p->NL64;
+        op.bdt = p->beta[p->order] * p->dt;
+    }
+    st = time_apply(p, op, s);
+    if (st != EXPD_OK) return st;
+    st = spatial_inverse64(p, p->Fh, Rd, p->Ns, s);
+    if (st != EXPD_OK) return st;
+    if (hR) {
+        EXPD_CUDA_TRY(cudaMemcpyAsync(R, Rd, (size_t)p->Ns * M * sizeof(double), cudaMemcpyDeviceToHost, s));
+        EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return EXPD_OK;
+}
+
+expd_status expd_precond_apply(expd_plan p, const double* R, double* S, void* stream) {
+    if (!p || !R || !S) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, R and S are required");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t M = (size_t)p->M;
+    const size_t bytes = (size_t)p->Ns * M * sizeof(double);
+    const double* Rd = R;
+    double* Sd = S;
+    const bool hR = !is_device_ptr(R), hS = !is_device_ptr(S);
+    if (hR || hS) {
+        expd_status st = ensure_stage(p);
+        if (st != EXPD_OK) return st;
+    }
+    if (hR) {
+        EXPD_CUDA_TRY(cudaMemcpyAsync(p->stage, R, bytes, cudaMemcpyHostToDevice, s));
+        Rd = p->stage;
+    }
+    if (hS) Sd = p->stage + (size_t)p->Nt * M;
+    expd_status st = spatial_forward64(p, Rd, p->Fh, p->Ns, s);
+    if (st != EXPD_OK) return st;
+    TimeOp op;
+    op.F = p->Fh;
+    op.precond = 1;
+    op.out = p->Fh;
+    op.f32 = p->precision == EXPD_PREC_MIXED;
+    st = time_apply(p, op, s);
+    if (st != EXPD_OK) return st;
+    st = spatial_inverse64(p, p->Fh, Sd, p->Ns, s);
+    if (st != EXPD_OK) return st;
+    if (hS) {
+        EXPD_CUDA_TRY(cudaMemcpyAsync(S, Sd, bytes, cudaMemcpyDeviceToHost, s));
+        EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return EXPD_OK;
+}
+
+expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double* U, expd_info* info,
+                          void* stream) {
+    if (!p || !u0 || !U) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, u0 and U are required");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    info_reset(info);
+    Staging sg;
+    expd_status st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
+    if (st != EXPD_OK) return st;
+    st = setup_start(p, sg.u0, sg.f, sg.U, s);
+    if (st != EXPD_OK) return st;
+    EXPD_CUDA_TRY(cudaMemsetAsync(p->Uh, 0, (size_t)p->Ns * p->Mcol * p->esz, s));
+
+    const bool nl = p->nonlin != EXPD_NL_NONE;
+    const bool mixed = p->precision == EXPD_PREC_MIXED;
+    bool spatial32 = mixed && nl && p->NL32 != nullptr;
+    double prev = 0.0, rho = 0.5, rho_phase = -1.0, measure = 1.0;
+    int it = 0, it32 = 0;
+    expd_status result = EXPD_ERR_NOT_CONVERGED;
+    for (it = 1; it <= p->max_iter; ++it) {
+        TimeOp op;
+        op.X = p->Uh;
+        op.F = p->Fh;
+        op.sigR = -1.0;
+        op.precond = 1;
+        op.accum = 1;
+        op.f32 = mixed;
+        const bool used32 = spatial32;
+        if (nl) {
+            void* NL = spatial32 ? p->NL32 : p->NL64;
+            st = nonlinear_eval(p, p->Uh, NL, spatial32 ? 1 : 0, s);
+            if (st != EXPD_OK) return st;
+            op.NL = NL;
+            op.nl_f32 = spatial32 ? 1 : 0;
+            op.bdt = p->beta[p->order] * p->dt;
+        }
+        st = time_apply(p, op, s);
+        if (st != EXPD_OK) return st;
+        double nr[4];
+        st = read_norms(p, s, nr);
+        if (st != EXPD_OK) return st;
+        if (used32) ++it32;
+        const double smax = nr[0], umax = nr[1];
+        if (!isfinite(smax) || !isfinite(umax) || (it > 1 && smax > 1e3 * prev && prev > 0)) {
+            result = expd_fail(EXPD_ERR_DIVERGED, "fixed-point update is non-finite or growing");
+            break;
+        }
+        const double rel = umax > 0 ? smax / umax : 0.0;
+        if (it > 1 && prev > 0) {
+            const double ratio = smax / prev;
+            rho = std::min(0.95, std::max(1e-12, ratio));
+        }
+        // in the float64 phase after a float32 phase, the contraction is the
+        // one observed before the float32 floor was reached
+        const double r_use = (rho_phase > 0 && !spatial32) ? rho_phase : rho;
+        measure = it == 1 ? rel : rel * r_use / (1.0 - r_use);
+        if (info && it <= EXPD_MAX_HISTORY) info->history[it - 1] = measure;
+        if (info) info->contraction = rho;
+        if (spatial32) {
+            // leave the float32 sweeps once the iterate is near tol or stalls
+            const bool stalled = it > 2 && rho > 0.5;
+            if (measure <= p->tol || stalled) {
+                spatial32 = false;
+                if (!stalled) rho_phase = rho;
+                else if (rho_phase < 0) rho_phase = 0.5;
+            } else if (rho < 0.5) {
+                rho_phase = rho;
+            }
+        } else if (measure <= p->tol) {
+            result = EXPD_OK;
+            prev = smax;
+            break;
+        }
+        prev = smax;
+    }
+    if (it > p->max_iter) it = p->max_iter;
+    if (info) {
+        info->iterations = it;
+        info->fp32_iterations = it32;
+        info->final_measure = measure;
+    }
+    st = write_solution(p, sg.U, s);
+    if (st != EXPD_OK) return st;
+    st = stage_out(p, sg, s);
+    if (st != EXPD_OK) return st;
+    if (result == EXPD_ERR_NOT_CONVERGED) g_err = "max_iter reached before tol";
+    return result;
+}
+
+expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, double* U, expd_info* info,
+                             void* stream) {
+    if (!p || !u0 || !U) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, u0 and U are required");
+    if (p->nonlin != EXPD_NL_NONE) return expd_fail(EXPD_ERR_INVALID_ARG, "GMRES needs a linear problem");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    info_reset(info);
+    const int m = p->restart;
+    const long long n = eigen_elems(p);
+    // block: V[0..m], c, w, then h/partials
+    const int dots_grid = p->sm_count * 4;
+    const size_t hblock = 128 + 65 * (size_t)dots_grid;
+    if (!p->gm || p->gm_cols < m) {
+        if (p->gm) {
+            cudaFree(p->gm);
+            p->bytes -= (size_t)(p->gm_cols + 3) * n * sizeof(double) + hblock * sizeof(double);
+            p->gm = nullptr;
+        }
+        expd_status st = dalloc(p, &p->gm, (size_t)(m + 3) * n * sizeof(double) + hblock * sizeof(double), "GMRES basis");
+        if (st != EXPD_OK) return st;
+        p->gm_cols = m;
+    }
+    double* V = static_cast<double*>(p->gm);
+    double* c = V + (size_t)(m + 1) * n;
+    double* w = c + n;
+    double* h = w + n;  // [128] results + partials
+    Staging sg;
+    expd_status st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
+    if (st != EXPD_OK) return st;
+    st = setup_start(p, sg.u0, sg.f, sg.U, s);
+    if (st != EXPD_OK) return st;
+    double* x = static_cast<double*>(p->Uh);
+    EXPD_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+
+    auto apply_op = [&](const double* v, double* out) -> expd_status {
+        TimeOp op;
+        op.X = v;
+        op.sigR = 1.0;
+        op.precond = 1;
+        op.out = out;
+        return time_apply(p, op, s);
+    };
+    auto dots = [&](const double* Vb, int k, const double* vec, double* hh) -> expd_status {
+        expd_status r = gm_dots(p, Vb, n, k, vec, h, s);
+        if (r != EXPD_OK) return r;
+        EXPD_CUDA_TRY(cudaMemcpyAsync(hh, h, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+        EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+        return EXPD_OK;
+    };
+    // c = P^{-1} f_s
+    {
+        TimeOp op;
+        op.F = p->Fh;
+        op.precond = 1;
+        op.out = c;
+        st = time_apply(p, op, s);
+        if (st != EXPD_OK) return st;
+    }
+    double cn2 = 0;
+    st = dots(c, 1, c, &cn2);
+    if (st != EXPD_OK) return st;
+    const double cn = sqrt(cn2);
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hh(m + 1), hh2(m + 1), y(m);
+    int total = 0;
+    double relres = 1.0;
+    expd_status result = EXPD_ERR_NOT_CONVERGED;
+    if (info) info->history[0] = 1.0;
+    bool first = true;
+    while (cn > 0 && total < p->max_iter) {
+        // r = c - P^{-1} R x   (x = 0 on the first cycle)
+        if (first) {
+            EXPD_CUDA_TRY(cudaMemcpyAsync(V, c, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        } else {
+            st = apply_op(x, V);
+            if (st == EXPD_OK) st = gm_axpby(p, n, 1.0, c, -1.0, V, s);
+            if (st != EXPD_OK) return st;
+        }
+        first = false;
+        double b2 = 0;
+        st = dots(V, 1, V, &b2);
+        if (st != EXPD_OK) return st;
+        const double beta = sqrt(b2);
+        relres = beta / cn;
+        if (relres <= p->tol) {
+            result = EXPD_OK;
+            break;
+        }
+        st = gm_axpby(p, n, 1.0 / beta, V, 0.0, V, s);
+        if (st != EXPD_OK) return st;
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int jdone = 0;
+        bool conv = false;
+        for (int j = 0; j < m && total < p->max_iter; ++j) {
+            double* vj1 = V + (size_t)(j + 1) * n;
+            st = apply_op(V + (size_t)j * n, w);
+            if (st != EXPD_OK) return st;
+            // classical Gram-Schmidt with one re-orthogonalisation
+            st = dots(V, j + 1, w, hh.data());
+            if (st == EXPD_OK) st = gm_update(p, V, n, j + 1, h, w, s);
+            if (st == EXPD_OK) st = dots(V, j + 1, w, hh2.data());
+            if (st == EXPD_OK) st = gm_update(p, V, n, j + 1, h, w, s);
+            if (st != EXPD_OK) return st;
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh2[i];
+            double wn2 = 0;
+            st = dots(w, 1, w, &wn2);
+            if (st != EXPD_OK) return st;
+            const double hn = sqrt(wn2);
+            H[(size_t)(j + 1) * m + j] = hn;
+            if (hn > 0) {
+                st = gm_axpby(p, n, 1.0 / hn, w, 0.0, vj1, s);
+                if (st != EXPD_OK) return st;
+            }
+            for (int i = 0; i < j; ++i) {
+                const double t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
+                H[(size_t)(i + 1) * m + j] = -sn[i] * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = t;
+            }
+            const double den = hypot(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j]);
+            cs[j] = H[(size_t)j * m + j] / den;
+            sn[j] = H[(size_t)(j + 1) * m + j] / den;
+            H[(size_t)j * m + j] = den;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++total;
+            jdone = j + 1;
+            relres = fabs(g[j + 1]) / cn;
+            if (info && total < EXPD_MAX_HISTORY) info->history[total] = relres;
+            if (relres <= p->tol) {
+                conv = true;
+                break;
+            }
+        }
+        // x += V y,  H y = g
+        for (int i = jdone - 1; i >= 0; --i) {
+            double acc = g[i];
+            for (int k = i + 1; k < jdone; ++k) acc -= H[(size_t)i * m + k] * y[k];
+            y[i] = acc / H[(size_t)i * m + i];
+        }
+        for (int i = 0; i < jdone; ++i) hh[i] = -y[i];
+        EXPD_CUDA_TRY(cudaMemcpyAsync(h, hh.data(), jdone * sizeof(double), cudaMemcpyHostToDevice, s));
+        st = gm_update(p, V, n, jdone, h, x, s);
+        if (st != EXPD_OK) return st;
+        EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+        if (conv) {
+            result = EXPD_OK;
+            break;
+        }
+    }
+    if (cn == 0) result = EXPD_OK;
+    if (info) {
+        info->iterations = total;
+        info->final_measure = relres;
+    }
+    st = write_solution(p, sg.U, s);
+    if (st != EXPD_OK) return st;
+    st = stage_out(p, sg, s);
+    if (st != EXPD_OK) return st;
+    if (result == EXPD_ERR_NOT_CONVERGED) g_err = "max_iter reached before tol";
+    return result;
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Vector kernels of the GMRES outer solver (Sec. 3.2): weighted multi-dot
+// products and multi-axpy over space-time vectors held in L_h's eigenbasis.
+//
+// The inner product is the physical one: for the periodic half spectrum a
+// mode with 0 < kx < NX/2 stands for itself and its conjugate and weighs 2
+// (Parseval), so GMRES in the eigenbasis reproduces physical-space GMRES.
+// Reductions are two-level with a fixed grid and fixed order (deterministic).
+#include "common.cuh"
+#include "plan.h"
+
+namespace {
+
+constexpr int GM_THREADS = 256;
+constexpr int GM_PER_THREAD = 4;
+constexpr int GM_CHUNK = GM_THREADS * GM_PER_THREAD;
+
+__device__ __forceinline__ double elem_weight(long long e, long long Mcol, int KX, int NX, int realcol) {
+    if (realcol) return 1.0;
+    const long long m = (e >> 1) % Mcol;
+    const int kx = (int)(m % KX);
+    return (kx == 0 || 2 * kx == NX) ? 1.0 : 2.0;
+}
+
+// partial[i][block] = sum over this block's elements of w_e V_i[e] x[e]
+__global__ void __launch_bounds__(GM_THREADS) dots_kernel(const double* __restrict__ V, long long ld, int k,
+                                                          const double* __restrict__ x, long long n,
+                                                          long long Mcol, int KX, int NX, int realcol,
+                                                          double* __restrict__ partial) {
+    __shared__ double red[GM_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = 0; i < k; ++i) {
+        double acc = 0.0;
+        for (long long base = (long long)blockIdx.x * GM_CHUNK; base < n; base += (long long)gridDim.x * GM_CHUNK) {
+#pragma unroll
+            for (int t = 0; t < GM_PER_THREAD; ++t) {
+                const long long e = base + t * GM_THREADS + threadIdx.x;
+                if (e < n) acc = fma(elem_weight(e, Mcol, KX, NX, realcol) * V[(long long)i * ld + e], x[e], acc);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) red[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < GM_THREADS / 32; ++w) s += red[w];
+            partial[(long long)i * gridDim.x + blockIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void dots_final(const double* __restrict__ partial, int grid, int k, double* __restrict__ h) {
+    const int i = blockIdx.x;
+    if (i >= k) return;
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int g = threadIdx.x; g < grid; g += blockDim.x) acc += partial[(long long)i * grid + g];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        h[i] = s;
+    }
+}
+
+__global__ void update_kernel(const double* __restrict__ V, long long ld, int k, const double* __restrict__ h,
+                              double* __restrict__ x, long long n) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double acc = x[e];
+        for (int i = 0; i < k; ++i) acc = fma(-h[i], V[(long long)i * ld + e], acc);
+        x[e] = acc;
+    }
+}
+
+__global__ void axpby_kernel(long long n, double a, const double* x, double b, double* y) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        y[e] = fma(a, x[e], b * y[e]);
+}
+
+}  // namespace
+
+long long eigen_elems(expd_plan p) { return (long long)p->Ns * p->Mcol * (p->realcol ? 1 : 2); }
+
+// The dots partial buffer lives at the end of the GMRES block (see api.cu).
+expd_status gm_dots(expd_plan p, const double* V, long long ld, int k, const double* w, double* h_dev,
+                    cudaStream_t s) {
+    const long long n = eigen_elems(p);
+    const int grid = p->sm_count * 4;
+    double* partial = h_dev + 128;  // caller reserves 128 + 65 * grid doubles
+    KProf kp(p, s, EXPD_K_GMRES, 8.0 * (k + 1) * (double)n, 3.0 * k * (double)n);
+    dots_kernel<<<grid, GM_THREADS, 0, s>>>(V, ld, k, w, n, p->Mcol, p->KX, p->NX, p->realcol, partial);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    dots_final<<<k, 256, 0, s>>>(partial, grid, k, h_dev);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+expd_status gm_update(expd_plan p, const double* V, long long ld, int k, const double* h_dev, double* w,
+                      cudaStream_t s) {
+    const long long n = eigen_elems(p);
+    KProf kp(p, s, EXPD_K_GMRES, 8.0 * (k + 2) * (double)n, 2.0 * k * (double)n);
+    update_kernel<<<p->sm_count * 8, 256, 0, s>>>(V, ld, k, h_dev, w, n);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+expd_status gm_axpby(expd_plan p, long long n, double a, const double* x, double b, double* y, cudaStream_t s) {
+    KProf kp(p, s, EXPD_K_GMRES, 24.0 * (double)n, 3.0 * (double)n);
+    axpby_kernel<<<p->sm_count * 8, 256, 0, s>>>(n, a, x, b, y);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}

@@ -1,0 +1,154 @@
+// Internal plan object and the host-side launchers shared by the .cu files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include <string>
+#include <vector>
+
+#include "expd.h"
+
+// Largest supported sizes (shared memory per warp-FFT column).
+#define EXPD_MAX_PERIODIC_N 4096
+#define EXPD_MAX_DIRICHLET_N 4096
+#define EXPD_MAX_NS 2048
+#define EXPD_TIME_COLS 8  // time-direction columns (spatial modes) per CTA
+
+expd_status expd_cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+expd_status expd_fail(expd_status s, const std::string& msg);
+
+struct TimeTables {
+    int L = 0, log2L = 0, bluestein = 0;
+    double* gamma = nullptr;  // [Ns]   alpha^(n/Ns)
+    void* lam = nullptr;      // [Ns]   lambda_n = alpha^(1/Ns) e^{2 pi i n/Ns}
+    void* tw = nullptr;       // [L/2]  e^{-2 pi i k/L}
+    void* chirp = nullptr;    // [Ns]   e^{+pi i n^2/Ns}           (Bluestein)
+    void* bplus = nullptr;    // [L]    FFT_L of conj-chirp kernel, bit-reversed order
+    void* bminus = nullptr;   // [L]    FFT_L of chirp kernel, bit-reversed order
+};
+
+struct expd_plan_s {
+    // ---- problem ----------------------------------------------------------
+    int ndim = 1, NX = 1, NY = 1;  // NX fast axis, NY slow axis (1 for 1D)
+    int bc = EXPD_BC_PERIODIC;
+    double LX = 1, LY = 1;
+    double a = 0, c = 0;
+    int nonlin = EXPD_NL_NONE;
+    double dt = 0;
+    int Nt = 0, order = 1, Ns = 0;
+    double alpha = 0;
+    int precision = EXPD_PREC_FP64, max_iter = 50, restart = 20, startup = EXPD_STARTUP_RAMP;
+    double tol = 1e-8;
+    double acoef[7][7] = {};  // acoef[q][j]: a_j of BDF-q, j = 1..q
+    double beta[7] = {};      // beta_q
+
+    // ---- layout -------------------------------------------------------------
+    long long M = 0;     // physical points per slice
+    int KX = 0;          // periodic: NX/2+1 complex per row; Dirichlet: NX real per row
+    long long Mcol = 0;  // time columns per slice (complex modes or real modes)
+    int realcol = 0;     // 1 for Dirichlet (real eigen-coefficients)
+    size_t esz = 16;     // bytes per eigen element (16 complex, 8 real)
+
+    // ---- tables ---------------------------------------------------------------
+    double* E = nullptr;       // [Mcol] exp(dt mu_m)
+    double2* Wx64 = nullptr;   // [NX/2+1] e^{-2 pi i k/NX}
+    float2* Wx32 = nullptr;
+    double2* Wy64 = nullptr;   // [NY/2]   e^{-2 pi i k/NY}
+    float2* Wy32 = nullptr;
+    double* Sx = nullptr;      // Dirichlet: [NX][NX] orthonormal DST-I matrix
+    double* Sy = nullptr;      // Dirichlet: [NY][NY]
+    TimeTables t64, t32;
+
+    // ---- state --------------------------------------------------------------
+    void* Uh = nullptr;        // [Ns][Mcol] iterate in L_h's eigenbasis
+    void* Fh = nullptr;        // [Ns][Mcol] known right-hand side f_s
+    void* Sh = nullptr;        // [order][Mcol] startup values u_0..u_{s-1}
+    void* fh = nullptr;        // [Nt][Mcol] transformed source (lazy)
+    void* NL64 = nullptr;      // [Ns][Mcol] N(v) transformed, float64
+    void* NL32 = nullptr;      // [Ns][Mcol] N(v) transformed, float32 (mixed)
+    void* work64 = nullptr;    // [Ns][NY][KX] double2 / physical scratch
+    void* work32 = nullptr;    // [Ns][NY][KX] float2 (mixed nonlinear)
+    double* startphys = nullptr;  // [order][M] physical u_0..u_{s-1}
+    double2* partial = nullptr;   // [time grid][Ns] per-slice norm partials
+    double* redout = nullptr;     // [4] reduced norms (device)
+    double* redhost = nullptr;    // [4] pinned host copy
+    int time_grid = 0;            // CTAs of the time kernel (multiple of SM count)
+    // host-pointer staging (lazy)
+    double* stage = nullptr;      // [(2*Nt + 1) * M]
+    size_t stage_elems = 0;
+    // GMRES basis (lazy)
+    void* gm = nullptr;
+    int gm_cols = 0;
+
+    size_t bytes = 0;             // device bytes held
+    int sm_count = 0;
+
+    // ---- per-kernel timing (expd_timing_enable / expd_timing_read) ----
+    int timing = 0;
+    long long launches = 0;
+    struct KRec {
+        int cls, e0;
+        double bytes, flops;
+    };
+    std::vector<cudaEvent_t> events;
+    std::vector<KRec> recs;
+    size_t ev_used = 0;
+};
+
+// Brackets one kernel launch: counts it and, with timing on, records events
+// around it on the launch stream.
+struct KProf {
+    expd_plan p;
+    cudaStream_t s;
+    int cls, e0 = -1;
+    double bytes, flops;
+    KProf(expd_plan p_, cudaStream_t s_, int cls_, double bytes_, double flops_ = 0.0);
+    ~KProf();
+};
+
+// ---- spatial transforms (spatial.cu) ----------------------------------------
+// physical [nslices][NY][NX] float64 <-> eigen [nslices][Mcol], float64.
+expd_status spatial_forward64(expd_plan p, const double* phys, void* eig, int nslices, cudaStream_t s);
+expd_status spatial_inverse64(expd_plan p, const void* eig, double* phys, int nslices, cudaStream_t s);
+// out = transform of N(inverse transform of Uh) for the Ns unknown slices, in
+// float32 (f32 = 1, out is float2/float) or float64.
+expd_status nonlinear_eval(expd_plan p, const void* Uh, void* out, int f32, cudaStream_t s);
+// u = solution of u - bdt N(u) = w, pointwise (float64 physical).
+expd_status pointwise_solve(expd_plan p, const double* w, double* u, long long n, double bdt, cudaStream_t s);
+// out[m] = sum_{j=1..q} coef[j] E_m^j in[j][m] + g * src[m]   (eigen arrays)
+expd_status eigen_combine(expd_plan p, void* out, const void* const* in, const double* coef, int q,
+                          const void* src, double g, cudaStream_t s);
+// f_s: Fh[i] = bdt f^(s+i) + sum_{j: s+i-j<s} a_j E^j Sh[s+i-j]
+expd_status assemble_rhs(expd_plan p, const void* fh, cudaStream_t s);
+
+// ---- time direction (time_kernel.cu) -----------------------------------------
+struct TimeOp {
+    const void* X = nullptr;   // state / operand in the eigenbasis (may be null)
+    const void* F = nullptr;   // additive right-hand side (may be null)
+    const void* NL = nullptr;  // transformed nonlinearity (may be null)
+    int nl_f32 = 0;
+    double bdt = 0;            // coefficient of NL
+    double sigR = -1;          // coefficient of R_s X
+    int precond = 1;           // apply (R_s^alpha)^{-1} to the combination
+    int accum = 0;             // X += result (X must be writable) instead of out = result
+    void* out = nullptr;
+    int f32 = 0;               // preconditioner precision
+};
+expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s);
+// reduce per-slice partials: redout[0] = max_n ||res_n||, [1] = max_n ||X_n||,
+// [2] = sum_n ||res_n||^2, [3] = sum_n ||X_n||^2 (weighted eigen norms).
+expd_status time_reduce(expd_plan p, cudaStream_t s);
+expd_status time_tables_build(expd_plan p, cudaStream_t s);
+void time_tables_free(expd_plan p);
+
+// ---- GMRES vector kernels (gmres.cu) ---------------------------------------------
+// weighted dot products h[i] = <V_i, w> for i < k (V_i = basis column i), deterministic
+expd_status gm_dots(expd_plan p, const double* V, long long ld, int k, const double* w, double* h_dev,
+                    cudaStream_t s);
+// w -= sum_i h[i] V_i
+expd_status gm_update(expd_plan p, const double* V, long long ld, int k, const double* h_dev, double* w,
+                      cudaStream_t s);
+// y = a*x + b*y  (plain elementwise)
+expd_status gm_axpby(expd_plan p, long long n, double a, const double* x, double b, double* y, cudaStream_t s);
+long long eigen_elems(expd_plan p);  // doubles per space-time eigen vector

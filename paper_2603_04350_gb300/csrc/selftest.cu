@@ -1,0 +1,171 @@
+// Host-only self-test of the device FFT routines and of the per-column
+// preconditioner solve (time_column.cuh), run without a GPU: the routines are
+// __host__ __device__ and run here with a single lane.  Compared with naive
+// O(n^2) DFTs.  Exit status 0 on success.  Not part of libexpd.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <complex>
+#include <random>
+#include <vector>
+
+#include "common.cuh"
+#include "time_column.cuh"
+
+typedef std::complex<double> cd;
+
+template <typename T2, typename T>
+static std::vector<T2> to_dev(const std::vector<cd>& v) {
+    std::vector<T2> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        o[i].x = (T)v[i].real();
+        o[i].y = (T)v[i].imag();
+    }
+    return o;
+}
+
+static std::vector<cd> naive_dft(const std::vector<cd>& x, int sign) {
+    const size_t n = x.size();
+    std::vector<cd> X(n);
+    for (size_t k = 0; k < n; ++k) {
+        cd acc = 0;
+        for (size_t j = 0; j < n; ++j) {
+            const long long r = (long long)((k * j) % n);
+            acc += x[j] * std::polar(1.0, sign * 2.0 * M_PI * (double)r / (double)n);
+        }
+        X[k] = acc;
+    }
+    return X;
+}
+
+static int failures = 0;
+
+static void check(const char* what, double err, double tol, int a, int b) {
+    if (!(err <= tol)) {
+        printf("FAIL %s (%d, %d): err %.3e > %.1e\n", what, a, b, err, tol);
+        ++failures;
+    }
+}
+
+template <typename T, typename T2>
+static void test_fft(int log2n, int sign, double tol, std::mt19937_64& rng) {
+    const int n = 1 << log2n;
+    std::normal_distribution<double> N01;
+    std::vector<cd> x(n), tw(n / 2 > 0 ? n / 2 : 1);
+    for (auto& v : x) v = cd(N01(rng), N01(rng));
+    for (int k = 0; k < n / 2; ++k) tw[k] = std::polar(1.0, -2.0 * M_PI * k / n);
+    const std::vector<cd> ref = naive_dft(x, sign);
+    double scale = 0;
+    for (auto& v : ref) scale = std::max(scale, std::abs(v));
+    std::vector<T2> twd = to_dev<T2, T>(tw);
+    // DIT: bit-reversed in, natural out
+    std::vector<cd> xb(n);
+    for (int j = 0; j < n; ++j) xb[bitrev(j, log2n)] = x[j];
+    std::vector<T2> buf = to_dev<T2, T>(xb);
+    fft_dit(buf.data(), log2n, twd.data(), 1, sign, 0, 1);
+    double err = 0;
+    for (int k = 0; k < n; ++k) err = std::max(err, std::abs(cd(buf[k].x, buf[k].y) - ref[k]));
+    check(sizeof(T) == 8 ? "fft_dit double" : "fft_dit float", err / scale, tol, n, sign);
+    // DIF: natural in, bit-reversed out
+    buf = to_dev<T2, T>(x);
+    fft_dif(buf.data(), log2n, twd.data(), 1, sign, 0, 1);
+    err = 0;
+    for (int k = 0; k < n; ++k) {
+        const T2 v = buf[bitrev(k, log2n)];
+        err = std::max(err, std::abs(cd(v.x, v.y) - ref[k]));
+    }
+    check(sizeof(T) == 8 ? "fft_dif double" : "fft_dif float", err / scale, tol, n, sign);
+    // strided twiddle table (table of 2n used with stride 2)
+    std::vector<cd> tw2(n);
+    for (int k = 0; k < n; ++k) tw2[k] = std::polar(1.0, -2.0 * M_PI * k / (2 * n));
+    std::vector<T2> tw2d = to_dev<T2, T>(tw2);
+    buf = to_dev<T2, T>(xb);
+    fft_dit(buf.data(), log2n, tw2d.data(), 2, sign, 0, 1);
+    err = 0;
+    for (int k = 0; k < n; ++k) err = std::max(err, std::abs(cd(buf[k].x, buf[k].y) - ref[k]));
+    check("fft_dit strided table", err / scale, tol, n, sign);
+}
+
+template <typename T, typename T2>
+static void test_column(int Ns, int order, double E, double alpha, double tol, std::mt19937_64& rng) {
+    static const double bdf[7][7] = {{0},
+                                     {0, 1.0},
+                                     {0, 4.0 / 3, -1.0 / 3},
+                                     {0, 18.0 / 11, -9.0 / 11, 2.0 / 11},
+                                     {0, 48.0 / 25, -36.0 / 25, 16.0 / 25, -3.0 / 25},
+                                     {0, 300.0 / 137, -300.0 / 137, 200.0 / 137, -75.0 / 137, 12.0 / 137},
+                                     {0, 360.0 / 147, -450.0 / 147, 400.0 / 147, -225.0 / 147, 72.0 / 147, -10.0 / 147}};
+    const TimeTablesHost t = time_tables_host(Ns, alpha);
+    std::normal_distribution<double> N01;
+    std::vector<cd> q(Ns);
+    for (auto& v : q) v = cd(N01(rng), N01(rng));
+    double cj[7] = {0};
+    double Ej = 1.0;
+    for (int j = 1; j <= order; ++j) {
+        Ej *= E;
+        cj[j] = bdf[order][j] * Ej;
+    }
+    // reference: s = Gamma^{-1} F* diag(1/d) F Gamma q
+    std::vector<cd> y(Ns);
+    for (int n = 0; n < Ns; ++n) y[n] = t.gamma[n] * q[n];
+    std::vector<cd> Y = naive_dft(y, +1);
+    for (int k = 0; k < Ns; ++k) {
+        cd d = 1.0, lk = t.lam[k], lp = 1.0;
+        for (int j = 1; j <= order; ++j) {
+            lp *= lk;
+            d -= cj[j] * lp;
+        }
+        Y[k] /= d;
+    }
+    std::vector<cd> z = naive_dft(Y, -1);
+    std::vector<cd> sref(Ns);
+    double scale = 0;
+    for (int n = 0; n < Ns; ++n) {
+        sref[n] = z[n] / ((double)Ns * t.gamma[n]);
+        scale = std::max(scale, std::abs(sref[n]));
+    }
+    // routine under test
+    std::vector<cd> w(t.L, 0.0);
+    for (int n = 0; n < Ns; ++n) w[t.bluestein ? n : bitrev(n, t.log2L)] = y[n];
+    std::vector<T2> wd = to_dev<T2, T>(w), twd = to_dev<T2, T>(t.tw), lamd = to_dev<T2, T>(t.lam);
+    std::vector<T2> chd = to_dev<T2, T>(t.chirp), bpd = to_dev<T2, T>(t.bplus), bmd = to_dev<T2, T>(t.bminus);
+    const double sc = precond_column<T, T2>(wd.data(), Ns, t.L, t.log2L, t.bluestein, twd.data(), lamd.data(),
+                                            t.bluestein ? chd.data() : nullptr, t.bluestein ? bpd.data() : nullptr,
+                                            t.bluestein ? bmd.data() : nullptr, cj, order, 0, 1);
+    double err = 0;
+    for (int n = 0; n < Ns; ++n) {
+        const T2 v = wd[t.bluestein ? n : bitrev(n, t.log2L)];
+        const cd s = cd(v.x, v.y) * sc / t.gamma[n];
+        err = std::max(err, std::abs(s - sref[n]));
+    }
+    check(sizeof(T) == 8 ? "precond_column double" : "precond_column float", err / scale, tol, Ns, order);
+}
+
+int main() {
+    std::mt19937_64 rng(1234);
+    for (int l = 1; l <= 12; ++l)
+        for (int sign = -1; sign <= 1; sign += 2) {
+            test_fft<double, double2>(l, sign, 1e-13, rng);
+            test_fft<float, float2>(l, sign, 2e-5, rng);
+        }
+    const int sizes[] = {2, 3, 4, 5, 7, 8, 11, 15, 16, 27, 31, 32, 59, 63, 64, 123, 127, 128, 251, 255, 256, 1000};
+    const int orders[] = {1, 2, 3, 6};
+    const double Es[] = {1.0, 0.7, 0.0};
+    for (int Ns : sizes)
+        for (int order : orders) {
+            if (Ns < order + 1) continue;
+            for (double E : Es) {
+                test_column<double, double2>(Ns, order, E, 1e-3, 1e-11, rng);
+                test_column<double, double2>(Ns, order, E, 0.3, 1e-12, rng);
+                test_column<float, float2>(Ns, order, E, 0.3, 1e-4 * std::max(1.0, Ns / 256.0), rng);
+                test_column<float, float2>(Ns, order, E, 1e-3, 3e-3, rng);
+            }
+        }
+    if (failures) {
+        printf("%d failures\n", failures);
+        return 1;
+    }
+    printf("OK\n");
+    return 0;
+}

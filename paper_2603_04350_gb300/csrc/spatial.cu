@@ -1,0 +1,490 @@
+// Spatial side of the hot path: the change of basis to L_h's eigenvectors and
+// back (the spatial half of the preconditioner's Step (b), Eq. (3.3), which is
+// diagonal in that basis), the pointwise nonlinearity and the pointwise implicit
+// solve of the IF scheme (Eq. (6.1)), and the eigen-space combinations that build
+// the startup ramp and the known right-hand side f_s (Eq. (4.2), Sec. 5).
+//
+// Periodic grids: real <-> half-spectrum FFTs.  The contiguous axis is one warp
+// per row (a real row of NX samples packed as NX/2 complex values, a radix-2
+// FFT in shared memory, then the even/odd split); the strided axis is one warp
+// per column of a [NY x C] tile staged through shared memory so that global
+// loads stay coalesced along the contiguous axis.  The nonlinear evaluation
+// fuses inverse row FFT, N(u) and forward row FFT in one pass.
+//
+// Dirichlet grids: the orthonormal DST-I as a dense matrix product (float64).
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "plan.h"
+
+namespace {
+
+template <typename T2>
+__device__ __forceinline__ T2 cvt2(double2 v);
+template <>
+__device__ __forceinline__ double2 cvt2<double2>(double2 v) { return v; }
+template <>
+__device__ __forceinline__ float2 cvt2<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+template <typename T2>
+__device__ __forceinline__ T2 cvt2(float2 v);
+template <>
+__device__ __forceinline__ double2 cvt2<double2>(float2 v) { return to_c64(v); }
+template <>
+__device__ __forceinline__ float2 cvt2<float2>(float2 v) { return v; }
+
+template <typename R>
+__device__ __forceinline__ R nl_ac(R u) { return u - u * u * u; }
+
+// ------------------------------------------------------------ row pass ----
+// KIND 0: complex half-spectrum row (KX = NX/2+1) -> real row      (c2r)
+// KIND 1: real row -> complex half-spectrum row                     (r2c)
+// KIND 2: c2r, u -> N(u), r2c (fused nonlinear evaluation)
+template <typename PT, typename TIN, typename TOUT, int KIND>
+__global__ void row_kernel(const TIN* in, TOUT* out, long long rows, int NX,
+                           int log2NH, const typename cplx<PT>::t* __restrict__ Wg, PT scale, int nonlin) {
+    typedef typename cplx<PT>::t PT2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int NH = NX >> 1;
+    const int KX = NH + 1;
+    PT2* W = reinterpret_cast<PT2*>(smem_raw);
+    PT2* buf = W + ((KX + 1) & ~1);
+    for (int i = threadIdx.x; i < KX; i += blockDim.x) W[i] = Wg[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, R = blockDim.x >> 5;
+    PT2* s = buf + (size_t)warp * NH;
+    for (long long row = (long long)blockIdx.x * R + warp; row < rows; row += (long long)gridDim.x * R) {
+        if constexpr (KIND == 1) {
+            const TIN* x = in + row * NX;
+            for (int n = lane; n < NH; n += 32)
+                s[bitrev(n, log2NH)] = c2((PT)x[2 * n], (PT)x[2 * n + 1]);
+        } else {
+            // Hermitian half spectrum -> packed even/odd spectrum Z = E + i O
+            const TIN* X = in + row * KX;
+            for (int k = lane; k < NH; k += 32) {
+                const PT2 xk = cvt2<PT2>(X[k]);
+                const PT2 xm = cconj(cvt2<PT2>(X[NH - k]));
+                const PT2 e = cscale(cadd(xk, xm), (PT)0.5);
+                const PT2 o = cmulc(cscale(csub(xk, xm), (PT)0.5), W[k]);
+                s[bitrev(k, log2NH)] = cadd(e, cmuli(o));
+            }
+        }
+        EXPD_SYNCWARP();
+        fft_dit(s, log2NH, W, 2, KIND == 1 ? -1 : +1, lane, 32);  // natural order
+        if constexpr (KIND == 0) {
+            // z_n = x_{2n} + i x_{2n+1}
+            TOUT* x = out + row * NX;
+            for (int n = lane; n < NH; n += 32) {
+                const PT2 z = s[n];
+                x[2 * n] = (TOUT)(z.x * scale);
+                x[2 * n + 1] = (TOUT)(z.y * scale);
+            }
+            EXPD_SYNCWARP();
+        } else {
+        if constexpr (KIND == 2) {
+            for (int n = lane; n < NH; n += 32) {
+                PT2 z = cscale(s[n], scale);
+                if (nonlin == EXPD_NL_ALLEN_CAHN) z = c2(nl_ac(z.x), nl_ac(z.y));
+                else z = c2((PT)0, (PT)0);
+                s[n] = z;
+            }
+            EXPD_SYNCWARP();
+            fft_dif(s, log2NH, W, 2, -1, lane, 32);  // bit-reversed order
+        }
+        // even/odd split: X_k = E_k + W^k O_k, k = 0..NH
+        TOUT* X = out + row * KX;
+        for (int k = lane; k <= NH; k += 32) {
+            const int k1 = (k == NH) ? 0 : k;
+            const int k2 = (k == 0) ? 0 : NH - k;
+            const int p1 = (KIND == 2) ? (int)bitrev(k1, log2NH) : k1;
+            const int p2 = (KIND == 2) ? (int)bitrev(k2, log2NH) : k2;
+            const PT2 zk = s[p1];
+            const PT2 zm = cconj(s[p2]);
+            const PT2 e = cscale(cadd(zk, zm), (PT)0.5);
+            const PT2 o = cscale(cmuli(csub(zm, zk)), (PT)0.5);
+            X[k] = cvt2<TOUT>(cadd(e, cmul(W[k], o)));
+        }
+        EXPD_SYNCWARP();
+        }
+    }
+}
+
+// --------------------------------------------------------- column pass ----
+// In-place-capable c2c FFT along the strided axis of [nslices][NY][KX] arrays.
+template <typename PT, typename TIN, typename TOUT>
+__global__ void col_kernel(const TIN* __restrict__ in, TOUT* __restrict__ out, int NY, int KX, int log2NY,
+                           int C, const typename cplx<PT>::t* __restrict__ Wg, int sign, PT scale) {
+    typedef typename cplx<PT>::t PT2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PT2* W = reinterpret_cast<PT2*>(smem_raw);
+    const int nw = NY >> 1;
+    PT2* buf = W + ((nw + 1) & ~1);
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) W[i] = Wg[i];
+    const long long base = (long long)blockIdx.y * NY * KX;
+    const int kx0 = blockIdx.x * C;
+    for (int idx = threadIdx.x; idx < NY * C; idx += blockDim.x) {
+        const int y = idx / C, c = idx - y * C, kx = kx0 + c;
+        PT2 v = c2((PT)0, (PT)0);
+        if (kx < KX) v = cvt2<PT2>(in[base + (long long)y * KX + kx]);
+        buf[c * NY + bitrev(y, log2NY)] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < C && kx0 + warp < KX) fft_dit(buf + warp * NY, log2NY, W, 1, sign, lane, 32);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NY * C; idx += blockDim.x) {
+        const int y = idx / C, c = idx - y * C, kx = kx0 + c;
+        if (kx < KX) out[base + (long long)y * KX + kx] = cvt2<TOUT>(cscale(buf[c * NY + y], scale));
+    }
+}
+
+// ---------------------------------------------------------- dense DST ----
+// C[b] = A[b] (MxK) * B[b] (KxN), row-major, float64, 64x64 tiles.
+__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, const double* __restrict__ A,
+                                                    long long lda, long long sA, const double* __restrict__ B,
+                                                    long long ldb, long long sB, double* __restrict__ C,
+                                                    long long ldc, long long sC) {
+    const long long b = blockIdx.z;
+    A += b * sA;
+    B += b * sB;
+    C += b * sC;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    __shared__ double As[16][65];
+    __shared__ double Bs[16][65];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int i = tid; i < 64 * 16; i += 256) {
+            const int r = i >> 4, kk = i & 15, gm = m0 + r, gk = k0 + kk;
+            As[kk][r] = (gm < M && gk < K) ? A[(long long)gm * lda + gk] : 0.0;
+        }
+        for (int i = tid; i < 16 * 64; i += 256) {
+            const int kk = i >> 6, cc = i & 63, gk = k0 + kk, gn = n0 + cc;
+            Bs[kk][cc] = (gk < K && gn < N) ? B[(long long)gk * ldb + gn] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
+            if (gm < M && gn < N) C[(long long)gm * ldc + gn] = acc[i][j];
+        }
+}
+
+// ----------------------------------------------------------- pointwise ----
+__global__ void newton_kernel(const double* w, double* u, long long n, double bdt,
+                              int nonlin) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double wi = w[i];
+        double x = wi;
+        if (nonlin == EXPD_NL_ALLEN_CAHN) {
+            for (int it = 0; it < 60; ++it) {
+                const double g = x - bdt * (x - x * x * x) - wi;
+                const double dg = 1.0 - bdt + 3.0 * bdt * x * x;
+                const double dx = g / dg;
+                x -= dx;
+                if (fabs(dx) <= 1e-16 * fmax(1.0, fabs(x))) break;
+            }
+        }
+        u[i] = x;
+    }
+}
+
+__global__ void nl_pointwise_kernel(double* __restrict__ u, long long n, int nonlin) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double x = u[i];
+        u[i] = (nonlin == EXPD_NL_ALLEN_CAHN) ? x - x * x * x : 0.0;
+    }
+}
+
+struct CombineArgs {
+    const double* in[6];
+    double coef[6];
+    int q;
+    const double* src;
+    double g;
+    double* out;
+    const double* E;
+    long long nelem;
+    int eshift;
+};
+
+__global__ void combine_kernel(CombineArgs a) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < a.nelem;
+         e += (long long)gridDim.x * blockDim.x) {
+        const double Em = a.E[e >> a.eshift];
+        double acc = a.src ? a.g * a.src[e] : 0.0;
+        double Ej = 1.0;
+        for (int j = 0; j < a.q; ++j) {
+            Ej *= Em;
+            acc = fma(a.coef[j] * Ej, a.in[j][e], acc);
+        }
+        a.out[e] = acc;
+    }
+}
+
+struct RhsArgs {
+    const double* fh;  // [Nt][nelem] or null
+    const double* Sh;  // [s][nelem]
+    double* Fh;        // [Ns][nelem]
+    const double* E;
+    double a[7];
+    double bdt;
+    long long nelem;
+    int eshift, s, Ns;
+};
+
+__global__ void rhs_kernel(RhsArgs r) {
+    const long long total = r.nelem * r.Ns;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / r.nelem);
+        const long long e = idx - (long long)i * r.nelem;
+        const int n = r.s + i;
+        double acc = r.fh ? r.bdt * r.fh[(long long)(n - 1) * r.nelem + e] : 0.0;
+        if (i < r.s) {
+            const double Em = r.E[e >> r.eshift];
+            double Ej = 1.0;
+            for (int j = 1; j <= r.s; ++j) {
+                Ej *= Em;
+                if (n - j < r.s) acc = fma(r.a[j] * Ej, r.Sh[(long long)(n - j) * r.nelem + e], acc);
+            }
+        }
+        r.Fh[idx] = acc;
+    }
+}
+
+int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152LL * 32) b = 152LL * 32;
+    return (int)b;
+}
+
+template <typename PT>
+const typename cplx<PT>::t* Wx(expd_plan p);
+template <>
+const double2* Wx<double>(expd_plan p) { return p->Wx64; }
+template <>
+const float2* Wx<float>(expd_plan p) { return p->Wx32; }
+template <typename PT>
+const typename cplx<PT>::t* Wy(expd_plan p);
+template <>
+const double2* Wy<double>(expd_plan p) { return p->Wy64; }
+template <>
+const float2* Wy<float>(expd_plan p) { return p->Wy32; }
+
+template <typename PT, typename TIN, typename TOUT, int KIND>
+expd_status launch_row(expd_plan p, const TIN* in, TOUT* out, long long rows, PT scale, cudaStream_t s) {
+    typedef typename cplx<PT>::t PT2;
+    const int NH = p->NX / 2;
+    const size_t per_row = (size_t)NH * sizeof(PT2);
+    int R = (int)std::max<size_t>(1, std::min<size_t>(8, (48 * 1024) / per_row));
+    const size_t smem = (size_t)((NH + 2) & ~1) * sizeof(PT2) + (size_t)R * per_row;
+    auto kern = row_kernel<PT, TIN, TOUT, KIND>;
+    if (smem > 48 * 1024)
+        EXPD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    long long blocks = (rows + R - 1) / R;
+    if (blocks > (long long)p->sm_count * 16) blocks = (long long)p->sm_count * 16;
+    const double in_row = (KIND == 1 ? p->NX : NH + 1) * (double)sizeof(TIN);
+    const double out_row = (KIND == 0 ? p->NX : NH + 1) * (double)sizeof(TOUT);
+    const double fl = (KIND == 2 ? 2.0 : 1.0) * 2.5 * p->NX * ilog2(p->NX) * (double)rows;
+    KProf kp(p, s, EXPD_K_FFT_ROW, (double)rows * (in_row + out_row), fl);
+    kern<<<(int)blocks, 32 * R, smem, s>>>(in, out, rows, p->NX, ilog2(NH), Wx<PT>(p), scale, p->nonlin);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+template <typename PT, typename TIN, typename TOUT>
+expd_status launch_col(expd_plan p, const TIN* in, TOUT* out, int nslices, int sign, PT scale, cudaStream_t s) {
+    typedef typename cplx<PT>::t PT2;
+    const int NY = p->NY, KX = p->KX;
+    const size_t per_col = (size_t)NY * sizeof(PT2);
+    int C = (int)std::max<size_t>(1, std::min<size_t>(8, (64 * 1024) / per_col));
+    const size_t smem = (size_t)(((NY >> 1) + 1) & ~1) * sizeof(PT2) + (size_t)C * per_col;
+    auto kern = col_kernel<PT, TIN, TOUT>;
+    if (smem > 48 * 1024)
+        EXPD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((KX + C - 1) / C, nslices);
+    KProf kp(p, s, EXPD_K_FFT_COL, (double)nslices * NY * KX * (sizeof(TIN) + sizeof(TOUT)),
+             5.0 * NY * ilog2(NY) * (double)KX * nslices);
+    kern<<<grid, 32 * C, smem, s>>>(in, out, NY, KX, ilog2(NY), C, Wy<PT>(p), sign, scale);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+expd_status dgemm(expd_plan p, const double* A, long long lda, long long sA, const double* B, long long ldb,
+                  long long sB, double* C, long long ldc, long long sC, int M, int N, int K, int batch,
+                  cudaStream_t s) {
+    dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
+    const double abytes = (sA ? (double)M * K : 0.0) + (sB ? (double)K * N : 0.0);
+    KProf kp(p, s, EXPD_K_DST, 8.0 * batch * (abytes + (double)M * N), 2.0 * M * N * (double)K * batch);
+    dgemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+// Orthonormal 2D DST-I: Y = Sy X Sx (S symmetric and its own inverse).
+expd_status dst2(expd_plan p, const double* X, double* Y, int ns, double* tmp, cudaStream_t s) {
+    const int NX = p->NX, NY = p->NY;
+    if (p->ndim == 1) return dgemm(p, X, NX, (long long)NX, p->Sx, NX, 0, Y, NX, 0, ns, NX, NX, 1, s);
+    expd_status st = dgemm(p, X, NX, (long long)NX, p->Sx, NX, 0, tmp, NX, 0, ns * NY, NX, NX, 1, s);
+    if (st != EXPD_OK) return st;
+    return dgemm(p, p->Sy, NY, 0, tmp, NX, (long long)NY * NX, Y, NX, (long long)NY * NX, NY, NX, NY, ns, s);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers ----
+expd_status spatial_forward64(expd_plan p, const double* phys, void* eig, int nslices, cudaStream_t s) {
+    const int chunk = p->Ns;
+    for (int b0 = 0; b0 < nslices; b0 += chunk) {
+        const int ns = std::min(chunk, nslices - b0);
+        const double* x = phys + (long long)b0 * p->M;
+        expd_status st;
+        if (p->bc == EXPD_BC_DIRICHLET) {
+            double* y = static_cast<double*>(eig) + (long long)b0 * p->Mcol;
+            st = dst2(p, x, y, ns, static_cast<double*>(p->work64), s);
+        } else {
+            double2* y = static_cast<double2*>(eig) + (long long)b0 * p->Mcol;
+            if (p->ndim == 1) {
+                st = launch_row<double, double, double2, 1>(p, x, y, ns, 1.0, s);
+            } else {
+                double2* w = static_cast<double2*>(p->work64);
+                st = launch_row<double, double, double2, 1>(p, x, w, (long long)ns * p->NY, 1.0, s);
+                if (st == EXPD_OK) st = launch_col<double, double2, double2>(p, w, y, ns, -1, 1.0, s);
+            }
+        }
+        if (st != EXPD_OK) return st;
+    }
+    return EXPD_OK;
+}
+
+expd_status spatial_inverse64(expd_plan p, const void* eig, double* phys, int nslices, cudaStream_t s) {
+    const int chunk = p->Ns;
+    for (int b0 = 0; b0 < nslices; b0 += chunk) {
+        const int ns = std::min(chunk, nslices - b0);
+        double* x = phys + (long long)b0 * p->M;
+        expd_status st;
+        if (p->bc == EXPD_BC_DIRICHLET) {
+            const double* y = static_cast<const double*>(eig) + (long long)b0 * p->Mcol;
+            st = dst2(p, y, x, ns, static_cast<double*>(p->work64), s);
+        } else {
+            const double2* y = static_cast<const double2*>(eig) + (long long)b0 * p->Mcol;
+            const double sx = 1.0 / (p->NX / 2);
+            if (p->ndim == 1) {
+                st = launch_row<double, double2, double, 0>(p, y, x, ns, sx, s);
+            } else {
+                double2* w = static_cast<double2*>(p->work64);
+                st = launch_col<double, double2, double2>(p, y, w, ns, +1, 1.0 / p->NY, s);
+                if (st == EXPD_OK) st = launch_row<double, double2, double, 0>(p, w, x, (long long)ns * p->NY, sx, s);
+            }
+        }
+        if (st != EXPD_OK) return st;
+    }
+    return EXPD_OK;
+}
+
+expd_status nonlinear_eval(expd_plan p, const void* Uh, void* out, int f32, cudaStream_t s) {
+    const int Ns = p->Ns;
+    if (p->bc == EXPD_BC_DIRICHLET) {
+        // float64 only: inverse DST, N(u), forward DST
+        double* phys = static_cast<double*>(p->work64) + (long long)Ns * p->M;
+        expd_status st = spatial_inverse64(p, Uh, phys, Ns, s);
+        if (st != EXPD_OK) return st;
+        const long long n = (long long)Ns * p->M;
+        KProf kp(p, s, EXPD_K_POINTWISE, 16.0 * n, 3.0 * n);
+        nl_pointwise_kernel<<<grid_for(n, 256), 256, 0, s>>>(phys, n, p->nonlin);
+        EXPD_CUDA_TRY(cudaGetLastError());
+        return spatial_forward64(p, phys, out, Ns, s);
+    }
+    const double2* U = static_cast<const double2*>(Uh);
+    const long long rows = (long long)Ns * p->NY;
+    if (f32) {
+        const float sx = 1.0f / (p->NX / 2);
+        float2* o = static_cast<float2*>(out);
+        if (p->ndim == 1) return launch_row<float, double2, float2, 2>(p, U, o, rows, sx, s);
+        float2* w = static_cast<float2*>(p->work32);
+        expd_status st = launch_col<float, double2, float2>(p, U, w, Ns, +1, 1.0f / p->NY, s);
+        if (st == EXPD_OK) st = launch_row<float, float2, float2, 2>(p, w, w, rows, sx, s);
+        if (st == EXPD_OK) st = launch_col<float, float2, float2>(p, w, o, Ns, -1, 1.0f, s);
+        return st;
+    }
+    const double sx = 1.0 / (p->NX / 2);
+    double2* o = static_cast<double2*>(out);
+    if (p->ndim == 1) return launch_row<double, double2, double2, 2>(p, U, o, rows, sx, s);
+    double2* w = static_cast<double2*>(p->work64);
+    expd_status st = launch_col<double, double2, double2>(p, U, w, Ns, +1, 1.0 / p->NY, s);
+    if (st == EXPD_OK) st = launch_row<double, double2, double2, 2>(p, w, w, rows, sx, s);
+    if (st == EXPD_OK) st = launch_col<double, double2, double2>(p, w, o, Ns, -1, 1.0, s);
+    return st;
+}
+
+expd_status pointwise_solve(expd_plan p, const double* w, double* u, long long n, double bdt, cudaStream_t s) {
+    KProf kp(p, s, EXPD_K_POINTWISE, 16.0 * n, 30.0 * n);
+    newton_kernel<<<grid_for(n, 256), 256, 0, s>>>(w, u, n, bdt, p->nonlin);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+expd_status eigen_combine(expd_plan p, void* out, const void* const* in, const double* coef, int q,
+                          const void* src, double g, cudaStream_t s) {
+    CombineArgs a;
+    for (int j = 0; j < 6; ++j) {
+        a.in[j] = j < q ? static_cast<const double*>(in[j]) : nullptr;
+        a.coef[j] = j < q ? coef[j] : 0.0;
+    }
+    a.q = q;
+    a.src = static_cast<const double*>(src);
+    a.g = g;
+    a.out = static_cast<double*>(out);
+    a.E = p->E;
+    a.eshift = p->realcol ? 0 : 1;
+    a.nelem = p->Mcol << a.eshift;
+    KProf kp(p, s, EXPD_K_POINTWISE, 8.0 * a.nelem * (q + (src ? 2 : 1)), 2.0 * a.nelem * q);
+    combine_kernel<<<grid_for(a.nelem, 256), 256, 0, s>>>(a);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+expd_status assemble_rhs(expd_plan p, const void* fh, cudaStream_t s) {
+    RhsArgs r;
+    r.fh = static_cast<const double*>(fh);
+    r.Sh = static_cast<const double*>(p->Sh);
+    r.Fh = static_cast<double*>(p->Fh);
+    r.E = p->E;
+    for (int j = 0; j < 7; ++j) r.a[j] = p->acoef[p->order][j];
+    r.bdt = p->beta[p->order] * p->dt;
+    r.eshift = p->realcol ? 0 : 1;
+    r.nelem = p->Mcol << r.eshift;
+    r.s = p->order;
+    r.Ns = p->Ns;
+    KProf kp(p, s, EXPD_K_POINTWISE, 8.0 * r.nelem * ((fh ? 2.0 : 1.0) * r.Ns + r.s), 2.0 * r.nelem * r.s * r.s);
+    rhs_kernel<<<grid_for(r.nelem * r.Ns, 256), 256, 0, s>>>(r);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}

@@ -1,0 +1,138 @@
+// Steps (a)-(c) of the preconditioner solve (Eq. (3.3) / Eq. (4.5)) on one
+// time column of length Ns held in a buffer w of length L, executed by one warp
+// (or, on the host self-test, by a single "lane").
+//
+// On entry w holds y_n = alpha^(n/Ns) q_n at position n (Bluestein, Ns not a
+// power of two) or at position bitrev(n) (Ns = L a power of two).
+// On exit position pos(n) (same rule) holds v_n with
+//     s_n = v_n * scale / alpha^(n/Ns),
+//     s   = Gamma^{-1} F^* diag(1/d) F Gamma q   (F: omega = e^{+2 pi i/Ns})
+// where d_k = 1 - sum_{j=1..order} cj[j] lambda_k^j and cj[j] = a_j E^j.
+#pragma once
+
+#include "common.cuh"
+
+template <typename PT, typename PT2>
+EXPD_HD double precond_column(PT2* w, int Ns, int L, int log2L, int bluestein, const PT2* tw, const PT2* lam,
+                              const PT2* chirp, const PT2* bp, const PT2* bm, const double* cj, int order,
+                              int lane, int nlanes) {
+    if (bluestein) {
+        for (int n = lane; n < Ns; n += nlanes) w[n] = cmul(w[n], chirp[n]);
+        for (int n = Ns + lane; n < L; n += nlanes) w[n] = c2((PT)0, (PT)0);
+        EXPD_SYNCWARP();
+        // Step (a) by chirp-z: Y_k = c_k sum_n (y_n c_n) conj(c_{k-n}),
+        // the convolution as FFT_L^{-1}(FFT_L(.) * FFT_L(kernel)).
+        fft_dif(w, log2L, tw, 1, -1, lane, nlanes);
+        for (int k = lane; k < L; k += nlanes) w[k] = cmul(w[k], bp[k]);
+        EXPD_SYNCWARP();
+        fft_dit(w, log2L, tw, 1, +1, lane, nlanes);
+        for (int k = lane; k < Ns; k += nlanes) w[k] = cmul(w[k], chirp[k]);  // = L * Y_k
+        EXPD_SYNCWARP();
+    } else {
+        fft_dit(w, log2L, tw, 1, +1, lane, nlanes);  // natural Y_k
+    }
+    // Step (b): Z_k = Y_k / d_k, d_k = 1 - sum_j cj[j] lambda_k^j (Horner)
+    for (int k = lane; k < Ns; k += nlanes) {
+        const PT2 lk = lam[k];
+        PT2 acc = c2((PT)cj[order], (PT)0);
+        for (int j = order - 1; j >= 1; --j) {
+            acc = cmul(lk, acc);
+            acc.x += (PT)cj[j];
+        }
+        acc = cmul(lk, acc);
+        const PT2 d = c2((PT)1 - acc.x, -acc.y);
+        PT2 z = cdiv(w[k], d);
+        if (bluestein) z = cmulc(z, chirp[k]);
+        w[k] = z;
+    }
+    if (bluestein)
+        for (int k = Ns + lane; k < L; k += nlanes) w[k] = c2((PT)0, (PT)0);
+    EXPD_SYNCWARP();
+    // Step (c): z_n = sum_k Z_k e^{-2 pi i kn/Ns}
+    fft_dif(w, log2L, tw, 1, -1, lane, nlanes);
+    if (!bluestein) return 1.0 / Ns;  // bit-reversed output
+    for (int k = lane; k < L; k += nlanes) w[k] = cmul(w[k], bm[k]);
+    EXPD_SYNCWARP();
+    fft_dit(w, log2L, tw, 1, +1, lane, nlanes);
+    for (int n = lane; n < Ns; n += nlanes) w[n] = cmulc(w[n], chirp[n]);
+    EXPD_SYNCWARP();
+    return 1.0 / ((double)L * (double)L * (double)Ns);
+}
+
+#ifndef __CUDACC_RTC__
+#include <math.h>
+
+#include <complex>
+#include <vector>
+
+// Host construction of the time-direction tables for Ns unknown slices.
+// Power-of-two Ns: radix-2 FFT of length L = Ns.  Otherwise Bluestein with
+// L = the smallest power of two >= 2 Ns - 1, chirp c_n = e^{+i pi n^2/Ns} and
+// the two convolution kernels' FFT_L stored in bit-reversed order.
+struct TimeTablesHost {
+    int L = 0, log2L = 0, bluestein = 0;
+    std::vector<std::complex<double>> tw, lam, chirp, bplus, bminus;
+    std::vector<double> gamma;
+};
+
+inline void host_fft_inplace(std::vector<std::complex<double>>& x, int sign) {
+    const size_t n = x.size();
+    for (size_t i = 1, j = 0; i < n; ++i) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(x[i], x[j]);
+    }
+    for (size_t len = 2; len <= n; len <<= 1)
+        for (size_t i = 0; i < n; i += len)
+            for (size_t k = 0; k < len / 2; ++k) {
+                const double ang = sign * 2.0 * M_PI * (double)k / (double)len;
+                const std::complex<double> w(cos(ang), sin(ang));
+                const std::complex<double> u = x[i + k], v = x[i + k + len / 2] * w;
+                x[i + k] = u + v;
+                x[i + k + len / 2] = u - v;
+            }
+}
+
+inline TimeTablesHost time_tables_host(int Ns, double alpha) {
+    TimeTablesHost t;
+    int L = 1;
+    while (L < Ns) L <<= 1;
+    t.bluestein = (L != Ns);
+    if (t.bluestein) {
+        L = 1;
+        while (L < 2 * Ns - 1) L <<= 1;
+    }
+    t.L = L;
+    t.log2L = ilog2(L);
+    t.tw.resize(L / 2 > 0 ? L / 2 : 1);
+    for (int k = 0; k < L / 2; ++k) t.tw[k] = std::polar(1.0, -2.0 * M_PI * k / L);
+    t.lam.resize(Ns);
+    t.gamma.resize(Ns);
+    const double ar = pow(alpha, 1.0 / Ns);
+    for (int k = 0; k < Ns; ++k) {
+        t.lam[k] = std::polar(ar, 2.0 * M_PI * k / Ns);
+        t.gamma[k] = pow(alpha, (double)k / Ns);
+    }
+    if (t.bluestein) {
+        t.chirp.resize(Ns);
+        for (int n = 0; n < Ns; ++n) {
+            const long long r = ((long long)n * n) % (2LL * Ns);
+            t.chirp[n] = std::polar(1.0, M_PI * (double)r / Ns);
+        }
+        for (int pass = 0; pass < 2; ++pass) {
+            std::vector<std::complex<double>> b(L, 0.0);
+            for (int j = 0; j < Ns; ++j) {
+                const std::complex<double> cj = pass == 0 ? std::conj(t.chirp[j]) : t.chirp[j];
+                b[j] = cj;
+                if (j > 0) b[L - j] = cj;
+            }
+            host_fft_inplace(b, -1);
+            std::vector<std::complex<double>> br(L);
+            for (int k = 0; k < L; ++k) br[bitrev((unsigned)k, t.log2L)] = b[k];
+            (pass == 0 ? t.bplus : t.bminus) = br;
+        }
+    }
+    return t;
+}
+#endif

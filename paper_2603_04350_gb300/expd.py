@@ -1,0 +1,246 @@
+"""Thin ctypes binding of libexpd (include/expd.h): argument marshalling only.
+
+Every function keeps the C name without the `expd_` prefix.  Arrays may be
+torch tensors (CUDA or CPU) or numpy arrays, float64 and C-contiguous; the
+library itself detects host versus device pointers.  Nothing here computes:
+a missing or unloadable libexpd.so raises instead of falling back to Python.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libexpd.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_CUDA, ERR_UNSUPPORTED = range(7)
+BC_PERIODIC, BC_DIRICHLET = 0, 1
+NL_NONE, NL_ALLEN_CAHN = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+STARTUP_RAMP, STARTUP_GIVEN = 0, 1
+MAX_HISTORY = 128
+
+SYMBOLS = ("expd_plan_create", "expd_plan_workspace_bytes", "expd_residual", "expd_precond_apply",
+           "expd_solve_fp", "expd_solve_gmres", "expd_timing_enable", "expd_timing_read", "expd_destroy",
+           "expd_status_string", "expd_last_error", "expd_version")
+K_TIME, K_FFT_COL, K_FFT_ROW, K_DST, K_GMRES, K_POINTWISE, K_REDUCE = range(7)
+NUM_KCLASS = 7
+KCLASS_NAMES = ("time", "fft_col", "fft_row", "dst", "gmres", "pointwise", "reduce")
+
+
+class Grid(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("n", C.c_int * 2), ("length", C.c_double * 2), ("bc", C.c_int)]
+
+
+class Operator(C.Structure):
+    _fields_ = [("a", C.c_double), ("c", C.c_double), ("nonlin", C.c_int)]
+
+
+class Scheme(C.Structure):
+    _fields_ = [("order", C.c_int), ("precision", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double),
+                ("gmres_restart", C.c_int), ("startup", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("fp32_iterations", C.c_int), ("final_measure", C.c_double),
+                ("contraction", C.c_double), ("history", C.c_double * MAX_HISTORY)]
+
+    def as_dict(self):
+        k = max(0, min(self.iterations + 1, MAX_HISTORY))
+        return {"iterations": self.iterations, "fp32_iterations": self.fp32_iterations,
+                "final_measure": self.final_measure, "contraction": self.contraction,
+                "history": [self.history[i] for i in range(k)]}
+
+
+class Timing(C.Structure):
+    _fields_ = [("launches", C.c_longlong), ("count", C.c_int * NUM_KCLASS), ("ms", C.c_double * NUM_KCLASS),
+                ("bytes", C.c_double * NUM_KCLASS), ("flops", C.c_double * NUM_KCLASS)]
+
+    def as_dict(self):
+        return {"launches": self.launches,
+                "classes": {KCLASS_NAMES[i]: {"count": self.count[i], "ms": self.ms[i], "bytes": self.bytes[i],
+                                              "flops": self.flops[i]} for i in range(NUM_KCLASS)}}
+
+
+class ExpdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"expd status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libexpd.so (built in-tree by paper_2603_04350_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libexpd.so not built ({LIB_PATH}); run paper_2603_04350_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, dp = C.c_void_p, C.c_void_p
+    L.expd_plan_create.argtypes = [C.POINTER(Grid), C.POINTER(Operator), C.c_double, C.c_int, C.c_double,
+                                   C.POINTER(Scheme), vp, C.POINTER(vp)]
+    L.expd_plan_workspace_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+    L.expd_residual.argtypes = [vp, dp, dp, dp, dp, vp]
+    L.expd_precond_apply.argtypes = [vp, dp, dp, vp]
+    L.expd_solve_fp.argtypes = [vp, dp, dp, dp, C.POINTER(Info), vp]
+    L.expd_solve_gmres.argtypes = [vp, dp, dp, dp, C.POINTER(Info), vp]
+    L.expd_timing_enable.argtypes = [vp, C.c_int]
+    L.expd_timing_read.argtypes = [vp, C.POINTER(Timing), C.c_int]
+    L.expd_destroy.argtypes = [vp]
+    L.expd_status_string.argtypes = [C.c_int]
+    L.expd_status_string.restype = C.c_char_p
+    L.expd_last_error.restype = C.c_char_p
+    L.expd_version.restype = C.c_int
+    for name in SYMBOLS:
+        if name not in ("expd_status_string", "expd_last_error", "expd_version"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int, allow=(OK,)) -> int:
+    if status not in allow:
+        raise ExpdError(status, lib().expd_last_error().decode() or lib().expd_status_string(status).decode())
+    return status
+
+
+def _ptr(x) -> Optional[int]:
+    """Data pointer of a float64 C-contiguous torch tensor or numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be float64 and C-contiguous")
+        return x.ctypes.data
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("tensors must be float64 and contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+@dataclass
+class PlanSpec:
+    bc: int
+    n: tuple
+    length: tuple
+    a: float
+    c: float
+    nonlin: int
+    dt: float
+    Nt: int
+    alpha: float
+    order: int
+    precision: int = PREC_FP64
+    max_iter: int = 100
+    tol: float = 1e-8
+    gmres_restart: int = 20
+    startup: int = STARTUP_RAMP
+
+
+def plan_create(spec: PlanSpec, stream=None) -> "Plan":
+    g = Grid()
+    g.ndim = len(spec.n)
+    for d in range(g.ndim):
+        g.n[d] = int(spec.n[d])
+        g.length[d] = float(spec.length[d])
+    g.bc = spec.bc
+    o = Operator(spec.a, spec.c, spec.nonlin)
+    s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup)
+    h = C.c_void_p()
+    _check(lib().expd_plan_create(C.byref(g), C.byref(o), spec.dt, spec.Nt, spec.alpha, C.byref(s),
+                                  _stream(stream), C.byref(h)))
+    return Plan(h, spec)
+
+
+class Plan:
+    """Owner of an expd_plan handle; the methods map one-to-one onto the C ABI."""
+
+    def __init__(self, handle: C.c_void_p, spec: PlanSpec):
+        self._h = handle
+        self.spec = spec
+        self.Ns = spec.Nt - spec.order + 1
+
+    def workspace_bytes(self) -> int:
+        b = C.c_size_t()
+        _check(lib().expd_plan_workspace_bytes(self._h, C.byref(b)))
+        return b.value
+
+    def residual(self, u0, f, U, R, stream=None) -> None:
+        _check(lib().expd_residual(self._h, _ptr(u0), _ptr(f), _ptr(U), _ptr(R), _stream(stream)))
+
+    def precond_apply(self, R, S, stream=None) -> None:
+        _check(lib().expd_precond_apply(self._h, _ptr(R), _ptr(S), _stream(stream)))
+
+    def solve_fp(self, u0, f, U, stream=None, allow_not_converged=False) -> dict:
+        info = Info()
+        allow = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
+        st = _check(lib().expd_solve_fp(self._h, _ptr(u0), _ptr(f), _ptr(U), C.byref(info), _stream(stream)), allow)
+        d = info.as_dict()
+        d["status"] = st
+        return d
+
+    def solve_gmres(self, u0, f, U, stream=None, allow_not_converged=False) -> dict:
+        info = Info()
+        allow = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
+        st = _check(lib().expd_solve_gmres(self._h, _ptr(u0), _ptr(f), _ptr(U), C.byref(info), _stream(stream)),
+                    allow)
+        d = info.as_dict()
+        d["status"] = st
+        return d
+
+    def timing_enable(self, enable: bool = True) -> None:
+        _check(lib().expd_timing_enable(self._h, 1 if enable else 0))
+
+    def timing_read(self, reset: bool = True) -> dict:
+        t = Timing()
+        _check(lib().expd_timing_read(self._h, C.byref(t), 1 if reset else 0))
+        return t.as_dict()
+
+    def destroy(self) -> None:
+        if self._h:
+            lib().expd_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def spec_from_problem(p, precision: int = PREC_FP64, max_iter: int = 100, tol: Optional[float] = None,
+                      gmres_restart: int = 20, startup: int = STARTUP_RAMP) -> PlanSpec:
+    """PlanSpec from a paper_2603_04350_gb300.inputs.Problem."""
+    return PlanSpec(bc=BC_PERIODIC if p.bc == "periodic" else BC_DIRICHLET, n=tuple(p.n), length=tuple(p.length),
+                    a=p.a, c=p.c, nonlin=NL_ALLEN_CAHN if p.nonlin == "allen_cahn" else NL_NONE, dt=p.dt,
+                    Nt=p.Nt, alpha=p.alpha, order=p.order, precision=precision, max_iter=max_iter,
+                    tol=p.tol if tol is None else tol, gmres_restart=gmres_restart, startup=startup)

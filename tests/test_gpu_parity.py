@@ -1,0 +1,264 @@
+"""CUDA path vs the CPU oracle, through the C ABI (marked gpu).
+
+Tolerances: the float64 path must match the oracle to 1e-11 relative (the
+stated 1e-10 bar with margin) on every element; float32-preconditioner (mixed)
+operations that are not refined are held to the float32 bound eps32/alpha
+derived in the design notes; solves of either precision must meet the
+workload's tolerance in the L^inf(0,T;L^2) relative error of Sec. 7.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2603_04350_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def expd():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2603_04350_gb300 import expd as E
+    return E
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def relmax(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def P(name, bc, n, order, nonlin="none", Nt=None, alpha=1e-2, a=None, c=0.1, dt=0.01, forcing=False):
+    length = tuple(2 * math.pi if bc == "periodic" else 1.0 for _ in n)
+    if a is None:
+        a = 0.05 if bc == "periodic" else 0.01
+    return I.Problem(name=name, bc=bc, n=tuple(n), length=length, a=a, c=c, nonlin=nonlin, dt=dt,
+                     Nt=Nt if Nt is not None else order + 9, alpha=alpha, order=order, forcing=forcing)
+
+
+# Sizes span several time-kernel tiles (8 modes each) and ragged tails:
+# periodic 1D n=64 -> 33 modes, 2D 16x32 -> 16*17 = 272 modes, Dirichlet 13x11 -> 143.
+CASES = [
+    P("p1d_s1", "periodic", (64,), 1),
+    P("p1d_s2_np2", "periodic", (64,), 2, Nt=12),          # Ns = 11 (Bluestein)
+    P("p2d_s1", "periodic", (16, 32), 1, Nt=16),           # Ns = 16 (radix-2)
+    P("p2d_s6", "periodic", (16, 32), 6, Nt=20),           # Ns = 15 (Bluestein)
+    P("p2d_s3", "periodic", (32, 16), 3, Nt=10),           # Ns = 8
+    P("d1d_s1", "dirichlet", (37,), 1, Nt=9),
+    P("d2d_s2", "dirichlet", (13, 11), 2, Nt=12),
+    P("d2d_s6", "dirichlet", (13, 11), 6, Nt=14),
+    P("p2d_ac_s1", "periodic", (16, 32), 1, nonlin="allen_cahn", a=0.01, c=0.0, dt=1e-3, Nt=16, alpha=1e-3),
+    P("p2d_ac_s2", "periodic", (16, 16), 2, nonlin="allen_cahn", a=0.01, c=0.0, dt=1e-3, Nt=21, alpha=1e-3),
+    P("d2d_ac_s2", "dirichlet", (9, 12), 2, nonlin="allen_cahn", a=0.01, c=0.0, dt=1e-3, Nt=12, alpha=1e-3),
+]
+IDS = [p.name for p in CASES]
+
+
+def rand_field(p, lead, seed, scale=1.0):
+    return scale * np.random.default_rng(seed).standard_normal(tuple(lead) + p.n)
+
+
+@pytest.mark.parametrize("p", CASES, ids=IDS)
+def test_precond_apply_fp64(expd, p):
+    r = rand_field(p, (p.Ns,), 1)
+    ref = O.precond_apply(O.spec_of(p), r)
+    S = torch.empty_like(dev(r))
+    with expd.plan_create(expd.spec_from_problem(p)) as plan:
+        plan.precond_apply(dev(r), S)
+    assert relmax(host(S), ref) < 1e-11
+
+
+@pytest.mark.parametrize("p", CASES[:5], ids=IDS[:5])
+def test_precond_apply_mixed_is_float32_accurate(expd, p):
+    # float32 steps (a)-(c): error bound ~ eps32 * log2(L) / alpha relative
+    r = rand_field(p, (p.Ns,), 2)
+    ref = O.precond_apply(O.spec_of(p), r)
+    S = torch.empty_like(dev(r))
+    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED)) as plan:
+        plan.precond_apply(dev(r), S)
+    bound = 6e-8 * 16 / p.alpha
+    assert relmax(host(S), ref) < bound
+
+
+@pytest.mark.parametrize("p", CASES, ids=IDS)
+def test_residual_fp64(expd, p):
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(3)
+    amp = 0.5 if p.nonlin != "none" else 1.0
+    u0 = amp * rng.uniform(-1, 1, p.n)
+    U = amp * rng.uniform(-1, 1, (p.Nt,) + p.n)
+    f = rng.standard_normal((p.Nt,) + p.n)
+    U_start = np.concatenate([u0[None], U[: p.order - 1]])
+    ref = O.residual(sp, U[p.order - 1:], O.rhs_known(sp, U_start, f))
+    R = torch.empty((p.Ns,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p)) as plan:
+        plan.residual(dev(u0), dev(f), dev(U), R)
+    assert relmax(host(R), ref) < 1e-11
+
+
+@pytest.mark.parametrize("p", CASES, ids=IDS)
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_fp_matches_sequential(expd, p, prec):
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(4)
+    u0 = rng.uniform(-0.8, 0.8, p.n)
+    f = rng.standard_normal((p.Nt,) + p.n) if p.nonlin == "none" else None
+    ref = O.sequential_solve(sp, u0, f)[1:]
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    precision = expd.PREC_FP64 if prec == "fp64" else expd.PREC_MIXED
+    with expd.plan_create(expd.spec_from_problem(p, precision=precision, tol=1e-12, max_iter=200)) as plan:
+        info = plan.solve_fp(dev(u0), None if f is None else dev(f), U)
+    assert O.rel_error(host(U), ref) < 1e-10, info
+
+
+@pytest.mark.parametrize("p", [CASES[i] for i in (0, 3, 6, 8, 9)], ids=[IDS[i] for i in (0, 3, 6, 8, 9)])
+def test_richardson_iterates_match_oracle(expd, p):
+    # per-iteration parity: the k-th iterate of the GPU fixed point equals the oracle's
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(5)
+    u0 = rng.uniform(-0.8, 0.8, p.n)
+    for k in (1, 2, 3):
+        ref = O.richardson(sp, u0, None, max_iter=k).U[1:]
+        U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+        with expd.plan_create(expd.spec_from_problem(p, tol=1e-300, max_iter=k)) as plan:
+            info = plan.solve_fp(dev(u0), None, U, allow_not_converged=True)
+        assert info["iterations"] == k
+        assert O.rel_error(host(U), ref) < 1e-12
+
+
+@pytest.mark.parametrize("p", [c for c in CASES if c.nonlin == "none"], ids=[c.name for c in CASES if c.nonlin == "none"])
+def test_gmres_matches_oracle(expd, p):
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(6)
+    u0 = rng.standard_normal(p.n)
+    f = rng.standard_normal((p.Nt,) + p.n)
+    pr = p.with_(alpha=0.3)       # slower convergence -> a longer history to compare
+    spr = O.spec_of(pr)
+    ref = O.gmres(spr, u0, f, tol=1e-12, restart=20)
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(pr, tol=1e-12, max_iter=200)) as plan:
+        info = plan.solve_gmres(dev(u0), dev(f), U)
+    seq = O.sequential_solve(spr, u0, f)[1:]
+    assert O.rel_error(host(U), seq) < 1e-10
+    h_gpu = np.array(info["history"][: len(ref.history)])
+    h_ref = np.array(ref.history[: len(h_gpu)])
+    k = min(len(h_gpu), len(h_ref))
+    big = h_ref[:k] > 1e-9
+    assert np.allclose(h_gpu[:k][big], h_ref[:k][big], rtol=1e-6)
+
+
+def test_startup_given_and_host_pointers(expd):
+    p = P("p2d_s3", "periodic", (16, 16), 3, Nt=12)
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(7)
+    u0 = rng.standard_normal(p.n)
+    Ustart = np.concatenate([u0[None], rng.standard_normal((2,) + p.n)])
+    ref = O.sequential_solve(sp, u0, None, U_start=Ustart)[1:]
+    Uh = np.zeros((p.Nt,) + p.n)
+    Uh[:2] = Ustart[1:]
+    with expd.plan_create(expd.spec_from_problem(p, tol=1e-13, startup=expd.STARTUP_GIVEN)) as plan:
+        plan.solve_fp(u0, None, Uh)                      # host numpy buffers
+        Ud = dev(Uh)
+        Ud[2:] = 0
+        plan.solve_fp(dev(u0), None, Ud)                 # device buffers
+    assert O.rel_error(Uh, ref) < 1e-11
+    assert np.array_equal(host(Ud), Uh)
+
+
+def test_deterministic_repeat(expd):
+    p = CASES[9]
+    u0 = np.random.default_rng(8).uniform(-0.9, 0.9, p.n)
+    outs = []
+    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED)) as plan:
+        for _ in range(2):
+            U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+            plan.solve_fp(dev(u0), None, U)
+            outs.append(host(U))
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_not_converged_and_diverged_status(expd):
+    p = CASES[8]
+    u0 = np.random.default_rng(9).uniform(-0.9, 0.9, p.n)
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, tol=1e-15, max_iter=1)) as plan:
+        with pytest.raises(expd.ExpdError) as ei:
+            plan.solve_fp(dev(u0), None, U)
+        assert ei.value.status == expd.ERR_NOT_CONVERGED
+        bad = u0.copy()
+        bad[0, 0] = np.nan
+        with pytest.raises(expd.ExpdError) as ei:
+            plan.solve_fp(dev(bad), None, U)
+        assert ei.value.status == expd.ERR_DIVERGED
+
+
+def test_minimum_window_and_alpha_near_one(expd):
+    # Ns = 2 (Nt = s + 1) and alpha = 0.9
+    for order in (1, 2, 6):
+        p = P(f"min_s{order}", "periodic", (16,), order, Nt=order + 1, alpha=0.9)
+        sp = O.spec_of(p)
+        u0 = np.random.default_rng(order).standard_normal(p.n)
+        ref = O.sequential_solve(sp, u0)[1:]
+        U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+        with expd.plan_create(expd.spec_from_problem(p, tol=1e-13, max_iter=400)) as plan:
+            plan.solve_fp(dev(u0), None, U)
+        assert O.rel_error(host(U), ref) < 1e-10
+
+
+# ---------------------------------------------------------------- full size --
+def solve_full(expd, p, precision, solver=None):
+    u0, f = I.make_inputs(p)
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, precision=precision, max_iter=200)) as plan:
+        fn = plan.solve_gmres if (solver or p.solver) == "gmres" else plan.solve_fp
+        info = fn(dev(u0), None if f is None else dev(f), U)
+    return u0, f, host(U), info
+
+
+def test_heat1d_full_exact_solution(expd):
+    p = I.HEAT1D
+    u0, f, U, info = solve_full(expd, p, expd.PREC_FP64)
+    x = I.grid_coords(p)[0]
+    rng = np.random.default_rng(p.seed)
+    ak, bk = rng.standard_normal(16), rng.standard_normal(16)
+    exact = np.array([sum(math.exp(-k * k * (n + 1) * p.dt) * (ak[k - 1] * np.cos(k * x) + bk[k - 1] * np.sin(k * x))
+                          / k**2 for k in range(1, 17)) for n in range(p.Nt)])
+    assert O.rel_error(U, exact) < 1e-10
+    assert O.rel_error(U, O.sequential_solve(O.spec_of(p), u0)[1:]) < 1e-10
+    assert info["iterations"] <= 6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_allen_cahn_256_full(expd, prec):
+    p = I.ALLEN_CAHN_256
+    u0, f, U, info = solve_full(expd, p, expd.PREC_FP64 if prec == "fp64" else expd.PREC_MIXED)
+    ref = O.sequential_solve(O.spec_of(p), u0)[1:]
+    assert O.rel_error(U, ref) < p.tol, info
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_allen_cahn_512_order6_full(expd, prec):
+    p = I.ALLEN_CAHN_512_S6
+    u0, f, U, info = solve_full(expd, p, expd.PREC_FP64 if prec == "fp64" else expd.PREC_MIXED)
+    ref = O.sequential_solve(O.spec_of(p), u0)[1:]
+    assert O.rel_error(U, ref) < p.tol, info
+
+
+def test_heat_dirichlet_1024_full_gmres(expd):
+    p = I.HEAT_DIRICHLET_1024
+    u0, f, U, info = solve_full(expd, p, expd.PREC_FP64)
+    ref = O.sequential_solve(O.spec_of(p), u0, f)[1:]
+    assert O.rel_error(U, ref) < p.tol, info
