@@ -56,7 +56,7 @@ typedef enum {
     EXPD_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range        */
     EXPD_ERR_OOM = 2,           /* device allocation failed                             */
     EXPD_ERR_NOT_CONVERGED = 3, /* max_iter reached; the last iterate is returned       */
-    EXPD_ERR_DIVERGED = 4,      /* update norm non-finite or growing 1e3-fold           */
+    EXPD_ERR_DIVERGED = 4,      /* update non-finite or 1e3 times the first update      */
     EXPD_ERR_CUDA = 5,          /* a CUDA runtime call failed                           */
     EXPD_ERR_UNSUPPORTED = 6    /* valid request that this build does not implement     */
 } expd_status;
@@ -89,9 +89,11 @@ typedef struct {
  *             the spatial FFTs that evaluate N in float32 until the update
  *             stalls, then float64 sweeps; the residual is always float64.
  *  max_iter   iteration cap of expd_solve_fp / expd_solve_gmres
- *  tol        stop when the estimated L^inf(0,T;L^2) relative error of the
- *             iterate is <= tol (fixed point) or the relative preconditioned
- *             residual is <= tol (GMRES)
+ *  tol        target L^inf(0,T;L^2) relative error (Sec. 7's norm).  The
+ *             fixed point stops when rho/(1-rho) * max_n||s_n|| / max_n||v_n||
+ *             <= tol (s the update, rho the observed contraction); GMRES stops
+ *             when sqrt(Ns) times the relative preconditioned residual is
+ *             <= tol
  *  gmres_restart  GMRES restart length m (1..64)
  *  startup    EXPD_STARTUP_RAMP or EXPD_STARTUP_GIVEN (u_1..u_{s-1} read
  *             from the first s-1 slices of the U argument of the solvers)   */
@@ -160,8 +162,9 @@ expd_status expd_precond_apply(expd_plan plan, const double* R, double* S, void*
  *   (input for its first s-1 slices when startup = EXPD_STARTUP_GIVEN)
  *   info may be NULL.
  * Returns EXPD_ERR_NOT_CONVERGED (U holds the last iterate) when max_iter
- * sweeps do not reach tol, EXPD_ERR_DIVERGED on a non-finite or exploding
- * update. */
+ * sweeps do not reach tol, EXPD_ERR_DIVERGED when an update is non-finite or
+ * exceeds 1e3 times the first one (the iteration matrix's spectral radius
+ * exceeds 1, e.g. alpha/(1 - alpha) > 1 for slowly decaying modes). */
 expd_status expd_solve_fp(expd_plan plan, const double* u0, const double* f, double* U,
                           expd_info* info, void* stream);
 

@@ -219,6 +219,9 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS) time_kernel(TimeArgs A) {
     for (int n = tid; n < Ns; n += nth) A.partial[(size_t)blockIdx.x * Ns + n] = sAcc[n];
 }
 
+// max that propagates NaN (fmax would drop it and hide a diverged iterate)
+__device__ __forceinline__ double nanmax(double a, double b) { return (a != a || b != b) ? NAN : fmax(a, b); }
+
 // Per-slice totals over the CTAs (fixed order), then max/sum over slices.
 __global__ void reduce_kernel(const double2* __restrict__ partial, int grid, int Ns, double* __restrict__ out) {
     __shared__ double smax[2][32], ssum[2][32];
@@ -230,14 +233,14 @@ __global__ void reduce_kernel(const double2* __restrict__ partial, int grid, int
             a += v.x;
             b += v.y;
         }
-        mx0 = fmax(mx0, a);
-        mx1 = fmax(mx1, b);
+        mx0 = nanmax(mx0, a);
+        mx1 = nanmax(mx1, b);
         sm0 += a;
         sm1 += b;
     }
     for (int o = 16; o > 0; o >>= 1) {
-        mx0 = fmax(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
-        mx1 = fmax(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
+        mx0 = nanmax(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
+        mx1 = nanmax(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
         sm0 += __shfl_xor_sync(0xffffffffu, sm0, o);
         sm1 += __shfl_xor_sync(0xffffffffu, sm1, o);
     }
@@ -252,8 +255,8 @@ __global__ void reduce_kernel(const double2* __restrict__ partial, int grid, int
     if (threadIdx.x == 0) {
         double a = 0, b = 0, c = 0, d = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            a = fmax(a, smax[0][w]);
-            b = fmax(b, smax[1][w]);
+            a = nanmax(a, smax[0][w]);
+            b = nanmax(b, smax[1][w]);
             c += ssum[0][w];
             d += ssum[1][w];
         }
