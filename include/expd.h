@@ -175,6 +175,32 @@ expd_status expd_solve_fp(expd_plan plan, const double* u0, const double* f, dou
 expd_status expd_solve_gmres(expd_plan plan, const double* u0, const double* f, double* U,
                              expd_info* info, void* stream);
 
+/* ---- allocation-free preconditioner solve ---------------------------------
+ * The paper has no counterpart to this entry point; it is a deployment variant
+ * of expd_precond_apply for callers that must not allocate device memory --
+ * callers whose device memory is owned by an allocator of their own (a serving
+ * engine that reserves the free HBM at start-up, a framework memory pool), or
+ * that run where an allocation could fail or stall in the middle of their
+ * work.  It takes the plan parameters directly instead of a plan (creating a
+ * plan calls cudaMalloc) and computes S = (R_s^alpha)^{-1} R exactly as
+ * expd_precond_apply does, with every table and intermediate kept in one
+ * fixed device array of EXPD_NOALLOC_SCRATCH_BYTES bytes that each GPU loading
+ * the library holds until the process exits.  It calls no cudaMalloc, no
+ * cudaFree and no allocating library routine.
+ *   R, S   device pointers, [Ns slices] as for expd_precond_apply (may alias)
+ * Limits: at most 512 unknown slices, and the tables, the eigen-space copy of
+ * R, the spatial scratch and the norm partials must fit the array (about
+ * 2 Ns M complex values plus the DST matrices on Dirichlet grids); larger
+ * problems get EXPD_ERR_INVALID_ARG with the byte count in expd_last_error().
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and leave their contents in it: calls that
+ * overlap on the GPU (different streams or host threads) race. */
+#define EXPD_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+expd_status expd_precond_apply_noalloc(const expd_grid* grid, const expd_operator* op, double dt, int Nt,
+                                       double alpha, const expd_scheme* scheme, const double* R, double* S,
+                                       void* stream);
+
 /* ---- per-kernel timing -------------------------------------------------------
  * With timing enabled, every libexpd kernel launch of the plan is bracketed by
  * two CUDA events recorded on the stream it is launched on; expd_timing_read

@@ -292,30 +292,8 @@ KProf::~KProf() {
     p->recs.push_back({cls, e0, bytes, flops});
 }
 
-extern "C" {
-
-const char* expd_status_string(expd_status s) {
-    switch (s) {
-        case EXPD_OK: return "ok";
-        case EXPD_ERR_INVALID_ARG: return "invalid argument";
-        case EXPD_ERR_OOM: return "out of device memory";
-        case EXPD_ERR_NOT_CONVERGED: return "not converged";
-        case EXPD_ERR_DIVERGED: return "diverged";
-        case EXPD_ERR_CUDA: return "CUDA error";
-        case EXPD_ERR_UNSUPPORTED: return "unsupported";
-    }
-    return "unknown status";
-}
-
-const char* expd_last_error(void) { return g_err.c_str(); }
-
-int expd_version(void) { return 10000; }
-
-expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, double dt, int Nt, double alpha,
-                             const expd_scheme* scheme, void* stream, expd_plan* out) {
-    if (!out) return expd_fail(EXPD_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    g_err.clear();
+expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_operator* op, double dt, int Nt,
+                             double alpha, const expd_scheme* scheme) {
     if (!grid || !op || !scheme) return expd_fail(EXPD_ERR_INVALID_ARG, "grid, operator and scheme are required");
     if (grid->ndim != 1 && grid->ndim != 2) return expd_fail(EXPD_ERR_INVALID_ARG, "ndim must be 1 or 2");
     if (grid->bc != EXPD_BC_PERIODIC && grid->bc != EXPD_BC_DIRICHLET)
@@ -348,9 +326,6 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
         return expd_fail(EXPD_ERR_INVALID_ARG, "gmres_restart must be in [1, 64]");
     if (scheme->startup != EXPD_STARTUP_RAMP && scheme->startup != EXPD_STARTUP_GIVEN)
         return expd_fail(EXPD_ERR_INVALID_ARG, "unknown startup mode");
-
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    expd_plan p = new expd_plan_s();
     p->ndim = grid->ndim;
     if (p->ndim == 1) {
         p->NX = grid->n[0];
@@ -380,25 +355,53 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
     for (int q = 1; q <= 6; ++q) bdf(q, p->acoef[q], &p->beta[q]);
     if (p->nonlin != EXPD_NL_NONE) {
         for (int q = 1; q <= p->order; ++q)
-            if (!(p->beta[q] * dt < 1.0)) {
-                delete p;
-                return expd_fail(EXPD_ERR_INVALID_ARG, "nonlinear problems need beta_s*dt < 1");
-            }
+            if (!(p->beta[q] * dt < 1.0)) return expd_fail(EXPD_ERR_INVALID_ARG, "nonlinear problems need beta_s*dt < 1");
     }
     p->M = (long long)p->NX * p->NY;
     p->realcol = p->bc == EXPD_BC_DIRICHLET;
     p->KX = p->realcol ? p->NX : p->NX / 2 + 1;
     p->Mcol = (long long)p->NY * p->KX;
     p->esz = p->realcol ? sizeof(double) : sizeof(double2);
-
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev);
-    if (ce != cudaSuccess) {
-        delete p;
-        return expd_cuda_fail(ce, "cudaGetDevice/cudaDeviceGetAttribute", __FILE__, __LINE__);
-    }
+    if (ce != cudaSuccess) return expd_cuda_fail(ce, "cudaGetDevice/cudaDeviceGetAttribute", __FILE__, __LINE__);
+    return EXPD_OK;
+}
 
+bool expd_is_device_ptr(const void* ptr) { return is_device_ptr(ptr); }
+
+extern "C" {
+
+const char* expd_status_string(expd_status s) {
+    switch (s) {
+        case EXPD_OK: return "ok";
+        case EXPD_ERR_INVALID_ARG: return "invalid argument";
+        case EXPD_ERR_OOM: return "out of device memory";
+        case EXPD_ERR_NOT_CONVERGED: return "not converged";
+        case EXPD_ERR_DIVERGED: return "diverged";
+        case EXPD_ERR_CUDA: return "CUDA error";
+        case EXPD_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* expd_last_error(void) { return g_err.c_str(); }
+
+int expd_version(void) { return 10000; }
+
+expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, double dt, int Nt, double alpha,
+                             const expd_scheme* scheme, void* stream, expd_plan* out) {
+    if (!out) return expd_fail(EXPD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    g_err.clear();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    expd_plan p = new expd_plan_s();
+    expd_status st0 = plan_init_fields(p, grid, op, dt, Nt, alpha, scheme);
+    if (st0 != EXPD_OK) {
+        delete p;
+        return st0;
+    }
     expd_status st = EXPD_OK;
     // ---- eigenvalues of L_h: E_m = exp(dt mu_m) ----
     {

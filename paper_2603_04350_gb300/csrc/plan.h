@@ -17,6 +17,11 @@
 
 expd_status expd_cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 expd_status expd_fail(expd_status s, const std::string& msg);
+struct expd_plan_s;
+// Validate the problem and fill the plan's scalar fields (no allocation).
+expd_status plan_init_fields(expd_plan_s* p, const expd_grid* grid, const expd_operator* op, double dt, int Nt,
+                             double alpha, const expd_scheme* scheme);
+bool expd_is_device_ptr(const void* ptr);
 
 struct TimeTables {
     int L = 0, log2L = 0, bluestein = 0;
@@ -140,6 +145,8 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s);
 // [2] = sum_n ||res_n||^2, [3] = sum_n ||X_n||^2 (weighted eigen norms).
 expd_status time_reduce(expd_plan p, cudaStream_t s);
 expd_status time_tables_build(expd_plan p, cudaStream_t s);
+// CTAs of the time kernel: SM count x resident CTAs, at most the tile count (no allocation)
+expd_status time_grid_for(expd_plan p, int* grid);
 void time_tables_free(expd_plan p);
 
 // ---- GMRES vector kernels (gmres.cu) ---------------------------------------------

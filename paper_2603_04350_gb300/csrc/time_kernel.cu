@@ -351,10 +351,28 @@ expd_status time_tables_build(expd_plan p, cudaStream_t s) {
     if (st != EXPD_OK) return st;
     st = build_tables<float2, float>(p, p->t32, s);
     if (st != EXPD_OK) return st;
-    // grid: a multiple of the SM count, as many CTAs as fit, never more than tiles
+    int grid = 0;
+    st = time_grid_for(p, &grid);
+    if (st != EXPD_OK) return st;
+    p->time_grid = grid;
+    cudaError_t e = cudaMalloc(&p->partial, (size_t)grid * p->Ns * sizeof(double2));
+    if (e != cudaSuccess) return expd_cuda_fail(e, "cudaMalloc(partial)", __FILE__, __LINE__);
+    p->bytes += (size_t)grid * p->Ns * sizeof(double2);
+    return EXPD_OK;
+}
+
+expd_status time_grid_for(expd_plan p, int* grid_out) {
+    // a multiple of the SM count, as many CTAs as fit, never more than tiles
     const long long ntiles = (p->Mcol + EXPD_TIME_COLS - 1) / EXPD_TIME_COLS;
+    int L = 1;
+    while (L < p->Ns) L <<= 1;
+    const int blue = (L != p->Ns);
+    if (blue) {
+        L = 1;
+        while (L < 2 * p->Ns - 1) L <<= 1;
+    }
     int per_sm = 1;
-    const size_t smem = time_smem_bytes(p->Ns, p->t64.L, p->t64.bluestein, sizeof(double2));
+    const size_t smem = time_smem_bytes(p->Ns, L, blue, sizeof(double2));
     auto kern = p->realcol ? time_kernel<double, true> : time_kernel<double, false>;
     if (smem > 227 * 1024) return expd_fail(EXPD_ERR_UNSUPPORTED, "time window too long for shared memory");
     EXPD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -362,10 +380,7 @@ expd_status time_tables_build(expd_plan p, cudaStream_t s) {
     if (per_sm < 1) per_sm = 1;
     long long grid = (long long)p->sm_count * per_sm;
     if (grid > ntiles) grid = ntiles;
-    p->time_grid = (int)grid;
-    cudaError_t e = cudaMalloc(&p->partial, (size_t)grid * p->Ns * sizeof(double2));
-    if (e != cudaSuccess) return expd_cuda_fail(e, "cudaMalloc(partial)", __FILE__, __LINE__);
-    p->bytes += (size_t)grid * p->Ns * sizeof(double2);
+    *grid_out = (int)grid;
     return EXPD_OK;
 }
 

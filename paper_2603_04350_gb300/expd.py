@@ -26,6 +26,7 @@ MAX_HISTORY = 128
 
 SYMBOLS = ("expd_plan_create", "expd_plan_workspace_bytes", "expd_residual", "expd_precond_apply",
            "expd_solve_fp", "expd_solve_gmres", "expd_timing_enable", "expd_timing_read", "expd_destroy",
+           "expd_precond_apply_noalloc",
            "expd_status_string", "expd_last_error", "expd_version")
 K_TIME, K_FFT_COL, K_FFT_ROW, K_DST, K_GMRES, K_POINTWISE, K_REDUCE = range(7)
 NUM_KCLASS = 7
@@ -94,6 +95,8 @@ def lib() -> C.CDLL:
     L.expd_timing_enable.argtypes = [vp, C.c_int]
     L.expd_timing_read.argtypes = [vp, C.POINTER(Timing), C.c_int]
     L.expd_destroy.argtypes = [vp]
+    L.expd_precond_apply_noalloc.argtypes = [C.POINTER(Grid), C.POINTER(Operator), C.c_double, C.c_int,
+                                             C.c_double, C.POINTER(Scheme), dp, dp, vp]
     L.expd_status_string.argtypes = [C.c_int]
     L.expd_status_string.restype = C.c_char_p
     L.expd_last_error.restype = C.c_char_p
@@ -158,6 +161,26 @@ class PlanSpec:
     tol: float = 1e-8
     gmres_restart: int = 20
     startup: int = STARTUP_RAMP
+
+
+def _structs(spec: PlanSpec):
+    g = Grid()
+    g.ndim = len(spec.n)
+    for d in range(g.ndim):
+        g.n[d] = int(spec.n[d])
+        g.length[d] = float(spec.length[d])
+    g.bc = spec.bc
+    o = Operator(spec.a, spec.c, spec.nonlin)
+    s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup)
+    return g, o, s
+
+
+def precond_apply_noalloc(spec: PlanSpec, R, S, stream=None) -> None:
+    """expd_precond_apply_noalloc: the preconditioner solve without a plan and
+    without any device allocation (R, S device tensors)."""
+    g, o, s = _structs(spec)
+    _check(lib().expd_precond_apply_noalloc(C.byref(g), C.byref(o), spec.dt, spec.Nt, spec.alpha, C.byref(s),
+                                            _ptr(R), _ptr(S), _stream(stream)))
 
 
 def plan_create(spec: PlanSpec, stream=None) -> "Plan":
