@@ -84,10 +84,14 @@ typedef struct {
 /* Scheme and solver controls.
  *  order      s in 1..6: exponential BDF-s (Eq. (2.2), Eq. (4.1), Sec. 5)
  *  precision  EXPD_PREC_FP64: every transform, the preconditioner and the
- *             residual in float64.  EXPD_PREC_MIXED: the preconditioner's time
- *             DFT and shifted solves in float32 and, for nonlinear problems,
- *             the spatial FFTs that evaluate N in float32 until the update
- *             stalls, then float64 sweeps; the residual is always float64.
+ *             residual in float64.  EXPD_PREC_MIXED: the fixed point first
+ *             sweeps entirely in float32 (iterate, residual, N and its FFTs,
+ *             preconditioner) until its error estimate reaches tol or the
+ *             float32 floor stalls it, then sweeps with a float64 iterate,
+ *             float64 residual and N, and the float32 preconditioner, which
+ *             converge to the float64 fixed point.  Start-up, right-hand side
+ *             and output transforms are float64.  (Dirichlet grids with a
+ *             nonlinearity skip the float32 sweeps.)
  *  max_iter   iteration cap of expd_solve_fp / expd_solve_gmres
  *  tol        target L^inf(0,T;L^2) relative error (Sec. 7's norm).  The
  *             fixed point stops when rho/(1-rho) * max_n||s_n|| / max_n||v_n||
@@ -134,6 +138,15 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
 
 /* Device bytes the plan holds (for admission by memory footprint). */
 expd_status expd_plan_workspace_bytes(expd_plan plan, size_t* bytes);
+
+/* Device bytes expd_plan_create would allocate for these arguments, computed
+ * without allocating anything (admission control before creating a plan).
+ * flags adds the buffers a plan allocates on first use: EXPD_FOOTPRINT_SOURCE
+ * (a source f is passed), EXPD_FOOTPRINT_HOST (host pointers are passed),
+ * EXPD_FOOTPRINT_GMRES (expd_solve_gmres is called). */
+enum { EXPD_FOOTPRINT_SOURCE = 1, EXPD_FOOTPRINT_HOST = 2, EXPD_FOOTPRINT_GMRES = 4 };
+expd_status expd_plan_footprint_bytes(const expd_grid* grid, const expd_operator* op, double dt, int Nt,
+                                      double alpha, const expd_scheme* scheme, int flags, size_t* bytes);
 
 /* Residual of the all-at-once system (Eq. (3.2) right-hand side; for the
  * lagged nonlinear form Eqs. (7.3)-(7.4)):
@@ -211,14 +224,21 @@ expd_status expd_precond_apply_noalloc(const expd_grid* grid, const expd_operato
  * `launches` counts all kernels launched by the plan since the last reset,
  * timed or not.  Timing adds two event records per launch. */
 enum {
-    EXPD_K_TIME = 0,      /* residual + alpha-scaled DFT + shifted solves + inverse DFT + update */
-    EXPD_K_FFT_COL = 1,   /* spatial FFT along the strided axis                              */
-    EXPD_K_FFT_ROW = 2,   /* spatial real FFT along the contiguous axis (incl. fused N(u))   */
+    EXPD_K_TIME = 0,      /* time kernel, float64 iterate: residual + alpha-scaled DFT +      */
+                          /* shifted solves + inverse DFT + update                            */
+    EXPD_K_FFT_COL = 1,   /* float64 spatial FFT along the strided axis                       */
+    EXPD_K_FFT_ROW = 2,   /* float64 real FFT along the contiguous axis (incl. fused N(u))    */
     EXPD_K_DST = 3,       /* Dirichlet DST-I as a dense matrix product                        */
     EXPD_K_GMRES = 4,     /* GMRES dot products and vector updates                            */
     EXPD_K_POINTWISE = 5, /* pointwise solves, eigen-space combinations, f_s assembly         */
     EXPD_K_REDUCE = 6,    /* per-slice norm reduction                                         */
-    EXPD_NUM_KCLASS = 7
+    EXPD_K_TIME32 = 7,    /* time kernel, float32 iterate (the mixed path's float32 sweeps)   */
+    EXPD_K_FFT_COL32 = 8, /* float32 spatial FFT along the strided axis                       */
+    EXPD_K_FFT_ROW32 = 9, /* float32 real FFT along the contiguous axis (incl. fused N(u))    */
+    EXPD_K_TIMEDD = 10,   /* time kernel, double-float iterate (the mixed path's last sweeps) */
+    EXPD_K_FFT_COLDD = 11, /* double-float spatial FFT along the strided axis                */
+    EXPD_K_FFT_ROWDD = 12, /* double-float real FFT along the contiguous axis                */
+    EXPD_NUM_KCLASS = 13
 };
 
 typedef struct {

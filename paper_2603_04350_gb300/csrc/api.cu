@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "plan.h"
+#include "time_column.cuh"
 
 namespace {
 
@@ -110,9 +111,9 @@ expd_status upload_vec(expd_plan p, T** dptr, const std::vector<T>& h, const cha
 
 void free_plan(expd_plan p) {
     if (!p) return;
-    void* bufs[] = {p->E,    p->Wx64, p->Wx32,   p->Wy64,    p->Wy32,    p->Sx,        p->Sy,
+    void* bufs[] = {p->E,    p->C64,  p->C32, p->Cdd, p->Wxdd, p->Wydd, p->gamdd, p->oscdd, p->Wx64, p->Wx32,   p->Wy64,    p->Wy32,    p->Sx,        p->Sy,
                     p->Uh,   p->Fh,   p->Sh,     p->fh,      p->NL64,    p->NL32,      p->work64,
-                    p->work32, p->startphys, p->partial, p->redout, p->stage, p->gm};
+                    p->work32, p->startphys, p->partial, p->redout, p->stage, p->gm, p->U32, p->F32};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->redhost) cudaFreeHost(p->redhost);
@@ -241,12 +242,22 @@ expd_status read_norms(expd_plan p, cudaStream_t s, double out[4]) {
 }
 
 // U output: u_1..u_{s-1} from the startup values, u_s..u_Nt from Uh.
-expd_status write_solution(expd_plan p, double* U, cudaStream_t s) {
+// Uh holds double-float values when uh_dd (the mixed path's accurate phase).
+expd_status write_solution(expd_plan p, double* U, cudaStream_t s, bool uh_dd = false) {
     const size_t M = (size_t)p->M;
     if (p->order > 1)
         EXPD_CUDA_TRY(cudaMemcpyAsync(U, p->startphys + M, (size_t)(p->order - 1) * M * sizeof(double),
                                       cudaMemcpyDeviceToDevice, s));
+    if (uh_dd) return spatial_inverse_dd(p, p->Uh, U + (size_t)(p->order - 1) * M, p->Ns, s);
     return spatial_inverse64(p, p->Uh, U + (size_t)(p->order - 1) * M, p->Ns, s);
+}
+
+struct float2_pair {
+    float hi, lo;
+};
+float2_pair split_dd(double v) {
+    const float hi = (float)v;
+    return {hi, (float)(v - (double)hi)};
 }
 
 void info_reset(expd_info* info) {
@@ -405,7 +416,8 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
     expd_status st = EXPD_OK;
     // ---- eigenvalues of L_h: E_m = exp(dt mu_m) ----
     {
-        std::vector<double> E(p->Mcol);
+        std::vector<double> E(p->Mcol), C64((size_t)p->order * p->Mcol);
+        std::vector<float> C32((size_t)p->order * p->Mcol);
         for (long long m = 0; m < p->Mcol; ++m) {
             const int kx = (int)(m % p->KX);
             const int ky = (int)(m / p->KX);
@@ -429,8 +441,25 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
                 }
             }
             E[m] = exp(dt * mu);
+            for (int j = 1; j <= p->order; ++j) {
+                const double cjm = p->acoef[p->order][j] * exp(j * dt * mu);
+                C64[(size_t)(j - 1) * p->Mcol + m] = cjm;
+                C32[(size_t)(j - 1) * p->Mcol + m] = (float)cjm;
+            }
         }
         st = upload_vec(p, &p->E, E, "E", s);
+        if (st == EXPD_OK) st = upload_vec(p, &p->C64, C64, "coefficients", s);
+        if (st == EXPD_OK) st = upload_vec(p, &p->C32, C32, "coefficients (float32)", s);
+        if (st == EXPD_OK && p->precision == EXPD_PREC_MIXED && p->bc == EXPD_BC_PERIODIC) {
+            std::vector<float2> Cdd(C64.size());
+            for (size_t i = 0; i < C64.size(); ++i) {
+                const float2_pair d = split_dd(C64[i]);
+                Cdd[i] = make_float2(d.hi, d.lo);
+            }
+            float2* dptr = nullptr;
+            st = upload_vec(p, &dptr, Cdd, "coefficients (double-float)", s);
+            p->Cdd = dptr;
+        }
     }
     // ---- spatial transform tables ----
     if (st == EXPD_OK && p->bc == EXPD_BC_PERIODIC) {
@@ -453,6 +482,39 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
             }
             st = upload_vec(p, &p->Wy64, y64, "Wy", s);
             if (st == EXPD_OK) st = upload_vec(p, &p->Wy32, y32, "Wy32", s);
+        }
+    }
+    // double-float copies of the twiddles and of Gamma_alpha / the output scale
+    if (st == EXPD_OK && p->precision == EXPD_PREC_MIXED && p->bc == EXPD_BC_PERIODIC) {
+        for (int d = 0; d < p->ndim && st == EXPD_OK; ++d) {
+            const int n = d == 0 ? p->NX : p->NY;
+            const int cnt = d == 0 ? n / 2 + 1 : std::max(1, n / 2);
+            std::vector<float4> w(cnt);
+            for (int k = 0; k < cnt; ++k) {
+                const double ang = -2.0 * M_PI * k / n;
+                const float2_pair c = split_dd(cos(ang)), sn = split_dd(sin(ang));
+                w[k] = make_float4(c.hi, c.lo, sn.hi, sn.lo);
+            }
+            float4* dptr = nullptr;
+            st = upload_vec(p, &dptr, w, "twiddles (double-float)", s);
+            (d == 0 ? p->Wxdd : p->Wydd) = dptr;
+        }
+        if (st == EXPD_OK) {
+            const TimeTablesHost th = time_tables_host(Nt - scheme->order + 1, alpha);
+            const double extra = th.bluestein ? 1.0 / ((double)th.L * (double)th.L) : 1.0;
+            std::vector<float2> g(th.gamma.size()), o(th.gamma.size());
+            for (size_t n = 0; n < g.size(); ++n) {
+                const float2_pair a = split_dd(th.gamma[n]);
+                const float2_pair b = split_dd(extra / ((double)p->Ns * th.gamma[n]));
+                g[n] = make_float2(a.hi, a.lo);
+                o[n] = make_float2(b.hi, b.lo);
+            }
+            float2* gp = nullptr;
+            float2* op = nullptr;
+            st = upload_vec(p, &gp, g, "Gamma (double-float)", s);
+            if (st == EXPD_OK) st = upload_vec(p, &op, o, "output scale (double-float)", s);
+            p->gamdd = gp;
+            p->oscdd = op;
         }
     }
     if (st == EXPD_OK && p->bc == EXPD_BC_DIRICHLET) {
@@ -485,7 +547,17 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
             if (st == EXPD_OK) st = dalloc(p, &p->work32, (size_t)p->Ns * p->NY * p->KX * sizeof(float2), "work32");
         }
     }
-    if (st == EXPD_OK) st = dalloc(p, reinterpret_cast<void**>(&p->redout), 8 * sizeof(double), "norms");
+    // float32 sweeps of the mixed path: iterate and right-hand side in float32
+    if (st == EXPD_OK && p->precision == EXPD_PREC_MIXED && (p->nonlin == EXPD_NL_NONE || p->bc == EXPD_BC_PERIODIC)) {
+        st = dalloc(p, &p->U32, vec / 2, "iterate (float32)");
+        if (st == EXPD_OK) st = dalloc(p, &p->F32, vec / 2, "right-hand side (float32)");
+    }
+    // norms: [0..3] results, [6] election counter of the reduction, [8..] per-slice totals
+    if (st == EXPD_OK) st = dalloc(p, reinterpret_cast<void**>(&p->redout), (8 + 2 * (size_t)p->Ns) * sizeof(double), "norms");
+    if (st == EXPD_OK) {
+        cudaError_t e = cudaMemsetAsync(p->redout, 0, (8 + 2 * (size_t)p->Ns) * sizeof(double), s);
+        if (e != cudaSuccess) st = expd_cuda_fail(e, "cudaMemsetAsync(norms)", __FILE__, __LINE__);
+    }
     if (st == EXPD_OK) {
         cudaError_t e = cudaMallocHost(&p->redhost, 8 * sizeof(double));
         if (e != cudaSuccess) st = expd_cuda_fail(e, "cudaMallocHost(norms)", __FILE__, __LINE__);
@@ -496,6 +568,61 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
         return st;
     }
     *out = p;
+    return EXPD_OK;
+}
+
+expd_status expd_plan_footprint_bytes(const expd_grid* grid, const expd_operator* op, double dt, int Nt,
+                                      double alpha, const expd_scheme* scheme, int flags, size_t* bytes) {
+    if (!bytes) return expd_fail(EXPD_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = 0;
+    expd_plan_s pl;
+    expd_plan p = &pl;
+    expd_status st = plan_init_fields(p, grid, op, dt, Nt, alpha, scheme);
+    if (st != EXPD_OK) return st;
+    const size_t Mcol = (size_t)p->Mcol, Ns = (size_t)p->Ns, ord = (size_t)p->order;
+    const bool per = p->bc == EXPD_BC_PERIODIC, mixed = p->precision == EXPD_PREC_MIXED;
+    const bool nl = p->nonlin != EXPD_NL_NONE;
+    const size_t vec = Ns * Mcol * p->esz;
+    size_t b = 0;
+    b += Mcol * 8 + ord * Mcol * 8 + ord * Mcol * 4;                       // E, C64, C32
+    if (mixed && per) b += ord * Mcol * 8;                                  // Cdd
+    if (per) {
+        b += (size_t)(p->NX / 2 + 1) * (16 + 8);                            // Wx64, Wx32
+        if (p->ndim == 2) b += (size_t)std::max(1, p->NY / 2) * (16 + 8);  // Wy64, Wy32
+        if (mixed) {
+            b += (size_t)(p->NX / 2 + 1) * 16;                              // Wxdd
+            if (p->ndim == 2) b += (size_t)std::max(1, p->NY / 2) * 16;    // Wydd
+            b += 2 * Ns * 8;                                                // gamdd, oscdd
+        }
+    } else {
+        b += (size_t)p->NX * p->NX * 8;
+        if (p->ndim == 2) b += (size_t)p->NY * p->NY * 8;
+    }
+    b += 2 * vec + ord * Mcol * p->esz + ord * (size_t)p->M * 8;            // Uh, Fh, Sh, startphys
+    b += Ns * p->NY * p->KX * 16;                                           // work64
+    if (nl) {
+        b += vec;
+        if (mixed && per) b += Ns * Mcol * 8 + Ns * p->NY * p->KX * 8;      // NL32, work32
+    }
+    if (mixed && (!nl || per)) b += vec;                                    // U32, F32
+    b += (8 + 2 * Ns) * 8;                                                  // norms
+    const TimeTablesHost th = time_tables_host(p->Ns, alpha);
+    for (int q = 0; q < 2; ++q) {
+        const size_t e = q == 0 ? 16 : 8, g = q == 0 ? 8 : 4;
+        b += e * (th.tw.size()) + 16 + e * Ns + 16 + 2 * g * Ns;
+        if (th.bluestein) b += e * Ns + 16 + 2 * (e * th.L + 16);
+    }
+    int grid_t = 0;
+    st = time_grid_for(p, &grid_t);
+    if (st != EXPD_OK) return st;
+    b += (size_t)grid_t * Ns * 16;                                          // norm partials
+    if (flags & EXPD_FOOTPRINT_SOURCE) b += (size_t)p->Nt * Mcol * p->esz;
+    if (flags & EXPD_FOOTPRINT_HOST) b += (size_t)(2 * p->Nt + 1) * p->M * 8;
+    if (flags & EXPD_FOOTPRINT_GMRES) {
+        const size_t n = (size_t)eigen_elems(p);
+        b += (size_t)(p->restart + 3) * n * 8 + (128 + 65 * (size_t)p->sm_count * 4) * 8;
+    }
+    *bytes = b;
     return EXPD_OK;
 }
 
@@ -631,29 +758,69 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     if (st != EXPD_OK) return st;
     st = setup_start(p, sg.u0, sg.f, sg.U, s);
     if (st != EXPD_OK) return st;
-    EXPD_CUDA_TRY(cudaMemsetAsync(p->Uh, 0, (size_t)p->Ns * p->Mcol * p->esz, s));
-
     const bool nl = p->nonlin != EXPD_NL_NONE;
     const bool mixed = p->precision == EXPD_PREC_MIXED;
-    bool spatial32 = mixed && nl && p->NL32 != nullptr;
+    const long long nelem = p->Mcol * (p->realcol ? 1 : 2);
+    const long long nvec = (long long)p->Ns * nelem;
+    // Mixed path: float32 sweeps (iterate, right-hand side, residual, N and the
+    // preconditioner all in float32) until the estimated error reaches tol or
+    // the float32 floor stops the contraction; then sweeps with an accurate
+    // iterate, residual and N -- double-float (float hi + float lo, on the
+    // float32 pipes) on periodic grids, float64 otherwise -- converge to the
+    // float64 fixed point with the float32 preconditioner.
+    enum { PH32, PHDD, PH64 };
+    const bool use_dd = mixed && p->bc == EXPD_BC_PERIODIC && p->Cdd != nullptr;
+    int phase = (mixed && p->U32 != nullptr) ? PH32 : PH64;
+    if (phase == PH32) {
+        st = convert_f64_to_f32(p, static_cast<const double*>(p->Fh), static_cast<float*>(p->F32), nvec, s);
+        if (st != EXPD_OK) return st;
+        EXPD_CUDA_TRY(cudaMemsetAsync(p->U32, 0, (size_t)nvec * sizeof(float), s));
+    } else {
+        EXPD_CUDA_TRY(cudaMemsetAsync(p->Uh, 0, (size_t)nvec * sizeof(double), s));
+    }
+    // leave the float32 sweeps: the iterate (exact in float32) becomes the
+    // accurate phase's starting point
+    auto leave32 = [&]() -> expd_status {
+        expd_status r;
+        if (use_dd) {
+            r = convert_f32_to_dd(p, static_cast<const float*>(p->U32), p->Uh, nvec, s);
+            if (r == EXPD_OK) r = convert_f64_to_dd_inplace(p, static_cast<double*>(p->Fh), nvec, s);
+            phase = PHDD;
+        } else {
+            r = convert_f32_to_f64(p, static_cast<const float*>(p->U32), static_cast<double*>(p->Uh), nvec, s);
+            phase = PH64;
+        }
+        return r;
+    };
     double prev = 0.0, rho = 0.5, rho_phase = -1.0, measure = 1.0, s_first = 0.0;
     int it = 0, it32 = 0;
     expd_status result = EXPD_ERR_NOT_CONVERGED;
     for (it = 1; it <= p->max_iter; ++it) {
         TimeOp op;
-        op.X = p->Uh;
-        op.F = p->Fh;
+        op.X = phase == PH32 ? p->U32 : p->Uh;
+        op.F = phase == PH32 ? p->F32 : p->Fh;
         op.sigR = -1.0;
         op.precond = 1;
         op.accum = 1;
         op.f32 = mixed;
-        const bool used32 = spatial32;
+        op.st32 = phase == PH32;
+        op.stdd = phase == PHDD;
+        const bool used32 = phase == PH32;
         if (nl) {
-            void* NL = spatial32 ? p->NL32 : p->NL64;
-            st = nonlinear_eval(p, p->Uh, NL, spatial32 ? 1 : 0, s);
+            void* NL;
+            if (phase == PH32) {
+                NL = p->NL32;
+                st = nonlinear_eval(p, op.X, NL, 1, s, 1);
+                op.nl_f32 = 1;
+            } else if (phase == PHDD) {
+                NL = p->NL64;  // holds double-float values in this phase
+                st = nonlinear_eval_dd(p, op.X, NL, s);
+            } else {
+                NL = p->NL64;
+                st = nonlinear_eval(p, op.X, NL, 0, s, 0);
+            }
             if (st != EXPD_OK) return st;
             op.NL = NL;
-            op.nl_f32 = spatial32 ? 1 : 0;
             op.bdt = p->beta[p->order] * p->dt;
         }
         st = time_apply(p, op, s);
@@ -674,17 +841,17 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
             const double ratio = smax / prev;
             rho = std::min(0.95, std::max(1e-12, ratio));
         }
-        // in the float64 phase after a float32 phase, the contraction is the
+        // in the accurate phase after a float32 phase, the contraction is the
         // one observed before the float32 floor was reached
-        const double r_use = (rho_phase > 0 && !spatial32) ? rho_phase : rho;
+        const double r_use = (rho_phase > 0 && phase != PH32) ? rho_phase : rho;
         measure = it == 1 ? rel : rel * r_use / (1.0 - r_use);
         if (info && it <= EXPD_MAX_HISTORY) info->history[it - 1] = measure;
         if (info) info->contraction = rho;
-        if (spatial32) {
-            // leave the float32 sweeps once the iterate is near tol or stalls
+        if (phase == PH32) {
             const bool stalled = it > 2 && rho > 0.5;
             if (measure <= p->tol || stalled) {
-                spatial32 = false;
+                st = leave32();
+                if (st != EXPD_OK) return st;
                 if (!stalled) rho_phase = rho;
                 else if (rho_phase < 0) rho_phase = 0.5;
             } else if (rho < 0.5) {
@@ -698,12 +865,16 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
         prev = smax;
     }
     if (it > p->max_iter) it = p->max_iter;
+    if (phase == PH32) {
+        st = leave32();
+        if (st != EXPD_OK) return st;
+    }
     if (info) {
         info->iterations = it;
         info->fp32_iterations = it32;
         info->final_measure = measure;
     }
-    st = write_solution(p, sg.U, s);
+    st = write_solution(p, sg.U, s, phase == PHDD);
     if (st != EXPD_OK) return st;
     st = stage_out(p, sg, s);
     if (st != EXPD_OK) return st;

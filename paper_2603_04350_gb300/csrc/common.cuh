@@ -99,23 +99,61 @@ EXPD_HD int ilog2(int n) {
 // ts is the stride of the table for this length (tables are shared between a
 // length and its divisors).  sign = -1 transforms with exp(-2 pi i jk/n),
 // sign = +1 with exp(+2 pi i jk/n); no normalisation.
+//
+// Both routines fuse pairs of radix-2 stages: the four elements a pair of
+// stages combines are held in registers, so each shared-memory round trip
+// (and each warp synchronisation) covers two stages; an odd leftover stage has
+// trivial twiddles.
+
+// -i*a (sign < 0) or +i*a (sign > 0): the twiddle W_{4h}^h of a fused stage pair.
+template <typename T2>
+EXPD_HD T2 cmul_quarter(T2 a, int sign) {
+    T2 r;
+    if (sign > 0) {
+        r.x = -a.y;
+        r.y = a.x;
+    } else {
+        r.x = a.y;
+        r.y = -a.x;
+    }
+    return r;
+}
 
 // Decimation in time: x in bit-reversed order -> X in natural order.
 template <typename T2>
 EXPD_HD void fft_dit(T2* x, int log2n, const T2* tw, int ts, int sign, int lane, int nlanes) {
     const int n = 1 << log2n;
-    for (int s = 0; s < log2n; ++s) {
-        const int h = 1 << s;
-        const int tstep = (n >> (s + 1)) * ts;
+    int s = 0;
+    if (log2n & 1) {
         for (int b = lane; b < (n >> 1); b += nlanes) {
-            const int k = b & (h - 1);
-            const int i = ((b >> s) << (s + 1)) + k;
-            T2 w = tw[k * tstep];
-            if (sign > 0) w.y = -w.y;
-            const T2 u = x[i];
-            const T2 v = cmul(x[i + h], w);
-            x[i] = cadd(u, v);
-            x[i + h] = csub(u, v);
+            const T2 u = x[2 * b], v = x[2 * b + 1];
+            x[2 * b] = cadd(u, v);
+            x[2 * b + 1] = csub(u, v);
+        }
+        EXPD_SYNCWARP();
+        s = 1;
+    }
+    for (; s < log2n; s += 2) {
+        const int h = 1 << s;
+        const int t2 = (n >> (s + 1)) * ts;  // W_{2h}^k = tw[k * t2]
+        const int t4 = (n >> (s + 2)) * ts;  // W_{4h}^k = tw[k * t4]
+        for (int g = lane; g < (n >> 2); g += nlanes) {
+            const int k = g & (h - 1);
+            const int i = ((g >> s) << (s + 2)) + k;
+            T2 w2 = tw[k * t2], w4 = tw[k * t4];
+            if (sign > 0) {
+                w2.y = -w2.y;
+                w4.y = -w4.y;
+            }
+            const T2 x0 = x[i], x1 = cmul(x[i + h], w2);
+            const T2 x2 = x[i + 2 * h], x3 = cmul(x[i + 3 * h], w2);
+            const T2 a0 = cadd(x0, x1), a1 = csub(x0, x1);
+            const T2 a2 = cmul(cadd(x2, x3), w4);
+            const T2 a3 = cmul_quarter(cmul(csub(x2, x3), w4), sign);
+            x[i] = cadd(a0, a2);
+            x[i + 2 * h] = csub(a0, a2);
+            x[i + h] = cadd(a1, a3);
+            x[i + 3 * h] = csub(a1, a3);
         }
         EXPD_SYNCWARP();
     }
@@ -125,18 +163,36 @@ EXPD_HD void fft_dit(T2* x, int log2n, const T2* tw, int ts, int sign, int lane,
 template <typename T2>
 EXPD_HD void fft_dif(T2* x, int log2n, const T2* tw, int ts, int sign, int lane, int nlanes) {
     const int n = 1 << log2n;
-    for (int s = log2n - 1; s >= 0; --s) {
-        const int h = 1 << s;
-        const int tstep = (n >> (s + 1)) * ts;
+    int s = log2n - 1;
+    for (; s >= 1; s -= 2) {
+        // stages s (span 2h) and s-1 (span h), h = 2^(s-1)
+        const int h = 1 << (s - 1);
+        const int t4 = (n >> (s + 1)) * ts;  // W_{4h}^k
+        const int t2 = (n >> s) * ts;        // W_{2h}^k
+        for (int g = lane; g < (n >> 2); g += nlanes) {
+            const int k = g & (h - 1);
+            const int i = ((g >> (s - 1)) << (s + 1)) + k;
+            T2 w2 = tw[k * t2], w4 = tw[k * t4];
+            if (sign > 0) {
+                w2.y = -w2.y;
+                w4.y = -w4.y;
+            }
+            const T2 x0 = x[i], x1 = x[i + h], x2 = x[i + 2 * h], x3 = x[i + 3 * h];
+            const T2 a0 = cadd(x0, x2), a1 = cadd(x1, x3);
+            const T2 a2 = cmul(csub(x0, x2), w4);
+            const T2 a3 = cmul_quarter(cmul(csub(x1, x3), w4), sign);
+            x[i] = cadd(a0, a1);
+            x[i + h] = cmul(csub(a0, a1), w2);
+            x[i + 2 * h] = cadd(a2, a3);
+            x[i + 3 * h] = cmul(csub(a2, a3), w2);
+        }
+        EXPD_SYNCWARP();
+    }
+    if (s == 0) {
         for (int b = lane; b < (n >> 1); b += nlanes) {
-            const int k = b & (h - 1);
-            const int i = ((b >> s) << (s + 1)) + k;
-            T2 w = tw[k * tstep];
-            if (sign > 0) w.y = -w.y;
-            const T2 u = x[i];
-            const T2 v = x[i + h];
-            x[i] = cadd(u, v);
-            x[i + h] = cmul(csub(u, v), w);
+            const T2 u = x[2 * b], v = x[2 * b + 1];
+            x[2 * b] = cadd(u, v);
+            x[2 * b + 1] = csub(u, v);
         }
         EXPD_SYNCWARP();
     }

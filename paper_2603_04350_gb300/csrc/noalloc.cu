@@ -60,9 +60,15 @@ struct Carve {
 
 // Spatial tables: E_m = exp(dt mu_m), FFT twiddles, DST-I matrices (float64,
 // the same formulas expd_plan_create evaluates on the host).
+struct BdfRow {
+    double a[7];
+    int order;
+};
+
 __global__ void spatial_tables_kernel(int bc, int ndim, int NX, int NY, double LX, double LY, double a, double c,
-                                      double dt, int KX, long long Mcol, double* E, double2* Wx64, float2* Wx32,
-                                      double2* Wy64, float2* Wy32, double* Sx, double* Sy) {
+                                      double dt, int KX, long long Mcol, double* E, double* C64, float* C32,
+                                      BdfRow bdf, double2* Wx64, float2* Wx32, double2* Wy64, float2* Wy32,
+                                      double* Sx, double* Sy) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     for (long long m = t0; m < Mcol; m += stride) {
@@ -87,6 +93,11 @@ __global__ void spatial_tables_kernel(int bc, int ndim, int NX, int NY, double L
             }
         }
         E[m] = exp(dt * mu);
+        for (int j = 1; j <= bdf.order; ++j) {
+            const double cjm = bdf.a[j] * exp(j * dt * mu);
+            C64[(long long)(j - 1) * Mcol + m] = cjm;
+            C32[(long long)(j - 1) * Mcol + m] = (float)cjm;
+        }
     }
     if (bc == EXPD_BC_PERIODIC) {
         for (long long k = t0; k <= NX / 2; k += stride) {
@@ -120,9 +131,10 @@ __global__ void spatial_tables_kernel(int bc, int ndim, int NX, int NY, double L
 // Bluestein the chirp and the FFT_L of the two convolution kernels, computed by
 // one warp with the same shared-memory FFT the time kernel uses (its
 // bit-reversed output order is the order the time kernel expects).
-__global__ void time_tables_kernel(int Ns, double alpha, int L, int log2L, int bluestein, double* gamma,
-                                   double2* tw64, float2* tw32, double2* lam64, float2* lam32, double2* ch64,
-                                   float2* ch32, double2* bp64, float2* bp32, double2* bm64, float2* bm32) {
+__global__ void time_tables_kernel(int Ns, double alpha, int L, int log2L, int bluestein, double* gam64,
+                                   double* osc64, float* gam32, float* osc32, double2* tw64, float2* tw32,
+                                   double2* lam64, float2* lam32, double2* ch64, float2* ch32, double2* bp64,
+                                   float2* bp32, double2* bm64, float2* bm32) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* stw = reinterpret_cast<double2*>(smem_raw);  // [L/2]
     double2* sb = stw + (L / 2 > 0 ? L / 2 : 1);           // [L]
@@ -139,7 +151,12 @@ __global__ void time_tables_kernel(int Ns, double alpha, int L, int log2L, int b
         sincospi(2.0 * (double)k / Ns, &sn, &cs);
         lam64[k] = make_double2(ar * cs, ar * sn);
         lam32[k] = make_float2((float)(ar * cs), (float)(ar * sn));
-        gamma[k] = pow(alpha, (double)k / Ns);
+        const double g = pow(alpha, (double)k / Ns);
+        const double o = (bluestein ? 1.0 / ((double)L * (double)L) : 1.0) / ((double)Ns * g);
+        gam64[k] = g;
+        osc64[k] = o;
+        gam32[k] = (float)g;
+        osc32[k] = (float)o;
         if (bluestein) {
             const long long r = ((long long)k * k) % (2LL * Ns);
             sincospi((double)r / Ns, &sn, &cs);
@@ -203,6 +220,8 @@ extern "C" expd_status expd_precond_apply_noalloc(const expd_grid* grid, const e
     for (int pass = 0; pass < 2; ++pass) {
         Carve cv{pass == 0 ? nullptr : base};
         p->E = cv.take<double>(p->Mcol);
+        p->C64 = cv.take<double>((size_t)p->order * p->Mcol);
+        p->C32 = cv.take<float>((size_t)p->order * p->Mcol);
         if (p->bc == EXPD_BC_PERIODIC) {
             p->Wx64 = cv.take<double2>(p->NX / 2 + 1);
             p->Wx32 = cv.take<float2>(p->NX / 2 + 1);
@@ -215,14 +234,14 @@ extern "C" expd_status expd_precond_apply_noalloc(const expd_grid* grid, const e
             if (p->ndim == 2) p->Sy = cv.take<double>((size_t)p->NY * p->NY);
         }
         TimeTables* tt[2] = {&p->t64, &p->t32};
-        double* gamma = cv.take<double>(p->Ns);
         for (int q = 0; q < 2; ++q) {
             const size_t e = q == 0 ? sizeof(double2) : sizeof(float2);
             TimeTables& t = *tt[q];
             t.L = L;
             t.log2L = ilog2(L);
             t.bluestein = blue;
-            t.gamma = gamma;
+            t.gam = cv.take<char>(e / 2 * p->Ns);
+            t.osc = cv.take<char>(e / 2 * p->Ns);
             t.tw = cv.take<char>(e * (L / 2 > 0 ? L / 2 : 1));
             t.lam = cv.take<char>(e * p->Ns);
             t.chirp = blue ? cv.take<char>(e * p->Ns) : nullptr;
@@ -246,16 +265,20 @@ extern "C" expd_status expd_precond_apply_noalloc(const expd_grid* grid, const e
     // ---- tables, then the three steps around the spatial transforms ----
     {
         KProf kp(p, s, EXPD_K_POINTWISE, 8.0 * (double)p->Mcol, 0.0);
+        BdfRow bdf;
+        for (int j = 0; j < 7; ++j) bdf.a[j] = p->acoef[p->order][j];
+        bdf.order = p->order;
         spatial_tables_kernel<<<p->sm_count * 4, 256, 0, s>>>(p->bc, p->ndim, p->NX, p->NY, p->LX, p->LY, p->a, p->c,
-                                                              p->dt, p->KX, p->Mcol, p->E, p->Wx64, p->Wx32, p->Wy64,
-                                                              p->Wy32, p->Sx, p->Sy);
+                                                              p->dt, p->KX, p->Mcol, p->E, p->C64, p->C32, bdf,
+                                                              p->Wx64, p->Wx32, p->Wy64, p->Wy32, p->Sx, p->Sy);
         EXPD_CUDA_TRY(cudaGetLastError());
     }
     {
         KProf kp(p, s, EXPD_K_POINTWISE, 64.0 * L, 0.0);
         const size_t smem = (size_t)((L / 2 > 0 ? L / 2 : 1) + L) * sizeof(double2);
         time_tables_kernel<<<1, 256, smem, s>>>(
-            p->Ns, p->alpha, L, ilog2(L), blue, p->t64.gamma, static_cast<double2*>(p->t64.tw),
+            p->Ns, p->alpha, L, ilog2(L), blue, static_cast<double*>(p->t64.gam), static_cast<double*>(p->t64.osc),
+            static_cast<float*>(p->t32.gam), static_cast<float*>(p->t32.osc), static_cast<double2*>(p->t64.tw),
             static_cast<float2*>(p->t32.tw), static_cast<double2*>(p->t64.lam), static_cast<float2*>(p->t32.lam),
             static_cast<double2*>(p->t64.chirp), static_cast<float2*>(p->t32.chirp), static_cast<double2*>(p->t64.bplus),
             static_cast<float2*>(p->t32.bplus), static_cast<double2*>(p->t64.bminus), static_cast<float2*>(p->t32.bminus));

@@ -23,9 +23,11 @@ expd_status plan_init_fields(expd_plan_s* p, const expd_grid* grid, const expd_o
                              double alpha, const expd_scheme* scheme);
 bool expd_is_device_ptr(const void* ptr);
 
+// Time-direction tables in one precision (t64: double, t32: float).
 struct TimeTables {
     int L = 0, log2L = 0, bluestein = 0;
-    double* gamma = nullptr;  // [Ns]   alpha^(n/Ns)
+    void* gam = nullptr;      // [Ns]   Gamma_alpha: alpha^(n/Ns)
+    void* osc = nullptr;      // [Ns]   output scale 1/(Ns alpha^(n/Ns)), times 1/L^2 for Bluestein
     void* lam = nullptr;      // [Ns]   lambda_n = alpha^(1/Ns) e^{2 pi i n/Ns}
     void* tw = nullptr;       // [L/2]  e^{-2 pi i k/L}
     void* chirp = nullptr;    // [Ns]   e^{+pi i n^2/Ns}           (Bluestein)
@@ -57,10 +59,17 @@ struct expd_plan_s {
 
     // ---- tables ---------------------------------------------------------------
     double* E = nullptr;       // [Mcol] exp(dt mu_m)
+    double* C64 = nullptr;     // [order][Mcol] a_j exp(j dt mu_m), j = 1..order (time-kernel coefficients)
+    float* C32 = nullptr;      // the same in float32
     double2* Wx64 = nullptr;   // [NX/2+1] e^{-2 pi i k/NX}
     float2* Wx32 = nullptr;
     double2* Wy64 = nullptr;   // [NY/2]   e^{-2 pi i k/NY}
     float2* Wy32 = nullptr;
+    void* Wxdd = nullptr;      // double-float copies of Wx / Wy (dd2)
+    void* Wydd = nullptr;
+    void* Cdd = nullptr;       // [order][Mcol] double-float coefficients (dd)
+    void* gamdd = nullptr;     // [Ns] Gamma_alpha as double-float
+    void* oscdd = nullptr;     // [Ns] output scale as double-float
     double* Sx = nullptr;      // Dirichlet: [NX][NX] orthonormal DST-I matrix
     double* Sy = nullptr;      // Dirichlet: [NY][NY]
     TimeTables t64, t32;
@@ -74,8 +83,10 @@ struct expd_plan_s {
     void* NL32 = nullptr;      // [Ns][Mcol] N(v) transformed, float32 (mixed)
     void* work64 = nullptr;    // [Ns][NY][KX] double2 / physical scratch
     void* work32 = nullptr;    // [Ns][NY][KX] float2 (mixed nonlinear)
+    void* U32 = nullptr;       // [Ns][Mcol] float32 iterate of the mixed path's float32 sweeps
+    void* F32 = nullptr;       // [Ns][Mcol] float32 copy of Fh
     double* startphys = nullptr;  // [order][M] physical u_0..u_{s-1}
-    double2* partial = nullptr;   // [time grid][Ns] per-slice norm partials
+    double2* partial = nullptr;   // [Ns][time grid] per-slice norm partials
     double* redout = nullptr;     // [4] reduced norms (device)
     double* redhost = nullptr;    // [4] pinned host copy
     int time_grid = 0;            // CTAs of the time kernel (multiple of SM count)
@@ -117,8 +128,16 @@ struct KProf {
 expd_status spatial_forward64(expd_plan p, const double* phys, void* eig, int nslices, cudaStream_t s);
 expd_status spatial_inverse64(expd_plan p, const void* eig, double* phys, int nslices, cudaStream_t s);
 // out = transform of N(inverse transform of Uh) for the Ns unknown slices, in
-// float32 (f32 = 1, out is float2/float) or float64.
-expd_status nonlinear_eval(expd_plan p, const void* Uh, void* out, int f32, cudaStream_t s);
+// float32 (f32 = 1, out is float2/float) or float64; Uh is float32 when in32.
+expd_status nonlinear_eval(expd_plan p, const void* Uh, void* out, int f32, cudaStream_t s, int in32 = 0);
+// elementwise precision conversion of n values (double <-> float)
+expd_status convert_f64_to_f32(expd_plan p, const double* in, float* out, long long n, cudaStream_t s);
+expd_status convert_f32_to_f64(expd_plan p, const float* in, double* out, long long n, cudaStream_t s);
+// double-float ("dd", float hi + float lo) helpers of the mixed path's accurate phase
+expd_status convert_f64_to_dd_inplace(expd_plan p, double* a, long long n, cudaStream_t s);
+expd_status convert_f32_to_dd(expd_plan p, const float* in, void* out, long long n, cudaStream_t s);
+expd_status nonlinear_eval_dd(expd_plan p, const void* Uh, void* out, cudaStream_t s);
+expd_status spatial_inverse_dd(expd_plan p, const void* eig, double* phys, int nslices, cudaStream_t s);
 // u = solution of u - bdt N(u) = w, pointwise (float64 physical).
 expd_status pointwise_solve(expd_plan p, const double* w, double* u, long long n, double bdt, cudaStream_t s);
 // out[m] = sum_{j=1..q} coef[j] E_m^j in[j][m] + g * src[m]   (eigen arrays)
@@ -138,7 +157,9 @@ struct TimeOp {
     int precond = 1;           // apply (R_s^alpha)^{-1} to the combination
     int accum = 0;             // X += result (X must be writable) instead of out = result
     void* out = nullptr;
-    int f32 = 0;               // preconditioner precision
+    int f32 = 0;               // preconditioner precision (steps (a)-(c))
+    int st32 = 0;              // X, F, NL, out and the residual arithmetic in float32
+    int stdd = 0;              // X, F, NL, out and the residual arithmetic in double-float
 };
 expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s);
 // reduce per-slice partials: redout[0] = max_n ||res_n||, [1] = max_n ||X_n||,

@@ -130,9 +130,11 @@ static void test_column(int Ns, int order, double E, double alpha, double tol, s
     for (int n = 0; n < Ns; ++n) w[t.bluestein ? n : bitrev(n, t.log2L)] = y[n];
     std::vector<T2> wd = to_dev<T2, T>(w), twd = to_dev<T2, T>(t.tw), lamd = to_dev<T2, T>(t.lam);
     std::vector<T2> chd = to_dev<T2, T>(t.chirp), bpd = to_dev<T2, T>(t.bplus), bmd = to_dev<T2, T>(t.bminus);
+    T cjT[7];
+    for (int j = 0; j < 7; ++j) cjT[j] = (T)cj[j];
     const double sc = precond_column<T, T2>(wd.data(), Ns, t.L, t.log2L, t.bluestein, twd.data(), lamd.data(),
                                             t.bluestein ? chd.data() : nullptr, t.bluestein ? bpd.data() : nullptr,
-                                            t.bluestein ? bmd.data() : nullptr, cj, order, 0, 1);
+                                            t.bluestein ? bmd.data() : nullptr, cjT, order, 0, 1);
     double err = 0;
     for (int n = 0; n < Ns; ++n) {
         const T2 v = wd[t.bluestein ? n : bitrev(n, t.log2L)];

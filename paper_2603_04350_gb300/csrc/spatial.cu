@@ -16,25 +16,14 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
+#include "dd.cuh"
 #include "plan.h"
 
 namespace {
-
-template <typename T2>
-__device__ __forceinline__ T2 cvt2(double2 v);
-template <>
-__device__ __forceinline__ double2 cvt2<double2>(double2 v) { return v; }
-template <>
-__device__ __forceinline__ float2 cvt2<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
-template <typename T2>
-__device__ __forceinline__ T2 cvt2(float2 v);
-template <>
-__device__ __forceinline__ double2 cvt2<double2>(float2 v) { return to_c64(v); }
-template <>
-__device__ __forceinline__ float2 cvt2<float2>(float2 v) { return v; }
 
 template <typename R>
 __device__ __forceinline__ R nl_ac(R u) { return u - u * u * u; }
@@ -125,19 +114,22 @@ __global__ void col_kernel(const TIN* __restrict__ in, TOUT* __restrict__ out, i
     for (int i = threadIdx.x; i < nw; i += blockDim.x) W[i] = Wg[i];
     const long long base = (long long)blockIdx.y * NY * KX;
     const int kx0 = blockIdx.x * C;
+    // columns are contiguous in shared memory with a padded stride, so the
+    // transposing load and store spread consecutive columns over the banks
+    const int NYP = NY + 1;
     for (int idx = threadIdx.x; idx < NY * C; idx += blockDim.x) {
         const int y = idx / C, c = idx - y * C, kx = kx0 + c;
         PT2 v = c2((PT)0, (PT)0);
         if (kx < KX) v = cvt2<PT2>(in[base + (long long)y * KX + kx]);
-        buf[c * NY + bitrev(y, log2NY)] = v;
+        buf[c * NYP + bitrev(y, log2NY)] = v;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (warp < C && kx0 + warp < KX) fft_dit(buf + warp * NY, log2NY, W, 1, sign, lane, 32);
+    if (warp < C && kx0 + warp < KX) fft_dit(buf + warp * NYP, log2NY, W, 1, sign, lane, 32);
     __syncthreads();
     for (int idx = threadIdx.x; idx < NY * C; idx += blockDim.x) {
         const int y = idx / C, c = idx - y * C, kx = kx0 + c;
-        if (kx < KX) out[base + (long long)y * KX + kx] = cvt2<TOUT>(cscale(buf[c * NY + y], scale));
+        if (kx < KX) out[base + (long long)y * KX + kx] = cvt2<TOUT>(cscale(buf[c * NYP + y], scale));
     }
 }
 
@@ -221,6 +213,29 @@ __global__ void nl_pointwise_kernel(double* __restrict__ u, long long n, int non
     }
 }
 
+__global__ void f64_to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+__global__ void f32_to_f64_kernel(const float* __restrict__ in, double* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+// double -> double-float in place (same 8 bytes per value)
+__global__ void f64_to_dd_kernel(double* __restrict__ a, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const dd v(a[i]);
+        reinterpret_cast<dd*>(a)[i] = v;
+    }
+}
+
+__global__ void f32_to_dd_kernel(const float* __restrict__ in, dd* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = dd(in[i]);
+}
+
 struct CombineArgs {
     const double* in[6];
     double coef[6];
@@ -291,12 +306,16 @@ template <>
 const double2* Wx<double>(expd_plan p) { return p->Wx64; }
 template <>
 const float2* Wx<float>(expd_plan p) { return p->Wx32; }
+template <>
+const dd2* Wx<dd>(expd_plan p) { return static_cast<const dd2*>(p->Wxdd); }
 template <typename PT>
 const typename cplx<PT>::t* Wy(expd_plan p);
 template <>
 const double2* Wy<double>(expd_plan p) { return p->Wy64; }
 template <>
 const float2* Wy<float>(expd_plan p) { return p->Wy32; }
+template <>
+const dd2* Wy<dd>(expd_plan p) { return static_cast<const dd2*>(p->Wydd); }
 
 template <typename PT, typename TIN, typename TOUT, int KIND>
 expd_status launch_row(expd_plan p, const TIN* in, TOUT* out, long long rows, PT scale, cudaStream_t s) {
@@ -313,7 +332,8 @@ expd_status launch_row(expd_plan p, const TIN* in, TOUT* out, long long rows, PT
     const double in_row = (KIND == 1 ? p->NX : NH + 1) * (double)sizeof(TIN);
     const double out_row = (KIND == 0 ? p->NX : NH + 1) * (double)sizeof(TOUT);
     const double fl = (KIND == 2 ? 2.0 : 1.0) * 2.5 * p->NX * ilog2(p->NX) * (double)rows;
-    KProf kp(p, s, EXPD_K_FFT_ROW, (double)rows * (in_row + out_row), fl);
+    KProf kp(p, s, sizeof(PT) == 4 ? EXPD_K_FFT_ROW32 : sizeof(PT) == 8 && !std::is_same<PT, double>::value ? EXPD_K_FFT_ROWDD : EXPD_K_FFT_ROW,
+             (double)rows * (in_row + out_row), fl);
     kern<<<(int)blocks, 32 * R, smem, s>>>(in, out, rows, p->NX, ilog2(NH), Wx<PT>(p), scale, p->nonlin);
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
@@ -323,14 +343,17 @@ template <typename PT, typename TIN, typename TOUT>
 expd_status launch_col(expd_plan p, const TIN* in, TOUT* out, int nslices, int sign, PT scale, cudaStream_t s) {
     typedef typename cplx<PT>::t PT2;
     const int NY = p->NY, KX = p->KX;
-    const size_t per_col = (size_t)NY * sizeof(PT2);
-    int C = (int)std::max<size_t>(1, std::min<size_t>(8, (64 * 1024) / per_col));
+    const size_t per_col = (size_t)(NY + 1) * sizeof(PT2);
+    // 128-byte row segments: 16 float2 or 8 double2 columns per CTA
+    const int cmax = sizeof(TIN) == 8 ? 16 : 8;
+    int C = (int)std::max<size_t>(1, std::min<size_t>(cmax, (64 * 1024) / per_col));
     const size_t smem = (size_t)(((NY >> 1) + 1) & ~1) * sizeof(PT2) + (size_t)C * per_col;
     auto kern = col_kernel<PT, TIN, TOUT>;
     if (smem > 48 * 1024)
         EXPD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((KX + C - 1) / C, nslices);
-    KProf kp(p, s, EXPD_K_FFT_COL, (double)nslices * NY * KX * (sizeof(TIN) + sizeof(TOUT)),
+    KProf kp(p, s, sizeof(PT) == 4 ? EXPD_K_FFT_COL32 : sizeof(PT) == 8 && !std::is_same<PT, double>::value ? EXPD_K_FFT_COLDD : EXPD_K_FFT_COL,
+             (double)nslices * NY * KX * (sizeof(TIN) + sizeof(TOUT)),
              5.0 * NY * ilog2(NY) * (double)KX * nslices);
     kern<<<grid, 32 * C, smem, s>>>(in, out, NY, KX, ilog2(NY), C, Wy<PT>(p), sign, scale);
     EXPD_CUDA_TRY(cudaGetLastError());
@@ -409,8 +432,22 @@ expd_status spatial_inverse64(expd_plan p, const void* eig, double* phys, int ns
     return EXPD_OK;
 }
 
-expd_status nonlinear_eval(expd_plan p, const void* Uh, void* out, int f32, cudaStream_t s) {
+expd_status nonlinear_eval(expd_plan p, const void* Uh, void* out, int f32, cudaStream_t s, int in32) {
     const int Ns = p->Ns;
+    if (in32) {
+        // float32 iterate (periodic grids only): float32 transforms throughout
+        if (p->bc != EXPD_BC_PERIODIC || !f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 N needs a periodic grid");
+        const float2* U = static_cast<const float2*>(Uh);
+        float2* o = static_cast<float2*>(out);
+        const long long rows = (long long)Ns * p->NY;
+        const float sx = 1.0f / (p->NX / 2);
+        if (p->ndim == 1) return launch_row<float, float2, float2, 2>(p, U, o, rows, sx, s);
+        float2* w = static_cast<float2*>(p->work32);
+        expd_status st = launch_col<float, float2, float2>(p, U, w, Ns, +1, 1.0f / p->NY, s);
+        if (st == EXPD_OK) st = launch_row<float, float2, float2, 2>(p, w, w, rows, sx, s);
+        if (st == EXPD_OK) st = launch_col<float, float2, float2>(p, w, o, Ns, -1, 1.0f, s);
+        return st;
+    }
     if (p->bc == EXPD_BC_DIRICHLET) {
         // float64 only: inverse DST, N(u), forward DST
         double* phys = static_cast<double*>(p->work64) + (long long)Ns * p->M;
@@ -442,6 +479,69 @@ expd_status nonlinear_eval(expd_plan p, const void* Uh, void* out, int f32, cuda
     if (st == EXPD_OK) st = launch_row<double, double2, double2, 2>(p, w, w, rows, sx, s);
     if (st == EXPD_OK) st = launch_col<double, double2, double2>(p, w, o, Ns, -1, 1.0, s);
     return st;
+}
+
+expd_status convert_f64_to_f32(expd_plan p, const double* in, float* out, long long n, cudaStream_t s) {
+    KProf kp(p, s, EXPD_K_POINTWISE, 12.0 * n, 0.0);
+    f64_to_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+expd_status convert_f64_to_dd_inplace(expd_plan p, double* a, long long n, cudaStream_t s) {
+    KProf kp(p, s, EXPD_K_POINTWISE, 16.0 * n, 0.0);
+    f64_to_dd_kernel<<<grid_for(n, 256), 256, 0, s>>>(a, n);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+expd_status convert_f32_to_dd(expd_plan p, const float* in, void* out, long long n, cudaStream_t s) {
+    KProf kp(p, s, EXPD_K_POINTWISE, 12.0 * n, 0.0);
+    f32_to_dd_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, static_cast<dd*>(out), n);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+expd_status convert_f32_to_f64(expd_plan p, const float* in, double* out, long long n, cudaStream_t s) {
+    KProf kp(p, s, EXPD_K_POINTWISE, 12.0 * n, 0.0);
+    f32_to_f64_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+expd_status nonlinear_eval_dd(expd_plan p, const void* Uh, void* out, cudaStream_t s) {
+    if (p->bc != EXPD_BC_PERIODIC) return expd_fail(EXPD_ERR_INVALID_ARG, "double-float N needs a periodic grid");
+    const dd2* U = static_cast<const dd2*>(Uh);
+    dd2* o = static_cast<dd2*>(out);
+    const long long rows = (long long)p->Ns * p->NY;
+    const dd sx(1.0 / (p->NX / 2));
+    if (p->ndim == 1) return launch_row<dd, dd2, dd2, 2>(p, U, o, rows, sx, s);
+    dd2* w = static_cast<dd2*>(p->work64);
+    expd_status st = launch_col<dd, dd2, dd2>(p, U, w, p->Ns, +1, dd(1.0 / p->NY), s);
+    if (st == EXPD_OK) st = launch_row<dd, dd2, dd2, 2>(p, w, w, rows, sx, s);
+    if (st == EXPD_OK) st = launch_col<dd, dd2, dd2>(p, w, o, p->Ns, -1, dd(1.0), s);
+    return st;
+}
+
+expd_status spatial_inverse_dd(expd_plan p, const void* eig, double* phys, int nslices, cudaStream_t s) {
+    if (p->bc != EXPD_BC_PERIODIC) return expd_fail(EXPD_ERR_INVALID_ARG, "double-float transforms need a periodic grid");
+    const int chunk = p->Ns;
+    const dd sx(1.0 / (p->NX / 2));
+    for (int b0 = 0; b0 < nslices; b0 += chunk) {
+        const int ns = std::min(chunk, nslices - b0);
+        double* x = phys + (long long)b0 * p->M;
+        const dd2* y = static_cast<const dd2*>(eig) + (long long)b0 * p->Mcol;
+        expd_status st;
+        if (p->ndim == 1) {
+            st = launch_row<dd, dd2, double, 0>(p, y, x, ns, sx, s);
+        } else {
+            dd2* w = static_cast<dd2*>(p->work64);
+            st = launch_col<dd, dd2, dd2>(p, y, w, ns, +1, dd(1.0 / p->NY), s);
+            if (st == EXPD_OK) st = launch_row<dd, dd2, double, 0>(p, w, x, (long long)ns * p->NY, sx, s);
+        }
+        if (st != EXPD_OK) return st;
+    }
+    return EXPD_OK;
 }
 
 expd_status pointwise_solve(expd_plan p, const double* w, double* u, long long n, double bdt, cudaStream_t s) {

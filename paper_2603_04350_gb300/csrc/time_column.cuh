@@ -7,14 +7,15 @@
 // On exit position pos(n) (same rule) holds v_n with
 //     s_n = v_n * scale / alpha^(n/Ns),
 //     s   = Gamma^{-1} F^* diag(1/d) F Gamma q   (F: omega = e^{+2 pi i/Ns})
-// where d_k = 1 - sum_{j=1..order} cj[j] lambda_k^j and cj[j] = a_j E^j.
+// where d_k = 1 - sum_{j=1..order} cj[j] lambda_k^j and cj[j] = a_j E^j
+// (cj[1..6] valid, entries beyond `order` ignored).
 #pragma once
 
 #include "common.cuh"
 
 template <typename PT, typename PT2>
 EXPD_HD double precond_column(PT2* w, int Ns, int L, int log2L, int bluestein, const PT2* tw, const PT2* lam,
-                              const PT2* chirp, const PT2* bp, const PT2* bm, const double* cj, int order,
+                              const PT2* chirp, const PT2* bp, const PT2* bm, const PT* cj, int order,
                               int lane, int nlanes) {
     if (bluestein) {
         for (int n = lane; n < Ns; n += nlanes) w[n] = cmul(w[n], chirp[n]);
@@ -31,13 +32,20 @@ EXPD_HD double precond_column(PT2* w, int Ns, int L, int log2L, int bluestein, c
     } else {
         fft_dit(w, log2L, tw, 1, +1, lane, nlanes);  // natural Y_k
     }
-    // Step (b): Z_k = Y_k / d_k, d_k = 1 - sum_j cj[j] lambda_k^j (Horner)
+    // Step (b): Z_k = Y_k / d_k, d_k = 1 - sum_j cj[j] lambda_k^j (Horner,
+    // unrolled over the at most six coefficients so they stay in registers)
+    PT cp[7];
+#pragma unroll
+    for (int j = 1; j <= 6; ++j) cp[j] = j <= order ? cj[j] : (PT)0;
     for (int k = lane; k < Ns; k += nlanes) {
         const PT2 lk = lam[k];
-        PT2 acc = c2((PT)cj[order], (PT)0);
-        for (int j = order - 1; j >= 1; --j) {
-            acc = cmul(lk, acc);
-            acc.x += (PT)cj[j];
+        PT2 acc = c2((PT)0, (PT)0);
+#pragma unroll
+        for (int j = 6; j >= 1; --j) {
+            if (j <= order) {
+                acc = cmul(lk, acc);
+                acc.x += cp[j];
+            }
         }
         acc = cmul(lk, acc);
         const PT2 d = c2((PT)1 - acc.x, -acc.y);

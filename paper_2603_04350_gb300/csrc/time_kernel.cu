@@ -30,6 +30,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "dd.cuh"
 #include "plan.h"
 #include "time_column.cuh"
 
@@ -45,68 +46,105 @@ struct TimeArgs {
     int precond, accum;
     long long Mcol;
     int Ns, order;
-    double a[7];
-    const double* E;
+    const double* C64;  // [order][Mcol] a_j E_m^j
+    const float* C32;
+    const dd* Cdd;
     int KX, NX, realcol;
-    const double* gamma;
-    const void* lam;
+    const void* gam;  // [Ns] in the storage precision ST
+    const void* osc;  // [Ns] in the storage precision ST
+    const void* lam;  // PT2 tables
     const void* tw;
     const void* chirp;
     const void* bplus;
     const void* bminus;
     int L, log2L, bluestein;
     long long ntiles;
-    double2* partial;
+    double2* partial;  // [Ns][gridDim.x]
 };
 
-template <bool REAL>
-__device__ __forceinline__ double2 ldcol(const void* p, long long i) {
-    if (REAL) return make_double2(static_cast<const double*>(p)[i], 0.0);
-    return static_cast<const double2*>(p)[i];
+// Loads and stores of one time-column element in the storage precision ST.
+template <typename ST, bool REAL>
+__device__ __forceinline__ typename cplx<ST>::t ldcol(const void* p, long long i) {
+    typedef typename cplx<ST>::t ST2;
+    if (REAL) return c2(static_cast<const ST*>(p)[i], (ST)0);
+    return static_cast<const ST2*>(p)[i];
 }
-template <bool REAL>
-__device__ __forceinline__ void stcol(void* p, long long i, double2 v) {
-    if (REAL) static_cast<double*>(p)[i] = v.x;
-    else static_cast<double2*>(p)[i] = v;
+template <typename ST, bool REAL>
+__device__ __forceinline__ void stcol(void* p, long long i, typename cplx<ST>::t v) {
+    typedef typename cplx<ST>::t ST2;
+    if (REAL) static_cast<ST*>(p)[i] = v.x;
+    else static_cast<ST2*>(p)[i] = v;
 }
-template <bool REAL>
-__device__ __forceinline__ double2 ldnl(const void* p, long long i, int f32) {
-    if (REAL) {
-        return make_double2(f32 ? (double)static_cast<const float*>(p)[i] : static_cast<const double*>(p)[i], 0.0);
+template <typename ST, bool REAL>
+__device__ __forceinline__ typename cplx<ST>::t ldnl(const void* p, long long i, int f32) {
+    typedef typename cplx<ST>::t ST2;
+    if (std::is_same<ST, dd>::value) return ldcol<ST, REAL>(p, i);  // double-float N
+    if (REAL) return c2(f32 ? (ST) static_cast<const float*>(p)[i] : (ST) static_cast<const double*>(p)[i], (ST)0);
+    if (f32) {
+        const float2 v = static_cast<const float2*>(p)[i];
+        return c2((ST)v.x, (ST)v.y);
     }
-    return f32 ? to_c64(static_cast<const float2*>(p)[i]) : static_cast<const double2*>(p)[i];
+    const double2 v = static_cast<const double2*>(p)[i];
+    return c2((ST)v.x, (ST)v.y);
 }
 
-__device__ __forceinline__ double mode_weight(long long m, int KX, int NX, int realcol) {
-    if (realcol) return 1.0;
+
+template <typename T>
+__device__ __forceinline__ T coef(const TimeArgs& A, int j, long long m);
+template <>
+__device__ __forceinline__ double coef<double>(const TimeArgs& A, int j, long long m) {
+    return A.C64[(long long)(j - 1) * A.Mcol + m];
+}
+template <>
+__device__ __forceinline__ float coef<float>(const TimeArgs& A, int j, long long m) {
+    return A.C32[(long long)(j - 1) * A.Mcol + m];
+}
+template <>
+__device__ __forceinline__ dd coef<dd>(const TimeArgs& A, int j, long long m) {
+    return A.Cdd[(long long)(j - 1) * A.Mcol + m];
+}
+
+template <typename ST>
+__device__ __forceinline__ ST mode_weight(long long m, int KX, int NX, int realcol) {
+    if (realcol) return (ST)1;
     const int kx = (int)(m % KX);
-    return (kx == 0 || 2 * kx == NX) ? 1.0 : 2.0;
+    return (kx == 0 || 2 * kx == NX) ? (ST)1 : (ST)2;
 }
 
-template <typename PT, bool REAL>
-__global__ void __launch_bounds__(32 * EXPD_TIME_COLS) time_kernel(TimeArgs A) {
+// PT: precision of steps (a)-(c); ST: precision of the stored state, the
+// right-hand side and the residual arithmetic (float32 sweeps never touch the
+// float64 pipe, whose rate on GB300 is 1/64 of float32).
+template <typename PT, typename ST, bool REAL>
+__global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A) {
     typedef typename cplx<PT>::t PT2;
+    typedef typename cplx<ST>::t ST2;
     constexpr int C = EXPD_TIME_COLS;
     const int Ns = A.Ns, L = A.L;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // ---- shared-memory carve-up (all offsets 16-byte aligned) ----
-    double2* sX = reinterpret_cast<double2*>(smem_raw);        // [Ns][C]
-    double2* sR = sX + (size_t)Ns * C;                          // [Ns][C]
-    double2* sAcc = sR + (size_t)Ns * C;                        // [Ns]
-    PT2* sW = reinterpret_cast<PT2*>(sAcc + Ns);                // [C][L]
-    PT2* tw = sW + (size_t)C * L;                               // [L/2]
-    PT2* lam = tw + (L >> 1);                                   // [Ns]
-    PT2* chirp = lam + ((Ns + 1) & ~1);                         // [Ns]   (Bluestein)
-    PT2* bp = chirp + (A.bluestein ? ((Ns + 1) & ~1) : 0);      // [L]
-    PT2* bm = bp + (A.bluestein ? L : 0);                       // [L]
-    double* gam = reinterpret_cast<double*>(bm + (A.bluestein ? L : 0));  // [Ns]
+    // ---- shared-memory carve-up (C even keeps every region 16-byte aligned) ----
+    // tiles are column-major with a padded column stride P = Ns + 1, so the
+    // per-column phase (a warp walking one column) is free of bank conflicts
+    const int P = Ns + 1;
+    ST2* sAcc = reinterpret_cast<ST2*>(smem_raw);             // [Ns + 1]
+    ST2* sX = sAcc + (Ns + 1);                                 // [C][P]
+    ST2* sR = sX + (size_t)P * C;                              // [C][P]
+    ST* sWgt = reinterpret_cast<ST*>(sR + (size_t)P * C);     // [C] norm weight of each column
+    PT2* sW = reinterpret_cast<PT2*>(sWgt + 2 * C);           // [C][L]
+    PT2* tw = sW + (size_t)C * L;                              // [L/2]
+    PT2* lam = tw + ((L >> 1) + 1);                            // [Ns]
+    PT2* chirp = lam + (Ns + 1);                               // [Ns]   (Bluestein)
+    PT2* bp = chirp + (A.bluestein ? Ns + 1 : 0);              // [L]
+    PT2* bm = bp + (A.bluestein ? L : 0);                      // [L]
+    ST* gam = reinterpret_cast<ST*>(bm + (A.bluestein ? L : 0));  // [Ns]
+    ST* osc = gam + Ns;                                        // [Ns]
 
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int i = tid; i < (L >> 1); i += nth) tw[i] = static_cast<const PT2*>(A.tw)[i];
     for (int i = tid; i < Ns; i += nth) {
         lam[i] = static_cast<const PT2*>(A.lam)[i];
-        gam[i] = A.gamma[i];
-        sAcc[i] = make_double2(0.0, 0.0);
+        gam[i] = static_cast<const ST*>(A.gam)[i];
+        osc[i] = static_cast<const ST*>(A.osc)[i];
+        sAcc[i] = c2((ST)0, (ST)0);
         if (A.bluestein) chirp[i] = static_cast<const PT2*>(A.chirp)[i];
     }
     if (A.bluestein)
@@ -118,168 +156,197 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS) time_kernel(TimeArgs A) {
 
     const int lane = tid & 31, warp = tid >> 5;
     const long long Mcol = A.Mcol;
+    const ST bdt = (ST)A.bdt, sigR = (ST)A.sigR;
     for (long long tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
         const long long m0 = tile * C;
         // ---- coalesced load of the tile: X and the additive right-hand side ----
         for (int idx = tid; idx < Ns * C; idx += nth) {
             const int n = idx / C, c = idx - n * C;
             const long long m = m0 + c;
-            double2 x = make_double2(0.0, 0.0), r = make_double2(0.0, 0.0);
+            ST2 x = c2((ST)0, (ST)0), r = c2((ST)0, (ST)0);
             if (m < Mcol) {
                 const long long g = (long long)n * Mcol + m;
-                if (A.X) x = ldcol<REAL>(A.X, g);
-                if (A.F) r = ldcol<REAL>(A.F, g);
+                if (A.X) x = ldcol<ST, REAL>(A.X, g);
+                if (A.F) r = ldcol<ST, REAL>(A.F, g);
                 if (A.NL) {
-                    const double2 v = ldnl<REAL>(A.NL, g, A.nl_f32);
-                    r.x = fma(A.bdt, v.x, r.x);
-                    r.y = fma(A.bdt, v.y, r.y);
+                    const ST2 v = ldnl<ST, REAL>(A.NL, g, A.nl_f32);
+                    r.x = fma(bdt, v.x, r.x);
+                    r.y = fma(bdt, v.y, r.y);
                 }
             }
-            sX[idx] = x;
-            sR[idx] = r;
+            sX[c * P + n] = x;
+            sR[c * P + n] = r;
+        }
+        if (tid < C) {
+            const long long m = m0 + tid;
+            sWgt[tid] = m < Mcol ? mode_weight<ST>(m, A.KX, A.NX, A.realcol) : (ST)0;
         }
         __syncthreads();
 
         // ---- one warp per column ----
         const long long m = m0 + warp;
         if (warp < C && m < Mcol) {
-            const double Em = A.E[m];
-            double cj[7];
-            {
-                double Ej = 1.0;
-                for (int j = 1; j <= A.order; ++j) {
-                    Ej *= Em;
-                    cj[j] = A.a[j] * Ej;
-                }
+            // a_j E_m^j from the plan's tables (no float64 arithmetic here)
+            ST cs[7];
+            PT cp[7];
+            cs[0] = (ST)0;
+            cp[0] = (PT)0;
+#pragma unroll
+            for (int j = 1; j <= 6; ++j) {
+                cs[j] = j <= A.order ? coef<ST>(A, j, m) : (ST)0;
+                cp[j] = j <= A.order ? coef<PT>(A, j, m) : (PT)0;
             }
             PT2* w = sW + (size_t)warp * L;
-            // residual-type combination q_n (float64), then Gamma_alpha
+            const ST2* xc = sX + (size_t)warp * P;
+            ST2* rc = sR + (size_t)warp * P;
+            // residual-type combination q_n in ST, then Gamma_alpha
             for (int n = lane; n < Ns; n += 32) {
-                double2 q = sR[n * C + warp];
+                ST2 q = rc[n];
                 if (A.X) {
-                    double2 rx = sX[n * C + warp];
-                    for (int j = 1; j <= A.order && j <= n; ++j) {
-                        const double2 xv = sX[(n - j) * C + warp];
-                        rx.x = fma(-cj[j], xv.x, rx.x);
-                        rx.y = fma(-cj[j], xv.y, rx.y);
+                    ST2 rx = xc[n];
+#pragma unroll
+                    for (int j = 1; j <= 6; ++j) {
+                        if (j <= A.order && j <= n) {
+                            const ST2 xv = xc[n - j];
+                            rx.x = fma(-cs[j], xv.x, rx.x);
+                            rx.y = fma(-cs[j], xv.y, rx.y);
+                        }
                     }
-                    q.x = fma(A.sigR, rx.x, q.x);
-                    q.y = fma(A.sigR, rx.y, q.y);
+                    q.x = fma(sigR, rx.x, q.x);
+                    q.y = fma(sigR, rx.y, q.y);
                 }
                 if (!A.precond) {
-                    sR[n * C + warp] = q;
+                    rc[n] = q;
                 } else {
-                    const PT2 y = from_c64<PT2>(cscale(q, gam[n]));
-                    w[A.bluestein ? n : (int)bitrev(n, A.log2L)] = y;
+                    w[A.bluestein ? n : (int)bitrev(n, A.log2L)] = cvt2<PT2>(cscale(q, gam[n]));
                 }
             }
             if (A.precond) {
                 EXPD_SYNCWARP();
-                const double scale_all = precond_column<PT, PT2>(w, Ns, L, A.log2L, A.bluestein, tw, lam, chirp,
-                                                                 bp, bm, cj, A.order, lane, 32);
+                precond_column<PT, PT2>(w, Ns, L, A.log2L, A.bluestein, tw, lam, chirp, bp, bm, cp, A.order, lane, 32);
                 for (int n = lane; n < Ns; n += 32) {
-                    const double2 v = to_c64(w[A.bluestein ? n : (int)bitrev(n, A.log2L)]);
-                    sR[n * C + warp] = cscale(v, scale_all / gam[n]);
+                    const ST2 v = cvt2<ST2>(w[A.bluestein ? n : (int)bitrev(n, A.log2L)]);
+                    rc[n] = cscale(v, osc[n]);
                 }
             }
         }
         __syncthreads();
 
-        // ---- coalesced write-back and per-slice norms ----
+        // ---- coalesced write-back; per-element norm terms into sX ----
         for (int idx = tid; idx < Ns * C; idx += nth) {
             const int n = idx / C, c = idx - n * C;
             const long long mm = m0 + c;
-            double2 nrm = make_double2(0.0, 0.0);
+            ST2 nrm = c2((ST)0, (ST)0);
             if (mm < Mcol) {
                 const long long g = (long long)n * Mcol + mm;
-                const double2 res = sR[idx];
-                const double wgt = mode_weight(mm, A.KX, A.NX, A.realcol);
-                nrm.x = wgt * (res.x * res.x + res.y * res.y);
+                const ST2 res = sR[c * P + n];
+                const ST wgt = sWgt[c];
+                nrm.x = wgt * fma(res.x, res.x, res.y * res.y);
                 if (A.accum) {
-                    const double2 xn = cadd(sX[idx], res);
-                    stcol<REAL>(const_cast<void*>(A.X), g, xn);
-                    nrm.y = wgt * (xn.x * xn.x + xn.y * xn.y);
+                    const ST2 xn = cadd(sX[c * P + n], res);
+                    stcol<ST, REAL>(const_cast<void*>(A.X), g, xn);
+                    nrm.y = wgt * fma(xn.x, xn.x, xn.y * xn.y);
                 } else {
-                    stcol<REAL>(A.out, g, res);
+                    stcol<ST, REAL>(A.out, g, res);
                 }
             }
-            sX[idx] = nrm;
+            sX[c * P + n] = nrm;
         }
         __syncthreads();
         for (int n = tid; n < Ns; n += nth) {
-            double2 acc = sAcc[n];
+            ST a = (ST)0, b = (ST)0;
             for (int c = 0; c < C; ++c) {
-                acc.x += sX[n * C + c].x;
-                acc.y += sX[n * C + c].y;
+                a += sX[c * P + n].x;
+                b += sX[c * P + n].y;
             }
-            sAcc[n] = acc;
+            sAcc[n].x += a;
+            sAcc[n].y += b;
         }
         __syncthreads();
     }
-    for (int n = tid; n < Ns; n += nth) A.partial[(size_t)blockIdx.x * Ns + n] = sAcc[n];
+    for (int n = tid; n < Ns; n += nth)
+        A.partial[(size_t)n * gridDim.x + blockIdx.x] = make_double2((double)sAcc[n].x, (double)sAcc[n].y);
 }
 
 // max that propagates NaN (fmax would drop it and hide a diverged iterate)
 __device__ __forceinline__ double nanmax(double a, double b) { return (a != a || b != b) ? NAN : fmax(a, b); }
 
-// Per-slice totals over the CTAs (fixed order), then max/sum over slices.
-__global__ void reduce_kernel(const double2* __restrict__ partial, int grid, int Ns, double* __restrict__ out) {
-    __shared__ double smax[2][32], ssum[2][32];
-    double mx0 = 0, mx1 = 0, sm0 = 0, sm1 = 0;
-    for (int n = threadIdx.x; n < Ns; n += blockDim.x) {
-        double a = 0, b = 0;
-        for (int g = 0; g < grid; ++g) {
-            const double2 v = partial[(size_t)g * Ns + n];
-            a += v.x;
-            b += v.y;
-        }
-        mx0 = nanmax(mx0, a);
-        mx1 = nanmax(mx1, b);
-        sm0 += a;
-        sm1 += b;
+// Per-slice totals over the time kernel's CTAs: block n sums slice n's
+// partials (fixed order), then the last block to finish takes the max and the
+// sum over slices in slice order.  The atomic counter only elects that block;
+// every sum has a fixed order, so the result is deterministic.
+__global__ void __launch_bounds__(256) reduce_kernel(const double2* __restrict__ partial, int grid, int Ns,
+                                                     double2* __restrict__ slice_tot, unsigned* __restrict__ counter,
+                                                     double* __restrict__ out) {
+    __shared__ double2 red[8];
+    __shared__ bool last;
+    const int n = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double a = 0, b = 0;
+    for (int g = threadIdx.x; g < grid; g += blockDim.x) {
+        const double2 v = partial[(size_t)n * grid + g];
+        a += v.x;
+        b += v.y;
     }
     for (int o = 16; o > 0; o >>= 1) {
-        mx0 = nanmax(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
-        mx1 = nanmax(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
-        sm0 += __shfl_xor_sync(0xffffffffu, sm0, o);
-        sm1 += __shfl_xor_sync(0xffffffffu, sm1, o);
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        smax[0][warp] = mx0;
-        smax[1][warp] = mx1;
-        ssum[0][warp] = sm0;
-        ssum[1][warp] = sm1;
-    }
+    if (lane == 0) red[warp] = make_double2(a, b);
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0, b = 0, c = 0, d = 0;
+        double2 t = make_double2(0.0, 0.0);
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            a = nanmax(a, smax[0][w]);
-            b = nanmax(b, smax[1][w]);
-            c += ssum[0][w];
-            d += ssum[1][w];
+            t.x += red[w].x;
+            t.y += red[w].y;
         }
-        out[0] = sqrt(a);
-        out[1] = sqrt(b);
-        out[2] = c;
-        out[3] = d;
+        slice_tot[n] = t;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == (unsigned)(Ns - 1));
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double mx0 = 0, mx1 = 0, sm0 = 0, sm1 = 0;
+    if (warp == 0) {
+        for (int k = lane; k < Ns; k += 32) {
+            const double2 t = __ldcg(&slice_tot[k]);
+            mx0 = nanmax(mx0, t.x);
+            mx1 = nanmax(mx1, t.y);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            mx0 = nanmax(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
+            mx1 = nanmax(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
+        }
+        if (lane == 0) {
+            for (int k = 0; k < Ns; ++k) {
+                const double2 t = __ldcg(&slice_tot[k]);
+                sm0 += t.x;
+                sm1 += t.y;
+            }
+            out[0] = sqrt(mx0);
+            out[1] = sqrt(mx1);
+            out[2] = sm0;
+            out[3] = sm1;
+            *counter = 0u;
+        }
     }
 }
 
-size_t time_smem_bytes(int Ns, int L, int bluestein, size_t pt2) {
+size_t time_smem_bytes(int Ns, int L, int bluestein, size_t pt2, size_t st) {
     const int C = EXPD_TIME_COLS;
-    size_t b = (size_t)(2 * Ns * C + Ns) * sizeof(double2);
-    b += (size_t)C * L * pt2 + (size_t)(L / 2) * pt2 + (size_t)((Ns + 1) & ~1) * pt2;
-    if (bluestein) b += (size_t)((Ns + 1) & ~1) * pt2 + 2 * (size_t)L * pt2;
-    b += (size_t)Ns * sizeof(double);
+    size_t b = (size_t)(Ns + 1) * 2 * st + 2 * (size_t)(Ns + 1) * C * 2 * st + 2 * (size_t)C * st;
+    b += (size_t)C * L * pt2 + (size_t)((L >> 1) + 1) * pt2 + (size_t)(Ns + 1) * pt2;
+    if (bluestein) b += (size_t)(Ns + 1) * pt2 + 2 * (size_t)L * pt2;
+    b += 2 * (size_t)Ns * st;
     return b;
 }
 
-template <typename PT, bool REAL>
+template <typename PT, typename ST, bool REAL>
 expd_status launch_time(expd_plan p, TimeArgs& a, cudaStream_t s) {
     const TimeTables& t = std::is_same<PT, float>::value ? p->t32 : p->t64;
-    a.gamma = t.gamma;
+    const TimeTables& ts = std::is_same<ST, float>::value ? p->t32 : p->t64;
+    a.gam = std::is_same<ST, dd>::value ? p->gamdd : ts.gam;
+    a.osc = std::is_same<ST, dd>::value ? p->oscdd : ts.osc;
     a.lam = t.lam;
     a.tw = t.tw;
     a.chirp = t.chirp;
@@ -288,15 +355,17 @@ expd_status launch_time(expd_plan p, TimeArgs& a, cudaStream_t s) {
     a.L = t.L;
     a.log2L = t.log2L;
     a.bluestein = t.bluestein;
-    const size_t smem = time_smem_bytes(p->Ns, t.L, t.bluestein, sizeof(typename cplx<PT>::t));
-    auto kern = time_kernel<PT, REAL>;
+    const size_t smem = time_smem_bytes(p->Ns, t.L, t.bluestein, sizeof(typename cplx<PT>::t), sizeof(ST));
+    auto kern = time_kernel<PT, ST, REAL>;
     EXPD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const double esz = REAL ? 8.0 : 16.0;
-    const double per = (a.X ? esz : 0.0) + (a.F ? esz : 0.0) + (a.NL ? (a.nl_f32 ? esz / 2 : esz) : 0.0) + esz;
+    const double esz = (REAL ? 1.0 : 2.0) * sizeof(ST);
+    const double nlsz = (REAL ? 1.0 : 2.0) * (a.nl_f32 ? 4.0 : 8.0);
+    const double per = (a.X ? esz : 0.0) + (a.F ? esz : 0.0) + (a.NL ? nlsz : 0.0) + esz;
     const double lg = (double)t.log2L;
     const double fl_col = (a.precond ? (t.bluestein ? 4.0 : 2.0) * 5.0 * t.L * lg + 8.0 * p->order * p->Ns : 0.0) +
                           4.0 * p->order * p->Ns;
-    KProf kp(p, s, EXPD_K_TIME, per * p->Ns * (double)p->Mcol, fl_col * (double)p->Mcol);
+    const int cls = sizeof(ST) == 4 ? EXPD_K_TIME32 : std::is_same<ST, dd>::value ? EXPD_K_TIMEDD : EXPD_K_TIME;
+    KProf kp(p, s, cls, per * p->Ns * (double)p->Mcol, fl_col * (double)p->Mcol);
     kern<<<p->time_grid, 32 * EXPD_TIME_COLS, smem, s>>>(a);
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
@@ -335,12 +404,23 @@ expd_status build_tables(expd_plan p, TimeTables& t, cudaStream_t s) {
     if (st == EXPD_OK && t.bluestein) t.bplus = upload<T2, T>(h.bplus, s, p->bytes, st);
     if (st == EXPD_OK && t.bluestein) t.bminus = upload<T2, T>(h.bminus, s, p->bytes, st);
     if (st != EXPD_OK) return st;
-    cudaError_t e = cudaMalloc(&t.gamma, h.gamma.size() * sizeof(double));
-    if (e != cudaSuccess) return expd_cuda_fail(e, "cudaMalloc(gamma)", __FILE__, __LINE__);
-    p->bytes += h.gamma.size() * sizeof(double);
-    e = cudaMemcpyAsync(t.gamma, h.gamma.data(), h.gamma.size() * sizeof(double), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return expd_cuda_fail(e, "cudaMemcpyAsync(gamma)", __FILE__, __LINE__);
+    // Gamma_alpha and the output scale in this table's precision
+    std::vector<T> g(h.gamma.size()), o(h.gamma.size());
+    const double extra = h.bluestein ? 1.0 / ((double)h.L * (double)h.L) : 1.0;
+    for (size_t n = 0; n < g.size(); ++n) {
+        g[n] = (T)h.gamma[n];
+        o[n] = (T)(extra / ((double)p->Ns * h.gamma[n]));
+    }
+    for (int k = 0; k < 2; ++k) {
+        void** dst = k == 0 ? &t.gam : &t.osc;
+        const std::vector<T>& src = k == 0 ? g : o;
+        cudaError_t e = cudaMalloc(dst, src.size() * sizeof(T));
+        if (e != cudaSuccess) return expd_cuda_fail(e, "cudaMalloc(gamma)", __FILE__, __LINE__);
+        p->bytes += src.size() * sizeof(T);
+        e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return expd_cuda_fail(e, "cudaMemcpyAsync(gamma)", __FILE__, __LINE__);
+    }
     return EXPD_OK;
 }
 
@@ -372,9 +452,11 @@ expd_status time_grid_for(expd_plan p, int* grid_out) {
         while (L < 2 * p->Ns - 1) L <<= 1;
     }
     int per_sm = 1;
-    const size_t smem = time_smem_bytes(p->Ns, L, blue, sizeof(double2));
-    auto kern = p->realcol ? time_kernel<double, true> : time_kernel<double, false>;
-    if (smem > 227 * 1024) return expd_fail(EXPD_ERR_UNSUPPORTED, "time window too long for shared memory");
+    const size_t smem64 = time_smem_bytes(p->Ns, L, blue, sizeof(double2), sizeof(double));
+    if (smem64 > 227 * 1024) return expd_fail(EXPD_ERR_UNSUPPORTED, "time window too long for shared memory");
+    // the float32-sweep variant (the most frequent launch) sets the grid
+    const size_t smem = time_smem_bytes(p->Ns, L, blue, sizeof(float2), sizeof(float));
+    auto kern = p->realcol ? time_kernel<float, float, true> : time_kernel<float, float, false>;
     EXPD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     EXPD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * EXPD_TIME_COLS, smem));
     if (per_sm < 1) per_sm = 1;
@@ -387,7 +469,8 @@ expd_status time_grid_for(expd_plan p, int* grid_out) {
 void time_tables_free(expd_plan p) {
     TimeTables* ts[2] = {&p->t64, &p->t32};
     for (TimeTables* t : ts) {
-        cudaFree(t->gamma);
+        cudaFree(t->gam);
+        cudaFree(t->osc);
         cudaFree(t->lam);
         cudaFree(t->tw);
         cudaFree(t->chirp);
@@ -411,20 +494,32 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s) {
     a.Mcol = p->Mcol;
     a.Ns = p->Ns;
     a.order = p->order;
-    for (int j = 0; j < 7; ++j) a.a[j] = p->acoef[p->order][j];
-    a.E = p->E;
+    a.C64 = p->C64;
+    a.C32 = p->C32;
+    a.Cdd = static_cast<const dd*>(p->Cdd);
     a.KX = p->KX;
     a.NX = p->NX;
     a.realcol = p->realcol;
     a.ntiles = (p->Mcol + EXPD_TIME_COLS - 1) / EXPD_TIME_COLS;
     a.partial = p->partial;
-    if (op.f32) return p->realcol ? launch_time<float, true>(p, a, s) : launch_time<float, false>(p, a, s);
-    return p->realcol ? launch_time<double, true>(p, a, s) : launch_time<double, false>(p, a, s);
+    if (op.stdd) {
+        if (!op.f32) return expd_fail(EXPD_ERR_INVALID_ARG, "double-float storage needs the float32 preconditioner");
+        return p->realcol ? launch_time<float, dd, true>(p, a, s) : launch_time<float, dd, false>(p, a, s);
+    }
+    if (op.st32) {
+        if (!op.f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 storage needs the float32 preconditioner");
+        if (op.NL && !op.nl_f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 storage needs float32 N");
+        return p->realcol ? launch_time<float, float, true>(p, a, s) : launch_time<float, float, false>(p, a, s);
+    }
+    if (op.f32) return p->realcol ? launch_time<float, double, true>(p, a, s) : launch_time<float, double, false>(p, a, s);
+    return p->realcol ? launch_time<double, double, true>(p, a, s) : launch_time<double, double, false>(p, a, s);
 }
 
 expd_status time_reduce(expd_plan p, cudaStream_t s) {
     KProf kp(p, s, EXPD_K_REDUCE, 16.0 * p->time_grid * p->Ns, 2.0 * p->time_grid * p->Ns);
-    reduce_kernel<<<1, 256, 0, s>>>(p->partial, p->time_grid, p->Ns, p->redout);
+    double2* slice_tot = reinterpret_cast<double2*>(p->redout + 8);
+    unsigned* counter = reinterpret_cast<unsigned*>(p->redout + 6);
+    reduce_kernel<<<p->Ns, 256, 0, s>>>(p->partial, p->time_grid, p->Ns, slice_tot, counter, p->redout);
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }

@@ -24,13 +24,15 @@ PREC_FP64, PREC_MIXED = 0, 1
 STARTUP_RAMP, STARTUP_GIVEN = 0, 1
 MAX_HISTORY = 128
 
-SYMBOLS = ("expd_plan_create", "expd_plan_workspace_bytes", "expd_residual", "expd_precond_apply",
+SYMBOLS = ("expd_plan_create", "expd_plan_workspace_bytes", "expd_plan_footprint_bytes", "expd_residual", "expd_precond_apply",
            "expd_solve_fp", "expd_solve_gmres", "expd_timing_enable", "expd_timing_read", "expd_destroy",
            "expd_precond_apply_noalloc",
            "expd_status_string", "expd_last_error", "expd_version")
-K_TIME, K_FFT_COL, K_FFT_ROW, K_DST, K_GMRES, K_POINTWISE, K_REDUCE = range(7)
-NUM_KCLASS = 7
-KCLASS_NAMES = ("time", "fft_col", "fft_row", "dst", "gmres", "pointwise", "reduce")
+(K_TIME, K_FFT_COL, K_FFT_ROW, K_DST, K_GMRES, K_POINTWISE, K_REDUCE, K_TIME32, K_FFT_COL32, K_FFT_ROW32,
+ K_TIMEDD, K_FFT_COLDD, K_FFT_ROWDD) = range(13)
+NUM_KCLASS = 13
+KCLASS_NAMES = ("time", "fft_col", "fft_row", "dst", "gmres", "pointwise", "reduce", "time32", "fft_col32",
+                "fft_row32", "timedd", "fft_coldd", "fft_rowdd")
 
 
 class Grid(C.Structure):
@@ -88,6 +90,8 @@ def lib() -> C.CDLL:
     L.expd_plan_create.argtypes = [C.POINTER(Grid), C.POINTER(Operator), C.c_double, C.c_int, C.c_double,
                                    C.POINTER(Scheme), vp, C.POINTER(vp)]
     L.expd_plan_workspace_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+    L.expd_plan_footprint_bytes.argtypes = [C.POINTER(Grid), C.POINTER(Operator), C.c_double, C.c_int, C.c_double,
+                                            C.POINTER(Scheme), C.c_int, C.POINTER(C.c_size_t)]
     L.expd_residual.argtypes = [vp, dp, dp, dp, dp, vp]
     L.expd_precond_apply.argtypes = [vp, dp, dp, vp]
     L.expd_solve_fp.argtypes = [vp, dp, dp, dp, C.POINTER(Info), vp]
@@ -173,6 +177,19 @@ def _structs(spec: PlanSpec):
     o = Operator(spec.a, spec.c, spec.nonlin)
     s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup)
     return g, o, s
+
+
+FOOTPRINT_SOURCE, FOOTPRINT_HOST, FOOTPRINT_GMRES = 1, 2, 4
+
+
+def plan_footprint_bytes(spec: PlanSpec, flags: int = 0) -> int:
+    """Device bytes plan_create(spec) would allocate (plus lazily allocated
+    buffers selected by flags), computed without allocating."""
+    g, o, s = _structs(spec)
+    b = C.c_size_t()
+    _check(lib().expd_plan_footprint_bytes(C.byref(g), C.byref(o), spec.dt, spec.Nt, spec.alpha, C.byref(s),
+                                           int(flags), C.byref(b)))
+    return b.value
 
 
 def precond_apply_noalloc(spec: PlanSpec, R, S, stream=None) -> None:
