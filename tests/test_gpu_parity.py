@@ -278,3 +278,21 @@ def test_heat_dirichlet_1024_full_gmres(expd):
     u0, f, U, info = solve_full(expd, p, expd.PREC_FP64)
     ref = O.sequential_solve(O.spec_of(p), u0, f)[1:]
     assert O.rel_error(U, ref) < p.tol, info
+
+
+def test_footprint_matches_allocation(expd):
+    # expd_plan_footprint_bytes predicts exactly what a plan allocates (admission control)
+    cases = [(CASES[0], expd.PREC_FP64, 0), (CASES[3], expd.PREC_MIXED, 0), (CASES[6], expd.PREC_MIXED, 0),
+             (CASES[9], expd.PREC_MIXED, 0), (CASES[10], expd.PREC_FP64, 0)]
+    for p, prec, _ in cases:
+        spec = expd.spec_from_problem(p, precision=prec)
+        want = expd.plan_footprint_bytes(spec)
+        with expd.plan_create(spec) as plan:
+            assert plan.workspace_bytes() == want, p.name
+            if p.nonlin == "none":
+                u0 = np.zeros(p.n)
+                f = np.zeros((p.Nt,) + p.n)
+                U = np.zeros((p.Nt,) + p.n)
+                plan.solve_gmres(u0, f, U)          # host pointers, a source, GMRES
+                flags = expd.FOOTPRINT_SOURCE | expd.FOOTPRINT_HOST | expd.FOOTPRINT_GMRES
+                assert plan.workspace_bytes() == expd.plan_footprint_bytes(spec, flags), p.name
