@@ -12,6 +12,7 @@
 //   4. the unknown slices return to physical space.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -377,6 +378,10 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (ce != cudaSuccess) return expd_cuda_fail(ce, "cudaGetDevice/cudaDeviceGetAttribute", __FILE__, __LINE__);
+    // EXPD_TIME_KERNEL=smem selects the shared-memory time kernel for every window
+    // (both kernels compute the same sweep; this lets them be compared)
+    const char* tk = getenv("EXPD_TIME_KERNEL");
+    p->no_reg_time = tk && strcmp(tk, "smem") == 0;
     return EXPD_OK;
 }
 
@@ -615,7 +620,7 @@ expd_status expd_plan_footprint_bytes(const expd_grid* grid, const expd_operator
     int grid_t = 0;
     st = time_grid_for(p, &grid_t);
     if (st != EXPD_OK) return st;
-    b += (size_t)grid_t * Ns * 16;                                          // norm partials
+    b += (size_t)std::max(grid_t, p->sm_count * 8) * Ns * 16;              // norm partials
     if (flags & EXPD_FOOTPRINT_SOURCE) b += (size_t)p->Nt * Mcol * p->esz;
     if (flags & EXPD_FOOTPRINT_HOST) b += (size_t)(2 * p->Nt + 1) * p->M * 8;
     if (flags & EXPD_FOOTPRINT_GMRES) {

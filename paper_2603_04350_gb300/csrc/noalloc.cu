@@ -261,6 +261,7 @@ extern "C" expd_status expd_precond_apply_noalloc(const expd_grid* grid, const e
         }
     }
     p->time_grid = tgrid;
+    p->partial_cap = tgrid;
 
     // ---- tables, then the three steps around the spatial transforms ----
     {

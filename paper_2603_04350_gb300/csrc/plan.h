@@ -90,6 +90,9 @@ struct expd_plan_s {
     double* redout = nullptr;     // [4] reduced norms (device)
     double* redhost = nullptr;    // [4] pinned host copy
     int time_grid = 0;            // CTAs of the time kernel (multiple of SM count)
+    int partial_cap = 0;          // CTAs the partial-norm buffer has room for
+    int time_grid_used = 0;       // CTAs of the last time-kernel launch (for the reduction)
+    int no_reg_time = 0;          // 1 forces the shared-memory time kernel (tests)
     // host-pointer staging (lazy)
     double* stage = nullptr;      // [(2*Nt + 1) * M]
     size_t stage_elems = 0;

@@ -268,6 +268,359 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
         A.partial[(size_t)n * gridDim.x + blockIdx.x] = make_double2((double)sAcc[n].x, (double)sAcc[n].y);
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident variant for power-of-two windows NS in {16, 32, 64} with the
+// float32 preconditioner.  A group of G consecutive lanes owns one spatial
+// mode's time column; lane g of the group holds slices n = G j + g, j < R = NS/G,
+// in registers.  Loads and stores are coalesced across the groups of a warp
+// (consecutive modes), and the length-NS transforms factor as NS = G x R:
+//   forward  Y[k1 + R k2] = sum_g w^(g k2)_G  w^(g k1)_NS  sum_j w^(j k1)_R y[G j + g]
+// (R-point FFT in registers, twiddle, G-point FFT across the lanes by
+// shuffles), and the inverse runs the same factors backwards.  The residual's
+// sliding window of the previous `order` iterates comes from the neighbouring
+// lanes by shuffles.  Per-slice norms are reduced over the warp's groups with a
+// transpose-reduce and over the CTA in shared memory.
+constexpr int REG_THREADS = 128;
+constexpr int REG_G = 4;
+
+constexpr int ilog2_ct(int n) { return n <= 1 ? 0 : 1 + ilog2_ct(n >> 1); }
+
+// R-point FFTs on a register array (compile-time indices).  tw[k * TS] =
+// exp(-2 pi i k / R) for k < R/2.  DIT: bit-reversed in -> natural out.
+template <int R, int TS, int SIGN>
+__device__ __forceinline__ void reg_fft_dit(float2 (&v)[R], const float2* tw) {
+#pragma unroll
+    for (int st = 0; st < ilog2_ct(R); ++st) {
+        const int h = 1 << st;
+#pragma unroll
+        for (int b = 0; b < R / 2; ++b) {
+            const int k = b & (h - 1);
+            const int i = ((b >> st) << (st + 1)) + k;
+            float2 t = v[i + h];
+            if (k != 0) {
+                float2 w = tw[k * (R / (2 * h)) * TS];
+                if (SIGN > 0) w.y = -w.y;
+                t = cmul(t, w);
+            }
+            v[i + h] = csub(v[i], t);
+            v[i] = cadd(v[i], t);
+        }
+    }
+}
+
+// DIF: natural in -> bit-reversed out
+template <int R, int TS, int SIGN>
+__device__ __forceinline__ void reg_fft_dif(float2 (&v)[R], const float2* tw) {
+#pragma unroll
+    for (int st = ilog2_ct(R) - 1; st >= 0; --st) {
+        const int h = 1 << st;
+#pragma unroll
+        for (int b = 0; b < R / 2; ++b) {
+            const int k = b & (h - 1);
+            const int i = ((b >> st) << (st + 1)) + k;
+            const float2 u = v[i], t = v[i + h];
+            v[i] = cadd(u, t);
+            float2 d = csub(u, t);
+            if (k != 0) {
+                float2 w = tw[k * (R / (2 * h)) * TS];
+                if (SIGN > 0) w.y = -w.y;
+                d = cmul(d, w);
+            }
+            v[i + h] = d;
+        }
+    }
+}
+
+__device__ __forceinline__ float2 shfl_c(float2 v, int lane) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, lane), __shfl_sync(0xffffffffu, v.y, lane));
+}
+__device__ __forceinline__ float2 shfl_xor_c(float2 v, int m) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+__device__ __forceinline__ double2 shfl_c(double2 v, int lane) {
+    return make_double2(__shfl_sync(0xffffffffu, v.x, lane), __shfl_sync(0xffffffffu, v.y, lane));
+}
+__device__ __forceinline__ dd shfl_d(dd v, int lane) {
+    return dd(__shfl_sync(0xffffffffu, v.hi, lane), __shfl_sync(0xffffffffu, v.lo, lane));
+}
+__device__ __forceinline__ dd2 shfl_c(dd2 v, int lane) { return c2(shfl_d(v.x, lane), shfl_d(v.y, lane)); }
+
+// Asynchronous global -> shared copy of one element (4, 8 or 16 bytes); a
+// source size of 0 fills the destination with zeros (columns past the end).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? BYTES : 0;
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(BYTES), "r"(n)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <int NS, int G, typename ST, bool REAL>
+__global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
+    typedef typename cplx<ST>::t ST2;
+    constexpr int R = NS / G;
+    constexpr int LOGR = ilog2_ct(R), LOGG = ilog2_ct(G);
+    constexpr int COLS = REG_THREADS / G;         // columns per CTA
+    constexpr int WG = 32 / G;                    // groups per warp
+    constexpr int V = R < WG ? WG : R;            // transpose-reduce width (padded)
+    constexpr int PER = V / WG;                   // slots each lane ends with
+    constexpr int NWIN = (G - 1 + 6) / G + 1;     // iterate window (slots j, j-1, ..)
+    constexpr int NW = REG_THREADS / 32;
+    // one element of a stored column array: ST (real columns) or its complex pair
+    typedef typename std::conditional<REAL, ST, ST2>::type SE;
+    constexpr int ESZ = (int)sizeof(SE);
+    // staging of this thread's X, F and N(u) elements: [array][j][thread]
+    extern __shared__ __align__(16) unsigned char stage_raw[];
+    SE* stage = reinterpret_cast<SE*>(stage_raw);
+    __shared__ float2 tw[NS / 2];   // exp(-2 pi i k/NS)
+    __shared__ float2 wfull[NS];    // exp(+2 pi i k/NS)
+    __shared__ float2 lam[NS];
+    __shared__ ST gam[NS], osc[NS];
+    __shared__ float red[NW][2][NS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane & (G - 1);        // slice residue of this lane
+    const int gl0 = lane & ~(G - 1);     // first lane of the group
+    for (int i = tid; i < NS / 2; i += REG_THREADS) {
+        const float2 t = static_cast<const float2*>(A.tw)[i];
+        tw[i] = t;
+        wfull[i] = make_float2(t.x, -t.y);
+        wfull[i + NS / 2] = make_float2(-t.x, t.y);
+    }
+    for (int i = tid; i < NS; i += REG_THREADS) {
+        lam[i] = static_cast<const float2*>(A.lam)[i];
+        gam[i] = static_cast<const ST*>(A.gam)[i];
+        osc[i] = static_cast<const ST*>(A.osc)[i];
+    }
+    for (int i = tid; i < NW * 2 * NS; i += REG_THREADS) (&red[0][0][0])[i] = 0.0f;
+    __syncthreads();
+    const long long Mcol = A.Mcol;
+    const ST bdt = (ST)A.bdt, sigR = (ST)A.sigR;
+    const int order = A.order;
+    const int k2R = (int)bitrev((unsigned)g, LOGG) * R;  // spectral block of this lane
+    float accs[PER], accx[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) accs[i] = accx[i] = 0.0f;
+    for (long long base = (long long)blockIdx.x * COLS; base < Mcol; base += (long long)gridDim.x * COLS) {
+        const long long m = base + (tid / G);
+        const bool valid = m < Mcol;
+        const long long mm = valid ? m : 0;
+        ST cs[7];
+        float cp[7];
+#pragma unroll
+        for (int j = 1; j <= 6; ++j) {
+            cs[j] = (valid && j <= order) ? coef<ST>(A, j, mm) : (ST)0;
+            cp[j] = (valid && j <= order) ? coef<float>(A, j, mm) : 0.0f;
+        }
+        const float wgt = valid ? (float)mode_weight<float>(mm, A.KX, A.NX, A.realcol) : 0.0f;
+        // ---- stage the column slices: every load of the tile in flight at once ----
+        const int ix = 0, iF = ix + (A.X ? 1 : 0), iN = iF + (A.F ? 1 : 0);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const long long gi = (long long)(G * j + g) * Mcol + mm;
+            if (A.X) cp_async_elem<ESZ>(&stage[(ix * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.X) + gi, valid);
+            if (A.F) cp_async_elem<ESZ>(&stage[(iF * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.F) + gi, valid);
+            if (A.NL) cp_async_elem<ESZ>(&stage[(iN * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.NL) + gi, valid);
+        }
+        cp_async_wait_all();  // each thread reads back only its own elements
+        // ---- residual q_n for n = G j + g, times Gamma_alpha ----
+        float2 w[R];
+        ST2 xw[NWIN];  // xw[d] = iterate at slot j - d of this lane
+#pragma unroll
+        for (int d = 0; d < NWIN; ++d) xw[d] = c2((ST)0, (ST)0);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int n = G * j + g;
+            ST2 q = c2((ST)0, (ST)0);
+#pragma unroll
+            for (int d = NWIN - 1; d >= 1; --d) xw[d] = xw[d - 1];
+            xw[0] = c2((ST)0, (ST)0);
+            if (A.X) xw[0] = ldcol<ST, REAL>(stage, (ix * R + j) * REG_THREADS + tid);
+            if (A.F) q = ldcol<ST, REAL>(stage, (iF * R + j) * REG_THREADS + tid);
+            if (A.NL) {
+                const ST2 v = ldcol<ST, REAL>(stage, (iN * R + j) * REG_THREADS + tid);
+                q.x = fma(bdt, v.x, q.x);
+                q.y = fma(bdt, v.y, q.y);
+            }
+            if (A.X) {
+                ST2 rx = xw[0];
+#pragma unroll
+                for (int i = 1; i <= 6; ++i) {
+                    if (i <= order) {  // warp-uniform
+                        // x at slice n - i lives in lane (g - i) mod G at slot j - (g' + i) / G
+                        const int gs = (g - i) & (G - 1);
+                        const int dsend = (g + i) / G;  // what this lane sends, as a source
+                        ST2 send = xw[0];
+#pragma unroll
+                        for (int d = 1; d < NWIN; ++d)
+                            if (dsend == d) send = xw[d];
+                        ST2 xv = shfl_c(send, gl0 + gs);
+                        if (n - i < 0) xv = c2((ST)0, (ST)0);  // before the window: in F
+                        rx.x = fma(-cs[i], xv.x, rx.x);
+                        rx.y = fma(-cs[i], xv.y, rx.y);
+                    }
+                }
+                q.x = fma(sigR, rx.x, q.x);
+                q.y = fma(sigR, rx.y, q.y);
+            }
+            w[j] = cvt2<float2>(cscale(q, gam[n]));
+        }
+        // ---- Step (a): Y[k1 + R k2] = sum_n y_n e^{+2 pi i kn/NS} ----
+        reg_fft_dif<R, G, +1>(w, tw);  // slot p: k1 = bitrev_R(p)
+#pragma unroll
+        for (int p = 0; p < R; ++p) {
+            const int k1 = (int)bitrev((unsigned)p, LOGR);
+            if (p != 0) w[p] = cmul(w[p], wfull[g * k1]);
+        }
+#pragma unroll
+        for (int h = G / 2; h >= 1; h >>= 1) {  // DIF across the group's lanes
+            const bool up = (g & h) != 0;
+            const float2 tw2 = wfull[(g & (h - 1)) * (NS / (2 * h))];
+#pragma unroll
+            for (int p = 0; p < R; ++p) {
+                const float2 o = shfl_xor_c(w[p], h);
+                w[p] = up ? cmul(csub(o, w[p]), tw2) : cadd(w[p], o);
+            }
+        }
+        // ---- Step (b): divide by d_k = 1 - sum_j cp_j lambda_k^j ----
+#pragma unroll
+        for (int p = 0; p < R; ++p) {
+            const float2 lk = lam[(int)bitrev((unsigned)p, LOGR) + k2R];
+            float2 acc = make_float2(cp[6], 0.0f);
+#pragma unroll
+            for (int j = 5; j >= 1; --j) {
+                acc = cmul(lk, acc);
+                acc.x += cp[j];
+            }
+            acc = cmul(lk, acc);
+            w[p] = cdiv(w[p], make_float2(1.0f - acc.x, -acc.y));
+        }
+        // ---- Step (c): z_n = sum_k Z_k e^{-2 pi i kn/NS} ----
+#pragma unroll
+        for (int h = 1; h < G; h <<= 1) {  // DIT across the group's lanes
+            const bool up = (g & h) != 0;
+            float2 tw2 = wfull[(g & (h - 1)) * (NS / (2 * h))];
+            tw2.y = -tw2.y;
+#pragma unroll
+            for (int p = 0; p < R; ++p) {
+                const float2 o = shfl_xor_c(w[p], h);
+                w[p] = up ? csub(o, cmul(w[p], tw2)) : cadd(w[p], cmul(o, tw2));
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < R; ++p) {
+            const int k1 = (int)bitrev((unsigned)p, LOGR);
+            if (p != 0) w[p] = cmulc(w[p], wfull[g * k1]);
+        }
+        reg_fft_dit<R, G, -1>(w, tw);  // slot j: z_{G j + g}
+        // ---- update (or output) and per-element norm terms ----
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int n = G * j + g;
+            const ST2 sv = cscale(cvt2<ST2>(w[j]), osc[n]);
+            const long long gi = (long long)n * Mcol + mm;
+            float ns = 0.0f, nx = 0.0f;
+            if (valid) {
+                if (A.accum) {
+                    const ST2 xn = cadd(ldcol<ST, REAL>(stage, (ix * R + j) * REG_THREADS + tid), sv);
+                    stcol<ST, REAL>(const_cast<void*>(A.X), gi, xn);
+                    const float2 xf = cvt2<float2>(xn);
+                    nx = wgt * fmaf(xf.x, xf.x, xf.y * xf.y);
+                } else {
+                    stcol<ST, REAL>(A.out, gi, sv);
+                }
+                const float2 sf = cvt2<float2>(sv);
+                ns = wgt * fmaf(sf.x, sf.x, sf.y * sf.y);
+            }
+            w[j] = make_float2(ns, nx);
+        }
+        // ---- transpose-reduce over the warp's groups (lane bits >= LOGG) ----
+        float vs[V], vx[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            vs[i] = i < R ? w[i].x : 0.0f;
+            vx[i] = i < R ? w[i].y : 0.0f;
+        }
+#pragma unroll
+        for (int st = 0; st < 5 - LOGG; ++st) {
+            const int off = 16 >> st, len = (V / 2) >> st;
+            const bool upper = (lane & off) != 0;
+#pragma unroll
+            for (int i = 0; i < len; ++i) {
+                // lanes with this bit clear keep slots [0, len), the others [len, 2 len)
+                const float ss = upper ? vs[i] : vs[i + len], sk = upper ? vs[i + len] : vs[i];
+                const float xs = upper ? vx[i] : vx[i + len], xk = upper ? vx[i + len] : vx[i];
+                vs[i] = sk + __shfl_xor_sync(0xffffffffu, ss, off);
+                vx[i] = xk + __shfl_xor_sync(0xffffffffu, xs, off);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            accs[i] += vs[i];
+            accx[i] += vx[i];
+        }
+    }
+    // lane (group c, residue g) holds slots j = c * PER + i of slice G j + g
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int j = (lane / G) * PER + i;
+        if (j < R) {
+            red[warp][0][G * j + g] = accs[i];
+            red[warp][1][G * j + g] = accx[i];
+        }
+    }
+    __syncthreads();
+    for (int n = tid; n < NS; n += REG_THREADS) {
+        float a = 0.0f, b = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+            a += red[q][0][n];
+            b += red[q][1][n];
+        }
+        A.partial[(size_t)n * gridDim.x + blockIdx.x] = make_double2((double)a, (double)b);
+    }
+}
+
+template <int NS, typename ST, bool REAL>
+expd_status launch_reg(expd_plan p, TimeArgs& a, cudaStream_t s) {
+    const TimeTables& ts = std::is_same<ST, float>::value ? p->t32 : p->t64;
+    a.gam = std::is_same<ST, dd>::value ? p->gamdd : ts.gam;
+    a.osc = std::is_same<ST, dd>::value ? p->oscdd : ts.osc;
+    a.lam = p->t32.lam;
+    a.tw = p->t32.tw;
+    constexpr int cols = REG_THREADS / REG_G;
+    long long grid = (p->Mcol + cols - 1) / cols;
+    if (grid > p->partial_cap) grid = p->partial_cap;
+    const double esz = (REAL ? 1.0 : 2.0) * sizeof(ST);
+    const double per = (a.X ? esz : 0.0) + (a.F ? esz : 0.0) + (a.NL ? esz : 0.0) + esz;  // N stored like X
+    const double fl_col = 2.0 * 5.0 * NS * ilog2(NS) + 8.0 * p->order * NS + 4.0 * p->order * NS;
+    const int cls = sizeof(ST) == 4 ? EXPD_K_TIME32 : std::is_same<ST, dd>::value ? EXPD_K_TIMEDD : EXPD_K_TIME;
+    KProf kp(p, s, cls, per * NS * (double)p->Mcol, fl_col * (double)p->Mcol);
+    const int narr = (a.X ? 1 : 0) + (a.F ? 1 : 0) + (a.NL ? 1 : 0);
+    const size_t smem = (size_t)narr * NS * REG_THREADS / REG_G * (size_t)esz;  // R slots per thread
+    auto kern = time_reg_kernel<NS, REG_G, ST, REAL>;
+    EXPD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(int)grid, REG_THREADS, smem, s>>>(a);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    p->time_grid_used = (int)grid;
+    return EXPD_OK;
+}
+
+template <typename ST, bool REAL>
+expd_status launch_reg_ns(expd_plan p, TimeArgs& a, cudaStream_t s) {
+    switch (p->Ns) {
+        case 16: return launch_reg<16, ST, REAL>(p, a, s);
+        case 32: return launch_reg<32, ST, REAL>(p, a, s);
+        case 64: return launch_reg<64, ST, REAL>(p, a, s);
+    }
+    return expd_fail(EXPD_ERR_UNSUPPORTED, "register time kernel needs Ns in {16, 32, 64}");
+}
+
 // max that propagates NaN (fmax would drop it and hide a diverged iterate)
 __device__ __forceinline__ double nanmax(double a, double b) { return (a != a || b != b) ? NAN : fmax(a, b); }
 
@@ -308,21 +661,21 @@ __global__ void __launch_bounds__(256) reduce_kernel(const double2* __restrict__
     __threadfence();
     double mx0 = 0, mx1 = 0, sm0 = 0, sm1 = 0;
     if (warp == 0) {
+        // lane-strided partial sums, then a fixed shuffle tree: a fixed order
         for (int k = lane; k < Ns; k += 32) {
             const double2 t = __ldcg(&slice_tot[k]);
             mx0 = nanmax(mx0, t.x);
             mx1 = nanmax(mx1, t.y);
+            sm0 += t.x;
+            sm1 += t.y;
         }
         for (int o = 16; o > 0; o >>= 1) {
             mx0 = nanmax(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
             mx1 = nanmax(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
+            sm0 += __shfl_xor_sync(0xffffffffu, sm0, o);
+            sm1 += __shfl_xor_sync(0xffffffffu, sm1, o);
         }
         if (lane == 0) {
-            for (int k = 0; k < Ns; ++k) {
-                const double2 t = __ldcg(&slice_tot[k]);
-                sm0 += t.x;
-                sm1 += t.y;
-            }
             out[0] = sqrt(mx0);
             out[1] = sqrt(mx1);
             out[2] = sm0;
@@ -368,6 +721,7 @@ expd_status launch_time(expd_plan p, TimeArgs& a, cudaStream_t s) {
     KProf kp(p, s, cls, per * p->Ns * (double)p->Mcol, fl_col * (double)p->Mcol);
     kern<<<p->time_grid, 32 * EXPD_TIME_COLS, smem, s>>>(a);
     EXPD_CUDA_TRY(cudaGetLastError());
+    p->time_grid_used = p->time_grid;
     return EXPD_OK;
 }
 
@@ -435,9 +789,10 @@ expd_status time_tables_build(expd_plan p, cudaStream_t s) {
     st = time_grid_for(p, &grid);
     if (st != EXPD_OK) return st;
     p->time_grid = grid;
-    cudaError_t e = cudaMalloc(&p->partial, (size_t)grid * p->Ns * sizeof(double2));
+    p->partial_cap = std::max(grid, p->sm_count * 8);
+    cudaError_t e = cudaMalloc(&p->partial, (size_t)p->partial_cap * p->Ns * sizeof(double2));
     if (e != cudaSuccess) return expd_cuda_fail(e, "cudaMalloc(partial)", __FILE__, __LINE__);
-    p->bytes += (size_t)grid * p->Ns * sizeof(double2);
+    p->bytes += (size_t)p->partial_cap * p->Ns * sizeof(double2);
     return EXPD_OK;
 }
 
@@ -502,6 +857,18 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s) {
     a.realcol = p->realcol;
     a.ntiles = (p->Mcol + EXPD_TIME_COLS - 1) / EXPD_TIME_COLS;
     a.partial = p->partial;
+    // power-of-two windows up to 64 with the float32 preconditioner: register kernel
+    const bool reg = op.precond && op.f32 && (p->Ns == 16 || p->Ns == 32 || p->Ns == 64) && !p->no_reg_time;
+    // (double-float storage stays on the shared-memory kernel: staging its 16-byte
+    // elements would leave two CTAs per SM)
+    if (reg && !op.stdd) {
+        if (op.st32) {
+            if (op.NL && !op.nl_f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 storage needs float32 N");
+            return p->realcol ? launch_reg_ns<float, true>(p, a, s) : launch_reg_ns<float, false>(p, a, s);
+        }
+        if (!op.NL || !op.nl_f32)
+            return p->realcol ? launch_reg_ns<double, true>(p, a, s) : launch_reg_ns<double, false>(p, a, s);
+    }
     if (op.stdd) {
         if (!op.f32) return expd_fail(EXPD_ERR_INVALID_ARG, "double-float storage needs the float32 preconditioner");
         return p->realcol ? launch_time<float, dd, true>(p, a, s) : launch_time<float, dd, false>(p, a, s);
@@ -516,10 +883,11 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s) {
 }
 
 expd_status time_reduce(expd_plan p, cudaStream_t s) {
-    KProf kp(p, s, EXPD_K_REDUCE, 16.0 * p->time_grid * p->Ns, 2.0 * p->time_grid * p->Ns);
+    const int grid = p->time_grid_used > 0 ? p->time_grid_used : p->time_grid;
+    KProf kp(p, s, EXPD_K_REDUCE, 16.0 * grid * p->Ns, 2.0 * grid * p->Ns);
     double2* slice_tot = reinterpret_cast<double2*>(p->redout + 8);
     unsigned* counter = reinterpret_cast<unsigned*>(p->redout + 6);
-    reduce_kernel<<<p->Ns, 256, 0, s>>>(p->partial, p->time_grid, p->Ns, slice_tot, counter, p->redout);
+    reduce_kernel<<<p->Ns, 256, 0, s>>>(p->partial, grid, p->Ns, slice_tot, counter, p->redout);
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }

@@ -296,3 +296,67 @@ def test_footprint_matches_allocation(expd):
                 plan.solve_gmres(u0, f, U)          # host pointers, a source, GMRES
                 flags = expd.FOOTPRINT_SOURCE | expd.FOOTPRINT_HOST | expd.FOOTPRINT_GMRES
                 assert plan.workspace_bytes() == expd.plan_footprint_bytes(spec, flags), p.name
+
+
+# ------------------------------------------- register-resident time kernel --
+# Power-of-two windows Ns in {16, 32, 64} with the float32 preconditioner run a
+# kernel that keeps each mode's time column in registers; EXPD_TIME_KERNEL=smem
+# selects the shared-memory kernel instead.  Grids give a ragged last CTA of
+# 128 columns: periodic 16x64 -> 16*33 = 528 columns, Dirichlet 13x23 -> 299.
+REG_CASES = [
+    P(f"reg_{bc[0]}_ns{ns}_s{s}", bc, (16, 64) if bc == "periodic" else (13, 23), s, Nt=ns + s - 1,
+      nonlin=nl, a=0.01, c=0.0 if nl != "none" else 0.1, dt=1e-3, alpha=1e-3)
+    for ns in (16, 32, 64) for bc in ("periodic", "dirichlet") for (s, nl) in ((1, "allen_cahn"), (2, "none"), (6, "none"))
+]
+REG_IDS = [p.name for p in REG_CASES]
+
+
+def _with_kernel(monkeypatch, kind):
+    if kind == "smem":
+        monkeypatch.setenv("EXPD_TIME_KERNEL", "smem")
+    else:
+        monkeypatch.delenv("EXPD_TIME_KERNEL", raising=False)
+
+
+@pytest.mark.parametrize("p", REG_CASES, ids=REG_IDS)
+def test_register_time_kernel_precond(expd, p, monkeypatch):
+    r = rand_field(p, (p.Ns,), 11)
+    ref = O.precond_apply(O.spec_of(p), r)
+    out = {}
+    for kind in ("reg", "smem"):
+        _with_kernel(monkeypatch, kind)
+        S = torch.empty_like(dev(r))
+        with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED)) as plan:
+            plan.precond_apply(dev(r), S)
+        out[kind] = host(S)
+    bound = 6e-8 * 16 / p.alpha
+    assert relmax(out["reg"], ref) < bound
+    assert relmax(out["smem"], ref) < bound
+    assert relmax(out["reg"], out["smem"]) < bound
+
+
+@pytest.mark.parametrize("p", REG_CASES, ids=REG_IDS)
+def test_register_time_kernel_solve(expd, p, monkeypatch):
+    # the mixed solve runs the register kernel for its float32 sweeps (and for
+    # accurate sweeps stored in float64); the per-slice norms its
+    # transpose-reduce produces drive the stopping test, so the first measures
+    # of the two kernels must agree
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(12)
+    u0 = rng.uniform(-0.8, 0.8, p.n)
+    f = rng.standard_normal((p.Nt,) + p.n) if p.nonlin == "none" else None
+    ref = O.sequential_solve(sp, u0, f)[1:]
+    res = {}
+    for kind in ("reg", "smem"):
+        _with_kernel(monkeypatch, kind)
+        U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+        with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-12, max_iter=200)) as plan:
+            info = plan.solve_fp(dev(u0), None if f is None else dev(f), U)
+        assert O.rel_error(host(U), ref) < 1e-10, (kind, info)
+        res[kind] = info
+    # the first sweep's measure is far above float32 rounding; later float32
+    # sweeps reach their rounding floor, where the two kernels' noise differs
+    h_reg = np.array(res["reg"]["history"][:2])
+    h_smem = np.array(res["smem"]["history"][:2])
+    assert np.allclose(h_reg, h_smem, rtol=1e-3), (h_reg, h_smem)
+    assert abs(res["reg"]["fp32_iterations"] - res["smem"]["fp32_iterations"]) <= 1
