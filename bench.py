@@ -14,6 +14,8 @@ returns to physical space.
              in HBM, L2 flushed (256 MiB write) between timed steps
   e2e        the same through the C ABI with pinned host buffers (u0 in, U out)
   fp64_path  the plain float64 GPU path on the same workload (for the speedup)
+  gpu_sequential  the same scheme stepped one time step after another on the
+             GPU in float64 (the time-stepping baseline)
   roofline   the dominant kernel class from CUDA events on its launch stream
   cpu_baseline  the CPU oracle (tests' reference), one full solve, host cores
 
@@ -288,6 +290,24 @@ def main():
     U_fp64 = U_d.cpu().numpy()
     value64 = p.unknowns / (statistics.mean(ms64) / 1e3)
 
+    # ---- the same scheme stepped sequentially on the GPU (float64): the
+    # time-stepping baseline that parallel-in-time has to beat ----
+    for k in range(3):
+        flush.fill_(float(k))
+        plan64.solve_sequential(u0_d, None, U_d)
+    barrier()
+    ms_seq = []
+    for k in range(K64):
+        flush.fill_(float(k + 1))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan64.solve_sequential(u0_d, None, U_d)
+        e1.record(stream)
+        barrier()
+        ms_seq.append(e0.elapsed_time(e1))
+    U_seq = U_d.cpu().numpy()
+    value_seq = p.unknowns / (statistics.mean(ms_seq) / 1e3)
+
     # ---- end to end through the C ABI with pinned host buffers ----
     u0_h = torch.from_numpy(u0).pin_memory()
     U_h = torch.empty((p.Nt,) + p.n, dtype=torch.float64).pin_memory()
@@ -334,6 +354,9 @@ def main():
            "fp64_path": {"value": value64, "ms_per_step": statistics.mean(ms64),
                          "iterations": infos64[-1]["iterations"]},
            "speedup_vs_fp64": value / (world * value64),
+           "gpu_sequential": {"value": value_seq, "ms_per_step": statistics.mean(ms_seq),
+                              "note": "float64 IF-BDF stepping, one time step after another"},
+           "speedup_vs_gpu_sequential": value / (world * value_seq),
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(u0.nbytes),
                    "d2h_bytes_per_step": int(U_h.numel() * 8)},
            "gpu_launches": int(tm_plain["launches"]),
@@ -344,7 +367,8 @@ def main():
     if rank == 0 and not args.no_check:
         import oracle as O
         ref = O.sequential_solve(O.spec_of(p), u0)[1:]
-        out["rel_err_vs_oracle"] = {"mixed": O.rel_error(U_mixed, ref), "fp64": O.rel_error(U_fp64, ref)}
+        out["rel_err_vs_oracle"] = {"mixed": O.rel_error(U_mixed, ref), "fp64": O.rel_error(U_fp64, ref),
+                                    "gpu_sequential": O.rel_error(U_seq, ref)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p, u0)
     plan.destroy()

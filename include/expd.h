@@ -188,6 +188,18 @@ expd_status expd_solve_fp(expd_plan plan, const double* u0, const double* f, dou
 expd_status expd_solve_gmres(expd_plan plan, const double* u0, const double* f, double* U,
                              expd_info* info, void* stream);
 
+/* Sequential time stepping of the same scheme: u_n = sum_j a_j A^j u_{n-j} +
+ * beta_s dt f(t_n) for n = s..Nt, with u_n - beta_s dt N(u_n) solved pointwise
+ * by Newton when N is nonzero (Eq. (2.2), Eq. (4.1), Eq. (7.3)), in float64,
+ * one step after the other on the GPU.  Its result is the exact solution of
+ * the all-at-once system that expd_solve_fp and expd_solve_gmres iterate
+ * towards (the system is block lower-triangular), so it is both a reference
+ * and the time-stepping baseline the parallel-in-time solve is measured
+ * against.  Arguments as expd_solve_fp (no info; the plan's precision, tol
+ * and max_iter are ignored).  Uses the plan's workspace: not concurrently
+ * with another call on the same plan. */
+expd_status expd_solve_sequential(expd_plan plan, const double* u0, const double* f, double* U, void* stream);
+
 /* ---- allocation-free preconditioner solve ---------------------------------
  * The paper has no counterpart to this entry point; it is a deployment variant
  * of expd_precond_apply for callers that must not allocate device memory --

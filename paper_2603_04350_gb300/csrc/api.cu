@@ -112,7 +112,7 @@ expd_status upload_vec(expd_plan p, T** dptr, const std::vector<T>& h, const cha
 
 void free_plan(expd_plan p) {
     if (!p) return;
-    void* bufs[] = {p->E,    p->C64,  p->C32, p->Cdd, p->Wxdd, p->Wydd, p->gamdd, p->oscdd, p->Wx64, p->Wx32,   p->Wy64,    p->Wy32,    p->Sx,        p->Sy,
+    void* bufs[] = {p->E,    p->C64,  p->C32, p->Cdd, p->Wxdd, p->Wydd, p->gamdd, p->oscdd, p->Wx64, p->Wx32,   p->Wy64,    p->Wy32,    p->Sx,        p->Sy, p->Dtx, p->Dty,
                     p->Uh,   p->Fh,   p->Sh,     p->fh,      p->NL64,    p->NL32,      p->work64,
                     p->work32, p->startphys, p->partial, p->redout, p->stage, p->gm, p->U32, p->F32};
     for (void* b : bufs)
@@ -374,6 +374,10 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     p->KX = p->realcol ? p->NX : p->NX / 2 + 1;
     p->Mcol = (long long)p->NY * p->KX;
     p->esz = p->realcol ? sizeof(double) : sizeof(double2);
+    if (p->bc == EXPD_BC_DIRICHLET) {
+        auto fast = [](int n) { return n >= 3 && n + 1 <= 4096 && ((n + 1) & n) == 0; };
+        p->fast_dst = fast(p->NX) && (p->ndim == 1 || fast(p->NY));
+    }
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -522,7 +526,15 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
             p->oscdd = op;
         }
     }
-    if (st == EXPD_OK && p->bc == EXPD_BC_DIRICHLET) {
+    if (st == EXPD_OK && p->fast_dst) {
+        for (int d = 0; d < p->ndim && st == EXPD_OK; ++d) {
+            const int n = d == 0 ? p->NX : p->NY;
+            const int N = 2 * (n + 1);
+            std::vector<double2> t((size_t)N / 2);
+            for (int k = 0; k < N / 2; ++k) t[k] = make_double2(cos(2.0 * M_PI * k / N), -sin(2.0 * M_PI * k / N));
+            st = upload_vec(p, d == 0 ? &p->Dtx : &p->Dty, t, "fast DST twiddles", s);
+        }
+    } else if (st == EXPD_OK && p->bc == EXPD_BC_DIRICHLET) {
         for (int d = 0; d < p->ndim && st == EXPD_OK; ++d) {
             const int n = d == 0 ? p->NX : p->NY;
             std::vector<double> S((size_t)n * n);
@@ -599,6 +611,9 @@ expd_status expd_plan_footprint_bytes(const expd_grid* grid, const expd_operator
             if (p->ndim == 2) b += (size_t)std::max(1, p->NY / 2) * 16;    // Wydd
             b += 2 * Ns * 8;                                                // gamdd, oscdd
         }
+    } else if (p->fast_dst) {
+        b += (size_t)(p->NX + 1) * 16;
+        if (p->ndim == 2) b += (size_t)(p->NY + 1) * 16;
     } else {
         b += (size_t)p->NX * p->NX * 8;
         if (p->ndim == 2) b += (size_t)p->NY * p->NY * 8;
@@ -885,6 +900,48 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     if (st != EXPD_OK) return st;
     if (result == EXPD_ERR_NOT_CONVERGED) g_err = "max_iter reached before tol";
     return result;
+}
+
+expd_status expd_solve_sequential(expd_plan p, const double* u0, const double* f, double* U, void* stream) {
+    if (!p || !u0 || !U) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, u0 and U are required");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Staging sg;
+    expd_status st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
+    if (st != EXPD_OK) return st;
+    // u_0 .. u_{s-1} (the ramp or the given values) exactly as the all-at-once solve takes them
+    st = setup_start(p, sg.u0, sg.f, sg.U, s);
+    if (st != EXPD_OK) return st;
+    const int so = p->order;
+    const long long M = p->M;
+    // eigen slice n: Sh for n < s, Uh for s <= n <= Nt
+    auto slice = [&](int n) -> void* { return n < so ? eig_slice(p, p->Sh, n) : eig_slice(p, p->Uh, n - so); };
+    const bool nl = p->nonlin != EXPD_NL_NONE;
+    void* tmp = p->Fh;                             // eigen scratch (the right-hand side is not used here)
+    double* phys = static_cast<double*>(p->NL64);  // physical scratch of M values (nonlinear plans)
+    const double bdt = p->beta[so] * p->dt;
+    for (int n = so; n <= p->Nt && st == EXPD_OK; ++n) {
+        // IF-BDF-s step: w = sum_j a_j A^j u_{n-j} + beta_s dt f(t_n), then
+        // u_n = w (linear) or u_n - beta_s dt N(u_n) = w pointwise (Eq. (7.3))
+        const void* in[6];
+        double coef[6];
+        for (int j = 1; j <= so; ++j) {
+            in[j - 1] = slice(n - j);
+            coef[j - 1] = p->acoef[so][j];
+        }
+        const void* src = f ? eig_slice(p, p->fh, n - 1) : nullptr;
+        if (!nl) {
+            st = eigen_combine(p, slice(n), in, coef, so, src, bdt, s);
+        } else {
+            st = eigen_combine(p, tmp, in, coef, so, src, bdt, s);
+            if (st == EXPD_OK) st = spatial_inverse64(p, tmp, phys, 1, s);
+            if (st == EXPD_OK) st = pointwise_solve(p, phys, phys, M, bdt, s);
+            if (st == EXPD_OK) st = spatial_forward64(p, phys, slice(n), 1, s);
+        }
+    }
+    if (st != EXPD_OK) return st;
+    st = write_solution(p, sg.U, s);
+    if (st != EXPD_OK) return st;
+    return stage_out(p, sg, s);
 }
 
 expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, double* U, expd_info* info,

@@ -70,8 +70,11 @@ struct expd_plan_s {
     void* Cdd = nullptr;       // [order][Mcol] double-float coefficients (dd)
     void* gamdd = nullptr;     // [Ns] Gamma_alpha as double-float
     void* oscdd = nullptr;     // [Ns] output scale as double-float
-    double* Sx = nullptr;      // Dirichlet: [NX][NX] orthonormal DST-I matrix
+    double* Sx = nullptr;      // Dirichlet: [NX][NX] orthonormal DST-I matrix (dense path)
     double* Sy = nullptr;      // Dirichlet: [NY][NY]
+    int fast_dst = 0;          // Dirichlet with n + 1 a power of two: FFT-based sine transforms
+    double2* Dtx = nullptr;    // fast DST twiddles exp(-2 pi i k / (2 (NX + 1))), k <= NX
+    double2* Dty = nullptr;    // the same for NY
     TimeTables t64, t32;
 
     // ---- state --------------------------------------------------------------

@@ -371,9 +371,102 @@ expd_status dgemm(expd_plan p, const double* A, long long lda, long long sA, con
     return EXPD_OK;
 }
 
-// Orthonormal 2D DST-I: Y = Sy X Sx (S symmetric and its own inverse).
+// Fast orthonormal DST-I along contiguous rows of length n, where N = 2(n + 1)
+// is a power of two.  Two rows share one complex FFT of length N: row a's odd
+// extension [0, x_1..x_n, 0, -x_n..-x_1] in the real part, row b's in the
+// imaginary part.  For an odd real sequence FFT(z)_k = -2i sum_j x_j
+// sin(pi jk/(n+1)), so the sine sums are -Im Z_k / 2 (row a) and Re Z_k / 2
+// (row b).  One warp per row pair, its length-N buffer in shared memory.
+__global__ void __launch_bounds__(128) dst_rows_kernel(const double* __restrict__ in, double* __restrict__ out,
+                                                       long long nrows, int n, int log2N,
+                                                       const double2* __restrict__ tw, double scale) {
+    extern __shared__ double2 dbuf[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int N = 1 << log2N;
+    double2* z = dbuf + (size_t)warp * N;
+    const long long npairs = (nrows + 1) / 2;
+    for (long long pr = (long long)blockIdx.x * nw + warp; pr < npairs; pr += (long long)gridDim.x * nw) {
+        const long long ra = 2 * pr, rb = ra + 1;
+        const bool hasb = rb < nrows;
+        const double* xa = in + ra * n;
+        const double* xb = in + rb * n;
+        for (int j = lane; j < N; j += 32) {
+            double2 v = make_double2(0.0, 0.0);
+            if (j >= 1 && j <= n) {
+                v = make_double2(xa[j - 1], hasb ? xb[j - 1] : 0.0);
+            } else if (j > n + 1) {
+                const int i = N - j - 1;
+                v = make_double2(-xa[i], hasb ? -xb[i] : 0.0);
+            }
+            z[bitrev((unsigned)j, log2N)] = v;
+        }
+        __syncwarp();
+        fft_dit(z, log2N, tw, 1, -1, lane, 32);
+        double* ya = out + ra * n;
+        double* yb = out + rb * n;
+        for (int k = lane + 1; k <= n; k += 32) {
+            const double2 Z = z[k];
+            ya[k - 1] = -0.5 * scale * Z.y;
+            if (hasb) yb[k - 1] = 0.5 * scale * Z.x;
+        }
+        __syncwarp();
+    }
+}
+
+// out[s][c][r] = in[s][r][c] for R x C slices
+__global__ void __launch_bounds__(256) transpose_kernel(const double* __restrict__ in, double* __restrict__ out,
+                                                        int R, int C) {
+    __shared__ double t[32][33];
+    const long long off = (long long)blockIdx.z * R * C;
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        if (r < R && c < C) t[i][threadIdx.x] = in[off + (long long)r * C + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (r < R && c < C) out[off + (long long)c * R + r] = t[threadIdx.x][i];
+    }
+}
+
+expd_status dst_rows(expd_plan p, const double* in, double* out, long long nrows, int n, const double2* tw,
+                     cudaStream_t s) {
+    const int log2N = ilog2(2 * (n + 1));
+    const int N = 1 << log2N;
+    const int warps = std::max(1, std::min(4, 131072 / (N * 16)));
+    const size_t smem = (size_t)warps * N * sizeof(double2);
+    const long long npairs = (nrows + 1) / 2;
+    const long long grid = std::min<long long>((npairs + warps - 1) / warps, (long long)p->sm_count * 32);
+    EXPD_CUDA_TRY(cudaFuncSetAttribute(dst_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    KProf kp(p, s, EXPD_K_DST, 16.0 * nrows * n, 5.0 * N * log2N * (double)npairs);
+    dst_rows_kernel<<<(int)grid, 32 * warps, smem, s>>>(in, out, nrows, n, log2N, tw, sqrt(2.0 / (n + 1)));
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+expd_status transpose(expd_plan p, const double* in, double* out, int R, int C, int ns, cudaStream_t s) {
+    KProf kp(p, s, EXPD_K_POINTWISE, 16.0 * R * C * ns, 0.0);
+    transpose_kernel<<<dim3((C + 31) / 32, (R + 31) / 32, ns), dim3(32, 8), 0, s>>>(in, out, R, C);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+// Orthonormal 2D DST-I: Y = Sy X Sx (S symmetric and its own inverse).  With
+// n + 1 a power of two in every direction: fast sine transforms along x, a
+// transpose, along y, and back; otherwise the dense products.
 expd_status dst2(expd_plan p, const double* X, double* Y, int ns, double* tmp, cudaStream_t s) {
     const int NX = p->NX, NY = p->NY;
+    if (p->fast_dst) {
+        if (p->ndim == 1) return dst_rows(p, X, Y, ns, NX, p->Dtx, s);
+        double* w1 = tmp;
+        double* w2 = tmp + (size_t)ns * p->M;
+        expd_status st = dst_rows(p, X, w1, (long long)ns * NY, NX, p->Dtx, s);
+        if (st == EXPD_OK) st = transpose(p, w1, w2, NY, NX, ns, s);
+        if (st == EXPD_OK) st = dst_rows(p, w2, w1, (long long)ns * NX, NY, p->Dty, s);
+        if (st == EXPD_OK) st = transpose(p, w1, Y, NX, NY, ns, s);
+        return st;
+    }
     if (p->ndim == 1) return dgemm(p, X, NX, (long long)NX, p->Sx, NX, 0, Y, NX, 0, ns, NX, NX, 1, s);
     expd_status st = dgemm(p, X, NX, (long long)NX, p->Sx, NX, 0, tmp, NX, 0, ns * NY, NX, NX, 1, s);
     if (st != EXPD_OK) return st;

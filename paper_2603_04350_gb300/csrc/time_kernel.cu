@@ -340,10 +340,6 @@ __device__ __forceinline__ float2 shfl_xor_c(float2 v, int m) {
 __device__ __forceinline__ double2 shfl_c(double2 v, int lane) {
     return make_double2(__shfl_sync(0xffffffffu, v.x, lane), __shfl_sync(0xffffffffu, v.y, lane));
 }
-__device__ __forceinline__ dd shfl_d(dd v, int lane) {
-    return dd(__shfl_sync(0xffffffffu, v.hi, lane), __shfl_sync(0xffffffffu, v.lo, lane));
-}
-__device__ __forceinline__ dd2 shfl_c(dd2 v, int lane) { return c2(shfl_d(v.x, lane), shfl_d(v.y, lane)); }
 
 // Asynchronous global -> shared copy of one element (4, 8 or 16 bytes); a
 // source size of 0 fills the destination with zeros (columns past the end).

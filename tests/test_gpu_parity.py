@@ -51,6 +51,7 @@ def P(name, bc, n, order, nonlin="none", Nt=None, alpha=1e-2, a=None, c=0.1, dt=
 
 # Sizes span several time-kernel tiles (8 modes each) and ragged tails:
 # periodic 1D n=64 -> 33 modes, 2D 16x32 -> 16*17 = 272 modes, Dirichlet 13x11 -> 143.
+# Dirichlet sizes with n + 1 a power of two take the FFT-based sine transforms.
 CASES = [
     P("p1d_s1", "periodic", (64,), 1),
     P("p1d_s2_np2", "periodic", (64,), 2, Nt=12),          # Ns = 11 (Bluestein)
@@ -63,6 +64,10 @@ CASES = [
     P("p2d_ac_s1", "periodic", (16, 32), 1, nonlin="allen_cahn", a=0.01, c=0.0, dt=1e-3, Nt=16, alpha=1e-3),
     P("p2d_ac_s2", "periodic", (16, 16), 2, nonlin="allen_cahn", a=0.01, c=0.0, dt=1e-3, Nt=21, alpha=1e-3),
     P("d2d_ac_s2", "dirichlet", (9, 12), 2, nonlin="allen_cahn", a=0.01, c=0.0, dt=1e-3, Nt=12, alpha=1e-3),
+    # n + 1 a power of two: FFT-based sine transforms instead of the dense ones
+    P("d1d_fast_s2", "dirichlet", (63,), 2, Nt=12),
+    P("d2d_fast_s6", "dirichlet", (15, 31), 6, Nt=14),
+    P("d2d_fast_ac_s1", "dirichlet", (31, 15), 1, nonlin="allen_cahn", a=0.01, c=0.0, dt=1e-3, Nt=16, alpha=1e-3),
 ]
 IDS = [p.name for p in CASES]
 
@@ -360,3 +365,45 @@ def test_register_time_kernel_solve(expd, p, monkeypatch):
     h_smem = np.array(res["smem"]["history"][:2])
     assert np.allclose(h_reg, h_smem, rtol=1e-3), (h_reg, h_smem)
     assert abs(res["reg"]["fp32_iterations"] - res["smem"]["fp32_iterations"]) <= 1
+
+
+# ------------------------------------------------- sequential time stepping --
+@pytest.mark.parametrize("p", CASES, ids=IDS)
+def test_sequential_stepper_matches_oracle(expd, p):
+    # the GPU stepper is the exact solution of the all-at-once system (block
+    # lower-triangular), so it matches the oracle's stepping to float64 rounding
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(13)
+    u0 = rng.uniform(-0.8, 0.8, p.n)
+    f = rng.standard_normal((p.Nt,) + p.n) if p.nonlin == "none" else None
+    ref = O.sequential_solve(sp, u0, f)[1:]
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p)) as plan:
+        plan.solve_sequential(dev(u0), None if f is None else dev(f), U)
+    assert O.rel_error(host(U), ref) < 1e-12
+
+
+def test_sequential_stepper_full_size_allen_cahn_256(expd):
+    p = I.ALLEN_CAHN_256
+    u0, f = I.make_inputs(p)
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p)) as plan:
+        plan.solve_sequential(dev(u0), None, U)
+    Uh = host(U)
+    sp = O.spec_of(p)
+    # every slice against the oracle's stepping (a few seconds on the CPU at this size)
+    ref = O.sequential_solve(sp, u0, None)[1:]
+    assert O.rel_error(Uh, ref) < 1e-12
+
+
+def test_fast_sine_transform_full_size_gmres(expd):
+    # heat equation on (0,1)^2 with 1023^2 interior points (h = 1/1024): the
+    # FFT-based sine transforms at full size, GMRES as for the 1024^2 workload
+    p = I.HEAT_DIRICHLET_1024.with_(name="heat_dirichlet_1023", n=(1023, 1023), Nt=32)
+    u0, f, U, info = solve_full(expd, p, expd.PREC_FP64)
+    ref = O.sequential_solve(O.spec_of(p), u0, f)[1:]
+    assert O.rel_error(U, ref) < 1e-8, info
+    Useq = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p)) as plan:
+        plan.solve_sequential(dev(u0), dev(f), Useq)
+    assert O.rel_error(host(Useq), ref) < 1e-12

@@ -92,12 +92,24 @@ def test_plan_create_rejects_bad_arguments_without_touching_the_gpu(expd, kw, ms
     assert msg in str(ei.value)
 
 
+def test_every_entry_point_has_declared_argument_types(expd):
+    # ctypes passes undeclared pointer arguments as 32-bit ints; every entry
+    # point that takes arguments must declare them
+    lib = expd.lib()
+    for name in expd.SYMBOLS:
+        if name in ("expd_last_error", "expd_version"):
+            continue
+        assert getattr(lib, name).argtypes, name
+
+
 def test_null_arguments_are_rejected(expd):
     lib = expd.lib()
     assert lib.expd_destroy(None) == expd.OK
     assert lib.expd_solve_fp(None, None, None, None, None, None) == expd.ERR_INVALID_ARG
     assert lib.expd_residual(None, None, None, None, None, None) == expd.ERR_INVALID_ARG
     assert lib.expd_precond_apply(None, None, None, None) == expd.ERR_INVALID_ARG
+    assert lib.expd_solve_gmres(None, None, None, None, None, None) == expd.ERR_INVALID_ARG
+    assert lib.expd_solve_sequential(None, None, None, None, None) == expd.ERR_INVALID_ARG
     assert lib.expd_timing_enable(None, 1) == expd.ERR_INVALID_ARG
     assert lib.expd_status_string(3) == b"not converged"
     assert lib.expd_version() >= 10000
