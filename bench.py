@@ -56,6 +56,9 @@ def parse_args():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mix", type=int, default=200, metavar="R",
+                    help="requests of the served mix to replay (0 skips it)")
+    ap.add_argument("--mix-workers", type=int, default=4)
     ap.add_argument("--profile-case", default=None, metavar="N,NT,PREC",
                     help="run two solves of the Allen-Cahn workload on an N x N grid with NT steps "
                          "(PREC mixed|fp64) and exit; the target of ncu captures")
@@ -205,6 +208,31 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm ---
+def served_mix(count: int, workers: int, local: int) -> dict:
+    """The served mix: heterogeneous requests (kind, grid, Nt, order drawn per
+    request, seed 5) replayed with Poisson arrivals at 70 % of the engine's
+    measured capacity; latency from arrival to result on the device.  Baseline:
+    the float64 path serving one request at a time, first come first served."""
+    from paper_2603_04350_gb300 import expd, inputs as I, serve
+    reqs = I.served_mix(count=count, seed=5)
+    eng = serve.Engine(device=local, workers=workers, precision=expd.PREC_MIXED)
+    eng.run(reqs[: min(8, count)], realtime=False)                 # warm-up: plans, kernels
+    t0 = time.perf_counter()
+    recs = eng.run(reqs, realtime=False)                          # all queued at t = 0
+    cap_span = time.perf_counter() - t0
+    capacity = count / cap_span
+    rate = 0.7 * capacity
+    timed = serve.with_rate(reqs, rate, seed=5)
+    recs = eng.run(timed, realtime=True)
+    mixed = serve.summary(recs)
+    base = serve.summary(serve.run_one_at_a_time(timed, device=local, precision=expd.PREC_FP64))
+    return {"requests": count, "seed": 5, "workers": workers, "capacity_req_per_s": capacity,
+            "rate_per_s": rate, "mixed_concurrent": mixed, "fp64_one_at_a_time": base,
+            "errors": eng.errors[:5],
+            "note": "grids {64..1024}^2 (Dirichlet: g-1 interior points), Nt {16..256}, s {1,2,6}, "
+                    "kind {Allen-Cahn periodic, heat Dirichlet}; inputs generated on the device"}
+
+
 def main():
     args = parse_args()
     if args.profile_case:
@@ -369,6 +397,8 @@ def main():
         ref = O.sequential_solve(O.spec_of(p), u0)[1:]
         out["rel_err_vs_oracle"] = {"mixed": O.rel_error(U_mixed, ref), "fp64": O.rel_error(U_fp64, ref),
                                     "gpu_sequential": O.rel_error(U_seq, ref)}
+    if args.mix > 0:
+        out["served_mix"] = served_mix(args.mix, args.mix_workers, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p, u0)
     plan.destroy()

@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <mutex>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -87,10 +88,37 @@ bool is_device_ptr(const void* ptr) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Pinned host words for the per-sweep norm read-back, handed out from one
+// process-wide arena (freeing pinned memory would synchronise the device).
+std::mutex g_pin_mu;
+std::vector<double*> g_pin_free;
+
+double* pinned_acquire() {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        const int slots = 256;
+        double* arena = nullptr;
+        if (cudaMallocHost(&arena, (size_t)slots * 8 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (int i = slots - 1; i >= 0; --i) g_pin_free.push_back(arena + (size_t)i * 8);
+    }
+    double* r = g_pin_free.back();
+    g_pin_free.pop_back();
+    return r;
+}
+
+void pinned_release(double* q) {
+    if (!q) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(q);
+}
+
 expd_status dalloc(expd_plan p, void** ptr, size_t bytes, const char* what) {
     *ptr = nullptr;
     if (bytes == 0) return EXPD_OK;
-    cudaError_t e = cudaMalloc(ptr, bytes);
+    cudaError_t e = plan_malloc(p, ptr, bytes);
     if (e != cudaSuccess) {
         *ptr = nullptr;
         cudaGetLastError();
@@ -115,9 +143,8 @@ void free_plan(expd_plan p) {
     void* bufs[] = {p->E,    p->C64,  p->C32, p->Cdd, p->Wxdd, p->Wydd, p->gamdd, p->oscdd, p->Wx64, p->Wx32,   p->Wy64,    p->Wy32,    p->Sx,        p->Sy, p->Dtx, p->Dty,
                     p->Uh,   p->Fh,   p->Sh,     p->fh,      p->NL64,    p->NL32,      p->work64,
                     p->work32, p->startphys, p->partial, p->redout, p->stage, p->gm, p->U32, p->F32};
-    for (void* b : bufs)
-        if (b) cudaFree(b);
-    if (p->redhost) cudaFreeHost(p->redhost);
+    for (void* b : bufs) plan_free(p, b);
+    pinned_release(p->redhost);
     for (cudaEvent_t e : p->events) cudaEventDestroy(e);
     time_tables_free(p);
     delete p;
@@ -267,6 +294,27 @@ void info_reset(expd_info* info) {
 }
 
 }  // namespace
+
+cudaError_t plan_malloc(expd_plan p, void** ptr, size_t bytes) {
+    if (!p->pooled) return cudaMalloc(ptr, bytes);
+    cudaError_t e = cudaMallocAsync(ptr, bytes, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    return e;
+}
+
+void plan_free(expd_plan p, void* ptr) {
+    if (!ptr) return;
+    if (p->pooled) cudaFreeAsync(ptr, p->stream);
+    else cudaFree(ptr);
+}
+
+cudaError_t plan_bind_stream(expd_plan p, cudaStream_t s) {
+    if (p->stream == s) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    p->stream = s;
+    return e;
+}
+
 
 expd_status expd_cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
     char buf[512];
@@ -422,6 +470,14 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
         delete p;
         return st0;
     }
+    p->stream = s;
+    {
+        int dev = 0, pools = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&pools, cudaDevAttrMemoryPoolsSupported, dev) == cudaSuccess)
+            p->pooled = pools;
+        cudaGetLastError();
+    }
     expd_status st = EXPD_OK;
     // ---- eigenvalues of L_h: E_m = exp(dt mu_m) ----
     {
@@ -576,8 +632,8 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
         if (e != cudaSuccess) st = expd_cuda_fail(e, "cudaMemsetAsync(norms)", __FILE__, __LINE__);
     }
     if (st == EXPD_OK) {
-        cudaError_t e = cudaMallocHost(&p->redhost, 8 * sizeof(double));
-        if (e != cudaSuccess) st = expd_cuda_fail(e, "cudaMallocHost(norms)", __FILE__, __LINE__);
+        p->redhost = pinned_acquire();
+        if (!p->redhost) st = expd_fail(EXPD_ERR_OOM, "pinned host memory for the norms");
     }
     if (st == EXPD_OK) st = time_tables_build(p, s);
     if (st != EXPD_OK) {
@@ -682,7 +738,7 @@ expd_status expd_timing_read(expd_plan p, expd_timing* out, int reset) {
 
 expd_status expd_destroy(expd_plan p) {
     if (!p) return EXPD_OK;
-    cudaDeviceSynchronize();
+    cudaStreamSynchronize(p->stream);  // the plan's last call has finished with its buffers
     free_plan(p);
     return EXPD_OK;
 }
@@ -691,6 +747,7 @@ expd_status expd_residual(expd_plan p, const double* u0, const double* f, const 
                           void* stream) {
     if (!p || !u0 || !U || !R) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, u0, U and R are required");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    EXPD_CUDA_TRY(plan_bind_stream(p, s));
     const size_t M = (size_t)p->M;
     Staging sg;
     expd_status st = stage_in(p, u0, f, const_cast<double*>(U), p->Nt, true, sg, s);
@@ -736,6 +793,7 @@ expd_status expd_residual(expd_plan p, const double* u0, const double* f, const 
 expd_status expd_precond_apply(expd_plan p, const double* R, double* S, void* stream) {
     if (!p || !R || !S) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, R and S are required");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    EXPD_CUDA_TRY(plan_bind_stream(p, s));
     const size_t M = (size_t)p->M;
     const size_t bytes = (size_t)p->Ns * M * sizeof(double);
     const double* Rd = R;
@@ -772,6 +830,7 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
                           void* stream) {
     if (!p || !u0 || !U) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, u0 and U are required");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    EXPD_CUDA_TRY(plan_bind_stream(p, s));
     info_reset(info);
     Staging sg;
     expd_status st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
@@ -905,6 +964,7 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
 expd_status expd_solve_sequential(expd_plan p, const double* u0, const double* f, double* U, void* stream) {
     if (!p || !u0 || !U) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, u0 and U are required");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    EXPD_CUDA_TRY(plan_bind_stream(p, s));
     Staging sg;
     expd_status st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
     if (st != EXPD_OK) return st;
@@ -949,6 +1009,7 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
     if (!p || !u0 || !U) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, u0 and U are required");
     if (p->nonlin != EXPD_NL_NONE) return expd_fail(EXPD_ERR_INVALID_ARG, "GMRES needs a linear problem");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    EXPD_CUDA_TRY(plan_bind_stream(p, s));
     info_reset(info);
     const int m = p->restart;
     const long long n = eigen_elems(p);
@@ -957,7 +1018,7 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
     const size_t hblock = 128 + 65 * (size_t)dots_grid;
     if (!p->gm || p->gm_cols < m) {
         if (p->gm) {
-            cudaFree(p->gm);
+            plan_free(p, p->gm);
             p->bytes -= (size_t)(p->gm_cols + 3) * n * sizeof(double) + hblock * sizeof(double);
             p->gm = nullptr;
         }

@@ -92,6 +92,8 @@ struct expd_plan_s {
     double2* partial = nullptr;   // [Ns][time grid] per-slice norm partials
     double* redout = nullptr;     // [4] reduced norms (device)
     double* redhost = nullptr;    // [4] pinned host copy
+    cudaStream_t stream = nullptr; // stream of the most recent call: allocations and frees are ordered on it
+    int pooled = 0;               // device supports stream-ordered allocation
     int time_grid = 0;            // CTAs of the time kernel (multiple of SM count)
     int partial_cap = 0;          // CTAs the partial-norm buffer has room for
     int time_grid_used = 0;       // CTAs of the last time-kernel launch (for the reduction)
@@ -120,6 +122,15 @@ struct expd_plan_s {
 
 // Brackets one kernel launch: counts it and, with timing on, records events
 // around it on the launch stream.
+// Device memory of a plan: stream-ordered (cudaMallocAsync / cudaFreeAsync on
+// the plan's stream), so creating and destroying plans while other streams
+// compute does not synchronise the device.  plan_malloc returns once the
+// allocation is usable from any stream.
+cudaError_t plan_malloc(expd_plan p, void** ptr, size_t bytes);
+void plan_free(expd_plan p, void* ptr);
+// Makes s the plan's stream; work still queued on the previous one finishes first.
+cudaError_t plan_bind_stream(expd_plan p, cudaStream_t s);
+
 struct KProf {
     expd_plan p;
     cudaStream_t s;

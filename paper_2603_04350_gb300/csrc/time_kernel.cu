@@ -722,14 +722,14 @@ expd_status launch_time(expd_plan p, TimeArgs& a, cudaStream_t s) {
 }
 
 template <typename T2, typename T>
-void* upload(const std::vector<std::complex<double>>& v, cudaStream_t s, size_t& bytes, expd_status& st) {
+void* upload(expd_plan p, const std::vector<std::complex<double>>& v, cudaStream_t s, size_t& bytes, expd_status& st) {
     std::vector<T2> h(v.size());
     for (size_t i = 0; i < v.size(); ++i) {
         h[i].x = (T)v[i].real();
         h[i].y = (T)v[i].imag();
     }
     void* d = nullptr;
-    cudaError_t e = cudaMalloc(&d, h.size() * sizeof(T2) + 16);
+    cudaError_t e = plan_malloc(p, &d, h.size() * sizeof(T2) + 16);
     if (e != cudaSuccess) {
         st = expd_cuda_fail(e, "cudaMalloc(time table)", __FILE__, __LINE__);
         return nullptr;
@@ -748,11 +748,11 @@ expd_status build_tables(expd_plan p, TimeTables& t, cudaStream_t s) {
     t.log2L = h.log2L;
     t.bluestein = h.bluestein;
     expd_status st = EXPD_OK;
-    t.tw = upload<T2, T>(h.tw, s, p->bytes, st);
-    if (st == EXPD_OK) t.lam = upload<T2, T>(h.lam, s, p->bytes, st);
-    if (st == EXPD_OK && t.bluestein) t.chirp = upload<T2, T>(h.chirp, s, p->bytes, st);
-    if (st == EXPD_OK && t.bluestein) t.bplus = upload<T2, T>(h.bplus, s, p->bytes, st);
-    if (st == EXPD_OK && t.bluestein) t.bminus = upload<T2, T>(h.bminus, s, p->bytes, st);
+    t.tw = upload<T2, T>(p, h.tw, s, p->bytes, st);
+    if (st == EXPD_OK) t.lam = upload<T2, T>(p, h.lam, s, p->bytes, st);
+    if (st == EXPD_OK && t.bluestein) t.chirp = upload<T2, T>(p, h.chirp, s, p->bytes, st);
+    if (st == EXPD_OK && t.bluestein) t.bplus = upload<T2, T>(p, h.bplus, s, p->bytes, st);
+    if (st == EXPD_OK && t.bluestein) t.bminus = upload<T2, T>(p, h.bminus, s, p->bytes, st);
     if (st != EXPD_OK) return st;
     // Gamma_alpha and the output scale in this table's precision
     std::vector<T> g(h.gamma.size()), o(h.gamma.size());
@@ -764,7 +764,7 @@ expd_status build_tables(expd_plan p, TimeTables& t, cudaStream_t s) {
     for (int k = 0; k < 2; ++k) {
         void** dst = k == 0 ? &t.gam : &t.osc;
         const std::vector<T>& src = k == 0 ? g : o;
-        cudaError_t e = cudaMalloc(dst, src.size() * sizeof(T));
+        cudaError_t e = plan_malloc(p, dst, src.size() * sizeof(T));
         if (e != cudaSuccess) return expd_cuda_fail(e, "cudaMalloc(gamma)", __FILE__, __LINE__);
         p->bytes += src.size() * sizeof(T);
         e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
@@ -786,7 +786,7 @@ expd_status time_tables_build(expd_plan p, cudaStream_t s) {
     if (st != EXPD_OK) return st;
     p->time_grid = grid;
     p->partial_cap = std::max(grid, p->sm_count * 8);
-    cudaError_t e = cudaMalloc(&p->partial, (size_t)p->partial_cap * p->Ns * sizeof(double2));
+    cudaError_t e = plan_malloc(p, reinterpret_cast<void**>(&p->partial), (size_t)p->partial_cap * p->Ns * sizeof(double2));
     if (e != cudaSuccess) return expd_cuda_fail(e, "cudaMalloc(partial)", __FILE__, __LINE__);
     p->bytes += (size_t)p->partial_cap * p->Ns * sizeof(double2);
     return EXPD_OK;
@@ -820,13 +820,7 @@ expd_status time_grid_for(expd_plan p, int* grid_out) {
 void time_tables_free(expd_plan p) {
     TimeTables* ts[2] = {&p->t64, &p->t32};
     for (TimeTables* t : ts) {
-        cudaFree(t->gam);
-        cudaFree(t->osc);
-        cudaFree(t->lam);
-        cudaFree(t->tw);
-        cudaFree(t->chirp);
-        cudaFree(t->bplus);
-        cudaFree(t->bminus);
+        for (void* b : {t->gam, t->osc, t->lam, t->tw, t->chirp, t->bplus, t->bminus}) plan_free(p, b);
         *t = TimeTables();
     }
 }

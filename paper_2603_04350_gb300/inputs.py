@@ -212,7 +212,8 @@ def served_mix(count: int = 2000, seed: int = 5, rate_per_s: float = 100.0,
     """Requests with Poisson arrivals; kind, grid, Nt and order drawn uniformly.
 
     Heat requests are Dirichlet (the Dirichlet workload's parameters with the
-    drawn sizes); Allen-Cahn requests are periodic (the 256^2 workload's
+    drawn sizes; a grid of g intervals per side, i.e. g - 1 interior points
+    and h = 1/g); Allen-Cahn requests are periodic (the 256^2 workload's
     parameters with the drawn sizes)."""
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate_per_s, size=count)
@@ -226,7 +227,7 @@ def served_mix(count: int = 2000, seed: int = 5, rate_per_s: float = 100.0,
         rseed = int(rng.integers(0, 2**31 - 1))
         if kind == 0:
             base = HEAT_DIRICHLET_1024
-            prob = base.with_(name=f"req{i}_heat_{g}_{nt}_{s}", n=(g, g), Nt=nt, dt=0.1 / nt,
+            prob = base.with_(name=f"req{i}_heat_{g}_{nt}_{s}", n=(g - 1, g - 1), Nt=nt, dt=0.1 / nt,
                               order=s, seed=rseed, solver="fp", tol=1e-8)
         else:
             base = ALLEN_CAHN_256
