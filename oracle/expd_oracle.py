@@ -427,6 +427,65 @@ def gmres(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None, tol: float =
     return SolveResult(assemble(sp, U_start, x.reshape(shape)), total, hist)
 
 
+def bicgstab_solve(matvec, b: np.ndarray, tol: float, max_iter: int):
+    """BiCGStab (van der Vorst, 1992) for matvec(x) = b from x = 0, in plain
+    float64: the BiCG direction step followed by a one-dimensional minimal
+    residual step each iteration.  Stops when ||r_k|| <= tol ||b||; on a
+    breakdown (rho exactly zero) it restarts the shadow residual rhat = r.
+    Returns (x, history of ||r_k|| / ||b||)."""
+    bn = np.linalg.norm(b)
+    x = np.zeros_like(b)
+    hist = [1.0]
+    if bn == 0:
+        return x, hist
+    r = b.copy()
+    rhat = r.copy()
+    rho = alpha = omega = 1.0
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    for _ in range(max_iter):
+        rho_new = float(np.dot(rhat, r))
+        if rho_new == 0.0:                     # breakdown: restart the shadow residual
+            rhat = r.copy()
+            rho, alpha, omega = 1.0, 1.0, 1.0
+            v[:] = 0.0
+            p[:] = 0.0
+            rho_new = float(np.dot(rhat, r))
+        beta = (rho_new / rho) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        v = matvec(p)
+        alpha = rho_new / float(np.dot(rhat, v))
+        s = r - alpha * v
+        t = matvec(s)
+        tt = float(np.dot(t, t))
+        omega = float(np.dot(t, s)) / tt if tt > 0 else 0.0
+        x = x + alpha * p + omega * s
+        r = s - omega * t
+        rho = rho_new
+        hist.append(float(np.linalg.norm(r)) / bn)
+        if hist[-1] <= tol:
+            break
+    return x, hist
+
+
+def bicgstab(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None, tol: float = 1e-10,
+             max_iter: int = 200, U_start: Optional[np.ndarray] = None) -> SolveResult:
+    """Left-preconditioned BiCGStab on P_alpha^{-1} R_s v = P_alpha^{-1} f_s
+    (the Krylov alternative to GMRES timed in Sec. 7, Table 2), v^0 = 0,
+    with the same stopping rule as `gmres`."""
+    if sp.nonlin != "none":
+        raise ValueError("BiCGStab is for linear problems")
+    U_start = startup_values(sp, u0, f, U_start)
+    b = rhs_known(sp, U_start, f)
+    shape = (sp.Ns,) + sp.n
+
+    def op(x):
+        return precond_apply(sp, apply_R(sp, x.reshape(shape))).ravel()
+
+    x, hist = bicgstab_solve(op, precond_apply(sp, b).ravel(), tol, max_iter)
+    return SolveResult(assemble(sp, U_start, x.reshape(shape)), len(hist) - 1, hist)
+
+
 # ---------------------------------------------------------------------------
 # Error metric: L^inf(0,T; L^2) relative error (Sec. 7).
 # ---------------------------------------------------------------------------

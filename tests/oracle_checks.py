@@ -327,3 +327,28 @@ def check_gmres_elman(sp, seed=7):
     res = O.gmres(sp, u0, None, tol=1e-14, restart=50, max_iter=30)
     q = 4 * sp.alpha * (1 - sp.alpha)
     return max(h / q ** (k / 2) for k, h in enumerate(res.history))
+
+
+def check_bicgstab_minimal_polynomial(eigs=(2.0, 2.0, 5.0, 5.0, 5.0, -1.5), seed=8, rotate=True):
+    """BiCGStab on A = Q diag(eigs) Q^{-1}: with d distinct eigenvalues the
+    BiCG residual polynomial annihilates r_0 after d steps (exact arithmetic),
+    so BiCGStab's history must reach rounding level by iteration d.  Returns
+    (history, d, error of x vs the direct solve)."""
+    rng = np.random.default_rng(seed)
+    n = len(eigs)
+    Q = np.eye(n) + (0.3 * rng.standard_normal((n, n)) if rotate else 0.0)
+    A = Q @ np.diag(eigs) @ np.linalg.inv(Q)
+    b = rng.standard_normal(n)
+    x, hist = O.bicgstab_solve(lambda v: A @ v, b, 1e-300, len(set(eigs)))
+    err = float(np.linalg.norm(x - np.linalg.solve(A, b)) / np.linalg.norm(np.linalg.solve(A, b)))
+    return hist, len(set(eigs)), err
+
+
+def check_bicgstab_reaches_sequential(sp, seed=9):
+    """Relative error of the oracle's BiCGStab solution vs sequential stepping."""
+    rng = np.random.default_rng(seed)
+    u0 = rng.standard_normal(sp.n)
+    f = rng.standard_normal((sp.Nt,) + sp.n)
+    ref = O.sequential_solve(sp, u0, f)
+    res = O.bicgstab(sp, u0, f, tol=1e-13)
+    return O.rel_error(res.U[1:], ref[1:]), res

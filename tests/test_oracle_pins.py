@@ -217,3 +217,21 @@ def test_one_iteration_claim_long_window():
     ref = O.sequential_solve(sp, u0)
     r = O.richardson(sp, u0, max_iter=1)
     assert O.rel_error(r.U[1:], ref[1:]) < claims["one_iteration_tol"]
+
+
+@pytest.mark.parametrize("eigs", [(3.0,) * 5, (2.0, 2.0, 5.0, 5.0, 5.0), (2.0, 2.0, 5.0, 5.0, 5.0, -1.5),
+                                  (1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 7.0)])
+def test_bicgstab_terminates_with_the_minimal_polynomial(eigs):
+    # BiCG-type finite termination: d distinct eigenvalues -> exact after d steps
+    hist, d, err = C.check_bicgstab_minimal_polynomial(eigs)
+    assert len(hist) == d + 1
+    assert hist[d] < 1e-10 and err < 1e-10, (hist, err)
+
+
+@pytest.mark.parametrize("order", [1, 2, 6])
+def test_bicgstab_reaches_sequential(order):
+    sp = C.spec("periodic", (4, 4), length=(1.0, 1.0), a=0.05, c=0.1, Nt=order + 9,
+                order=order, alpha=1e-3, dt=0.02)
+    err, res = C.check_bicgstab_reaches_sequential(sp)
+    assert err < 1e-12
+    assert res.iterations <= 6          # preconditioned spectrum clustered at 1 (Lemma 3.4)

@@ -125,3 +125,34 @@ def test_planted_wrong_nonlinear_sign_is_caught(monkeypatch):
     ref = O.sequential_solve(sp, u0)
     r = O.richardson(sp, u0, max_iter=30)
     assert O.rel_error(r.U[1:], ref[1:]) > 1e-6
+
+
+@pytest.mark.parametrize("mistake", ["beta_sign", "omega_dropped"])
+def test_planted_bicgstab_mistakes_are_caught(monkeypatch, mistake):
+    def bicgstab_solve(matvec, b, tol, max_iter):
+        x = np.zeros_like(b)
+        r = b.copy()
+        rhat = r.copy()
+        rho = alpha = omega = 1.0
+        v = np.zeros_like(b)
+        p = np.zeros_like(b)
+        hist = [1.0]
+        for _ in range(max_iter):
+            rho_new = float(np.dot(rhat, r))
+            beta = (rho_new / rho) * (alpha / omega)
+            if mistake == "beta_sign":
+                beta = -beta
+            p = r + beta * (p - omega * v)
+            v = matvec(p)
+            alpha = rho_new / float(np.dot(rhat, v))
+            s = r - alpha * v
+            t = matvec(s)
+            omega = float(np.dot(t, s)) / float(np.dot(t, t))
+            x = x + alpha * p + (0.0 if mistake == "omega_dropped" else omega) * s
+            r = s - omega * t
+            rho = rho_new
+            hist.append(float(np.linalg.norm(r)) / np.linalg.norm(b))
+        return x, hist
+    patch(monkeypatch, "bicgstab_solve", bicgstab_solve)
+    hist, d, err = C.check_bicgstab_minimal_polynomial((2.0, 2.0, 5.0, 5.0, 5.0, -1.5))
+    assert hist[d] > 1e-6 or err > 1e-6
