@@ -143,7 +143,7 @@ expd_status expd_plan_workspace_bytes(expd_plan plan, size_t* bytes);
  * without allocating anything (admission control before creating a plan).
  * flags adds the buffers a plan allocates on first use: EXPD_FOOTPRINT_SOURCE
  * (a source f is passed), EXPD_FOOTPRINT_HOST (host pointers are passed),
- * EXPD_FOOTPRINT_GMRES (expd_solve_gmres is called). */
+ * EXPD_FOOTPRINT_GMRES (expd_solve_gmres or expd_solve_bicgstab is called). */
 enum { EXPD_FOOTPRINT_SOURCE = 1, EXPD_FOOTPRINT_HOST = 2, EXPD_FOOTPRINT_GMRES = 4 };
 expd_status expd_plan_footprint_bytes(const expd_grid* grid, const expd_operator* op, double dt, int Nt,
                                       double alpha, const expd_scheme* scheme, int flags, size_t* bytes);
@@ -198,6 +198,18 @@ expd_status expd_solve_gmres(expd_plan plan, const double* u0, const double* f, 
  * against.  Arguments as expd_solve_fp (no info; the plan's precision, tol
  * and max_iter are ignored).  Uses the plan's workspace: not concurrently
  * with another call on the same plan. */
+/* Left-preconditioned BiCGStab (van der Vorst's recurrences) on
+ * (R_s^alpha)^{-1} R_s v = (R_s^alpha)^{-1} f_s, v^0 = 0, float64: the
+ * short-recurrence alternative to GMRES that Sec. 7 (Table 2) times beside it
+ * (two preconditioned operator applications and three reductions per
+ * iteration, seven vectors of storage whatever the iteration count).  Stops
+ * like expd_solve_gmres; restarts its shadow residual on a breakdown; returns
+ * EXPD_ERR_DIVERGED when the residual turns non-finite.  Linear problems
+ * only.  Arguments as expd_solve_fp; info->history[k] is the relative
+ * preconditioned residual after k iterations. */
+expd_status expd_solve_bicgstab(expd_plan plan, const double* u0, const double* f, double* U,
+                                expd_info* info, void* stream);
+
 expd_status expd_solve_sequential(expd_plan plan, const double* u0, const double* f, double* U, void* stream);
 
 /* ---- allocation-free preconditioner solve ---------------------------------

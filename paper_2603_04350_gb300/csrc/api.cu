@@ -696,7 +696,7 @@ expd_status expd_plan_footprint_bytes(const expd_grid* grid, const expd_operator
     if (flags & EXPD_FOOTPRINT_HOST) b += (size_t)(2 * p->Nt + 1) * p->M * 8;
     if (flags & EXPD_FOOTPRINT_GMRES) {
         const size_t n = (size_t)eigen_elems(p);
-        b += (size_t)(p->restart + 3) * n * 8 + (128 + 65 * (size_t)p->sm_count * 4) * 8;
+        b += (size_t)std::max(p->restart + 3, 7) * n * 8 + (128 + 65 * (size_t)p->sm_count * 4) * 8;
     }
     *bytes = b;
     return EXPD_OK;
@@ -961,6 +961,24 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     return result;
 }
 
+// The Krylov block: nvec vectors of eigen_elems doubles, then the dot results
+// and partials (128 + 65 x dots grid doubles).
+static size_t krylov_hblock(expd_plan p) { return 128 + 65 * (size_t)(p->sm_count * 4); }
+
+static expd_status ensure_krylov(expd_plan p, int nvec) {
+    const size_t n = (size_t)eigen_elems(p);
+    if (p->gm && p->gm_vecs >= nvec) return EXPD_OK;
+    if (p->gm) {
+        plan_free(p, p->gm);
+        p->bytes -= ((size_t)p->gm_vecs * n + krylov_hblock(p)) * sizeof(double);
+        p->gm = nullptr;
+        p->gm_vecs = 0;
+    }
+    expd_status st = dalloc(p, &p->gm, ((size_t)nvec * n + krylov_hblock(p)) * sizeof(double), "Krylov vectors");
+    if (st == EXPD_OK) p->gm_vecs = nvec;
+    return st;
+}
+
 expd_status expd_solve_sequential(expd_plan p, const double* u0, const double* f, double* U, void* stream) {
     if (!p || !u0 || !U) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, u0 and U are required");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1014,17 +1032,9 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
     const int m = p->restart;
     const long long n = eigen_elems(p);
     // block: V[0..m], c, w, then h/partials
-    const int dots_grid = p->sm_count * 4;
-    const size_t hblock = 128 + 65 * (size_t)dots_grid;
-    if (!p->gm || p->gm_cols < m) {
-        if (p->gm) {
-            plan_free(p, p->gm);
-            p->bytes -= (size_t)(p->gm_cols + 3) * n * sizeof(double) + hblock * sizeof(double);
-            p->gm = nullptr;
-        }
-        expd_status st = dalloc(p, &p->gm, (size_t)(m + 3) * n * sizeof(double) + hblock * sizeof(double), "GMRES basis");
+    {
+        expd_status st = ensure_krylov(p, m + 3);
         if (st != EXPD_OK) return st;
-        p->gm_cols = m;
     }
     double* V = static_cast<double*>(p->gm);
     double* c = V + (size_t)(m + 1) * n;
@@ -1169,6 +1179,133 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
     st = stage_out(p, sg, s);
     if (st != EXPD_OK) return st;
     if (result == EXPD_ERR_NOT_CONVERGED) g_err = "max_iter reached before tol";
+    return result;
+}
+
+expd_status expd_solve_bicgstab(expd_plan p, const double* u0, const double* f, double* U, expd_info* info,
+                                void* stream) {
+    if (!p || !u0 || !U) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, u0 and U are required");
+    if (p->nonlin != EXPD_NL_NONE) return expd_fail(EXPD_ERR_INVALID_ARG, "BiCGStab needs a linear problem");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    EXPD_CUDA_TRY(plan_bind_stream(p, s));
+    info_reset(info);
+    const long long n = eigen_elems(p);
+    expd_status st = ensure_krylov(p, 7);
+    if (st != EXPD_OK) return st;
+    // [rhat][r] and [s][t] adjacent, so one dot kernel gives two products
+    double* rhat = static_cast<double*>(p->gm);
+    double* r = rhat + n;
+    double* sv = r + n;
+    double* t = sv + n;
+    double* pv = t + n;
+    double* v = pv + n;
+    double* c = v + n;
+    double* h = c + n;
+    Staging sg;
+    st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
+    if (st != EXPD_OK) return st;
+    st = setup_start(p, sg.u0, sg.f, sg.U, s);
+    if (st != EXPD_OK) return st;
+    double* x = static_cast<double*>(p->Uh);
+    EXPD_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    auto apply_op = [&](const double* in, double* out) -> expd_status {  // out = P^{-1} R in
+        TimeOp op;
+        op.X = in;
+        op.sigR = 1.0;
+        op.precond = 1;
+        op.out = out;
+        return time_apply(p, op, s);
+    };
+    auto dots = [&](const double* Vb, int k, const double* w, double* hh) -> expd_status {
+        expd_status e = gm_dots(p, Vb, n, k, w, h, s);
+        if (e != EXPD_OK) return e;
+        EXPD_CUDA_TRY(cudaMemcpyAsync(hh, h, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+        EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+        return EXPD_OK;
+    };
+    auto copy = [&](const double* from, double* to) -> expd_status {
+        EXPD_CUDA_TRY(cudaMemcpyAsync(to, from, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        return EXPD_OK;
+    };
+    // c = P^{-1} f_s;  r = rhat = c
+    {
+        TimeOp op;
+        op.F = p->Fh;
+        op.precond = 1;
+        op.out = c;
+        st = time_apply(p, op, s);
+    }
+    if (st == EXPD_OK) st = copy(c, r);
+    if (st == EXPD_OK) st = copy(c, rhat);
+    if (st == EXPD_OK) EXPD_CUDA_TRY(cudaMemsetAsync(pv, 0, 2 * n * sizeof(double), s));  // p, v
+    if (st != EXPD_OK) return st;
+    double cc = 0;
+    st = dots(c, 1, c, &cc);
+    if (st != EXPD_OK) return st;
+    const double cn = sqrt(cc);
+    // stop as GMRES does: sqrt(Ns) * ||P^{-1}(f - R v)|| / ||P^{-1} f|| <= tol
+    const double tol_res = p->tol / sqrt((double)p->Ns);
+    double rho = 1.0, alpha = 1.0, omega = 1.0, relres = 1.0;
+    int it = 0;
+    expd_status result = EXPD_ERR_NOT_CONVERGED;
+    if (info) info->history[0] = 1.0;
+    while (cn > 0) {
+        double d2[2];
+        st = dots(rhat, 2, r, d2);  // (rhat, r), (r, r)
+        if (st != EXPD_OK) return st;
+        relres = sqrt(d2[1]) / cn;
+        if (it > 0 && info && it < EXPD_MAX_HISTORY) info->history[it] = relres;
+        if (!(relres == relres) || relres > 1e12) {
+            result = EXPD_ERR_DIVERGED;
+            break;
+        }
+        if (relres <= tol_res) {
+            result = EXPD_OK;
+            break;
+        }
+        if (it >= p->max_iter) break;
+        double rho_new = d2[0];
+        if (rho_new == 0.0) {  // breakdown: restart the shadow residual from r
+            st = copy(r, rhat);
+            if (st == EXPD_OK) EXPD_CUDA_TRY(cudaMemsetAsync(pv, 0, 2 * n * sizeof(double), s));
+            if (st != EXPD_OK) return st;
+            rho = alpha = omega = 1.0;
+            rho_new = d2[1];
+        }
+        const double beta = (rho_new / rho) * (alpha / omega);
+        st = gm_axpby(p, n, -omega, v, 1.0, pv, s);             // p = r + beta (p - omega v)
+        if (st == EXPD_OK) st = gm_axpby(p, n, 1.0, r, beta, pv, s);
+        if (st == EXPD_OK) st = apply_op(pv, v);                // v = P^{-1} R p
+        double rv = 0;
+        if (st == EXPD_OK) st = dots(rhat, 1, v, &rv);
+        if (st != EXPD_OK) return st;
+        alpha = rho_new / rv;
+        st = copy(r, sv);                                       // s = r - alpha v
+        if (st == EXPD_OK) st = gm_axpby(p, n, -alpha, v, 1.0, sv, s);
+        if (st == EXPD_OK) st = apply_op(sv, t);                // t = P^{-1} R s
+        double d3[2];
+        if (st == EXPD_OK) st = dots(sv, 2, t, d3);            // (s, t), (t, t)
+        if (st != EXPD_OK) return st;
+        omega = d3[1] > 0 ? d3[0] / d3[1] : 0.0;
+        st = gm_axpby(p, n, alpha, pv, 1.0, x, s);              // x += alpha p + omega s
+        if (st == EXPD_OK) st = gm_axpby(p, n, omega, sv, 1.0, x, s);
+        if (st == EXPD_OK) st = copy(sv, r);                    // r = s - omega t
+        if (st == EXPD_OK) st = gm_axpby(p, n, -omega, t, 1.0, r, s);
+        if (st != EXPD_OK) return st;
+        rho = rho_new;
+        ++it;
+    }
+    if (cn == 0) result = EXPD_OK;
+    if (info) {
+        info->iterations = it;
+        info->final_measure = relres;
+    }
+    st = write_solution(p, sg.U, s);
+    if (st != EXPD_OK) return st;
+    st = stage_out(p, sg, s);
+    if (st != EXPD_OK) return st;
+    if (result == EXPD_ERR_NOT_CONVERGED) g_err = "max_iter reached before tol";
+    if (result == EXPD_ERR_DIVERGED) g_err = "BiCGStab residual non-finite or growing without bound";
     return result;
 }
 

@@ -102,8 +102,8 @@ struct expd_plan_s {
     double* stage = nullptr;      // [(2*Nt + 1) * M]
     size_t stage_elems = 0;
     // GMRES basis (lazy)
-    void* gm = nullptr;
-    int gm_cols = 0;
+    void* gm = nullptr;           // Krylov vectors (GMRES basis or BiCGStab vectors) + dot partials
+    int gm_vecs = 0;              // vectors of length eigen_elems the block holds
 
     size_t bytes = 0;             // device bytes held
     int sm_count = 0;

@@ -25,7 +25,7 @@ STARTUP_RAMP, STARTUP_GIVEN = 0, 1
 MAX_HISTORY = 128
 
 SYMBOLS = ("expd_plan_create", "expd_plan_workspace_bytes", "expd_plan_footprint_bytes", "expd_residual", "expd_precond_apply",
-           "expd_solve_fp", "expd_solve_gmres", "expd_solve_sequential", "expd_timing_enable", "expd_timing_read", "expd_destroy",
+           "expd_solve_fp", "expd_solve_gmres", "expd_solve_bicgstab", "expd_solve_sequential", "expd_timing_enable", "expd_timing_read", "expd_destroy",
            "expd_precond_apply_noalloc",
            "expd_status_string", "expd_last_error", "expd_version")
 (K_TIME, K_FFT_COL, K_FFT_ROW, K_DST, K_GMRES, K_POINTWISE, K_REDUCE, K_TIME32, K_FFT_COL32, K_FFT_ROW32,
@@ -97,6 +97,7 @@ def lib() -> C.CDLL:
     L.expd_solve_fp.argtypes = [vp, dp, dp, dp, C.POINTER(Info), vp]
     L.expd_solve_gmres.argtypes = [vp, dp, dp, dp, C.POINTER(Info), vp]
     L.expd_solve_sequential.argtypes = [vp, dp, dp, dp, vp]
+    L.expd_solve_bicgstab.argtypes = [vp, dp, dp, dp, C.POINTER(Info), vp]
     L.expd_timing_enable.argtypes = [vp, C.c_int]
     L.expd_timing_read.argtypes = [vp, C.POINTER(Timing), C.c_int]
     L.expd_destroy.argtypes = [vp]
@@ -247,6 +248,15 @@ class Plan:
         info = Info()
         allow = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
         st = _check(lib().expd_solve_gmres(self._h, _ptr(u0), _ptr(f), _ptr(U), C.byref(info), _stream(stream)),
+                    allow)
+        d = info.as_dict()
+        d["status"] = st
+        return d
+
+    def solve_bicgstab(self, u0, f, U, stream=None, allow_not_converged=False) -> dict:
+        info = Info()
+        allow = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
+        st = _check(lib().expd_solve_bicgstab(self._h, _ptr(u0), _ptr(f), _ptr(U), C.byref(info), _stream(stream)),
                     allow)
         d = info.as_dict()
         d["status"] = st

@@ -407,3 +407,37 @@ def test_fast_sine_transform_full_size_gmres(expd):
     with expd.plan_create(expd.spec_from_problem(p)) as plan:
         plan.solve_sequential(dev(u0), dev(f), Useq)
     assert O.rel_error(host(Useq), ref) < 1e-12
+
+
+# ------------------------------------------------------------------ BiCGStab --
+@pytest.mark.parametrize("p", [c for c in CASES if c.nonlin == "none"], ids=[c.name for c in CASES if c.nonlin == "none"])
+def test_bicgstab_matches_oracle(expd, p):
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(14)
+    u0 = rng.standard_normal(p.n)
+    f = rng.standard_normal((p.Nt,) + p.n)
+    pr = p.with_(alpha=0.3)       # slower convergence -> a longer history to compare
+    spr = O.spec_of(pr)
+    ref = O.bicgstab(spr, u0, f, tol=1e-12 / math.sqrt(pr.Ns))
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(pr, tol=1e-12, max_iter=200)) as plan:
+        info = plan.solve_bicgstab(dev(u0), dev(f), U)
+    seq = O.sequential_solve(spr, u0, f)[1:]
+    assert O.rel_error(host(U), seq) < 1e-10
+    assert O.rel_error(ref.U[1:], seq) < 1e-10
+    # iterate-by-iterate parity: the relative preconditioned residuals agree
+    h_gpu = np.array(info["history"])
+    h_ref = np.array(ref.history)
+    k = min(len(h_gpu), len(h_ref))
+    big = h_ref[:k] > 1e-8
+    assert np.allclose(h_gpu[:k][big], h_ref[:k][big], rtol=1e-6), (h_gpu[:k], h_ref[:k])
+
+
+def test_bicgstab_full_size_heat_dirichlet(expd):
+    p = I.HEAT_DIRICHLET_1024.with_(name="heat_dirichlet_1023_bicgstab", n=(1023, 1023), Nt=32)
+    u0, f = I.make_inputs(p)
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, max_iter=200)) as plan:
+        info = plan.solve_bicgstab(dev(u0), dev(f), U)
+    ref = O.sequential_solve(O.spec_of(p), u0, f)[1:]
+    assert O.rel_error(host(U), ref) < 1e-8, info

@@ -109,6 +109,7 @@ def test_null_arguments_are_rejected(expd):
     assert lib.expd_residual(None, None, None, None, None, None) == expd.ERR_INVALID_ARG
     assert lib.expd_precond_apply(None, None, None, None) == expd.ERR_INVALID_ARG
     assert lib.expd_solve_gmres(None, None, None, None, None, None) == expd.ERR_INVALID_ARG
+    assert lib.expd_solve_bicgstab(None, None, None, None, None, None) == expd.ERR_INVALID_ARG
     assert lib.expd_solve_sequential(None, None, None, None, None) == expd.ERR_INVALID_ARG
     assert lib.expd_timing_enable(None, 1) == expd.ERR_INVALID_ARG
     assert lib.expd_status_string(3) == b"not converged"
