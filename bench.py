@@ -97,6 +97,17 @@ def workload(rank: int):
     return p.with_(seed=p.seed + 1000 * rank) if rank else p
 
 
+def aggregate(total_ms: float, unknowns: int, steps: int, world: int, pg=None, device=None):
+    """Whole-job timing of a weak-scaled replica run: the slowest rank's time
+    (max over ranks) and the units all ranks processed in it."""
+    if pg is not None:
+        import torch
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * unknowns * steps / (total_ms / 1e3)
+
+
 def config_dict(p, world):
     return {"workload": p.name, "grid": list(p.n), "Nt": p.Nt, "Ns": p.Ns, "order": p.order, "alpha": p.alpha,
             "dt": p.dt, "tol": p.tol, "nonlin": p.nonlin, "unknowns_per_solve": p.unknowns,
@@ -301,12 +312,7 @@ def main():
     ms, infos, tm = timed_steps(plan, args.steps, args.warmup, timing=True)
     clk = clocks.stop()
     U_mixed = U_d.cpu().numpy()
-    total_ms = sum(ms)
-    if pg is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * p.unknowns * args.steps / (total_ms / 1e3)
+    total_ms, value = aggregate(sum(ms), p.unknowns, args.steps, world, pg, dev)
 
     # untimed-by-events repeat of the same loop: event records around every launch
     # add overhead, so report how much (kept as the headline's own check)
