@@ -39,7 +39,9 @@
  *    be in flight at a time.
  *  - Errors.  Every entry point returns an expd_status; nothing is thrown
  *    across the ABI.  expd_last_error() gives a thread-local message for the
- *    last failure.  EXPD_ERR_CUDA means a CUDA call failed (the message names
+ *    last failure.  Different plans may be used from different host threads
+ *    at the same time (plan memory is stream-ordered; kernel launch limits are
+ *    set once per process and never lowered).  EXPD_ERR_CUDA means a CUDA call failed (the message names
  *    it); the plan stays valid unless the CUDA context itself is lost.
  */
 #ifndef EXPD_H

@@ -308,6 +308,33 @@ void plan_free(expd_plan p, void* ptr) {
     else cudaFree(ptr);
 }
 
+cudaError_t smem_allow(const void* kern, size_t smem) {
+    static std::mutex mu;
+    static std::vector<const void*> done;
+    static int optin = -1;
+    std::lock_guard<std::mutex> lk(mu);
+    if (optin < 0) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) {
+            optin = -1;
+            return e;
+        }
+    }
+    if (smem > (size_t)optin) return cudaErrorInvalidValue;
+    if (std::find(done.begin(), done.end(), kern) != done.end()) return cudaSuccess;
+    // the limit covers static plus dynamic shared memory
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    const int dyn_max = optin - (int)fa.sharedSizeBytes;
+    if (smem > (size_t)std::max(dyn_max, 0)) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+    if (e == cudaSuccess) done.push_back(kern);
+    return e;
+}
+
 cudaError_t plan_bind_stream(expd_plan p, cudaStream_t s) {
     if (p->stream == s) return cudaSuccess;
     cudaError_t e = cudaStreamSynchronize(p->stream);
@@ -434,6 +461,9 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     // (both kernels compute the same sweep; this lets them be compared)
     const char* tk = getenv("EXPD_TIME_KERNEL");
     p->no_reg_time = tk && strcmp(tk, "smem") == 0;
+    // EXPD_COL_FFT=radix4 selects the shared-memory column FFT for every size
+    const char* cf = getenv("EXPD_COL_FFT");
+    p->no_col4 = cf && strcmp(cf, "radix4") == 0;
     return EXPD_OK;
 }
 

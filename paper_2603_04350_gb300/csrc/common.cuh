@@ -198,6 +198,57 @@ EXPD_HD void fft_dif(T2* x, int log2n, const T2* tw, int ts, int sign, int lane,
     }
 }
 
+// ------------------------------------------------------- register FFTs ---
+// Length-R FFTs on a register array (compile-time indices, fully unrolled).
+// tw[k * TS] = exp(-2 pi i k / R) for k < R/2 (a table of a longer length,
+// read at stride TS).  SIGN < 0: exp(-2 pi i jk/R); SIGN > 0: exp(+2 pi i jk/R).
+constexpr int ilog2_ct(int n) { return n <= 1 ? 0 : 1 + ilog2_ct(n >> 1); }
+
+// DIT: bit-reversed in -> natural out
+template <int R, int TS, int SIGN, typename T2>
+EXPD_HD void reg_fft_dit(T2 (&v)[R], const T2* tw) {
+#pragma unroll
+    for (int st = 0; st < ilog2_ct(R); ++st) {
+        const int h = 1 << st;
+#pragma unroll
+        for (int b = 0; b < R / 2; ++b) {
+            const int k = b & (h - 1);
+            const int i = ((b >> st) << (st + 1)) + k;
+            T2 t = v[i + h];
+            if (k != 0) {
+                T2 w = tw[k * (R / (2 * h)) * TS];
+                if (SIGN > 0) w.y = -w.y;
+                t = cmul(t, w);
+            }
+            v[i + h] = csub(v[i], t);
+            v[i] = cadd(v[i], t);
+        }
+    }
+}
+
+// DIF: natural in -> bit-reversed out
+template <int R, int TS, int SIGN, typename T2>
+EXPD_HD void reg_fft_dif(T2 (&v)[R], const T2* tw) {
+#pragma unroll
+    for (int st = ilog2_ct(R) - 1; st >= 0; --st) {
+        const int h = 1 << st;
+#pragma unroll
+        for (int b = 0; b < R / 2; ++b) {
+            const int k = b & (h - 1);
+            const int i = ((b >> st) << (st + 1)) + k;
+            const T2 u = v[i], t = v[i + h];
+            v[i] = cadd(u, t);
+            T2 d = csub(u, t);
+            if (k != 0) {
+                T2 w = tw[k * (R / (2 * h)) * TS];
+                if (SIGN > 0) w.y = -w.y;
+                d = cmul(d, w);
+            }
+            v[i + h] = d;
+        }
+    }
+}
+
 // Error checking used by every host launcher.
 #define EXPD_CUDA_TRY(expr)                                                    \
     do {                                                                       \

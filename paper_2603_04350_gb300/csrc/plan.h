@@ -98,6 +98,7 @@ struct expd_plan_s {
     int partial_cap = 0;          // CTAs the partial-norm buffer has room for
     int time_grid_used = 0;       // CTAs of the last time-kernel launch (for the reduction)
     int no_reg_time = 0;          // 1 forces the shared-memory time kernel (tests)
+    int no_col4 = 0;              // 1 forces the radix-4 shared-memory column FFT (tests)
     // host-pointer staging (lazy)
     double* stage = nullptr;      // [(2*Nt + 1) * M]
     size_t stage_elems = 0;
@@ -130,6 +131,13 @@ cudaError_t plan_malloc(expd_plan p, void** ptr, size_t bytes);
 void plan_free(expd_plan p, void* ptr);
 // Makes s the plan's stream; work still queued on the previous one finishes first.
 cudaError_t plan_bind_stream(expd_plan p, cudaStream_t s);
+
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in
+// maximum, once per kernel and never lowering it: plans used from several host
+// threads launch the same kernels with different sizes, and a per-launch limit
+// set by one thread would undercut another thread's launch.  Fails for
+// requests above the device maximum.
+cudaError_t smem_allow(const void* kern, size_t smem);
 
 struct KProf {
     expd_plan p;

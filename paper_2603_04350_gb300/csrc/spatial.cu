@@ -300,6 +300,122 @@ int grid_for(long long n, int threads) {
     return (int)b;
 }
 
+// Strided-axis FFT of length N = N1 x N2 along the columns of every slice,
+// four-step: the CTA stages C columns (flattened over slices) in shared memory
+// with coalesced row loads; per column, N2 threads each run an N1-point FFT
+// in registers over n1 (elements n1 N2 + n2), multiply by the twiddle
+// w_N^(n2 k1), and write the transposed intermediate back to shared memory;
+// then N1 threads each run an N2-point FFT over n2, giving X[k1 + N1 k2].  Two
+// register FFTs and one shared-memory transpose replace log2(N)/2 shared
+// round trips.  sign > 0 runs the inverse by conjugating input and output.
+constexpr int COL4_THREADS = 256;
+
+// Columns per CTA: 128-byte row segments where 96 KB of shared memory allows,
+// and at least one round of COL4_THREADS / N1 columns.
+constexpr int col4_columns(int N1, int N2, int esz) {
+    const int CS = N1 * N2 + N1 + 1, CR = COL4_THREADS / N1;
+    int C = esz == 8 ? 16 : 8;
+    while (C > 1 && (long long)C * CS * esz > 96 * 1024) C >>= 1;
+    return C < CR ? CR : C;
+}
+
+template <typename PT, typename TIN, typename TOUT, int N1, int N2>
+__global__ void __launch_bounds__(COL4_THREADS, N1 >= 32 ? 2 : 3) col4_kernel(const TIN* __restrict__ in, TOUT* __restrict__ out,
+                                                                long long ncols, int KX,
+                                                                const typename cplx<PT>::t* __restrict__ Wg,
+                                                                int sign, PT scale) {
+    typedef typename cplx<PT>::t PT2;
+    constexpr int N = N1 * N2;
+    constexpr int C = col4_columns(N1, N2, (int)sizeof(PT2));
+    constexpr int LOADS = (N * C + COL4_THREADS - 1) / COL4_THREADS;
+    constexpr int CS = N + N1 + 1;  // column stride in shared memory (odd)
+    constexpr int CR = COL4_THREADS / N1;  // columns per round
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PT2* TW = reinterpret_cast<PT2*>(smem_raw);  // exp(-2 pi i k/N), k < N
+    long long* cbase = reinterpret_cast<long long*>(TW + N);
+    PT2* tile = reinterpret_cast<PT2*>(cbase + C);
+    const int tid = threadIdx.x;
+    for (int k = tid; k < N / 2; k += COL4_THREADS) {
+        const PT2 w = Wg[k];
+        TW[k] = w;
+        TW[k + N / 2] = c2(-w.x, -w.y);
+    }
+    const long long g0 = (long long)blockIdx.x * C;
+    for (int c = tid; c < C; c += COL4_THREADS) {
+        const long long g = g0 + c;
+        const long long sl = g / KX;
+        cbase[c] = g < ncols ? sl * (long long)N * KX + (g - sl * KX) : -1;
+    }
+    __syncthreads();
+    const bool inv = sign > 0;
+    // ---- coalesced load: row y of C consecutive columns, all loads in flight ----
+    {
+        TIN ld[LOADS];
+#pragma unroll
+        for (int it = 0; it < LOADS; ++it) {
+            const int i = tid + it * COL4_THREADS;
+            const int y = i / C, c = i % C;
+            const long long b = i < N * C ? cbase[c] : -1;
+            if (b >= 0) ld[it] = in[b + (long long)y * KX];
+            else ld[it] = TIN{};
+        }
+#pragma unroll
+        for (int it = 0; it < LOADS; ++it) {
+            const int i = tid + it * COL4_THREADS;
+            if (i < N * C) {
+                PT2 v = cvt2<PT2>(ld[it]);
+                if (inv) v.y = -v.y;
+                tile[(i % C) * CS + i / C] = v;
+            }
+        }
+    }
+    __syncthreads();
+    const int q = tid / N1, r = tid - q * N1;
+    for (int c0 = 0; c0 < C; c0 += CR) {
+        PT2* col = tile + (c0 + q) * CS;
+        const bool act = c0 + q < C;
+        PT2 v[N1];
+        // step 1: N1-point FFT over n1 (bit-reversed slots), twiddle
+        if (act && r < N2) {
+#pragma unroll
+            for (int j = 0; j < N1; ++j) v[j] = col[(int)bitrev((unsigned)j, ilog2_ct(N1)) * N2 + r];
+            reg_fft_dit<N1, N2, -1>(v, TW);
+#pragma unroll
+            for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul(v[k1], TW[r * k1]);
+        }
+        __syncthreads();
+        if (act && r < N2) {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) col[k1 * (N2 + 1) + r] = v[k1];
+        }
+        __syncthreads();
+        // step 2: N2-point FFT over n2 for k1 = r
+        PT2 w[N2];
+        if (act) {
+#pragma unroll
+            for (int j = 0; j < N2; ++j) w[j] = col[r * (N2 + 1) + (int)bitrev((unsigned)j, ilog2_ct(N2))];
+            reg_fft_dit<N2, N1, -1>(w, TW);
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) col[r + N1 * k2] = w[k2];
+        }
+    }
+    __syncthreads();
+    // ---- coalesced store ----
+#pragma unroll 4
+    for (int it = 0; it < LOADS; ++it) {
+        const int i = tid + it * COL4_THREADS;
+        const int y = i / C, c = i % C;
+        const long long b = i < N * C ? cbase[c] : -1;
+        if (b < 0) continue;
+        PT2 v = tile[c * CS + y];
+        if (inv) v.y = -v.y;
+        out[b + (long long)y * KX] = cvt2<TOUT>(cscale(v, scale));
+    }
+}
+
 template <typename PT>
 const typename cplx<PT>::t* Wx(expd_plan p);
 template <>
@@ -326,7 +442,7 @@ expd_status launch_row(expd_plan p, const TIN* in, TOUT* out, long long rows, PT
     const size_t smem = (size_t)((NH + 2) & ~1) * sizeof(PT2) + (size_t)R * per_row;
     auto kern = row_kernel<PT, TIN, TOUT, KIND>;
     if (smem > 48 * 1024)
-        EXPD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
     long long blocks = (rows + R - 1) / R;
     if (blocks > (long long)p->sm_count * 16) blocks = (long long)p->sm_count * 16;
     const double in_row = (KIND == 1 ? p->NX : NH + 1) * (double)sizeof(TIN);
@@ -339,10 +455,42 @@ expd_status launch_row(expd_plan p, const TIN* in, TOUT* out, long long rows, PT
     return EXPD_OK;
 }
 
+template <typename PT, typename TIN, typename TOUT, int N1, int N2>
+expd_status launch_col4(expd_plan p, const TIN* in, TOUT* out, int nslices, int sign, PT scale, cudaStream_t s) {
+    typedef typename cplx<PT>::t PT2;
+    constexpr int N = N1 * N2, CS = N + N1 + 1;
+    constexpr int C = col4_columns(N1, N2, (int)sizeof(PT2));
+    const int KX = p->KX;
+    const size_t smem = (size_t)N * sizeof(PT2) + (size_t)C * sizeof(long long) + (size_t)C * CS * sizeof(PT2);
+    auto kern = col4_kernel<PT, TIN, TOUT, N1, N2>;
+    EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
+    const long long ncols = (long long)nslices * KX;
+    const long long grid = (ncols + C - 1) / C;
+    KProf kp(p, s, sizeof(PT) == 4 ? EXPD_K_FFT_COL32 : sizeof(PT) == 8 && !std::is_same<PT, double>::value ? EXPD_K_FFT_COLDD : EXPD_K_FFT_COL,
+             (double)nslices * N * KX * (sizeof(TIN) + sizeof(TOUT)), 5.0 * N * ilog2(N) * (double)KX * nslices);
+    kern<<<(int)grid, COL4_THREADS, smem, s>>>(in, out, ncols, KX, Wy<PT>(p), sign, scale);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
 template <typename PT, typename TIN, typename TOUT>
 expd_status launch_col(expd_plan p, const TIN* in, TOUT* out, int nslices, int sign, PT scale, cudaStream_t s) {
     typedef typename cplx<PT>::t PT2;
     const int NY = p->NY, KX = p->KX;
+    if constexpr (std::is_same<PT, float>::value) {
+        // four-step kernel (float32): 16 to 1024 rows
+        if (!p->no_col4) switch (NY) {
+            case 16: return launch_col4<PT, TIN, TOUT, 4, 4>(p, in, out, nslices, sign, scale, s);
+            case 32: return launch_col4<PT, TIN, TOUT, 8, 4>(p, in, out, nslices, sign, scale, s);
+            case 64: return launch_col4<PT, TIN, TOUT, 8, 8>(p, in, out, nslices, sign, scale, s);
+            case 128: return launch_col4<PT, TIN, TOUT, 16, 8>(p, in, out, nslices, sign, scale, s);
+            case 256: return launch_col4<PT, TIN, TOUT, 16, 16>(p, in, out, nslices, sign, scale, s);
+            case 512: return launch_col4<PT, TIN, TOUT, 32, 16>(p, in, out, nslices, sign, scale, s);
+            case 1024: return launch_col4<PT, TIN, TOUT, 32, 32>(p, in, out, nslices, sign, scale, s);
+            default:
+                break;
+        }
+    }
     const size_t per_col = (size_t)(NY + 1) * sizeof(PT2);
     // 128-byte row segments: 16 float2 or 8 double2 columns per CTA
     const int cmax = sizeof(TIN) == 8 ? 16 : 8;
@@ -350,7 +498,7 @@ expd_status launch_col(expd_plan p, const TIN* in, TOUT* out, int nslices, int s
     const size_t smem = (size_t)(((NY >> 1) + 1) & ~1) * sizeof(PT2) + (size_t)C * per_col;
     auto kern = col_kernel<PT, TIN, TOUT>;
     if (smem > 48 * 1024)
-        EXPD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
     dim3 grid((KX + C - 1) / C, nslices);
     KProf kp(p, s, sizeof(PT) == 4 ? EXPD_K_FFT_COL32 : sizeof(PT) == 8 && !std::is_same<PT, double>::value ? EXPD_K_FFT_COLDD : EXPD_K_FFT_COL,
              (double)nslices * NY * KX * (sizeof(TIN) + sizeof(TOUT)),
@@ -438,7 +586,7 @@ expd_status dst_rows(expd_plan p, const double* in, double* out, long long nrows
     const size_t smem = (size_t)warps * N * sizeof(double2);
     const long long npairs = (nrows + 1) / 2;
     const long long grid = std::min<long long>((npairs + warps - 1) / warps, (long long)p->sm_count * 32);
-    EXPD_CUDA_TRY(cudaFuncSetAttribute(dst_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    EXPD_CUDA_TRY(smem_allow((const void*)dst_rows_kernel, smem));
     KProf kp(p, s, EXPD_K_DST, 16.0 * nrows * n, 5.0 * N * log2N * (double)npairs);
     dst_rows_kernel<<<(int)grid, 32 * warps, smem, s>>>(in, out, nrows, n, log2N, tw, sqrt(2.0 / (n + 1)));
     EXPD_CUDA_TRY(cudaGetLastError());

@@ -283,54 +283,6 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
 constexpr int REG_THREADS = 128;
 constexpr int REG_G = 4;
 
-constexpr int ilog2_ct(int n) { return n <= 1 ? 0 : 1 + ilog2_ct(n >> 1); }
-
-// R-point FFTs on a register array (compile-time indices).  tw[k * TS] =
-// exp(-2 pi i k / R) for k < R/2.  DIT: bit-reversed in -> natural out.
-template <int R, int TS, int SIGN>
-__device__ __forceinline__ void reg_fft_dit(float2 (&v)[R], const float2* tw) {
-#pragma unroll
-    for (int st = 0; st < ilog2_ct(R); ++st) {
-        const int h = 1 << st;
-#pragma unroll
-        for (int b = 0; b < R / 2; ++b) {
-            const int k = b & (h - 1);
-            const int i = ((b >> st) << (st + 1)) + k;
-            float2 t = v[i + h];
-            if (k != 0) {
-                float2 w = tw[k * (R / (2 * h)) * TS];
-                if (SIGN > 0) w.y = -w.y;
-                t = cmul(t, w);
-            }
-            v[i + h] = csub(v[i], t);
-            v[i] = cadd(v[i], t);
-        }
-    }
-}
-
-// DIF: natural in -> bit-reversed out
-template <int R, int TS, int SIGN>
-__device__ __forceinline__ void reg_fft_dif(float2 (&v)[R], const float2* tw) {
-#pragma unroll
-    for (int st = ilog2_ct(R) - 1; st >= 0; --st) {
-        const int h = 1 << st;
-#pragma unroll
-        for (int b = 0; b < R / 2; ++b) {
-            const int k = b & (h - 1);
-            const int i = ((b >> st) << (st + 1)) + k;
-            const float2 u = v[i], t = v[i + h];
-            v[i] = cadd(u, t);
-            float2 d = csub(u, t);
-            if (k != 0) {
-                float2 w = tw[k * (R / (2 * h)) * TS];
-                if (SIGN > 0) w.y = -w.y;
-                d = cmul(d, w);
-            }
-            v[i + h] = d;
-        }
-    }
-}
-
 __device__ __forceinline__ float2 shfl_c(float2 v, int lane) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, lane), __shfl_sync(0xffffffffu, v.y, lane));
 }
@@ -600,7 +552,7 @@ expd_status launch_reg(expd_plan p, TimeArgs& a, cudaStream_t s) {
     const int narr = (a.X ? 1 : 0) + (a.F ? 1 : 0) + (a.NL ? 1 : 0);
     const size_t smem = (size_t)narr * NS * REG_THREADS / REG_G * (size_t)esz;  // R slots per thread
     auto kern = time_reg_kernel<NS, REG_G, ST, REAL>;
-    EXPD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
     kern<<<(int)grid, REG_THREADS, smem, s>>>(a);
     EXPD_CUDA_TRY(cudaGetLastError());
     p->time_grid_used = (int)grid;
@@ -706,7 +658,7 @@ expd_status launch_time(expd_plan p, TimeArgs& a, cudaStream_t s) {
     a.bluestein = t.bluestein;
     const size_t smem = time_smem_bytes(p->Ns, t.L, t.bluestein, sizeof(typename cplx<PT>::t), sizeof(ST));
     auto kern = time_kernel<PT, ST, REAL>;
-    EXPD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
     const double esz = (REAL ? 1.0 : 2.0) * sizeof(ST);
     const double nlsz = (REAL ? 1.0 : 2.0) * (a.nl_f32 ? 4.0 : 8.0);
     const double per = (a.X ? esz : 0.0) + (a.F ? esz : 0.0) + (a.NL ? nlsz : 0.0) + esz;
@@ -808,7 +760,7 @@ expd_status time_grid_for(expd_plan p, int* grid_out) {
     // the float32-sweep variant (the most frequent launch) sets the grid
     const size_t smem = time_smem_bytes(p->Ns, L, blue, sizeof(float2), sizeof(float));
     auto kern = p->realcol ? time_kernel<float, float, true> : time_kernel<float, float, false>;
-    EXPD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
     EXPD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * EXPD_TIME_COLS, smem));
     if (per_sm < 1) per_sm = 1;
     long long grid = (long long)p->sm_count * per_sm;

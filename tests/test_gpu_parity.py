@@ -441,3 +441,23 @@ def test_bicgstab_full_size_heat_dirichlet(expd):
         info = plan.solve_bicgstab(dev(u0), dev(f), U)
     ref = O.sequential_solve(O.spec_of(p), u0, f)[1:]
     assert O.rel_error(host(U), ref) < 1e-8, info
+
+
+# ------------------------------------------- radix-4 shared-memory column FFT --
+@pytest.mark.parametrize("p", [CASES[i] for i in (2, 3, 8, 9)], ids=[IDS[i] for i in (2, 3, 8, 9)])
+def test_radix4_column_fft_path(expd, p, monkeypatch):
+    # EXPD_COL_FFT=radix4 keeps the shared-memory column FFT (used for sizes
+    # the four-step kernel does not take) covered on the small grids
+    monkeypatch.setenv("EXPD_COL_FFT", "radix4")
+    sp = O.spec_of(p)
+    r = rand_field(p, (p.Ns,), 15)
+    S = torch.empty_like(dev(r))
+    rng = np.random.default_rng(16)
+    u0 = rng.uniform(-0.8, 0.8, p.n)
+    f = rng.standard_normal((p.Nt,) + p.n) if p.nonlin == "none" else None
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-12, max_iter=200)) as plan:
+        plan.precond_apply(dev(r), S)
+        plan.solve_fp(dev(u0), None if f is None else dev(f), U)
+    assert relmax(host(S), O.precond_apply(sp, r)) < 6e-8 * 16 / p.alpha
+    assert O.rel_error(host(U), O.sequential_solve(sp, u0, f)[1:]) < 1e-10
