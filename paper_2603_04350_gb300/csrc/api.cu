@@ -461,9 +461,10 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     // (both kernels compute the same sweep; this lets them be compared)
     const char* tk = getenv("EXPD_TIME_KERNEL");
     p->no_reg_time = tk && strcmp(tk, "smem") == 0;
-    // EXPD_COL_FFT=radix4 selects the shared-memory column FFT for every size
-    const char* cf = getenv("EXPD_COL_FFT");
-    p->no_col4 = cf && strcmp(cf, "radix4") == 0;
+    // EXPD_FFT_KERNEL=radix4 selects the shared-memory radix-4 row and column
+    // FFTs for every size (both compute the same transforms)
+    const char* cf = getenv("EXPD_FFT_KERNEL");
+    p->no_fft4 = cf && strcmp(cf, "radix4") == 0;
     return EXPD_OK;
 }
 

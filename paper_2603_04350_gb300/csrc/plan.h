@@ -98,7 +98,7 @@ struct expd_plan_s {
     int partial_cap = 0;          // CTAs the partial-norm buffer has room for
     int time_grid_used = 0;       // CTAs of the last time-kernel launch (for the reduction)
     int no_reg_time = 0;          // 1 forces the shared-memory time kernel (tests)
-    int no_col4 = 0;              // 1 forces the radix-4 shared-memory column FFT (tests)
+    int no_fft4 = 0;              // 1 forces the radix-4 shared-memory row / column FFTs (tests)
     // host-pointer staging (lazy)
     double* stage = nullptr;      // [(2*Nt + 1) * M]
     size_t stage_elems = 0;

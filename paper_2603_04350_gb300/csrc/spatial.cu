@@ -433,10 +433,212 @@ const float2* Wy<float>(expd_plan p) { return p->Wy32; }
 template <>
 const dd2* Wy<dd>(expd_plan p) { return static_cast<const dd2*>(p->Wydd); }
 
+// Contiguous-axis real FFTs of length NX = 2 NH on C rows per CTA, with the
+// length-NH complex FFT done four-step (NH = N1 x N2: register FFTs of N1 and
+// N2 points around one shared-memory transpose, as in col4_kernel).  Rows are
+// staged in shared memory with one contiguous coalesced load (in place is
+// allowed: a CTA reads all its rows before writing any).
+//   KIND 1: real row -> half spectrum X_k, k = 0..NH (forward)
+//   KIND 0: half spectrum -> real row (inverse, times scale)
+//   KIND 2: half spectrum -> real row -> N(u) pointwise -> half spectrum
+// Real data of length 2 NH is packed as z_n = x_{2n} + i x_{2n+1}; the
+// half spectrum and Z = FFT_NH(z) are related by the even/odd split with
+// w^k = exp(-2 pi i k / NX).
+constexpr int ROW4_THREADS = 256;
+
+constexpr int row4_stride(int N1, int N2) {
+    const int need = (N1 * N2 + 1) > N1 * (N2 + 1) ? N1 * N2 + 1 : N1 * (N2 + 1);
+    return need | 1;
+}
+// rows per CTA: one round of ROW4_THREADS / N1 rows (one per thread group)
+constexpr int row4_rows(int N1, int N2, int esz) { return (void)N2, (void)esz, ROW4_THREADS / N1; }
+
+template <typename PT, typename TIN, typename TOUT, int KIND, int N1, int N2>
+__global__ void __launch_bounds__(ROW4_THREADS, 3) row4_kernel(const TIN* in, TOUT* out, long long rows,
+                                                                const typename cplx<PT>::t* __restrict__ Wg,
+                                                                PT scale, int nonlin) {
+    typedef typename cplx<PT>::t PT2;
+    constexpr int NH = N1 * N2, NX = 2 * NH, KXc = NH + 1;
+    constexpr int CS = row4_stride(N1, N2);
+    constexpr int C = row4_rows(N1, N2, (int)sizeof(PT2));
+    constexpr int RR = ROW4_THREADS / N1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PT2* Wn = reinterpret_cast<PT2*>(smem_raw);  // exp(-2 pi i k / NX), k <= NH
+    PT2* TW = Wn + ((KXc + 1) & ~1);             // exp(-2 pi i k / NH), k < NH
+    PT2* tile = TW + NH;
+    const int tid = threadIdx.x;
+    for (int k = tid; k < KXc; k += ROW4_THREADS) Wn[k] = Wg[k];
+    for (int k = tid; k < NH / 2; k += ROW4_THREADS) {
+        const PT2 w = Wg[2 * k];
+        TW[k] = w;
+        TW[k + NH / 2] = c2(-w.x, -w.y);
+    }
+    const long long r0 = (long long)blockIdx.x * C;
+    const int nr = (int)(rows - r0 < C ? rows - r0 : C);
+    // ---- load the CTA's rows: one contiguous block ----
+    if constexpr (KIND == 1) {
+        const TIN* src = in + r0 * NX;
+        for (int e = tid; e < nr * NX; e += ROW4_THREADS) {
+            const int c = e / NX, x = e - c * NX;
+            reinterpret_cast<PT*>(tile + c * CS)[x] = (PT)src[e];
+        }
+    } else {
+        const TIN* src = in + r0 * KXc;
+        for (int e = tid; e < nr * KXc; e += ROW4_THREADS) {
+            const int c = e / KXc, k = e - c * KXc;
+            tile[c * CS + k] = cvt2<PT2>(src[e]);
+        }
+    }
+    __syncthreads();
+    const int q = tid / N1, r = tid - q * N1;
+    for (int c0 = 0; c0 < C; c0 += RR) {
+        PT2* row = tile + (c0 + q) * CS;
+        const bool act = c0 + q < nr;
+        // ---- first transform ----
+        {
+            constexpr int SG1 = KIND == 1 ? -1 : +1;
+            PT2 v[N1];
+            if (act && r < N2) {
+#pragma unroll
+                for (int j = 0; j < N1; ++j) {
+                    const int n = (int)bitrev((unsigned)j, ilog2_ct(N1)) * N2 + r;
+                    if constexpr (KIND == 1) {
+                        v[j] = row[n];
+                    } else {
+                        const PT2 xk = row[n];
+                        const PT2 xm = cconj(row[NH - n]);
+                        const PT2 ev = cscale(cadd(xk, xm), (PT)0.5);
+                        const PT2 od = cmulc(cscale(csub(xk, xm), (PT)0.5), Wn[n]);
+                        v[j] = cadd(ev, cmuli(od));
+                    }
+                }
+                reg_fft_dit<N1, N2, SG1>(v, TW);
+#pragma unroll
+                for (int k1 = 1; k1 < N1; ++k1) {
+                    PT2 w = TW[r * k1];
+                    if (SG1 > 0) w.y = -w.y;
+                    v[k1] = cmul(v[k1], w);
+                }
+            }
+            __syncthreads();
+            if (act && r < N2) {
+#pragma unroll
+                for (int k1 = 0; k1 < N1; ++k1) row[k1 * (N2 + 1) + r] = v[k1];
+            }
+            __syncthreads();
+            PT2 w2[N2];
+            if (act) {
+#pragma unroll
+                for (int j = 0; j < N2; ++j) w2[j] = row[r * (N2 + 1) + (int)bitrev((unsigned)j, ilog2_ct(N2))];
+                reg_fft_dit<N2, N1, SG1>(w2, TW);
+                if constexpr (KIND != 1) {
+#pragma unroll
+                    for (int k2 = 0; k2 < N2; ++k2) {
+                        PT2 z = cscale(w2[k2], scale);
+                        if constexpr (KIND == 2) {
+                            if (nonlin == EXPD_NL_ALLEN_CAHN) z = c2(nl_ac(z.x), nl_ac(z.y));
+                            else z = c2((PT)0, (PT)0);
+                        }
+                        w2[k2] = z;
+                    }
+                }
+            }
+            __syncthreads();
+            if (act) {
+#pragma unroll
+                for (int k2 = 0; k2 < N2; ++k2) row[r + N1 * k2] = w2[k2];
+            }
+            __syncthreads();
+        }
+        // ---- second transform (KIND 2: forward FFT of N(u)) ----
+        if constexpr (KIND == 2) {
+            PT2 v[N1];
+            if (act && r < N2) {
+#pragma unroll
+                for (int j = 0; j < N1; ++j) v[j] = row[(int)bitrev((unsigned)j, ilog2_ct(N1)) * N2 + r];
+                reg_fft_dit<N1, N2, -1>(v, TW);
+#pragma unroll
+                for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul(v[k1], TW[r * k1]);
+            }
+            __syncthreads();
+            if (act && r < N2) {
+#pragma unroll
+                for (int k1 = 0; k1 < N1; ++k1) row[k1 * (N2 + 1) + r] = v[k1];
+            }
+            __syncthreads();
+            PT2 w2[N2];
+            if (act) {
+#pragma unroll
+                for (int j = 0; j < N2; ++j) w2[j] = row[r * (N2 + 1) + (int)bitrev((unsigned)j, ilog2_ct(N2))];
+                reg_fft_dit<N2, N1, -1>(w2, TW);
+            }
+            __syncthreads();
+            if (act) {
+#pragma unroll
+                for (int k2 = 0; k2 < N2; ++k2) row[r + N1 * k2] = w2[k2];
+            }
+            __syncthreads();
+        }
+    }
+    // ---- store: one contiguous block ----
+    if constexpr (KIND == 0) {
+        TOUT* dst = out + r0 * NX;
+        for (int e = tid; e < nr * NX; e += ROW4_THREADS) {
+            const int c = e / NX, x = e - c * NX;
+            dst[e] = (TOUT)reinterpret_cast<const PT*>(tile + c * CS)[x];
+        }
+    } else {
+        // even/odd split: X_k = E_k + w^k O_k from Z_k and conj(Z_{NH-k})
+        TOUT* dst = out + r0 * KXc;
+        for (int e = tid; e < nr * KXc; e += ROW4_THREADS) {
+            const int c = e / KXc, k = e - c * KXc;
+            const PT2* z = tile + c * CS;
+            const PT2 zk = z[k == NH ? 0 : k];
+            const PT2 zm = cconj(z[k == 0 ? 0 : NH - k]);
+            const PT2 ev = cscale(cadd(zk, zm), (PT)0.5);
+            const PT2 od = cscale(cmuli(csub(zm, zk)), (PT)0.5);
+            dst[e] = cvt2<TOUT>(cadd(ev, cmul(Wn[k], od)));
+        }
+    }
+}
+
+template <typename PT, typename TIN, typename TOUT, int KIND, int N1, int N2>
+expd_status launch_row4(expd_plan p, const TIN* in, TOUT* out, long long rows, PT scale, cudaStream_t s) {
+    typedef typename cplx<PT>::t PT2;
+    constexpr int NH = N1 * N2, KXc = NH + 1;
+    constexpr int CS = row4_stride(N1, N2), C = row4_rows(N1, N2, (int)sizeof(PT2));
+    const size_t smem = ((size_t)((KXc + 1) & ~1) + NH + (size_t)C * CS) * sizeof(PT2);
+    auto kern = row4_kernel<PT, TIN, TOUT, KIND, N1, N2>;
+    EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
+    const long long grid = (rows + C - 1) / C;
+    const double in_row = (KIND == 1 ? 2 * NH : KXc) * (double)sizeof(TIN);
+    const double out_row = (KIND == 0 ? 2 * NH : KXc) * (double)sizeof(TOUT);
+    const double fl = (KIND == 2 ? 2.0 : 1.0) * 2.5 * (2 * NH) * ilog2(2 * NH) * (double)rows;
+    KProf kp(p, s, sizeof(PT) == 4 ? EXPD_K_FFT_ROW32 : sizeof(PT) == 8 && !std::is_same<PT, double>::value ? EXPD_K_FFT_ROWDD : EXPD_K_FFT_ROW,
+             (double)rows * (in_row + out_row), fl);
+    kern<<<(int)grid, ROW4_THREADS, smem, s>>>(in, out, rows, Wx<PT>(p), scale, p->nonlin);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
 template <typename PT, typename TIN, typename TOUT, int KIND>
 expd_status launch_row(expd_plan p, const TIN* in, TOUT* out, long long rows, PT scale, cudaStream_t s) {
     typedef typename cplx<PT>::t PT2;
     const int NH = p->NX / 2;
+    if constexpr (std::is_same<PT, float>::value) {
+        // four-step kernel (float32): rows of 32 to 2048 points
+        if (!p->no_fft4) switch (NH) {
+            case 16: return launch_row4<PT, TIN, TOUT, KIND, 4, 4>(p, in, out, rows, scale, s);
+            case 32: return launch_row4<PT, TIN, TOUT, KIND, 8, 4>(p, in, out, rows, scale, s);
+            case 64: return launch_row4<PT, TIN, TOUT, KIND, 8, 8>(p, in, out, rows, scale, s);
+            case 128: return launch_row4<PT, TIN, TOUT, KIND, 16, 8>(p, in, out, rows, scale, s);
+            case 256: return launch_row4<PT, TIN, TOUT, KIND, 16, 16>(p, in, out, rows, scale, s);
+            case 512: return launch_row4<PT, TIN, TOUT, KIND, 32, 16>(p, in, out, rows, scale, s);
+            case 1024: return launch_row4<PT, TIN, TOUT, KIND, 32, 32>(p, in, out, rows, scale, s);
+            default:
+                break;
+        }
+    }
     const size_t per_row = (size_t)NH * sizeof(PT2);
     int R = (int)std::max<size_t>(1, std::min<size_t>(8, (48 * 1024) / per_row));
     const size_t smem = (size_t)((NH + 2) & ~1) * sizeof(PT2) + (size_t)R * per_row;
@@ -479,7 +681,7 @@ expd_status launch_col(expd_plan p, const TIN* in, TOUT* out, int nslices, int s
     const int NY = p->NY, KX = p->KX;
     if constexpr (std::is_same<PT, float>::value) {
         // four-step kernel (float32): 16 to 1024 rows
-        if (!p->no_col4) switch (NY) {
+        if (!p->no_fft4) switch (NY) {
             case 16: return launch_col4<PT, TIN, TOUT, 4, 4>(p, in, out, nslices, sign, scale, s);
             case 32: return launch_col4<PT, TIN, TOUT, 8, 4>(p, in, out, nslices, sign, scale, s);
             case 64: return launch_col4<PT, TIN, TOUT, 8, 8>(p, in, out, nslices, sign, scale, s);

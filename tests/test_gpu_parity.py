@@ -443,12 +443,12 @@ def test_bicgstab_full_size_heat_dirichlet(expd):
     assert O.rel_error(host(U), ref) < 1e-8, info
 
 
-# ------------------------------------------- radix-4 shared-memory column FFT --
+# ------------------------------------- radix-4 shared-memory row / column FFTs --
 @pytest.mark.parametrize("p", [CASES[i] for i in (2, 3, 8, 9)], ids=[IDS[i] for i in (2, 3, 8, 9)])
-def test_radix4_column_fft_path(expd, p, monkeypatch):
-    # EXPD_COL_FFT=radix4 keeps the shared-memory column FFT (used for sizes
-    # the four-step kernel does not take) covered on the small grids
-    monkeypatch.setenv("EXPD_COL_FFT", "radix4")
+def test_radix4_fft_path(expd, p, monkeypatch):
+    # EXPD_FFT_KERNEL=radix4 keeps the shared-memory row and column FFTs (used
+    # for sizes and precisions the four-step kernels do not take) covered
+    monkeypatch.setenv("EXPD_FFT_KERNEL", "radix4")
     sp = O.spec_of(p)
     r = rand_field(p, (p.Ns,), 15)
     S = torch.empty_like(dev(r))
