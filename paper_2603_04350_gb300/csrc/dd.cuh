@@ -12,15 +12,54 @@
 // analysis of an FFT butterfly needs.
 #pragma once
 
+#include <string.h>
+
 #include "common.cuh"
+
+// ---- float64 -> float32 / double-float by integer operations -------------
+// GB300 runs float64 arithmetic and float64 conversions on a pipe 1/58 the
+// rate of float32, so converting a large float64 array is ALU-bound.  These
+// split the binary64 encoding with integer operations instead: sign, the
+// 11-bit exponent e and the 52 fraction bits.
+EXPD_HD unsigned long long f64_bits(double v) {
+#ifdef __CUDA_ARCH__
+    return (unsigned long long)__double_as_longlong(v);
+#else
+    unsigned long long b;
+    memcpy(&b, &v, 8);
+    return b;
+#endif
+}
+EXPD_HD float f32_from_bits(unsigned u) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+#endif
+}
+
+// Round to nearest even, as the hardware conversion; values whose float is
+// subnormal, zero, infinite or NaN take the ordinary conversion.
+EXPD_HD float f32_rn_from_f64(double v) {
+    const unsigned long long b = f64_bits(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 897 || e > 1150) return (float)v;  // outside float's normal range
+    const unsigned long long m = b & 0xfffffffffffffULL;
+    unsigned u = ((unsigned)(b >> 63) << 31) | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29);
+    const unsigned long long tail = m & 0x1fffffffULL;  // the 29 dropped bits
+    if (tail > 0x10000000ULL || (tail == 0x10000000ULL && (u & 1u))) ++u;  // carries into the exponent
+    return f32_from_bits(u);
+}
+
+struct dd;
+EXPD_HD dd dd_from_f64(double v);
 
 struct dd {
     float hi, lo;
     dd() = default;
-    EXPD_HD explicit dd(double v) {
-        hi = (float)v;
-        lo = (float)(v - (double)hi);
-    }
+    EXPD_HD explicit dd(double v);
     EXPD_HD explicit dd(float v) : hi(v), lo(0.0f) {}
     EXPD_HD explicit dd(int v) : hi((float)v), lo(0.0f) {}
     EXPD_HD dd(float h, float l) : hi(h), lo(l) {}
@@ -41,6 +80,30 @@ EXPD_HD dd dd_fast_two_sum(float a, float b) {
     const float s = a + b;
     return dd(s, b - (s - a));
 }
+
+// hi = the leading 24 significand bits (truncated), lo = the next 29 bits
+// rounded to a float, renormalised: hi + lo equals v to 2^-48 relative.
+// |v| < 2^-74 keeps hi only (lo would be subnormal), |v| < 2^-126 gives 0,
+// |v| >= 2^128, infinities and NaN take the float64 path (NaN propagates).
+EXPD_HD dd dd_from_f64(double v) {
+    const unsigned long long b = f64_bits(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const unsigned sgn = (unsigned)(b >> 63) << 31;
+    if (e > 1150) {
+        const float h = (float)v;
+        return dd(h, 0.0f);
+    }
+    if (e < 897) return dd(f32_from_bits(sgn), 0.0f);
+    const unsigned long long m = b & 0xfffffffffffffULL;
+    const float hi = f32_from_bits(sgn | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29));
+    if (e < 949) return dd(hi, 0.0f);
+    // (m mod 2^29) * 2^(e - 1075); 2^(e - 1075) is a normal float for e >= 949
+    float lo = (float)(unsigned)(m & 0x1fffffffULL) * f32_from_bits((unsigned)(e - 948) << 23);
+    if (sgn) lo = -lo;
+    return dd_fast_two_sum(hi, lo);
+}
+
+EXPD_HD dd::dd(double v) { *this = dd_from_f64(v); }
 
 EXPD_HD dd dd_two_sum(float a, float b) {
     const float s = a + b;
@@ -105,7 +168,7 @@ EXPD_HD T2 cvt2(dd2 v);
 template <>
 EXPD_HD double2 cvt2<double2>(double2 v) { return v; }
 template <>
-EXPD_HD float2 cvt2<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+EXPD_HD float2 cvt2<float2>(double2 v) { return make_float2(f32_rn_from_f64(v.x), f32_rn_from_f64(v.y)); }
 template <>
 EXPD_HD dd2 cvt2<dd2>(double2 v) { return to_dd2(v); }
 template <>

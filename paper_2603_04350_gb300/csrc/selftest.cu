@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dd.cuh"
 #include "time_column.cuh"
 
 typedef std::complex<double> cd;
@@ -144,8 +145,41 @@ static void test_column(int Ns, int order, double E, double alpha, double tol, s
     check(sizeof(T) == 8 ? "precond_column double" : "precond_column float", err / scale, tol, Ns, order);
 }
 
+// The integer-path conversions against the hardware ones: round to nearest
+// even for float32 (bit-exact), and |hi + lo - v| <= 2^-47 |v| for
+// double-float, over exponents spanning float's range, zeros and NaN.
+static void test_conversions(std::mt19937_64& rng) {
+    std::uniform_real_distribution<double> frac(1.0, 2.0);
+    std::uniform_int_distribution<int> ex(-140, 140);
+    int bad = 0;
+    double worst = 0;
+    for (int i = 0; i < 400000; ++i) {
+        double v = ldexp(frac(rng), ex(rng));
+        if (i & 1) v = -v;
+        if (i % 97 == 0) v = nextafter((double)(float)v, 0.0);  // near a float tie / boundary
+        const float f = f32_rn_from_f64(v);
+        if (f != (float)v) ++bad;
+        const dd d = dd_from_f64(v);
+        const double r = (double)d.hi + (double)d.lo;
+        if (fabs(v) >= ldexp(1.0, -74) && fabs(v) < ldexp(1.0, 127)) worst = std::max(worst, fabs(r - v) / fabs(v));
+        if (fabs(d.lo) > ldexp(fabs((double)d.hi), -23)) ++bad;  // normalised pair
+    }
+    const double specials[] = {0.0, -0.0, 1.0, -1.0, 3.0e38, -3.4e38, 1e-40, 1e300};
+    for (double v : specials)
+        if (f32_rn_from_f64(v) != (float)v) ++bad;
+    const dd n = dd_from_f64(NAN);
+    if (!(n.hi != n.hi)) ++bad;
+    const dd z = dd_from_f64(0.0);
+    if (z.hi != 0.0f || z.lo != 0.0f) ++bad;
+    if (bad || worst > ldexp(1.0, -47)) {
+        printf("FAIL conversions: %d mismatches, worst double-float error %.3e\n", bad, worst);
+        ++failures;
+    }
+}
+
 int main() {
     std::mt19937_64 rng(1234);
+    test_conversions(rng);
     for (int l = 1; l <= 12; ++l)
         for (int sign = -1; sign <= 1; sign += 2) {
             test_fft<double, double2>(l, sign, 1e-13, rng);

@@ -273,12 +273,12 @@ struct RhsArgs {
     int eshift, s, Ns;
 };
 
+// grid: x over a slice's elements, y over the Ns slices
 __global__ void rhs_kernel(RhsArgs r) {
-    const long long total = r.nelem * r.Ns;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(idx / r.nelem);
-        const long long e = idx - (long long)i * r.nelem;
+    const int i = blockIdx.y;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < r.nelem;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long idx = (long long)i * r.nelem + e;
         const int n = r.s + i;
         double acc = r.fh ? r.bdt * r.fh[(long long)(n - 1) * r.nelem + e] : 0.0;
         if (i < r.s) {
@@ -641,6 +641,7 @@ expd_status launch_row(expd_plan p, const TIN* in, TOUT* out, long long rows, PT
     }
     const size_t per_row = (size_t)NH * sizeof(PT2);
     int R = (int)std::max<size_t>(1, std::min<size_t>(8, (48 * 1024) / per_row));
+    while (R > 1 && (rows + R - 1) / R < 2LL * p->sm_count) R >>= 1;  // small launches: more CTAs
     const size_t smem = (size_t)((NH + 2) & ~1) * sizeof(PT2) + (size_t)R * per_row;
     auto kern = row_kernel<PT, TIN, TOUT, KIND>;
     if (smem > 48 * 1024)
@@ -697,6 +698,8 @@ expd_status launch_col(expd_plan p, const TIN* in, TOUT* out, int nslices, int s
     // 128-byte row segments: 16 float2 or 8 double2 columns per CTA
     const int cmax = sizeof(TIN) == 8 ? 16 : 8;
     int C = (int)std::max<size_t>(1, std::min<size_t>(cmax, (64 * 1024) / per_col));
+    // small launches (a slice or two): fewer columns per CTA, more CTAs
+    while (C > 1 && (long long)((KX + C - 1) / C) * nslices < 2LL * p->sm_count) C >>= 1;
     const size_t smem = (size_t)(((NY >> 1) + 1) & ~1) * sizeof(PT2) + (size_t)C * per_col;
     auto kern = col_kernel<PT, TIN, TOUT>;
     if (smem > 48 * 1024)
@@ -1027,7 +1030,8 @@ expd_status assemble_rhs(expd_plan p, const void* fh, cudaStream_t s) {
     r.s = p->order;
     r.Ns = p->Ns;
     KProf kp(p, s, EXPD_K_POINTWISE, 8.0 * r.nelem * ((fh ? 2.0 : 1.0) * r.Ns + r.s), 2.0 * r.nelem * r.s * r.s);
-    rhs_kernel<<<grid_for(r.nelem * r.Ns, 256), 256, 0, s>>>(r);
+    const long long bx = std::max(1LL, std::min<long long>((r.nelem + 255) / 256, (4LL * p->sm_count * 8) / r.Ns + 1));
+    rhs_kernel<<<dim3((unsigned)bx, (unsigned)r.Ns), 256, 0, s>>>(r);
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }
