@@ -91,28 +91,38 @@ bool is_device_ptr(const void* ptr) {
 // Pinned host words for the per-sweep norm read-back, handed out from one
 // process-wide arena (freeing pinned memory would synchronise the device).
 std::mutex g_pin_mu;
-std::vector<double*> g_pin_free;
 
-double* pinned_acquire() {
+// Blocks of 2^c doubles (c >= 3), carved from pinned chunks that are never
+// freed; released blocks return to their size class's free list.
+std::vector<double*> g_pin_class[24];
+
+double* pinned_acquire(size_t ndoubles) {
+    int c = 3;
+    while (((size_t)1 << c) < ndoubles) ++c;
+    if (c >= 24) return nullptr;
     std::lock_guard<std::mutex> lk(g_pin_mu);
-    if (g_pin_free.empty()) {
-        const int slots = 256;
-        double* arena = nullptr;
-        if (cudaMallocHost(&arena, (size_t)slots * 8 * sizeof(double)) != cudaSuccess) {
+    std::vector<double*>& fl = g_pin_class[c];
+    if (fl.empty()) {
+        const size_t block = (size_t)1 << c;
+        const size_t count = std::max<size_t>(1, ((size_t)64 << 10) / (block * sizeof(double)));
+        double* chunk = nullptr;
+        if (cudaMallocHost(&chunk, count * block * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
-        for (int i = slots - 1; i >= 0; --i) g_pin_free.push_back(arena + (size_t)i * 8);
+        for (size_t i = count; i-- > 0;) fl.push_back(chunk + i * block);
     }
-    double* r = g_pin_free.back();
-    g_pin_free.pop_back();
+    double* r = fl.back();
+    fl.pop_back();
     return r;
 }
 
-void pinned_release(double* q) {
+void pinned_release(double* q, size_t ndoubles) {
     if (!q) return;
+    int c = 3;
+    while (((size_t)1 << c) < ndoubles) ++c;
     std::lock_guard<std::mutex> lk(g_pin_mu);
-    g_pin_free.push_back(q);
+    g_pin_class[c].push_back(q);
 }
 
 expd_status dalloc(expd_plan p, void** ptr, size_t bytes, const char* what) {
@@ -144,7 +154,7 @@ void free_plan(expd_plan p) {
                     p->Uh,   p->Fh,   p->Sh,     p->fh,      p->NL64,    p->NL32,      p->work64,
                     p->work32, p->startphys, p->partial, p->redout, p->stage, p->gm, p->U32, p->F32};
     for (void* b : bufs) plan_free(p, b);
-    pinned_release(p->redhost);
+    pinned_release(p->redhost, 2 * (size_t)p->Ns);
     for (cudaEvent_t e : p->events) cudaEventDestroy(e);
     time_tables_free(p);
     delete p;
@@ -212,7 +222,8 @@ void* eig_slice(expd_plan p, void* base, long long n) {
 // ---- startup values and f_s ----------------------------------------------------
 // Sh[n] (eigen) and startphys[n] (physical) for n = 0..s-1, fh (eigen source)
 // when f is given, and the assembled right-hand side Fh.
-expd_status setup_start(expd_plan p, const double* u0, const double* f, const double* Ugiven, cudaStream_t s) {
+expd_status setup_start(expd_plan p, const double* u0, const double* f, const double* Ugiven, cudaStream_t s,
+                        float* F32 = nullptr, int fh_dd = 0) {
     const size_t M = (size_t)p->M;
     const int so = p->order;
     EXPD_CUDA_TRY(cudaMemcpyAsync(p->startphys, u0, M * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -257,15 +268,31 @@ expd_status setup_start(expd_plan p, const double* u0, const double* f, const do
         }
         if (st != EXPD_OK) return st;
     }
-    return assemble_rhs(p, f ? p->fh : nullptr, s);
+    return assemble_rhs(p, f ? p->fh : nullptr, s, F32, fh_dd);
 }
 
+// out = {sqrt(max_n ||s_n||^2), sqrt(max_n ||x_n||^2), sum_n ||s_n||^2, sum_n ||x_n||^2}
+// from the per-slice totals, in slice order; the max propagates NaN (fmax
+// would drop it and hide a diverged iterate)
 expd_status read_norms(expd_plan p, cudaStream_t s, double out[4]) {
     expd_status st = time_reduce(p, s);
     if (st != EXPD_OK) return st;
-    EXPD_CUDA_TRY(cudaMemcpyAsync(p->redhost, p->redout, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    const size_t nb = 2 * (size_t)p->Ns * sizeof(double);
+    EXPD_CUDA_TRY(cudaMemcpyAsync(p->redhost, p->redout + 8, nb, cudaMemcpyDeviceToHost, s));
     EXPD_CUDA_TRY(cudaStreamSynchronize(s));
-    for (int i = 0; i < 4; ++i) out[i] = p->redhost[i];
+    auto nanmax = [](double a, double b) { return (a != a || b != b) ? NAN : std::max(a, b); };
+    double m0 = 0, m1 = 0, s0 = 0, s1 = 0;
+    for (int n = 0; n < p->Ns; ++n) {
+        const double a = p->redhost[2 * n], b = p->redhost[2 * n + 1];
+        m0 = nanmax(m0, a);
+        m1 = nanmax(m1, b);
+        s0 += a;
+        s1 += b;
+    }
+    out[0] = sqrt(m0);
+    out[1] = sqrt(m1);
+    out[2] = s0;
+    out[3] = s1;
     return EXPD_OK;
 }
 
@@ -656,14 +683,14 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
         st = dalloc(p, &p->U32, vec / 2, "iterate (float32)");
         if (st == EXPD_OK) st = dalloc(p, &p->F32, vec / 2, "right-hand side (float32)");
     }
-    // norms: [0..3] results, [6] election counter of the reduction, [8..] per-slice totals
+    // norms: [8..] per-slice totals of the update and iterate norms (the host reduces them)
     if (st == EXPD_OK) st = dalloc(p, reinterpret_cast<void**>(&p->redout), (8 + 2 * (size_t)p->Ns) * sizeof(double), "norms");
     if (st == EXPD_OK) {
         cudaError_t e = cudaMemsetAsync(p->redout, 0, (8 + 2 * (size_t)p->Ns) * sizeof(double), s);
         if (e != cudaSuccess) st = expd_cuda_fail(e, "cudaMemsetAsync(norms)", __FILE__, __LINE__);
     }
     if (st == EXPD_OK) {
-        p->redhost = pinned_acquire();
+        p->redhost = pinned_acquire(2 * (size_t)p->Ns);
         if (!p->redhost) st = expd_fail(EXPD_ERR_OOM, "pinned host memory for the norms");
     }
     if (st == EXPD_OK) st = time_tables_build(p, s);
@@ -866,10 +893,14 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     Staging sg;
     expd_status st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
     if (st != EXPD_OK) return st;
-    st = setup_start(p, sg.u0, sg.f, sg.U, s);
-    if (st != EXPD_OK) return st;
     const bool nl = p->nonlin != EXPD_NL_NONE;
     const bool mixed = p->precision == EXPD_PREC_MIXED;
+    // the mixed path's right-hand side comes out of its assembly in float32
+    // and, for the double-float phase, as double-float pairs
+    const bool start32 = mixed && p->U32 != nullptr;
+    const bool dd_rhs = start32 && p->bc == EXPD_BC_PERIODIC && p->Cdd != nullptr;
+    st = setup_start(p, sg.u0, sg.f, sg.U, s, start32 ? static_cast<float*>(p->F32) : nullptr, dd_rhs ? 1 : 0);
+    if (st != EXPD_OK) return st;
     const long long nelem = p->Mcol * (p->realcol ? 1 : 2);
     const long long nvec = (long long)p->Ns * nelem;
     // Mixed path: float32 sweeps (iterate, right-hand side, residual, N and the
@@ -882,8 +913,6 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     const bool use_dd = mixed && p->bc == EXPD_BC_PERIODIC && p->Cdd != nullptr;
     int phase = (mixed && p->U32 != nullptr) ? PH32 : PH64;
     if (phase == PH32) {
-        st = convert_f64_to_f32(p, static_cast<const double*>(p->Fh), static_cast<float*>(p->F32), nvec, s);
-        if (st != EXPD_OK) return st;
         EXPD_CUDA_TRY(cudaMemsetAsync(p->U32, 0, (size_t)nvec * sizeof(float), s));
     } else {
         EXPD_CUDA_TRY(cudaMemsetAsync(p->Uh, 0, (size_t)nvec * sizeof(double), s));
@@ -893,8 +922,7 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     auto leave32 = [&]() -> expd_status {
         expd_status r;
         if (use_dd) {
-            r = convert_f32_to_dd(p, static_cast<const float*>(p->U32), p->Uh, nvec, s);
-            if (r == EXPD_OK) r = convert_f64_to_dd_inplace(p, static_cast<double*>(p->Fh), nvec, s);
+            r = convert_f32_to_dd(p, static_cast<const float*>(p->U32), p->Uh, nvec, s);  // Fh is double-float already
             phase = PHDD;
         } else {
             r = convert_f32_to_f64(p, static_cast<const float*>(p->U32), static_cast<double*>(p->Uh), nvec, s);
@@ -902,6 +930,16 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
         }
         return r;
     };
+    // Output of a nonlinear double-float solve: the last sweep's N evaluation
+    // leaves the physical iterate before that sweep's update in U (float64), and
+    // its time kernel a float32 copy of the update s; U + inverse transform of
+    // s in float32 is the solution (the update is orders of magnitude below U,
+    // so float32 rounding of its transform is far below the tolerance), which
+    // replaces the double-float output transform.
+    double* phys_out = sg.U + (size_t)(p->order - 1) * p->M;
+    const bool fast_out = use_dd && nl && inverse32_accum_supported(p);
+    bool phys_valid = false;
+    double last_rel = 1.0;
     double prev = 0.0, rho = 0.5, rho_phase = -1.0, measure = 1.0, s_first = 0.0;
     int it = 0, it32 = 0;
     expd_status result = EXPD_ERR_NOT_CONVERGED;
@@ -924,7 +962,8 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
                 op.nl_f32 = 1;
             } else if (phase == PHDD) {
                 NL = p->NL64;  // holds double-float values in this phase
-                st = nonlinear_eval_dd(p, op.X, NL, s);
+                st = nonlinear_eval_dd(p, op.X, NL, s, fast_out ? phys_out : nullptr);
+                if (fast_out) op.sout = p->U32;  // free in this phase
             } else {
                 NL = p->NL64;
                 st = nonlinear_eval(p, op.X, NL, 0, s, 0);
@@ -935,11 +974,13 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
         }
         st = time_apply(p, op, s);
         if (st != EXPD_OK) return st;
+        phys_valid = op.sout != nullptr;
         double nr[4];
         st = read_norms(p, s, nr);
         if (st != EXPD_OK) return st;
         if (used32) ++it32;
         const double smax = nr[0], umax = nr[1];
+        last_rel = umax > 0 ? smax / umax : 1.0;
         if (it == 1) s_first = smax;
         if (!isfinite(smax) || !isfinite(umax) || !isfinite(nr[2]) || !isfinite(nr[3]) ||
             (it > 1 && smax > 1e3 * s_first)) {
@@ -984,7 +1025,14 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
         info->fp32_iterations = it32;
         info->final_measure = measure;
     }
-    st = write_solution(p, sg.U, s, phase == PHDD);
+    if (phase == PHDD && phys_valid && last_rel <= 1e-4) {
+        if (p->order > 1)
+            EXPD_CUDA_TRY(cudaMemcpyAsync(sg.U, p->startphys + p->M, (size_t)(p->order - 1) * p->M * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, s));
+        st = spatial_inverse32_accum(p, p->U32, phys_out, s);
+    } else {
+        st = write_solution(p, sg.U, s, phase == PHDD);
+    }
     if (st != EXPD_OK) return st;
     st = stage_out(p, sg, s);
     if (st != EXPD_OK) return st;

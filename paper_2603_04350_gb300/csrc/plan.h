@@ -90,8 +90,8 @@ struct expd_plan_s {
     void* F32 = nullptr;       // [Ns][Mcol] float32 copy of Fh
     double* startphys = nullptr;  // [order][M] physical u_0..u_{s-1}
     double2* partial = nullptr;   // [Ns][time grid] per-slice norm partials
-    double* redout = nullptr;     // [4] reduced norms (device)
-    double* redhost = nullptr;    // [4] pinned host copy
+    double* redout = nullptr;     // [8 + 2 Ns]: per-slice totals (||res_n||^2, ||X_n||^2) from [8] (device)
+    double* redhost = nullptr;    // [2 Ns] pinned host copy of the per-slice totals
     cudaStream_t stream = nullptr; // stream of the most recent call: allocations and frees are ordered on it
     int pooled = 0;               // device supports stream-ordered allocation
     int time_grid = 0;            // CTAs of the time kernel (multiple of SM count)
@@ -161,7 +161,12 @@ expd_status convert_f32_to_f64(expd_plan p, const float* in, double* out, long l
 // double-float ("dd", float hi + float lo) helpers of the mixed path's accurate phase
 expd_status convert_f64_to_dd_inplace(expd_plan p, double* a, long long n, cudaStream_t s);
 expd_status convert_f32_to_dd(expd_plan p, const float* in, void* out, long long n, cudaStream_t s);
-expd_status nonlinear_eval_dd(expd_plan p, const void* Uh, void* out, cudaStream_t s);
+// phys (optional): the physical rows before N, float64 [Ns][NY][NX]
+expd_status nonlinear_eval_dd(expd_plan p, const void* Uh, void* out, cudaStream_t s, double* phys = nullptr);
+// phys += inverse transform of a float32 half-spectrum [Ns][NY][KX] (float32
+// four-step kernels; periodic grids with NX in 32..2048, NY in 16..1024)
+bool inverse32_accum_supported(expd_plan p);
+expd_status spatial_inverse32_accum(expd_plan p, const void* eig, double* phys, cudaStream_t s);
 expd_status spatial_inverse_dd(expd_plan p, const void* eig, double* phys, int nslices, cudaStream_t s);
 // u = solution of u - bdt N(u) = w, pointwise (float64 physical).
 expd_status pointwise_solve(expd_plan p, const double* w, double* u, long long n, double bdt, cudaStream_t s);
@@ -169,13 +174,15 @@ expd_status pointwise_solve(expd_plan p, const double* w, double* u, long long n
 expd_status eigen_combine(expd_plan p, void* out, const void* const* in, const double* coef, int q,
                           const void* src, double g, cudaStream_t s);
 // f_s: Fh[i] = bdt f^(s+i) + sum_{j: s+i-j<s} a_j E^j Sh[s+i-j]
-expd_status assemble_rhs(expd_plan p, const void* fh, cudaStream_t s);
+// F32 (optional): also the float32 copy; fh_dd: Fh stored as double-float pairs
+expd_status assemble_rhs(expd_plan p, const void* fh, cudaStream_t s, float* F32 = nullptr, int fh_dd = 0);
 
 // ---- time direction (time_kernel.cu) -----------------------------------------
 struct TimeOp {
     const void* X = nullptr;   // state / operand in the eigenbasis (may be null)
     const void* F = nullptr;   // additive right-hand side (may be null)
     const void* NL = nullptr;  // transformed nonlinearity (may be null)
+    void* sout = nullptr;      // optional copy of the update s in float32 (accum mode)
     int nl_f32 = 0;
     double bdt = 0;            // coefficient of NL
     double sigR = -1;          // coefficient of R_s X
@@ -187,8 +194,8 @@ struct TimeOp {
     int stdd = 0;              // X, F, NL, out and the residual arithmetic in double-float
 };
 expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s);
-// reduce per-slice partials: redout[0] = max_n ||res_n||, [1] = max_n ||X_n||,
-// [2] = sum_n ||res_n||^2, [3] = sum_n ||X_n||^2 (weighted eigen norms).
+// per-slice totals of the time kernel's CTA partials into redout[8..]:
+// (||res_n||^2, ||X_n||^2) per slice n (weighted eigen norms), fixed order.
 expd_status time_reduce(expd_plan p, cudaStream_t s);
 expd_status time_tables_build(expd_plan p, cudaStream_t s);
 // CTAs of the time kernel: SM count x resident CTAs, at most the tile count (no allocation)

@@ -34,7 +34,8 @@ __device__ __forceinline__ R nl_ac(R u) { return u - u * u * u; }
 // KIND 2: c2r, u -> N(u), r2c (fused nonlinear evaluation)
 template <typename PT, typename TIN, typename TOUT, int KIND>
 __global__ void row_kernel(const TIN* in, TOUT* out, long long rows, int NX,
-                           int log2NH, const typename cplx<PT>::t* __restrict__ Wg, PT scale, int nonlin) {
+                           int log2NH, const typename cplx<PT>::t* __restrict__ Wg, PT scale, int nonlin,
+                           double* phys) {
     typedef typename cplx<PT>::t PT2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int NH = NX >> 1;
@@ -76,6 +77,10 @@ __global__ void row_kernel(const TIN* in, TOUT* out, long long rows, int NX,
         if constexpr (KIND == 2) {
             for (int n = lane; n < NH; n += 32) {
                 PT2 z = cscale(s[n], scale);
+                if (phys) {  // the physical row before N, in float64 (phys[row][NX])
+                    phys[row * NX + 2 * n] = (double)z.x;
+                    phys[row * NX + 2 * n + 1] = (double)z.y;
+                }
                 if (nonlin == EXPD_NL_ALLEN_CAHN) z = c2(nl_ac(z.x), nl_ac(z.y));
                 else z = c2((PT)0, (PT)0);
                 s[n] = z;
@@ -266,6 +271,8 @@ struct RhsArgs {
     const double* fh;  // [Nt][nelem] or null
     const double* Sh;  // [s][nelem]
     double* Fh;        // [Ns][nelem]
+    float* F32;        // optional float32 copy [Ns][nelem]
+    int fh_dd;         // write Fh as double-float (hi, lo) instead of float64
     const double* E;
     double a[7];
     double bdt;
@@ -289,7 +296,9 @@ __global__ void rhs_kernel(RhsArgs r) {
                 if (n - j < r.s) acc = fma(r.a[j] * Ej, r.Sh[(long long)(n - j) * r.nelem + e], acc);
             }
         }
-        r.Fh[idx] = acc;
+        if (r.F32) r.F32[idx] = f32_rn_from_f64(acc);
+        if (r.fh_dd) reinterpret_cast<dd*>(r.Fh)[idx] = dd_from_f64(acc);
+        else r.Fh[idx] = acc;
     }
 }
 
@@ -441,6 +450,7 @@ const dd2* Wy<dd>(expd_plan p) { return static_cast<const dd2*>(p->Wydd); }
 //   KIND 1: real row -> half spectrum X_k, k = 0..NH (forward)
 //   KIND 0: half spectrum -> real row (inverse, times scale)
 //   KIND 2: half spectrum -> real row -> N(u) pointwise -> half spectrum
+//   KIND 3: as KIND 0, added to the output row (out += result)
 // Real data of length 2 NH is packed as z_n = x_{2n} + i x_{2n+1}; the
 // half spectrum and Z = FFT_NH(z) are related by the even/odd split with
 // w^k = exp(-2 pi i k / NX).
@@ -462,6 +472,7 @@ __global__ void __launch_bounds__(ROW4_THREADS, 3) row4_kernel(const TIN* in, TO
     constexpr int CS = row4_stride(N1, N2);
     constexpr int C = row4_rows(N1, N2, (int)sizeof(PT2));
     constexpr int RR = ROW4_THREADS / N1;
+    constexpr bool C2R = KIND == 0 || KIND == 3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PT2* Wn = reinterpret_cast<PT2*>(smem_raw);  // exp(-2 pi i k / NX), k <= NH
     PT2* TW = Wn + ((KXc + 1) & ~1);             // exp(-2 pi i k / NH), k < NH
@@ -581,11 +592,13 @@ __global__ void __launch_bounds__(ROW4_THREADS, 3) row4_kernel(const TIN* in, TO
         }
     }
     // ---- store: one contiguous block ----
-    if constexpr (KIND == 0) {
+    if constexpr (C2R) {
         TOUT* dst = out + r0 * NX;
         for (int e = tid; e < nr * NX; e += ROW4_THREADS) {
             const int c = e / NX, x = e - c * NX;
-            dst[e] = (TOUT)reinterpret_cast<const PT*>(tile + c * CS)[x];
+            const TOUT v = (TOUT)reinterpret_cast<const PT*>(tile + c * CS)[x];
+            if constexpr (KIND == 3) dst[e] += v;
+            else dst[e] = v;
         }
     } else {
         // even/odd split: X_k = E_k + w^k O_k from Z_k and conj(Z_{NH-k})
@@ -612,7 +625,7 @@ expd_status launch_row4(expd_plan p, const TIN* in, TOUT* out, long long rows, P
     EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
     const long long grid = (rows + C - 1) / C;
     const double in_row = (KIND == 1 ? 2 * NH : KXc) * (double)sizeof(TIN);
-    const double out_row = (KIND == 0 ? 2 * NH : KXc) * (double)sizeof(TOUT);
+    const double out_row = (KIND == 0 ? 2 * NH : KIND == 3 ? 4 * NH : KXc) * (double)sizeof(TOUT);
     const double fl = (KIND == 2 ? 2.0 : 1.0) * 2.5 * (2 * NH) * ilog2(2 * NH) * (double)rows;
     KProf kp(p, s, sizeof(PT) == 4 ? EXPD_K_FFT_ROW32 : sizeof(PT) == 8 && !std::is_same<PT, double>::value ? EXPD_K_FFT_ROWDD : EXPD_K_FFT_ROW,
              (double)rows * (in_row + out_row), fl);
@@ -622,7 +635,12 @@ expd_status launch_row4(expd_plan p, const TIN* in, TOUT* out, long long rows, P
 }
 
 template <typename PT, typename TIN, typename TOUT, int KIND>
-expd_status launch_row(expd_plan p, const TIN* in, TOUT* out, long long rows, PT scale, cudaStream_t s) {
+expd_status launch_row_r4(expd_plan p, const TIN* in, TOUT* out, long long rows, PT scale, cudaStream_t s,
+                          double* phys);
+
+template <typename PT, typename TIN, typename TOUT, int KIND>
+expd_status launch_row(expd_plan p, const TIN* in, TOUT* out, long long rows, PT scale, cudaStream_t s,
+                       double* phys = nullptr) {
     typedef typename cplx<PT>::t PT2;
     const int NH = p->NX / 2;
     if constexpr (std::is_same<PT, float>::value) {
@@ -639,6 +657,19 @@ expd_status launch_row(expd_plan p, const TIN* in, TOUT* out, long long rows, PT
                 break;
         }
     }
+    if constexpr (KIND == 3) {
+        return expd_fail(EXPD_ERR_UNSUPPORTED, "accumulating c2r needs a float32 row of 32..2048 points");
+    } else {
+        return launch_row_r4<PT, TIN, TOUT, KIND>(p, in, out, rows, scale, s, phys);
+    }
+}
+
+// the radix-4 shared-memory row kernel (every size and precision)
+template <typename PT, typename TIN, typename TOUT, int KIND>
+expd_status launch_row_r4(expd_plan p, const TIN* in, TOUT* out, long long rows, PT scale, cudaStream_t s,
+                          double* phys) {
+    typedef typename cplx<PT>::t PT2;
+    const int NH = p->NX / 2;
     const size_t per_row = (size_t)NH * sizeof(PT2);
     int R = (int)std::max<size_t>(1, std::min<size_t>(8, (48 * 1024) / per_row));
     while (R > 1 && (rows + R - 1) / R < 2LL * p->sm_count) R >>= 1;  // small launches: more CTAs
@@ -653,7 +684,7 @@ expd_status launch_row(expd_plan p, const TIN* in, TOUT* out, long long rows, PT
     const double fl = (KIND == 2 ? 2.0 : 1.0) * 2.5 * p->NX * ilog2(p->NX) * (double)rows;
     KProf kp(p, s, sizeof(PT) == 4 ? EXPD_K_FFT_ROW32 : sizeof(PT) == 8 && !std::is_same<PT, double>::value ? EXPD_K_FFT_ROWDD : EXPD_K_FFT_ROW,
              (double)rows * (in_row + out_row), fl);
-    kern<<<(int)blocks, 32 * R, smem, s>>>(in, out, rows, p->NX, ilog2(NH), Wx<PT>(p), scale, p->nonlin);
+    kern<<<(int)blocks, 32 * R, smem, s>>>(in, out, rows, p->NX, ilog2(NH), Wx<PT>(p), scale, p->nonlin, phys);
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }
@@ -955,17 +986,35 @@ expd_status convert_f32_to_f64(expd_plan p, const float* in, double* out, long l
     return EXPD_OK;
 }
 
-expd_status nonlinear_eval_dd(expd_plan p, const void* Uh, void* out, cudaStream_t s) {
+expd_status nonlinear_eval_dd(expd_plan p, const void* Uh, void* out, cudaStream_t s, double* phys) {
     if (p->bc != EXPD_BC_PERIODIC) return expd_fail(EXPD_ERR_INVALID_ARG, "double-float N needs a periodic grid");
     const dd2* U = static_cast<const dd2*>(Uh);
     dd2* o = static_cast<dd2*>(out);
     const long long rows = (long long)p->Ns * p->NY;
     const dd sx(1.0 / (p->NX / 2));
-    if (p->ndim == 1) return launch_row<dd, dd2, dd2, 2>(p, U, o, rows, sx, s);
+    if (p->ndim == 1) return launch_row<dd, dd2, dd2, 2>(p, U, o, rows, sx, s, phys);
     dd2* w = static_cast<dd2*>(p->work64);
     expd_status st = launch_col<dd, dd2, dd2>(p, U, w, p->Ns, +1, dd(1.0 / p->NY), s);
-    if (st == EXPD_OK) st = launch_row<dd, dd2, dd2, 2>(p, w, w, rows, sx, s);
+    if (st == EXPD_OK) st = launch_row<dd, dd2, dd2, 2>(p, w, w, rows, sx, s, phys);
     if (st == EXPD_OK) st = launch_col<dd, dd2, dd2>(p, w, o, p->Ns, -1, dd(1.0), s);
+    return st;
+}
+
+bool inverse32_accum_supported(expd_plan p) {
+    if (p->bc != EXPD_BC_PERIODIC || p->no_fft4 || !p->work32) return false;
+    auto pow2 = [](int n) { return n >= 16 && n <= 1024 && (n & (n - 1)) == 0; };
+    return p->NX >= 32 && p->NX <= 2048 && ((p->NX / 2) & (p->NX / 2 - 1)) == 0 && (p->ndim == 1 || pow2(p->NY));
+}
+
+expd_status spatial_inverse32_accum(expd_plan p, const void* eig, double* phys, cudaStream_t s) {
+    if (!inverse32_accum_supported(p)) return expd_fail(EXPD_ERR_UNSUPPORTED, "float32 accumulating inverse transform");
+    const float2* y = static_cast<const float2*>(eig);
+    const float sx = 1.0f / (float)(p->NX / 2);
+    const long long rows = (long long)p->Ns * p->NY;
+    if (p->ndim == 1) return launch_row<float, float2, double, 3>(p, y, phys, rows, sx, s);
+    float2* w = static_cast<float2*>(p->work32);
+    expd_status st = launch_col<float, float2, float2>(p, y, w, p->Ns, +1, 1.0f / (float)p->NY, s);
+    if (st == EXPD_OK) st = launch_row<float, float2, double, 3>(p, w, phys, rows, sx, s);
     return st;
 }
 
@@ -1017,11 +1066,13 @@ expd_status eigen_combine(expd_plan p, void* out, const void* const* in, const d
     return EXPD_OK;
 }
 
-expd_status assemble_rhs(expd_plan p, const void* fh, cudaStream_t s) {
+expd_status assemble_rhs(expd_plan p, const void* fh, cudaStream_t s, float* F32, int fh_dd) {
     RhsArgs r;
     r.fh = static_cast<const double*>(fh);
     r.Sh = static_cast<const double*>(p->Sh);
     r.Fh = static_cast<double*>(p->Fh);
+    r.F32 = F32;
+    r.fh_dd = fh_dd;
     r.E = p->E;
     for (int j = 0; j < 7; ++j) r.a[j] = p->acoef[p->order][j];
     r.bdt = p->beta[p->order] * p->dt;

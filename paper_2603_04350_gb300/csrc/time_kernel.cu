@@ -41,6 +41,7 @@ struct TimeArgs {
     const void* F;
     const void* NL;
     void* out;
+    void* sout;  // optional float32 copy of the update (accum mode)
     int nl_f32;
     double bdt, sigR;
     int precond, accum;
@@ -246,6 +247,7 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
                     const ST2 xn = cadd(sX[c * P + n], res);
                     stcol<ST, REAL>(const_cast<void*>(A.X), g, xn);
                     nrm.y = wgt * fma(xn.x, xn.x, xn.y * xn.y);
+                    if (A.sout) stcol<float, REAL>(A.sout, g, cvt2<float2>(res));
                 } else {
                     stcol<ST, REAL>(A.out, g, res);
                 }
@@ -281,7 +283,9 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
 // lanes by shuffles.  Per-slice norms are reduced over the warp's groups with a
 // transpose-reduce and over the CTA in shared memory.
 constexpr int REG_THREADS = 128;
-constexpr int REG_G = 4;
+// lanes per column (4: measured faster than 8 lanes with 8 slices each, whose
+// third cross-lane stage costs more than the extra occupancy gains)
+constexpr int reg_lanes(int NS) { return (void)NS, 4; }
 
 __device__ __forceinline__ float2 shfl_c(float2 v, int lane) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, lane), __shfl_sync(0xffffffffu, v.y, lane));
@@ -292,6 +296,10 @@ __device__ __forceinline__ float2 shfl_xor_c(float2 v, int m) {
 __device__ __forceinline__ double2 shfl_c(double2 v, int lane) {
     return make_double2(__shfl_sync(0xffffffffu, v.x, lane), __shfl_sync(0xffffffffu, v.y, lane));
 }
+__device__ __forceinline__ dd shfl_d(dd v, int lane) {
+    return dd(__shfl_sync(0xffffffffu, v.hi, lane), __shfl_sync(0xffffffffu, v.lo, lane));
+}
+__device__ __forceinline__ dd2 shfl_c(dd2 v, int lane) { return c2(shfl_d(v.x, lane), shfl_d(v.y, lane)); }
 
 // Asynchronous global -> shared copy of one element (4, 8 or 16 bytes); a
 // source size of 0 fills the destination with zeros (columns past the end).
@@ -309,7 +317,10 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-template <int NS, int G, typename ST, bool REAL>
+// STAGE_ALL: X, F and N(u) staged through shared memory; otherwise only X (read
+// twice) is staged and F, N(u) are loaded where they are used (wide elements
+// would otherwise limit the CTAs per SM by shared memory).
+template <int NS, int G, typename ST, bool REAL, bool STAGE_ALL>
 __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
     typedef typename cplx<ST>::t ST2;
     constexpr int R = NS / G;
@@ -372,8 +383,10 @@ __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
         for (int j = 0; j < R; ++j) {
             const long long gi = (long long)(G * j + g) * Mcol + mm;
             if (A.X) cp_async_elem<ESZ>(&stage[(ix * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.X) + gi, valid);
-            if (A.F) cp_async_elem<ESZ>(&stage[(iF * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.F) + gi, valid);
-            if (A.NL) cp_async_elem<ESZ>(&stage[(iN * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.NL) + gi, valid);
+            if (STAGE_ALL && A.F)
+                cp_async_elem<ESZ>(&stage[(iF * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.F) + gi, valid);
+            if (STAGE_ALL && A.NL)
+                cp_async_elem<ESZ>(&stage[(iN * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.NL) + gi, valid);
         }
         cp_async_wait_all();  // each thread reads back only its own elements
         // ---- residual q_n for n = G j + g, times Gamma_alpha ----
@@ -389,11 +402,21 @@ __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
             for (int d = NWIN - 1; d >= 1; --d) xw[d] = xw[d - 1];
             xw[0] = c2((ST)0, (ST)0);
             if (A.X) xw[0] = ldcol<ST, REAL>(stage, (ix * R + j) * REG_THREADS + tid);
-            if (A.F) q = ldcol<ST, REAL>(stage, (iF * R + j) * REG_THREADS + tid);
-            if (A.NL) {
-                const ST2 v = ldcol<ST, REAL>(stage, (iN * R + j) * REG_THREADS + tid);
-                q.x = fma(bdt, v.x, q.x);
-                q.y = fma(bdt, v.y, q.y);
+            if constexpr (STAGE_ALL) {
+                if (A.F) q = ldcol<ST, REAL>(stage, (iF * R + j) * REG_THREADS + tid);
+                if (A.NL) {
+                    const ST2 v = ldcol<ST, REAL>(stage, (iN * R + j) * REG_THREADS + tid);
+                    q.x = fma(bdt, v.x, q.x);
+                    q.y = fma(bdt, v.y, q.y);
+                }
+            } else if (valid) {
+                const long long gi = (long long)n * Mcol + mm;
+                if (A.F) q = ldcol<ST, REAL>(A.F, gi);
+                if (A.NL) {
+                    const ST2 v = ldcol<ST, REAL>(A.NL, gi);
+                    q.x = fma(bdt, v.x, q.x);
+                    q.y = fma(bdt, v.y, q.y);
+                }
             }
             if (A.X) {
                 ST2 rx = xw[0];
@@ -483,6 +506,7 @@ __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
                     stcol<ST, REAL>(A.out, gi, sv);
                 }
                 const float2 sf = cvt2<float2>(sv);
+                if (A.sout) stcol<float, REAL>(A.sout, gi, sf);
                 ns = wgt * fmaf(sf.x, sf.x, sf.y * sf.y);
             }
             w[j] = make_float2(ns, nx);
@@ -541,7 +565,8 @@ expd_status launch_reg(expd_plan p, TimeArgs& a, cudaStream_t s) {
     a.osc = std::is_same<ST, dd>::value ? p->oscdd : ts.osc;
     a.lam = p->t32.lam;
     a.tw = p->t32.tw;
-    constexpr int cols = REG_THREADS / REG_G;
+    constexpr int G = reg_lanes(NS);
+    constexpr int cols = REG_THREADS / G;
     long long grid = (p->Mcol + cols - 1) / cols;
     if (grid > p->partial_cap) grid = p->partial_cap;
     const double esz = (REAL ? 1.0 : 2.0) * sizeof(ST);
@@ -549,9 +574,10 @@ expd_status launch_reg(expd_plan p, TimeArgs& a, cudaStream_t s) {
     const double fl_col = 2.0 * 5.0 * NS * ilog2(NS) + 8.0 * p->order * NS + 4.0 * p->order * NS;
     const int cls = sizeof(ST) == 4 ? EXPD_K_TIME32 : std::is_same<ST, dd>::value ? EXPD_K_TIMEDD : EXPD_K_TIME;
     KProf kp(p, s, cls, per * NS * (double)p->Mcol, fl_col * (double)p->Mcol);
-    const int narr = (a.X ? 1 : 0) + (a.F ? 1 : 0) + (a.NL ? 1 : 0);
-    const size_t smem = (size_t)narr * NS * REG_THREADS / REG_G * (size_t)esz;  // R slots per thread
-    auto kern = time_reg_kernel<NS, REG_G, ST, REAL>;
+    constexpr bool all = !std::is_same<ST, dd>::value;  // double-float (16-byte) elements stage only X
+    const int narr = (a.X ? 1 : 0) + (all ? (a.F ? 1 : 0) + (a.NL ? 1 : 0) : 0);
+    const size_t smem = (size_t)std::max(narr, 1) * NS * REG_THREADS / G * (size_t)esz;  // R slots per thread
+    auto kern = time_reg_kernel<NS, G, ST, REAL, all>;
     EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
     kern<<<(int)grid, REG_THREADS, smem, s>>>(a);
     EXPD_CUDA_TRY(cudaGetLastError());
@@ -569,67 +595,48 @@ expd_status launch_reg_ns(expd_plan p, TimeArgs& a, cudaStream_t s) {
     return expd_fail(EXPD_ERR_UNSUPPORTED, "register time kernel needs Ns in {16, 32, 64}");
 }
 
-// max that propagates NaN (fmax would drop it and hide a diverged iterate)
-__device__ __forceinline__ double nanmax(double a, double b) { return (a != a || b != b) ? NAN : fmax(a, b); }
 
 // Per-slice totals over the time kernel's CTAs: block n sums slice n's
-// partials (fixed order), then the last block to finish takes the max and the
-// sum over slices in slice order.  The atomic counter only elects that block;
-// every sum has a fixed order, so the result is deterministic.
-__global__ void __launch_bounds__(256) reduce_kernel(const double2* __restrict__ partial, int grid, int Ns,
-                                                     double2* __restrict__ slice_tot, unsigned* __restrict__ counter,
-                                                     double* __restrict__ out) {
+// partials in a fixed order (four independent strided accumulators per thread,
+// a shuffle tree, then the warps in order), so the totals are deterministic.
+// The host takes the max and the sum over slices (in slice order).
+__global__ void __launch_bounds__(256) reduce_kernel(const double2* __restrict__ partial, int grid,
+                                                     double2* __restrict__ slice_tot) {
     __shared__ double2 red[8];
-    __shared__ bool last;
     const int n = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double a = 0, b = 0;
-    for (int g = threadIdx.x; g < grid; g += blockDim.x) {
-        const double2 v = partial[(size_t)n * grid + g];
-        a += v.x;
-        b += v.y;
+    const double2* src = partial + (size_t)n * grid;
+    double a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
+    int g = threadIdx.x;
+    for (; g + 3 * 256 < grid; g += 4 * 256) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double2 v = src[g + u * 256];
+            a[u] += v.x;
+            b[u] += v.y;
+        }
     }
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+        if (g + u * 256 < grid) {
+            const double2 v = src[g + u * 256];
+            a[u] += v.x;
+            b[u] += v.y;
+        }
+    }
+    double x = (a[0] + a[1]) + (a[2] + a[3]), y = (b[0] + b[1]) + (b[2] + b[3]);
     for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
     }
-    if (lane == 0) red[warp] = make_double2(a, b);
+    if (lane == 0) red[warp] = make_double2(x, y);
     __syncthreads();
     if (threadIdx.x == 0) {
         double2 t = make_double2(0.0, 0.0);
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        for (int w = 0; w < 8; ++w) {
             t.x += red[w].x;
             t.y += red[w].y;
         }
         slice_tot[n] = t;
-        __threadfence();
-        last = (atomicAdd(counter, 1u) == (unsigned)(Ns - 1));
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double mx0 = 0, mx1 = 0, sm0 = 0, sm1 = 0;
-    if (warp == 0) {
-        // lane-strided partial sums, then a fixed shuffle tree: a fixed order
-        for (int k = lane; k < Ns; k += 32) {
-            const double2 t = __ldcg(&slice_tot[k]);
-            mx0 = nanmax(mx0, t.x);
-            mx1 = nanmax(mx1, t.y);
-            sm0 += t.x;
-            sm1 += t.y;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            mx0 = nanmax(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
-            mx1 = nanmax(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
-            sm0 += __shfl_xor_sync(0xffffffffu, sm0, o);
-            sm1 += __shfl_xor_sync(0xffffffffu, sm1, o);
-        }
-        if (lane == 0) {
-            out[0] = sqrt(mx0);
-            out[1] = sqrt(mx1);
-            out[2] = sm0;
-            out[3] = sm1;
-            *counter = 0u;
-        }
     }
 }
 
@@ -799,10 +806,11 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s) {
     a.realcol = p->realcol;
     a.ntiles = (p->Mcol + EXPD_TIME_COLS - 1) / EXPD_TIME_COLS;
     a.partial = p->partial;
+    a.sout = op.accum ? op.sout : nullptr;
     // power-of-two windows up to 64 with the float32 preconditioner: register kernel
     const bool reg = op.precond && op.f32 && (p->Ns == 16 || p->Ns == 32 || p->Ns == 64) && !p->no_reg_time;
-    // (double-float storage stays on the shared-memory kernel: staging its 16-byte
-    // elements would leave two CTAs per SM)
+    // (double-float storage stays on the shared-memory kernel: with 16-byte
+    // elements the register kernel's staging or its direct loads measured slower)
     if (reg && !op.stdd) {
         if (op.st32) {
             if (op.NL && !op.nl_f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 storage needs float32 N");
@@ -828,8 +836,7 @@ expd_status time_reduce(expd_plan p, cudaStream_t s) {
     const int grid = p->time_grid_used > 0 ? p->time_grid_used : p->time_grid;
     KProf kp(p, s, EXPD_K_REDUCE, 16.0 * grid * p->Ns, 2.0 * grid * p->Ns);
     double2* slice_tot = reinterpret_cast<double2*>(p->redout + 8);
-    unsigned* counter = reinterpret_cast<unsigned*>(p->redout + 6);
-    reduce_kernel<<<p->Ns, 256, 0, s>>>(p->partial, grid, p->Ns, slice_tot, counter, p->redout);
+    reduce_kernel<<<p->Ns, 256, 0, s>>>(p->partial, grid, slice_tot);
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }
