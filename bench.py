@@ -46,6 +46,11 @@ FALLBACK_HBM_GBS = 6800.0
 # float64 FMA throughput measured on this machine's GB300 (152 SMs x 2 FMA/clk x 2.07 GHz)
 FP64_PEAK_TFLOPS = 1.248
 FP64_CLASSES = ("time", "fft_col", "fft_row", "dst")
+# DRAM bytes (read + write) per launch of the dominant kernels at the bench
+# workload (256^2 x 64 slices), from one ncu capture of each kernel as built
+# now (dram__bytes_read.sum + dram__bytes_write.sum, cold caches)
+NCU_TRAFFIC_256x64 = {"time32": 50.937088e6 + 7.68e3, "fft_col32": 16.930304e6 + 2.048e3,
+                      "fft_row32": 16.939008e6, "timedd": 101.922816e6 + 12.87424e6}
 
 
 def parse_args():
@@ -371,8 +376,10 @@ def main():
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None}
     else:
         achieved = (c["bytes"] / c["count"]) / (c["ms"] / c["count"] / 1e3) / 1e9 if c["count"] else 0.0
+        traffic = NCU_TRAFFIC_256x64.get(dom) if p.n == (256, 256) and p.Nt == 64 else None
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "peak_source": peak_src,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None}
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "algorithmic_bytes_per_launch": c["bytes"] / c["count"] if c["count"] else None}
     kernels = {k: {"launches": v["count"], "ms_total": round(v["ms"], 4),
                    "avg_us": round(1e3 * v["ms"] / v["count"], 3) if v["count"] else None,
                    "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] else None,
