@@ -289,7 +289,25 @@ def gamma_alpha(sp: Spec) -> np.ndarray:
     return sp.alpha ** (np.arange(sp.Ns) / sp.Ns)
 
 
-def precond_apply(sp: Spec, r: np.ndarray) -> np.ndarray:
+def nonlinearity_derivative(sp: Spec, u: np.ndarray) -> np.ndarray:
+    """N'(u): zero for linear problems, 1 - 3 u^2 for Allen-Cahn."""
+    if sp.nonlin == "none":
+        return np.zeros_like(u)
+    if sp.nonlin == "allen_cahn":
+        return 1.0 - 3.0 * u**2
+    raise ValueError(sp.nonlin)
+
+
+def jacobian_shift(sp: Spec, u0: np.ndarray) -> float:
+    """beta_s dt nbar, nbar the spatial mean of N'(u_0): the inexact Jacobian
+    that Sec. 6 proposes after Eq. (6.5), I_t (x) diag(N'(u_0)) (the Jacobian at
+    the initial value), averaged over space so that Step (b) stays diagonal in
+    L_h's eigenbasis."""
+    _, beta = bdf_float(sp.order)
+    return beta * sp.dt * float(np.mean(nonlinearity_derivative(sp, u0)))
+
+
+def precond_apply(sp: Spec, r: np.ndarray, shift: float = 0.0) -> np.ndarray:
     """s = P_alpha^{-1} r by the three steps of Eq. (3.3) / Eq. (4.5).
 
     Step (a): S_a = (F (x) I)(Gamma_alpha (x) I) r, F the unitary DFT with
@@ -297,7 +315,10 @@ def precond_apply(sp: Spec, r: np.ndarray) -> np.ndarray:
     Step (b): S_b,n = (I - sum_j a_j lambda_n^j A^j)^{-1} S_a,n per slice
               (lambda_{j-1,n} = lambda_{0,n}^j, Sec. 4 after Eq. (4.4)); the spatial solve
               is diagonal in L_h's eigenbasis;
-    Step (c): s = (Gamma_alpha^{-1} (x) I)(F^* (x) I) S_b."""
+    Step (c): s = (Gamma_alpha^{-1} (x) I)(F^* (x) I) S_b.
+    shift != 0 solves with P_alpha - shift I instead (Step (b) of the inexact
+    Newton variant, Eq. (6.5), with a scalar Jacobian): per slice
+    ((1 - shift) I - sum_j a_j lambda_n^j A^j)^{-1}."""
     Ns = sp.Ns
     a, _ = bdf_float(sp.order)
     gam = gamma_alpha(sp).reshape((Ns,) + (1,) * sp.ndim)
@@ -308,7 +329,7 @@ def precond_apply(sp: Spec, r: np.ndarray) -> np.ndarray:
     # Step (b)
     Sb = np.empty_like(Sa)
     for n in range(Ns):
-        d = np.ones(sp.n, dtype=complex)
+        d = np.full(sp.n, 1.0 - shift, dtype=complex)
         for j in range(1, sp.order + 1):
             d -= a[j - 1] * lam[n] ** j * np.exp(j * sp.dt * mu)
         Sb[n] = from_eigen(sp, to_eigen(sp, Sa[n]) / d)
@@ -338,18 +359,21 @@ def assemble(sp: Spec, U_start: np.ndarray, V: np.ndarray) -> np.ndarray:
 def richardson(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None,
                max_iter: int = 50, tol: float = 0.0, keep_iterates: bool = False,
                V0: Optional[np.ndarray] = None,
-               U_start: Optional[np.ndarray] = None) -> SolveResult:
+               U_start: Optional[np.ndarray] = None, jacobian: str = "lagged") -> SolveResult:
     """Preconditioned fixed-point iteration v^{k+1} = v^k + P_alpha^{-1}(f_s +
     beta dt N(v^k) - R_s v^k) from v^0 = 0 (Eqs. (3.2), (4.4), (7.3)-(7.4);
     Sec. 7 starts from zero).  Stops when max_n ||s_n|| <= tol * max_n ||v_n||
-    or after max_iter iterations."""
+    or after max_iter iterations.  jacobian="mean_u0" preconditions with
+    P_alpha - beta dt nbar I (see `jacobian_shift`): the same fixed point,
+    reached by inexact Newton steps."""
+    shift = jacobian_shift(sp, u0) if jacobian == "mean_u0" else 0.0
     U_start = startup_values(sp, u0, f, U_start)
     b = rhs_known(sp, U_start, f)
     V = np.zeros((sp.Ns,) + sp.n) if V0 is None else V0.copy()
     hist, its = [], []
     k = 0
     for k in range(1, max_iter + 1):
-        s = precond_apply(sp, residual(sp, V, b))
+        s = precond_apply(sp, residual(sp, V, b), shift)
         V = V + s
         sn = np.sqrt((s.reshape(sp.Ns, -1) ** 2).sum(1)).max()
         vn = np.sqrt((V.reshape(sp.Ns, -1) ** 2).sum(1)).max()
@@ -628,9 +652,10 @@ def _dense_pointwise(sp: Spec, w: np.ndarray, bdt: float) -> np.ndarray:
     return u
 
 
-def dense_precond_apply(sp: Spec, r: np.ndarray) -> np.ndarray:
-    """P_alpha^{-1} r by an LU solve with the explicit dense R_s^alpha."""
-    return np.linalg.solve(dense_R(sp, sp.alpha), r.ravel()).reshape(r.shape)
+def dense_precond_apply(sp: Spec, r: np.ndarray, shift: float = 0.0) -> np.ndarray:
+    """(P_alpha - shift I)^{-1} r by an LU solve with the explicit dense R_s^alpha."""
+    P = dense_R(sp, sp.alpha)
+    return np.linalg.solve(P - shift * np.eye(P.shape[0]), r.ravel()).reshape(r.shape)
 
 
 def dense_iteration_matrix(sp: Spec) -> np.ndarray:

@@ -352,3 +352,27 @@ def check_bicgstab_reaches_sequential(sp, seed=9):
     ref = O.sequential_solve(sp, u0, f)
     res = O.bicgstab(sp, u0, f, tol=1e-13)
     return O.rel_error(res.U[1:], ref[1:]), res
+
+
+def check_precond_shift_vs_dense(sp, shift=0.3, seed=11):
+    """(P_alpha - shift I)^{-1} by the three steps vs the dense LU solve."""
+    r = rng_field(sp, seed, (sp.Ns,))
+    ref = O.dense_precond_apply(sp, r, shift)
+    return np.abs(O.precond_apply(sp, r, shift) - ref).max() / np.abs(ref).max()
+
+
+def check_mean_jacobian_contraction(order=1, c0=0.1, iters=4):
+    """Allen-Cahn from a constant state u_0 = c0 (N'(u_0) = 1 - 3 c0^2 ~ 1 is the
+    Jacobian at t = 0 everywhere): observed contraction of the lagged iteration
+    and of the mean-Jacobian (inexact Newton) iteration, (rho_lagged, rho_newton)."""
+    sp = O.Spec("periodic", (8,), (1.0,), 0.01, 0.0, "allen_cahn", 0.05, 24, 1e-3, order)
+    u0 = np.full(sp.n, c0) + 1e-3 * np.cos(2 * np.pi * np.arange(8) / 8)
+    ref = O.sequential_solve(sp, u0)[1:]
+    out = []
+    for jac in ("lagged", "mean_u0"):
+        errs = []
+        for k in range(1, iters + 1):
+            U = O.richardson(sp, u0, None, max_iter=k, jacobian=jac).U[1:]
+            errs.append(O.rel_error(U, ref))
+        out.append(max(errs[k] / errs[k - 1] for k in range(1, len(errs))))
+    return tuple(out)

@@ -235,3 +235,27 @@ def test_bicgstab_reaches_sequential(order):
     err, res = C.check_bicgstab_reaches_sequential(sp)
     assert err < 1e-12
     assert res.iterations <= 6          # preconditioned spectrum clustered at 1 (Lemma 3.4)
+
+
+@pytest.mark.parametrize("bc,order", [("periodic", 1), ("dirichlet", 2), ("periodic", 6)])
+def test_shifted_preconditioner_matches_dense(bc, order):
+    # Step (b) of the inexact Newton variant (Eq. (6.5)) with a scalar Jacobian
+    sp = C.spec(bc, (5,) if bc == "dirichlet" else (6,), Nt=order + 7, order=order, alpha=0.05, a=0.3)
+    assert C.check_precond_shift_vs_dense(sp) < 1e-11
+
+
+@pytest.mark.parametrize("order", [1, 2, 6])
+def test_mean_jacobian_reaches_sequential(order):
+    sp = C.spec("periodic", (8, 8), length=(1.0, 1.0), a=0.0025, c=0.0, nonlin="allen_cahn",
+                Nt=order + 15, order=order, alpha=1e-3, dt=1e-3)
+    u0 = np.random.default_rng(20 + order).uniform(-0.9, 0.9, sp.n)
+    ref = O.sequential_solve(sp, u0)
+    r = O.richardson(sp, u0, max_iter=40, tol=1e-14, jacobian="mean_u0")
+    assert O.rel_error(r.U[1:], ref[1:]) < 1e-12
+
+
+def test_mean_jacobian_contracts_faster_near_uniform_state():
+    # near a uniform state the mean of N'(u_0) is the Jacobian: the inexact
+    # Newton iteration contracts much faster than the lagged one
+    rho_lag, rho_newton = C.check_mean_jacobian_contraction()
+    assert rho_newton < 0.2 * rho_lag, (rho_lag, rho_newton)

@@ -156,3 +156,10 @@ def test_planted_bicgstab_mistakes_are_caught(monkeypatch, mistake):
     patch(monkeypatch, "bicgstab_solve", bicgstab_solve)
     hist, d, err = C.check_bicgstab_minimal_polynomial((2.0, 2.0, 5.0, 5.0, 5.0, -1.5))
     assert hist[d] > 1e-6 or err > 1e-6
+
+
+def test_planted_jacobian_shift_sign_is_caught(monkeypatch):
+    real = E.jacobian_shift
+    patch(monkeypatch, "jacobian_shift", lambda sp, u0: -real(sp, u0))
+    rho_lag, rho_newton = C.check_mean_jacobian_contraction()
+    assert not rho_newton < 0.2 * rho_lag
