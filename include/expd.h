@@ -102,7 +102,14 @@ typedef struct {
  *             <= tol
  *  gmres_restart  GMRES restart length m (1..64)
  *  startup    EXPD_STARTUP_RAMP or EXPD_STARTUP_GIVEN (u_1..u_{s-1} read
- *             from the first s-1 slices of the U argument of the solvers)   */
+ *             from the first s-1 slices of the U argument of the solvers)
+ *  jacobian   EXPD_JAC_LAGGED: the fixed point preconditions with R_s^alpha
+ *             (N lagged, Eqs. (7.3)-(7.4)).  EXPD_JAC_MEAN_U0: inexact Newton
+ *             steps with the Jacobian at the initial value (proposed after
+ *             Eq. (6.5)) averaged over space, i.e. R_s^alpha - beta_s dt nbar I,
+ *             nbar = mean of N'(u_0); Step (b) stays diagonal and the fixed
+ *             point is unchanged.  Ignored for linear problems.            */
+enum { EXPD_JAC_LAGGED = 0, EXPD_JAC_MEAN_U0 = 1 };
 typedef struct {
     int order;
     int precision;
@@ -110,6 +117,7 @@ typedef struct {
     double tol;
     int gmres_restart;
     int startup;
+    int jacobian;               /* EXPD_JAC_*                                          */
 } expd_scheme;
 
 #define EXPD_MAX_HISTORY 128

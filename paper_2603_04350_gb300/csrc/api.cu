@@ -438,6 +438,8 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     if (!(scheme->tol > 0)) return expd_fail(EXPD_ERR_INVALID_ARG, "tol must be positive");
     if (scheme->gmres_restart < 1 || scheme->gmres_restart > 64)
         return expd_fail(EXPD_ERR_INVALID_ARG, "gmres_restart must be in [1, 64]");
+    if (scheme->jacobian != EXPD_JAC_LAGGED && scheme->jacobian != EXPD_JAC_MEAN_U0)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "jacobian must be EXPD_JAC_LAGGED or EXPD_JAC_MEAN_U0");
     if (scheme->startup != EXPD_STARTUP_RAMP && scheme->startup != EXPD_STARTUP_GIVEN)
         return expd_fail(EXPD_ERR_INVALID_ARG, "unknown startup mode");
     p->ndim = grid->ndim;
@@ -466,6 +468,7 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     p->tol = scheme->tol;
     p->restart = scheme->gmres_restart;
     p->startup = scheme->startup;
+    p->jacobian = scheme->jacobian;
     for (int q = 1; q <= 6; ++q) bdf(q, p->acoef[q], &p->beta[q]);
     if (p->nonlin != EXPD_NL_NONE) {
         for (int q = 1; q <= p->order; ++q)
@@ -936,6 +939,18 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     // s in float32 is the solution (the update is orders of magnitude below U,
     // so float32 rounding of its transform is far below the tolerance), which
     // replaces the double-float output transform.
+    // inexact Newton with the mean Jacobian at u_0: Step (b) solves with
+    // (1 - beta dt nbar) I - ..., nbar = mean of N'(u_0) = 1 - 3 mean(u_0^2)
+    double dshift = 0.0;
+    if (nl && p->jacobian == EXPD_JAC_MEAN_U0) {
+        double* scratch = reinterpret_cast<double*>(p->partial);  // free until the first time kernel
+        st = sum_squares(p, p->startphys, p->M, p->redout, scratch, s);
+        if (st != EXPD_OK) return st;
+        EXPD_CUDA_TRY(cudaMemcpyAsync(p->redhost, p->redout, sizeof(double), cudaMemcpyDeviceToHost, s));
+        EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+        const double nbar = 1.0 - 3.0 * p->redhost[0] / (double)p->M;
+        dshift = p->beta[p->order] * p->dt * nbar;
+    }
     double* phys_out = sg.U + (size_t)(p->order - 1) * p->M;
     const bool fast_out = use_dd && nl && inverse32_accum_supported(p);
     bool phys_valid = false;
@@ -953,6 +968,7 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
         op.f32 = mixed;
         op.st32 = phase == PH32;
         op.stdd = phase == PHDD;
+        op.dshift = dshift;
         const bool used32 = phase == PH32;
         if (nl) {
             void* NL;

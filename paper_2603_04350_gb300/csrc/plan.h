@@ -97,6 +97,7 @@ struct expd_plan_s {
     int time_grid = 0;            // CTAs of the time kernel (multiple of SM count)
     int partial_cap = 0;          // CTAs the partial-norm buffer has room for
     int time_grid_used = 0;       // CTAs of the last time-kernel launch (for the reduction)
+    int jacobian = 0;             // EXPD_JAC_*
     int no_reg_time = 0;          // 1 forces the shared-memory time kernel (tests)
     int no_fft4 = 0;              // 1 forces the radix-4 shared-memory row / column FFTs (tests)
     // host-pointer staging (lazy)
@@ -174,6 +175,8 @@ expd_status pointwise_solve(expd_plan p, const double* w, double* u, long long n
 expd_status eigen_combine(expd_plan p, void* out, const void* const* in, const double* coef, int q,
                           const void* src, double g, cudaStream_t s);
 // f_s: Fh[i] = bdt f^(s+i) + sum_{j: s+i-j<s} a_j E^j Sh[s+i-j]
+// *out_dev = sum of x[i]^2 (deterministic); scratch holds 64 doubles
+expd_status sum_squares(expd_plan p, const double* x, long long n, double* out_dev, double* scratch, cudaStream_t s);
 // F32 (optional): also the float32 copy; fh_dd: Fh stored as double-float pairs
 expd_status assemble_rhs(expd_plan p, const void* fh, cudaStream_t s, float* F32 = nullptr, int fh_dd = 0);
 
@@ -183,6 +186,7 @@ struct TimeOp {
     const void* F = nullptr;   // additive right-hand side (may be null)
     const void* NL = nullptr;  // transformed nonlinearity (may be null)
     void* sout = nullptr;      // optional copy of the update s in float32 (accum mode)
+    double dshift = 0;         // Step (b) solves with (1 - dshift) I - sum_j a_j (lambda A)^j
     int nl_f32 = 0;
     double bdt = 0;            // coefficient of NL
     double sigR = -1;          // coefficient of R_s X

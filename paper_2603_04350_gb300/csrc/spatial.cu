@@ -302,6 +302,32 @@ __global__ void rhs_kernel(RhsArgs r) {
     }
 }
 
+// Sum of squares of n doubles: fixed-order per-block partials, then one block
+// sums them in order (deterministic).
+__global__ void __launch_bounds__(256) sumsq_partial_kernel(const double* __restrict__ x, long long n,
+                                                            double* __restrict__ partial) {
+    __shared__ double red[8];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+        acc = fma(x[i], x[i], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        partial[blockIdx.x] = t;
+    }
+}
+
+__global__ void sumsq_final_kernel(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < nb; ++b) t += partial[b];
+        *out = t;
+    }
+}
+
 int grid_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -1036,6 +1062,16 @@ expd_status spatial_inverse_dd(expd_plan p, const void* eig, double* phys, int n
         }
         if (st != EXPD_OK) return st;
     }
+    return EXPD_OK;
+}
+
+expd_status sum_squares(expd_plan p, const double* x, long long n, double* out_dev, double* scratch, cudaStream_t s) {
+    const int nb = 64;
+    KProf kp(p, s, EXPD_K_POINTWISE, 8.0 * n, 2.0 * n);
+    sumsq_partial_kernel<<<nb, 256, 0, s>>>(x, n, scratch);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    sumsq_final_kernel<<<1, 32, 0, s>>>(scratch, nb, out_dev);
+    EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }
 

@@ -7,8 +7,9 @@
 // On exit position pos(n) (same rule) holds v_n with
 //     s_n = v_n * scale / alpha^(n/Ns),
 //     s   = Gamma^{-1} F^* diag(1/d) F Gamma q   (F: omega = e^{+2 pi i/Ns})
-// where d_k = 1 - sum_{j=1..order} cj[j] lambda_k^j and cj[j] = a_j E^j
-// (cj[1..6] valid, entries beyond `order` ignored).
+// where d_k = one - sum_{j=1..order} cj[j] lambda_k^j and cj[j] = a_j E^j
+// (cj[1..6] valid, entries beyond `order` ignored; one = 1 except for the
+// shifted solve of the inexact Newton variant).
 #pragma once
 
 #include "common.cuh"
@@ -16,7 +17,7 @@
 template <typename PT, typename PT2>
 EXPD_HD double precond_column(PT2* w, int Ns, int L, int log2L, int bluestein, const PT2* tw, const PT2* lam,
                               const PT2* chirp, const PT2* bp, const PT2* bm, const PT* cj, int order,
-                              int lane, int nlanes) {
+                              int lane, int nlanes, PT one = (PT)1) {
     if (bluestein) {
         for (int n = lane; n < Ns; n += nlanes) w[n] = cmul(w[n], chirp[n]);
         for (int n = Ns + lane; n < L; n += nlanes) w[n] = c2((PT)0, (PT)0);
@@ -48,7 +49,7 @@ EXPD_HD double precond_column(PT2* w, int Ns, int L, int log2L, int bluestein, c
             }
         }
         acc = cmul(lk, acc);
-        const PT2 d = c2((PT)1 - acc.x, -acc.y);
+        const PT2 d = c2(one - acc.x, -acc.y);
         PT2 z = cdiv(w[k], d);
         if (bluestein) z = cmulc(z, chirp[k]);
         w[k] = z;

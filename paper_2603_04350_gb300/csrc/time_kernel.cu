@@ -42,6 +42,7 @@ struct TimeArgs {
     const void* NL;
     void* out;
     void* sout;  // optional float32 copy of the update (accum mode)
+    double dshift;  // Step (b) divisor (1 - dshift) - sum_j c_j lambda^j
     int nl_f32;
     double bdt, sigR;
     int precond, accum;
@@ -224,7 +225,8 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
             }
             if (A.precond) {
                 EXPD_SYNCWARP();
-                precond_column<PT, PT2>(w, Ns, L, A.log2L, A.bluestein, tw, lam, chirp, bp, bm, cp, A.order, lane, 32);
+                precond_column<PT, PT2>(w, Ns, L, A.log2L, A.bluestein, tw, lam, chirp, bp, bm, cp, A.order, lane, 32,
+                                        (PT)(1.0 - A.dshift));
                 for (int n = lane; n < Ns; n += 32) {
                     const ST2 v = cvt2<ST2>(w[A.bluestein ? n : (int)bitrev(n, A.log2L)]);
                     rc[n] = cscale(v, osc[n]);
@@ -296,10 +298,7 @@ __device__ __forceinline__ float2 shfl_xor_c(float2 v, int m) {
 __device__ __forceinline__ double2 shfl_c(double2 v, int lane) {
     return make_double2(__shfl_sync(0xffffffffu, v.x, lane), __shfl_sync(0xffffffffu, v.y, lane));
 }
-__device__ __forceinline__ dd shfl_d(dd v, int lane) {
-    return dd(__shfl_sync(0xffffffffu, v.hi, lane), __shfl_sync(0xffffffffu, v.lo, lane));
-}
-__device__ __forceinline__ dd2 shfl_c(dd2 v, int lane) { return c2(shfl_d(v.x, lane), shfl_d(v.y, lane)); }
+
 
 // Asynchronous global -> shared copy of one element (4, 8 or 16 bytes); a
 // source size of 0 fills the destination with zeros (columns past the end).
@@ -361,6 +360,7 @@ __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
     const long long Mcol = A.Mcol;
     const ST bdt = (ST)A.bdt, sigR = (ST)A.sigR;
     const int order = A.order;
+    const float one = (float)(1.0 - A.dshift);
     const int k2R = (int)bitrev((unsigned)g, LOGG) * R;  // spectral block of this lane
     float accs[PER], accx[PER];
 #pragma unroll
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
                 acc.x += cp[j];
             }
             acc = cmul(lk, acc);
-            w[p] = cdiv(w[p], make_float2(1.0f - acc.x, -acc.y));
+            w[p] = cdiv(w[p], make_float2(one - acc.x, -acc.y));
         }
         // ---- Step (c): z_n = sum_k Z_k e^{-2 pi i kn/NS} ----
 #pragma unroll
@@ -807,6 +807,7 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s) {
     a.ntiles = (p->Mcol + EXPD_TIME_COLS - 1) / EXPD_TIME_COLS;
     a.partial = p->partial;
     a.sout = op.accum ? op.sout : nullptr;
+    a.dshift = op.dshift;
     // power-of-two windows up to 64 with the float32 preconditioner: register kernel
     const bool reg = op.precond && op.f32 && (p->Ns == 16 || p->Ns == 32 || p->Ns == 64) && !p->no_reg_time;
     // (double-float storage stays on the shared-memory kernel: with 16-byte

@@ -22,6 +22,7 @@ BC_PERIODIC, BC_DIRICHLET = 0, 1
 NL_NONE, NL_ALLEN_CAHN = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 STARTUP_RAMP, STARTUP_GIVEN = 0, 1
+JAC_LAGGED, JAC_MEAN_U0 = 0, 1
 MAX_HISTORY = 128
 
 SYMBOLS = ("expd_plan_create", "expd_plan_workspace_bytes", "expd_plan_footprint_bytes", "expd_residual", "expd_precond_apply",
@@ -45,7 +46,7 @@ class Operator(C.Structure):
 
 class Scheme(C.Structure):
     _fields_ = [("order", C.c_int), ("precision", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double),
-                ("gmres_restart", C.c_int), ("startup", C.c_int)]
+                ("gmres_restart", C.c_int), ("startup", C.c_int), ("jacobian", C.c_int)]
 
 
 class Info(C.Structure):
@@ -167,6 +168,7 @@ class PlanSpec:
     tol: float = 1e-8
     gmres_restart: int = 20
     startup: int = STARTUP_RAMP
+    jacobian: int = 0
 
 
 def _structs(spec: PlanSpec):
@@ -177,7 +179,7 @@ def _structs(spec: PlanSpec):
         g.length[d] = float(spec.length[d])
     g.bc = spec.bc
     o = Operator(spec.a, spec.c, spec.nonlin)
-    s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup)
+    s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup, spec.jacobian)
     return g, o, s
 
 
@@ -210,7 +212,7 @@ def plan_create(spec: PlanSpec, stream=None) -> "Plan":
         g.length[d] = float(spec.length[d])
     g.bc = spec.bc
     o = Operator(spec.a, spec.c, spec.nonlin)
-    s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup)
+    s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup, spec.jacobian)
     h = C.c_void_p()
     _check(lib().expd_plan_create(C.byref(g), C.byref(o), spec.dt, spec.Nt, spec.alpha, C.byref(s),
                                   _stream(stream), C.byref(h)))
@@ -293,9 +295,10 @@ class Plan:
 
 
 def spec_from_problem(p, precision: int = PREC_FP64, max_iter: int = 100, tol: Optional[float] = None,
-                      gmres_restart: int = 20, startup: int = STARTUP_RAMP) -> PlanSpec:
+                      gmres_restart: int = 20, startup: int = STARTUP_RAMP, jacobian: int = 0) -> PlanSpec:
     """PlanSpec from a paper_2603_04350_gb300.inputs.Problem."""
     return PlanSpec(bc=BC_PERIODIC if p.bc == "periodic" else BC_DIRICHLET, n=tuple(p.n), length=tuple(p.length),
                     a=p.a, c=p.c, nonlin=NL_ALLEN_CAHN if p.nonlin == "allen_cahn" else NL_NONE, dt=p.dt,
                     Nt=p.Nt, alpha=p.alpha, order=p.order, precision=precision, max_iter=max_iter,
-                    tol=p.tol if tol is None else tol, gmres_restart=gmres_restart, startup=startup)
+                    tol=p.tol if tol is None else tol, gmres_restart=gmres_restart, startup=startup,
+                    jacobian=jacobian)

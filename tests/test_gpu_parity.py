@@ -461,3 +461,51 @@ def test_radix4_fft_path(expd, p, monkeypatch):
         plan.solve_fp(dev(u0), None if f is None else dev(f), U)
     assert relmax(host(S), O.precond_apply(sp, r)) < 6e-8 * 16 / p.alpha
     assert O.rel_error(host(U), O.sequential_solve(sp, u0, f)[1:]) < 1e-10
+
+
+# --------------------------------------- inexact Newton, mean Jacobian at u0 --
+NL_CASES = [c for c in CASES if c.nonlin != "none"]
+NL_IDS = [c.name for c in NL_CASES]
+
+
+@pytest.mark.parametrize("p", NL_CASES, ids=NL_IDS)
+def test_mean_jacobian_iterates_match_oracle(expd, p):
+    sp = O.spec_of(p)
+    u0 = np.random.default_rng(17).uniform(-0.8, 0.8, p.n)
+    for k in (1, 2, 3):
+        ref = O.richardson(sp, u0, None, max_iter=k, jacobian="mean_u0").U[1:]
+        U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+        spec = expd.spec_from_problem(p, tol=1e-300, max_iter=k, jacobian=expd.JAC_MEAN_U0)
+        with expd.plan_create(spec) as plan:
+            info = plan.solve_fp(dev(u0), None, U, allow_not_converged=True)
+        assert info["iterations"] == k
+        assert O.rel_error(host(U), ref) < 1e-12
+
+
+@pytest.mark.parametrize("p", NL_CASES, ids=NL_IDS)
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_mean_jacobian_solve_matches_sequential(expd, p, prec):
+    sp = O.spec_of(p)
+    u0 = np.random.default_rng(18).uniform(-0.8, 0.8, p.n)
+    ref = O.sequential_solve(sp, u0)[1:]
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    precision = expd.PREC_FP64 if prec == "fp64" else expd.PREC_MIXED
+    spec = expd.spec_from_problem(p, precision=precision, tol=1e-12, max_iter=200, jacobian=expd.JAC_MEAN_U0)
+    with expd.plan_create(spec) as plan:
+        info = plan.solve_fp(dev(u0), None, U)
+    assert O.rel_error(host(U), ref) < 1e-10, info
+
+
+def test_mean_jacobian_full_size_allen_cahn_256(expd):
+    p = I.ALLEN_CAHN_256
+    u0, _ = I.make_inputs(p)
+    ref = O.sequential_solve(O.spec_of(p), u0)[1:]
+    its = {}
+    for jac in (expd.JAC_LAGGED, expd.JAC_MEAN_U0):
+        U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+        spec = expd.spec_from_problem(p, precision=expd.PREC_MIXED, max_iter=200, jacobian=jac)
+        with expd.plan_create(spec) as plan:
+            info = plan.solve_fp(dev(u0), None, U)
+        assert O.rel_error(host(U), ref) < p.tol, (jac, info)
+        its[jac] = info["iterations"]
+    assert its[expd.JAC_MEAN_U0] <= its[expd.JAC_LAGGED], its
