@@ -33,6 +33,7 @@ brute force; nothing is "parity unpinned".
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 from dataclasses import dataclass
 from fractions import Fraction
@@ -61,6 +62,7 @@ class Spec:
     Nt: int
     alpha: float
     order: int                   # s in 1..6
+    b: Tuple[float, ...] = ()    # advection velocity: L = a*Lap - b.grad - c (periodic only)
 
     @property
     def ndim(self):
@@ -74,7 +76,11 @@ class Spec:
 def spec_of(p) -> Spec:
     """Build a Spec from any object with the same attribute names."""
     return Spec(p.bc, tuple(p.n), tuple(p.length), p.a, p.c, p.nonlin, p.dt, p.Nt,
-                p.alpha, p.order)
+                p.alpha, p.order, tuple(getattr(p, "b", ()) or ()))
+
+
+def has_advection(sp: Spec) -> bool:
+    return any(v != 0.0 for v in sp.b)
 
 
 # ---------------------------------------------------------------------------
@@ -111,18 +117,31 @@ def spatial_eigenvalues(sp: Spec) -> np.ndarray:
     numpy FFT order (the Nyquist index carries (pi*n/L)^2).
     Dirichlet: 3-point (1D) / 5-point (2D) finite differences on n interior
     points, h = L/(n+1): mu = -a*sum_d (4/h^2) sin^2(pi k_d h/(2 L_d)) - c,
-    k_d = 1..n, eigenvectors sin(pi k_d x/L_d) (the DST-I basis)."""
-    parts = []
-    for n, L in zip(sp.n, sp.length):
+    k_d = 1..n, eigenvectors sin(pi k_d x/L_d) (the DST-I basis).
+    Advection (periodic, the advection-diffusion operator of Sec. 7 and
+    Remark 3.7): the spectral first derivative adds -i sum_d b_d (2 pi k_d/L_d)
+    with the Nyquist wavenumber's first-derivative symbol 0 (so real fields
+    stay real); mu is then complex with mu(-k) = conj(mu(k))."""
+    parts, adv = [], []
+    for d, (n, L) in enumerate(zip(sp.n, sp.length)):
         if sp.bc == PERIODIC:
             k = np.fft.fftfreq(n, 1.0 / n)
             parts.append(-(2.0 * np.pi * k / L) ** 2)
+            k1 = k.copy()
+            if n % 2 == 0:
+                k1[n // 2] = 0.0
+            adv.append(2.0 * np.pi * k1 / L * (sp.b[d] if d < len(sp.b) else 0.0))
         else:
             h = L / (n + 1)
             k = np.arange(1, n + 1)
             parts.append(-(4.0 / h**2) * np.sin(np.pi * k * h / (2.0 * L)) ** 2)
+    if has_advection(sp) and sp.bc != PERIODIC:
+        raise ValueError("advection needs a periodic grid")
     grids = np.meshgrid(*parts, indexing="ij")
-    return sp.a * sum(grids) - sp.c
+    mu = sp.a * sum(grids) - sp.c
+    if has_advection(sp):
+        mu = mu - 1j * sum(np.meshgrid(*adv, indexing="ij"))
+    return mu
 
 
 def _axes(sp: Spec, x: np.ndarray):
@@ -232,8 +251,7 @@ def startup_values(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None,
     """u_0..u_{s-1}: the given values, or u0 and the sequential ramp."""
     if U_start is not None:
         return np.array(U_start, dtype=float).reshape((sp.order,) + sp.n)
-    short = Spec(sp.bc, sp.n, sp.length, sp.a, sp.c, sp.nonlin, sp.dt, sp.order - 1,
-                 sp.alpha, sp.order)
+    short = dataclasses.replace(sp, Nt=sp.order - 1)
     if sp.order == 1:
         return u0[None].copy()
     return sequential_solve(short, u0, f)
@@ -542,17 +560,41 @@ def dense_laplacian_1d(bc: str, n: int, L: float) -> np.ndarray:
             + np.diag(np.ones(n - 1), -1)) / h**2
 
 
+def dense_derivative_1d(n: int, L: float) -> np.ndarray:
+    """Periodic spectral first-derivative matrix of the sinc interpolant (even
+    n): D[j, k] = (-1)^(j-k) cot((j - k) h/2)/2 off the diagonal, 0 on it
+    (h = 2 pi/n), scaled to length L; its eigenvalues are i*2 pi k/L for
+    |k| < n/2 and 0 at n/2."""
+    if n % 2:
+        raise ValueError("even n only")
+    h = 2.0 * np.pi / n
+    col = np.zeros(n)
+    j = np.arange(1, n)
+    col[1:] = 0.5 * ((-1.0) ** j) / np.tan(j * h / 2.0)   # D[j, 0]
+    row = col[(-np.arange(n)) % n]                         # D[0, k] = D[n - k, 0]
+    return scipy.linalg.toeplitz(col, row) * (2.0 * np.pi / L)
+
+
 def dense_Lh(sp: Spec) -> np.ndarray:
-    """L_h = a Delta_h - c I as an explicit matrix (row-major grid ordering)."""
+    """L_h = a Delta_h - b.grad_h - c I as an explicit matrix (row-major grid ordering)."""
     mats = [dense_laplacian_1d(sp.bc, n, L) for n, L in zip(sp.n, sp.length)]
     M = int(np.prod(sp.n))
-    lap = np.zeros((M, M))
-    for d, D in enumerate(mats):
+
+    def embed(D, d):
         term = np.ones((1, 1))
         for e in range(sp.ndim):
             term = np.kron(term, D if e == d else np.eye(sp.n[e]))
-        lap += term
-    return sp.a * lap - sp.c * np.eye(M)
+        return term
+
+    lap = np.zeros((M, M))
+    for d, D in enumerate(mats):
+        lap += embed(D, d)
+    out = sp.a * lap - sp.c * np.eye(M)
+    if has_advection(sp):
+        for d, (n, L) in enumerate(zip(sp.n, sp.length)):
+            if d < len(sp.b) and sp.b[d] != 0.0:
+                out -= sp.b[d] * embed(dense_derivative_1d(n, L), d)
+    return out
 
 
 def dense_A(sp: Spec) -> np.ndarray:

@@ -376,3 +376,26 @@ def check_mean_jacobian_contraction(order=1, c0=0.1, iters=4):
             errs.append(O.rel_error(U, ref))
         out.append(max(errs[k] / errs[k - 1] for k in range(1, len(errs))))
     return tuple(out)
+
+
+# --- advection-diffusion (periodic) ----------------------------------------
+def adv_spec(n=(8,), length=None, b=(0.7,), order=1, Nt=9, nonlin="none", a=0.3, c=0.1, alpha=0.05, dt=0.05):
+    if length is None:
+        length = tuple(2 * math.pi for _ in n)
+    return O.Spec("periodic", tuple(n), tuple(length), a, c, nonlin, dt, Nt, alpha, order, tuple(b))
+
+
+def check_advection_exact(Nx=64, Nt=16, b=2.0, a=0.1, seed=2):
+    """u_t = a u_xx - b u_x on [0, 2 pi): u = sum_k e^{-a k^2 t} (a_k cos k(x - bt)
+    + b_k sin k(x - bt))/k^2 exactly; spectral exponential Euler is exact in time."""
+    sp = O.Spec("periodic", (Nx,), (2 * math.pi,), a, 0.0, "none", 1.0 / Nt, Nt, 1e-2, 1, (b,))
+    rng = np.random.default_rng(seed)
+    ak, bk = rng.standard_normal(16), rng.standard_normal(16)
+    x = np.arange(Nx) * 2 * math.pi / Nx
+
+    def exact(t):
+        return sum(math.exp(-a * k * k * t) * (ak[k - 1] * np.cos(k * (x - b * t)) + bk[k - 1] * np.sin(k * (x - b * t)))
+                   / k**2 for k in range(1, 17))
+    U = O.sequential_solve(sp, exact(0.0))
+    Ue = np.array([exact(n * sp.dt) for n in range(Nt + 1)])
+    return O.rel_error(U[1:], Ue[1:])

@@ -259,3 +259,37 @@ def test_mean_jacobian_contracts_faster_near_uniform_state():
     # Newton iteration contracts much faster than the lagged one
     rho_lag, rho_newton = C.check_mean_jacobian_contraction()
     assert rho_newton < 0.2 * rho_lag, (rho_lag, rho_newton)
+
+
+# ------------------------------------------ advection-diffusion (periodic) --
+ADV_SPECS = [C.adv_spec(), C.adv_spec(n=(4, 6), length=(1.0, 1.5), b=(0.7, -0.4), order=2, Nt=10),
+             C.adv_spec(n=(6,), b=(-1.3,), order=6, Nt=14)]
+
+
+@pytest.mark.parametrize("sp", ADV_SPECS, ids=["1d_s1", "2d_s2", "1d_s6"])
+def test_advection_symbol_and_system_vs_dense(sp):
+    # the complex symbol -a|k|^2 - i b.k - c against expm of the explicit
+    # a D2 - b.D1 - c (spectral sinc derivative matrices), and the all-at-once
+    # operators built on it
+    assert C.check_A_vs_dense(sp) < 1e-12
+    assert C.check_apply_R_vs_dense(sp) < 1e-12
+    assert C.check_precond_vs_dense(sp) < 1e-10
+    assert C.check_sequential_vs_dense(sp) < 1e-12
+    assert C.check_rhs_vs_dense(sp) < 1e-12
+
+
+def test_advection_exact_transport():
+    # spectral exponential Euler transports and damps each Fourier mode exactly
+    assert C.check_advection_exact() < 1e-12
+
+
+@pytest.mark.parametrize("order", [1, 2, 6])
+def test_advection_solvers_reach_sequential(order):
+    sp = C.adv_spec(n=(8, 8), length=(1.0, 1.0), b=(2.0, -1.0), order=order, Nt=order + 11, a=0.01, alpha=1e-3, dt=0.01)
+    rng = np.random.default_rng(30 + order)
+    u0 = rng.standard_normal(sp.n)
+    f = rng.standard_normal((sp.Nt,) + sp.n)
+    ref = O.sequential_solve(sp, u0, f)[1:]
+    assert O.rel_error(O.richardson(sp, u0, f, max_iter=12).U[1:], ref) < 1e-11
+    assert O.rel_error(O.gmres(sp, u0, f, tol=1e-13).U[1:], ref) < 1e-11
+    assert O.rel_error(O.bicgstab(sp, u0, f, tol=1e-13).U[1:], ref) < 1e-11

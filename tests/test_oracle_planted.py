@@ -163,3 +163,9 @@ def test_planted_jacobian_shift_sign_is_caught(monkeypatch):
     patch(monkeypatch, "jacobian_shift", lambda sp, u0: -real(sp, u0))
     rho_lag, rho_newton = C.check_mean_jacobian_contraction()
     assert not rho_newton < 0.2 * rho_lag
+
+
+def test_planted_advection_sign_is_caught(monkeypatch):
+    real = E.spatial_eigenvalues
+    patch(monkeypatch, "spatial_eigenvalues", lambda sp: np.conj(real(sp)))
+    assert C.check_advection_exact() > 1e-3
