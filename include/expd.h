@@ -76,11 +76,17 @@ typedef struct {
     int bc;                     /* EXPD_BC_*                                           */
 } expd_grid;
 
-/* L = a*Lap - c (Sec. 1, Eq. (1.2)) and the nonlinearity N. */
+/* L = a*Lap - b.grad - c (Sec. 1, Eq. (1.2); the advection term as in the
+ * advection-diffusion experiments of Sec. 7 and Remark 3.7) and the
+ * nonlinearity N.  b[d] is the velocity along grid axis d (the axis of n[d]);
+ * advection needs a periodic grid: its spectral first derivative gives the
+ * complex symbol -a|k|^2 - i b.k - c (the Nyquist wavenumber's first-derivative
+ * symbol is 0, so real fields stay real).  b = {0, 0} for pure diffusion. */
 typedef struct {
     double a;
     double c;
     int nonlin;                 /* EXPD_NL_*                                           */
+    double b[2];
 } expd_operator;
 
 /* Scheme and solver controls.
@@ -238,7 +244,8 @@ expd_status expd_solve_sequential(expd_plan plan, const double* u0, const double
  * Limits: at most 512 unknown slices, and the tables, the eigen-space copy of
  * R, the spatial scratch and the norm partials must fit the array (about
  * 2 Ns M complex values plus the DST matrices on Dirichlet grids); larger
- * problems get EXPD_ERR_INVALID_ARG with the byte count in expd_last_error().
+ * problems get EXPD_ERR_INVALID_ARG with the byte count in expd_last_error();
+ * an operator with advection (b != 0) gets EXPD_ERR_UNSUPPORTED.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the array and leave their contents in it: calls that

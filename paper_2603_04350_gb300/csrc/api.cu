@@ -458,6 +458,16 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     p->a = op->a;
     p->c = op->c;
     p->nonlin = op->nonlin;
+    if (!isfinite(op->b[0]) || !isfinite(op->b[1])) return expd_fail(EXPD_ERR_INVALID_ARG, "b must be finite");
+    if (grid->ndim == 1) {
+        p->bx = op->b[0];
+    } else {
+        p->by = op->b[0];  // axis 0 is the slow (NY) axis
+        p->bx = op->b[1];
+    }
+    p->adv = p->bx != 0.0 || p->by != 0.0;
+    if (p->adv && grid->bc != EXPD_BC_PERIODIC)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "advection needs a periodic grid (the sine basis does not diagonalise it)");
     p->dt = dt;
     p->Nt = Nt;
     p->order = scheme->order;
@@ -542,19 +552,22 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
     expd_status st = EXPD_OK;
     // ---- eigenvalues of L_h: E_m = exp(dt mu_m) ----
     {
-        std::vector<double> E(p->Mcol), C64((size_t)p->order * p->Mcol);
-        std::vector<float> C32((size_t)p->order * p->Mcol);
+        const int cw = p->adv ? 2 : 1;  // complex tables (re, im) with advection
+        std::vector<double> E((size_t)cw * p->Mcol), C64((size_t)cw * p->order * p->Mcol);
+        std::vector<float> C32((size_t)cw * p->order * p->Mcol);
         for (long long m = 0; m < p->Mcol; ++m) {
             const int kx = (int)(m % p->KX);
             const int ky = (int)(m / p->KX);
-            double mu = -p->c;
+            double mu = -p->c, nu = 0.0;  // symbol mu + i nu
             if (p->bc == EXPD_BC_PERIODIC) {
                 const double wx = 2.0 * M_PI * kx / p->LX;
                 mu -= p->a * wx * wx;
+                if (2 * kx != p->NX) nu -= p->bx * wx;  // first derivative: 0 at the Nyquist wavenumber
                 if (p->ndim == 2) {
                     const int kyf = ky <= p->NY / 2 ? ky : ky - p->NY;
                     const double wy = 2.0 * M_PI * kyf / p->LY;
                     mu -= p->a * wy * wy;
+                    if (2 * ky != p->NY) nu -= p->by * wy;
                 }
             } else {
                 const double hx = p->LX / (p->NX + 1);
@@ -566,11 +579,25 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
                     mu -= p->a * (4.0 / (hy * hy)) * sy * sy;
                 }
             }
-            E[m] = exp(dt * mu);
-            for (int j = 1; j <= p->order; ++j) {
-                const double cjm = p->acoef[p->order][j] * exp(j * dt * mu);
-                C64[(size_t)(j - 1) * p->Mcol + m] = cjm;
-                C32[(size_t)(j - 1) * p->Mcol + m] = (float)cjm;
+            if (!p->adv) {
+                E[m] = exp(dt * mu);
+                for (int j = 1; j <= p->order; ++j) {
+                    const double cjm = p->acoef[p->order][j] * exp(j * dt * mu);
+                    C64[(size_t)(j - 1) * p->Mcol + m] = cjm;
+                    C32[(size_t)(j - 1) * p->Mcol + m] = (float)cjm;
+                }
+            } else {
+                // E = e^{dt mu} (cos dt nu + i sin dt nu), a_j E^j likewise
+                E[2 * m] = exp(dt * mu) * cos(dt * nu);
+                E[2 * m + 1] = exp(dt * mu) * sin(dt * nu);
+                for (int j = 1; j <= p->order; ++j) {
+                    const double r = p->acoef[p->order][j] * exp(j * dt * mu);
+                    const size_t i = (size_t)(j - 1) * p->Mcol + m;
+                    C64[2 * i] = r * cos(j * dt * nu);
+                    C64[2 * i + 1] = r * sin(j * dt * nu);
+                    C32[2 * i] = (float)C64[2 * i];
+                    C32[2 * i + 1] = (float)C64[2 * i + 1];
+                }
             }
         }
         st = upload_vec(p, &p->E, E, "E", s);
@@ -718,8 +745,9 @@ expd_status expd_plan_footprint_bytes(const expd_grid* grid, const expd_operator
     const bool nl = p->nonlin != EXPD_NL_NONE;
     const size_t vec = Ns * Mcol * p->esz;
     size_t b = 0;
-    b += Mcol * 8 + ord * Mcol * 8 + ord * Mcol * 4;                       // E, C64, C32
-    if (mixed && per) b += ord * Mcol * 8;                                  // Cdd
+    const size_t cw = p->adv ? 2 : 1;                                      // complex tables with advection
+    b += cw * (Mcol * 8 + ord * Mcol * 8 + ord * Mcol * 4);                 // E, C64, C32
+    if (mixed && per) b += cw * ord * Mcol * 8;                             // Cdd
     if (per) {
         b += (size_t)(p->NX / 2 + 1) * (16 + 8);                            // Wx64, Wx32
         if (p->ndim == 2) b += (size_t)std::max(1, p->NY / 2) * (16 + 8);  // Wy64, Wy32

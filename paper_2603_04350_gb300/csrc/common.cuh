@@ -198,6 +198,27 @@ EXPD_HD void fft_dif(T2* x, int log2n, const T2* tw, int ts, int sign, int lane,
     }
 }
 
+// ---- coefficient helpers: real a_j E^j (diffusion) or complex (advection) ----
+// acc + c, and r - c x, for a real or a complex coefficient c
+EXPD_HD float2 acc_add(float2 a, float c) { return make_float2(a.x + c, a.y); }
+EXPD_HD float2 acc_add(float2 a, float2 c) { return cadd(a, c); }
+EXPD_HD double2 acc_add(double2 a, double c) { return make_double2(a.x + c, a.y); }
+EXPD_HD double2 acc_add(double2 a, double2 c) { return cadd(a, c); }
+EXPD_HD float2 sub_cx(float2 r, float c, float2 x) { return make_float2(fmaf(-c, x.x, r.x), fmaf(-c, x.y, r.y)); }
+EXPD_HD float2 sub_cx(float2 r, float2 c, float2 x) { return csub(r, cmul(c, x)); }
+EXPD_HD double2 sub_cx(double2 r, double c, double2 x) { return make_double2(fma(-c, x.x, r.x), fma(-c, x.y, r.y)); }
+EXPD_HD double2 sub_cx(double2 r, double2 c, double2 x) { return csub(r, cmul(c, x)); }
+template <typename C>
+EXPD_HD C coef_zero();
+template <>
+EXPD_HD float coef_zero<float>() { return 0.0f; }
+template <>
+EXPD_HD double coef_zero<double>() { return 0.0; }
+template <>
+EXPD_HD float2 coef_zero<float2>() { return make_float2(0.0f, 0.0f); }
+template <>
+EXPD_HD double2 coef_zero<double2>() { return make_double2(0.0, 0.0); }
+
 // ------------------------------------------------------- register FFTs ---
 // Length-R FFTs on a register array (compile-time indices, fully unrolled).
 // tw[k * TS] = exp(-2 pi i k / R) for k < R/2 (a table of a longer length,

@@ -183,3 +183,13 @@ template <>
 EXPD_HD float2 cvt2<float2>(dd2 v) { return dd2_to_c32(v); }
 template <>
 EXPD_HD dd2 cvt2<dd2>(dd2 v) { return v; }
+
+// coefficient helpers (see common.cuh) for double-float storage
+EXPD_HD dd2 acc_add(dd2 a, dd c) { return c2(a.x + c, a.y); }
+EXPD_HD dd2 acc_add(dd2 a, dd2 c) { return cadd(a, c); }
+EXPD_HD dd2 sub_cx(dd2 r, dd c, dd2 x) { return c2(r.x - c * x.x, r.y - c * x.y); }
+EXPD_HD dd2 sub_cx(dd2 r, dd2 c, dd2 x) { return csub(r, cmul(c, x)); }
+template <>
+EXPD_HD dd coef_zero<dd>() { return dd(0.0f, 0.0f); }
+template <>
+EXPD_HD dd2 coef_zero<dd2>() { return c2(dd(0.0f, 0.0f), dd(0.0f, 0.0f)); }

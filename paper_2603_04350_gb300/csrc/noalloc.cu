@@ -203,6 +203,7 @@ extern "C" expd_status expd_precond_apply_noalloc(const expd_grid* grid, const e
     expd_plan p = &pl;
     expd_status st = plan_init_fields(p, grid, op, dt, Nt, alpha, scheme);
     if (st != EXPD_OK) return st;
+    if (p->adv) return expd_fail(EXPD_ERR_UNSUPPORTED, "the no-allocation entry point has no advection tables");
     p->fast_dst = 0;  // Dirichlet transforms use the dense sine matrices built below
     int L = 1;
     while (L < p->Ns) L <<= 1;

@@ -41,6 +41,8 @@ struct expd_plan_s {
     int bc = EXPD_BC_PERIODIC;
     double LX = 1, LY = 1;
     double a = 0, c = 0;
+    double bx = 0, by = 0;  // advection velocity along NX / NY
+    int adv = 0;            // advection present: complex symbol, complex E and coefficient tables
     int nonlin = EXPD_NL_NONE;
     double dt = 0;
     int Nt = 0, order = 1, Ns = 0;

@@ -248,20 +248,40 @@ struct CombineArgs {
     const double* src;
     double g;
     double* out;
-    const double* E;
+    const double* E;  // E_m (real), or (Re, Im) pairs with advection
     long long nelem;
     int eshift;
+    int adv;
 };
+
+// a_j E^j z for one stored double of a complex mode z: with a complex E the
+// element e (real part for even e, imaginary for odd) also needs its partner
+__device__ __forceinline__ double cmul_elem(double cr, double ci, const double* z, long long e) {
+    const double self = z[e], other = z[e ^ 1];
+    return (e & 1) ? fma(cr, self, ci * other) : fma(cr, self, -ci * other);
+}
 
 __global__ void combine_kernel(CombineArgs a) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < a.nelem;
          e += (long long)gridDim.x * blockDim.x) {
-        const double Em = a.E[e >> a.eshift];
         double acc = a.src ? a.g * a.src[e] : 0.0;
-        double Ej = 1.0;
-        for (int j = 0; j < a.q; ++j) {
-            Ej *= Em;
-            acc = fma(a.coef[j] * Ej, a.in[j][e], acc);
+        if (!a.adv) {
+            const double Em = a.E[e >> a.eshift];
+            double Ej = 1.0;
+            for (int j = 0; j < a.q; ++j) {
+                Ej *= Em;
+                acc = fma(a.coef[j] * Ej, a.in[j][e], acc);
+            }
+        } else {
+            const long long m = e >> 1;
+            const double er = a.E[2 * m], ei = a.E[2 * m + 1];
+            double pr = 1.0, pi = 0.0;  // E^j
+            for (int j = 0; j < a.q; ++j) {
+                const double t = pr * er - pi * ei;
+                pi = pr * ei + pi * er;
+                pr = t;
+                acc += cmul_elem(a.coef[j] * pr, a.coef[j] * pi, a.in[j], e);
+            }
         }
         a.out[e] = acc;
     }
@@ -273,6 +293,7 @@ struct RhsArgs {
     double* Fh;        // [Ns][nelem]
     float* F32;        // optional float32 copy [Ns][nelem]
     int fh_dd;         // write Fh as double-float (hi, lo) instead of float64
+    int adv;           // E holds complex (Re, Im) pairs
     const double* E;
     double a[7];
     double bdt;
@@ -288,12 +309,22 @@ __global__ void rhs_kernel(RhsArgs r) {
         const long long idx = (long long)i * r.nelem + e;
         const int n = r.s + i;
         double acc = r.fh ? r.bdt * r.fh[(long long)(n - 1) * r.nelem + e] : 0.0;
-        if (i < r.s) {
+        if (i < r.s && !r.adv) {
             const double Em = r.E[e >> r.eshift];
             double Ej = 1.0;
             for (int j = 1; j <= r.s; ++j) {
                 Ej *= Em;
                 if (n - j < r.s) acc = fma(r.a[j] * Ej, r.Sh[(long long)(n - j) * r.nelem + e], acc);
+            }
+        } else if (i < r.s) {
+            const long long m = e >> 1;
+            const double er = r.E[2 * m], ei = r.E[2 * m + 1];
+            double pr = 1.0, pi = 0.0;
+            for (int j = 1; j <= r.s; ++j) {
+                const double t = pr * er - pi * ei;
+                pi = pr * ei + pi * er;
+                pr = t;
+                if (n - j < r.s) acc += cmul_elem(r.a[j] * pr, r.a[j] * pi, r.Sh + (long long)(n - j) * r.nelem, e);
             }
         }
         if (r.F32) r.F32[idx] = f32_rn_from_f64(acc);
@@ -1094,6 +1125,7 @@ expd_status eigen_combine(expd_plan p, void* out, const void* const* in, const d
     a.g = g;
     a.out = static_cast<double*>(out);
     a.E = p->E;
+    a.adv = p->adv;
     a.eshift = p->realcol ? 0 : 1;
     a.nelem = p->Mcol << a.eshift;
     KProf kp(p, s, EXPD_K_POINTWISE, 8.0 * a.nelem * (q + (src ? 2 : 1)), 2.0 * a.nelem * q);
@@ -1110,6 +1142,7 @@ expd_status assemble_rhs(expd_plan p, const void* fh, cudaStream_t s, float* F32
     r.F32 = F32;
     r.fh_dd = fh_dd;
     r.E = p->E;
+    r.adv = p->adv;
     for (int j = 0; j < 7; ++j) r.a[j] = p->acoef[p->order][j];
     r.bdt = p->beta[p->order] * p->dt;
     r.eshift = p->realcol ? 0 : 1;

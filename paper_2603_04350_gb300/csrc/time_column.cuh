@@ -8,15 +8,16 @@
 //     s_n = v_n * scale / alpha^(n/Ns),
 //     s   = Gamma^{-1} F^* diag(1/d) F Gamma q   (F: omega = e^{+2 pi i/Ns})
 // where d_k = one - sum_{j=1..order} cj[j] lambda_k^j and cj[j] = a_j E^j
-// (cj[1..6] valid, entries beyond `order` ignored; one = 1 except for the
-// shifted solve of the inexact Newton variant).
+// (cj[1..6] valid, entries beyond `order` ignored; real, or complex with
+// advection; one = 1 except for the shifted solve of the inexact Newton
+// variant).
 #pragma once
 
 #include "common.cuh"
 
-template <typename PT, typename PT2>
+template <typename PT, typename PT2, typename CJ>
 EXPD_HD double precond_column(PT2* w, int Ns, int L, int log2L, int bluestein, const PT2* tw, const PT2* lam,
-                              const PT2* chirp, const PT2* bp, const PT2* bm, const PT* cj, int order,
+                              const PT2* chirp, const PT2* bp, const PT2* bm, const CJ* cj, int order,
                               int lane, int nlanes, PT one = (PT)1) {
     if (bluestein) {
         for (int n = lane; n < Ns; n += nlanes) w[n] = cmul(w[n], chirp[n]);
@@ -35,9 +36,9 @@ EXPD_HD double precond_column(PT2* w, int Ns, int L, int log2L, int bluestein, c
     }
     // Step (b): Z_k = Y_k / d_k, d_k = 1 - sum_j cj[j] lambda_k^j (Horner,
     // unrolled over the at most six coefficients so they stay in registers)
-    PT cp[7];
+    CJ cp[7];
 #pragma unroll
-    for (int j = 1; j <= 6; ++j) cp[j] = j <= order ? cj[j] : (PT)0;
+    for (int j = 1; j <= 6; ++j) cp[j] = j <= order ? cj[j] : coef_zero<CJ>();
     for (int k = lane; k < Ns; k += nlanes) {
         const PT2 lk = lam[k];
         PT2 acc = c2((PT)0, (PT)0);
@@ -45,7 +46,7 @@ EXPD_HD double precond_column(PT2* w, int Ns, int L, int log2L, int bluestein, c
         for (int j = 6; j >= 1; --j) {
             if (j <= order) {
                 acc = cmul(lk, acc);
-                acc.x += cp[j];
+                acc = acc_add(acc, cp[j]);
             }
         }
         acc = cmul(lk, acc);

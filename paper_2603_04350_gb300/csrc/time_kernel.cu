@@ -91,8 +91,22 @@ __device__ __forceinline__ typename cplx<ST>::t ldnl(const void* p, long long i,
 }
 
 
+// a_j E_m^j: real tables, or (with advection) complex tables of the same
+// layout with (Re, Im) pairs
 template <typename T>
 __device__ __forceinline__ T coef(const TimeArgs& A, int j, long long m);
+template <>
+__device__ __forceinline__ double2 coef<double2>(const TimeArgs& A, int j, long long m) {
+    return reinterpret_cast<const double2*>(A.C64)[(long long)(j - 1) * A.Mcol + m];
+}
+template <>
+__device__ __forceinline__ float2 coef<float2>(const TimeArgs& A, int j, long long m) {
+    return reinterpret_cast<const float2*>(A.C32)[(long long)(j - 1) * A.Mcol + m];
+}
+template <>
+__device__ __forceinline__ dd2 coef<dd2>(const TimeArgs& A, int j, long long m) {
+    return reinterpret_cast<const dd2*>(A.Cdd)[(long long)(j - 1) * A.Mcol + m];
+}
 template <>
 __device__ __forceinline__ double coef<double>(const TimeArgs& A, int j, long long m) {
     return A.C64[(long long)(j - 1) * A.Mcol + m];
@@ -116,7 +130,7 @@ __device__ __forceinline__ ST mode_weight(long long m, int KX, int NX, int realc
 // PT: precision of steps (a)-(c); ST: precision of the stored state, the
 // right-hand side and the residual arithmetic (float32 sweeps never touch the
 // float64 pipe, whose rate on GB300 is 1/64 of float32).
-template <typename PT, typename ST, bool REAL>
+template <typename PT, typename ST, bool REAL, bool ADV>
 __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A) {
     typedef typename cplx<PT>::t PT2;
     typedef typename cplx<ST>::t ST2;
@@ -189,14 +203,16 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
         const long long m = m0 + warp;
         if (warp < C && m < Mcol) {
             // a_j E_m^j from the plan's tables (no float64 arithmetic here)
-            ST cs[7];
-            PT cp[7];
-            cs[0] = (ST)0;
-            cp[0] = (PT)0;
+            typedef typename std::conditional<ADV, ST2, ST>::type CS;
+            typedef typename std::conditional<ADV, PT2, PT>::type CP;
+            CS cs[7];
+            CP cp[7];
+            cs[0] = coef_zero<CS>();
+            cp[0] = coef_zero<CP>();
 #pragma unroll
             for (int j = 1; j <= 6; ++j) {
-                cs[j] = j <= A.order ? coef<ST>(A, j, m) : (ST)0;
-                cp[j] = j <= A.order ? coef<PT>(A, j, m) : (PT)0;
+                cs[j] = j <= A.order ? coef<CS>(A, j, m) : coef_zero<CS>();
+                cp[j] = j <= A.order ? coef<CP>(A, j, m) : coef_zero<CP>();
             }
             PT2* w = sW + (size_t)warp * L;
             const ST2* xc = sX + (size_t)warp * P;
@@ -208,11 +224,7 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
                     ST2 rx = xc[n];
 #pragma unroll
                     for (int j = 1; j <= 6; ++j) {
-                        if (j <= A.order && j <= n) {
-                            const ST2 xv = xc[n - j];
-                            rx.x = fma(-cs[j], xv.x, rx.x);
-                            rx.y = fma(-cs[j], xv.y, rx.y);
-                        }
+                        if (j <= A.order && j <= n) rx = sub_cx(rx, cs[j], xc[n - j]);
                     }
                     q.x = fma(sigR, rx.x, q.x);
                     q.y = fma(sigR, rx.y, q.y);
@@ -225,8 +237,8 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
             }
             if (A.precond) {
                 EXPD_SYNCWARP();
-                precond_column<PT, PT2>(w, Ns, L, A.log2L, A.bluestein, tw, lam, chirp, bp, bm, cp, A.order, lane, 32,
-                                        (PT)(1.0 - A.dshift));
+                precond_column<PT, PT2, CP>(w, Ns, L, A.log2L, A.bluestein, tw, lam, chirp, bp, bm, cp, A.order, lane,
+                                            32, (PT)(1.0 - A.dshift));
                 for (int n = lane; n < Ns; n += 32) {
                     const ST2 v = cvt2<ST2>(w[A.bluestein ? n : (int)bitrev(n, A.log2L)]);
                     rc[n] = cscale(v, osc[n]);
@@ -319,7 +331,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // STAGE_ALL: X, F and N(u) staged through shared memory; otherwise only X (read
 // twice) is staged and F, N(u) are loaded where they are used (wide elements
 // would otherwise limit the CTAs per SM by shared memory).
-template <int NS, int G, typename ST, bool REAL, bool STAGE_ALL>
+template <int NS, int G, typename ST, bool REAL, bool STAGE_ALL, bool ADV>
 __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
     typedef typename cplx<ST>::t ST2;
     constexpr int R = NS / G;
@@ -369,12 +381,14 @@ __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
         const long long m = base + (tid / G);
         const bool valid = m < Mcol;
         const long long mm = valid ? m : 0;
-        ST cs[7];
-        float cp[7];
+        typedef typename std::conditional<ADV, ST2, ST>::type CS;
+        typedef typename std::conditional<ADV, float2, float>::type CP;
+        CS cs[7];
+        CP cp[7];
 #pragma unroll
         for (int j = 1; j <= 6; ++j) {
-            cs[j] = (valid && j <= order) ? coef<ST>(A, j, mm) : (ST)0;
-            cp[j] = (valid && j <= order) ? coef<float>(A, j, mm) : 0.0f;
+            cs[j] = (valid && j <= order) ? coef<CS>(A, j, mm) : coef_zero<CS>();
+            cp[j] = (valid && j <= order) ? coef<CP>(A, j, mm) : coef_zero<CP>();
         }
         const float wgt = valid ? (float)mode_weight<float>(mm, A.KX, A.NX, A.realcol) : 0.0f;
         // ---- stage the column slices: every load of the tile in flight at once ----
@@ -432,8 +446,7 @@ __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
                             if (dsend == d) send = xw[d];
                         ST2 xv = shfl_c(send, gl0 + gs);
                         if (n - i < 0) xv = c2((ST)0, (ST)0);  // before the window: in F
-                        rx.x = fma(-cs[i], xv.x, rx.x);
-                        rx.y = fma(-cs[i], xv.y, rx.y);
+                        rx = sub_cx(rx, cs[i], xv);
                     }
                 }
                 q.x = fma(sigR, rx.x, q.x);
@@ -462,11 +475,11 @@ __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
 #pragma unroll
         for (int p = 0; p < R; ++p) {
             const float2 lk = lam[(int)bitrev((unsigned)p, LOGR) + k2R];
-            float2 acc = make_float2(cp[6], 0.0f);
+            float2 acc = acc_add(make_float2(0.0f, 0.0f), cp[6]);
 #pragma unroll
             for (int j = 5; j >= 1; --j) {
                 acc = cmul(lk, acc);
-                acc.x += cp[j];
+                acc = acc_add(acc, cp[j]);
             }
             acc = cmul(lk, acc);
             w[p] = cdiv(w[p], make_float2(one - acc.x, -acc.y));
@@ -558,7 +571,7 @@ __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
     }
 }
 
-template <int NS, typename ST, bool REAL>
+template <int NS, typename ST, bool REAL, bool ADV>
 expd_status launch_reg(expd_plan p, TimeArgs& a, cudaStream_t s) {
     const TimeTables& ts = std::is_same<ST, float>::value ? p->t32 : p->t64;
     a.gam = std::is_same<ST, dd>::value ? p->gamdd : ts.gam;
@@ -577,7 +590,7 @@ expd_status launch_reg(expd_plan p, TimeArgs& a, cudaStream_t s) {
     constexpr bool all = !std::is_same<ST, dd>::value;  // double-float (16-byte) elements stage only X
     const int narr = (a.X ? 1 : 0) + (all ? (a.F ? 1 : 0) + (a.NL ? 1 : 0) : 0);
     const size_t smem = (size_t)std::max(narr, 1) * NS * REG_THREADS / G * (size_t)esz;  // R slots per thread
-    auto kern = time_reg_kernel<NS, G, ST, REAL, all>;
+    auto kern = time_reg_kernel<NS, G, ST, REAL, all, ADV>;
     EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
     kern<<<(int)grid, REG_THREADS, smem, s>>>(a);
     EXPD_CUDA_TRY(cudaGetLastError());
@@ -585,12 +598,12 @@ expd_status launch_reg(expd_plan p, TimeArgs& a, cudaStream_t s) {
     return EXPD_OK;
 }
 
-template <typename ST, bool REAL>
+template <typename ST, bool REAL, bool ADV>
 expd_status launch_reg_ns(expd_plan p, TimeArgs& a, cudaStream_t s) {
     switch (p->Ns) {
-        case 16: return launch_reg<16, ST, REAL>(p, a, s);
-        case 32: return launch_reg<32, ST, REAL>(p, a, s);
-        case 64: return launch_reg<64, ST, REAL>(p, a, s);
+        case 16: return launch_reg<16, ST, REAL, ADV>(p, a, s);
+        case 32: return launch_reg<32, ST, REAL, ADV>(p, a, s);
+        case 64: return launch_reg<64, ST, REAL, ADV>(p, a, s);
     }
     return expd_fail(EXPD_ERR_UNSUPPORTED, "register time kernel needs Ns in {16, 32, 64}");
 }
@@ -649,7 +662,7 @@ size_t time_smem_bytes(int Ns, int L, int bluestein, size_t pt2, size_t st) {
     return b;
 }
 
-template <typename PT, typename ST, bool REAL>
+template <typename PT, typename ST, bool REAL, bool ADV>
 expd_status launch_time(expd_plan p, TimeArgs& a, cudaStream_t s) {
     const TimeTables& t = std::is_same<PT, float>::value ? p->t32 : p->t64;
     const TimeTables& ts = std::is_same<ST, float>::value ? p->t32 : p->t64;
@@ -664,7 +677,7 @@ expd_status launch_time(expd_plan p, TimeArgs& a, cudaStream_t s) {
     a.log2L = t.log2L;
     a.bluestein = t.bluestein;
     const size_t smem = time_smem_bytes(p->Ns, t.L, t.bluestein, sizeof(typename cplx<PT>::t), sizeof(ST));
-    auto kern = time_kernel<PT, ST, REAL>;
+    auto kern = time_kernel<PT, ST, REAL, ADV>;
     EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
     const double esz = (REAL ? 1.0 : 2.0) * sizeof(ST);
     const double nlsz = (REAL ? 1.0 : 2.0) * (a.nl_f32 ? 4.0 : 8.0);
@@ -766,7 +779,7 @@ expd_status time_grid_for(expd_plan p, int* grid_out) {
     if (smem64 > 227 * 1024) return expd_fail(EXPD_ERR_UNSUPPORTED, "time window too long for shared memory");
     // the float32-sweep variant (the most frequent launch) sets the grid
     const size_t smem = time_smem_bytes(p->Ns, L, blue, sizeof(float2), sizeof(float));
-    auto kern = p->realcol ? time_kernel<float, float, true> : time_kernel<float, float, false>;
+    auto kern = p->realcol ? time_kernel<float, float, true, false> : time_kernel<float, float, false, false>;
     EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
     EXPD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * EXPD_TIME_COLS, smem));
     if (per_sm < 1) per_sm = 1;
@@ -815,22 +828,35 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s) {
     if (reg && !op.stdd) {
         if (op.st32) {
             if (op.NL && !op.nl_f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 storage needs float32 N");
-            return p->realcol ? launch_reg_ns<float, true>(p, a, s) : launch_reg_ns<float, false>(p, a, s);
+            return p->realcol ? launch_reg_ns<float, true, false>(p, a, s)
+                   : p->adv   ? launch_reg_ns<float, false, true>(p, a, s)
+                              : launch_reg_ns<float, false, false>(p, a, s);
         }
         if (!op.NL || !op.nl_f32)
-            return p->realcol ? launch_reg_ns<double, true>(p, a, s) : launch_reg_ns<double, false>(p, a, s);
+            return p->realcol ? launch_reg_ns<double, true, false>(p, a, s)
+                   : p->adv   ? launch_reg_ns<double, false, true>(p, a, s)
+                              : launch_reg_ns<double, false, false>(p, a, s);
     }
     if (op.stdd) {
         if (!op.f32) return expd_fail(EXPD_ERR_INVALID_ARG, "double-float storage needs the float32 preconditioner");
-        return p->realcol ? launch_time<float, dd, true>(p, a, s) : launch_time<float, dd, false>(p, a, s);
+        return p->realcol ? launch_time<float, dd, true, false>(p, a, s)
+               : p->adv   ? launch_time<float, dd, false, true>(p, a, s)
+                          : launch_time<float, dd, false, false>(p, a, s);
     }
     if (op.st32) {
         if (!op.f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 storage needs the float32 preconditioner");
         if (op.NL && !op.nl_f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 storage needs float32 N");
-        return p->realcol ? launch_time<float, float, true>(p, a, s) : launch_time<float, float, false>(p, a, s);
+        return p->realcol ? launch_time<float, float, true, false>(p, a, s)
+               : p->adv   ? launch_time<float, float, false, true>(p, a, s)
+                          : launch_time<float, float, false, false>(p, a, s);
     }
-    if (op.f32) return p->realcol ? launch_time<float, double, true>(p, a, s) : launch_time<float, double, false>(p, a, s);
-    return p->realcol ? launch_time<double, double, true>(p, a, s) : launch_time<double, double, false>(p, a, s);
+    if (op.f32)
+        return p->realcol ? launch_time<float, double, true, false>(p, a, s)
+               : p->adv   ? launch_time<float, double, false, true>(p, a, s)
+                          : launch_time<float, double, false, false>(p, a, s);
+    return p->realcol ? launch_time<double, double, true, false>(p, a, s)
+           : p->adv   ? launch_time<double, double, false, true>(p, a, s)
+                      : launch_time<double, double, false, false>(p, a, s);
 }
 
 expd_status time_reduce(expd_plan p, cudaStream_t s) {

@@ -41,7 +41,7 @@ class Grid(C.Structure):
 
 
 class Operator(C.Structure):
-    _fields_ = [("a", C.c_double), ("c", C.c_double), ("nonlin", C.c_int)]
+    _fields_ = [("a", C.c_double), ("c", C.c_double), ("nonlin", C.c_int), ("b", C.c_double * 2)]
 
 
 class Scheme(C.Structure):
@@ -169,6 +169,7 @@ class PlanSpec:
     gmres_restart: int = 20
     startup: int = STARTUP_RAMP
     jacobian: int = 0
+    b: tuple = (0.0, 0.0)
 
 
 def _structs(spec: PlanSpec):
@@ -178,7 +179,7 @@ def _structs(spec: PlanSpec):
         g.n[d] = int(spec.n[d])
         g.length[d] = float(spec.length[d])
     g.bc = spec.bc
-    o = Operator(spec.a, spec.c, spec.nonlin)
+    o = Operator(spec.a, spec.c, spec.nonlin, (C.c_double * 2)(*(tuple(spec.b) + (0.0, 0.0))[:2]))
     s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup, spec.jacobian)
     return g, o, s
 
@@ -211,7 +212,7 @@ def plan_create(spec: PlanSpec, stream=None) -> "Plan":
         g.n[d] = int(spec.n[d])
         g.length[d] = float(spec.length[d])
     g.bc = spec.bc
-    o = Operator(spec.a, spec.c, spec.nonlin)
+    o = Operator(spec.a, spec.c, spec.nonlin, (C.c_double * 2)(*(tuple(spec.b) + (0.0, 0.0))[:2]))
     s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup, spec.jacobian)
     h = C.c_void_p()
     _check(lib().expd_plan_create(C.byref(g), C.byref(o), spec.dt, spec.Nt, spec.alpha, C.byref(s),
@@ -301,4 +302,4 @@ def spec_from_problem(p, precision: int = PREC_FP64, max_iter: int = 100, tol: O
                     a=p.a, c=p.c, nonlin=NL_ALLEN_CAHN if p.nonlin == "allen_cahn" else NL_NONE, dt=p.dt,
                     Nt=p.Nt, alpha=p.alpha, order=p.order, precision=precision, max_iter=max_iter,
                     tol=p.tol if tol is None else tol, gmres_restart=gmres_restart, startup=startup,
-                    jacobian=jacobian)
+                    jacobian=jacobian, b=tuple(getattr(p, "b", ()) or (0.0, 0.0)))

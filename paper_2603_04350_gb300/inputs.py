@@ -32,7 +32,7 @@ class Problem:
     n       grid points per dimension (periodic) or interior points (Dirichlet)
     length  domain length per dimension; periodic grid x_j = j*L/n,
             Dirichlet grid x_j = j*L/(n+1), j = 1..n
-    a, c    L = a*Lap - c  (Sec. 1, Eq. (1.2))
+    a, c    L = a*Lap - c  (Sec. 1, Eq. (1.2)); b adds advection -b.grad
     nonlin  N(u): "none" or "allen_cahn" (N(u) = u - u^3)
     dt, Nt  time step and number of steps; the window is T = Nt*dt
     alpha   the alpha-circulant parameter (Sec. 2)
@@ -57,6 +57,7 @@ class Problem:
     u0_kind: str = "uniform"
     u0_range: Tuple[float, float] = (-0.9, 0.9)
     u0_lowpass: Optional[int] = None
+    b: Tuple[float, ...] = ()   # advection velocity per axis (periodic): L = a*Lap - b.grad - c
 
     @property
     def ndim(self) -> int:

@@ -41,12 +41,12 @@ def relmax(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-def P(name, bc, n, order, nonlin="none", Nt=None, alpha=1e-2, a=None, c=0.1, dt=0.01, forcing=False):
+def P(name, bc, n, order, nonlin="none", Nt=None, alpha=1e-2, a=None, c=0.1, dt=0.01, forcing=False, b=()):
     length = tuple(2 * math.pi if bc == "periodic" else 1.0 for _ in n)
     if a is None:
         a = 0.05 if bc == "periodic" else 0.01
     return I.Problem(name=name, bc=bc, n=tuple(n), length=length, a=a, c=c, nonlin=nonlin, dt=dt,
-                     Nt=Nt if Nt is not None else order + 9, alpha=alpha, order=order, forcing=forcing)
+                     Nt=Nt if Nt is not None else order + 9, alpha=alpha, order=order, forcing=forcing, b=tuple(b))
 
 
 # Sizes span several time-kernel tiles (8 modes each) and ragged tails:
@@ -509,3 +509,76 @@ def test_mean_jacobian_full_size_allen_cahn_256(expd):
         assert O.rel_error(host(U), ref) < p.tol, (jac, info)
         its[jac] = info["iterations"]
     assert its[expd.JAC_MEAN_U0] <= its[expd.JAC_LAGGED], its
+
+
+# ------------------------------------------- advection-diffusion (periodic) --
+# complex symbol -a|k|^2 - i b.k - c: register kernel (Ns = 16, 32) and
+# shared-memory kernel (Ns = 11, Bluestein), float64, mixed and double-float
+ADV_CASES = [
+    P("adv_1d_s1", "periodic", (64,), 1, Nt=16, b=(1.5,)),
+    P("adv_2d_s2", "periodic", (16, 32), 2, Nt=12, b=(0.7, -1.2)),
+    P("adv_2d_s6", "periodic", (32, 32), 6, Nt=37, b=(2.0, 0.5)),
+    P("adv_2d_ac_s1", "periodic", (16, 32), 1, nonlin="allen_cahn", a=0.01, c=0.0, dt=1e-3, Nt=16, alpha=1e-3,
+      b=(0.5, 1.0)),
+]
+ADV_IDS = [p.name for p in ADV_CASES]
+
+
+@pytest.mark.parametrize("p", ADV_CASES, ids=ADV_IDS)
+def test_advection_precond_and_residual(expd, p):
+    sp = O.spec_of(p)
+    r = rand_field(p, (p.Ns,), 21)
+    ref = O.precond_apply(sp, r)
+    for prec, bound in ((expd.PREC_FP64, 1e-11), (expd.PREC_MIXED, 6e-8 * 16 / p.alpha)):
+        S = torch.empty_like(dev(r))
+        with expd.plan_create(expd.spec_from_problem(p, precision=prec)) as plan:
+            plan.precond_apply(dev(r), S)
+        assert relmax(host(S), ref) < bound, prec
+    rng = np.random.default_rng(22)
+    u0 = rng.uniform(-0.5, 0.5, p.n)
+    U = rng.uniform(-0.5, 0.5, (p.Nt,) + p.n)
+    f = rng.standard_normal((p.Nt,) + p.n)
+    U_start = np.concatenate([u0[None], U[: p.order - 1]])
+    ref = O.residual(sp, U[p.order - 1:], O.rhs_known(sp, U_start, f))
+    R = torch.empty((p.Ns,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p)) as plan:
+        plan.residual(dev(u0), dev(f), dev(U), R)
+    assert relmax(host(R), ref) < 1e-11
+
+
+@pytest.mark.parametrize("p", ADV_CASES, ids=ADV_IDS)
+def test_advection_solvers_match_sequential(expd, p):
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(23)
+    u0 = rng.uniform(-0.8, 0.8, p.n)
+    f = rng.standard_normal((p.Nt,) + p.n) if p.nonlin == "none" else None
+    ref = O.sequential_solve(sp, u0, f)[1:]
+    fd = None if f is None else dev(f)
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p)) as plan:
+        plan.solve_sequential(dev(u0), fd, U)
+        assert O.rel_error(host(U), ref) < 1e-12
+    for prec in (expd.PREC_FP64, expd.PREC_MIXED):
+        with expd.plan_create(expd.spec_from_problem(p, precision=prec, tol=1e-12, max_iter=200)) as plan:
+            info = plan.solve_fp(dev(u0), fd, U)
+        assert O.rel_error(host(U), ref) < 1e-10, (prec, info)
+    if p.nonlin == "none":
+        with expd.plan_create(expd.spec_from_problem(p, tol=1e-12, max_iter=200)) as plan:
+            plan.solve_gmres(dev(u0), fd, U)
+            assert O.rel_error(host(U), ref) < 1e-10
+            plan.solve_bicgstab(dev(u0), fd, U)
+            assert O.rel_error(host(U), ref) < 1e-10
+
+
+def test_advection_richardson_iterates_match_oracle(expd):
+    p = ADV_CASES[1]
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(24)
+    u0 = rng.uniform(-0.8, 0.8, p.n)
+    f = rng.standard_normal((p.Nt,) + p.n)
+    for k in (1, 2, 3):
+        ref = O.richardson(sp, u0, f, max_iter=k).U[1:]
+        U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+        with expd.plan_create(expd.spec_from_problem(p, tol=1e-300, max_iter=k)) as plan:
+            plan.solve_fp(dev(u0), dev(f), U, allow_not_converged=True)
+        assert O.rel_error(host(U), ref) < 1e-12

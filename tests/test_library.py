@@ -75,6 +75,8 @@ def _spec(expd, **kw):
     (dict(gmres_restart=0), "gmres_restart"),
     (dict(precision=7), "precision"),
     (dict(n=(8, 8, 8)), "ndim"),
+    (dict(bc=1, n=(7, 7), b=(0.5, 0.0)), "advection needs a periodic grid"),
+    (dict(jacobian=5), "jacobian"),
 ])
 def test_plan_create_rejects_bad_arguments_without_touching_the_gpu(expd, kw, msg):
     spec = _spec(expd, **kw)
