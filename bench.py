@@ -399,6 +399,7 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
            "config": config_dict(p, world),
            "iterations": infos[-1]["iterations"], "fp32_iterations": infos[-1]["fp32_iterations"],
+           "error_estimate_history": infos[-1]["history"],
            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
            "ms_per_step_with_kernel_events": statistics.mean(ms_ev),
            "fp64_path": {"value": value64, "ms_per_step": statistics.mean(ms64),

@@ -145,8 +145,10 @@ typedef struct expd_plan_s* expd_plan;
  * (see expd_plan_workspace_bytes) and builds the spectral tables (the
  * eigenvalues of L_h, exp(dt mu), the alpha-circulant eigenvalues
  * lambda_n = alpha^(1/Ns) e^{2 pi i n/Ns} and Gamma_alpha of Sec. 2, BDF
- * coefficients).  Requires 0 < alpha < 1, dt > 0, Nt >= order + 1,
- * beta_s*dt < 1 for nonlinear problems.  `stream` orders the table uploads.
+ * coefficients).  Requires 0 < alpha < 1, dt > 0, order + 1 <= Nt and
+ * Nt - order + 1 <= 512 (EXPD_ERR_UNSUPPORTED above: a time column of 8 modes
+ * must fit one CTA's shared memory), beta_s*dt < 1 for nonlinear problems.
+ * `stream` orders the table uploads.
  * On failure *out is NULL and nothing stays allocated. */
 expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, double dt, int Nt,
                              double alpha, const expd_scheme* scheme, void* stream,

@@ -12,7 +12,9 @@
 // Largest supported sizes (shared memory per warp-FFT column).
 #define EXPD_MAX_PERIODIC_N 4096
 #define EXPD_MAX_DIRICHLET_N 4096
-#define EXPD_MAX_NS 2048
+// Unknown slices per plan: a time column (Ns values, or the Bluestein length
+// L <= 1024 for Ns <= 512) of 8 modes sits in one CTA's shared memory in float64
+#define EXPD_MAX_NS 512
 #define EXPD_TIME_COLS 8  // time-direction columns (spatial modes) per CTA
 
 expd_status expd_cuda_fail(cudaError_t e, const char* what, const char* file, int line);

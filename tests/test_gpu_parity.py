@@ -582,3 +582,20 @@ def test_advection_richardson_iterates_match_oracle(expd):
         with expd.plan_create(expd.spec_from_problem(p, tol=1e-300, max_iter=k)) as plan:
             plan.solve_fp(dev(u0), dev(f), U, allow_not_converged=True)
         assert O.rel_error(host(U), ref) < 1e-12
+
+
+# ------------------------------------------------------------ largest window --
+@pytest.mark.parametrize("Nt,order", [(512, 1), (517, 6)])   # Ns = 512 (radix-2), 512 (order 6)
+def test_largest_window(expd, Nt, order):
+    p = P(f"max_ns_s{order}", "periodic", (16,), order, Nt=Nt, alpha=0.05, a=0.05, c=0.1, dt=1e-3, forcing=True)
+    assert p.Ns == 512
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(25)
+    u0 = rng.standard_normal(p.n)
+    f = rng.standard_normal((p.Nt,) + p.n)
+    ref = O.sequential_solve(sp, u0, f)[1:]
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    for prec in (expd.PREC_FP64, expd.PREC_MIXED):
+        with expd.plan_create(expd.spec_from_problem(p, precision=prec, tol=1e-12, max_iter=200)) as plan:
+            plan.solve_fp(dev(u0), dev(f), U)
+        assert O.rel_error(host(U), ref) < 1e-10, prec

@@ -60,6 +60,12 @@ def _spec(expd, **kw):
     return expd.PlanSpec(**base)
 
 
+def test_plan_create_rejects_too_long_windows_without_touching_the_gpu(expd):
+    with pytest.raises(expd.ExpdError) as ei:
+        expd.plan_create(_spec(expd, n=(16,), length=(1.0,), Nt=514, order=2))   # Ns = 513
+    assert ei.value.status == expd.ERR_UNSUPPORTED and "512" in str(ei.value)
+
+
 @pytest.mark.parametrize("kw,msg", [
     (dict(alpha=1.5), "alpha"),
     (dict(alpha=0.0), "alpha"),
