@@ -328,10 +328,8 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// STAGE_ALL: X, F and N(u) staged through shared memory; otherwise only X (read
-// twice) is staged and F, N(u) are loaded where they are used (wide elements
-// would otherwise limit the CTAs per SM by shared memory).
-template <int NS, int G, typename ST, bool REAL, bool STAGE_ALL, bool ADV>
+// ADV: complex a_j E^j (advection); otherwise real.
+template <int NS, int G, typename ST, bool REAL, bool ADV>
 __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
     typedef typename cplx<ST>::t ST2;
     constexpr int R = NS / G;
@@ -397,10 +395,8 @@ __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
         for (int j = 0; j < R; ++j) {
             const long long gi = (long long)(G * j + g) * Mcol + mm;
             if (A.X) cp_async_elem<ESZ>(&stage[(ix * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.X) + gi, valid);
-            if (STAGE_ALL && A.F)
-                cp_async_elem<ESZ>(&stage[(iF * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.F) + gi, valid);
-            if (STAGE_ALL && A.NL)
-                cp_async_elem<ESZ>(&stage[(iN * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.NL) + gi, valid);
+            if (A.F) cp_async_elem<ESZ>(&stage[(iF * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.F) + gi, valid);
+            if (A.NL) cp_async_elem<ESZ>(&stage[(iN * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.NL) + gi, valid);
         }
         cp_async_wait_all();  // each thread reads back only its own elements
         // ---- residual q_n for n = G j + g, times Gamma_alpha ----
@@ -416,21 +412,11 @@ __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
             for (int d = NWIN - 1; d >= 1; --d) xw[d] = xw[d - 1];
             xw[0] = c2((ST)0, (ST)0);
             if (A.X) xw[0] = ldcol<ST, REAL>(stage, (ix * R + j) * REG_THREADS + tid);
-            if constexpr (STAGE_ALL) {
-                if (A.F) q = ldcol<ST, REAL>(stage, (iF * R + j) * REG_THREADS + tid);
-                if (A.NL) {
-                    const ST2 v = ldcol<ST, REAL>(stage, (iN * R + j) * REG_THREADS + tid);
-                    q.x = fma(bdt, v.x, q.x);
-                    q.y = fma(bdt, v.y, q.y);
-                }
-            } else if (valid) {
-                const long long gi = (long long)n * Mcol + mm;
-                if (A.F) q = ldcol<ST, REAL>(A.F, gi);
-                if (A.NL) {
-                    const ST2 v = ldcol<ST, REAL>(A.NL, gi);
-                    q.x = fma(bdt, v.x, q.x);
-                    q.y = fma(bdt, v.y, q.y);
-                }
+            if (A.F) q = ldcol<ST, REAL>(stage, (iF * R + j) * REG_THREADS + tid);
+            if (A.NL) {
+                const ST2 v = ldcol<ST, REAL>(stage, (iN * R + j) * REG_THREADS + tid);
+                q.x = fma(bdt, v.x, q.x);
+                q.y = fma(bdt, v.y, q.y);
             }
             if (A.X) {
                 ST2 rx = xw[0];
@@ -587,10 +573,9 @@ expd_status launch_reg(expd_plan p, TimeArgs& a, cudaStream_t s) {
     const double fl_col = 2.0 * 5.0 * NS * ilog2(NS) + 8.0 * p->order * NS + 4.0 * p->order * NS;
     const int cls = sizeof(ST) == 4 ? EXPD_K_TIME32 : std::is_same<ST, dd>::value ? EXPD_K_TIMEDD : EXPD_K_TIME;
     KProf kp(p, s, cls, per * NS * (double)p->Mcol, fl_col * (double)p->Mcol);
-    constexpr bool all = !std::is_same<ST, dd>::value;  // double-float (16-byte) elements stage only X
-    const int narr = (a.X ? 1 : 0) + (all ? (a.F ? 1 : 0) + (a.NL ? 1 : 0) : 0);
+    const int narr = (a.X ? 1 : 0) + (a.F ? 1 : 0) + (a.NL ? 1 : 0);
     const size_t smem = (size_t)std::max(narr, 1) * NS * REG_THREADS / G * (size_t)esz;  // R slots per thread
-    auto kern = time_reg_kernel<NS, G, ST, REAL, all, ADV>;
+    auto kern = time_reg_kernel<NS, G, ST, REAL, ADV>;
     EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
     kern<<<(int)grid, REG_THREADS, smem, s>>>(a);
     EXPD_CUDA_TRY(cudaGetLastError());
@@ -823,8 +808,8 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s) {
     a.dshift = op.dshift;
     // power-of-two windows up to 64 with the float32 preconditioner: register kernel
     const bool reg = op.precond && op.f32 && (p->Ns == 16 || p->Ns == 32 || p->Ns == 64) && !p->no_reg_time;
-    // (double-float storage stays on the shared-memory kernel: with 16-byte
-    // elements the register kernel's staging or its direct loads measured slower)
+    // (double-float storage stays on the shared-memory kernel: staging its
+    // 16-byte elements, or loading them without staging, measured slower)
     if (reg && !op.stdd) {
         if (op.st32) {
             if (op.NL && !op.nl_f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 storage needs float32 N");
