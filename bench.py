@@ -283,7 +283,9 @@ def main():
     u0_d = torch.from_numpy(u0).to(dev)
     U_d = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
+    # a stream of its own (the legacy default stream cannot hold CUDA graphs)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
 
     plan = expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, max_iter=100), stream)
     plan64 = expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_FP64, max_iter=100), stream)

@@ -102,6 +102,17 @@ struct expd_plan_s {
     int partial_cap = 0;          // CTAs the partial-norm buffer has room for
     int time_grid_used = 0;       // CTAs of the last time-kernel launch (for the reduction)
     int jacobian = 0;             // EXPD_JAC_*
+    // One sweep of the fixed point (N evaluation, time kernel, per-slice
+    // reduction) per phase, captured as a CUDA graph on first use and relaunched
+    // every iteration; keyed by the per-call values the launches bake in.
+    struct SweepGraph {
+        cudaGraphExec_t exec = nullptr;
+        const void* key_ptr = nullptr;
+        double key_shift = 0;
+        long long launches = 0;
+        int eager = 0;  // sweeps launched directly (the first one sets kernel attributes)
+    } sweep_graph[3];
+    int no_graphs = 0;            // 1: launch kernel by kernel (EXPD_GRAPHS=0)
     int no_reg_time = 0;          // 1 forces the shared-memory time kernel (tests)
     int no_fft4 = 0;              // 1 forces the radix-4 shared-memory row / column FFTs (tests)
     // host-pointer staging (lazy)
