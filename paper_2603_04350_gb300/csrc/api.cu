@@ -1181,25 +1181,32 @@ expd_status expd_solve_sequential(expd_plan p, const double* u0, const double* f
     void* tmp = p->Fh;                             // eigen scratch (the right-hand side is not used here)
     double* phys = static_cast<double*>(p->NL64);  // physical scratch of M values (nonlinear plans)
     const double bdt = p->beta[so] * p->dt;
-    for (int n = so; n <= p->Nt && st == EXPD_OK; ++n) {
-        // IF-BDF-s step: w = sum_j a_j A^j u_{n-j} + beta_s dt f(t_n), then
-        // u_n = w (linear) or u_n - beta_s dt N(u_n) = w pointwise (Eq. (7.3))
-        const void* in[6];
-        double coef[6];
-        for (int j = 1; j <= so; ++j) {
-            in[j - 1] = slice(n - j);
-            coef[j - 1] = p->acoef[so][j];
+    auto steps = [&]() -> expd_status {
+        expd_status r = EXPD_OK;
+        for (int n = so; n <= p->Nt && r == EXPD_OK; ++n) {
+            // IF-BDF-s step: w = sum_j a_j A^j u_{n-j} + beta_s dt f(t_n), then
+            // u_n = w (linear) or u_n - beta_s dt N(u_n) = w pointwise (Eq. (7.3))
+            const void* in[6];
+            double coef[6];
+            for (int j = 1; j <= so; ++j) {
+                in[j - 1] = slice(n - j);
+                coef[j - 1] = p->acoef[so][j];
+            }
+            const void* src = f ? eig_slice(p, p->fh, n - 1) : nullptr;
+            if (!nl) {
+                r = eigen_combine(p, slice(n), in, coef, so, src, bdt, s);
+            } else {
+                r = eigen_combine(p, tmp, in, coef, so, src, bdt, s);
+                if (r == EXPD_OK) r = spatial_inverse64(p, tmp, phys, 1, s);
+                if (r == EXPD_OK) r = pointwise_solve(p, phys, phys, M, bdt, s);
+                if (r == EXPD_OK) r = spatial_forward64(p, phys, slice(n), 1, s);
+            }
         }
-        const void* src = f ? eig_slice(p, p->fh, n - 1) : nullptr;
-        if (!nl) {
-            st = eigen_combine(p, slice(n), in, coef, so, src, bdt, s);
-        } else {
-            st = eigen_combine(p, tmp, in, coef, so, src, bdt, s);
-            if (st == EXPD_OK) st = spatial_inverse64(p, tmp, phys, 1, s);
-            if (st == EXPD_OK) st = pointwise_solve(p, phys, phys, M, bdt, s);
-            if (st == EXPD_OK) st = spatial_forward64(p, phys, slice(n), 1, s);
-        }
-    }
+        return r;
+    };
+    // the Nt - s + 1 steps are launch-bound on small grids: one CUDA graph
+    // (keyed by whether a source is present), like the fixed point's sweeps
+    st = run_sweep(p, 3, f ? p->fh : nullptr, 0.0, s, steps);
     if (st != EXPD_OK) return st;
     st = write_solution(p, sg.U, s);
     if (st != EXPD_OK) return st;

@@ -111,7 +111,7 @@ struct expd_plan_s {
         double key_shift = 0;
         long long launches = 0;
         int eager = 0;  // sweeps launched directly (the first one sets kernel attributes)
-    } sweep_graph[3];
+    } sweep_graph[4];             // [0..2] fixed-point phases, [3] sequential stepping
     int no_graphs = 0;            // 1: launch kernel by kernel (EXPD_GRAPHS=0)
     int no_reg_time = 0;          // 1 forces the shared-memory time kernel (tests)
     int no_fft4 = 0;              // 1 forces the radix-4 shared-memory row / column FFTs (tests)

@@ -624,3 +624,22 @@ def test_graph_sweeps_match_direct_launches(expd, p):
                 plan.solve_fp(dev(u0), fd, U, stream=side)
                 side.synchronize()
                 assert np.array_equal(U.cpu().numpy(), ref), (jac, k)
+
+
+@pytest.mark.parametrize("p", [CASES[8], CASES[6], CASES[0]], ids=[IDS[8], IDS[6], IDS[0]])
+def test_graph_sequential_stepping_matches_direct(expd, p):
+    u0 = np.random.default_rng(26).uniform(-0.8, 0.8, p.n)
+    f = np.random.default_rng(27).standard_normal((p.Nt,) + p.n) if p.nonlin == "none" else None
+    fd = None if f is None else dev(f)
+    spec = expd.spec_from_problem(p)
+    ref = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(spec) as plan:
+        plan.solve_sequential(dev(u0), fd, ref)
+    ref = host(ref)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side), expd.plan_create(spec, side) as plan:
+        for k in range(3):
+            U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+            plan.solve_sequential(dev(u0), fd, U, stream=side)
+            side.synchronize()
+            assert np.array_equal(U.cpu().numpy(), ref), k
