@@ -244,7 +244,7 @@ def served_mix(count: int, workers: int, local: int) -> dict:
     base = serve.summary(serve.run_one_at_a_time(timed, device=local, precision=expd.PREC_FP64))
     return {"requests": count, "seed": 5, "workers": workers, "capacity_req_per_s": capacity,
             "rate_per_s": rate, "mixed_concurrent": mixed, "fp64_one_at_a_time": base,
-            "errors": eng.errors[:5],
+            "errors": eng.errors[:5], "oom_retries": eng.retries,
             "note": "grids {64..1024}^2 (Dirichlet: g-1 interior points), Nt {16..256}, s {1,2,6}, "
                     "kind {Allen-Cahn periodic, heat Dirichlet}; inputs generated on the device"}
 

@@ -120,7 +120,7 @@ class Engine:
         self.dev = torch.device("cuda", device)
         torch.cuda.set_device(self.dev)
         free, _ = torch.cuda.mem_get_info(self.dev)
-        self.budget = int(budget_bytes if budget_bytes is not None else 0.8 * free)
+        self.budget = int(budget_bytes if budget_bytes is not None else 0.7 * free)
         self.workers = workers
         self.precision = precision
         self.max_iter = max_iter
@@ -132,6 +132,7 @@ class Engine:
         self.errors: List[str] = []
         self.results: dict = {}
         self.keep_results = False
+        self.retries = 0
 
     def _worker(self, wid: int, t0: float, caches: dict):
         torch.cuda.set_device(self.dev)
@@ -159,40 +160,56 @@ class Engine:
             status, iters = expd.OK, 0
             spec = _spec(p, self.precision, self.max_iter)
             key = _key(spec)
-            plan = None
-            try:
-                with torch.cuda.stream(stream):
-                    entry = cache.pop(key, None)
-                    if entry is None:
-                        plan = expd.plan_create(spec, stream)
-                        pbytes = plan.workspace_bytes()
-                    else:
-                        plan, pbytes = entry
-                        with self._cv:
-                            self._adm.cached -= pbytes
-                    u0, f = device_inputs(p, self.dev, stream)
-                    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=self.dev)
-                    if p.solver == "gmres":
-                        info = plan.solve_gmres(u0, f, U, stream=stream)
-                    else:
-                        info = plan.solve_fp(u0, f, U, stream=stream)
-                    iters = info["iterations"]
-                    stream.synchronize()
-                    if self.keep_results:
-                        self.results[rid] = U.cpu().numpy()
-                    del u0, f, U
-                    if self.cache_plans:
-                        cache[key] = (plan, pbytes)
-                        with self._cv:
-                            self._adm.cached += pbytes
-                    else:
+            for attempt in range(3):
+                plan = None
+                status = expd.OK
+                try:
+                    with torch.cuda.stream(stream):
+                        entry = cache.pop(key, None)
+                        if entry is None:
+                            plan = expd.plan_create(spec, stream)
+                            pbytes = plan.workspace_bytes()
+                        else:
+                            plan, pbytes = entry
+                            with self._cv:
+                                self._adm.cached -= pbytes
+                        u0, f = device_inputs(p, self.dev, stream)
+                        U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=self.dev)
+                        if p.solver == "gmres":
+                            info = plan.solve_gmres(u0, f, U, stream=stream)
+                        else:
+                            info = plan.solve_fp(u0, f, U, stream=stream)
+                        iters = info["iterations"]
+                        stream.synchronize()
+                        if self.keep_results:
+                            self.results[rid] = U.cpu().numpy()
+                        del u0, f, U
+                        if self.cache_plans:
+                            cache[key] = (plan, pbytes)
+                            with self._cv:
+                                self._adm.cached += pbytes
+                        else:
+                            plan.destroy()
+                        plan = None
+                    break
+                except (expd.ExpdError, torch.cuda.OutOfMemoryError) as e:
+                    status = e.status if isinstance(e, expd.ExpdError) else expd.ERR_OOM
+                    if plan is not None:
                         plan.destroy()
-                    plan = None
-            except expd.ExpdError as e:
-                status = e.status
-                self.errors.append(f"{p.name}: {e}")
-                if plan is not None:
-                    plan.destroy()
+                    u0 = f = U = None
+                    if status != expd.ERR_OOM or attempt == 2:
+                        self.errors.append(f"{p.name}: {e}")
+                        break
+                    # device memory held outside the budget (PyTorch's cache of
+                    # earlier inputs, this worker's cached plans): release and retry
+                    with self._cv:
+                        while cache:
+                            _, (pl, b) = cache.popitem(last=False)
+                            pl.destroy()
+                            self._adm.cached -= b
+                    stream.synchronize()
+                    torch.cuda.empty_cache()
+                    self.retries += 1
             end = time.perf_counter() - t0
             with self._cv:
                 self._adm.done(need)
@@ -203,7 +220,7 @@ class Engine:
     def run(self, requests: List[I.Request], realtime: bool = True, keep_results: bool = False) -> List[Record]:
         """Replays the trace (arrivals at their offsets when realtime) and waits.
         keep_results copies every solution to the host (self.results[rid])."""
-        self.records, self.errors, self.results = [], [], {}
+        self.records, self.errors, self.results, self.retries = [], [], {}, 0
         self.keep_results = keep_results
         needs = [request_bytes(r.problem, self.precision, self.max_iter) for r in requests]
         for r, n in zip(requests, needs):
