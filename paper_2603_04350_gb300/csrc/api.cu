@@ -906,6 +906,7 @@ expd_status expd_residual(expd_plan p, const double* u0, const double* f, const 
     TimeOp op;
     op.X = p->Uh;
     op.F = p->Fh;
+    op.f_slices = p->f_slices;
     op.sigR = -1.0;
     op.precond = 0;
     op.out = p->Fh;  // in-place per tile: each tile is loaded before it is written
@@ -947,7 +948,7 @@ expd_status expd_precond_apply(expd_plan p, const double* R, double* S, void* st
     expd_status st = spatial_forward64(p, Rd, p->Fh, p->Ns, s);
     if (st != EXPD_OK) return st;
     TimeOp op;
-    op.F = p->Fh;
+    op.F = p->Fh;  // the transformed R: every slice
     op.precond = 1;
     op.out = p->Fh;
     op.f32 = p->precision == EXPD_PREC_MIXED;
@@ -1037,6 +1038,7 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
         TimeOp op;
         op.X = phase == PH32 ? p->U32 : p->Uh;
         op.F = phase == PH32 ? p->F32 : p->Fh;
+        op.f_slices = p->f_slices;
         op.sigR = -1.0;
         op.precond = 1;
         op.accum = 1;
@@ -1258,6 +1260,7 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
     {
         TimeOp op;
         op.F = p->Fh;
+        op.f_slices = p->f_slices;
         op.precond = 1;
         op.out = c;
         st = time_apply(p, op, s);
@@ -1422,6 +1425,7 @@ expd_status expd_solve_bicgstab(expd_plan p, const double* u0, const double* f, 
     {
         TimeOp op;
         op.F = p->Fh;
+        op.f_slices = p->f_slices;
         op.precond = 1;
         op.out = c;
         st = time_apply(p, op, s);

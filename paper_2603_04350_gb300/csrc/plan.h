@@ -102,6 +102,7 @@ struct expd_plan_s {
     int partial_cap = 0;          // CTAs the partial-norm buffer has room for
     int time_grid_used = 0;       // CTAs of the last time-kernel launch (for the reduction)
     int jacobian = 0;             // EXPD_JAC_*
+    int f_slices = 0;             // leading slices of the right-hand side Fh / F32 that can be nonzero
     // One sweep of the fixed point (N evaluation, time kernel, per-slice
     // reduction) per phase, captured as a CUDA graph on first use and relaunched
     // every iteration; keyed by the per-call values the launches bake in.
@@ -202,6 +203,7 @@ struct TimeOp {
     const void* NL = nullptr;  // transformed nonlinearity (may be null)
     void* sout = nullptr;      // optional copy of the update s in float32 (accum mode)
     double dshift = 0;         // Step (b) solves with (1 - dshift) I - sum_j a_j (lambda A)^j
+    int f_slices = -1;         // F is zero beyond its first f_slices slices (-1: all may be nonzero)
     int nl_f32 = 0;
     double bdt = 0;            // coefficient of NL
     double sigR = -1;          // coefficient of R_s X

@@ -1150,8 +1150,13 @@ expd_status assemble_rhs(expd_plan p, const void* fh, cudaStream_t s, float* F32
     r.s = p->order;
     r.Ns = p->Ns;
     KProf kp(p, s, EXPD_K_POINTWISE, 8.0 * r.nelem * ((fh ? 2.0 : 1.0) * r.Ns + r.s), 2.0 * r.nelem * r.s * r.s);
-    const long long bx = std::max(1LL, std::min<long long>((r.nelem + 255) / 256, (4LL * p->sm_count * 8) / r.Ns + 1));
-    rhs_kernel<<<dim3((unsigned)bx, (unsigned)r.Ns), 256, 0, s>>>(r);
+    // without a source only the first s slices (the start-up terms) are
+    // nonzero: the time kernels read F as zero beyond them, so only those are
+    // written
+    const int ny = fh ? r.Ns : std::min(r.s, r.Ns);
+    p->f_slices = ny;
+    const long long bx = std::max(1LL, std::min<long long>((r.nelem + 255) / 256, (4LL * p->sm_count * 8) / ny + 1));
+    rhs_kernel<<<dim3((unsigned)bx, (unsigned)ny), 256, 0, s>>>(r);
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }

@@ -43,6 +43,7 @@ struct TimeArgs {
     void* out;
     void* sout;  // optional float32 copy of the update (accum mode)
     double dshift;  // Step (b) divisor (1 - dshift) - sum_j c_j lambda^j
+    int f_slices;   // F is zero from this slice on
     int nl_f32;
     double bdt, sigR;
     int precond, accum;
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
             if (m < Mcol) {
                 const long long g = (long long)n * Mcol + m;
                 if (A.X) x = ldcol<ST, REAL>(A.X, g);
-                if (A.F) r = ldcol<ST, REAL>(A.F, g);
+                if (A.F && n < A.f_slices) r = ldcol<ST, REAL>(A.F, g);
                 if (A.NL) {
                     const ST2 v = ldnl<ST, REAL>(A.NL, g, A.nl_f32);
                     r.x = fma(bdt, v.x, r.x);
@@ -395,7 +396,9 @@ __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
         for (int j = 0; j < R; ++j) {
             const long long gi = (long long)(G * j + g) * Mcol + mm;
             if (A.X) cp_async_elem<ESZ>(&stage[(ix * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.X) + gi, valid);
-            if (A.F) cp_async_elem<ESZ>(&stage[(iF * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.F) + gi, valid);
+            if (A.F)  // zero-filled beyond the right-hand side's nonzero slices
+                cp_async_elem<ESZ>(&stage[(iF * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.F) + gi,
+                                   valid && G * j + g < A.f_slices);
             if (A.NL) cp_async_elem<ESZ>(&stage[(iN * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.NL) + gi, valid);
         }
         cp_async_wait_all();  // each thread reads back only its own elements
@@ -569,7 +572,8 @@ expd_status launch_reg(expd_plan p, TimeArgs& a, cudaStream_t s) {
     long long grid = (p->Mcol + cols - 1) / cols;
     if (grid > p->partial_cap) grid = p->partial_cap;
     const double esz = (REAL ? 1.0 : 2.0) * sizeof(ST);
-    const double per = (a.X ? esz : 0.0) + (a.F ? esz : 0.0) + (a.NL ? esz : 0.0) + esz;  // N stored like X
+    const double ffrac = (double)a.f_slices / p->Ns;  // F is read only where it can be nonzero
+    const double per = (a.X ? esz : 0.0) + (a.F ? esz * ffrac : 0.0) + (a.NL ? esz : 0.0) + esz;  // N stored like X
     const double fl_col = 2.0 * 5.0 * NS * ilog2(NS) + 8.0 * p->order * NS + 4.0 * p->order * NS;
     const int cls = sizeof(ST) == 4 ? EXPD_K_TIME32 : std::is_same<ST, dd>::value ? EXPD_K_TIMEDD : EXPD_K_TIME;
     KProf kp(p, s, cls, per * NS * (double)p->Mcol, fl_col * (double)p->Mcol);
@@ -666,7 +670,8 @@ expd_status launch_time(expd_plan p, TimeArgs& a, cudaStream_t s) {
     EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
     const double esz = (REAL ? 1.0 : 2.0) * sizeof(ST);
     const double nlsz = (REAL ? 1.0 : 2.0) * (a.nl_f32 ? 4.0 : 8.0);
-    const double per = (a.X ? esz : 0.0) + (a.F ? esz : 0.0) + (a.NL ? nlsz : 0.0) + esz;
+    const double ffrac = (double)a.f_slices / p->Ns;
+    const double per = (a.X ? esz : 0.0) + (a.F ? esz * ffrac : 0.0) + (a.NL ? nlsz : 0.0) + esz;
     const double lg = (double)t.log2L;
     const double fl_col = (a.precond ? (t.bluestein ? 4.0 : 2.0) * 5.0 * t.L * lg + 8.0 * p->order * p->Ns : 0.0) +
                           4.0 * p->order * p->Ns;
@@ -806,6 +811,7 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s) {
     a.partial = p->partial;
     a.sout = op.accum ? op.sout : nullptr;
     a.dshift = op.dshift;
+    a.f_slices = op.f_slices < 0 ? p->Ns : op.f_slices;
     // power-of-two windows up to 64 with the float32 preconditioner: register kernel
     const bool reg = op.precond && op.f32 && (p->Ns == 16 || p->Ns == 32 || p->Ns == 64) && !p->no_reg_time;
     // (double-float storage stays on the shared-memory kernel: staging its
