@@ -386,7 +386,7 @@ constexpr int col4_columns(int N1, int N2, int esz) {
 }
 
 template <typename PT, typename TIN, typename TOUT, int N1, int N2>
-__global__ void __launch_bounds__(COL4_THREADS, N1 >= 32 ? 2 : 3) col4_kernel(const TIN* __restrict__ in, TOUT* __restrict__ out,
+__global__ void __launch_bounds__(COL4_THREADS, N1 >= 32 ? 2 : 4) col4_kernel(const TIN* __restrict__ in, TOUT* __restrict__ out,
                                                                 long long ncols, int KX,
                                                                 const typename cplx<PT>::t* __restrict__ Wg,
                                                                 int sign, PT scale) {
@@ -521,7 +521,7 @@ constexpr int row4_stride(int N1, int N2) {
 constexpr int row4_rows(int N1, int N2, int esz) { return (void)N2, (void)esz, ROW4_THREADS / N1; }
 
 template <typename PT, typename TIN, typename TOUT, int KIND, int N1, int N2>
-__global__ void __launch_bounds__(ROW4_THREADS, 3) row4_kernel(const TIN* in, TOUT* out, long long rows,
+__global__ void __launch_bounds__(ROW4_THREADS, N1 >= 32 ? 2 : 4) row4_kernel(const TIN* in, TOUT* out, long long rows,
                                                                 const typename cplx<PT>::t* __restrict__ Wg,
                                                                 PT scale, int nonlin) {
     typedef typename cplx<PT>::t PT2;
