@@ -515,18 +515,18 @@ bool expd_is_device_ptr(const void* ptr) { return is_device_ptr(ptr); }
 // Runs one fixed-point sweep: launched kernel by kernel when per-kernel timing
 // is on (its events cannot sit in a graph), on the legacy default stream
 // (which cannot be captured) or with EXPD_GRAPHS=0; otherwise captured once per
-// phase (and per value of the pointers and shift baked into its launches) and
-// relaunched as one CUDA graph.
+// phase (and per value of the pointer, shift and right-hand side slice count
+// baked into its launches) and relaunched as one CUDA graph.
 template <typename Issue>
-static expd_status run_sweep(expd_plan p, int phase, const void* key_ptr, double key_shift, cudaStream_t s,
-                             Issue&& issue) {
+static expd_status run_sweep(expd_plan p, int phase, const void* key_ptr, double key_shift, int key_fs,
+                             cudaStream_t s, Issue&& issue) {
     if (p->timing || p->no_graphs || s == nullptr) return issue();
     auto& G = p->sweep_graph[phase];
     if (!G.eager) {  // the first sweep of a phase runs directly (one-time kernel set-up outside capture)
         G.eager = 1;
         return issue();
     }
-    if (!G.exec || G.key_ptr != key_ptr || G.key_shift != key_shift) {
+    if (!G.exec || G.key_ptr != key_ptr || G.key_shift != key_shift || G.key_fs != key_fs) {
         if (G.exec) {
             cudaGraphExecDestroy(G.exec);
             G.exec = nullptr;
@@ -549,6 +549,7 @@ static expd_status run_sweep(expd_plan p, int phase, const void* key_ptr, double
         }
         G.key_ptr = key_ptr;
         G.key_shift = key_shift;
+        G.key_fs = key_fs;
         G.launches = p->launches - before;
         p->launches = before;
     }
@@ -1074,7 +1075,7 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
             if (r == EXPD_OK) r = time_reduce(p, s);
             return r;
         };
-        st = run_sweep(p, phase, fast_out && phase == PHDD ? phys_out : nullptr, dshift, s, issue);
+        st = run_sweep(p, phase, fast_out && phase == PHDD ? phys_out : nullptr, dshift, op.f_slices, s, issue);
         if (st != EXPD_OK) return st;
         phys_valid = op.sout != nullptr;
         double nr[4];
@@ -1208,7 +1209,7 @@ expd_status expd_solve_sequential(expd_plan p, const double* u0, const double* f
     };
     // the Nt - s + 1 steps are launch-bound on small grids: one CUDA graph
     // (keyed by whether a source is present), like the fixed point's sweeps
-    st = run_sweep(p, 3, f ? p->fh : nullptr, 0.0, s, steps);
+    st = run_sweep(p, 3, f ? p->fh : nullptr, 0.0, 0, s, steps);
     if (st != EXPD_OK) return st;
     st = write_solution(p, sg.U, s);
     if (st != EXPD_OK) return st;

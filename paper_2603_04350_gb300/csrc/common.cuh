@@ -222,7 +222,8 @@ EXPD_HD double2 coef_zero<double2>() { return make_double2(0.0, 0.0); }
 // ------------------------------------------------------- register FFTs ---
 // Length-R FFTs on a register array (compile-time indices, fully unrolled).
 // tw[k * TS] = exp(-2 pi i k / R) for k < R/2 (a table of a longer length,
-// read at stride TS).  SIGN < 0: exp(-2 pi i jk/R); SIGN > 0: exp(+2 pi i jk/R).
+// read at stride TS); the quarter-turn twiddle is applied as a swap.
+// SIGN < 0: exp(-2 pi i jk/R); SIGN > 0: exp(+2 pi i jk/R).
 constexpr int ilog2_ct(int n) { return n <= 1 ? 0 : 1 + ilog2_ct(n >> 1); }
 
 // DIT: bit-reversed in -> natural out
@@ -236,7 +237,9 @@ EXPD_HD void reg_fft_dit(T2 (&v)[R], const T2* tw) {
             const int k = b & (h - 1);
             const int i = ((b >> st) << (st + 1)) + k;
             T2 t = v[i + h];
-            if (k != 0) {
+            if (2 * k == h) {
+                t = cmul_quarter(t, SIGN);  // exp(-+ i pi/2) = -+i, no table read
+            } else if (k != 0) {
                 T2 w = tw[k * (R / (2 * h)) * TS];
                 if (SIGN > 0) w.y = -w.y;
                 t = cmul(t, w);
@@ -260,7 +263,9 @@ EXPD_HD void reg_fft_dif(T2 (&v)[R], const T2* tw) {
             const T2 u = v[i], t = v[i + h];
             v[i] = cadd(u, t);
             T2 d = csub(u, t);
-            if (k != 0) {
+            if (2 * k == h) {
+                d = cmul_quarter(d, SIGN);
+            } else if (k != 0) {
                 T2 w = tw[k * (R / (2 * h)) * TS];
                 if (SIGN > 0) w.y = -w.y;
                 d = cmul(d, w);

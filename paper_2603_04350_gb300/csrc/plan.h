@@ -110,6 +110,7 @@ struct expd_plan_s {
         cudaGraphExec_t exec = nullptr;
         const void* key_ptr = nullptr;
         double key_shift = 0;
+        int key_fs = 0;  // right-hand side slices baked into the time kernel's launch
         long long launches = 0;
         int eager = 0;  // sweeps launched directly (the first one sets kernel attributes)
     } sweep_graph[4];             // [0..2] fixed-point phases, [3] sequential stepping

@@ -88,6 +88,43 @@ static void test_fft(int log2n, int sign, double tol, std::mt19937_64& rng) {
     check("fft_dit strided table", err / scale, tol, n, sign);
 }
 
+// Register FFTs (compile-time length R, twiddles from a table of length R*TS
+// read at stride TS), both directions, against the naive DFT.
+template <typename T, typename T2, int R, int TS, int SIGN>
+static void test_reg_fft(double tol, std::mt19937_64& rng) {
+    std::normal_distribution<double> N01;
+    std::vector<cd> x(R), tw(R * TS / 2);
+    for (auto& v : x) v = cd(N01(rng), N01(rng));
+    for (int k = 0; k < R * TS / 2; ++k) tw[k] = std::polar(1.0, -2.0 * M_PI * k / (R * TS));
+    const std::vector<cd> ref = naive_dft(x, SIGN);
+    double scale = 0;
+    for (auto& v : ref) scale = std::max(scale, std::abs(v));
+    const std::vector<T2> twd = to_dev<T2, T>(tw);
+    const int lg = ilog2_ct(R);
+    T2 v[R];
+    for (int j = 0; j < R; ++j) v[bitrev(j, lg)] = to_dev<T2, T>({x[j]})[0];
+    reg_fft_dit<R, TS, SIGN>(v, twd.data());
+    double err = 0;
+    for (int k = 0; k < R; ++k) err = std::max(err, std::abs(cd(v[k].x, v[k].y) - ref[k]));
+    check(sizeof(T) == 8 ? "reg_fft_dit double" : "reg_fft_dit float", err / scale, tol, R, SIGN * TS);
+    for (int j = 0; j < R; ++j) v[j] = to_dev<T2, T>({x[j]})[0];
+    reg_fft_dif<R, TS, SIGN>(v, twd.data());
+    err = 0;
+    for (int k = 0; k < R; ++k) {
+        const T2 w = v[bitrev(k, lg)];
+        err = std::max(err, std::abs(cd(w.x, w.y) - ref[k]));
+    }
+    check(sizeof(T) == 8 ? "reg_fft_dif double" : "reg_fft_dif float", err / scale, tol, R, SIGN * TS);
+}
+
+template <typename T, typename T2, int R>
+static void test_reg_fft_all(double tol, std::mt19937_64& rng) {
+    test_reg_fft<T, T2, R, 1, -1>(tol, rng);
+    test_reg_fft<T, T2, R, 1, +1>(tol, rng);
+    test_reg_fft<T, T2, R, 4, -1>(tol, rng);
+    test_reg_fft<T, T2, R, 4, +1>(tol, rng);
+}
+
 template <typename T, typename T2>
 static void test_column(int Ns, int order, double E, double alpha, double tol, std::mt19937_64& rng) {
     static const double bdf[7][7] = {{0},
@@ -185,6 +222,14 @@ int main() {
             test_fft<double, double2>(l, sign, 1e-13, rng);
             test_fft<float, float2>(l, sign, 2e-5, rng);
         }
+    test_reg_fft_all<double, double2, 2>(1e-14, rng);
+    test_reg_fft_all<double, double2, 4>(1e-14, rng);
+    test_reg_fft_all<double, double2, 8>(1e-14, rng);
+    test_reg_fft_all<double, double2, 16>(1e-14, rng);
+    test_reg_fft_all<double, double2, 32>(1e-14, rng);
+    test_reg_fft_all<float, float2, 4>(1e-6, rng);
+    test_reg_fft_all<float, float2, 16>(2e-6, rng);
+    test_reg_fft_all<float, float2, 32>(2e-6, rng);
     const int sizes[] = {2, 3, 4, 5, 7, 8, 11, 15, 16, 27, 31, 32, 59, 63, 64, 123, 127, 128, 251, 255, 256, 1000};
     const int orders[] = {1, 2, 3, 6};
     const double Es[] = {1.0, 0.7, 0.0};

@@ -1,0 +1,111 @@
+// Argument block and element helpers shared by the time-direction kernels
+// (the shared-memory kernel and the register-resident one live in separate
+// translation units so that they compile in parallel).
+#pragma once
+
+#include <type_traits>
+
+#include "common.cuh"
+#include "dd.cuh"
+#include "plan.h"
+
+namespace expd_time {
+
+struct TimeArgs {
+    const void* X;
+    const void* F;
+    const void* NL;
+    void* out;
+    void* sout;  // optional float32 copy of the update (accum mode)
+    double dshift;  // Step (b) divisor (1 - dshift) - sum_j c_j lambda^j
+    int f_slices;   // F is zero from this slice on
+    int nl_f32;
+    double bdt, sigR;
+    int precond, accum;
+    long long Mcol;
+    int Ns, order;
+    const double* C64;  // [order][Mcol] a_j E_m^j
+    const float* C32;
+    const dd* Cdd;
+    int KX, NX, realcol;
+    const void* gam;  // [Ns] in the storage precision ST
+    const void* osc;  // [Ns] in the storage precision ST
+    const void* lam;  // PT2 tables
+    const void* tw;
+    const void* chirp;
+    const void* bplus;
+    const void* bminus;
+    int L, log2L, bluestein;
+    long long ntiles;
+    double2* partial;  // [Ns][gridDim.x]
+};
+
+// Loads and stores of one time-column element in the storage precision ST.
+template <typename ST, bool REAL>
+__device__ __forceinline__ typename cplx<ST>::t ldcol(const void* p, long long i) {
+    typedef typename cplx<ST>::t ST2;
+    if (REAL) return c2(static_cast<const ST*>(p)[i], (ST)0);
+    return static_cast<const ST2*>(p)[i];
+}
+template <typename ST, bool REAL>
+__device__ __forceinline__ void stcol(void* p, long long i, typename cplx<ST>::t v) {
+    typedef typename cplx<ST>::t ST2;
+    if (REAL) static_cast<ST*>(p)[i] = v.x;
+    else static_cast<ST2*>(p)[i] = v;
+}
+template <typename ST, bool REAL>
+__device__ __forceinline__ typename cplx<ST>::t ldnl(const void* p, long long i, int f32) {
+    typedef typename cplx<ST>::t ST2;
+    if (std::is_same<ST, dd>::value) return ldcol<ST, REAL>(p, i);  // double-float N
+    if (REAL) return c2(f32 ? (ST) static_cast<const float*>(p)[i] : (ST) static_cast<const double*>(p)[i], (ST)0);
+    if (f32) {
+        const float2 v = static_cast<const float2*>(p)[i];
+        return c2((ST)v.x, (ST)v.y);
+    }
+    const double2 v = static_cast<const double2*>(p)[i];
+    return c2((ST)v.x, (ST)v.y);
+}
+
+
+// a_j E_m^j: real tables, or (with advection) complex tables of the same
+// layout with (Re, Im) pairs
+template <typename T>
+__device__ __forceinline__ T coef(const TimeArgs& A, int j, long long m);
+template <>
+__device__ __forceinline__ double2 coef<double2>(const TimeArgs& A, int j, long long m) {
+    return reinterpret_cast<const double2*>(A.C64)[(long long)(j - 1) * A.Mcol + m];
+}
+template <>
+__device__ __forceinline__ float2 coef<float2>(const TimeArgs& A, int j, long long m) {
+    return reinterpret_cast<const float2*>(A.C32)[(long long)(j - 1) * A.Mcol + m];
+}
+template <>
+__device__ __forceinline__ dd2 coef<dd2>(const TimeArgs& A, int j, long long m) {
+    return reinterpret_cast<const dd2*>(A.Cdd)[(long long)(j - 1) * A.Mcol + m];
+}
+template <>
+__device__ __forceinline__ double coef<double>(const TimeArgs& A, int j, long long m) {
+    return A.C64[(long long)(j - 1) * A.Mcol + m];
+}
+template <>
+__device__ __forceinline__ float coef<float>(const TimeArgs& A, int j, long long m) {
+    return A.C32[(long long)(j - 1) * A.Mcol + m];
+}
+template <>
+__device__ __forceinline__ dd coef<dd>(const TimeArgs& A, int j, long long m) {
+    return A.Cdd[(long long)(j - 1) * A.Mcol + m];
+}
+
+template <typename ST>
+__device__ __forceinline__ ST mode_weight(long long m, int KX, int NX, int realcol) {
+    if (realcol) return (ST)1;
+    const int kx = (int)(m % KX);
+    return (kx == 0 || 2 * kx == NX) ? (ST)1 : (ST)2;
+}
+
+}  // namespace expd_time
+
+// Register-resident time kernel for power-of-two windows Ns in {16, 32, 64}
+// with the float32 preconditioner; st = 1 for float32 storage, 2 for
+// double-float, 0 for float64.
+expd_status time_reg_launch(expd_plan p, expd_time::TimeArgs& a, int st, cudaStream_t s);

@@ -32,101 +32,12 @@
 #include "common.cuh"
 #include "dd.cuh"
 #include "plan.h"
+#include "time_args.cuh"
 #include "time_column.cuh"
 
 namespace {
 
-struct TimeArgs {
-    const void* X;
-    const void* F;
-    const void* NL;
-    void* out;
-    void* sout;  // optional float32 copy of the update (accum mode)
-    double dshift;  // Step (b) divisor (1 - dshift) - sum_j c_j lambda^j
-    int f_slices;   // F is zero from this slice on
-    int nl_f32;
-    double bdt, sigR;
-    int precond, accum;
-    long long Mcol;
-    int Ns, order;
-    const double* C64;  // [order][Mcol] a_j E_m^j
-    const float* C32;
-    const dd* Cdd;
-    int KX, NX, realcol;
-    const void* gam;  // [Ns] in the storage precision ST
-    const void* osc;  // [Ns] in the storage precision ST
-    const void* lam;  // PT2 tables
-    const void* tw;
-    const void* chirp;
-    const void* bplus;
-    const void* bminus;
-    int L, log2L, bluestein;
-    long long ntiles;
-    double2* partial;  // [Ns][gridDim.x]
-};
-
-// Loads and stores of one time-column element in the storage precision ST.
-template <typename ST, bool REAL>
-__device__ __forceinline__ typename cplx<ST>::t ldcol(const void* p, long long i) {
-    typedef typename cplx<ST>::t ST2;
-    if (REAL) return c2(static_cast<const ST*>(p)[i], (ST)0);
-    return static_cast<const ST2*>(p)[i];
-}
-template <typename ST, bool REAL>
-__device__ __forceinline__ void stcol(void* p, long long i, typename cplx<ST>::t v) {
-    typedef typename cplx<ST>::t ST2;
-    if (REAL) static_cast<ST*>(p)[i] = v.x;
-    else static_cast<ST2*>(p)[i] = v;
-}
-template <typename ST, bool REAL>
-__device__ __forceinline__ typename cplx<ST>::t ldnl(const void* p, long long i, int f32) {
-    typedef typename cplx<ST>::t ST2;
-    if (std::is_same<ST, dd>::value) return ldcol<ST, REAL>(p, i);  // double-float N
-    if (REAL) return c2(f32 ? (ST) static_cast<const float*>(p)[i] : (ST) static_cast<const double*>(p)[i], (ST)0);
-    if (f32) {
-        const float2 v = static_cast<const float2*>(p)[i];
-        return c2((ST)v.x, (ST)v.y);
-    }
-    const double2 v = static_cast<const double2*>(p)[i];
-    return c2((ST)v.x, (ST)v.y);
-}
-
-
-// a_j E_m^j: real tables, or (with advection) complex tables of the same
-// layout with (Re, Im) pairs
-template <typename T>
-__device__ __forceinline__ T coef(const TimeArgs& A, int j, long long m);
-template <>
-__device__ __forceinline__ double2 coef<double2>(const TimeArgs& A, int j, long long m) {
-    return reinterpret_cast<const double2*>(A.C64)[(long long)(j - 1) * A.Mcol + m];
-}
-template <>
-__device__ __forceinline__ float2 coef<float2>(const TimeArgs& A, int j, long long m) {
-    return reinterpret_cast<const float2*>(A.C32)[(long long)(j - 1) * A.Mcol + m];
-}
-template <>
-__device__ __forceinline__ dd2 coef<dd2>(const TimeArgs& A, int j, long long m) {
-    return reinterpret_cast<const dd2*>(A.Cdd)[(long long)(j - 1) * A.Mcol + m];
-}
-template <>
-__device__ __forceinline__ double coef<double>(const TimeArgs& A, int j, long long m) {
-    return A.C64[(long long)(j - 1) * A.Mcol + m];
-}
-template <>
-__device__ __forceinline__ float coef<float>(const TimeArgs& A, int j, long long m) {
-    return A.C32[(long long)(j - 1) * A.Mcol + m];
-}
-template <>
-__device__ __forceinline__ dd coef<dd>(const TimeArgs& A, int j, long long m) {
-    return A.Cdd[(long long)(j - 1) * A.Mcol + m];
-}
-
-template <typename ST>
-__device__ __forceinline__ ST mode_weight(long long m, int KX, int NX, int realcol) {
-    if (realcol) return (ST)1;
-    const int kx = (int)(m % KX);
-    return (kx == 0 || 2 * kx == NX) ? (ST)1 : (ST)2;
-}
+using namespace expd_time;
 
 // PT: precision of steps (a)-(c); ST: precision of the stored state, the
 // right-hand side and the residual arithmetic (float32 sweeps never touch the
@@ -284,319 +195,6 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
     for (int n = tid; n < Ns; n += nth)
         A.partial[(size_t)n * gridDim.x + blockIdx.x] = make_double2((double)sAcc[n].x, (double)sAcc[n].y);
 }
-
-// ---------------------------------------------------------------------------
-// Register-resident variant for power-of-two windows NS in {16, 32, 64} with the
-// float32 preconditioner.  A group of G consecutive lanes owns one spatial
-// mode's time column; lane g of the group holds slices n = G j + g, j < R = NS/G,
-// in registers.  Loads and stores are coalesced across the groups of a warp
-// (consecutive modes), and the length-NS transforms factor as NS = G x R:
-//   forward  Y[k1 + R k2] = sum_g w^(g k2)_G  w^(g k1)_NS  sum_j w^(j k1)_R y[G j + g]
-// (R-point FFT in registers, twiddle, G-point FFT across the lanes by
-// shuffles), and the inverse runs the same factors backwards.  The residual's
-// sliding window of the previous `order` iterates comes from the neighbouring
-// lanes by shuffles.  Per-slice norms are reduced over the warp's groups with a
-// transpose-reduce and over the CTA in shared memory.
-constexpr int REG_THREADS = 128;
-// lanes per column (4: measured faster than 8 lanes with 8 slices each, whose
-// third cross-lane stage costs more than the extra occupancy gains)
-constexpr int reg_lanes(int NS) { return (void)NS, 4; }
-
-__device__ __forceinline__ float2 shfl_c(float2 v, int lane) {
-    return make_float2(__shfl_sync(0xffffffffu, v.x, lane), __shfl_sync(0xffffffffu, v.y, lane));
-}
-__device__ __forceinline__ float2 shfl_xor_c(float2 v, int m) {
-    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
-}
-__device__ __forceinline__ double2 shfl_c(double2 v, int lane) {
-    return make_double2(__shfl_sync(0xffffffffu, v.x, lane), __shfl_sync(0xffffffffu, v.y, lane));
-}
-
-
-// Asynchronous global -> shared copy of one element (4, 8 or 16 bytes); a
-// source size of 0 fills the destination with zeros (columns past the end).
-template <int BYTES>
-__device__ __forceinline__ void cp_async_elem(void* dst, const void* src, bool valid) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    const int n = valid ? BYTES : 0;
-    if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(BYTES), "r"(n)
-                     : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-// ADV: complex a_j E^j (advection); otherwise real.
-template <int NS, int G, typename ST, bool REAL, bool ADV>
-__global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
-    typedef typename cplx<ST>::t ST2;
-    constexpr int R = NS / G;
-    constexpr int LOGR = ilog2_ct(R), LOGG = ilog2_ct(G);
-    constexpr int COLS = REG_THREADS / G;         // columns per CTA
-    constexpr int WG = 32 / G;                    // groups per warp
-    constexpr int V = R < WG ? WG : R;            // transpose-reduce width (padded)
-    constexpr int PER = V / WG;                   // slots each lane ends with
-    constexpr int NWIN = (G - 1 + 6) / G + 1;     // iterate window (slots j, j-1, ..)
-    constexpr int NW = REG_THREADS / 32;
-    // one element of a stored column array: ST (real columns) or its complex pair
-    typedef typename std::conditional<REAL, ST, ST2>::type SE;
-    constexpr int ESZ = (int)sizeof(SE);
-    // staging of this thread's X, F and N(u) elements: [array][j][thread]
-    extern __shared__ __align__(16) unsigned char stage_raw[];
-    SE* stage = reinterpret_cast<SE*>(stage_raw);
-    __shared__ float2 tw[NS / 2];   // exp(-2 pi i k/NS)
-    __shared__ float2 wfull[NS];    // exp(+2 pi i k/NS)
-    __shared__ float2 lam[NS];
-    __shared__ ST gam[NS], osc[NS];
-    __shared__ float red[NW][2][NS];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int g = lane & (G - 1);        // slice residue of this lane
-    const int gl0 = lane & ~(G - 1);     // first lane of the group
-    for (int i = tid; i < NS / 2; i += REG_THREADS) {
-        const float2 t = static_cast<const float2*>(A.tw)[i];
-        tw[i] = t;
-        wfull[i] = make_float2(t.x, -t.y);
-        wfull[i + NS / 2] = make_float2(-t.x, t.y);
-    }
-    for (int i = tid; i < NS; i += REG_THREADS) {
-        lam[i] = static_cast<const float2*>(A.lam)[i];
-        gam[i] = static_cast<const ST*>(A.gam)[i];
-        osc[i] = static_cast<const ST*>(A.osc)[i];
-    }
-    for (int i = tid; i < NW * 2 * NS; i += REG_THREADS) (&red[0][0][0])[i] = 0.0f;
-    __syncthreads();
-    const long long Mcol = A.Mcol;
-    const ST bdt = (ST)A.bdt, sigR = (ST)A.sigR;
-    const int order = A.order;
-    const float one = (float)(1.0 - A.dshift);
-    const int k2R = (int)bitrev((unsigned)g, LOGG) * R;  // spectral block of this lane
-    float accs[PER], accx[PER];
-#pragma unroll
-    for (int i = 0; i < PER; ++i) accs[i] = accx[i] = 0.0f;
-    for (long long base = (long long)blockIdx.x * COLS; base < Mcol; base += (long long)gridDim.x * COLS) {
-        const long long m = base + (tid / G);
-        const bool valid = m < Mcol;
-        const long long mm = valid ? m : 0;
-        typedef typename std::conditional<ADV, ST2, ST>::type CS;
-        typedef typename std::conditional<ADV, float2, float>::type CP;
-        CS cs[7];
-        CP cp[7];
-#pragma unroll
-        for (int j = 1; j <= 6; ++j) {
-            cs[j] = (valid && j <= order) ? coef<CS>(A, j, mm) : coef_zero<CS>();
-            cp[j] = (valid && j <= order) ? coef<CP>(A, j, mm) : coef_zero<CP>();
-        }
-        const float wgt = valid ? (float)mode_weight<float>(mm, A.KX, A.NX, A.realcol) : 0.0f;
-        // ---- stage the column slices: every load of the tile in flight at once ----
-        const int ix = 0, iF = ix + (A.X ? 1 : 0), iN = iF + (A.F ? 1 : 0);
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-            const long long gi = (long long)(G * j + g) * Mcol + mm;
-            if (A.X) cp_async_elem<ESZ>(&stage[(ix * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.X) + gi, valid);
-            if (A.F)  // zero-filled beyond the right-hand side's nonzero slices
-                cp_async_elem<ESZ>(&stage[(iF * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.F) + gi,
-                                   valid && G * j + g < A.f_slices);
-            if (A.NL) cp_async_elem<ESZ>(&stage[(iN * R + j) * REG_THREADS + tid], static_cast<const SE*>(A.NL) + gi, valid);
-        }
-        cp_async_wait_all();  // each thread reads back only its own elements
-        // ---- residual q_n for n = G j + g, times Gamma_alpha ----
-        float2 w[R];
-        ST2 xw[NWIN];  // xw[d] = iterate at slot j - d of this lane
-#pragma unroll
-        for (int d = 0; d < NWIN; ++d) xw[d] = c2((ST)0, (ST)0);
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-            const int n = G * j + g;
-            ST2 q = c2((ST)0, (ST)0);
-#pragma unroll
-            for (int d = NWIN - 1; d >= 1; --d) xw[d] = xw[d - 1];
-            xw[0] = c2((ST)0, (ST)0);
-            if (A.X) xw[0] = ldcol<ST, REAL>(stage, (ix * R + j) * REG_THREADS + tid);
-            if (A.F) q = ldcol<ST, REAL>(stage, (iF * R + j) * REG_THREADS + tid);
-            if (A.NL) {
-                const ST2 v = ldcol<ST, REAL>(stage, (iN * R + j) * REG_THREADS + tid);
-                q.x = fma(bdt, v.x, q.x);
-                q.y = fma(bdt, v.y, q.y);
-            }
-            if (A.X) {
-                ST2 rx = xw[0];
-#pragma unroll
-                for (int i = 1; i <= 6; ++i) {
-                    if (i <= order) {  // warp-uniform
-                        // x at slice n - i lives in lane (g - i) mod G at slot j - (g' + i) / G
-                        const int gs = (g - i) & (G - 1);
-                        const int dsend = (g + i) / G;  // what this lane sends, as a source
-                        ST2 send = xw[0];
-#pragma unroll
-                        for (int d = 1; d < NWIN; ++d)
-                            if (dsend == d) send = xw[d];
-                        ST2 xv = shfl_c(send, gl0 + gs);
-                        if (n - i < 0) xv = c2((ST)0, (ST)0);  // before the window: in F
-                        rx = sub_cx(rx, cs[i], xv);
-                    }
-                }
-                q.x = fma(sigR, rx.x, q.x);
-                q.y = fma(sigR, rx.y, q.y);
-            }
-            w[j] = cvt2<float2>(cscale(q, gam[n]));
-        }
-        // ---- Step (a): Y[k1 + R k2] = sum_n y_n e^{+2 pi i kn/NS} ----
-        reg_fft_dif<R, G, +1>(w, tw);  // slot p: k1 = bitrev_R(p)
-#pragma unroll
-        for (int p = 0; p < R; ++p) {
-            const int k1 = (int)bitrev((unsigned)p, LOGR);
-            if (p != 0) w[p] = cmul(w[p], wfull[g * k1]);
-        }
-#pragma unroll
-        for (int h = G / 2; h >= 1; h >>= 1) {  // DIF across the group's lanes
-            const bool up = (g & h) != 0;
-            const float2 tw2 = wfull[(g & (h - 1)) * (NS / (2 * h))];
-#pragma unroll
-            for (int p = 0; p < R; ++p) {
-                const float2 o = shfl_xor_c(w[p], h);
-                w[p] = up ? cmul(csub(o, w[p]), tw2) : cadd(w[p], o);
-            }
-        }
-        // ---- Step (b): divide by d_k = 1 - sum_j cp_j lambda_k^j ----
-#pragma unroll
-        for (int p = 0; p < R; ++p) {
-            const float2 lk = lam[(int)bitrev((unsigned)p, LOGR) + k2R];
-            float2 acc = acc_add(make_float2(0.0f, 0.0f), cp[6]);
-#pragma unroll
-            for (int j = 5; j >= 1; --j) {
-                acc = cmul(lk, acc);
-                acc = acc_add(acc, cp[j]);
-            }
-            acc = cmul(lk, acc);
-            w[p] = cdiv(w[p], make_float2(one - acc.x, -acc.y));
-        }
-        // ---- Step (c): z_n = sum_k Z_k e^{-2 pi i kn/NS} ----
-#pragma unroll
-        for (int h = 1; h < G; h <<= 1) {  // DIT across the group's lanes
-            const bool up = (g & h) != 0;
-            float2 tw2 = wfull[(g & (h - 1)) * (NS / (2 * h))];
-            tw2.y = -tw2.y;
-#pragma unroll
-            for (int p = 0; p < R; ++p) {
-                const float2 o = shfl_xor_c(w[p], h);
-                w[p] = up ? csub(o, cmul(w[p], tw2)) : cadd(w[p], cmul(o, tw2));
-            }
-        }
-#pragma unroll
-        for (int p = 0; p < R; ++p) {
-            const int k1 = (int)bitrev((unsigned)p, LOGR);
-            if (p != 0) w[p] = cmulc(w[p], wfull[g * k1]);
-        }
-        reg_fft_dit<R, G, -1>(w, tw);  // slot j: z_{G j + g}
-        // ---- update (or output) and per-element norm terms ----
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-            const int n = G * j + g;
-            const ST2 sv = cscale(cvt2<ST2>(w[j]), osc[n]);
-            const long long gi = (long long)n * Mcol + mm;
-            float ns = 0.0f, nx = 0.0f;
-            if (valid) {
-                if (A.accum) {
-                    const ST2 xn = cadd(ldcol<ST, REAL>(stage, (ix * R + j) * REG_THREADS + tid), sv);
-                    stcol<ST, REAL>(const_cast<void*>(A.X), gi, xn);
-                    const float2 xf = cvt2<float2>(xn);
-                    nx = wgt * fmaf(xf.x, xf.x, xf.y * xf.y);
-                } else {
-                    stcol<ST, REAL>(A.out, gi, sv);
-                }
-                const float2 sf = cvt2<float2>(sv);
-                if (A.sout) stcol<float, REAL>(A.sout, gi, sf);
-                ns = wgt * fmaf(sf.x, sf.x, sf.y * sf.y);
-            }
-            w[j] = make_float2(ns, nx);
-        }
-        // ---- transpose-reduce over the warp's groups (lane bits >= LOGG) ----
-        float vs[V], vx[V];
-#pragma unroll
-        for (int i = 0; i < V; ++i) {
-            vs[i] = i < R ? w[i].x : 0.0f;
-            vx[i] = i < R ? w[i].y : 0.0f;
-        }
-#pragma unroll
-        for (int st = 0; st < 5 - LOGG; ++st) {
-            const int off = 16 >> st, len = (V / 2) >> st;
-            const bool upper = (lane & off) != 0;
-#pragma unroll
-            for (int i = 0; i < len; ++i) {
-                // lanes with this bit clear keep slots [0, len), the others [len, 2 len)
-                const float ss = upper ? vs[i] : vs[i + len], sk = upper ? vs[i + len] : vs[i];
-                const float xs = upper ? vx[i] : vx[i + len], xk = upper ? vx[i + len] : vx[i];
-                vs[i] = sk + __shfl_xor_sync(0xffffffffu, ss, off);
-                vx[i] = xk + __shfl_xor_sync(0xffffffffu, xs, off);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            accs[i] += vs[i];
-            accx[i] += vx[i];
-        }
-    }
-    // lane (group c, residue g) holds slots j = c * PER + i of slice G j + g
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int j = (lane / G) * PER + i;
-        if (j < R) {
-            red[warp][0][G * j + g] = accs[i];
-            red[warp][1][G * j + g] = accx[i];
-        }
-    }
-    __syncthreads();
-    for (int n = tid; n < NS; n += REG_THREADS) {
-        float a = 0.0f, b = 0.0f;
-#pragma unroll
-        for (int q = 0; q < NW; ++q) {
-            a += red[q][0][n];
-            b += red[q][1][n];
-        }
-        A.partial[(size_t)n * gridDim.x + blockIdx.x] = make_double2((double)a, (double)b);
-    }
-}
-
-template <int NS, typename ST, bool REAL, bool ADV>
-expd_status launch_reg(expd_plan p, TimeArgs& a, cudaStream_t s) {
-    const TimeTables& ts = std::is_same<ST, float>::value ? p->t32 : p->t64;
-    a.gam = std::is_same<ST, dd>::value ? p->gamdd : ts.gam;
-    a.osc = std::is_same<ST, dd>::value ? p->oscdd : ts.osc;
-    a.lam = p->t32.lam;
-    a.tw = p->t32.tw;
-    constexpr int G = reg_lanes(NS);
-    constexpr int cols = REG_THREADS / G;
-    long long grid = (p->Mcol + cols - 1) / cols;
-    if (grid > p->partial_cap) grid = p->partial_cap;
-    const double esz = (REAL ? 1.0 : 2.0) * sizeof(ST);
-    const double ffrac = (double)a.f_slices / p->Ns;  // F is read only where it can be nonzero
-    const double per = (a.X ? esz : 0.0) + (a.F ? esz * ffrac : 0.0) + (a.NL ? esz : 0.0) + esz;  // N stored like X
-    const double fl_col = 2.0 * 5.0 * NS * ilog2(NS) + 8.0 * p->order * NS + 4.0 * p->order * NS;
-    const int cls = sizeof(ST) == 4 ? EXPD_K_TIME32 : std::is_same<ST, dd>::value ? EXPD_K_TIMEDD : EXPD_K_TIME;
-    KProf kp(p, s, cls, per * NS * (double)p->Mcol, fl_col * (double)p->Mcol);
-    const int narr = (a.X ? 1 : 0) + (a.F ? 1 : 0) + (a.NL ? 1 : 0);
-    const size_t smem = (size_t)std::max(narr, 1) * NS * REG_THREADS / G * (size_t)esz;  // R slots per thread
-    auto kern = time_reg_kernel<NS, G, ST, REAL, ADV>;
-    EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
-    kern<<<(int)grid, REG_THREADS, smem, s>>>(a);
-    EXPD_CUDA_TRY(cudaGetLastError());
-    p->time_grid_used = (int)grid;
-    return EXPD_OK;
-}
-
-template <typename ST, bool REAL, bool ADV>
-expd_status launch_reg_ns(expd_plan p, TimeArgs& a, cudaStream_t s) {
-    switch (p->Ns) {
-        case 16: return launch_reg<16, ST, REAL, ADV>(p, a, s);
-        case 32: return launch_reg<32, ST, REAL, ADV>(p, a, s);
-        case 64: return launch_reg<64, ST, REAL, ADV>(p, a, s);
-    }
-    return expd_fail(EXPD_ERR_UNSUPPORTED, "register time kernel needs Ns in {16, 32, 64}");
-}
-
 
 // Per-slice totals over the time kernel's CTAs: block n sums slice n's
 // partials in a fixed order (four independent strided accumulators per thread,
@@ -814,19 +412,16 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s) {
     a.f_slices = op.f_slices < 0 ? p->Ns : op.f_slices;
     // power-of-two windows up to 64 with the float32 preconditioner: register kernel
     const bool reg = op.precond && op.f32 && (p->Ns == 16 || p->Ns == 32 || p->Ns == 64) && !p->no_reg_time;
-    // (double-float storage stays on the shared-memory kernel: staging its
-    // 16-byte elements, or loading them without staging, measured slower)
-    if (reg && !op.stdd) {
+    // (double-float storage included: with the right-hand side staged only on
+    // its nonzero slices, 16-byte X and N elements measured 60 us against 96 us
+    // for the shared-memory kernel on 256^2 x 64)
+    if (reg && op.stdd) return time_reg_launch(p, a, 2, s);
+    if (reg) {
         if (op.st32) {
             if (op.NL && !op.nl_f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 storage needs float32 N");
-            return p->realcol ? launch_reg_ns<float, true, false>(p, a, s)
-                   : p->adv   ? launch_reg_ns<float, false, true>(p, a, s)
-                              : launch_reg_ns<float, false, false>(p, a, s);
+            return time_reg_launch(p, a, 1, s);
         }
-        if (!op.NL || !op.nl_f32)
-            return p->realcol ? launch_reg_ns<double, true, false>(p, a, s)
-                   : p->adv   ? launch_reg_ns<double, false, true>(p, a, s)
-                              : launch_reg_ns<double, false, false>(p, a, s);
+        if (!op.NL || !op.nl_f32) return time_reg_launch(p, a, 0, s);
     }
     if (op.stdd) {
         if (!op.f32) return expd_fail(EXPD_ERR_INVALID_ARG, "double-float storage needs the float32 preconditioner");

@@ -626,6 +626,30 @@ def test_graph_sweeps_match_direct_launches(expd, p):
                 assert np.array_equal(U.cpu().numpy(), ref), (jac, k)
 
 
+@pytest.mark.parametrize("p", [CASES[8], CASES[2]], ids=[IDS[8], IDS[2]])
+def test_graph_recaptured_when_forcing_changes(expd, p):
+    # the time kernel reads the right-hand side only on its nonzero slices (the
+    # start-up slices without a forcing term, all of them with one): a plan that
+    # alternates between the two must not relaunch a sweep captured for the other
+    u0 = np.random.default_rng(41).uniform(-0.8, 0.8, p.n)
+    f = 0.3 * np.random.default_rng(42).standard_normal((p.Nt,) + p.n)
+    spec = expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-12, max_iter=200)
+    refs = {}
+    for key, ff in (("none", None), ("f", f)):
+        ref = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+        with expd.plan_create(spec) as plan:
+            plan.solve_fp(dev(u0), None if ff is None else dev(ff), ref)   # default stream: no graphs
+        refs[key] = host(ref)
+    assert relmax(refs["f"], refs["none"]) > 1e-3
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side), expd.plan_create(spec, side) as plan:
+        for key in ("none", "none", "none", "f", "f", "none", "f"):
+            U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+            plan.solve_fp(dev(u0), None if key == "none" else dev(f), U, stream=side)
+            side.synchronize()
+            assert np.array_equal(U.cpu().numpy(), refs[key]), key
+
+
 @pytest.mark.parametrize("p", [CASES[8], CASES[6], CASES[0]], ids=[IDS[8], IDS[6], IDS[0]])
 def test_graph_sequential_stepping_matches_direct(expd, p):
     u0 = np.random.default_rng(26).uniform(-0.8, 0.8, p.n)
