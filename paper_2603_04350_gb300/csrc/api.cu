@@ -1104,10 +1104,11 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
         if (phase == PH32) {
             const bool stalled = it > 2 && rho > 0.5;
             // the next (accurate) sweep contracts the iterate's error and the
-            // float32 rounding floor (a few float32 ulps) by rho: leave now if
-            // that is predicted to reach the tolerance with margin
+            // float32 rounding floor by rho: leave now if that is predicted to
+            // reach the tolerance (the floor is taken as 4 float32 ulps, above
+            // the 2-3 ulps the accurate sweep's first update measures)
             const double floor32 = 4.0 * 5.96e-8;
-            const bool one_more = it > 2 && rho * (measure + floor32) <= 0.5 * p->tol;
+            const bool one_more = it > 2 && rho * (measure + floor32) <= p->tol;
             if (measure <= p->tol || stalled || one_more) {
                 st = leave32();
                 if (st != EXPD_OK) return st;

@@ -385,8 +385,15 @@ constexpr int col4_columns(int N1, int N2, int esz) {
     return C < CR ? CR : C;
 }
 
+// resident CTAs per SM the register budget is sized for: float32 data takes
+// 2 registers per complex value, double-float 4
+template <typename PT>
+constexpr int fft4_min_blocks(int N1) {
+    return sizeof(PT) == 4 ? (N1 >= 32 ? 2 : 4) : (N1 >= 32 ? 1 : 2);
+}
+
 template <typename PT, typename TIN, typename TOUT, int N1, int N2>
-__global__ void __launch_bounds__(COL4_THREADS, N1 >= 32 ? 2 : 4) col4_kernel(const TIN* __restrict__ in, TOUT* __restrict__ out,
+__global__ void __launch_bounds__(COL4_THREADS, fft4_min_blocks<PT>(N1)) col4_kernel(const TIN* __restrict__ in, TOUT* __restrict__ out,
                                                                 long long ncols, int KX,
                                                                 const typename cplx<PT>::t* __restrict__ Wg,
                                                                 int sign, PT scale) {
@@ -768,6 +775,19 @@ template <typename PT, typename TIN, typename TOUT>
 expd_status launch_col(expd_plan p, const TIN* in, TOUT* out, int nslices, int sign, PT scale, cudaStream_t s) {
     typedef typename cplx<PT>::t PT2;
     const int NY = p->NY, KX = p->KX;
+    if constexpr (std::is_same<PT, dd>::value) {
+        // four-step kernel (double-float): 16 to 256 rows (the row pass stays on
+        // the radix-4 kernel: its double-float four-step variant measured slower)
+        if (!p->no_fft4) switch (NY) {
+            case 16: return launch_col4<PT, TIN, TOUT, 4, 4>(p, in, out, nslices, sign, scale, s);
+            case 32: return launch_col4<PT, TIN, TOUT, 8, 4>(p, in, out, nslices, sign, scale, s);
+            case 64: return launch_col4<PT, TIN, TOUT, 8, 8>(p, in, out, nslices, sign, scale, s);
+            case 128: return launch_col4<PT, TIN, TOUT, 16, 8>(p, in, out, nslices, sign, scale, s);
+            case 256: return launch_col4<PT, TIN, TOUT, 16, 16>(p, in, out, nslices, sign, scale, s);
+            default:
+                break;
+        }
+    }
     if constexpr (std::is_same<PT, float>::value) {
         // four-step kernel (float32): 16 to 1024 rows
         if (!p->no_fft4) switch (NY) {
