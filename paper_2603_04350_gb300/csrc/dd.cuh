@@ -145,10 +145,27 @@ EXPD_HD dd2 c2(dd x, dd y) {
 }
 EXPD_HD dd2 cadd(dd2 a, dd2 b) { return c2(a.x + b.x, a.y + b.y); }
 EXPD_HD dd2 csub(dd2 a, dd2 b) { return c2(a.x - b.x, a.y - b.y); }
-EXPD_HD dd2 cmul(dd2 a, dd2 b) { return c2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+// a b + s c d (s = +-1) with one renormalisation: the two leading products
+// and their exact errors (fma), an exact two-sum of the leading products, and
+// the cross terms accumulated in float (a.lo b.lo, of relative size 2^-48, is
+// dropped as in operator*)
+EXPD_HD dd dd_dot2(dd a, dd b, float sg, dd c, dd d) {
+    const float p1 = a.hi * b.hi;
+    const float e1 = fmaf(a.hi, b.hi, -p1);
+    const float p2 = sg * (c.hi * d.hi);
+    const float e2 = fmaf(sg * c.hi, d.hi, -p2);
+    const dd s = dd_two_sum(p1, p2);
+    float lo = s.lo + (e1 + e2);
+    lo = fmaf(a.hi, b.lo, lo);
+    lo = fmaf(a.lo, b.hi, lo);
+    lo = fmaf(sg * c.hi, d.lo, lo);
+    lo = fmaf(sg * c.lo, d.hi, lo);
+    return dd_fast_two_sum(s.hi, lo);
+}
+EXPD_HD dd2 cmul(dd2 a, dd2 b) { return c2(dd_dot2(a.x, b.x, -1.0f, a.y, b.y), dd_dot2(a.x, b.y, 1.0f, a.y, b.x)); }
 EXPD_HD dd2 cconj(dd2 a) { return c2(a.x, -a.y); }
 EXPD_HD dd2 cscale(dd2 a, dd s) { return c2(a.x * s, a.y * s); }
-EXPD_HD dd2 cmulc(dd2 a, dd2 b) { return c2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); }
+EXPD_HD dd2 cmulc(dd2 a, dd2 b) { return c2(dd_dot2(a.x, b.x, 1.0f, a.y, b.y), dd_dot2(a.y, b.x, -1.0f, a.x, b.y)); }
 EXPD_HD dd2 cmuli(dd2 a) { return c2(-a.y, a.x); }
 
 // conversions between the complex storage types

@@ -214,9 +214,50 @@ static void test_conversions(std::mt19937_64& rng) {
     }
 }
 
+// Double-float complex products (cmul, cmulc) against long double, and a
+// double-float register FFT against the naive DFT.
+static void test_dd_complex(std::mt19937_64& rng) {
+    std::normal_distribution<double> N01;
+    std::uniform_int_distribution<int> ex(-20, 20);
+    double worst = 0;
+    for (int i = 0; i < 200000; ++i) {
+        double v[4];
+        for (double& x : v) x = ldexp(N01(rng), ex(rng));
+        const dd2 a = c2(dd(v[0]), dd(v[1])), b = c2(dd(v[2]), dd(v[3]));
+        typedef long double ld;
+        const ld ax = (ld)a.x.hi + (ld)a.x.lo, ay = (ld)a.y.hi + (ld)a.y.lo;
+        const ld bx = (ld)b.x.hi + (ld)b.x.lo, by = (ld)b.y.hi + (ld)b.y.lo;
+        const ld scale = (fabsl(ax) + fabsl(ay)) * (fabsl(bx) + fabsl(by));
+        const dd2 m = cmul(a, b), mc = cmulc(a, b);
+        const ld err[4] = {(ld)m.x.hi + (ld)m.x.lo - (ax * bx - ay * by), (ld)m.y.hi + (ld)m.y.lo - (ax * by + ay * bx),
+                           (ld)mc.x.hi + (ld)mc.x.lo - (ax * bx + ay * by),
+                           (ld)mc.y.hi + (ld)mc.y.lo - (ay * bx - ax * by)};
+        for (ld e : err) worst = std::max(worst, (double)(fabsl(e) / scale));
+    }
+    check("double-float complex products", worst, ldexp(1.0, -45), 0, 0);
+    // 16-point register FFT in double-float
+    constexpr int R = 16;
+    std::vector<cd> x(R), tw(R / 2);
+    for (auto& v : x) v = cd(N01(rng), N01(rng));
+    for (int k = 0; k < R / 2; ++k) tw[k] = std::polar(1.0, -2.0 * M_PI * k / R);
+    std::vector<dd2> twd(R / 2);
+    for (int k = 0; k < R / 2; ++k) twd[k] = c2(dd(tw[k].real()), dd(tw[k].imag()));
+    const std::vector<cd> ref = naive_dft(x, -1);
+    dd2 v[R];
+    for (int j = 0; j < R; ++j) v[bitrev(j, 4)] = c2(dd(x[j].real()), dd(x[j].imag()));
+    reg_fft_dit<R, 1, -1>(v, twd.data());
+    double e = 0, sc = 0;
+    for (int k = 0; k < R; ++k) {
+        e = std::max(e, std::abs(cd((double)v[k].x, (double)v[k].y) - ref[k]));
+        sc = std::max(sc, std::abs(ref[k]));
+    }
+    check("reg_fft_dit double-float", e / sc, 1e-13, R, -1);
+}
+
 int main() {
     std::mt19937_64 rng(1234);
     test_conversions(rng);
+    test_dd_complex(rng);
     for (int l = 1; l <= 12; ++l)
         for (int sign = -1; sign <= 1; sign += 2) {
             test_fft<double, double2>(l, sign, 1e-13, rng);
