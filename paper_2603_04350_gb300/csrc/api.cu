@@ -11,6 +11,7 @@
 //      through the spatial FFTs (lagged form, Eqs. (7.3)-(7.4));
 //   4. the unknown slices return to physical space.
 #include <math.h>
+#include <math_constants.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -156,7 +157,8 @@ void free_plan(expd_plan p) {
     for (void* b : bufs) plan_free(p, b);
     for (auto& g : p->sweep_graph)
         if (g.exec) cudaGraphExecDestroy(g.exec);
-    pinned_release(p->redhost, 2 * (size_t)p->Ns);
+    if (p->loop_graph.exec) cudaGraphExecDestroy(p->loop_graph.exec);
+    pinned_release(p->redhost, 2 * (size_t)p->Ns + EXPD_CTL_DOUBLES + 1);
     for (cudaEvent_t e : p->events) cudaEventDestroy(e);
     time_tables_free(p);
     delete p;
@@ -277,8 +279,7 @@ expd_status setup_start(expd_plan p, const double* u0, const double* f, const do
 // from the per-slice totals, in slice order; the max propagates NaN (fmax
 // would drop it and hide a diverged iterate)
 expd_status read_reduced_norms(expd_plan p, cudaStream_t s, double out[4]) {
-    const size_t nb = 2 * (size_t)p->Ns * sizeof(double);
-    EXPD_CUDA_TRY(cudaMemcpyAsync(p->redhost, p->redout + 8, nb, cudaMemcpyDeviceToHost, s));
+    // the reduction kernel wrote the per-slice totals into mapped host memory
     EXPD_CUDA_TRY(cudaStreamSynchronize(s));
     auto nanmax = [](double a, double b) { return (a != a || b != b) ? NAN : std::max(a, b); };
     double m0 = 0, m1 = 0, s0 = 0, s1 = 0;
@@ -505,6 +506,12 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     // FFTs for every size (both compute the same transforms)
     const char* gr = getenv("EXPD_GRAPHS");
     p->no_graphs = gr && strcmp(gr, "0") == 0;
+    // the device-controlled loop is opt-in (EXPD_DEVICE_LOOP=1): on GB300 its
+    // while-node iterations measured slower than host round trips that read
+    // the norms from mapped memory (0.624 against 0.594 ms per solve on
+    // 256^2 x 64)
+    const char* dl = getenv("EXPD_DEVICE_LOOP");
+    p->no_device_loop = !(dl && strcmp(dl, "1") == 0);
     const char* cf = getenv("EXPD_FFT_KERNEL");
     p->no_fft4 = cf && strcmp(cf, "radix4") == 0;
     return EXPD_OK;
@@ -555,6 +562,251 @@ static expd_status run_sweep(expd_plan p, int phase, const void* key_ptr, double
     }
     EXPD_CUDA_TRY(cudaGraphLaunch(G.exec, s));
     p->launches += G.launches;
+    return EXPD_OK;
+}
+
+// ---- the fixed point under device control ----------------------------------
+// After every sweep one warp reduces the per-slice totals (max over slices of
+// the update and iterate norms, sums only for the finiteness test), runs the
+// stopping test of expd_solve_fp's host loop on the same double values, and
+// sets the while-node conditions: this loop continues, or it ends and (float32
+// loop only) the accurate loop is entered.  A run is bounded by max_iter
+// sweeps in all (the counter lives in LoopCtl), so the loop always ends.
+struct CtlArgs {
+    LoopCtl* c;
+    const double2* tot;  // [Ns] per-slice totals from time_reduce
+    int Ns, phase32, max_iter, sout_set;
+    double tol;
+    cudaGraphConditionalHandle self, next;
+    int has_next;
+};
+
+__device__ __forceinline__ double ctl_nanmax(double a, double b) { return (a != a || b != b) ? CUDART_NAN : (a < b ? b : a); }
+
+__global__ void loop_init_kernel(LoopCtl* c) {
+    c->it = 0;
+    c->it32 = 0;
+    c->result = EXPD_ERR_NOT_CONVERGED;
+    c->phys_valid = 0;
+    c->prev = 0.0;
+    c->rho = 0.5;
+    c->rho_phase = -1.0;
+    c->measure = 1.0;
+    c->s_first = 0.0;
+    c->last_rel = 1.0;
+}
+
+__global__ void set_slot_kernel(double** slot, double* v) { *slot = v; }
+
+// the loop state into mapped host memory (no copy-engine round trip)
+__global__ void loop_out_kernel(const LoopCtl* c, LoopCtl* h) {
+    const double* src = reinterpret_cast<const double*>(c);
+    double* dst = reinterpret_cast<double*>(h);
+    for (int i = threadIdx.x; i < (int)EXPD_CTL_DOUBLES; i += blockDim.x) dst[i] = src[i];
+}
+
+__global__ void loop_ctl_kernel(CtlArgs a) {
+    const int lane = threadIdx.x;
+    double m0 = 0.0, m1 = 0.0, s0 = 0.0, s1 = 0.0;
+    for (int n = lane; n < a.Ns; n += 32) {
+        const double2 v = a.tot[n];
+        m0 = ctl_nanmax(m0, v.x);
+        m1 = ctl_nanmax(m1, v.y);
+        s0 += v.x;
+        s1 += v.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m0 = ctl_nanmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        m1 = ctl_nanmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (lane != 0) return;
+    LoopCtl& c = *a.c;
+    const int it = ++c.it;
+    if (a.phase32) ++c.it32;
+    c.phys_valid = a.sout_set;
+    const double smax = sqrt(m0), umax = sqrt(m1);
+    c.last_rel = umax > 0 ? smax / umax : 1.0;
+    if (it == 1) c.s_first = smax;
+    bool stop = false, leave = false;
+    if (!isfinite(smax) || !isfinite(umax) || !isfinite(s0) || !isfinite(s1) || (it > 1 && smax > 1e3 * c.s_first)) {
+        c.result = EXPD_ERR_DIVERGED;
+        stop = true;
+    } else {
+        const double rel = umax > 0 ? smax / umax : 0.0;
+        if (it > 1 && c.prev > 0) {
+            const double ratio = smax / c.prev;
+            const double lo = 1e-12 < ratio ? ratio : 1e-12;
+            c.rho = 0.95 < lo ? 0.95 : lo;
+        }
+        const double r_use = (c.rho_phase > 0 && !a.phase32) ? c.rho_phase : c.rho;
+        c.measure = it == 1 ? rel : rel * r_use / (1.0 - r_use);
+        if (it <= EXPD_MAX_HISTORY) c.history[it - 1] = c.measure;
+        if (a.phase32) {
+            const bool stalled = it > 2 && c.rho > 0.5;
+            const double floor32 = 4.0 * 5.96e-8;
+            const bool one_more = it > 2 && c.rho * (c.measure + floor32) <= a.tol;
+            if (c.measure <= a.tol || stalled || one_more) {
+                leave = true;
+                if (!stalled) c.rho_phase = c.rho;
+                else if (c.rho_phase < 0) c.rho_phase = 0.5;
+            } else if (c.rho < 0.5) {
+                c.rho_phase = c.rho;
+            }
+        } else if (c.measure <= a.tol) {
+            c.result = EXPD_OK;
+            stop = true;
+        }
+        c.prev = smax;
+    }
+    const bool budget = it < a.max_iter;
+    cudaGraphSetConditional(a.self, (!stop && !leave && budget) ? 1u : 0u);
+    if (a.has_next) cudaGraphSetConditional(a.next, (!stop && budget) ? 1u : 0u);
+}
+
+// Captures what f() launches on s into graph g after the nodes deps; leaves
+// receives the capture's final dependency set (the nodes to continue from).
+template <typename F>
+static expd_status capture_into(cudaStream_t s, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps,
+                                std::vector<cudaGraphNode_t>* leaves, F&& f) {
+    EXPD_CUDA_TRY(cudaStreamBeginCaptureToGraph(s, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                                                cudaStreamCaptureModeThreadLocal));
+    const expd_status st = f();
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaGraphNode_t* d = nullptr;
+    size_t nd = 0;
+    const cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &d, nullptr, &nd);
+    if (e == cudaSuccess && leaves) leaves->assign(d, d + nd);
+    cudaGraph_t out = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s, &out);
+    if (st != EXPD_OK) return st;
+    if (e != cudaSuccess) return expd_cuda_fail(e, "cudaStreamGetCaptureInfo", __FILE__, __LINE__);
+    if (e2 != cudaSuccess) return expd_cuda_fail(e2, "cudaStreamEndCapture", __FILE__, __LINE__);
+    return EXPD_OK;
+}
+
+static expd_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, cudaGraphConditionalHandle h,
+                             cudaGraphNode_t* node, cudaGraph_t* body) {
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    EXPD_CUDA_TRY(cudaGraphAddNode(node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &np));
+    *body = np.conditional.phGraph_out[0];
+    return EXPD_OK;
+}
+
+struct LoopBody {
+    int phase32;   // 1: the float32 loop (ends into the accurate loop)
+    int sout_set;  // the sweep writes the float32 update copy
+};
+
+// Runs the fixed point as one graph: init, while(loop 1) { sweep1; control },
+// then (two = true) between(), while(loop 2) { sweep2; control }.  The graph
+// is built on the first call and relaunched while the pointer, shift and
+// right-hand side slice count baked into its launches are unchanged.
+template <typename Sweep1, typename Between, typename Sweep2>
+static expd_status run_device_loop(expd_plan p, cudaStream_t s, bool two, LoopBody b1, LoopBody b2,
+                                   const void* key_ptr, double key_shift, int key_fs, Sweep1&& sweep1,
+                                   Between&& between, Sweep2&& sweep2, LoopCtl* out) {
+    auto& LG = p->loop_graph;
+    LoopCtl* dctl = reinterpret_cast<LoopCtl*>(p->redout + 8 + 2 * (size_t)p->Ns);
+    const double2* tot = reinterpret_cast<const double2*>(p->redout + 8);
+    if (!LG.exec || LG.key_ptr != key_ptr || LG.key_shift != key_shift || LG.key_fs != key_fs || LG.two != (int)two) {
+        if (LG.exec) {
+            cudaGraphExecDestroy(LG.exec);
+            LG.exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        EXPD_CUDA_TRY(cudaGraphCreate(&g, 0));
+        const long long before = p->launches;
+        auto build = [&]() -> expd_status {
+            cudaGraphConditionalHandle h1 = 0, h2 = 0;
+            EXPD_CUDA_TRY(cudaGraphConditionalHandleCreate(&h1, g, 1, cudaGraphCondAssignDefault));
+            if (two) EXPD_CUDA_TRY(cudaGraphConditionalHandleCreate(&h2, g, 0, cudaGraphCondAssignDefault));
+            std::vector<cudaGraphNode_t> deps;
+            long long l0 = p->launches;
+            expd_status st = capture_into(s, g, {}, &deps, [&]() -> expd_status {
+                loop_init_kernel<<<1, 1, 0, s>>>(dctl);
+                ++p->launches;
+                EXPD_CUDA_TRY(cudaGetLastError());
+                return EXPD_OK;
+            });
+            if (st != EXPD_OK) return st;
+            LG.l_init = p->launches - l0;
+            auto body = [&](cudaGraphConditionalHandle self, const LoopBody& lb, auto&& sweep, long long* count)
+                -> expd_status {
+                cudaGraphNode_t wn = nullptr;
+                cudaGraph_t bg = nullptr;
+                expd_status r = add_while(g, deps, self, &wn, &bg);
+                if (r != EXPD_OK) return r;
+                const long long c0 = p->launches;
+                r = capture_into(s, bg, {}, nullptr, [&]() -> expd_status {
+                    expd_status q = sweep();
+                    if (q != EXPD_OK) return q;
+                    CtlArgs a;
+                    a.c = dctl;
+                    a.tot = tot;
+                    a.Ns = p->Ns;
+                    a.phase32 = lb.phase32;
+                    a.max_iter = p->max_iter;
+                    a.sout_set = lb.sout_set;
+                    a.tol = p->tol;
+                    a.self = self;
+                    a.next = h2;
+                    a.has_next = lb.phase32 && two;
+                    loop_ctl_kernel<<<1, 32, 0, s>>>(a);
+                    ++p->launches;
+                    EXPD_CUDA_TRY(cudaGetLastError());
+                    return EXPD_OK;
+                });
+                if (r != EXPD_OK) return r;
+                *count = p->launches - c0;
+                deps.assign(1, wn);
+                return EXPD_OK;
+            };
+            st = body(h1, b1, sweep1, &LG.l_body1);
+            if (st != EXPD_OK) return st;
+            if (two) {
+                l0 = p->launches;
+                st = capture_into(s, g, deps, &deps, between);
+                if (st != EXPD_OK) return st;
+                LG.l_between = p->launches - l0;
+                st = body(h2, b2, sweep2, &LG.l_body2);
+                if (st != EXPD_OK) return st;
+            }
+            // tail: the loop state into mapped host memory
+            return capture_into(s, g, deps, nullptr, [&]() -> expd_status {
+                loop_out_kernel<<<1, 64, 0, s>>>(dctl, reinterpret_cast<LoopCtl*>(p->redhost_dev + 2 * (size_t)p->Ns));
+                ++p->launches;
+                EXPD_CUDA_TRY(cudaGetLastError());
+                return EXPD_OK;
+            });
+        };
+        const expd_status st = build();
+        p->launches = before;
+        if (st != EXPD_OK) {
+            cudaGraphDestroy(g);
+            return st;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&LG.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            LG.exec = nullptr;
+            return expd_cuda_fail(ei, "cudaGraphInstantiate(fixed point)", __FILE__, __LINE__);
+        }
+        LG.key_ptr = key_ptr;
+        LG.key_shift = key_shift;
+        LG.key_fs = key_fs;
+        LG.two = two;
+    }
+    EXPD_CUDA_TRY(cudaGraphLaunch(LG.exec, s));
+    EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = *reinterpret_cast<const LoopCtl*>(p->redhost + 2 * (size_t)p->Ns);
+    const long long n1 = two ? out->it32 : out->it;
+    p->launches += LG.l_init + n1 * LG.l_body1 + (two ? LG.l_between + (out->it - n1) * LG.l_body2 : 0) + 1;
     return EXPD_OK;
 }
 
@@ -761,14 +1013,23 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
         st = dalloc(p, &p->U32, vec / 2, "iterate (float32)");
         if (st == EXPD_OK) st = dalloc(p, &p->F32, vec / 2, "right-hand side (float32)");
     }
-    // norms: [8..] per-slice totals of the update and iterate norms (the host reduces them)
-    if (st == EXPD_OK) st = dalloc(p, reinterpret_cast<void**>(&p->redout), (8 + 2 * (size_t)p->Ns) * sizeof(double), "norms");
+    // norms: [8..] per-slice totals of the update and iterate norms (the host
+    // or the device loop reduces them), then the device loop's state
+    const size_t nred = 8 + 2 * (size_t)p->Ns + EXPD_CTL_DOUBLES + 1;
+    if (st == EXPD_OK) st = dalloc(p, reinterpret_cast<void**>(&p->redout), nred * sizeof(double), "norms");
     if (st == EXPD_OK) {
-        cudaError_t e = cudaMemsetAsync(p->redout, 0, (8 + 2 * (size_t)p->Ns) * sizeof(double), s);
+        cudaError_t e = cudaMemsetAsync(p->redout, 0, nred * sizeof(double), s);
         if (e != cudaSuccess) st = expd_cuda_fail(e, "cudaMemsetAsync(norms)", __FILE__, __LINE__);
     }
     if (st == EXPD_OK) {
-        p->redhost = pinned_acquire(2 * (size_t)p->Ns);
+        p->redhost = pinned_acquire(2 * (size_t)p->Ns + EXPD_CTL_DOUBLES + 1);
+        p->phys_slot = reinterpret_cast<double**>(p->redout + nred - 1);
+        if (p->redhost) {
+            void* d = nullptr;
+            const cudaError_t e = cudaHostGetDevicePointer(&d, p->redhost, 0);
+            if (e != cudaSuccess) st = expd_cuda_fail(e, "cudaHostGetDevicePointer(norms)", __FILE__, __LINE__);
+            p->redhost_dev = static_cast<double*>(d);
+        }
         if (!p->redhost) st = expd_fail(EXPD_ERR_OOM, "pinned host memory for the norms");
     }
     if (st == EXPD_OK) st = time_tables_build(p, s);
@@ -818,7 +1079,7 @@ expd_status expd_plan_footprint_bytes(const expd_grid* grid, const expd_operator
         if (mixed && per) b += Ns * Mcol * 8 + Ns * p->NY * p->KX * 8;      // NL32, work32
     }
     if (mixed && (!nl || per)) b += vec;                                    // U32, F32
-    b += (8 + 2 * Ns) * 8;                                                  // norms
+    b += (8 + 2 * Ns + EXPD_CTL_DOUBLES + 1) * 8;                           // norms, loop state, slot
     const TimeTablesHost th = time_tables_host(p->Ns, alpha);
     for (int q = 0; q < 2; ++q) {
         const size_t e = q == 0 ? 16 : 8, g = q == 0 ? 8 : 4;
@@ -1030,54 +1291,100 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     }
     double* phys_out = sg.U + (size_t)(p->order - 1) * p->M;
     const bool fast_out = use_dd && nl && inverse32_accum_supported(p);
-    bool phys_valid = false;
-    double last_rel = 1.0;
-    double prev = 0.0, rho = 0.5, rho_phase = -1.0, measure = 1.0, s_first = 0.0;
-    int it = 0, it32 = 0;
-    expd_status result = EXPD_ERR_NOT_CONVERGED;
-    for (it = 1; it <= p->max_iter; ++it) {
+    // the time operator of a sweep of phase ph
+    auto make_op = [&](int ph) -> TimeOp {
         TimeOp op;
-        op.X = phase == PH32 ? p->U32 : p->Uh;
-        op.F = phase == PH32 ? p->F32 : p->Fh;
+        op.X = ph == PH32 ? p->U32 : p->Uh;
+        op.F = ph == PH32 ? p->F32 : p->Fh;
         op.f_slices = p->f_slices;
         op.sigR = -1.0;
         op.precond = 1;
         op.accum = 1;
         op.f32 = mixed;
-        op.st32 = phase == PH32;
-        op.stdd = phase == PHDD;
+        op.st32 = ph == PH32;
+        op.stdd = ph == PHDD;
         op.dshift = dshift;
-        const bool used32 = phase == PH32;
-        if (nl && phase == PHDD && fast_out) op.sout = p->U32;  // free in this phase
-        // one sweep: N(iterate) through the spatial transforms, the time
-        // kernel, the per-slice reduction
-        auto issue = [&]() -> expd_status {
-            expd_status r = EXPD_OK;
-            TimeOp o = op;
-            if (nl) {
-                void* NL;
-                if (phase == PH32) {
-                    NL = p->NL32;
-                    r = nonlinear_eval(p, o.X, NL, 1, s, 1);
-                    o.nl_f32 = 1;
-                } else if (phase == PHDD) {
-                    NL = p->NL64;  // holds double-float values in this phase
-                    r = nonlinear_eval_dd(p, o.X, NL, s, fast_out ? phys_out : nullptr);
-                } else {
-                    NL = p->NL64;
-                    r = nonlinear_eval(p, o.X, NL, 0, s, 0);
-                }
-                if (r != EXPD_OK) return r;
-                o.NL = NL;
-                o.bdt = p->beta[p->order] * p->dt;
+        if (nl && ph == PHDD && fast_out) op.sout = p->U32;  // free in this phase
+        return op;
+    };
+    // one sweep: N(iterate) through the spatial transforms, the time kernel,
+    // the per-slice reduction
+    auto sweep = [&](int ph) -> expd_status {
+        expd_status r = EXPD_OK;
+        TimeOp o = make_op(ph);
+        if (nl) {
+            void* NL;
+            if (ph == PH32) {
+                NL = p->NL32;
+                r = nonlinear_eval(p, o.X, NL, 1, s, 1);
+                o.nl_f32 = 1;
+            } else if (ph == PHDD) {
+                NL = p->NL64;  // holds double-float values in this phase
+                r = nonlinear_eval_dd(p, o.X, NL, s, fast_out ? p->phys_slot : nullptr);
+            } else {
+                NL = p->NL64;
+                r = nonlinear_eval(p, o.X, NL, 0, s, 0);
             }
-            r = time_apply(p, o, s);
-            if (r == EXPD_OK) r = time_reduce(p, s);
-            return r;
+            if (r != EXPD_OK) return r;
+            o.NL = NL;
+            o.bdt = p->beta[p->order] * p->dt;
+        }
+        r = time_apply(p, o, s);
+        if (r == EXPD_OK) r = time_reduce(p, s);
+        return r;
+    };
+    const int acc_phase = use_dd ? PHDD : PH64;
+    if (fast_out && p->phys_slot_value != phys_out) {  // the destination of the physical iterate
+        set_slot_kernel<<<1, 1, 0, s>>>(p->phys_slot, phys_out);
+        ++p->launches;
+        EXPD_CUDA_TRY(cudaGetLastError());
+        p->phys_slot_value = phys_out;
+    }
+    bool phys_valid = false;
+    double last_rel = 1.0;
+    double prev = 0.0, rho = 0.5, rho_phase = -1.0, measure = 1.0, s_first = 0.0;
+    int it = 0, it32 = 0;
+    expd_status result = EXPD_ERR_NOT_CONVERGED;
+    // With EXPD_DEVICE_LOOP=1 the stopping test runs on the GPU (one graph per
+    // solve, no host round trip per sweep) on a capturable stream once the
+    // plan has run a solve (its first solve sets up every kernel outside
+    // capture); otherwise the host reads the norms after every sweep.
+    const bool device_loop = !p->timing && !p->no_graphs && !p->no_device_loop && s != nullptr &&
+                             p->fp_solves > 0 && p->max_iter >= 1;
+    ++p->fp_solves;
+    if (device_loop) {
+        const bool two = phase == PH32;
+        LoopBody b1{two ? 1 : 0, make_op(two ? PH32 : acc_phase).sout != nullptr ? 1 : 0};
+        LoopBody b2{0, make_op(acc_phase).sout != nullptr ? 1 : 0};
+        const int ph1 = two ? PH32 : acc_phase;
+        auto convert = [&]() -> expd_status {
+            return use_dd ? convert_f32_to_dd(p, static_cast<const float*>(p->U32), p->Uh, nvec, s)
+                          : convert_f32_to_f64(p, static_cast<const float*>(p->U32), static_cast<double*>(p->Uh), nvec, s);
         };
-        st = run_sweep(p, phase, fast_out && phase == PHDD ? phys_out : nullptr, dshift, op.f_slices, s, issue);
+        LoopCtl c;
+        st = run_device_loop(p, s, two, b1, b2, nullptr, dshift, p->f_slices,
+                             [&]() { return sweep(ph1); }, convert, [&]() { return sweep(acc_phase); }, &c);
         if (st != EXPD_OK) return st;
-        phys_valid = op.sout != nullptr;
+        phase = acc_phase;  // the conversion always follows the float32 loop
+        it = c.it;
+        it32 = c.it32;
+        measure = c.measure;
+        rho = c.rho;
+        last_rel = c.last_rel;
+        phys_valid = c.phys_valid != 0;
+        if (info) {
+            for (int i = 0; i < it && i < EXPD_MAX_HISTORY; ++i) info->history[i] = c.history[i];
+            info->contraction = rho;
+        }
+        result = c.result == EXPD_ERR_DIVERGED ? expd_fail(EXPD_ERR_DIVERGED, "fixed-point update is non-finite or growing")
+                                               : static_cast<expd_status>(c.result);
+    } else {
+    for (it = 1; it <= p->max_iter; ++it) {
+        const bool used32 = phase == PH32;
+        const int ph = phase;
+        st = run_sweep(p, phase, nullptr, dshift, p->f_slices, s, [&]() { return sweep(ph); });
+        if (st != EXPD_OK) return st;
+        phys_valid = make_op(ph).sout != nullptr;
         double nr[4];
         st = read_reduced_norms(p, s, nr);
         if (st != EXPD_OK) return st;
@@ -1128,6 +1435,7 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     if (phase == PH32) {
         st = leave32();
         if (st != EXPD_OK) return st;
+    }
     }
     if (info) {
         info->iterations = it;

@@ -37,6 +37,17 @@ struct TimeTables {
     void* bminus = nullptr;   // [L]    FFT_L of chirp kernel, bit-reversed order
 };
 
+// State of the device-controlled fixed point (the stopping test of the
+// host loop, run by one warp after every sweep); read back once per solve.
+struct LoopCtl {
+    int it, it32, result, phys_valid;
+    int pad[4];
+    double prev, rho, rho_phase, measure, s_first, last_rel;
+    double history[EXPD_MAX_HISTORY];
+};
+constexpr size_t EXPD_CTL_DOUBLES = sizeof(LoopCtl) / sizeof(double);
+static_assert(sizeof(LoopCtl) % sizeof(double) == 0, "loop state in whole doubles");
+
 struct expd_plan_s {
     // ---- problem ----------------------------------------------------------
     int ndim = 1, NX = 1, NY = 1;  // NX fast axis, NY slow axis (1 for 1D)
@@ -114,6 +125,21 @@ struct expd_plan_s {
         long long launches = 0;
         int eager = 0;  // sweeps launched directly (the first one sets kernel attributes)
     } sweep_graph[4];             // [0..2] fixed-point phases, [3] sequential stepping
+    // The whole fixed point as one graph: initialisation, a device-controlled
+    // loop over float32 sweeps, the conversion, a loop over accurate sweeps
+    // (conditional while-nodes; the stopping test runs on the GPU).
+    struct LoopGraph {
+        cudaGraphExec_t exec = nullptr;
+        const void* key_ptr = nullptr;
+        double key_shift = 0;
+        int key_fs = 0, two = 0;
+        long long l_init = 0, l_body1 = 0, l_between = 0, l_body2 = 0;
+    } loop_graph;
+    int no_device_loop = 1;       // 0: stopping test on the GPU (EXPD_DEVICE_LOOP=1)
+    double** phys_slot = nullptr; // device: destination of the physical iterate (in the norms buffer)
+    double* phys_slot_value = nullptr;  // what phys_slot holds (rewritten only when it changes)
+    double* redhost_dev = nullptr;      // redhost as the GPU addresses it (mapped pinned memory)
+    long long fp_solves = 0;      // fixed-point solves run on this plan
     int no_graphs = 0;            // 1: launch kernel by kernel (EXPD_GRAPHS=0)
     int no_reg_time = 0;          // 1 forces the shared-memory time kernel (tests)
     int no_fft4 = 0;              // 1 forces the radix-4 shared-memory row / column FFTs (tests)
@@ -179,8 +205,10 @@ expd_status convert_f32_to_f64(expd_plan p, const float* in, double* out, long l
 // double-float ("dd", float hi + float lo) helpers of the mixed path's accurate phase
 expd_status convert_f64_to_dd_inplace(expd_plan p, double* a, long long n, cudaStream_t s);
 expd_status convert_f32_to_dd(expd_plan p, const float* in, void* out, long long n, cudaStream_t s);
-// phys (optional): the physical rows before N, float64 [Ns][NY][NX]
-expd_status nonlinear_eval_dd(expd_plan p, const void* Uh, void* out, cudaStream_t s, double* phys = nullptr);
+// phys_slot (optional): device memory holding where the physical rows before
+// N go (float64 [Ns][NY][NX]); the pointer is read by the kernel, so a captured
+// sweep serves any destination
+expd_status nonlinear_eval_dd(expd_plan p, const void* Uh, void* out, cudaStream_t s, double* const* phys_slot = nullptr);
 // phys += inverse transform of a float32 half-spectrum [Ns][NY][KX] (float32
 // four-step kernels; periodic grids with NX in 32..2048, NY in 16..1024)
 bool inverse32_accum_supported(expd_plan p);

@@ -35,9 +35,12 @@ __device__ __forceinline__ R nl_ac(R u) { return u - u * u * u; }
 template <typename PT, typename TIN, typename TOUT, int KIND>
 __global__ void row_kernel(const TIN* in, TOUT* out, long long rows, int NX,
                            int log2NH, const typename cplx<PT>::t* __restrict__ Wg, PT scale, int nonlin,
-                           double* phys) {
+                           double* const* phys_slot) {
     typedef typename cplx<PT>::t PT2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // KIND 2: where to write the physical rows (read from device memory, so a
+    // captured launch serves any output buffer), or nowhere
+    double* const phys = (KIND == 2 && phys_slot) ? *phys_slot : nullptr;
     const int NH = NX >> 1;
     const int KX = NH + 1;
     PT2* W = reinterpret_cast<PT2*>(smem_raw);
@@ -700,11 +703,11 @@ expd_status launch_row4(expd_plan p, const TIN* in, TOUT* out, long long rows, P
 
 template <typename PT, typename TIN, typename TOUT, int KIND>
 expd_status launch_row_r4(expd_plan p, const TIN* in, TOUT* out, long long rows, PT scale, cudaStream_t s,
-                          double* phys);
+                          double* const* phys_slot);
 
 template <typename PT, typename TIN, typename TOUT, int KIND>
 expd_status launch_row(expd_plan p, const TIN* in, TOUT* out, long long rows, PT scale, cudaStream_t s,
-                       double* phys = nullptr) {
+                       double* const* phys_slot = nullptr) {
     typedef typename cplx<PT>::t PT2;
     const int NH = p->NX / 2;
     if constexpr (std::is_same<PT, float>::value) {
@@ -724,14 +727,14 @@ expd_status launch_row(expd_plan p, const TIN* in, TOUT* out, long long rows, PT
     if constexpr (KIND == 3) {
         return expd_fail(EXPD_ERR_UNSUPPORTED, "accumulating c2r needs a float32 row of 32..2048 points");
     } else {
-        return launch_row_r4<PT, TIN, TOUT, KIND>(p, in, out, rows, scale, s, phys);
+        return launch_row_r4<PT, TIN, TOUT, KIND>(p, in, out, rows, scale, s, phys_slot);
     }
 }
 
 // the radix-4 shared-memory row kernel (every size and precision)
 template <typename PT, typename TIN, typename TOUT, int KIND>
 expd_status launch_row_r4(expd_plan p, const TIN* in, TOUT* out, long long rows, PT scale, cudaStream_t s,
-                          double* phys) {
+                          double* const* phys_slot) {
     typedef typename cplx<PT>::t PT2;
     const int NH = p->NX / 2;
     const size_t per_row = (size_t)NH * sizeof(PT2);
@@ -748,7 +751,7 @@ expd_status launch_row_r4(expd_plan p, const TIN* in, TOUT* out, long long rows,
     const double fl = (KIND == 2 ? 2.0 : 1.0) * 2.5 * p->NX * ilog2(p->NX) * (double)rows;
     KProf kp(p, s, sizeof(PT) == 4 ? EXPD_K_FFT_ROW32 : sizeof(PT) == 8 && !std::is_same<PT, double>::value ? EXPD_K_FFT_ROWDD : EXPD_K_FFT_ROW,
              (double)rows * (in_row + out_row), fl);
-    kern<<<(int)blocks, 32 * R, smem, s>>>(in, out, rows, p->NX, ilog2(NH), Wx<PT>(p), scale, p->nonlin, phys);
+    kern<<<(int)blocks, 32 * R, smem, s>>>(in, out, rows, p->NX, ilog2(NH), Wx<PT>(p), scale, p->nonlin, phys_slot);
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }
@@ -1063,16 +1066,16 @@ expd_status convert_f32_to_f64(expd_plan p, const float* in, double* out, long l
     return EXPD_OK;
 }
 
-expd_status nonlinear_eval_dd(expd_plan p, const void* Uh, void* out, cudaStream_t s, double* phys) {
+expd_status nonlinear_eval_dd(expd_plan p, const void* Uh, void* out, cudaStream_t s, double* const* phys_slot) {
     if (p->bc != EXPD_BC_PERIODIC) return expd_fail(EXPD_ERR_INVALID_ARG, "double-float N needs a periodic grid");
     const dd2* U = static_cast<const dd2*>(Uh);
     dd2* o = static_cast<dd2*>(out);
     const long long rows = (long long)p->Ns * p->NY;
     const dd sx(1.0 / (p->NX / 2));
-    if (p->ndim == 1) return launch_row<dd, dd2, dd2, 2>(p, U, o, rows, sx, s, phys);
+    if (p->ndim == 1) return launch_row<dd, dd2, dd2, 2>(p, U, o, rows, sx, s, phys_slot);
     dd2* w = static_cast<dd2*>(p->work64);
     expd_status st = launch_col<dd, dd2, dd2>(p, U, w, p->Ns, +1, dd(1.0 / p->NY), s);
-    if (st == EXPD_OK) st = launch_row<dd, dd2, dd2, 2>(p, w, w, rows, sx, s, phys);
+    if (st == EXPD_OK) st = launch_row<dd, dd2, dd2, 2>(p, w, w, rows, sx, s, phys_slot);
     if (st == EXPD_OK) st = launch_col<dd, dd2, dd2>(p, w, o, p->Ns, -1, dd(1.0), s);
     return st;
 }

@@ -199,9 +199,10 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
 // Per-slice totals over the time kernel's CTAs: block n sums slice n's
 // partials in a fixed order (four independent strided accumulators per thread,
 // a shuffle tree, then the warps in order), so the totals are deterministic.
-// The host takes the max and the sum over slices (in slice order).
+// The totals go to device memory (for the device-side stopping test) and to
+// host-mapped memory (the host loop reads them there without a copy).
 __global__ void __launch_bounds__(256) reduce_kernel(const double2* __restrict__ partial, int grid,
-                                                     double2* __restrict__ slice_tot) {
+                                                     double2* __restrict__ slice_tot, double2* host_tot) {
     __shared__ double2 red[8];
     const int n = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double2* src = partial + (size_t)n * grid;
@@ -237,6 +238,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const double2* __restrict__
             t.y += red[w].y;
         }
         slice_tot[n] = t;
+        if (host_tot) host_tot[n] = t;
     }
 }
 
@@ -449,7 +451,7 @@ expd_status time_reduce(expd_plan p, cudaStream_t s) {
     const int grid = p->time_grid_used > 0 ? p->time_grid_used : p->time_grid;
     KProf kp(p, s, EXPD_K_REDUCE, 16.0 * grid * p->Ns, 2.0 * grid * p->Ns);
     double2* slice_tot = reinterpret_cast<double2*>(p->redout + 8);
-    reduce_kernel<<<p->Ns, 256, 0, s>>>(p->partial, grid, slice_tot);
+    reduce_kernel<<<p->Ns, 256, 0, s>>>(p->partial, grid, slice_tot, reinterpret_cast<double2*>(p->redhost_dev));
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }

@@ -626,6 +626,44 @@ def test_graph_sweeps_match_direct_launches(expd, p):
                 assert np.array_equal(U.cpu().numpy(), ref), (jac, k)
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("max_iter", [200, 3])
+@pytest.mark.parametrize("p", [CASES[8], CASES[10], CASES[2], CASES[13]], ids=[IDS[8], IDS[10], IDS[2], IDS[13]])
+def test_device_loop_matches_host_loop(expd, p, max_iter, prec, monkeypatch):
+    # with EXPD_DEVICE_LOOP=1, from its second solve a plan on a capturable
+    # stream runs the fixed point as one graph whose stopping test runs on the
+    # GPU (while-nodes); the iterate, the iteration counts, the error-estimate
+    # history and the status must be those of the host-side loop, bit for bit
+    u0 = np.random.default_rng(51).uniform(-0.8, 0.8, p.n)
+    f = 0.3 * np.random.default_rng(52).standard_normal((p.Nt,) + p.n) if p.nonlin == "none" else None
+    fd = None if f is None else dev(f)
+    precision = expd.PREC_MIXED if prec == "mixed" else expd.PREC_FP64
+    spec = expd.spec_from_problem(p, precision=precision, tol=1e-12, max_iter=max_iter)
+    side = torch.cuda.Stream()
+    runs = {}
+    for mode in ("host", "device"):
+        monkeypatch.setenv("EXPD_DEVICE_LOOP", "1" if mode == "device" else "0")
+        out = []
+        with torch.cuda.stream(side), expd.plan_create(spec, side) as plan:
+            for _ in range(3):
+                U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+                plan.timing_read(reset=True)
+                info = plan.solve_fp(dev(u0), fd, U, stream=side, allow_not_converged=True)
+                side.synchronize()
+                info["launches"] = plan.timing_read(reset=True)["launches"]
+                out.append((U.cpu().numpy(), info))
+        runs[mode] = out
+    # the device loop adds its init, per-sweep control and output launches
+    last_h, last_d = runs["host"][-1][1], runs["device"][-1][1]
+    assert last_d["launches"] == last_h["launches"] + last_d["iterations"] + 2
+    for (Uh, ih), (Ud, idv) in zip(runs["host"], runs["device"]):
+        assert np.array_equal(Uh, Ud)
+        for k in ("iterations", "fp32_iterations", "final_measure", "contraction", "history", "status"):
+            assert ih[k] == idv[k], k
+    if max_iter == 3:
+        assert runs["device"][-1][1]["status"] == expd.ERR_NOT_CONVERGED
+
+
 @pytest.mark.parametrize("p", [CASES[8], CASES[2]], ids=[IDS[8], IDS[2]])
 def test_graph_recaptured_when_forcing_changes(expd, p):
     # the time kernel reads the right-hand side only on its nonzero slices (the
