@@ -374,20 +374,40 @@ def assemble(sp: Spec, U_start: np.ndarray, V: np.ndarray) -> np.ndarray:
     return U
 
 
+def linear_guess(sp: Spec, U_start: np.ndarray) -> np.ndarray:
+    """The unknown slices u_s..u_Nt propagated from the last start-up value
+    without N and f: u_n = A^{n-s+1} u_{s-1}, A = exp(dt L_h) (Eq. (2.2)).
+    This is what the scheme itself produces when N = 0 and f = 0, since the
+    BDF coefficients sum to one (Eq. (4.1), Sec. 5): sum_j a_j A^j A^{n-j} u =
+    A^n u.  The paper runs the iteration from several initial guesses (Sec. 7)
+    without fixing one; this one is the default initial iterate here."""
+    u_last = U_start[sp.order - 1]
+    return np.stack([apply_A_power(sp, u_last, k + 1) for k in range(sp.Ns)])
+
+
 def richardson(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None,
                max_iter: int = 50, tol: float = 0.0, keep_iterates: bool = False,
                V0: Optional[np.ndarray] = None,
-               U_start: Optional[np.ndarray] = None, jacobian: str = "lagged") -> SolveResult:
+               U_start: Optional[np.ndarray] = None, jacobian: str = "lagged",
+               init: str = "zero") -> SolveResult:
     """Preconditioned fixed-point iteration v^{k+1} = v^k + P_alpha^{-1}(f_s +
-    beta dt N(v^k) - R_s v^k) from v^0 = 0 (Eqs. (3.2), (4.4), (7.3)-(7.4);
-    Sec. 7 starts from zero).  Stops when max_n ||s_n|| <= tol * max_n ||v_n||
-    or after max_iter iterations.  jacobian="mean_u0" preconditions with
-    P_alpha - beta dt nbar I (see `jacobian_shift`): the same fixed point,
-    reached by inexact Newton steps."""
+    beta dt N(v^k) - R_s v^k) (Eqs. (3.2), (4.4), (7.3)-(7.4)) from v^0 = V0,
+    else from zero (init="zero") or from `linear_guess` (init="linear").
+    Stops when max_n ||s_n|| <= tol * max_n ||v_n|| or after max_iter
+    iterations.  jacobian="mean_u0" preconditions with P_alpha - beta dt nbar I
+    (see `jacobian_shift`): the same fixed point, reached by inexact Newton
+    steps."""
     shift = jacobian_shift(sp, u0) if jacobian == "mean_u0" else 0.0
     U_start = startup_values(sp, u0, f, U_start)
     b = rhs_known(sp, U_start, f)
-    V = np.zeros((sp.Ns,) + sp.n) if V0 is None else V0.copy()
+    if V0 is not None:
+        V = V0.copy()
+    elif init == "linear":
+        V = linear_guess(sp, U_start)
+    elif init == "zero":
+        V = np.zeros((sp.Ns,) + sp.n)
+    else:
+        raise ValueError(f"unknown initial guess {init!r}")
     hist, its = [], []
     k = 0
     for k in range(1, max_iter + 1):

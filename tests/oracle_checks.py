@@ -399,3 +399,22 @@ def check_advection_exact(Nx=64, Nt=16, b=2.0, a=0.1, seed=2):
     U = O.sequential_solve(sp, exact(0.0))
     Ue = np.array([exact(n * sp.dt) for n in range(Nt + 1)])
     return O.rel_error(U[1:], Ue[1:])
+
+
+# --- initial iterate --------------------------------------------------------
+def check_linear_guess_is_homogeneous_solution():
+    """Without N and f the scheme's solution is u_n = A^n u_0 (the BDF
+    coefficients sum to one), so `linear_guess` must equal sequential stepping
+    there, for every order and grid, advection included; returns the worst
+    relative difference."""
+    worst = 0.0
+    cases = [spec("periodic", (12,), a=0.05, c=0.1, Nt=order + 9, order=order, dt=0.03) for order in (1, 2, 6)]
+    cases += [spec("dirichlet", (7, 5), a=0.02, c=0.1, Nt=order + 7, order=order, dt=0.05) for order in (1, 3)]
+    cases += [O.Spec("periodic", (16,), (1.0,), 0.01, 0.0, "none", 0.02, 10, 0.01, 2, b=(0.7,))]
+    for sp in cases:
+        u0 = np.random.default_rng(sp.order + sp.Nt).standard_normal(sp.n)
+        ref = O.sequential_solve(sp, u0)
+        U_start = O.startup_values(sp, u0)
+        V = O.linear_guess(sp, U_start)
+        worst = max(worst, O.rel_error(V, ref[sp.order:]))
+    return worst

@@ -293,3 +293,22 @@ def test_advection_solvers_reach_sequential(order):
     assert O.rel_error(O.richardson(sp, u0, f, max_iter=12).U[1:], ref) < 1e-11
     assert O.rel_error(O.gmres(sp, u0, f, tol=1e-13).U[1:], ref) < 1e-11
     assert O.rel_error(O.bicgstab(sp, u0, f, tol=1e-13).U[1:], ref) < 1e-11
+
+
+def test_linear_guess_solves_the_homogeneous_scheme():
+    # the default initial iterate of the fixed point: exact for N = 0, f = 0
+    assert C.check_linear_guess_is_homogeneous_solution() < 1e-12
+
+
+def test_linear_guess_reaches_the_same_fixed_point_one_sweep_sooner():
+    # Allen-Cahn: both initial iterates converge to the same fixed point; the
+    # zero iterate's first sweep produces (up to the alpha perturbation) what
+    # the linear guess already is, so the histories are shifted by one sweep
+    sp = C.spec("periodic", (16, 16), length=(1.0, 1.0), a=0.0025, c=0.0, nonlin="allen_cahn",
+                Nt=32, order=1, alpha=1e-3, dt=1e-3)
+    u0 = np.random.default_rng(21).uniform(-0.9, 0.9, sp.n)
+    rz = O.richardson(sp, u0, max_iter=8, init="zero")
+    rl = O.richardson(sp, u0, max_iter=8, init="linear")
+    assert O.rel_error(rl.U[1:], rz.U[1:]) < 1e-12
+    for k in range(1, 5):
+        assert rl.history[k - 1] < 3.0 * rz.history[k]

@@ -169,3 +169,12 @@ def test_planted_advection_sign_is_caught(monkeypatch):
     real = E.spatial_eigenvalues
     patch(monkeypatch, "spatial_eigenvalues", lambda sp: np.conj(real(sp)))
     assert C.check_advection_exact() > 1e-3
+
+
+def test_planted_linear_guess_power_is_caught(monkeypatch):
+    # off by one in the propagation power: A^k instead of A^(k+1)
+    def linear_guess(sp, U_start):
+        u_last = U_start[sp.order - 1]
+        return np.stack([E.apply_A_power(sp, u_last, k) for k in range(sp.Ns)])
+    patch(monkeypatch, "linear_guess", linear_guess)
+    assert C.check_linear_guess_is_homogeneous_solution() > 1e-6
