@@ -114,8 +114,17 @@ typedef struct {
  *             steps with the Jacobian at the initial value (proposed after
  *             Eq. (6.5)) averaged over space, i.e. R_s^alpha - beta_s dt nbar I,
  *             nbar = mean of N'(u_0); Step (b) stays diagonal and the fixed
- *             point is unchanged.  Ignored for linear problems.            */
+ *             point is unchanged.  Ignored for linear problems.
+ *  guess      the fixed point's initial iterate.  EXPD_GUESS_LINEAR (0, the
+ *             default): u_n = A^(n-s+1) u_{s-1}, the scheme's own solution
+ *             when N = 0 and f = 0 (the BDF coefficients sum to one; Eq. (2.2),
+ *             Eq. (4.1)) -- one sweep of the zero start produces it up to the
+ *             alpha perturbation, so the iteration needs one sweep fewer.
+ *             EXPD_GUESS_ZERO (1): u_n = 0.  The paper runs several initial
+ *             guesses (Sec. 7) without fixing one.  GMRES and BiCGStab start
+ *             from zero.                                                   */
 enum { EXPD_JAC_LAGGED = 0, EXPD_JAC_MEAN_U0 = 1 };
+enum { EXPD_GUESS_LINEAR = 0, EXPD_GUESS_ZERO = 1 };
 typedef struct {
     int order;
     int precision;
@@ -124,6 +133,7 @@ typedef struct {
     int gmres_restart;
     int startup;
     int jacobian;               /* EXPD_JAC_*                                          */
+    int guess;                  /* EXPD_GUESS_*                                        */
 } expd_scheme;
 
 #define EXPD_MAX_HISTORY 128

@@ -441,6 +441,8 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
         return expd_fail(EXPD_ERR_INVALID_ARG, "gmres_restart must be in [1, 64]");
     if (scheme->jacobian != EXPD_JAC_LAGGED && scheme->jacobian != EXPD_JAC_MEAN_U0)
         return expd_fail(EXPD_ERR_INVALID_ARG, "jacobian must be EXPD_JAC_LAGGED or EXPD_JAC_MEAN_U0");
+    if (scheme->guess != EXPD_GUESS_LINEAR && scheme->guess != EXPD_GUESS_ZERO)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "guess must be EXPD_GUESS_LINEAR or EXPD_GUESS_ZERO");
     if (scheme->startup != EXPD_STARTUP_RAMP && scheme->startup != EXPD_STARTUP_GIVEN)
         return expd_fail(EXPD_ERR_INVALID_ARG, "unknown startup mode");
     p->ndim = grid->ndim;
@@ -480,6 +482,7 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     p->restart = scheme->gmres_restart;
     p->startup = scheme->startup;
     p->jacobian = scheme->jacobian;
+    p->guess = scheme->guess;
     for (int q = 1; q <= 6; ++q) bdf(q, p->acoef[q], &p->beta[q]);
     if (p->nonlin != EXPD_NL_NONE) {
         for (int q = 1; q <= p->order; ++q)
@@ -1253,7 +1256,11 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     enum { PH32, PHDD, PH64 };
     const bool use_dd = mixed && p->bc == EXPD_BC_PERIODIC && p->Cdd != nullptr;
     int phase = (mixed && p->U32 != nullptr) ? PH32 : PH64;
-    if (phase == PH32) {
+    // the initial iterate: the last start-up slice propagated by A, or zero
+    if (p->guess == EXPD_GUESS_LINEAR) {
+        st = linear_guess(p, phase == PH32 ? p->U32 : p->Uh, phase == PH32, s);
+        if (st != EXPD_OK) return st;
+    } else if (phase == PH32) {
         EXPD_CUDA_TRY(cudaMemsetAsync(p->U32, 0, (size_t)nvec * sizeof(float), s));
     } else {
         EXPD_CUDA_TRY(cudaMemsetAsync(p->Uh, 0, (size_t)nvec * sizeof(double), s));

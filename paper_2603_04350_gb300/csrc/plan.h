@@ -113,6 +113,7 @@ struct expd_plan_s {
     int partial_cap = 0;          // CTAs the partial-norm buffer has room for
     int time_grid_used = 0;       // CTAs of the last time-kernel launch (for the reduction)
     int jacobian = 0;             // EXPD_JAC_*
+    int guess = 0;                // EXPD_GUESS_*: the fixed point's initial iterate
     int f_slices = 0;             // leading slices of the right-hand side Fh / F32 that can be nonzero
     // One sweep of the fixed point (N evaluation, time kernel, per-slice
     // reduction) per phase, captured as a CUDA graph on first use and relaunched
@@ -208,6 +209,9 @@ expd_status convert_f32_to_dd(expd_plan p, const float* in, void* out, long long
 // phys_slot (optional): device memory holding where the physical rows before
 // N go (float64 [Ns][NY][NX]); the pointer is read by the kernel, so a captured
 // sweep serves any destination
+// The fixed point's initial iterate X (float32 when x32, else float64, eigen
+// layout): X_k = E^(k+1) S_{s-1}, the last start-up slice propagated by A.
+expd_status linear_guess(expd_plan p, void* X, int x32, cudaStream_t s);
 expd_status nonlinear_eval_dd(expd_plan p, const void* Uh, void* out, cudaStream_t s, double* const* phys_slot = nullptr);
 // phys += inverse transform of a float32 half-spectrum [Ns][NY][KX] (float32
 // four-step kernels; periodic grids with NX in 32..2048, NY in 16..1024)

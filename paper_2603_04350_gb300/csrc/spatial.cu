@@ -304,6 +304,42 @@ struct RhsArgs {
     int eshift, s, Ns;
 };
 
+// Initial iterate X_k[m] = E_m^(k+1) S[m], k < Ns: one thread per mode walks
+// the slices (multiplying by E_m, complex with advection), coalesced across
+// the modes; in float32 for the float32 iterate (a guess needs no more).
+template <typename ST, bool REAL, bool ADV>
+__global__ void linear_guess_kernel(const double* __restrict__ E, const double* __restrict__ S, ST* __restrict__ X,
+                                    long long Mcol, int Ns) {
+    typedef typename cplx<ST>::t ST2;
+    for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < Mcol;
+         m += (long long)gridDim.x * blockDim.x) {
+        if constexpr (REAL) {
+            ST e, x;
+            if constexpr (std::is_same<ST, float>::value) {
+                e = f32_rn_from_f64(E[m]);
+                x = f32_rn_from_f64(S[m]);
+            } else {
+                e = E[m];
+                x = S[m];
+            }
+            for (int k = 0; k < Ns; ++k) {
+                x *= e;
+                X[(long long)k * Mcol + m] = x;
+            }
+        } else {
+            const ST2 x0 = cvt2<ST2>(reinterpret_cast<const double2*>(S)[m]);
+            ST2 e = c2((ST)0, (ST)0), x = x0;
+            if constexpr (ADV) e = cvt2<ST2>(reinterpret_cast<const double2*>(E)[m]);
+            else e.x = std::is_same<ST, float>::value ? (ST)f32_rn_from_f64(E[m]) : (ST)E[m];
+            ST2* X2 = reinterpret_cast<ST2*>(X);
+            for (int k = 0; k < Ns; ++k) {
+                x = ADV ? cmul(x, e) : cscale(x, e.x);
+                X2[(long long)k * Mcol + m] = x;
+            }
+        }
+    }
+}
+
 // grid: x over a slice's elements, y over the Ns slices
 __global__ void rhs_kernel(RhsArgs r) {
     const int i = blockIdx.y;
@@ -1266,6 +1302,28 @@ expd_status eigen_combine(expd_plan p, void* out, const void* const* in, const d
     a.nelem = p->Mcol << a.eshift;
     KProf kp(p, s, EXPD_K_POINTWISE, 8.0 * a.nelem * (q + (src ? 2 : 1)), 2.0 * a.nelem * q);
     combine_kernel<<<grid_for(a.nelem, 256), 256, 0, s>>>(a);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+expd_status linear_guess(expd_plan p, void* X, int x32, cudaStream_t s) {
+    const double* S = reinterpret_cast<const double*>(static_cast<const char*>(p->Sh) +
+                                                      (size_t)(p->order - 1) * p->Mcol * p->esz);
+    const int threads = 256;
+    const long long blocks = std::max(1LL, std::min<long long>((p->Mcol + threads - 1) / threads, 32LL * p->sm_count));
+    const double esz = (p->realcol ? 1.0 : 2.0) * (x32 ? 4.0 : 8.0);
+    KProf kp(p, s, EXPD_K_POINTWISE, (double)p->Mcol * (p->esz + esz * p->Ns), 2.0 * (double)p->Mcol * p->Ns);
+    if (x32) {
+        float* Xf = static_cast<float*>(X);
+        if (p->realcol) linear_guess_kernel<float, true, false><<<(int)blocks, threads, 0, s>>>(p->E, S, Xf, p->Mcol, p->Ns);
+        else if (p->adv) linear_guess_kernel<float, false, true><<<(int)blocks, threads, 0, s>>>(p->E, S, Xf, p->Mcol, p->Ns);
+        else linear_guess_kernel<float, false, false><<<(int)blocks, threads, 0, s>>>(p->E, S, Xf, p->Mcol, p->Ns);
+    } else {
+        double* Xd = static_cast<double*>(X);
+        if (p->realcol) linear_guess_kernel<double, true, false><<<(int)blocks, threads, 0, s>>>(p->E, S, Xd, p->Mcol, p->Ns);
+        else if (p->adv) linear_guess_kernel<double, false, true><<<(int)blocks, threads, 0, s>>>(p->E, S, Xd, p->Mcol, p->Ns);
+        else linear_guess_kernel<double, false, false><<<(int)blocks, threads, 0, s>>>(p->E, S, Xd, p->Mcol, p->Ns);
+    }
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }

@@ -23,6 +23,7 @@ NL_NONE, NL_ALLEN_CAHN = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 STARTUP_RAMP, STARTUP_GIVEN = 0, 1
 JAC_LAGGED, JAC_MEAN_U0 = 0, 1
+GUESS_LINEAR, GUESS_ZERO = 0, 1
 MAX_HISTORY = 128
 
 SYMBOLS = ("expd_plan_create", "expd_plan_workspace_bytes", "expd_plan_footprint_bytes", "expd_residual", "expd_precond_apply",
@@ -46,7 +47,7 @@ class Operator(C.Structure):
 
 class Scheme(C.Structure):
     _fields_ = [("order", C.c_int), ("precision", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double),
-                ("gmres_restart", C.c_int), ("startup", C.c_int), ("jacobian", C.c_int)]
+                ("gmres_restart", C.c_int), ("startup", C.c_int), ("jacobian", C.c_int), ("guess", C.c_int)]
 
 
 class Info(C.Structure):
@@ -170,6 +171,7 @@ class PlanSpec:
     startup: int = STARTUP_RAMP
     jacobian: int = 0
     b: tuple = (0.0, 0.0)
+    guess: int = GUESS_LINEAR
 
 
 def _structs(spec: PlanSpec):
@@ -180,7 +182,8 @@ def _structs(spec: PlanSpec):
         g.length[d] = float(spec.length[d])
     g.bc = spec.bc
     o = Operator(spec.a, spec.c, spec.nonlin, (C.c_double * 2)(*(tuple(spec.b) + (0.0, 0.0))[:2]))
-    s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup, spec.jacobian)
+    s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup, spec.jacobian,
+               spec.guess)
     return g, o, s
 
 
@@ -213,7 +216,8 @@ def plan_create(spec: PlanSpec, stream=None) -> "Plan":
         g.length[d] = float(spec.length[d])
     g.bc = spec.bc
     o = Operator(spec.a, spec.c, spec.nonlin, (C.c_double * 2)(*(tuple(spec.b) + (0.0, 0.0))[:2]))
-    s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup, spec.jacobian)
+    s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup, spec.jacobian,
+               spec.guess)
     h = C.c_void_p()
     _check(lib().expd_plan_create(C.byref(g), C.byref(o), spec.dt, spec.Nt, spec.alpha, C.byref(s),
                                   _stream(stream), C.byref(h)))
@@ -296,10 +300,11 @@ class Plan:
 
 
 def spec_from_problem(p, precision: int = PREC_FP64, max_iter: int = 100, tol: Optional[float] = None,
-                      gmres_restart: int = 20, startup: int = STARTUP_RAMP, jacobian: int = 0) -> PlanSpec:
+                      gmres_restart: int = 20, startup: int = STARTUP_RAMP, jacobian: int = 0,
+                      guess: int = GUESS_LINEAR) -> PlanSpec:
     """PlanSpec from a paper_2603_04350_gb300.inputs.Problem."""
     return PlanSpec(bc=BC_PERIODIC if p.bc == "periodic" else BC_DIRICHLET, n=tuple(p.n), length=tuple(p.length),
                     a=p.a, c=p.c, nonlin=NL_ALLEN_CAHN if p.nonlin == "allen_cahn" else NL_NONE, dt=p.dt,
                     Nt=p.Nt, alpha=p.alpha, order=p.order, precision=precision, max_iter=max_iter,
                     tol=p.tol if tol is None else tol, gmres_restart=gmres_restart, startup=startup,
-                    jacobian=jacobian, b=tuple(getattr(p, "b", ()) or (0.0, 0.0)))
+                    jacobian=jacobian, b=tuple(getattr(p, "b", ()) or (0.0, 0.0)), guess=guess)

@@ -129,16 +129,26 @@ def test_solve_fp_matches_sequential(expd, p, prec):
     assert O.rel_error(host(U), ref) < 1e-10, info
 
 
+GUESSES = ["linear", "zero"]
+
+
+def guess_code(expd, guess):
+    return expd.GUESS_LINEAR if guess == "linear" else expd.GUESS_ZERO
+
+
+@pytest.mark.parametrize("guess", GUESSES)
 @pytest.mark.parametrize("p", [CASES[i] for i in (0, 3, 6, 8, 9)], ids=[IDS[i] for i in (0, 3, 6, 8, 9)])
-def test_richardson_iterates_match_oracle(expd, p):
-    # per-iteration parity: the k-th iterate of the GPU fixed point equals the oracle's
+def test_richardson_iterates_match_oracle(expd, p, guess):
+    # per-iteration parity: the k-th iterate of the GPU fixed point equals the
+    # oracle's, from either initial iterate
     sp = O.spec_of(p)
     rng = np.random.default_rng(5)
     u0 = rng.uniform(-0.8, 0.8, p.n)
     for k in (1, 2, 3):
-        ref = O.richardson(sp, u0, None, max_iter=k).U[1:]
+        ref = O.richardson(sp, u0, None, max_iter=k, init=guess).U[1:]
         U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
-        with expd.plan_create(expd.spec_from_problem(p, tol=1e-300, max_iter=k)) as plan:
+        spec = expd.spec_from_problem(p, tol=1e-300, max_iter=k, guess=guess_code(expd, guess))
+        with expd.plan_create(spec) as plan:
             info = plan.solve_fp(dev(u0), None, U, allow_not_converged=True)
         assert info["iterations"] == k
         assert O.rel_error(host(U), ref) < 1e-12
@@ -225,11 +235,14 @@ def test_minimum_window_and_large_alpha(expd):
 
 
 def test_alpha_beyond_convergence_bound_reports_divergence(expd):
-    # alpha = 0.9 with E ~ 1: spectral radius alpha/(1 - alpha) = 9 > 1
+    # alpha = 0.9 with E ~ 1: spectral radius alpha/(1 - alpha) = 9 > 1.  From
+    # the zero iterate (the linear guess is already this homogeneous problem's
+    # solution, so it would stop at once)
     p = P("div", "periodic", (16,), 1, Nt=4, alpha=0.9, a=1e-4, c=0.0)
     u0 = np.random.default_rng(0).standard_normal(p.n)
     U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
-    with expd.plan_create(expd.spec_from_problem(p, tol=1e-13, max_iter=400)) as plan:
+    spec = expd.spec_from_problem(p, tol=1e-13, max_iter=400, guess=expd.GUESS_ZERO)
+    with expd.plan_create(spec) as plan:
         with pytest.raises(expd.ExpdError) as ei:
             info = plan.solve_fp(dev(u0), None, U)
         assert ei.value.status == expd.ERR_DIVERGED
@@ -468,14 +481,16 @@ NL_CASES = [c for c in CASES if c.nonlin != "none"]
 NL_IDS = [c.name for c in NL_CASES]
 
 
+@pytest.mark.parametrize("guess", GUESSES)
 @pytest.mark.parametrize("p", NL_CASES, ids=NL_IDS)
-def test_mean_jacobian_iterates_match_oracle(expd, p):
+def test_mean_jacobian_iterates_match_oracle(expd, p, guess):
     sp = O.spec_of(p)
     u0 = np.random.default_rng(17).uniform(-0.8, 0.8, p.n)
     for k in (1, 2, 3):
-        ref = O.richardson(sp, u0, None, max_iter=k, jacobian="mean_u0").U[1:]
+        ref = O.richardson(sp, u0, None, max_iter=k, jacobian="mean_u0", init=guess).U[1:]
         U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
-        spec = expd.spec_from_problem(p, tol=1e-300, max_iter=k, jacobian=expd.JAC_MEAN_U0)
+        spec = expd.spec_from_problem(p, tol=1e-300, max_iter=k, jacobian=expd.JAC_MEAN_U0,
+                                      guess=guess_code(expd, guess))
         with expd.plan_create(spec) as plan:
             info = plan.solve_fp(dev(u0), None, U, allow_not_converged=True)
         assert info["iterations"] == k
@@ -570,16 +585,18 @@ def test_advection_solvers_match_sequential(expd, p):
             assert O.rel_error(host(U), ref) < 1e-10
 
 
-def test_advection_richardson_iterates_match_oracle(expd):
+@pytest.mark.parametrize("guess", GUESSES)
+def test_advection_richardson_iterates_match_oracle(expd, guess):
     p = ADV_CASES[1]
     sp = O.spec_of(p)
     rng = np.random.default_rng(24)
     u0 = rng.uniform(-0.8, 0.8, p.n)
     f = rng.standard_normal((p.Nt,) + p.n)
     for k in (1, 2, 3):
-        ref = O.richardson(sp, u0, f, max_iter=k).U[1:]
+        ref = O.richardson(sp, u0, f, max_iter=k, init=guess).U[1:]
         U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
-        with expd.plan_create(expd.spec_from_problem(p, tol=1e-300, max_iter=k)) as plan:
+        spec = expd.spec_from_problem(p, tol=1e-300, max_iter=k, guess=guess_code(expd, guess))
+        with expd.plan_create(spec) as plan:
             plan.solve_fp(dev(u0), dev(f), U, allow_not_converged=True)
         assert O.rel_error(host(U), ref) < 1e-12
 

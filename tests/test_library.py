@@ -83,6 +83,7 @@ def test_plan_create_rejects_too_long_windows_without_touching_the_gpu(expd):
     (dict(n=(8, 8, 8)), "ndim"),
     (dict(bc=1, n=(7, 7), b=(0.5, 0.0)), "advection needs a periodic grid"),
     (dict(jacobian=5), "jacobian"),
+    (dict(guess=2), "guess"),
 ])
 def test_plan_create_rejects_bad_arguments_without_touching_the_gpu(expd, kw, msg):
     spec = _spec(expd, **kw)
