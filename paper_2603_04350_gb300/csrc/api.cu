@@ -230,15 +230,24 @@ expd_status setup_start(expd_plan p, const double* u0, const double* f, const do
                         float* F32 = nullptr, int fh_dd = 0) {
     const size_t M = (size_t)p->M;
     const int so = p->order;
+    // the mixed path transforms its data with double-float arithmetic (2^-48
+    // roundoff, far below any tolerance it is run at) on the float32 pipes
+    const bool ddt = p->precision == EXPD_PREC_MIXED;
+    auto fwd = [&](const double* x, void* y, int n) {
+        return ddt ? spatial_forward_dd64(p, x, y, n, s) : spatial_forward64(p, x, y, n, s);
+    };
+    auto inv = [&](const void* y, double* x, int n) {
+        return ddt ? spatial_inverse_dd64(p, y, x, n, s) : spatial_inverse64(p, y, x, n, s);
+    };
     EXPD_CUDA_TRY(cudaMemcpyAsync(p->startphys, u0, M * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    expd_status st = spatial_forward64(p, p->startphys, p->Sh, 1, s);
+    expd_status st = fwd(p->startphys, p->Sh, 1);
     if (st != EXPD_OK) return st;
     if (f) {
         if (!p->fh) {
             st = dalloc(p, &p->fh, (size_t)p->Nt * p->Mcol * p->esz, "source (eigen)");
             if (st != EXPD_OK) return st;
         }
-        st = spatial_forward64(p, f, p->fh, p->Nt, s);
+        st = fwd(f, p->fh, p->Nt);
         if (st != EXPD_OK) return st;
     }
     void* tmp = p->Fh;  // slice 0 of Fh is free until assemble_rhs
@@ -248,7 +257,7 @@ expd_status setup_start(expd_plan p, const double* u0, const double* f, const do
         if (p->startup == EXPD_STARTUP_GIVEN) {
             EXPD_CUDA_TRY(cudaMemcpyAsync(phys_n, Ugiven + (size_t)(n - 1) * M, M * sizeof(double),
                                           cudaMemcpyDeviceToDevice, s));
-            st = spatial_forward64(p, phys_n, eig_n, 1, s);
+            st = fwd(phys_n, eig_n, 1);
             if (st != EXPD_OK) return st;
             continue;
         }
@@ -263,12 +272,12 @@ expd_status setup_start(expd_plan p, const double* u0, const double* f, const do
         const double bdt = p->beta[n] * p->dt;
         if (p->nonlin == EXPD_NL_NONE) {
             st = eigen_combine(p, eig_n, in, coef, n, src, bdt, s);
-            if (st == EXPD_OK) st = spatial_inverse64(p, eig_n, phys_n, 1, s);
+            if (st == EXPD_OK) st = inv(eig_n, phys_n, 1);
         } else {
             st = eigen_combine(p, tmp, in, coef, n, src, bdt, s);
-            if (st == EXPD_OK) st = spatial_inverse64(p, tmp, phys_n, 1, s);
+            if (st == EXPD_OK) st = inv(tmp, phys_n, 1);
             if (st == EXPD_OK) st = pointwise_solve(p, phys_n, phys_n, (long long)M, bdt, s);
-            if (st == EXPD_OK) st = spatial_forward64(p, phys_n, eig_n, 1, s);
+            if (st == EXPD_OK) st = fwd(phys_n, eig_n, 1);
         }
         if (st != EXPD_OK) return st;
     }

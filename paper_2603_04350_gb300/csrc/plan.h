@@ -197,6 +197,10 @@ struct KProf {
 // physical [nslices][NY][NX] float64 <-> eigen [nslices][Mcol], float64.
 expd_status spatial_forward64(expd_plan p, const double* phys, void* eig, int nslices, cudaStream_t s);
 expd_status spatial_inverse64(expd_plan p, const void* eig, double* phys, int nslices, cudaStream_t s);
+// the same with double-float arithmetic (periodic grids with double-float
+// tables; otherwise the float64 transforms)
+expd_status spatial_forward_dd64(expd_plan p, const double* phys, void* eig, int nslices, cudaStream_t s);
+expd_status spatial_inverse_dd64(expd_plan p, const void* eig, double* phys, int nslices, cudaStream_t s);
 // out = transform of N(inverse transform of Uh) for the Ns unknown slices, in
 // float32 (f32 = 1, out is float2/float) or float64; Uh is float32 when in32.
 expd_status nonlinear_eval(expd_plan p, const void* Uh, void* out, int f32, cudaStream_t s, int in32 = 0);

@@ -929,8 +929,11 @@ expd_status launch_col(expd_plan p, const TIN* in, TOUT* out, int nslices, int s
     if constexpr (std::is_same<PT, dd>::value) {
         // four-step kernel (double-float, tile-staged): 16 to 256 rows (the row
         // pass stays on the radix-4 kernel: its double-float four-step variant
-        // measured slower)
-        if (!p->no_fft4) switch (NY) {
+        // measured slower).  Launches too small to give every SM a CTA of 16
+        // columns (a start-up slice) take the radix-4 kernel with one column
+        // per warp instead.
+        const long long ctas4 = ((long long)nslices * KX + 15) / 16;
+        if (!p->no_fft4 && ctas4 >= p->sm_count) switch (NY) {
             case 16: return launch_col4s<PT, TIN, TOUT, 4, 4>(p, in, out, nslices, sign, scale, s);
             case 32: return launch_col4s<PT, TIN, TOUT, 8, 4>(p, in, out, nslices, sign, scale, s);
             case 64: return launch_col4s<PT, TIN, TOUT, 8, 8>(p, in, out, nslices, sign, scale, s);
@@ -1261,6 +1264,49 @@ expd_status spatial_inverse_dd(expd_plan p, const void* eig, double* phys, int n
         } else {
             dd2* w = static_cast<dd2*>(p->work64);
             st = launch_col<dd, dd2, dd2>(p, y, w, ns, +1, dd(1.0 / p->NY), s);
+            if (st == EXPD_OK) st = launch_row<dd, dd2, double, 0>(p, w, x, (long long)ns * p->NY, sx, s);
+        }
+        if (st != EXPD_OK) return st;
+    }
+    return EXPD_OK;
+}
+
+// float64 data transformed with double-float arithmetic on the float32
+// pipes (2^-48 unit roundoff), for the start-up transforms of the mixed path
+expd_status spatial_forward_dd64(expd_plan p, const double* phys, void* eig, int nslices, cudaStream_t s) {
+    if (p->bc != EXPD_BC_PERIODIC || !p->Wxdd) return spatial_forward64(p, phys, eig, nslices, s);
+    const int chunk = p->Ns;
+    for (int b0 = 0; b0 < nslices; b0 += chunk) {
+        const int ns = std::min(chunk, nslices - b0);
+        const double* x = phys + (long long)b0 * p->M;
+        double2* y = static_cast<double2*>(eig) + (long long)b0 * p->Mcol;
+        expd_status st;
+        if (p->ndim == 1) {
+            st = launch_row<dd, double, double2, 1>(p, x, y, ns, dd(1.0), s);
+        } else {
+            dd2* w = static_cast<dd2*>(p->work64);
+            st = launch_row<dd, double, dd2, 1>(p, x, w, (long long)ns * p->NY, dd(1.0), s);
+            if (st == EXPD_OK) st = launch_col<dd, dd2, double2>(p, w, y, ns, -1, dd(1.0), s);
+        }
+        if (st != EXPD_OK) return st;
+    }
+    return EXPD_OK;
+}
+
+expd_status spatial_inverse_dd64(expd_plan p, const void* eig, double* phys, int nslices, cudaStream_t s) {
+    if (p->bc != EXPD_BC_PERIODIC || !p->Wxdd) return spatial_inverse64(p, eig, phys, nslices, s);
+    const int chunk = p->Ns;
+    const dd sx(1.0 / (p->NX / 2));
+    for (int b0 = 0; b0 < nslices; b0 += chunk) {
+        const int ns = std::min(chunk, nslices - b0);
+        double* x = phys + (long long)b0 * p->M;
+        const double2* y = static_cast<const double2*>(eig) + (long long)b0 * p->Mcol;
+        expd_status st;
+        if (p->ndim == 1) {
+            st = launch_row<dd, double2, double, 0>(p, y, x, ns, sx, s);
+        } else {
+            dd2* w = static_cast<dd2*>(p->work64);
+            st = launch_col<dd, double2, dd2>(p, y, w, ns, +1, dd(1.0 / p->NY), s);
             if (st == EXPD_OK) st = launch_row<dd, dd2, double, 0>(p, w, x, (long long)ns * p->NY, sx, s);
         }
         if (st != EXPD_OK) return st;
