@@ -119,16 +119,25 @@ EXPD_HD T2 cmul_quarter(T2 a, int sign) {
     return r;
 }
 
+// Optional shared-memory padding for 16-byte elements: element i lives at
+// i + 2 (i >> 3).  The radix-4 passes touch elements 0, 1, 8, 9, 16, 17, ...
+// from consecutive lanes; unpadded, a quarter-warp's eight 16-byte accesses
+// then fall on two bank groups (4-way conflicts), padded on eight.
+template <int PAD>
+EXPD_HD int padi(int i) { return PAD ? i + ((i >> 3) << 1) : i; }
+template <int PAD>
+EXPD_HD int padded_len(int n) { return PAD ? n + ((n >> 3) << 1) : n; }
+
 // Decimation in time: x in bit-reversed order -> X in natural order.
-template <typename T2>
+template <typename T2, int PAD = 0>
 EXPD_HD void fft_dit(T2* x, int log2n, const T2* tw, int ts, int sign, int lane, int nlanes) {
     const int n = 1 << log2n;
     int s = 0;
     if (log2n & 1) {
         for (int b = lane; b < (n >> 1); b += nlanes) {
-            const T2 u = x[2 * b], v = x[2 * b + 1];
-            x[2 * b] = cadd(u, v);
-            x[2 * b + 1] = csub(u, v);
+            const T2 u = x[padi<PAD>(2 * b)], v = x[padi<PAD>(2 * b + 1)];
+            x[padi<PAD>(2 * b)] = cadd(u, v);
+            x[padi<PAD>(2 * b + 1)] = csub(u, v);
         }
         EXPD_SYNCWARP();
         s = 1;
@@ -145,22 +154,22 @@ EXPD_HD void fft_dit(T2* x, int log2n, const T2* tw, int ts, int sign, int lane,
                 w2.y = -w2.y;
                 w4.y = -w4.y;
             }
-            const T2 x0 = x[i], x1 = cmul(x[i + h], w2);
-            const T2 x2 = x[i + 2 * h], x3 = cmul(x[i + 3 * h], w2);
+            const T2 x0 = x[padi<PAD>(i)], x1 = cmul(x[padi<PAD>(i + h)], w2);
+            const T2 x2 = x[padi<PAD>(i + 2 * h)], x3 = cmul(x[padi<PAD>(i + 3 * h)], w2);
             const T2 a0 = cadd(x0, x1), a1 = csub(x0, x1);
             const T2 a2 = cmul(cadd(x2, x3), w4);
             const T2 a3 = cmul_quarter(cmul(csub(x2, x3), w4), sign);
-            x[i] = cadd(a0, a2);
-            x[i + 2 * h] = csub(a0, a2);
-            x[i + h] = cadd(a1, a3);
-            x[i + 3 * h] = csub(a1, a3);
+            x[padi<PAD>(i)] = cadd(a0, a2);
+            x[padi<PAD>(i + 2 * h)] = csub(a0, a2);
+            x[padi<PAD>(i + h)] = cadd(a1, a3);
+            x[padi<PAD>(i + 3 * h)] = csub(a1, a3);
         }
         EXPD_SYNCWARP();
     }
 }
 
 // Decimation in frequency: x in natural order -> X in bit-reversed order.
-template <typename T2>
+template <typename T2, int PAD = 0>
 EXPD_HD void fft_dif(T2* x, int log2n, const T2* tw, int ts, int sign, int lane, int nlanes) {
     const int n = 1 << log2n;
     int s = log2n - 1;
@@ -177,22 +186,23 @@ EXPD_HD void fft_dif(T2* x, int log2n, const T2* tw, int ts, int sign, int lane,
                 w2.y = -w2.y;
                 w4.y = -w4.y;
             }
-            const T2 x0 = x[i], x1 = x[i + h], x2 = x[i + 2 * h], x3 = x[i + 3 * h];
+            const T2 x0 = x[padi<PAD>(i)], x1 = x[padi<PAD>(i + h)], x2 = x[padi<PAD>(i + 2 * h)],
+                     x3 = x[padi<PAD>(i + 3 * h)];
             const T2 a0 = cadd(x0, x2), a1 = cadd(x1, x3);
             const T2 a2 = cmul(csub(x0, x2), w4);
             const T2 a3 = cmul_quarter(cmul(csub(x1, x3), w4), sign);
-            x[i] = cadd(a0, a1);
-            x[i + h] = cmul(csub(a0, a1), w2);
-            x[i + 2 * h] = cadd(a2, a3);
-            x[i + 3 * h] = cmul(csub(a2, a3), w2);
+            x[padi<PAD>(i)] = cadd(a0, a1);
+            x[padi<PAD>(i + h)] = cmul(csub(a0, a1), w2);
+            x[padi<PAD>(i + 2 * h)] = cadd(a2, a3);
+            x[padi<PAD>(i + 3 * h)] = cmul(csub(a2, a3), w2);
         }
         EXPD_SYNCWARP();
     }
     if (s == 0) {
         for (int b = lane; b < (n >> 1); b += nlanes) {
-            const T2 u = x[2 * b], v = x[2 * b + 1];
-            x[2 * b] = cadd(u, v);
-            x[2 * b + 1] = csub(u, v);
+            const T2 u = x[padi<PAD>(2 * b)], v = x[padi<PAD>(2 * b + 1)];
+            x[padi<PAD>(2 * b)] = cadd(u, v);
+            x[padi<PAD>(2 * b + 1)] = csub(u, v);
         }
         EXPD_SYNCWARP();
     }

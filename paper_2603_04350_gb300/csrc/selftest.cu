@@ -86,6 +86,21 @@ static void test_fft(int log2n, int sign, double tol, std::mt19937_64& rng) {
     err = 0;
     for (int k = 0; k < n; ++k) err = std::max(err, std::abs(cd(buf[k].x, buf[k].y) - ref[k]));
     check("fft_dit strided table", err / scale, tol, n, sign);
+    // padded layout (element i at i + 2 (i >> 3)), both directions
+    std::vector<T2> pb((size_t)padded_len<1>(n));
+    for (int j = 0; j < n; ++j) pb[padi<1>(bitrev(j, log2n))] = to_dev<T2, T>({x[j]})[0];
+    fft_dit<T2, 1>(pb.data(), log2n, twd.data(), 1, sign, 0, 1);
+    err = 0;
+    for (int k = 0; k < n; ++k) err = std::max(err, std::abs(cd(pb[padi<1>(k)].x, pb[padi<1>(k)].y) - ref[k]));
+    check("fft_dit padded", err / scale, tol, n, sign);
+    for (int j = 0; j < n; ++j) pb[padi<1>(j)] = to_dev<T2, T>({x[j]})[0];
+    fft_dif<T2, 1>(pb.data(), log2n, twd.data(), 1, sign, 0, 1);
+    err = 0;
+    for (int k = 0; k < n; ++k) {
+        const T2 v = pb[padi<1>(bitrev(k, log2n))];
+        err = std::max(err, std::abs(cd(v.x, v.y) - ref[k]));
+    }
+    check("fft_dif padded", err / scale, tol, n, sign);
 }
 
 // Register FFTs (compile-time length R, twiddles from a table of length R*TS

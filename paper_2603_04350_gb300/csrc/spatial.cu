@@ -37,6 +37,7 @@ __global__ void row_kernel(const TIN* in, TOUT* out, long long rows, int NX,
                            int log2NH, const typename cplx<PT>::t* __restrict__ Wg, PT scale, int nonlin,
                            double* const* phys_slot) {
     typedef typename cplx<PT>::t PT2;
+    constexpr int PAD = sizeof(PT2) >= 16;  // padded rows for 16-byte elements
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // KIND 2: where to write the physical rows (read from device memory, so a
     // captured launch serves any output buffer), or nowhere
@@ -48,12 +49,12 @@ __global__ void row_kernel(const TIN* in, TOUT* out, long long rows, int NX,
     for (int i = threadIdx.x; i < KX; i += blockDim.x) W[i] = Wg[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, R = blockDim.x >> 5;
-    PT2* s = buf + (size_t)warp * NH;
+    PT2* s = buf + (size_t)warp * padded_len<PAD>(NH);
     for (long long row = (long long)blockIdx.x * R + warp; row < rows; row += (long long)gridDim.x * R) {
         if constexpr (KIND == 1) {
             const TIN* x = in + row * NX;
             for (int n = lane; n < NH; n += 32)
-                s[bitrev(n, log2NH)] = c2((PT)x[2 * n], (PT)x[2 * n + 1]);
+                s[padi<PAD>(bitrev(n, log2NH))] = c2((PT)x[2 * n], (PT)x[2 * n + 1]);
         } else {
             // Hermitian half spectrum -> packed even/odd spectrum Z = E + i O
             const TIN* X = in + row * KX;
@@ -62,16 +63,16 @@ __global__ void row_kernel(const TIN* in, TOUT* out, long long rows, int NX,
                 const PT2 xm = cconj(cvt2<PT2>(X[NH - k]));
                 const PT2 e = cscale(cadd(xk, xm), (PT)0.5);
                 const PT2 o = cmulc(cscale(csub(xk, xm), (PT)0.5), W[k]);
-                s[bitrev(k, log2NH)] = cadd(e, cmuli(o));
+                s[padi<PAD>(bitrev(k, log2NH))] = cadd(e, cmuli(o));
             }
         }
         EXPD_SYNCWARP();
-        fft_dit(s, log2NH, W, 2, KIND == 1 ? -1 : +1, lane, 32);  // natural order
+        fft_dit<PT2, PAD>(s, log2NH, W, 2, KIND == 1 ? -1 : +1, lane, 32);  // natural order
         if constexpr (KIND == 0) {
             // z_n = x_{2n} + i x_{2n+1}
             TOUT* x = out + row * NX;
             for (int n = lane; n < NH; n += 32) {
-                const PT2 z = s[n];
+                const PT2 z = s[padi<PAD>(n)];
                 x[2 * n] = (TOUT)(z.x * scale);
                 x[2 * n + 1] = (TOUT)(z.y * scale);
             }
@@ -79,17 +80,17 @@ __global__ void row_kernel(const TIN* in, TOUT* out, long long rows, int NX,
         } else {
         if constexpr (KIND == 2) {
             for (int n = lane; n < NH; n += 32) {
-                PT2 z = cscale(s[n], scale);
+                PT2 z = cscale(s[padi<PAD>(n)], scale);
                 if (phys) {  // the physical row before N, in float64 (phys[row][NX])
                     phys[row * NX + 2 * n] = (double)z.x;
                     phys[row * NX + 2 * n + 1] = (double)z.y;
                 }
                 if (nonlin == EXPD_NL_ALLEN_CAHN) z = c2(nl_ac(z.x), nl_ac(z.y));
                 else z = c2((PT)0, (PT)0);
-                s[n] = z;
+                s[padi<PAD>(n)] = z;
             }
             EXPD_SYNCWARP();
-            fft_dif(s, log2NH, W, 2, -1, lane, 32);  // bit-reversed order
+            fft_dif<PT2, PAD>(s, log2NH, W, 2, -1, lane, 32);  // bit-reversed order
         }
         // even/odd split: X_k = E_k + W^k O_k, k = 0..NH
         TOUT* X = out + row * KX;
@@ -98,8 +99,8 @@ __global__ void row_kernel(const TIN* in, TOUT* out, long long rows, int NX,
             const int k2 = (k == 0) ? 0 : NH - k;
             const int p1 = (KIND == 2) ? (int)bitrev(k1, log2NH) : k1;
             const int p2 = (KIND == 2) ? (int)bitrev(k2, log2NH) : k2;
-            const PT2 zk = s[p1];
-            const PT2 zm = cconj(s[p2]);
+            const PT2 zk = s[padi<PAD>(p1)];
+            const PT2 zm = cconj(s[padi<PAD>(p2)]);
             const PT2 e = cscale(cadd(zk, zm), (PT)0.5);
             const PT2 o = cscale(cmuli(csub(zm, zk)), (PT)0.5);
             X[k] = cvt2<TOUT>(cadd(e, cmul(W[k], o)));
@@ -867,7 +868,7 @@ expd_status launch_row_r4(expd_plan p, const TIN* in, TOUT* out, long long rows,
                           double* const* phys_slot) {
     typedef typename cplx<PT>::t PT2;
     const int NH = p->NX / 2;
-    const size_t per_row = (size_t)NH * sizeof(PT2);
+    const size_t per_row = (size_t)padded_len<(sizeof(PT2) >= 16)>(NH) * sizeof(PT2);
     int R = (int)std::max<size_t>(1, std::min<size_t>(8, (48 * 1024) / per_row));
     while (R > 1 && (rows + R - 1) / R < 2LL * p->sm_count) R >>= 1;  // small launches: more CTAs
     const size_t smem = (size_t)((NH + 2) & ~1) * sizeof(PT2) + (size_t)R * per_row;
