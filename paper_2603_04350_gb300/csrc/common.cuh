@@ -285,6 +285,32 @@ EXPD_HD void reg_fft_dif(T2 (&v)[R], const T2* tw) {
     }
 }
 
+// ---- programmatic dependent launch ----
+// Kernels of a sweep are launched so that each may start (load its constant
+// tables into shared memory) while the previous one drains; pdl_wait() then
+// blocks until the previous grid has completed and its writes are visible.
+// Without a programmatic dependency (an ordinary launch) it returns at once.
+__device__ __forceinline__ void pdl_wait() {
+#ifdef __CUDA_ARCH__
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Error checking used by every host launcher.
 #define EXPD_CUDA_TRY(expr)                                                    \
     do {                                                                       \

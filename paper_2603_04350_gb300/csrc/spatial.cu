@@ -47,6 +47,7 @@ __global__ void row_kernel(const TIN* in, TOUT* out, long long rows, int NX,
     PT2* W = reinterpret_cast<PT2*>(smem_raw);
     PT2* buf = W + ((KX + 1) & ~1);
     for (int i = threadIdx.x; i < KX; i += blockDim.x) W[i] = Wg[i];
+    pdl_wait();  // the rows come from the previous kernel
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, R = blockDim.x >> 5;
     PT2* s = buf + (size_t)warp * padded_len<PAD>(NH);
@@ -121,6 +122,7 @@ __global__ void col_kernel(const TIN* __restrict__ in, TOUT* __restrict__ out, i
     const int nw = NY >> 1;
     PT2* buf = W + ((nw + 1) & ~1);
     for (int i = threadIdx.x; i < nw; i += blockDim.x) W[i] = Wg[i];
+    pdl_wait();
     const long long base = (long long)blockIdx.y * NY * KX;
     const int kx0 = blockIdx.x * C;
     // columns are contiguous in shared memory with a padded stride, so the
@@ -240,8 +242,18 @@ __global__ void f64_to_dd_kernel(double* __restrict__ a, long long n) {
     }
 }
 
+// float32 -> double-float (exact: lo = 0), four values per thread and step
 __global__ void f32_to_dd_kernel(const float* __restrict__ in, dd* __restrict__ out, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    pdl_wait();
+    const long long n4 = n >> 2;
+    const float4* in4 = reinterpret_cast<const float4*>(in);
+    float4* out4 = reinterpret_cast<float4*>(out);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+        const float4 v = in4[i];
+        out4[2 * i] = make_float4(v.x, 0.0f, v.y, 0.0f);
+        out4[2 * i + 1] = make_float4(v.z, 0.0f, v.w, 0.0f);
+    }
+    for (long long i = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         out[i] = dd(in[i]);
 }
 
@@ -453,7 +465,14 @@ __global__ void __launch_bounds__(COL4_THREADS, fft4_min_blocks<PT>(N1)) col4_ke
     const TIN* src = in + base;  // this column; element y at src[y KX] (N KX < 2^31)
     TOUT* dst = out + base;
     const bool inv = sign > 0;
-    // ---- step 1 loads first (all in flight), then the twiddle table ----
+    // ---- the twiddle table, then (once the previous kernel is done) the
+    // step-1 loads, all in flight ----
+    for (int k = tid; k < N / 2; k += COL4_THREADS) {
+        const PT2 w = Wg[k];
+        TW[k] = w;
+        TW[k + N / 2] = c2(-w.x, -w.y);
+    }
+    pdl_wait();
     PT2 v[N1];
 #pragma unroll
     for (int j = 0; j < N1; ++j) {
@@ -461,11 +480,6 @@ __global__ void __launch_bounds__(COL4_THREADS, fft4_min_blocks<PT>(N1)) col4_ke
         if (valid) x = cvt2<PT2>(src[((int)bitrev((unsigned)j, ilog2_ct(N1)) * N2 + r) * KX]);
         if (inv) x.y = -x.y;
         v[j] = x;
-    }
-    for (int k = tid; k < N / 2; k += COL4_THREADS) {
-        const PT2 w = Wg[k];
-        TW[k] = w;
-        TW[k + N / 2] = c2(-w.x, -w.y);
     }
     __syncthreads();
     // ---- step 1: N1-point FFT over n1 (bit-reversed slots), twiddle ----
@@ -534,6 +548,7 @@ __global__ void __launch_bounds__(COL4_THREADS, fft4_min_blocks<PT>(N1)) col4s_k
         const long long sl = g / KX;
         cbase[c] = g < ncols ? sl * (long long)N * KX + (g - sl * KX) : -1;
     }
+    pdl_wait();
     __syncthreads();
     const bool inv = sign > 0;
     // ---- coalesced load: row y of C consecutive columns, all loads in flight ----
@@ -670,6 +685,7 @@ __global__ void __launch_bounds__(row4_threads(N1, N2), row4_min_blocks(N1, N2))
         TW[k] = w;
         TW[k + NH / 2] = c2(-w.x, -w.y);
     }
+    pdl_wait();
     const long long r0 = (long long)blockIdx.x * C;
     const int nr = (int)(rows - r0 < C ? rows - r0 : C);
     // ---- load the CTA's rows: one contiguous block ----
@@ -827,8 +843,8 @@ expd_status launch_row4(expd_plan p, const TIN* in, TOUT* out, long long rows, P
     const double fl = (KIND == 2 ? 2.0 : 1.0) * 2.5 * (2 * NH) * ilog2(2 * NH) * (double)rows;
     KProf kp(p, s, sizeof(PT) == 4 ? EXPD_K_FFT_ROW32 : sizeof(PT) == 8 && !std::is_same<PT, double>::value ? EXPD_K_FFT_ROWDD : EXPD_K_FFT_ROW,
              (double)rows * (in_row + out_row), fl);
-    kern<<<(int)grid, row4_threads(N1, N2), smem, s>>>(in, out, rows, Wx<PT>(p), scale, p->nonlin);
-    EXPD_CUDA_TRY(cudaGetLastError());
+    EXPD_CUDA_TRY(launch_pdl(kern, dim3((unsigned)grid), dim3(row4_threads(N1, N2)), smem, s, in, out, rows, Wx<PT>(p),
+                             scale, p->nonlin));
     return EXPD_OK;
 }
 
@@ -882,8 +898,8 @@ expd_status launch_row_r4(expd_plan p, const TIN* in, TOUT* out, long long rows,
     const double fl = (KIND == 2 ? 2.0 : 1.0) * 2.5 * p->NX * ilog2(p->NX) * (double)rows;
     KProf kp(p, s, sizeof(PT) == 4 ? EXPD_K_FFT_ROW32 : sizeof(PT) == 8 && !std::is_same<PT, double>::value ? EXPD_K_FFT_ROWDD : EXPD_K_FFT_ROW,
              (double)rows * (in_row + out_row), fl);
-    kern<<<(int)blocks, 32 * R, smem, s>>>(in, out, rows, p->NX, ilog2(NH), Wx<PT>(p), scale, p->nonlin, phys_slot);
-    EXPD_CUDA_TRY(cudaGetLastError());
+    EXPD_CUDA_TRY(launch_pdl(kern, dim3((unsigned)blocks), dim3(32 * R), smem, s, in, out, rows, p->NX, ilog2(NH),
+                             Wx<PT>(p), scale, p->nonlin, phys_slot));
     return EXPD_OK;
 }
 
@@ -900,8 +916,8 @@ expd_status launch_col4(expd_plan p, const TIN* in, TOUT* out, int nslices, int 
     const long long grid = (ncols + C - 1) / C;
     KProf kp(p, s, sizeof(PT) == 4 ? EXPD_K_FFT_COL32 : sizeof(PT) == 8 && !std::is_same<PT, double>::value ? EXPD_K_FFT_COLDD : EXPD_K_FFT_COL,
              (double)nslices * N * KX * (sizeof(TIN) + sizeof(TOUT)), 5.0 * N * ilog2(N) * (double)KX * nslices);
-    kern<<<(int)grid, COL4_THREADS, smem, s>>>(in, out, ncols, KX, Wy<PT>(p), sign, scale);
-    EXPD_CUDA_TRY(cudaGetLastError());
+    EXPD_CUDA_TRY(launch_pdl(kern, dim3((unsigned)grid), dim3(COL4_THREADS), smem, s, in, out, ncols, KX, Wy<PT>(p), sign,
+                             scale));
     return EXPD_OK;
 }
 
@@ -918,8 +934,8 @@ expd_status launch_col4s(expd_plan p, const TIN* in, TOUT* out, int nslices, int
     const long long grid = (ncols + C - 1) / C;
     KProf kp(p, s, sizeof(PT) == 4 ? EXPD_K_FFT_COL32 : sizeof(PT) == 8 && !std::is_same<PT, double>::value ? EXPD_K_FFT_COLDD : EXPD_K_FFT_COL,
              (double)nslices * N * KX * (sizeof(TIN) + sizeof(TOUT)), 5.0 * N * ilog2(N) * (double)KX * nslices);
-    kern<<<(int)grid, COL4_THREADS, smem, s>>>(in, out, ncols, KX, Wy<PT>(p), sign, scale);
-    EXPD_CUDA_TRY(cudaGetLastError());
+    EXPD_CUDA_TRY(launch_pdl(kern, dim3((unsigned)grid), dim3(COL4_THREADS), smem, s, in, out, ncols, KX, Wy<PT>(p), sign,
+                             scale));
     return EXPD_OK;
 }
 
@@ -972,8 +988,7 @@ expd_status launch_col(expd_plan p, const TIN* in, TOUT* out, int nslices, int s
     KProf kp(p, s, sizeof(PT) == 4 ? EXPD_K_FFT_COL32 : sizeof(PT) == 8 && !std::is_same<PT, double>::value ? EXPD_K_FFT_COLDD : EXPD_K_FFT_COL,
              (double)nslices * NY * KX * (sizeof(TIN) + sizeof(TOUT)),
              5.0 * NY * ilog2(NY) * (double)KX * nslices);
-    kern<<<grid, 32 * C, smem, s>>>(in, out, NY, KX, ilog2(NY), C, Wy<PT>(p), sign, scale);
-    EXPD_CUDA_TRY(cudaGetLastError());
+    EXPD_CUDA_TRY(launch_pdl(kern, grid, dim3(32 * C), smem, s, in, out, NY, KX, ilog2(NY), C, Wy<PT>(p), sign, scale));
     return EXPD_OK;
 }
 
@@ -1207,7 +1222,7 @@ expd_status convert_f64_to_dd_inplace(expd_plan p, double* a, long long n, cudaS
 
 expd_status convert_f32_to_dd(expd_plan p, const float* in, void* out, long long n, cudaStream_t s) {
     KProf kp(p, s, EXPD_K_POINTWISE, 12.0 * n, 0.0);
-    f32_to_dd_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, static_cast<dd*>(out), n);
+    EXPD_CUDA_TRY(launch_pdl(f32_to_dd_kernel, dim3(grid_for((n + 3) / 4, 256)), dim3(256), 0, s, in, static_cast<dd*>(out), n));
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }

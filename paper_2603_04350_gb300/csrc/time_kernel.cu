@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
             bp[i] = static_cast<const PT2*>(A.bplus)[i];
             bm[i] = static_cast<const PT2*>(A.bminus)[i];
         }
+    pdl_wait();
     __syncthreads();
 
     const int lane = tid & 31, warp = tid >> 5;
@@ -204,6 +205,7 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
 __global__ void __launch_bounds__(256) reduce_kernel(const double2* __restrict__ partial, int grid,
                                                      double2* __restrict__ slice_tot, double2* host_tot) {
     __shared__ double2 red[8];
+    pdl_wait();
     const int n = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double2* src = partial + (size_t)n * grid;
     double a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
@@ -277,8 +279,7 @@ expd_status launch_time(expd_plan p, TimeArgs& a, cudaStream_t s) {
                           4.0 * p->order * p->Ns;
     const int cls = sizeof(ST) == 4 ? EXPD_K_TIME32 : std::is_same<ST, dd>::value ? EXPD_K_TIMEDD : EXPD_K_TIME;
     KProf kp(p, s, cls, per * p->Ns * (double)p->Mcol, fl_col * (double)p->Mcol);
-    kern<<<p->time_grid, 32 * EXPD_TIME_COLS, smem, s>>>(a);
-    EXPD_CUDA_TRY(cudaGetLastError());
+    EXPD_CUDA_TRY(launch_pdl(kern, dim3(p->time_grid), dim3(32 * EXPD_TIME_COLS), smem, s, a));
     p->time_grid_used = p->time_grid;
     return EXPD_OK;
 }
@@ -451,7 +452,7 @@ expd_status time_reduce(expd_plan p, cudaStream_t s) {
     const int grid = p->time_grid_used > 0 ? p->time_grid_used : p->time_grid;
     KProf kp(p, s, EXPD_K_REDUCE, 16.0 * grid * p->Ns, 2.0 * grid * p->Ns);
     double2* slice_tot = reinterpret_cast<double2*>(p->redout + 8);
-    reduce_kernel<<<p->Ns, 256, 0, s>>>(p->partial, grid, slice_tot, reinterpret_cast<double2*>(p->redhost_dev));
-    EXPD_CUDA_TRY(cudaGetLastError());
+    EXPD_CUDA_TRY(launch_pdl(reduce_kernel, dim3(p->Ns), dim3(256), 0, s, (const double2*)p->partial, grid, slice_tot,
+                             reinterpret_cast<double2*>(p->redhost_dev)));
     return EXPD_OK;
 }

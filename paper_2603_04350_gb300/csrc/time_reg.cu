@@ -306,6 +306,7 @@ __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
         osc[i] = static_cast<const ST*>(A.osc)[i];
     }
     for (int i = tid; i < NW * 2 * NS; i += REG_THREADS) (&red[0][0][0])[i] = 0.0f;
+    pdl_wait();  // the iterate and N(u) come from the previous kernels
     __syncthreads();
     float accs[PER], accx[PER];
 #pragma unroll
@@ -357,8 +358,7 @@ expd_status launch_reg(expd_plan p, TimeArgs& a, cudaStream_t s) {
     // order 1 (exponential Euler) has a kernel of its own; the others share one
     auto kern = p->order == 1 ? time_reg_kernel<NS, G, ST, REAL, ADV, 1> : time_reg_kernel<NS, G, ST, REAL, ADV, 0>;
     EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
-    kern<<<(int)grid, REG_THREADS, smem, s>>>(a);
-    EXPD_CUDA_TRY(cudaGetLastError());
+    EXPD_CUDA_TRY(launch_pdl(kern, dim3((unsigned)grid), dim3(REG_THREADS), smem, s, a));
     p->time_grid_used = (int)grid;
     return EXPD_OK;
 }
