@@ -1274,12 +1274,24 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     } else {
         EXPD_CUDA_TRY(cudaMemsetAsync(p->Uh, 0, (size_t)nvec * sizeof(double), s));
     }
+    // With EXPD_DEVICE_LOOP=1 the stopping test runs on the GPU (one graph per
+    // solve, no host round trip per sweep) on a capturable stream once the
+    // plan has run a solve (its first solve sets up every kernel outside
+    // capture); otherwise the host reads the norms after every sweep.
+    const bool device_loop = !p->timing && !p->no_graphs && !p->no_device_loop && s != nullptr &&
+                             p->fp_solves > 0 && p->max_iter >= 1;
+    // The host loop's first double-float sweep reads the float32 iterate itself
+    // (exact in double-float) and writes X + s in double-float: no conversion
+    // pass.  The same values as converting first, so results do not change.
+    const bool x32_first = use_dd && !device_loop && time_reg_usable(p);
+    bool dd_first = false;  // the next double-float sweep is the first
     // leave the float32 sweeps: the iterate (exact in float32) becomes the
     // accurate phase's starting point
     auto leave32 = [&]() -> expd_status {
-        expd_status r;
+        expd_status r = EXPD_OK;
         if (use_dd) {
-            r = convert_f32_to_dd(p, static_cast<const float*>(p->U32), p->Uh, nvec, s);  // Fh is double-float already
+            if (x32_first) dd_first = true;
+            else r = convert_f32_to_dd(p, static_cast<const float*>(p->U32), p->Uh, nvec, s);  // Fh is double-float already
             phase = PHDD;
         } else {
             r = convert_f32_to_f64(p, static_cast<const float*>(p->U32), static_cast<double*>(p->Uh), nvec, s);
@@ -1307,10 +1319,12 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     }
     double* phys_out = sg.U + (size_t)(p->order - 1) * p->M;
     const bool fast_out = use_dd && nl && inverse32_accum_supported(p);
-    // the time operator of a sweep of phase ph
-    auto make_op = [&](int ph) -> TimeOp {
+    // the time operator of a sweep of phase ph (first: the first double-float
+    // sweep reading the float32 iterate)
+    auto make_op = [&](int ph, bool first = false) -> TimeOp {
         TimeOp op;
         op.X = ph == PH32 ? p->U32 : p->Uh;
+        if (first) op.X32 = p->U32;  // read; X + s goes to Uh
         op.F = ph == PH32 ? p->F32 : p->Fh;
         op.f_slices = p->f_slices;
         op.sigR = -1.0;
@@ -1325,9 +1339,9 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     };
     // one sweep: N(iterate) through the spatial transforms, the time kernel,
     // the per-slice reduction
-    auto sweep = [&](int ph) -> expd_status {
+    auto sweep = [&](int ph, bool first = false) -> expd_status {
         expd_status r = EXPD_OK;
-        TimeOp o = make_op(ph);
+        TimeOp o = make_op(ph, first);
         if (nl) {
             void* NL;
             if (ph == PH32) {
@@ -1336,7 +1350,7 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
                 o.nl_f32 = 1;
             } else if (ph == PHDD) {
                 NL = p->NL64;  // holds double-float values in this phase
-                r = nonlinear_eval_dd(p, o.X, NL, s, fast_out ? p->phys_slot : nullptr);
+                r = nonlinear_eval_dd(p, first ? o.X32 : o.X, NL, s, fast_out ? p->phys_slot : nullptr, first ? 1 : 0);
             } else {
                 NL = p->NL64;
                 r = nonlinear_eval(p, o.X, NL, 0, s, 0);
@@ -1361,12 +1375,6 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     double prev = 0.0, rho = 0.5, rho_phase = -1.0, measure = 1.0, s_first = 0.0;
     int it = 0, it32 = 0;
     expd_status result = EXPD_ERR_NOT_CONVERGED;
-    // With EXPD_DEVICE_LOOP=1 the stopping test runs on the GPU (one graph per
-    // solve, no host round trip per sweep) on a capturable stream once the
-    // plan has run a solve (its first solve sets up every kernel outside
-    // capture); otherwise the host reads the norms after every sweep.
-    const bool device_loop = !p->timing && !p->no_graphs && !p->no_device_loop && s != nullptr &&
-                             p->fp_solves > 0 && p->max_iter >= 1;
     ++p->fp_solves;
     if (device_loop) {
         const bool two = phase == PH32;
@@ -1398,8 +1406,12 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     for (it = 1; it <= p->max_iter; ++it) {
         const bool used32 = phase == PH32;
         const int ph = phase;
-        st = run_sweep(p, phase, nullptr, dshift, p->f_slices, s, [&]() { return sweep(ph); });
+        const bool first = ph == PHDD && dd_first;
+        // graphs: one per phase, the double-float sweeps after the first apart
+        st = run_sweep(p, ph == PHDD && !first ? 4 : ph, nullptr, dshift, p->f_slices, s,
+                       [&]() { return sweep(ph, first); });
         if (st != EXPD_OK) return st;
+        if (first) dd_first = false;
         phys_valid = make_op(ph).sout != nullptr;
         double nr[4];
         st = read_reduced_norms(p, s, nr);
@@ -1451,6 +1463,11 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     if (phase == PH32) {
         st = leave32();
         if (st != EXPD_OK) return st;
+    }
+    if (dd_first) {  // no double-float sweep ran: the output reads the converted iterate
+        st = convert_f32_to_dd(p, static_cast<const float*>(p->U32), p->Uh, nvec, s);
+        if (st != EXPD_OK) return st;
+        dd_first = false;
     }
     }
     if (info) {

@@ -125,7 +125,8 @@ struct expd_plan_s {
         int key_fs = 0;  // right-hand side slices baked into the time kernel's launch
         long long launches = 0;
         int eager = 0;  // sweeps launched directly (the first one sets kernel attributes)
-    } sweep_graph[4];             // [0..2] fixed-point phases, [3] sequential stepping
+    } sweep_graph[5];             // [0..2] fixed-point phases, [3] sequential stepping,
+                                  // [4] double-float sweeps after the first
     // The whole fixed point as one graph: initialisation, a device-controlled
     // loop over float32 sweeps, the conversion, a loop over accurate sweeps
     // (conditional while-nodes; the stopping test runs on the GPU).
@@ -216,7 +217,9 @@ expd_status convert_f32_to_dd(expd_plan p, const float* in, void* out, long long
 // The fixed point's initial iterate X (float32 when x32, else float64, eigen
 // layout): X_k = E^(k+1) S_{s-1}, the last start-up slice propagated by A.
 expd_status linear_guess(expd_plan p, void* X, int x32, cudaStream_t s);
-expd_status nonlinear_eval_dd(expd_plan p, const void* Uh, void* out, cudaStream_t s, double* const* phys_slot = nullptr);
+// x32: Uh is the float32 iterate (exact in double-float)
+expd_status nonlinear_eval_dd(expd_plan p, const void* Uh, void* out, cudaStream_t s, double* const* phys_slot = nullptr,
+                              int x32 = 0);
 // phys += inverse transform of a float32 half-spectrum [Ns][NY][KX] (float32
 // four-step kernels; periodic grids with NX in 32..2048, NY in 16..1024)
 bool inverse32_accum_supported(expd_plan p);
@@ -250,8 +253,12 @@ struct TimeOp {
     int f32 = 0;               // preconditioner precision (steps (a)-(c))
     int st32 = 0;              // X, F, NL, out and the residual arithmetic in float32
     int stdd = 0;              // X, F, NL, out and the residual arithmetic in double-float
+    const void* X32 = nullptr; // double-float accumulation: read the iterate from this float32 array
+                               // (exact in double-float) and write X + s to X (register kernel)
 };
 expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s);
+// The register time kernel serves this plan's window (Ns in {16, 32, 64}).
+bool time_reg_usable(expd_plan p);
 // per-slice totals of the time kernel's CTA partials into redout[8..]:
 // (||res_n||^2, ||X_n||^2) per slice n (weighted eigen norms), fixed order.
 expd_status time_reduce(expd_plan p, cudaStream_t s);

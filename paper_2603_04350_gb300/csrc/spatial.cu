@@ -1234,15 +1234,20 @@ expd_status convert_f32_to_f64(expd_plan p, const float* in, double* out, long l
     return EXPD_OK;
 }
 
-expd_status nonlinear_eval_dd(expd_plan p, const void* Uh, void* out, cudaStream_t s, double* const* phys_slot) {
+expd_status nonlinear_eval_dd(expd_plan p, const void* Uh, void* out, cudaStream_t s, double* const* phys_slot,
+                              int x32) {
     if (p->bc != EXPD_BC_PERIODIC) return expd_fail(EXPD_ERR_INVALID_ARG, "double-float N needs a periodic grid");
     const dd2* U = static_cast<const dd2*>(Uh);
+    const float2* U32 = static_cast<const float2*>(Uh);
     dd2* o = static_cast<dd2*>(out);
     const long long rows = (long long)p->Ns * p->NY;
     const dd sx(1.0 / (p->NX / 2));
-    if (p->ndim == 1) return launch_row<dd, dd2, dd2, 2>(p, U, o, rows, sx, s, phys_slot);
+    if (p->ndim == 1)
+        return x32 ? launch_row<dd, float2, dd2, 2>(p, U32, o, rows, sx, s, phys_slot)
+                   : launch_row<dd, dd2, dd2, 2>(p, U, o, rows, sx, s, phys_slot);
     dd2* w = static_cast<dd2*>(p->work64);
-    expd_status st = launch_col<dd, dd2, dd2>(p, U, w, p->Ns, +1, dd(1.0 / p->NY), s);
+    expd_status st = x32 ? launch_col<dd, float2, dd2>(p, U32, w, p->Ns, +1, dd(1.0 / p->NY), s)
+                         : launch_col<dd, dd2, dd2>(p, U, w, p->Ns, +1, dd(1.0 / p->NY), s);
     if (st == EXPD_OK) st = launch_row<dd, dd2, dd2, 2>(p, w, w, rows, sx, s, phys_slot);
     if (st == EXPD_OK) st = launch_col<dd, dd2, dd2>(p, w, o, p->Ns, -1, dd(1.0), s);
     return st;

@@ -17,6 +17,7 @@ struct TimeArgs {
     const void* NL;
     void* out;
     void* sout;  // optional float32 copy of the update (accum mode)
+    const void* X32;  // register kernel, double-float storage: the iterate read from float32 (X written)
     double dshift;  // Step (b) divisor (1 - dshift) - sum_j c_j lambda^j
     int f_slices;   // F is zero from this slice on
     int nl_f32;

@@ -411,6 +411,7 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s) {
     a.ntiles = (p->Mcol + EXPD_TIME_COLS - 1) / EXPD_TIME_COLS;
     a.partial = p->partial;
     a.sout = op.accum ? op.sout : nullptr;
+    a.X32 = op.X32;
     a.dshift = op.dshift;
     a.f_slices = op.f_slices < 0 ? p->Ns : op.f_slices;
     // power-of-two windows up to 64 with the float32 preconditioner: register kernel
@@ -419,6 +420,7 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s) {
     // its nonzero slices, 16-byte X and N elements measured 60 us against 96 us
     // for the shared-memory kernel on 256^2 x 64)
     if (reg && op.stdd) return time_reg_launch(p, a, 2, s);
+    if (op.X32) return expd_fail(EXPD_ERR_INVALID_ARG, "a float32 iterate input needs the register time kernel");
     if (reg) {
         if (op.st32) {
             if (op.NL && !op.nl_f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 storage needs float32 N");

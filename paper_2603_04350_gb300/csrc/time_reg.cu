@@ -68,9 +68,8 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // Columns of the register kernel for a fixed order ORD (1..6), or ORD = 0 for
 // the plan's order read at run time (at most 6).  ADV: complex a_j E^j
 // (advection); otherwise real.
-template <int NS, int G, typename ST, bool REAL, bool ADV, int ORD, int PER>
-__device__ __forceinline__ void reg_columns(const TimeArgs& A,
-                                            typename std::conditional<REAL, ST, typename cplx<ST>::t>::type* stage,
+template <int NS, int G, typename ST, bool REAL, bool ADV, int ORD, int PER, bool XF>
+__device__ __forceinline__ void reg_columns(const TimeArgs& A, unsigned char* stage_raw,
                                             const float2* tw, const float2* wfull, const float2* lamp, const ST* gam,
                                             const ST* osc, float (&accs)[PER], float (&accx)[PER]) {
     typedef typename cplx<ST>::t ST2;
@@ -95,7 +94,24 @@ __device__ __forceinline__ void reg_columns(const TimeArgs& A,
     // staging slots [slot][thread]: X, then N(u), then F on the slots j < RF
     // only (F is zero from slice f_slices on)
     const int RF = A.F ? min(R, (A.f_slices + G - 1) / G) : 0;
-    const int sx = 0, sn = A.X ? R : 0, sf = sn + (A.NL ? R : 0);
+    // XF: the iterate comes from A.X32 in float32 (staged as such) and X + s
+    // goes to A.X
+    typedef typename std::conditional<REAL, float, float2>::type XE32;
+    typedef typename std::conditional<XF, XE32, SE>::type XS;
+    constexpr int XSZ = (int)sizeof(XS);
+    const bool hasX = XF || A.X != nullptr;
+    XS* stage_x = reinterpret_cast<XS*>(stage_raw);
+    SE* stage = reinterpret_cast<SE*>(stage_raw + (hasX ? (size_t)R * REG_THREADS * XSZ : 0));
+    const int sn = 0, sf = sn + (A.NL ? R : 0);
+    const void* xsrc = XF ? A.X32 : A.X;
+    auto ldx = [&](int j) -> ST2 {
+        if constexpr (XF) {
+            if constexpr (REAL) return c2(ST(stage_x[j * REG_THREADS + tid]), (ST)0);
+            else return cvt2<ST2>(stage_x[j * REG_THREADS + tid]);
+        } else {
+            return ldcol<ST, REAL>(stage_x, j * REG_THREADS + tid);
+        }
+    };
     for (long long base = (long long)blockIdx.x * COLS; base < Mcol; base += (long long)gridDim.x * COLS) {
         const long long m = base + (tid / G);
         const bool valid = m < Mcol;
@@ -114,7 +130,7 @@ __device__ __forceinline__ void reg_columns(const TimeArgs& A,
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             const long long gi = (long long)(G * j + g) * Mcol + mm;
-            if (A.X) cp_async_elem<ESZ>(&stage[(sx + j) * REG_THREADS + tid], static_cast<const SE*>(A.X) + gi, valid);
+            if (hasX) cp_async_elem<XSZ>(&stage_x[j * REG_THREADS + tid], static_cast<const XS*>(xsrc) + gi, valid);
             if (A.NL) cp_async_elem<ESZ>(&stage[(sn + j) * REG_THREADS + tid], static_cast<const SE*>(A.NL) + gi, valid);
             if (j < RF)  // zero-filled beyond the right-hand side's nonzero slices
                 cp_async_elem<ESZ>(&stage[(sf + j) * REG_THREADS + tid], static_cast<const SE*>(A.F) + gi,
@@ -133,14 +149,14 @@ __device__ __forceinline__ void reg_columns(const TimeArgs& A,
 #pragma unroll
             for (int d = NWIN - 1; d >= 1; --d) xw[d] = xw[d - 1];
             xw[0] = c2((ST)0, (ST)0);
-            if (A.X) xw[0] = ldcol<ST, REAL>(stage, (sx + j) * REG_THREADS + tid);
+            if (hasX) xw[0] = ldx(j);
             if (j < RF) q = ldcol<ST, REAL>(stage, (sf + j) * REG_THREADS + tid);
             if (A.NL) {
                 const ST2 v = ldcol<ST, REAL>(stage, (sn + j) * REG_THREADS + tid);
                 q.x = fma(bdt, v.x, q.x);
                 q.y = fma(bdt, v.y, q.y);
             }
-            if (A.X) {
+            if (hasX) {
                 ST2 rx = xw[0];
 #pragma unroll
                 for (int i = 1; i <= JM; ++i) {
@@ -229,7 +245,7 @@ __device__ __forceinline__ void reg_columns(const TimeArgs& A,
             float ns = 0.0f, nx = 0.0f;
             if (valid) {
                 if (A.accum) {
-                    const ST2 xn = cadd(ldcol<ST, REAL>(stage, (sx + j) * REG_THREADS + tid), sv);
+                    const ST2 xn = cadd(ldx(j), sv);
                     stcol<ST, REAL>(const_cast<void*>(A.X), gi, xn);
                     const float2 xf = cvt2<float2>(xn);
                     nx = wgt * fmaf(xf.x, xf.x, xf.y * xf.y);
@@ -270,7 +286,7 @@ __device__ __forceinline__ void reg_columns(const TimeArgs& A,
     }
 }
 
-template <int NS, int G, typename ST, bool REAL, bool ADV, int ORD>
+template <int NS, int G, typename ST, bool REAL, bool ADV, int ORD, bool XF>
 __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
     typedef typename cplx<ST>::t ST2;
     typedef typename std::conditional<REAL, ST, ST2>::type SE;
@@ -311,8 +327,7 @@ __global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
     float accs[PER], accx[PER];
 #pragma unroll
     for (int i = 0; i < PER; ++i) accs[i] = accx[i] = 0.0f;
-    SE* stage = reinterpret_cast<SE*>(stage_raw);
-    reg_columns<NS, G, ST, REAL, ADV, ORD, PER>(A, stage, tw, wfull, lamp, gam, osc, accs, accx);
+    reg_columns<NS, G, ST, REAL, ADV, ORD, PER, XF>(A, stage_raw, tw, wfull, lamp, gam, osc, accs, accx);
     // lane (group c, residue g) holds slots j = c * PER + i of slice G j + g
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
@@ -341,22 +356,32 @@ expd_status launch_reg(expd_plan p, TimeArgs& a, cudaStream_t s) {
     a.osc = std::is_same<ST, dd>::value ? p->oscdd : ts.osc;
     a.lam = p->t32.lam;
     a.tw = p->t32.tw;
+    constexpr bool DDS = std::is_same<ST, dd>::value;
+    const bool xf = DDS && a.X32 != nullptr;  // iterate read in float32 (double-float storage only)
+    if (a.X32 && !DDS) return expd_fail(EXPD_ERR_INVALID_ARG, "a float32 iterate input needs double-float storage");
     constexpr int G = reg_lanes(NS);
     constexpr int cols = REG_THREADS / G;
     long long grid = (p->Mcol + cols - 1) / cols;
     if (grid > p->partial_cap) grid = p->partial_cap;
     const double esz = (REAL ? 1.0 : 2.0) * sizeof(ST);
+    const double xsz = xf ? (REAL ? 4.0 : 8.0) : esz;  // the iterate's element as read
+    const bool hasX = a.X != nullptr;
     const double ffrac = (double)a.f_slices / p->Ns;  // F is read only where it can be nonzero
-    const double per = (a.X ? esz : 0.0) + (a.F ? esz * ffrac : 0.0) + (a.NL ? esz : 0.0) + esz;  // N stored like X
+    const double per = (hasX ? xsz : 0.0) + (a.F ? esz * ffrac : 0.0) + (a.NL ? esz : 0.0) + esz +
+                       (a.sout ? (REAL ? 4.0 : 8.0) : 0.0);  // N stored like X
     const double fl_col = 2.0 * 5.0 * NS * ilog2(NS) + 8.0 * p->order * NS + 4.0 * p->order * NS;
-    const int cls = sizeof(ST) == 4 ? EXPD_K_TIME32 : std::is_same<ST, dd>::value ? EXPD_K_TIMEDD : EXPD_K_TIME;
+    const int cls = sizeof(ST) == 4 ? EXPD_K_TIME32 : DDS ? EXPD_K_TIMEDD : EXPD_K_TIME;
     KProf kp(p, s, cls, per * NS * (double)p->Mcol, fl_col * (double)p->Mcol);
     constexpr int R = NS / G;
     const int RF = a.F ? std::min(R, (a.f_slices + G - 1) / G) : 0;  // F slots that can be nonzero
-    const int slots = (a.X ? R : 0) + (a.NL ? R : 0) + RF;
-    const size_t smem = (size_t)std::max(slots, 1) * REG_THREADS * (size_t)esz;
+    const size_t smem = std::max<size_t>(
+        (size_t)(hasX ? R : 0) * REG_THREADS * (size_t)xsz + (size_t)((a.NL ? R : 0) + RF) * REG_THREADS * (size_t)esz,
+        (size_t)REG_THREADS * (size_t)esz);
     // order 1 (exponential Euler) has a kernel of its own; the others share one
-    auto kern = p->order == 1 ? time_reg_kernel<NS, G, ST, REAL, ADV, 1> : time_reg_kernel<NS, G, ST, REAL, ADV, 0>;
+    auto kern = p->order == 1 ? time_reg_kernel<NS, G, ST, REAL, ADV, 1, false> : time_reg_kernel<NS, G, ST, REAL, ADV, 0, false>;
+    if constexpr (DDS) {
+        if (xf) kern = p->order == 1 ? time_reg_kernel<NS, G, ST, REAL, ADV, 1, true> : time_reg_kernel<NS, G, ST, REAL, ADV, 0, true>;
+    }
     EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
     EXPD_CUDA_TRY(launch_pdl(kern, dim3((unsigned)grid), dim3(REG_THREADS), smem, s, a));
     p->time_grid_used = (int)grid;
@@ -374,6 +399,8 @@ expd_status launch_reg_ns(expd_plan p, TimeArgs& a, cudaStream_t s) {
 }
 
 }  // namespace
+
+bool time_reg_usable(expd_plan p) { return (p->Ns == 16 || p->Ns == 32 || p->Ns == 64) && !p->no_reg_time; }
 
 expd_status time_reg_launch(expd_plan p, TimeArgs& a, int st, cudaStream_t s) {
     if (st == 1)

@@ -671,8 +671,10 @@ def test_device_loop_matches_host_loop(expd, p, max_iter, prec, monkeypatch):
                 out.append((U.cpu().numpy(), info))
         runs[mode] = out
     # the device loop adds its init, per-sweep control and output launches
+    # (and converts the float32 iterate, which the host loop's first
+    # double-float sweep reads directly on register-kernel windows)
     last_h, last_d = runs["host"][-1][1], runs["device"][-1][1]
-    assert last_d["launches"] == last_h["launches"] + last_d["iterations"] + 2
+    assert last_d["launches"] - last_h["launches"] in (last_d["iterations"] + 2, last_d["iterations"] + 3)
     for (Uh, ih), (Ud, idv) in zip(runs["host"], runs["device"]):
         assert np.array_equal(Uh, Ud)
         for k in ("iterations", "fp32_iterations", "final_measure", "contraction", "history", "status"):
