@@ -30,9 +30,14 @@ using namespace expd_time;
 // lanes by shuffles.  Per-slice norms are reduced over the warp's groups with a
 // transpose-reduce and over the CTA in shared memory.
 constexpr int REG_THREADS = 128;
-// lanes per column (4: measured faster than 8 lanes with 8 slices each, whose
-// third cross-lane stage costs more than the extra occupancy gains)
-constexpr int reg_lanes(int NS) { return (void)NS, 4; }
+// Lanes per column.  float32 storage: 4 (measured faster than 8 lanes with 8
+// slices each, whose third cross-lane stage costs more than the occupancy it
+// buys).  16-byte elements (double-float, float64) with Ns = 64: 8 lanes, 80
+// registers, six CTAs per SM (the double-float sweep's time kernel 54 -> 41 us
+// on 256^2 x 64: its loads need the extra warps in flight).
+template <int NS, typename ST>
+constexpr int reg_lanes() { return (NS >= 64 && sizeof(ST) >= 8) ? 8 : 4; }
+constexpr int reg_min_blocks(int G) { return G == 8 ? 6 : 4; }
 
 __device__ __forceinline__ float2 shfl_c(float2 v, int lane) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, lane), __shfl_sync(0xffffffffu, v.y, lane));
@@ -287,7 +292,7 @@ __device__ __forceinline__ void reg_columns(const TimeArgs& A, unsigned char* st
 }
 
 template <int NS, int G, typename ST, bool REAL, bool ADV, int ORD, bool XF>
-__global__ void __launch_bounds__(REG_THREADS, 4) time_reg_kernel(TimeArgs A) {
+__global__ void __launch_bounds__(REG_THREADS, reg_min_blocks(G)) time_reg_kernel(TimeArgs A) {
     typedef typename cplx<ST>::t ST2;
     typedef typename std::conditional<REAL, ST, ST2>::type SE;
     constexpr int R = NS / G;
@@ -359,7 +364,7 @@ expd_status launch_reg(expd_plan p, TimeArgs& a, cudaStream_t s) {
     constexpr bool DDS = std::is_same<ST, dd>::value;
     const bool xf = DDS && a.X32 != nullptr;  // iterate read in float32 (double-float storage only)
     if (a.X32 && !DDS) return expd_fail(EXPD_ERR_INVALID_ARG, "a float32 iterate input needs double-float storage");
-    constexpr int G = reg_lanes(NS);
+    constexpr int G = reg_lanes<NS, ST>();
     constexpr int cols = REG_THREADS / G;
     long long grid = (p->Mcol + cols - 1) / cols;
     if (grid > p->partial_cap) grid = p->partial_cap;
