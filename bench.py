@@ -74,6 +74,10 @@ def parse_args():
     ap.add_argument("--profile-case", default=None, metavar="N,NT,PREC",
                     help="run two solves of the Allen-Cahn workload on an N x N grid with NT steps "
                          "(PREC mixed|fp64) and exit; the target of ncu captures")
+    ap.add_argument("--profile-dirichlet", default=None, metavar="N,NT",
+                    help="run two mixed GMRES solves of the Dirichlet heat workload on an N x N grid with NT "
+                         "steps (tensor-core DST) and exit; the target of ncu captures")
+    ap.add_argument("--no-dirichlet", action="store_true", help="skip the 1024^2 Dirichlet heat leg")
     return ap.parse_args()
 
 
@@ -96,6 +100,90 @@ def profile_case(spec: str) -> int:
     torch.cuda.synchronize()
     print("iterations", info["iterations"], "float32 sweeps", info["fp32_iterations"])
     return 0
+
+
+def profile_dirichlet(spec: str) -> int:
+    """Two mixed GMRES solves of the Dirichlet heat workload at another size."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2603_04350_gb300 import expd, inputs as I
+    n, nt = (int(v) for v in spec.split(","))
+    p = I.HEAT_DIRICHLET_1024.with_(n=(n, n), Nt=nt, dt=0.1 / nt)
+    u0, f = I.make_inputs(p)
+    u0d, fd = torch.from_numpy(u0).cuda(), torch.from_numpy(f).cuda()
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device="cuda")
+    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, max_iter=200)) as plan:
+        for _ in range(2):
+            info = plan.solve_gmres(u0d, fd, U)
+    torch.cuda.synchronize()
+    print("iterations", info["iterations"])
+    return 0
+
+
+def dirichlet_leg(stream, flush, barrier, check: bool) -> dict:
+    """The 1024^2 Dirichlet heat workload (s = 2, Nt = 128, GMRES, tol 1e-9):
+    the mixed path (tensor-core DST) against the float64 path (float64 dense
+    products), inputs resident, L2 flushed between solves; the tensor-core
+    kernel's rate from per-launch events."""
+    import torch
+    from paper_2603_04350_gb300 import expd, inputs as I
+    p = I.HEAT_DIRICHLET_1024
+    u0, f = I.make_inputs(p)
+    dev = flush.device
+    u0d, fd = torch.from_numpy(u0).to(dev), torch.from_numpy(f).to(dev)
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=dev)
+
+    def run(prec, K, warm, timing=False):
+        with expd.plan_create(expd.spec_from_problem(p, precision=prec, max_iter=200), stream) as pl:
+            for k in range(warm):
+                flush.fill_(float(k))
+                pl.solve_gmres(u0d, fd, U)
+            barrier()
+            pl.timing_read(reset=True)
+            pl.timing_enable(timing)
+            ms, info = [], None
+            for k in range(K):
+                flush.fill_(float(k + 1))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = pl.solve_gmres(u0d, fd, U)
+                e1.record(stream)
+                barrier()
+                ms.append(e0.elapsed_time(e1))
+            tm = pl.timing_read(reset=True)
+        return ms, info, tm
+
+    ms, info, tm_plain = run(expd.PREC_MIXED, 3, 3)
+    U_mixed = U.cpu().numpy()
+    _, _, tm = run(expd.PREC_MIXED, 1, 1, timing=True)
+    ms64, info64, _ = run(expd.PREC_FP64, 1, 1)
+    U_fp64 = U.cpu().numpy()
+    value = p.unknowns / (statistics.mean(ms) / 1e3)
+    value64 = p.unknowns / (statistics.mean(ms64) / 1e3)
+    cls = tm["classes"]
+    out = {"workload": p.name, "unknowns": p.unknowns, "tol": p.tol,
+           "mixed": {"value": value, "unit": UNIT, "ms_per_step": statistics.mean(ms), "steps": len(ms),
+                     "iterations": info["iterations"], "gpu_launches": int(tm_plain["launches"])},
+           "fp64_path": {"value": value64, "unit": UNIT, "ms_per_step": statistics.mean(ms64), "steps": len(ms64),
+                         "iterations": info64["iterations"]},
+           "speedup_vs_fp64": value / value64,
+           "kernels": {k: {"launches": v["count"], "ms_total": round(v["ms"], 4),
+                           "avg_us": round(1e3 * v["ms"] / v["count"], 3)}
+                       for k, v in cls.items() if v["count"]}}
+    c = cls.get("dst_tc")
+    if c and c["count"]:
+        peak = bf16_peak(sustained=True)
+        ach = (c["flops"] / c["count"]) / (c["ms"] / c["count"] / 1e3) / 1e12
+        out["roofline_tensor"] = {"bound": "tensor", "kernel": "dst_tc", "achieved": ach, "peak": peak[0],
+                                  "peak_source": peak[1], "unit": "TFLOP/s", "frac": ach / peak[0], "traffic": None,
+                                  "flops_per_launch": c["flops"] / c["count"],
+                                  "note": "bf16 digit products executed (pairs x 2 rows N K) per launch"}
+    if check:
+        import oracle as O
+        ref = O.sequential_solve(O.spec_of(p), u0, f)[1:]
+        out["rel_err_vs_oracle"] = {"mixed": O.rel_error(U_mixed, ref), "fp64": O.rel_error(U_fp64, ref)}
+    return out
 
 
 def dist_env():
@@ -186,6 +274,18 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def bf16_peak(sustained: bool):
+    """Dense bf16 tensor peak in TFLOP/s: the measured cuBLAS figure (sustained
+    for a kernel timed inside a long step, burst otherwise), else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)[key]), f"measured ({key})"
+    except Exception:
+        return (1700.0 if sustained else 1900.0), "fallback"
+
+
 # ------------------------------------------------------------ cpu oracle ---
 def cpu_oracle_solve(p, u0):
     """One oracle Exp-ParaDiag solve (lagged fixed point to tol): (seconds, iters, U)."""
@@ -260,6 +360,8 @@ def main():
     args = parse_args()
     if args.profile_case:
         return profile_case(args.profile_case)
+    if args.profile_dirichlet:
+        return profile_dirichlet(args.profile_dirichlet)
     if args.impl == "reference":
         args.steps = min(args.steps, 4)
         args.warmup = min(args.warmup, 1)
@@ -448,6 +550,8 @@ def main():
         out["rel_err_vs_oracle"] = {"mixed": O.rel_error(U_mixed, ref), "fp64": O.rel_error(U_fp64, ref),
                                     "gpu_sequential": O.rel_error(U_seq, ref),
                                     "mean_jacobian_variant": O.rel_error(U_nt, ref)}
+    if not args.no_dirichlet:
+        out["heat_dirichlet_1024"] = dirichlet_leg(stream, flush, barrier, rank == 0 and not args.no_check)
     if args.mix > 0:
         out["served_mix"] = served_mix(args.mix, args.mix_workers, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

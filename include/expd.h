@@ -99,7 +99,16 @@ typedef struct {
  *             float64 residual and N, and the float32 preconditioner, which
  *             converge to the float64 fixed point.  Start-up, right-hand side
  *             and output transforms are float64.  (Dirichlet grids with a
- *             nonlinearity skip the float32 sweeps.)
+ *             nonlinearity skip the float32 sweeps.)  On 2D Dirichlet grids
+ *             whose sizes are multiples of 128 up to 1024 (n + 1 not a power
+ *             of two) the mixed path's sine transforms (Sec. 3.1, the
+ *             eigenbasis of L_h) run on the tensor cores as split-bf16
+ *             products: every row cut into k 7-bit digits, the digit
+ *             products summed exactly in float32, the pairs in double-float,
+ *             k = ceil((6 - log2 tol) / 7) in 3..7, relative error about
+ *             2^(-7k); the environment variable EXPD_DST_TC=0, read at plan
+ *             creation, keeps the float64 products.  A pipeline wait of that
+ *             kernel that gives up (2 s) makes the call return EXPD_ERR_CUDA.
  *  max_iter   iteration cap of expd_solve_fp / expd_solve_gmres
  *  tol        target L^inf(0,T;L^2) relative error (Sec. 7's norm).  The
  *             fixed point stops when rho/(1-rho) * max_n||s_n|| / max_n||v_n||
@@ -291,7 +300,9 @@ enum {
     EXPD_K_TIMEDD = 10,   /* time kernel, double-float iterate (the mixed path's last sweeps) */
     EXPD_K_FFT_COLDD = 11, /* double-float spatial FFT along the strided axis                */
     EXPD_K_FFT_ROWDD = 12, /* double-float real FFT along the contiguous axis                */
-    EXPD_NUM_KCLASS = 13
+    EXPD_K_DST_TC = 13,   /* Dirichlet DST-I on the tensor cores: split-BF16 digit products   */
+    EXPD_K_DST_SPLIT = 14, /* Dirichlet DST-I on the tensor cores: rows cut into bf16 digits  */
+    EXPD_NUM_KCLASS = 15
 };
 
 typedef struct {

@@ -153,7 +153,8 @@ void free_plan(expd_plan p) {
     if (!p) return;
     void* bufs[] = {p->E,    p->C64,  p->C32, p->Cdd, p->Wxdd, p->Wydd, p->gamdd, p->oscdd, p->Wx64, p->Wx32,   p->Wy64,    p->Wy32,    p->Sx,        p->Sy, p->Dtx, p->Dty,
                     p->Uh,   p->Fh,   p->Sh,     p->fh,      p->NL64,    p->NL32,      p->work64,
-                    p->work32, p->startphys, p->partial, p->redout, p->stage, p->gm, p->U32, p->F32};
+                    p->work32, p->startphys, p->partial, p->redout, p->stage, p->gm, p->U32, p->F32,
+                    p->tc_S, p->tc_pack, p->tc_ex};
     for (void* b : bufs) plan_free(p, b);
     for (auto& g : p->sweep_graph)
         if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -314,7 +315,8 @@ expd_status write_solution(expd_plan p, double* U, cudaStream_t s, bool uh_dd = 
         EXPD_CUDA_TRY(cudaMemcpyAsync(U, p->startphys + M, (size_t)(p->order - 1) * M * sizeof(double),
                                       cudaMemcpyDeviceToDevice, s));
     if (uh_dd) return spatial_inverse_dd(p, p->Uh, U + (size_t)(p->order - 1) * M, p->Ns, s);
-    return spatial_inverse64(p, p->Uh, U + (size_t)(p->order - 1) * M, p->Ns, s);
+    const expd_status st = spatial_inverse64(p, p->Uh, U + (size_t)(p->order - 1) * M, p->Ns, s);
+    return st == EXPD_OK ? dst_tc_check(p, s) : st;
 }
 
 struct float2_pair {
@@ -506,6 +508,8 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
         auto fast = [](int n) { return n >= 3 && n + 1 <= 4096 && ((n + 1) & n) == 0; };
         p->fast_dst = fast(p->NX) && (p->ndim == 1 || fast(p->NY));
     }
+    p->tc_dst = dst_tc_eligible(p) ? 1 : 0;
+    if (p->tc_dst) dst_tc_layout(p);
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -1002,6 +1006,7 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
                 }
             st = upload_vec(p, d == 0 ? &p->Sx : &p->Sy, S, "DST matrix", s);
         }
+        if (st == EXPD_OK && p->tc_dst) st = dst_tc_setup(p, s);
     }
     // ---- state and workspace ----
     const size_t vec = (size_t)p->Ns * p->Mcol * p->esz;
@@ -1083,6 +1088,7 @@ expd_status expd_plan_footprint_bytes(const expd_grid* grid, const expd_operator
     } else {
         b += (size_t)p->NX * p->NX * 8;
         if (p->ndim == 2) b += (size_t)p->NY * p->NY * 8;
+        if (p->tc_dst) b += dst_tc_bytes(p);                                // tensor-core DST digits
     }
     b += 2 * vec + ord * Mcol * p->esz + ord * (size_t)p->M * 8;            // Uh, Fh, Sh, startphys
     b += Ns * p->NY * p->KX * 16;                                           // work64
@@ -1193,6 +1199,7 @@ expd_status expd_residual(expd_plan p, const double* u0, const double* f, const 
     st = time_apply(p, op, s);
     if (st != EXPD_OK) return st;
     st = spatial_inverse64(p, p->Fh, Rd, p->Ns, s);
+    if (st == EXPD_OK) st = dst_tc_check(p, s);
     if (st != EXPD_OK) return st;
     if (hR) {
         EXPD_CUDA_TRY(cudaMemcpyAsync(R, Rd, (size_t)p->Ns * M * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1229,6 +1236,7 @@ expd_status expd_precond_apply(expd_plan p, const double* R, double* S, void* st
     st = time_apply(p, op, s);
     if (st != EXPD_OK) return st;
     st = spatial_inverse64(p, p->Fh, Sd, p->Ns, s);
+    if (st == EXPD_OK) st = dst_tc_check(p, s);
     if (st != EXPD_OK) return st;
     if (hS) {
         EXPD_CUDA_TRY(cudaMemcpyAsync(S, Sd, bytes, cudaMemcpyDeviceToHost, s));

@@ -1,0 +1,673 @@
+// Dirichlet DST-I on the tensor cores (sm_103a: tcgen05 MMA, TMEM accumulators,
+// bulk asynchronous copies).
+//
+// Step (b) of Eq. (3.3) is diagonal in L_h's eigenbasis; on a Dirichlet grid
+// that basis is the orthonormal DST-I S (Sec. 3.1, L_h = V_h D_h V_h^{-1}), and
+// the 2D transform of a slice is Y = S_y X S_x.  For sizes whose n + 1 is not a
+// power of two it is a dense product.  Here it runs as split-BF16 products on
+// the tensor cores with an exact float32 accumulation:
+//
+//  * every row of the left operand (a data row, or a row of S) is scaled by a
+//    power of two 2^e with max|x| < 2^e and cut into k digits of 7 bits,
+//    x = 2^e sum_i d_i 2^{-7i} (balanced digits, |d_1| <= 128, |d_i| <= 64 for
+//    i > 1, rounded to nearest at the last one); every digit is an integer, so
+//    it is exact in bf16;
+//  * the product of two digit matrices over K <= 1024 is a sum of integers
+//    below 1024 * 128 * 128 = 2^24 in magnitude: the float32 accumulator of
+//    the tensor core holds it exactly;
+//  * the pairs (i, j) with i + j <= k + 1 are summed with weights 2^{-7(i+j)}
+//    in double-float (float hi + float lo) held in TMEM, then scaled by
+//    2^{e_row + e_col} and written in float64.
+//
+// The truncation leaves a relative error of about 2^{-7k} (k = 6: 2^{-42}), so
+// the transform meets tolerances far below the float32 floor; the slice count
+// follows the plan's tolerance.
+//
+// Two passes give the 2D transform: T_s = (X_s S_x)^T, then Y_s = (T_s S_y)^T.
+// Each pass is C = A B^T with A = the slice rows (K contiguous) and B = S (its
+// rows K contiguous; S is symmetric); the epilogue writes C transposed within
+// each slice, which makes its stores coalesced (consecutive TMEM lanes are
+// consecutive output addresses).
+//
+// Operand layout in global memory ("packed"): the split kernel writes every
+// 128-row x 64-K tile as the 16 KB image the MMA reads from shared memory,
+// K-major without swizzle: 8x8 core matrices of 128 contiguous bytes, the
+// core matrix of row group g and K group c at byte (8 g + c) * 128.  One bulk
+// copy moves a tile; no tensor map is needed.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <climits>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+#include "dst_digits.cuh"
+#include "plan.h"
+
+namespace {
+
+constexpr int TC_BM = 128;                          // rows per tile (TMEM lanes)
+constexpr int TC_BN = 128;                          // columns per tile
+constexpr int TC_BK = 64;                           // K per stage (bf16: 128 bytes per row)
+constexpr int TC_TILE_ELEMS = TC_BM * TC_BK;        // 8192 bf16 per operand tile
+constexpr int TC_TILE_BYTES = TC_TILE_ELEMS * 2;    // 16 KB
+constexpr int TC_STAGES = 6;
+constexpr int TC_EPI_WARPS = 8;                     // two per TMEM lane quarter, 64 columns each
+constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS); // warp 0 copies, warp 1 issues MMAs, warps 2..9 drain
+constexpr int TC_NACC = 2;                          // accumulator buffers of 128 columns
+constexpr int TC_TMEM_COLS = 512;                   // acc[0], acc[1], hi, lo: 128 columns each
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // every wait gives up after 2 s
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * 2 * TC_TILE_BYTES + 256 + 1024;
+
+// kind::f16 instruction descriptor: D float32 (bits 4-5 = 1), A and B bf16
+// (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
+// M >> 4 at bit 24.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                              ((uint32_t)(TC_BM >> 4) << 24);
+
+struct TcArgs {
+    const uint16_t* A;        // packed digit slices of the rows: [nsl][rows/128][KB][8192]
+    const uint16_t* B;        // packed digit slices of S:         [nsl][N/128][KB][8192]
+    const int* ea;            // [rows] row exponents of A
+    int eb;                   // exponent of S: max|S| < 2^eb (one for all its rows)
+    double* out;              // [rows / R][N][R]: C transposed within each slice
+    long long a_slice;        // elements per digit slice of A (rows * K)
+    long long b_slice;        // elements per digit slice of B (N * K)
+    int rows, R, N, KB;       // rows (multiple of 128), rows per slice, columns, K / 64
+    int npairs, ngroups;
+    unsigned char pi[32], pj[32];  // digit pair (i, j), 0-based, most significant first
+    // pairs gstart[q] .. gstart[q+1]-1 share one float32 accumulator (the sum of
+    // their products stays within 2^24); gw[q] = i + j of the group's pairs
+    unsigned char gstart[33], gw[32];
+    int* err;                 // set to 1 when a pipeline wait gave up
+};
+
+// ------------------------------------------------------------ PTX helpers ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Waits for the phase of the given parity; gives up after TC_WAIT_NS or when
+// another role of the CTA has given up (abort != 0, unless ignore_abort).
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort, bool ignore_abort = false) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 0) {
+            if (!ignore_abort && *abort) return false;
+            if (globaltimer() - t0 > TC_WAIT_NS) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_alloc(uint32_t slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// the mbarrier arrives once every MMA this thread issued so far has completed
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// D (TMEM, 128 lanes x 128 float32 columns) (+)= A (128 x 16) B^T (16 x 128)
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(acc)
+        : "memory");
+}
+
+
+// acc, hi and lo: three 32-column loads of this warp's 32 lanes, then the wait
+__device__ __forceinline__ void tm_ld3(uint32_t ta, uint32_t th, uint32_t tl, uint32_t (&a)[32], uint32_t (&h)[32],
+                                       uint32_t (&l)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%96];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%97];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%64, %65, %66, %67, %68, %69, %70, %71, %72, %73, %74, %75, %76, %77, %78, %79, %80, %81, %82, %83, %84, %85, %86, %87, %88, %89, %90, %91, %92, %93, %94, %95}, [%98];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(a[16]), "=r"(a[17]), "=r"(a[18]), "=r"(a[19]), "=r"(a[20]), "=r"(a[21]), "=r"(a[22]), "=r"(a[23]), "=r"(a[24]), "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), "=r"(a[28]), "=r"(a[29]), "=r"(a[30]), "=r"(a[31]), "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]), "=r"(h[7]), "=r"(h[8]), "=r"(h[9]), "=r"(h[10]), "=r"(h[11]), "=r"(h[12]), "=r"(h[13]), "=r"(h[14]), "=r"(h[15]), "=r"(h[16]), "=r"(h[17]), "=r"(h[18]), "=r"(h[19]), "=r"(h[20]), "=r"(h[21]), "=r"(h[22]), "=r"(h[23]), "=r"(h[24]), "=r"(h[25]), "=r"(h[26]), "=r"(h[27]), "=r"(h[28]), "=r"(h[29]), "=r"(h[30]), "=r"(h[31]), "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]), "=r"(l[6]), "=r"(l[7]), "=r"(l[8]), "=r"(l[9]), "=r"(l[10]), "=r"(l[11]), "=r"(l[12]), "=r"(l[13]), "=r"(l[14]), "=r"(l[15]), "=r"(l[16]), "=r"(l[17]), "=r"(l[18]), "=r"(l[19]), "=r"(l[20]), "=r"(l[21]), "=r"(l[22]), "=r"(l[23]), "=r"(l[24]), "=r"(l[25]), "=r"(l[26]), "=r"(l[27]), "=r"(l[28]), "=r"(l[29]), "=r"(l[30]), "=r"(l[31])
+        : "r"(ta), "r"(th), "r"(tl)
+        : "memory");
+}
+
+// hi and lo only
+__device__ __forceinline__ void tm_ld2(uint32_t th, uint32_t tl, uint32_t (&h)[32], uint32_t (&l)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%64];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%65];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]), "=r"(h[7]), "=r"(h[8]), "=r"(h[9]), "=r"(h[10]), "=r"(h[11]), "=r"(h[12]), "=r"(h[13]), "=r"(h[14]), "=r"(h[15]), "=r"(h[16]), "=r"(h[17]), "=r"(h[18]), "=r"(h[19]), "=r"(h[20]), "=r"(h[21]), "=r"(h[22]), "=r"(h[23]), "=r"(h[24]), "=r"(h[25]), "=r"(h[26]), "=r"(h[27]), "=r"(h[28]), "=r"(h[29]), "=r"(h[30]), "=r"(h[31]), "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]), "=r"(l[6]), "=r"(l[7]), "=r"(l[8]), "=r"(l[9]), "=r"(l[10]), "=r"(l[11]), "=r"(l[12]), "=r"(l[13]), "=r"(l[14]), "=r"(l[15]), "=r"(l[16]), "=r"(l[17]), "=r"(l[18]), "=r"(l[19]), "=r"(l[20]), "=r"(l[21]), "=r"(l[22]), "=r"(l[23]), "=r"(l[24]), "=r"(l[25]), "=r"(l[26]), "=r"(l[27]), "=r"(l[28]), "=r"(l[29]), "=r"(l[30]), "=r"(l[31])
+        : "r"(th), "r"(tl)
+        : "memory");
+}
+
+// one 32-column load
+__device__ __forceinline__ void tm_ld1(uint32_t ta, uint32_t (&a)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(a[16]), "=r"(a[17]), "=r"(a[18]), "=r"(a[19]), "=r"(a[20]), "=r"(a[21]), "=r"(a[22]), "=r"(a[23]), "=r"(a[24]), "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), "=r"(a[28]), "=r"(a[29]), "=r"(a[30]), "=r"(a[31])
+        : "r"(ta)
+        : "memory");
+}
+
+// hi and lo back to their 32 columns, then the wait
+__device__ __forceinline__ void tm_st2(uint32_t th, uint32_t tl, const uint32_t (&h)[32], const uint32_t (&l)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%1], {%34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63, %64, %65};\n\t"
+        "tcgen05.wait::st.sync.aligned;"
+        :
+        : "r"(th), "r"(tl), "r"(h[0]), "r"(h[1]), "r"(h[2]), "r"(h[3]), "r"(h[4]), "r"(h[5]), "r"(h[6]), "r"(h[7]), "r"(h[8]), "r"(h[9]), "r"(h[10]), "r"(h[11]), "r"(h[12]), "r"(h[13]), "r"(h[14]), "r"(h[15]), "r"(h[16]), "r"(h[17]), "r"(h[18]), "r"(h[19]), "r"(h[20]), "r"(h[21]), "r"(h[22]), "r"(h[23]), "r"(h[24]), "r"(h[25]), "r"(h[26]), "r"(h[27]), "r"(h[28]), "r"(h[29]), "r"(h[30]), "r"(h[31]), "r"(l[0]), "r"(l[1]), "r"(l[2]), "r"(l[3]), "r"(l[4]), "r"(l[5]), "r"(l[6]), "r"(l[7]), "r"(l[8]), "r"(l[9]), "r"(l[10]), "r"(l[11]), "r"(l[12]), "r"(l[13]), "r"(l[14]), "r"(l[15]), "r"(l[16]), "r"(l[17]), "r"(l[18]), "r"(l[19]), "r"(l[20]), "r"(l[21]), "r"(l[22]), "r"(l[23]), "r"(l[24]), "r"(l[25]), "r"(l[26]), "r"(l[27]), "r"(l[28]), "r"(l[29]), "r"(l[30]), "r"(l[31])
+        : "memory");
+}
+
+// ------------------------------------------------------------ split rows ----
+// float value of a small integer d (|d| < 2^22) without the conversion unit:
+// 1.5 * 2^23 + d has d in its low mantissa bits
+__device__ __forceinline__ uint32_t bf16_of_int(int d) {
+    return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
+}
+
+// One warp per row of K float64 values (K a multiple of 64, rows of a 128-row
+// tile consecutive): the row exponent e (max|x| < 2^e, or fixed_e for every
+// row unless it is INT_MIN) into ex[r] (when ex is given), and the
+// nsl balanced 7-bit digits of x 2^{-e} into the packed slices, digit 0 the
+// most significant.  All arithmetic is on the binary64 encoding (integer
+// operations); a row holding a non-finite value gets NaN digits.
+__global__ void __launch_bounds__(256) split_rows_kernel(const double* __restrict__ in, long long rows, int K,
+                                                         int nsl, uint16_t* __restrict__ out, long long slice_elems,
+                                                         int* __restrict__ ex, int fixed_e) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long r = (long long)blockIdx.x * 8 + warp;
+    if (r >= rows) return;
+    const double2* x = reinterpret_cast<const double2*>(in + r * K);
+    const int nch = K >> 3;  // chunks of 8 values (16 bytes of bf16 per digit slice)
+    unsigned long long mx = 0;
+    for (int c = lane; c < nch; c += 32) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const double2 v = __ldg(x + 4 * c + h);
+            mx = max(mx, (unsigned long long)__double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFull);
+            mx = max(mx, (unsigned long long)__double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFull);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const bool bad = (mx >> 52) == 2047;
+    // max|x| < 2^e (fixed_e: one exponent given for every row, at least the row's)
+    const int e = fixed_e != INT_MIN ? fixed_e : digit_row_exponent(mx);
+    if (lane == 0 && ex) ex[r] = bad ? 0 : e;
+    const int KB = K >> 6;
+    for (int c = lane; c < nch; c += 32) {
+        unsigned long long Y[8];
+        unsigned neg = 0;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const double2 v = __ldg(x + 4 * c + h);
+            unsigned n0, n1;
+            Y[2 * h] = digit_magnitude((unsigned long long)__double_as_longlong(v.x), e, nsl, &n0);
+            Y[2 * h + 1] = digit_magnitude((unsigned long long)__double_as_longlong(v.y), e, nsl, &n1);
+            neg |= (n0 << (2 * h)) | (n1 << (2 * h + 1));
+        }
+        // the 8 values' 16 bytes of each digit slice (same 8x8 core matrix row)
+        uint16_t* o = out + packed_offset(r, 8 * c, KB);
+        for (int i = nsl - 1; i >= 0; --i) {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                int d = digit_next(&Y[t], i);
+                if ((neg >> t) & 1u) d = -d;
+                const uint32_t hb = bad ? 0x7FC0u : bf16_of_int(d);
+                w[t >> 1] |= hb << (16 * (t & 1));
+            }
+            *reinterpret_cast<uint4*>(o + (long long)i * slice_elems) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// f 2^E as a float64 from the float's encoding (integer operations); false
+// when f is zero, subnormal, non-finite or the result leaves the normal range
+__device__ __forceinline__ bool f32_scaled_to_f64(float f, int E, double* out) {
+    const uint32_t u = __float_as_uint(f);
+    const int ex = (int)((u >> 23) & 0xFFu);
+    if (ex == 0 || ex == 255) return false;
+    const int ne = ex - 127 + 1023 + E;
+    if (ne < 1 || ne > 2046) return false;
+    *out = __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) | ((unsigned long long)ne << 52) |
+                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+    return true;
+}
+
+// zeros, non-finite values, range edges
+__device__ __noinline__ double scaled_sum_edge(float hi, float lo, int E) { return ldexp((double)hi + (double)lo, E); }
+
+// (hi + lo) 2^E rounded once to float64: both terms scaled exactly, one add
+__device__ __forceinline__ double scaled_sum(float hi, float lo, int E) {
+    double dh, dl;
+    const bool okh = f32_scaled_to_f64(hi, E, &dh) || hi == 0.0f;
+    const bool okl = f32_scaled_to_f64(lo, E, &dl) || lo == 0.0f;
+    if (okh && okl) return (hi == 0.0f ? 0.0 : dh) + (lo == 0.0f ? 0.0 : dl);
+    return scaled_sum_edge(hi, lo, E);
+}
+
+// ---------------------------------------------------------- MMA kernel ----
+// Persistent: each CTA takes tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// (column tile fastest, so the CTAs running together share their A tiles in
+// L2).  Per tile and digit pair, K / 64 stages of one A and one B tile flow
+// through a TC_STAGES-deep ring: warp 0 (one lane) issues their bulk copies,
+// warp 1 (one lane) the four K = 16 MMAs per stage into accumulator buffer
+// group % 2 (a group: digit pairs of one weight whose products sum exactly in
+// float32), and warps 2..9 drain the finished buffer into the double-float sum
+// in TMEM while the next group accumulates.  After a tile's last group the
+// drain warps write the float64 result.
+__global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_constant__ TcArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                         ~static_cast<uintptr_t>(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (size_t)TC_STAGES * 2 * TC_TILE_BYTES);
+    // full[s], empty[s], accf[b], acce[b], drain
+    const uint32_t bar0 = smem_u32(bars);
+    auto full = [&](int s) { return bar0 + 8u * (uint32_t)s; };
+    auto empty = [&](int s) { return bar0 + 8u * (uint32_t)(TC_STAGES + s); };
+    auto accf = [&](int b) { return bar0 + 8u * (uint32_t)(2 * TC_STAGES + b); };
+    auto acce = [&](int b) { return bar0 + 8u * (uint32_t)(2 * TC_STAGES + TC_NACC + b); };
+    const uint32_t drain = bar0 + 8u * (uint32_t)(2 * TC_STAGES + 2 * TC_NACC);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 2 * TC_NACC + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        for (int b = 0; b < TC_NACC; ++b) {
+            mbar_init(accf(b), 1);
+            mbar_init(acce(b), TC_EPI_WARPS);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        tc_alloc(smem_u32(tmem_slot), TC_TMEM_COLS);
+        tc_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int nct = a.N / TC_BN;
+    const long long ntiles = (long long)(a.rows / TC_BM) * nct;
+    const int KB = a.KB;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- copies ----
+            uint32_t it = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const long long rt = t / nct;
+                const int ct = (int)(t - rt * nct);
+                for (int p = 0; p < a.npairs && ok; ++p) {
+                    const uint16_t* Ab = a.A + a.pi[p] * a.a_slice + rt * KB * TC_TILE_ELEMS;
+                    const uint16_t* Bb = a.B + a.pj[p] * a.b_slice + (long long)ct * KB * TC_TILE_ELEMS;
+                    for (int kb = 0; kb < KB; ++kb, ++it) {
+                        const int s = (int)(it % TC_STAGES);
+                        const uint32_t ph = (it / TC_STAGES) & 1u;
+                        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        unsigned char* st = sm + (size_t)s * 2 * TC_TILE_BYTES;
+                        mbar_arrive_expect_tx(full(s), 2 * TC_TILE_BYTES);
+                        bulk_g2s(smem_u32(st), Ab + (long long)kb * TC_TILE_ELEMS, TC_TILE_BYTES, full(s));
+                        bulk_g2s(smem_u32(st + TC_TILE_BYTES), Bb + (long long)kb * TC_TILE_ELEMS, TC_TILE_BYTES,
+                                 full(s));
+                    }
+                }
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                atomicExch(a.err, 1);
+            }
+            // copies still in flight land before the CTA leaves: the last one
+            // issued into each stage completes that stage's phase
+            for (uint32_t q = it > (uint32_t)TC_STAGES ? it - TC_STAGES : 0u; q < it; ++q)
+                mbar_wait(full((int)(q % TC_STAGES)), (q / TC_STAGES) & 1u, abort_flag, true);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMAs ----
+            uint32_t it = 0, pc = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int g = 0; g < a.ngroups && ok; ++g, ++pc) {
+                    const int b = (int)(pc % TC_NACC);
+                    if (!mbar_wait(acce(b), ((pc / TC_NACC) & 1u) ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)(b * TC_BN);
+                    for (int p = a.gstart[g]; p < a.gstart[g + 1] && ok; ++p) {
+                        const bool first = p == a.gstart[g];
+                        for (int kb = 0; kb < KB; ++kb, ++it) {
+                            const int s = (int)(it % TC_STAGES);
+                            if (!mbar_wait(full(s), (it / TC_STAGES) & 1u, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t sa = smem_u32(sm + (size_t)s * 2 * TC_TILE_BYTES);
+                            const uint32_t sb = sa + TC_TILE_BYTES;
+#pragma unroll
+                            for (int q = 0; q < TC_BK / 16; ++q)  // 16 bf16 of K = two core matrices = 256 bytes
+                                tc_mma(d, smem_desc(sa + 256u * q), smem_desc(sb + 256u * q),
+                                       !first || (kb | q) != 0);
+                            tc_commit(empty(s));
+                        }
+                    }
+                    if (ok) tc_commit(accf(b));
+                }
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                atomicExch(a.err, 1);
+            }
+            // every MMA issued has completed before TMEM is released
+            tc_commit(drain);
+            mbar_wait(drain, 0u, abort_flag, true);
+        }
+    } else {
+        // ---- drain and output (warps 2..9): TMEM lane quarter warp % 4, columns
+        // 64 (warp - 2) / 4 .. +63; the double-float sums in TMEM columns 256..511 ----
+        const int lq = warp & 3, half = (warp - 2) >> 2;
+        const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(half * 64);
+        const uint32_t thi = tl + 2u * TC_BN, tlo = tl + 3u * TC_BN;
+        uint32_t pc = 0;
+        bool ok = true;
+        for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const long long rt = t / nct;
+            const int ct = (int)(t - rt * nct);
+            for (int g = 0; g < a.ngroups && ok; ++g, ++pc) {
+                const int b = (int)(pc % TC_NACC);
+                // every lane waits; the warp goes on only together (the TMEM
+                // loads and stores below are warp-collective)
+                if (!__all_sync(0xffffffffu, mbar_wait(accf(b), (pc / TC_NACC) & 1u, abort_flag))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                // weight 2^{-7(i+j+2)} of the group's pairs (digits are 0-based)
+                const float wsc = __int_as_float((127 - 7 * (a.gw[g] + 2)) << 23);
+                const uint32_t tacc = tl + (uint32_t)(b * TC_BN);
+#pragma unroll 1
+                for (int c = 0; c < 2; ++c) {
+                    uint32_t v[32], h[32], l[32];
+                    if (g == 0) {
+                        tm_ld1(tacc + 32u * c, v);
+                    } else {
+                        tm_ld3(tacc + 32u * c, thi + 32u * c, tlo + 32u * c, v, h, l);
+                    }
+                    if (c == 1) {  // the accumulator buffer is free for the group after next
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(acce(b));
+                    }
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const float w = __fmul_rn(__uint_as_float(v[e]), wsc);  // exact: a power of two
+                        if (g == 0) {
+                            h[e] = __float_as_uint(w);
+                            l[e] = 0u;
+                        } else {
+                            // (hi, lo) += w: two-sum, error into lo, renormalise
+                            const float hi = __uint_as_float(h[e]), lo = __uint_as_float(l[e]);
+                            const float sm_ = __fadd_rn(hi, w);
+                            const float bb = __fsub_rn(sm_, hi);
+                            const float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(sm_, bb)), __fsub_rn(w, bb));
+                            const float l1 = __fadd_rn(lo, er);
+                            const float h1 = __fadd_rn(sm_, l1);
+                            h[e] = __float_as_uint(h1);
+                            l[e] = __float_as_uint(__fsub_rn(l1, __fsub_rn(h1, sm_)));
+                        }
+                    }
+                    tm_st2(thi + 32u * c, tlo + 32u * c, h, l);
+                }
+            }
+            if (!ok) break;
+            // ---- output: C[row][col] = (hi + lo) 2^{ea[row] + eb}, transposed within the slice ----
+            const long long row = rt * TC_BM + lq * 32 + lane;
+            const long long slc = row / a.R;
+            const int rin = (int)(row - slc * a.R);
+            const int E = a.ea[row] + a.eb;
+            double* o = a.out + slc * (long long)a.R * a.N + (long long)(ct * TC_BN + half * 64) * a.R + rin;
+#pragma unroll 1
+            for (int c = 0; c < 2; ++c) {
+                uint32_t h[32], l[32];
+                tm_ld2(thi + 32u * c, tlo + 32u * c, h, l);
+#pragma unroll
+                for (int e = 0; e < 32; ++e)
+                    o[(long long)(32 * c + e) * a.R] = scaled_sum(__uint_as_float(h[e]), __uint_as_float(l[e]), E);
+            }
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicExch(a.err, 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        tc_dealloc(tmem, TC_TMEM_COLS);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host ----
+namespace {
+
+expd_status tc_dalloc(expd_plan p, void** ptr, size_t bytes, const char* what) {
+    *ptr = nullptr;
+    cudaError_t e = plan_malloc(p, ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return expd_fail(EXPD_ERR_OOM, std::string("cudaMalloc failed for ") + what + " (" + std::to_string(bytes) +
+                                           " bytes): " + cudaGetErrorString(e));
+    }
+    p->bytes += bytes;
+    return EXPD_OK;
+}
+
+expd_status split_rows(expd_plan p, const double* in, long long rows, int K, uint16_t* out, long long slice_elems,
+                       int* ex, int fixed_e, cudaStream_t s) {
+    const int nsl = p->tc_nsl;
+    KProf kp(p, s, EXPD_K_DST_SPLIT, (double)rows * K * (8.0 + 2.0 * nsl) + 4.0 * rows, 0.0);
+    split_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(in, rows, K, nsl, out, slice_elems, ex, fixed_e);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+// out (transposed within slices of R rows) = A B^T over the plan's digit pairs
+expd_status mma_pass(expd_plan p, const uint16_t* A, const int* ea, long long rows, int R, const uint16_t* B,
+                     int eb, int N, int K, double* out, cudaStream_t s) {
+    TcArgs a = {};
+    a.A = A;
+    a.B = B;
+    a.ea = ea;
+    a.eb = eb;
+    a.out = out;
+    a.a_slice = rows * K;
+    a.b_slice = (long long)N * K;
+    a.rows = (int)rows;
+    a.R = R;
+    a.N = N;
+    a.KB = K / TC_BK;
+    const int nsl = p->tc_nsl;
+    int np = 0, ng = 0;
+    tc_groups(nsl, K, &np, &ng, a.pi, a.pj, a.gstart, a.gw);
+    a.npairs = np;
+    a.ngroups = ng;
+    a.err = p->tc_err;
+    const long long ntiles = (rows / TC_BM) * (N / TC_BN);
+    const int grid = (int)std::min<long long>(ntiles, (long long)p->sm_count);
+    EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel, TC_SMEM));
+    KProf kp(p, s, EXPD_K_DST_TC, 2.0 * nsl * ((double)rows * K + (double)N * K) + 8.0 * rows * N,
+             2.0 * np * (double)rows * N * K);
+    dst_mma_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>(a);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+// smallest e with sqrt(2 / (n + 1)) < 2^e: a bound on every entry of the
+// orthonormal DST-I matrix of size n
+int dst_exponent(int n) {
+    int e;
+    frexp(std::sqrt(2.0 / (n + 1)), &e);  // 2^(e-1) <= v < 2^e
+    return e;
+}
+
+int tc_slices_for(double tol) {
+    // digits of 7 bits; the transform's relative error is about 2^{-7 k}
+    // times a small factor, kept 2^6 below the tolerance
+    const double bits = -std::log2(std::max(tol, 1e-30)) + 6.0;
+    return std::min(7, std::max(3, (int)std::ceil(bits / 7.0)));
+}
+
+}  // namespace
+
+bool dst_tc_eligible(expd_plan p) {
+    if (p->bc != EXPD_BC_DIRICHLET || p->fast_dst || p->ndim != 2 || p->precision != EXPD_PREC_MIXED) return false;
+    const char* env = getenv("EXPD_DST_TC");
+    if (env && strcmp(env, "0") == 0) return false;
+    auto ok = [](int n) { return n % TC_BM == 0 && n <= 1024; };
+    return ok(p->NX) && ok(p->NY);
+}
+
+void dst_tc_layout(expd_plan p) {
+    p->tc_nsl = tc_slices_for(p->tol);
+    const double per_slice = (double)p->tc_nsl * p->M * 2.0;
+    p->tc_chunk = (int)std::max(1.0, std::min((double)p->Ns, std::floor(2147483648.0 / per_slice)));
+}
+
+size_t dst_tc_bytes(expd_plan p) {
+    const size_t nx = p->NX, ny = p->NY, nsl = p->tc_nsl;
+    return nsl * (nx * nx + ny * ny) * 2 + (nx + ny) * 4 + nsl * (size_t)p->tc_chunk * p->M * 2 +
+           (size_t)p->tc_chunk * std::max(nx, ny) * 4 + 256;
+}
+
+expd_status dst_tc_setup(expd_plan p, cudaStream_t s) {
+    const int NX = p->NX, NY = p->NY, nsl = p->tc_nsl;
+    expd_status st = tc_dalloc(p, reinterpret_cast<void**>(&p->tc_S), (size_t)nsl * ((size_t)NX * NX + (size_t)NY * NY) * 2,
+                               "DST digit slices");
+    if (st == EXPD_OK)
+        st = tc_dalloc(p, reinterpret_cast<void**>(&p->tc_pack), (size_t)nsl * p->tc_chunk * p->M * 2, "digit slices");
+    if (st == EXPD_OK)
+        st = tc_dalloc(p, reinterpret_cast<void**>(&p->tc_ex),
+                       ((size_t)NX + NY + (size_t)p->tc_chunk * std::max(NX, NY)) * 4 + 256, "digit exponents");
+    if (st != EXPD_OK) return st;
+    p->tc_err = p->tc_ex + NX + NY + (size_t)p->tc_chunk * std::max(NX, NY);
+    EXPD_CUDA_TRY(cudaMemsetAsync(p->tc_err, 0, sizeof(int), s));
+    // digits of S_x and S_y with one exponent per matrix: |S| <= sqrt(2/(n+1)) < 2^e
+    p->tc_eSx = dst_exponent(NX);
+    p->tc_eSy = dst_exponent(NY);
+    st = split_rows(p, p->Sx, NX, NX, p->tc_S, (long long)NX * NX, nullptr, p->tc_eSx, s);
+    if (st == EXPD_OK)
+        st = split_rows(p, p->Sy, NY, NY, p->tc_S + (size_t)nsl * NX * NX, (long long)NY * NY, nullptr, p->tc_eSy, s);
+    if (st != EXPD_OK) return st;
+    EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+    return EXPD_OK;
+}
+
+// Y[s] = S_y X[s] S_x for ns slices [NY][NX]; tmp holds tc_chunk slices.
+expd_status dst2_tc(expd_plan p, const double* X, double* Y, int ns, double* tmp, cudaStream_t s) {
+    const int NX = p->NX, NY = p->NY, nsl = p->tc_nsl;
+    const long long M = p->M;
+    const uint16_t* Sxd = p->tc_S;
+    const uint16_t* Syd = p->tc_S + (size_t)nsl * NX * NX;
+    int* exA = p->tc_ex + NX + NY;
+    for (int b0 = 0; b0 < ns; b0 += p->tc_chunk) {
+        const int cs = std::min(p->tc_chunk, ns - b0);
+        const double* x = X + (long long)b0 * M;
+        double* y = Y + (long long)b0 * M;
+        // pass 1: rows of X (cs*NY rows of NX), T[s] = (X[s] S_x)^T, [NX][NY]
+        const long long r1 = (long long)cs * NY;
+        expd_status st = split_rows(p, x, r1, NX, p->tc_pack, r1 * NX, exA, INT_MIN, s);
+        if (st == EXPD_OK) st = mma_pass(p, p->tc_pack, exA, r1, NY, Sxd, p->tc_eSx, NX, NX, tmp, s);
+        // pass 2: rows of T (cs*NX rows of NY), Y[s] = (T[s] S_y)^T, [NY][NX]
+        const long long r2 = (long long)cs * NX;
+        if (st == EXPD_OK) st = split_rows(p, tmp, r2, NY, p->tc_pack, r2 * NY, exA, INT_MIN, s);
+        if (st == EXPD_OK) st = mma_pass(p, p->tc_pack, exA, r2, NX, Syd, p->tc_eSy, NY, NY, y, s);
+        if (st != EXPD_OK) return st;
+    }
+    return EXPD_OK;
+}
+
+// Reports (and clears) a pipeline wait of the tensor-core kernel that gave up.
+expd_status dst_tc_check(expd_plan p, cudaStream_t s) {
+    if (!p->tc_dst || !p->tc_err) return EXPD_OK;
+    int h = 0;
+    EXPD_CUDA_TRY(cudaMemcpyAsync(&h, p->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) {
+        EXPD_CUDA_TRY(cudaMemsetAsync(p->tc_err, 0, sizeof(int), s));
+        return expd_fail(EXPD_ERR_CUDA, "tensor-core DST: a pipeline wait gave up after 2 s (results invalid)");
+    }
+    return EXPD_OK;
+}

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stddef.h>
+#include <stdint.h>
 
 #include <string>
 #include <vector>
@@ -90,6 +91,15 @@ struct expd_plan_s {
     int fast_dst = 0;          // Dirichlet with n + 1 a power of two: FFT-based sine transforms
     double2* Dtx = nullptr;    // fast DST twiddles exp(-2 pi i k / (2 (NX + 1))), k <= NX
     double2* Dty = nullptr;    // the same for NY
+    // Dirichlet dense sizes on the mixed path: split-BF16 tensor-core products
+    int tc_dst = 0;            // the dense DST runs on the tensor cores (dst_tc.cu)
+    int tc_nsl = 0;            // 7-bit digits per value
+    int tc_chunk = 0;          // slices transformed per pass
+    int tc_eSx = 0, tc_eSy = 0;  // exponents of the S_x and S_y digits (|S| < 2^e)
+    uint16_t* tc_S = nullptr;  // packed digit slices of S_x then S_y
+    uint16_t* tc_pack = nullptr;  // packed digit slices of the rows being transformed
+    int* tc_ex = nullptr;      // row exponents: [NX + NY] unused, rows [tc_chunk * max(NX, NY)]
+    int* tc_err = nullptr;     // set by the kernel when a pipeline wait gave up
     TimeTables t64, t32;
 
     // ---- state --------------------------------------------------------------
@@ -235,6 +245,18 @@ expd_status eigen_combine(expd_plan p, void* out, const void* const* in, const d
 expd_status sum_squares(expd_plan p, const double* x, long long n, double* out_dev, double* scratch, cudaStream_t s);
 // F32 (optional): also the float32 copy; fh_dd: Fh stored as double-float pairs
 expd_status assemble_rhs(expd_plan p, const void* fh, cudaStream_t s, float* F32 = nullptr, int fh_dd = 0);
+
+// ---- tensor-core DST (dst_tc.cu) ----------------------------------------------
+// The mixed path on a 2D Dirichlet grid with both sizes multiples of 128 up to
+// 1024 (and n + 1 not a power of two) transforms with split-BF16 products on
+// the tensor cores; EXPD_DST_TC=0 keeps the float64 products.
+bool dst_tc_eligible(expd_plan p);
+void dst_tc_layout(expd_plan p);     // digit count (from tol) and slices per pass
+size_t dst_tc_bytes(expd_plan p);    // device bytes dst_tc_setup allocates
+expd_status dst_tc_setup(expd_plan p, cudaStream_t s);  // needs Sx, Sy on the device
+// Y[s] = S_y X[s] S_x, ns slices; tmp holds tc_chunk slices of M doubles
+expd_status dst2_tc(expd_plan p, const double* X, double* Y, int ns, double* tmp, cudaStream_t s);
+expd_status dst_tc_check(expd_plan p, cudaStream_t s);
 
 // ---- time direction (time_kernel.cu) -----------------------------------------
 struct TimeOp {

@@ -4,14 +4,17 @@
 // O(n^2) DFTs.  Exit status 0 on success.  Not part of libexpd.
 #include <math.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <complex>
 #include <random>
 #include <vector>
 
 #include "common.cuh"
 #include "dd.cuh"
+#include "dst_digits.cuh"
 #include "time_column.cuh"
 
 typedef std::complex<double> cd;
@@ -269,10 +272,159 @@ static void test_dd_complex(std::mt19937_64& rng) {
     check("reg_fft_dit double-float", e / sc, 1e-13, R, -1);
 }
 
+// ---- tensor-core DST: digits, packed operands, MMA descriptors ----------------
+static uint16_t bf16_bits_of_int(int d) {
+    const float f = (float)d;  // |d| <= 128: exact, and exact in bf16
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return (uint16_t)(u >> 16);
+}
+static double bf16_value(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+static unsigned long long bits_of(double v) {
+    unsigned long long b;
+    memcpy(&b, &v, 8);
+    return b;
+}
+
+// the split kernel, row by row: exponents and packed digit slices
+static void split_host(const std::vector<double>& x, long long rows, int K, int nsl, std::vector<uint16_t>& pack,
+                       std::vector<int>& ex, int fixed_e) {
+    pack.assign((size_t)nsl * rows * K, 0);
+    ex.assign((size_t)rows, 0);
+    for (long long r = 0; r < rows; ++r) {
+        unsigned long long mx = 0;
+        for (int k = 0; k < K; ++k) mx = std::max(mx, bits_of(x[r * K + k]) & 0x7FFFFFFFFFFFFFFFull);
+        const int e = fixed_e != INT_MIN ? fixed_e : digit_row_exponent(mx);
+        if (fixed_e != INT_MIN && mx >= bits_of(ldexp(1.0, e))) ++failures;  // the given exponent must bound the row
+        ex[r] = e;
+        for (int k = 0; k < K; ++k) {
+            unsigned neg;
+            unsigned long long Y = digit_magnitude(bits_of(x[r * K + k]), e, nsl, &neg);
+            for (int i = nsl - 1; i >= 0; --i) {
+                int d = digit_next(&Y, i);
+                if (i == 0 && (d < 0 || d > 128)) ++failures;
+                if (i > 0 && (d < -64 || d > 63)) ++failures;
+                if (neg) d = -d;
+                pack[(size_t)i * rows * K + packed_offset(r, k, K / 64)] = bf16_bits_of_int(d);
+            }
+        }
+    }
+}
+
+// One M = N = 128, K = 16 MMA with K-major operands, reading shared memory the
+// way the descriptor fields say: element (m, k) at start + (m / 8) SBO +
+// (m % 8) 16 + (k / 8) LBO + 2 (k % 8).
+static void mma_emulate(const uint8_t* smem, uint64_t adesc, uint64_t bdesc, std::vector<double>& D, bool acc) {
+    auto elem = [&](uint64_t desc, int m, int k) {
+        const size_t start = (size_t)(desc & 0x3FFF) << 4, lbo = (size_t)((desc >> 16) & 0x3FFF) << 4,
+                     sbo = (size_t)((desc >> 32) & 0x3FFF) << 4;
+        uint16_t h;
+        memcpy(&h, smem + start + (m / 8) * sbo + (m % 8) * 16 + (k / 8) * lbo + 2 * (k % 8), 2);
+        return bf16_value(h);
+    };
+    if (((adesc >> 46) & 7) != 1 || ((bdesc >> 46) & 7) != 1 || (adesc >> 61) != 0) ++failures;
+    for (int m = 0; m < 128; ++m)
+        for (int n = 0; n < 128; ++n) {
+            double s = acc ? D[m * 128 + n] : 0.0;
+            for (int k = 0; k < 16; ++k) s += elem(adesc, m, k) * elem(bdesc, n, k);
+            D[m * 128 + n] = s;
+        }
+}
+
+// One pass of the tensor-core DST as the kernel schedules it: out (transposed
+// within slices of R rows) = A B^T over the digit pairs i + j < nsl, B's
+// digits with the one exponent eB, the pairs summed group by group.
+static void tc_pass_host(const std::vector<double>& A, long long rows, int R, const std::vector<double>& B, int N, int K,
+                         int nsl, int eB, std::vector<double>& out) {
+    std::vector<uint16_t> pa, pb;
+    std::vector<int> ea, eb;
+    split_host(A, rows, K, nsl, pa, ea, INT_MIN);
+    split_host(B, N, K, nsl, pb, eb, eB);
+    int np = 0, ng = 0;
+    unsigned char pi[32], pj[32], gstart[33], gw[32];
+    tc_groups(nsl, K, &np, &ng, pi, pj, gstart, gw);
+    if (np != nsl * (nsl + 1) / 2) ++failures;
+    const int KB = K / 64;
+    std::vector<uint8_t> smem(2 * 16384);
+    std::vector<double> D(128 * 128), hi(128 * 128);
+    out.assign((size_t)rows * N, 0.0);
+    for (long long rt = 0; rt < rows / 128; ++rt)
+        for (int ct = 0; ct < N / 128; ++ct) {
+            for (int q = 0; q < ng; ++q) {
+                for (int k = gstart[q]; k < gstart[q + 1]; ++k) {
+                    const int i = pi[k], j = pj[k];
+                    if (i + j != gw[q]) ++failures;
+                    for (int kb = 0; kb < KB; ++kb) {
+                        memcpy(smem.data(), pa.data() + (size_t)i * rows * K + ((size_t)rt * KB + kb) * 8192, 16384);
+                        memcpy(smem.data() + 16384, pb.data() + (size_t)j * N * K + ((size_t)ct * KB + kb) * 8192,
+                               16384);
+                        for (int c = 0; c < 4; ++c)
+                            mma_emulate(smem.data(), smem_desc(256u * c), smem_desc(16384u + 256u * c), D,
+                                        k != gstart[q] || (kb | c) != 0);
+                    }
+                }
+                for (int t = 0; t < 128 * 128; ++t) {
+                    if (std::fabs(D[t]) > 16777216.0) ++failures;  // float32 accumulation must stay exact
+                    const double w = ldexp(D[t], -7 * (gw[q] + 2));
+                    hi[t] = q == 0 ? w : hi[t] + w;
+                }
+            }
+            for (int m = 0; m < 128; ++m)
+                for (int n = 0; n < 128; ++n) {
+                    const long long row = rt * 128 + m, col = (long long)ct * 128 + n;
+                    const long long sl = row / R, rin = row % R;
+                    out[(size_t)(sl * R * N + col * R + rin)] = ldexp(hi[m * 128 + n], ea[row] + eB);
+                }
+        }
+}
+
+static void test_tc_dst(std::mt19937_64& rng) {
+    const int NY = 256, NX = 128, ns = 2, nsl = 5;
+    auto dst = [](int n) {
+        std::vector<double> S((size_t)n * n);
+        for (int j = 0; j < n; ++j)
+            for (int k = 0; k < n; ++k) S[(size_t)j * n + k] = sqrt(2.0 / (n + 1)) * sin(M_PI * (j + 1.0) * (k + 1.0) / (n + 1));
+        return S;
+    };
+    const std::vector<double> Sx = dst(NX), Sy = dst(NY);
+    std::normal_distribution<double> N01;
+    std::vector<double> X((size_t)ns * NY * NX);
+    for (size_t t = 0; t < X.size(); ++t) X[t] = N01(rng) * ((t % 7) == 0 ? 1e3 : 1.0);  // uneven row scales
+    std::vector<double> T, Y;
+    auto ebound = [](int n) {  // the exponent the library gives the DST digits
+        int e;
+        frexp(sqrt(2.0 / (n + 1)), &e);
+        return e;
+    };
+    tc_pass_host(X, (long long)ns * NY, NY, Sx, NX, NX, nsl, ebound(NX), T);   // T[s] = (X[s] S_x)^T
+    tc_pass_host(T, (long long)ns * NX, NX, Sy, NY, NY, nsl, ebound(NY), Y);   // Y[s] = (T[s] S_y)^T = S_y X[s] S_x
+    double e2 = 0, r2 = 0;
+    for (int s = 0; s < ns; ++s)
+        for (int y = 0; y < NY; ++y)
+            for (int x = 0; x < NX; ++x) {
+                double ref = 0;
+                for (int a = 0; a < NY; ++a) {
+                    double t = 0;
+                    for (int b = 0; b < NX; ++b) t += X[((size_t)s * NY + a) * NX + b] * Sx[(size_t)b * NX + x];
+                    ref += Sy[(size_t)y * NY + a] * t;
+                }
+                const double d = Y[((size_t)s * NY + y) * NX + x] - ref;
+                e2 += d * d;
+                r2 += ref * ref;
+            }
+    check("tensor-core DST (digits, packing, descriptors)", sqrt(e2 / r2), 1e-9, NY, NX);
+}
+
 int main() {
     std::mt19937_64 rng(1234);
     test_conversions(rng);
     test_dd_complex(rng);
+    test_tc_dst(rng);
     for (int l = 1; l <= 12; ++l)
         for (int sign = -1; sign <= 1; sign += 2) {
             test_fft<double, double2>(l, sign, 1e-13, rng);

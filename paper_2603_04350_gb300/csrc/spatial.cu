@@ -1086,7 +1086,8 @@ expd_status transpose(expd_plan p, const double* in, double* out, int R, int C, 
 
 // Orthonormal 2D DST-I: Y = Sy X Sx (S symmetric and its own inverse).  With
 // n + 1 a power of two in every direction: fast sine transforms along x, a
-// transpose, along y, and back; otherwise the dense products.
+// transpose, along y, and back; otherwise the dense products (on the tensor
+// cores when the plan allows, dst_tc.cu).
 expd_status dst2(expd_plan p, const double* X, double* Y, int ns, double* tmp, cudaStream_t s) {
     const int NX = p->NX, NY = p->NY;
     if (p->fast_dst) {
@@ -1099,6 +1100,7 @@ expd_status dst2(expd_plan p, const double* X, double* Y, int ns, double* tmp, c
         if (st == EXPD_OK) st = transpose(p, w1, Y, NX, NY, ns, s);
         return st;
     }
+    if (p->tc_dst) return dst2_tc(p, X, Y, ns, tmp, s);
     if (p->ndim == 1) return dgemm(p, X, NX, (long long)NX, p->Sx, NX, 0, Y, NX, 0, ns, NX, NX, 1, s);
     expd_status st = dgemm(p, X, NX, (long long)NX, p->Sx, NX, 0, tmp, NX, 0, ns * NY, NX, NX, 1, s);
     if (st != EXPD_OK) return st;

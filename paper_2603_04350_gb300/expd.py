@@ -31,10 +31,10 @@ SYMBOLS = ("expd_plan_create", "expd_plan_workspace_bytes", "expd_plan_footprint
            "expd_precond_apply_noalloc",
            "expd_status_string", "expd_last_error", "expd_version")
 (K_TIME, K_FFT_COL, K_FFT_ROW, K_DST, K_GMRES, K_POINTWISE, K_REDUCE, K_TIME32, K_FFT_COL32, K_FFT_ROW32,
- K_TIMEDD, K_FFT_COLDD, K_FFT_ROWDD) = range(13)
-NUM_KCLASS = 13
+ K_TIMEDD, K_FFT_COLDD, K_FFT_ROWDD, K_DST_TC, K_DST_SPLIT) = range(15)
+NUM_KCLASS = 15
 KCLASS_NAMES = ("time", "fft_col", "fft_row", "dst", "gmres", "pointwise", "reduce", "time32", "fft_col32",
-                "fft_row32", "timedd", "fft_coldd", "fft_rowdd")
+                "fft_row32", "timedd", "fft_coldd", "fft_rowdd", "dst_tc", "dst_split")
 
 
 class Grid(C.Structure):

@@ -1,0 +1,130 @@
+"""Tensor-core DST-I (split-BF16 digit products, tcgen05) vs the CPU oracle, through the C ABI (marked gpu).
+
+The mixed path transforms Dirichlet grids whose sizes are multiples of 128 (up
+to 1024, n + 1 not a power of two) with exact float32 sums of bf16 digit
+products; its error is about 2^(-7k) for k digits (k from the plan's
+tolerance), so results are held to 1e-9 relative here (the float64 path's bar
+is 1e-11; the transform with tol 1e-10 keeps 6 digits, about 2^-42 per digit
+product, summed over up to 1024 terms and two passes).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2603_04350_gb300 import inputs as I
+
+from .test_gpu_parity import DEV, P, dev, host, relmax
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def expd():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2603_04350_gb300 import expd as E
+    return E
+
+
+# rectangular (slow axis 256, fast axis 128: a swapped axis would show), both
+# multiples of 128, several 128-row tiles per slice and a slice count that
+# leaves a ragged last wave of tiles
+TC_CASES = [
+    P("tc_d2d_s1", "dirichlet", (256, 128), 1, Nt=9),
+    P("tc_d2d_s2", "dirichlet", (128, 256), 2, Nt=10),
+    P("tc_d2d_s6", "dirichlet", (128, 128), 6, Nt=13),
+    P("tc_d2d_ac_s1", "dirichlet", (128, 256), 1, nonlin="allen_cahn", a=0.01, c=0.0, dt=1e-3, Nt=12, alpha=1e-3),
+]
+TC_IDS = [p.name for p in TC_CASES]
+
+
+def _counts(plan):
+    return plan.timing_read(reset=True)["classes"]
+
+
+@pytest.mark.parametrize("p", TC_CASES, ids=TC_IDS)
+def test_tc_residual_matches_oracle(expd, p):
+    # the residual of a mixed plan is float64 arithmetic around the two
+    # transforms, so its error is the transforms' error
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(13)
+    amp = 0.5 if p.nonlin != "none" else 1.0
+    u0 = amp * rng.uniform(-1, 1, p.n)
+    U = amp * rng.uniform(-1, 1, (p.Nt,) + p.n)
+    f = rng.standard_normal((p.Nt,) + p.n)
+    U_start = np.concatenate([u0[None], U[: p.order - 1]])
+    ref = O.residual(sp, U[p.order - 1:], O.rhs_known(sp, U_start, f))
+    R = torch.empty((p.Ns,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-10)) as plan:
+        plan.timing_enable(True)
+        plan.residual(dev(u0), dev(f), dev(U), R)
+        cls = _counts(plan)
+    assert cls["dst_tc"]["count"] > 0 and cls["dst"]["count"] == 0, cls
+    assert relmax(host(R), ref) < 1e-9
+
+
+@pytest.mark.parametrize("p", TC_CASES, ids=TC_IDS)
+def test_tc_solve_matches_sequential(expd, p):
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(14)
+    u0 = rng.uniform(-0.8, 0.8, p.n)
+    f = rng.standard_normal((p.Nt,) + p.n) if p.nonlin == "none" else None
+    ref = O.sequential_solve(sp, u0, f)[1:]
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-10, max_iter=200)) as plan:
+        info = plan.solve_fp(dev(u0), None if f is None else dev(f), U)
+    assert O.rel_error(host(U), ref) < 1e-9, info
+    if p.nonlin == "none":
+        U2 = torch.empty_like(U)
+        with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-10)) as plan:
+            info = plan.solve_gmres(dev(u0), dev(f), U2)
+        assert O.rel_error(host(U2), ref) < 1e-9, info
+
+
+def test_tc_agrees_with_float64_products(expd, monkeypatch):
+    # the same mixed solve with the float64 dense products (EXPD_DST_TC=0)
+    p = TC_CASES[1]
+    rng = np.random.default_rng(15)
+    u0 = rng.uniform(-0.8, 0.8, p.n)
+    f = rng.standard_normal((p.Nt,) + p.n)
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("EXPD_DST_TC", mode)
+        U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+        with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-11)) as plan:
+            plan.timing_enable(True)
+            plan.solve_gmres(dev(u0), dev(f), U)
+            cls = _counts(plan)
+        assert (cls["dst_tc"]["count"] > 0) == (mode == "1"), cls
+        out[mode] = host(U)
+    assert O.rel_error(out["1"], out["0"]) < 1e-9
+
+
+def test_tc_deterministic(expd):
+    p = TC_CASES[0]
+    rng = np.random.default_rng(16)
+    u0 = rng.uniform(-1, 1, p.n)
+    f = rng.standard_normal((p.Nt,) + p.n)
+    res = []
+    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-10)) as plan:
+        for _ in range(2):
+            U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+            plan.solve_fp(dev(u0), dev(f), U)
+            res.append(host(U))
+    assert np.array_equal(res[0], res[1])
+
+
+def test_tc_heat_dirichlet_1024_full_mixed_gmres(expd):
+    # the 1024^2 Dirichlet heat workload (s = 2, Nt = 128, GMRES, tol 1e-9) on
+    # the mixed path: every spatial transform on the tensor cores
+    p = I.HEAT_DIRICHLET_1024
+    u0, f = I.make_inputs(p)
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, max_iter=200)) as plan:
+        plan.timing_enable(True)
+        info = plan.solve_gmres(dev(u0), dev(f), U)
+        cls = _counts(plan)
+    assert cls["dst_tc"]["count"] > 0 and cls["dst"]["count"] == 0, cls
+    ref = O.sequential_solve(O.spec_of(p), u0, f)[1:]
+    assert O.rel_error(host(U), ref) < p.tol, info
