@@ -198,6 +198,47 @@ static void test_column(int Ns, int order, double E, double alpha, double tol, s
         err = std::max(err, std::abs(s - sref[n]));
     }
     check(sizeof(T) == 8 ? "precond_column double" : "precond_column float", err / scale, tol, Ns, order);
+
+    // two real columns (this one's real part with E, a second with E2) packed
+    // into one complex column, against two single-column solves
+    std::vector<double> q1(Ns), q2(Ns);
+    for (int n = 0; n < Ns; ++n) {
+        q1[n] = N01(rng);
+        q2[n] = N01(rng);
+    }
+    const double E2 = 0.5 * E + 0.1;
+    T cj2[7] = {0};
+    double Ej2 = 1.0;
+    for (int j = 1; j <= order; ++j) {
+        Ej2 *= E2;
+        cj2[j] = (T)(bdf[order][j] * Ej2);
+    }
+    auto single = [&](const std::vector<double>& qq, const T* c) {
+        std::vector<cd> ww(t.L, 0.0);
+        for (int n = 0; n < Ns; ++n) ww[t.bluestein ? n : bitrev(n, t.log2L)] = t.gamma[n] * qq[n];
+        std::vector<T2> wv = to_dev<T2, T>(ww);
+        const double s1 = precond_column<T, T2>(wv.data(), Ns, t.L, t.log2L, t.bluestein, twd.data(), lamd.data(),
+                                                t.bluestein ? chd.data() : nullptr, t.bluestein ? bpd.data() : nullptr,
+                                                t.bluestein ? bmd.data() : nullptr, c, order, 0, 1);
+        std::vector<double> out(Ns);
+        for (int n = 0; n < Ns; ++n) out[n] = (double)wv[t.bluestein ? n : bitrev(n, t.log2L)].x * s1 / t.gamma[n];
+        return out;
+    };
+    const std::vector<double> r1 = single(q1, cjT), r2 = single(q2, cj2);
+    std::vector<cd> wp(t.L, 0.0);
+    for (int n = 0; n < Ns; ++n) wp[t.bluestein ? n : bitrev(n, t.log2L)] = t.gamma[n] * cd(q1[n], q2[n]);
+    std::vector<T2> wpd = to_dev<T2, T>(wp);
+    const double sp = precond_column_pair<T, T2>(wpd.data(), Ns, t.L, t.log2L, t.bluestein, twd.data(), lamd.data(),
+                                                 t.bluestein ? chd.data() : nullptr, t.bluestein ? bpd.data() : nullptr,
+                                                 t.bluestein ? bmd.data() : nullptr, cjT, cj2, order, 0, 1);
+    double perr = 0, pscale = 0;
+    for (int n = 0; n < Ns; ++n) {
+        const T2 v = wpd[t.bluestein ? n : bitrev(n, t.log2L)];
+        perr = std::max(perr, std::max(std::fabs((double)v.x * sp / t.gamma[n] - r1[n]),
+                                       std::fabs((double)v.y * sp / t.gamma[n] - r2[n])));
+        pscale = std::max(pscale, std::max(std::fabs(r1[n]), std::fabs(r2[n])));
+    }
+    check(sizeof(T) == 8 ? "precond_column_pair double" : "precond_column_pair float", perr / pscale, tol, Ns, order);
 }
 
 // The integer-path conversions against the hardware ones: round to nearest

@@ -15,10 +15,10 @@
 
 #include "common.cuh"
 
-template <typename PT, typename PT2, typename CJ>
-EXPD_HD double precond_column(PT2* w, int Ns, int L, int log2L, int bluestein, const PT2* tw, const PT2* lam,
-                              const PT2* chirp, const PT2* bp, const PT2* bm, const CJ* cj, int order,
-                              int lane, int nlanes, PT one = (PT)1) {
+// Step (a): on exit w[k] holds Y_k (radix-2) or L Y_k (Bluestein), natural order.
+template <typename PT, typename PT2>
+EXPD_HD void precond_step_a(PT2* w, int Ns, int L, int log2L, int bluestein, const PT2* tw, const PT2* chirp,
+                            const PT2* bp, int lane, int nlanes) {
     if (bluestein) {
         for (int n = lane; n < Ns; n += nlanes) w[n] = cmul(w[n], chirp[n]);
         for (int n = Ns + lane; n < L; n += nlanes) w[n] = c2((PT)0, (PT)0);
@@ -34,27 +34,29 @@ EXPD_HD double precond_column(PT2* w, int Ns, int L, int log2L, int bluestein, c
     } else {
         fft_dit(w, log2L, tw, 1, +1, lane, nlanes);  // natural Y_k
     }
-    // Step (b): Z_k = Y_k / d_k, d_k = 1 - sum_j cj[j] lambda_k^j (Horner,
-    // unrolled over the at most six coefficients so they stay in registers)
-    CJ cp[7];
+}
+
+// d_k = one - sum_{j=1..order} cp[j] lambda_k^j (Horner, unrolled over the at
+// most six coefficients so they stay in registers)
+template <typename PT, typename PT2, typename CJ>
+EXPD_HD PT2 precond_divisor(PT2 lk, const CJ* cp, int order, PT one) {
+    PT2 acc = c2((PT)0, (PT)0);
 #pragma unroll
-    for (int j = 1; j <= 6; ++j) cp[j] = j <= order ? cj[j] : coef_zero<CJ>();
-    for (int k = lane; k < Ns; k += nlanes) {
-        const PT2 lk = lam[k];
-        PT2 acc = c2((PT)0, (PT)0);
-#pragma unroll
-        for (int j = 6; j >= 1; --j) {
-            if (j <= order) {
-                acc = cmul(lk, acc);
-                acc = acc_add(acc, cp[j]);
-            }
+    for (int j = 6; j >= 1; --j) {
+        if (j <= order) {
+            acc = cmul(lk, acc);
+            acc = acc_add(acc, cp[j]);
         }
-        acc = cmul(lk, acc);
-        const PT2 d = c2(one - acc.x, -acc.y);
-        PT2 z = cdiv(w[k], d);
-        if (bluestein) z = cmulc(z, chirp[k]);
-        w[k] = z;
     }
+    acc = cmul(lk, acc);
+    return c2(one - acc.x, -acc.y);
+}
+
+// Step (c) from Z_k in natural order (Bluestein: already times conj(c_k));
+// returns the output scale.
+template <typename PT, typename PT2>
+EXPD_HD double precond_step_c(PT2* w, int Ns, int L, int log2L, int bluestein, const PT2* tw, const PT2* chirp,
+                              const PT2* bm, int lane, int nlanes) {
     if (bluestein)
         for (int k = Ns + lane; k < L; k += nlanes) w[k] = c2((PT)0, (PT)0);
     EXPD_SYNCWARP();
@@ -67,6 +69,62 @@ EXPD_HD double precond_column(PT2* w, int Ns, int L, int log2L, int bluestein, c
     for (int n = lane; n < Ns; n += nlanes) w[n] = cmulc(w[n], chirp[n]);
     EXPD_SYNCWARP();
     return 1.0 / ((double)L * (double)L * (double)Ns);
+}
+
+template <typename PT, typename PT2, typename CJ>
+EXPD_HD double precond_column(PT2* w, int Ns, int L, int log2L, int bluestein, const PT2* tw, const PT2* lam,
+                              const PT2* chirp, const PT2* bp, const PT2* bm, const CJ* cj, int order,
+                              int lane, int nlanes, PT one = (PT)1) {
+    precond_step_a<PT, PT2>(w, Ns, L, log2L, bluestein, tw, chirp, bp, lane, nlanes);
+    // Step (b): Z_k = Y_k / d_k
+    CJ cp[7];
+#pragma unroll
+    for (int j = 1; j <= 6; ++j) cp[j] = j <= order ? cj[j] : coef_zero<CJ>();
+    for (int k = lane; k < Ns; k += nlanes) {
+        const PT2 d = precond_divisor<PT, PT2, CJ>(lam[k], cp, order, one);
+        PT2 z = cdiv(w[k], d);
+        if (bluestein) z = cmulc(z, chirp[k]);
+        w[k] = z;
+    }
+    return precond_step_c<PT, PT2>(w, Ns, L, log2L, bluestein, tw, chirp, bm, lane, nlanes);
+}
+
+// The same solve for two real columns at once (real coefficients cj1, cj2):
+// on entry w holds y1_n + i y2_n at position pos(n), on exit v1_n + i v2_n.
+// The DFT of a real sequence is conjugate-symmetric (Y_{Ns-k} = conj(Y_k)),
+// and so is d_k for real coefficients (lambda_{Ns-k} = conj(lambda_k)), so
+// with W = DFT(y1 + i y2): Y1_k = (W_k + conj(W_{Ns-k})) / 2,
+// Y2_k = (W_k - conj(W_{Ns-k})) / 2i, and Z1 + i Z2 goes into step (c).  One
+// lane handles k and Ns - k together.  Two columns for the FFT work of one.
+template <typename PT, typename PT2>
+EXPD_HD double precond_column_pair(PT2* w, int Ns, int L, int log2L, int bluestein, const PT2* tw, const PT2* lam,
+                                   const PT2* chirp, const PT2* bp, const PT2* bm, const PT* cj1, const PT* cj2,
+                                   int order, int lane, int nlanes, PT one = (PT)1) {
+    precond_step_a<PT, PT2>(w, Ns, L, log2L, bluestein, tw, chirp, bp, lane, nlanes);
+    PT c1[7], c2v[7];
+#pragma unroll
+    for (int j = 1; j <= 6; ++j) {
+        c1[j] = j <= order ? cj1[j] : (PT)0;
+        c2v[j] = j <= order ? cj2[j] : (PT)0;
+    }
+    const PT h = (PT)0.5;
+    for (int k = lane; k <= Ns / 2; k += nlanes) {
+        const int kk = k == 0 ? 0 : Ns - k;
+        const PT2 a = w[k], b = w[kk];
+        const PT2 y1 = c2(h * (a.x + b.x), h * (a.y - b.y));
+        const PT2 y2 = c2(h * (a.y + b.y), h * (b.x - a.x));
+        const PT2 z1 = cdiv(y1, precond_divisor<PT, PT2, PT>(lam[k], c1, order, one));
+        const PT2 z2 = cdiv(y2, precond_divisor<PT, PT2, PT>(lam[k], c2v, order, one));
+        PT2 wk = c2(z1.x - z2.y, z1.y + z2.x);     // Z1_k + i Z2_k
+        PT2 wkk = c2(z1.x + z2.y, z2.x - z1.y);    // conj(Z1_k) + i conj(Z2_k)
+        if (bluestein) {
+            wk = cmulc(wk, chirp[k]);
+            wkk = cmulc(wkk, chirp[kk]);
+        }
+        w[k] = wk;
+        if (kk != k) w[kk] = wkk;
+    }
+    return precond_step_c<PT, PT2>(w, Ns, L, log2L, bluestein, tw, chirp, bm, lane, nlanes);
 }
 
 #ifndef __CUDACC_RTC__

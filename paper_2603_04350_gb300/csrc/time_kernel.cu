@@ -19,7 +19,9 @@
 // coalesced reads along the mode index into shared memory, each warp then
 // transforms one column in shared memory (radix-2 FFT for power-of-two Ns,
 // Bluestein's chirp-z with a power-of-two length otherwise), and the tile is
-// written back coalesced.  The grid is a multiple of the SM count and loops
+// written back coalesced.  On Dirichlet grids the columns are real and one warp
+// solves two of them as one complex column (precond_column_pair: the FFT work
+// of one column for two).  The grid is a multiple of the SM count and loops
 // over tiles in a fixed order, so the per-slice norm partials are deterministic.
 #include <math.h>
 
@@ -112,6 +114,54 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
         }
         __syncthreads();
 
+        if (REAL && !ADV && A.precond) {
+            // ---- real columns (Dirichlet): one warp per two columns, packed as
+            // one complex column (precond_column_pair) ----
+            const int ca = 2 * warp;
+            const long long ma = m0 + ca, mb = ma + 1;
+            if (ca < C && ma < Mcol) {
+                const bool hasb = ca + 1 < C && mb < Mcol;
+                ST csa[7], csb[7];
+                PT cpa[7], cpb[7];
+                csa[0] = csb[0] = (ST)0;
+                cpa[0] = cpb[0] = (PT)0;
+#pragma unroll
+                for (int j = 1; j <= 6; ++j) {
+                    csa[j] = j <= A.order ? coef<ST>(A, j, ma) : (ST)0;
+                    cpa[j] = j <= A.order ? coef<PT>(A, j, ma) : (PT)0;
+                    csb[j] = j <= A.order && hasb ? coef<ST>(A, j, mb) : csa[j];
+                    cpb[j] = j <= A.order && hasb ? coef<PT>(A, j, mb) : cpa[j];
+                }
+                PT2* w = sW + (size_t)warp * L;
+                const ST2* xa = sX + (size_t)ca * P;
+                ST2* ra = sR + (size_t)ca * P;
+                auto qcol = [&](const ST2* xc, const ST2* rc, const ST* cs, int n) {
+                    ST2 q = rc[n];
+                    if (A.X) {
+                        ST2 rx = xc[n];
+#pragma unroll
+                        for (int j = 1; j <= 6; ++j) {
+                            if (j <= A.order && j <= n) rx = sub_cx(rx, cs[j], xc[n - j]);
+                        }
+                        q.x = fma(sigR, rx.x, q.x);
+                    }
+                    return q.x;
+                };
+                for (int n = lane; n < Ns; n += 32) {
+                    const ST qa = qcol(xa, ra, csa, n);
+                    const ST qb = hasb ? qcol(xa + P, ra + P, csb, n) : (ST)0;
+                    w[A.bluestein ? n : (int)bitrev(n, A.log2L)] = cvt2<PT2>(cscale(c2(qa, qb), gam[n]));
+                }
+                EXPD_SYNCWARP();
+                precond_column_pair<PT, PT2>(w, Ns, L, A.log2L, A.bluestein, tw, lam, chirp, bp, bm, cpa, cpb,
+                                             A.order, lane, 32, (PT)(1.0 - A.dshift));
+                for (int n = lane; n < Ns; n += 32) {
+                    const ST2 v = cscale(cvt2<ST2>(w[A.bluestein ? n : (int)bitrev(n, A.log2L)]), osc[n]);
+                    ra[n] = c2(v.x, (ST)0);
+                    if (hasb) ra[P + n] = c2(v.y, (ST)0);
+                }
+            }
+        } else {
         // ---- one warp per column ----
         const long long m = m0 + warp;
         if (warp < C && m < Mcol) {
@@ -157,6 +207,7 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
                     rc[n] = cscale(v, osc[n]);
                 }
             }
+        }
         }
         __syncthreads();
 
