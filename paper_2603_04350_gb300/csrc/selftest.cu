@@ -424,6 +424,33 @@ static void tc_pass_host(const std::vector<double>& A, long long rows, int R, co
         }
 }
 
+// every digit pair once, most significant weight first, each group of one
+// weight and its worst-case float32 sum within 2^24
+static void test_tc_groups() {
+    for (int nsl = 1; nsl <= 7; ++nsl)
+        for (int K = 64; K <= 1024; K += 64) {
+            int np = 0, ng = 0;
+            unsigned char pi[32], pj[32], gstart[33], gw[32];
+            tc_groups(nsl, K, &np, &ng, pi, pj, gstart, gw);
+            int seen[8][8] = {{0}};
+            if (np != nsl * (nsl + 1) / 2 || ng < nsl || ng > np || gstart[0] != 0 || gstart[ng] != np) ++failures;
+            for (int q = 0; q < ng; ++q) {
+                long long sum = 0;
+                if (gstart[q + 1] <= gstart[q] || (q > 0 && gw[q] < gw[q - 1])) ++failures;
+                for (int k = gstart[q]; k < gstart[q + 1]; ++k) {
+                    if (pi[k] + pj[k] != gw[q]) ++failures;
+                    ++seen[pi[k]][pj[k]];
+                    sum += (long long)K * (pi[k] ? 64 : 128) * (pj[k] ? 64 : 128);
+                }
+                if (sum > (1LL << 24)) ++failures;
+            }
+            for (int i = 0; i < nsl; ++i)
+                for (int j = 0; j < nsl; ++j)
+                    if (seen[i][j] != (i + j < nsl ? 1 : 0)) ++failures;
+            if (K == 1024 && nsl == 6 && ng != 10) ++failures;  // 21 pairs in 10 groups at the 1024^2 workload
+        }
+}
+
 static void test_tc_dst(std::mt19937_64& rng) {
     const int NY = 256, NX = 128, ns = 2, nsl = 5;
     auto dst = [](int n) {
@@ -465,6 +492,7 @@ int main() {
     std::mt19937_64 rng(1234);
     test_conversions(rng);
     test_dd_complex(rng);
+    test_tc_groups();
     test_tc_dst(rng);
     for (int l = 1; l <= 12; ++l)
         for (int sign = -1; sign <= 1; sign += 2) {
