@@ -116,7 +116,8 @@ class Engine:
     """Runs a request trace with `workers` concurrent solves on one GPU."""
 
     def __init__(self, device: int = 0, workers: int = 4, budget_bytes: Optional[int] = None,
-                 precision: int = expd.PREC_MIXED, max_iter: int = 200, cache_plans: bool = True):
+                 precision: int = expd.PREC_MIXED, max_iter: int = 200, cache_plans: bool = True,
+                 tuner=None):
         self.dev = torch.device("cuda", device)
         torch.cuda.set_device(self.dev)
         free, _ = torch.cuda.mem_get_info(self.dev)
@@ -125,6 +126,9 @@ class Engine:
         self.precision = precision
         self.max_iter = max_iter
         self.cache_plans = cache_plans
+        # autotune.Tuner: plans of shapes it has measured use its fastest
+        # kernel variants (the defaults otherwise; it never measures here)
+        self.tuner = tuner
         self._cv = threading.Condition()
         self._adm = Admission(self.budget)
         self._closed = False
@@ -167,7 +171,10 @@ class Engine:
                     with torch.cuda.stream(stream):
                         entry = cache.pop(key, None)
                         if entry is None:
-                            plan = expd.plan_create(spec, stream)
+                            if self.tuner is not None:
+                                plan = self.tuner.plan_create(p, spec, stream)
+                            else:
+                                plan = expd.plan_create(spec, stream)
                             pbytes = plan.workspace_bytes()
                         else:
                             plan, pbytes = entry
