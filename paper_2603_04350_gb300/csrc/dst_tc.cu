@@ -9,18 +9,20 @@
 //
 //  * every row of the left operand (a data row, or a row of S) is scaled by a
 //    power of two 2^e with max|x| < 2^e and cut into k digits of 7 bits,
-//    x = 2^e sum_i d_i 2^{-7i} (balanced digits, |d_1| <= 128, |d_i| <= 64 for
-//    i > 1, rounded to nearest at the last one); every digit is an integer, so
-//    it is exact in bf16;
-//  * the product of two digit matrices over K <= 1024 is a sum of integers
-//    below 1024 * 128 * 128 = 2^24 in magnitude: the float32 accumulator of
-//    the tensor core holds it exactly;
-//  * the pairs (i, j) with i + j <= k + 1 are summed with weights 2^{-7(i+j)}
-//    in double-float (float hi + float lo) held in TMEM, then scaled by
-//    2^{e_row + e_col} and written in float64.
+//    x = 2^e sum_{i=0}^{k-1} d_i 2^{-7(i+1)} (balanced digits, |d_0| <= 128,
+//    |d_i| <= 64 for i > 0, rounded to nearest at the last one); every digit
+//    is an integer, so it is exact in bf16.  The data rows carry one exponent
+//    each, S one exponent for the whole matrix;
+//  * the product of two digit matrices over K <= 1024 is a sum of integers of
+//    at most 1024 * 128 * 128 = 2^24 in magnitude: the float32 accumulator of
+//    the tensor core holds it exactly.  Pairs of one weight share an
+//    accumulator while their bounds add up to at most 2^24 (tc_groups);
+//  * the pairs (i, j) with i + j < k are summed with weights 2^{-7(i+j+2)} in
+//    double-float (float hi + float lo) held in TMEM, then scaled by
+//    2^{e_row + e_S} and rounded once to float64.
 //
 // The truncation leaves a relative error of about 2^{-7k} (k = 6: 2^{-42}), so
-// the transform meets tolerances far below the float32 floor; the slice count
+// the transform meets tolerances far below the float32 floor; the digit count
 // follows the plan's tolerance.
 //
 // Two passes give the 2D transform: T_s = (X_s S_x)^T, then Y_s = (T_s S_y)^T.
