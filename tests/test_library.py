@@ -123,3 +123,16 @@ def test_null_arguments_are_rejected(expd):
     assert lib.expd_timing_enable(None, 1) == expd.ERR_INVALID_ARG
     assert lib.expd_status_string(3) == b"not converged"
     assert lib.expd_version() >= 10000
+
+
+def test_kernel_classes_match_the_header(expd):
+    # the binding's timing struct and class names follow the header's enum
+    text = open(os.path.join(ROOT, "include", "expd.h")).read()
+    n = int(re.search(r"EXPD_NUM_KCLASS\s*=\s*(\d+)", text).group(1))
+    assert expd.NUM_KCLASS == n == len(expd.KCLASS_NAMES)
+    enum = {m.group(1): int(m.group(2)) for m in re.finditer(r"EXPD_K_(\w+)\s*=\s*(\d+)", text)}
+    assert sorted(enum.values()) == list(range(n))
+    assert enum["DST_TC"] == expd.KCLASS_NAMES.index("dst_tc") == expd.K_DST_TC
+    assert enum["DST_SPLIT"] == expd.KCLASS_NAMES.index("dst_split") == expd.K_DST_SPLIT
+    assert C.sizeof(expd.Timing) == C.sizeof(C.c_longlong) + n * (C.sizeof(C.c_int) + 3 * C.sizeof(C.c_double)) + \
+        (4 if (n * C.sizeof(C.c_int)) % 8 else 0)
