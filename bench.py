@@ -18,6 +18,10 @@ returns to physical space.
              GPU in float64 (the time-stepping baseline)
   roofline   the dominant kernel class from CUDA events on its launch stream
   cpu_baseline  the CPU oracle (tests' reference), one full solve, host cores
+  heat_dirichlet_1024  the 1024^2 Dirichlet heat workload (s = 2, Nt = 128,
+             GMRES, tol 1e-9): mixed path (tensor-core sine transforms) vs
+             the float64 path, and the tensor-core kernel's TFLOP/s against
+             the measured bf16 peak (roofline_tensor)
 
 Launch: python bench.py [--gpus N --steps K --warmup W] (N > 1 under torchrun:
 every rank solves its own seeded problem, no collective on the data path).
