@@ -78,9 +78,9 @@ def parse_args():
     ap.add_argument("--profile-case", default=None, metavar="N,NT,PREC",
                     help="run two solves of the Allen-Cahn workload on an N x N grid with NT steps "
                          "(PREC mixed|fp64) and exit; the target of ncu captures")
-    ap.add_argument("--profile-dirichlet", default=None, metavar="N,NT",
-                    help="run two mixed GMRES solves of the Dirichlet heat workload on an N x N grid with NT "
-                         "steps (tensor-core DST) and exit; the target of ncu captures")
+    ap.add_argument("--profile-dirichlet", default=None, metavar="N,NT[,M]",
+                    help="run two mixed GMRES(M) solves of the Dirichlet heat workload on an N x N grid with NT "
+                         "steps (tensor-core DST; M = 20 by default) and exit; the target of ncu captures")
     ap.add_argument("--no-dirichlet", action="store_true", help="skip the 1024^2 Dirichlet heat leg")
     return ap.parse_args()
 
@@ -112,12 +112,15 @@ def profile_dirichlet(spec: str) -> int:
     import __graft_entry__ as g
     g.build()
     from paper_2603_04350_gb300 import expd, inputs as I
-    n, nt = (int(v) for v in spec.split(","))
+    parts = [int(v) for v in spec.split(",")]
+    n, nt = parts[0], parts[1]
+    restart = parts[2] if len(parts) > 2 else 20
     p = I.HEAT_DIRICHLET_1024.with_(n=(n, n), Nt=nt, dt=0.1 / nt)
     u0, f = I.make_inputs(p)
     u0d, fd = torch.from_numpy(u0).cuda(), torch.from_numpy(f).cuda()
     U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device="cuda")
-    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, max_iter=200)) as plan:
+    spec = expd.spec_from_problem(p, precision=expd.PREC_MIXED, max_iter=200, gmres_restart=restart)
+    with expd.plan_create(spec) as plan:
         for _ in range(2):
             info = plan.solve_gmres(u0d, fd, U)
     torch.cuda.synchronize()

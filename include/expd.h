@@ -60,7 +60,10 @@ typedef enum {
     EXPD_ERR_NOT_CONVERGED = 3, /* max_iter reached; the last iterate is returned       */
     EXPD_ERR_DIVERGED = 4,      /* update non-finite or 1e3 times the first update      */
     EXPD_ERR_CUDA = 5,          /* a CUDA runtime call failed                           */
-    EXPD_ERR_UNSUPPORTED = 6    /* valid request that this build does not implement     */
+    EXPD_ERR_UNSUPPORTED = 6,   /* valid request that this build does not implement     */
+    EXPD_ERR_TIMEOUT = 7,       /* the scheme's time limit ran out, or a pipeline wait  */
+                                /* inside a kernel gave up (the GPU stays usable)       */
+    EXPD_ERR_CANCELLED = 8      /* expd_plan_cancel stopped the call                    */
 } expd_status;
 
 enum { EXPD_BC_PERIODIC = 0, EXPD_BC_DIRICHLET = 1 };
@@ -92,29 +95,38 @@ typedef struct {
 /* Scheme and solver controls.
  *  order      s in 1..6: exponential BDF-s (Eq. (2.2), Eq. (4.1), Sec. 5)
  *  precision  EXPD_PREC_FP64: every transform, the preconditioner and the
- *             residual in float64.  EXPD_PREC_MIXED: the fixed point first
- *             sweeps entirely in float32 (iterate, residual, N and its FFTs,
- *             preconditioner) until its error estimate reaches tol or the
- *             float32 floor stalls it, then sweeps with a float64 iterate,
- *             float64 residual and N, and the float32 preconditioner, which
- *             converge to the float64 fixed point.  Start-up, right-hand side
- *             and output transforms are float64.  (Dirichlet grids with a
- *             nonlinearity skip the float32 sweeps.)  On 2D Dirichlet grids
- *             whose sizes are multiples of 128 up to 1024 (n + 1 not a power
- *             of two) the mixed path's sine transforms (Sec. 3.1, the
- *             eigenbasis of L_h) run on the tensor cores as split-bf16
- *             products: every row cut into k 7-bit digits, the digit
- *             products summed exactly in float32, the pairs in double-float,
- *             k = ceil((6 - log2 tol) / 7) in 3..7, relative error about
- *             2^(-7k); the environment variable EXPD_DST_TC=0, read at plan
- *             creation, keeps the float64 products.  A pipeline wait of that
- *             kernel that gives up (2 s) makes the call return EXPD_ERR_CUDA.
- *  max_iter   iteration cap of expd_solve_fp / expd_solve_gmres
+ *             residual in float64.  EXPD_PREC_MIXED:
+ *             - the fixed point first sweeps entirely in float32 (iterate,
+ *               residual, N and its FFTs, preconditioner) until its error
+ *               estimate reaches tol or the float32 floor stalls it, then
+ *               sweeps with an accurate iterate, residual and N (double-float
+ *               on periodic grids, float64 on Dirichlet grids) and the float32
+ *               preconditioner, which converge to the float64 fixed point
+ *               (Dirichlet grids with a nonlinearity skip the float32 sweeps);
+ *             - GMRES and BiCGStab run on the float32 preconditioner too, with
+ *               iterative refinement: every time the Krylov recurrence has
+ *               reduced its residual by 1e-3, or claims convergence, the
+ *               residual f_s - R_s v is recomputed in float64 and
+ *               preconditioned, and the method restarts from it; convergence
+ *               is declared on that recomputed residual only;
+ *             - start-up, right-hand side and output transforms use
+ *               double-float arithmetic on periodic grids and float64 on
+ *               Dirichlet grids, except that on 2D Dirichlet grids whose sizes
+ *               are multiples of 128 up to 1024 (n + 1 not a power of two) the
+ *               sine transforms (Sec. 3.1, the eigenbasis of L_h) run on the
+ *               tensor cores as split-bf16 products: every row cut into k
+ *               7-bit digits, the digit products summed exactly in float32,
+ *               the pairs in double-float, k = ceil((6 - log2 tol) / 7) in
+ *               3..7, relative error about 2^(-7k).  A pipeline wait of that
+ *               kernel that gives up (after 2 s, or at once when the plan is
+ *               cancelled) makes the call return EXPD_ERR_TIMEOUT, or
+ *               EXPD_ERR_CANCELLED after expd_plan_cancel.
+ *  max_iter   iteration cap of the iterative solvers
  *  tol        target L^inf(0,T;L^2) relative error (Sec. 7's norm).  The
  *             fixed point stops when rho/(1-rho) * max_n||s_n|| / max_n||v_n||
- *             <= tol (s the update, rho the observed contraction); GMRES stops
- *             when sqrt(Ns) times the relative preconditioned residual is
- *             <= tol
+ *             <= tol (s the update, rho the observed contraction); GMRES and
+ *             BiCGStab stop when sqrt(Ns) times the relative preconditioned
+ *             residual is <= tol
  *  gmres_restart  GMRES restart length m (1..64)
  *  startup    EXPD_STARTUP_RAMP or EXPD_STARTUP_GIVEN (u_1..u_{s-1} read
  *             from the first s-1 slices of the U argument of the solvers)
@@ -131,9 +143,29 @@ typedef struct {
  *             alpha perturbation, so the iteration needs one sweep fewer.
  *             EXPD_GUESS_ZERO (1): u_n = 0.  The paper runs several initial
  *             guesses (Sec. 7) without fixing one.  GMRES and BiCGStab start
- *             from zero.                                                   */
+ *             from zero.
+ *  kernel_flags  interchangeable kernel variants (each pair computes the same
+ *             result; the autotuner chooses among them): EXPD_KF_TIME_SMEM
+ *             takes the shared-memory time kernel where the register kernel
+ *             would run, EXPD_KF_FFT_RADIX4 the radix-4 shared-memory FFTs
+ *             instead of the four-step register FFTs, EXPD_KF_DST_FP64 the
+ *             float64 sine-transform products instead of the tensor cores.
+ *             The environment variables EXPD_TIME_KERNEL=smem,
+ *             EXPD_FFT_KERNEL=radix4 and EXPD_DST_TC=0, read at plan
+ *             creation, set the same flags.  0 = the default kernels.
+ *  nl_form    how the nonlinear term enters the scheme: EXPD_NLF_IF (0, the
+ *             paper's integrating-factor form, Eq. (6.1), Eq. (7.3)) or
+ *             EXPD_NLF_ETD1 (first-order exponential time differencing,
+ *             u_n = A u_{n-1} + dt phi_1(dt L) N(u_{n-1}),
+ *             phi_1(z) = (e^z - 1)/z, the ETD alternative named at the start
+ *             of Sec. 6; order 1 only).  Ignored for linear problems.
+ *  time_limit_ms  wall-clock limit of one solver call in milliseconds, checked
+ *             between iterations (EXPD_ERR_TIMEOUT when exceeded; the last
+ *             iterate is returned); 0 = none.                              */
 enum { EXPD_JAC_LAGGED = 0, EXPD_JAC_MEAN_U0 = 1 };
 enum { EXPD_GUESS_LINEAR = 0, EXPD_GUESS_ZERO = 1 };
+enum { EXPD_KF_TIME_SMEM = 1, EXPD_KF_FFT_RADIX4 = 2, EXPD_KF_DST_FP64 = 4 };
+enum { EXPD_NLF_IF = 0, EXPD_NLF_ETD1 = 1 };
 typedef struct {
     int order;
     int precision;
@@ -143,19 +175,34 @@ typedef struct {
     int startup;
     int jacobian;               /* EXPD_JAC_*                                          */
     int guess;                  /* EXPD_GUESS_*                                        */
+    int kernel_flags;           /* EXPD_KF_* bits                                      */
+    int nl_form;                /* EXPD_NLF_*                                          */
+    double time_limit_ms;       /* 0 = no limit                                        */
 } expd_scheme;
 
 #define EXPD_MAX_HISTORY 128
 
 /* Per-solve report.  history[k] is the convergence measure after iteration
  * k+1: the estimated relative error (fixed point) or the relative
- * preconditioned residual (GMRES). */
+ * preconditioned residual (GMRES, BiCGStab; with the mixed precision's
+ * refinement, the Krylov recurrence's value, while final_measure is the
+ * recomputed one).  The phase times are device times between CUDA events
+ * recorded on the call's stream: ms_setup from the start of the call to the
+ * start of the first iteration (host-buffer staging, start-up values and their
+ * transforms, the right-hand side f_s), ms_iterate for the iterations,
+ * ms_output for the inverse transforms and staging of the result; reading them
+ * makes the call wait for its stream once more at the end.  A NULL info skips
+ * them. */
 typedef struct {
     int iterations;
     int fp32_iterations;        /* fixed-point sweeps that evaluated N with float32 FFTs */
     double final_measure;
     double contraction;         /* last observed ratio of successive update norms    */
     double history[EXPD_MAX_HISTORY];
+    int refinements;            /* mixed Krylov: residuals recomputed in float64     */
+    double ms_setup;
+    double ms_iterate;
+    double ms_output;
 } expd_info;
 
 typedef struct expd_plan_s* expd_plan;
@@ -206,48 +253,71 @@ expd_status expd_residual(expd_plan plan, const double* u0, const double* f, con
 expd_status expd_precond_apply(expd_plan plan, const double* R, double* S, void* stream);
 
 /* Preconditioned fixed-point (Richardson) iteration v^{k+1} = v^k +
- * (R_s^alpha)^{-1}(f_s + beta_s dt N(v^k) - R_s v^k) from v^0 = 0
- * (Eq. (3.2), Eq. (4.4); lagged N as in Eqs. (7.3)-(7.4)).
+ * (R_s^alpha)^{-1}(f_s + beta_s dt N(v^k) - R_s v^k) (Eq. (3.2), Eq. (4.4);
+ * lagged N as in Eqs. (7.3)-(7.4)) from the initial iterate the scheme's
+ * `guess` selects: by default (EXPD_GUESS_LINEAR) v^0_n = A^(n-s+1) u_{s-1},
+ * with EXPD_GUESS_ZERO v^0 = 0.
  *   u0 [1 slice]; f [Nt slices] or NULL; U [Nt slices] output u_1..u_Nt
  *   (input for its first s-1 slices when startup = EXPD_STARTUP_GIVEN)
  *   info may be NULL.
  * Returns EXPD_ERR_NOT_CONVERGED (U holds the last iterate) when max_iter
  * sweeps do not reach tol, EXPD_ERR_DIVERGED when an update is non-finite or
  * exceeds 1e3 times the first one (the iteration matrix's spectral radius
- * exceeds 1, e.g. alpha/(1 - alpha) > 1 for slowly decaying modes). */
+ * exceeds 1, e.g. alpha/(1 - alpha) > 1 for slowly decaying modes),
+ * EXPD_ERR_TIMEOUT / EXPD_ERR_CANCELLED (U holds the last iterate) when the
+ * scheme's time limit ran out or expd_plan_cancel was called. */
 expd_status expd_solve_fp(expd_plan plan, const double* u0, const double* f, double* U,
                           expd_info* info, void* stream);
 
 /* Left-preconditioned restarted GMRES(m) on (R_s^alpha)^{-1} R_s v =
- * (R_s^alpha)^{-1} f_s (Sec. 3.2, Theorem 3.3), v^0 = 0, classical
- * Gram-Schmidt with one re-orthogonalisation, float64.  Linear problems
- * only (EXPD_ERR_INVALID_ARG otherwise).  Arguments as expd_solve_fp. */
+ * (R_s^alpha)^{-1} f_s (Sec. 3.2, Theorem 3.3), v^0 = 0, float64 vectors.
+ * EXPD_PREC_FP64: classical Gram-Schmidt with one re-orthogonalisation, the
+ * float64 preconditioner, restarts every m iterations.  EXPD_PREC_MIXED: the
+ * float32 preconditioner, one Gram-Schmidt pass, and a restart from the
+ * residual recomputed in float64 whenever a cycle has reduced its residual by
+ * 1e-3 or claims convergence (iterative refinement; the float32
+ * preconditioner's rounding, about eps32/alpha relative, then limits only how
+ * fast the restarts contract, never the accuracy).  Linear problems only
+ * (EXPD_ERR_INVALID_ARG otherwise).  Arguments and the time-limit and cancel
+ * statuses as expd_solve_fp. */
 expd_status expd_solve_gmres(expd_plan plan, const double* u0, const double* f, double* U,
                              expd_info* info, void* stream);
 
-/* Sequential time stepping of the same scheme: u_n = sum_j a_j A^j u_{n-j} +
- * beta_s dt f(t_n) for n = s..Nt, with u_n - beta_s dt N(u_n) solved pointwise
- * by Newton when N is nonzero (Eq. (2.2), Eq. (4.1), Eq. (7.3)), in float64,
- * one step after the other on the GPU.  Its result is the exact solution of
- * the all-at-once system that expd_solve_fp and expd_solve_gmres iterate
- * towards (the system is block lower-triangular), so it is both a reference
- * and the time-stepping baseline the parallel-in-time solve is measured
- * against.  Arguments as expd_solve_fp (no info; the plan's precision, tol
- * and max_iter are ignored).  Uses the plan's workspace: not concurrently
- * with another call on the same plan. */
 /* Left-preconditioned BiCGStab (van der Vorst's recurrences) on
- * (R_s^alpha)^{-1} R_s v = (R_s^alpha)^{-1} f_s, v^0 = 0, float64: the
+ * (R_s^alpha)^{-1} R_s v = (R_s^alpha)^{-1} f_s, v^0 = 0, float64 vectors: the
  * short-recurrence alternative to GMRES that Sec. 7 (Table 2) times beside it
  * (two preconditioned operator applications and three reductions per
  * iteration, seven vectors of storage whatever the iteration count).  Stops
  * like expd_solve_gmres; restarts its shadow residual on a breakdown; returns
- * EXPD_ERR_DIVERGED when the residual turns non-finite.  Linear problems
- * only.  Arguments as expd_solve_fp; info->history[k] is the relative
- * preconditioned residual after k iterations. */
+ * EXPD_ERR_DIVERGED when the residual turns non-finite.  EXPD_PREC_MIXED runs
+ * the float32 preconditioner and replaces the recurrence's residual by the one
+ * recomputed in float64 (restarting the recurrences) under the same rule as
+ * GMRES.  Linear problems only.  Arguments as expd_solve_fp;
+ * info->history[k] is the relative preconditioned residual after k
+ * iterations. */
 expd_status expd_solve_bicgstab(expd_plan plan, const double* u0, const double* f, double* U,
                                 expd_info* info, void* stream);
 
+/* Sequential time stepping of the same scheme: u_n = sum_j a_j A^j u_{n-j} +
+ * beta_s dt f(t_n) for n = s..Nt, with u_n - beta_s dt N(u_n) solved pointwise
+ * by Newton when N is nonzero (Eq. (2.2), Eq. (4.1), Eq. (7.3); with
+ * EXPD_NLF_ETD1, u_n = A u_{n-1} + dt phi_1(dt L) N(u_{n-1}) explicitly), in
+ * float64, one step after the other on the GPU.  Its result is the exact
+ * solution of the all-at-once system that expd_solve_fp and expd_solve_gmres
+ * iterate towards (the system is block lower-triangular), so it is both a
+ * reference and the time-stepping baseline the parallel-in-time solve is
+ * measured against.  Arguments as expd_solve_fp (no info; the plan's
+ * precision, tol and max_iter are ignored).  Uses the plan's workspace: not
+ * concurrently with another call on the same plan. */
 expd_status expd_solve_sequential(expd_plan plan, const double* u0, const double* f, double* U, void* stream);
+
+/* Ask the solver call in flight on this plan -- or, when none is, the plan's
+ * next solver call -- to stop at its next iteration boundary (and a
+ * tensor-core sine-transform launch in flight to give up its pipeline waits):
+ * that call returns EXPD_ERR_CANCELLED with the last iterate in U, and the
+ * request is consumed.  Thread-safe: meant to be called from another host
+ * thread than the one running the solve. */
+expd_status expd_plan_cancel(expd_plan plan);
 
 /* ---- allocation-free preconditioner solve ---------------------------------
  * The paper has no counterpart to this entry point; it is a deployment variant

@@ -118,6 +118,10 @@ double* pinned_acquire(size_t ndoubles) {
     return r;
 }
 
+// pinned words of a plan: per-slice norm totals, the device loop's state, one
+// spare, and the cancel flag
+size_t pinned_words(const expd_plan_s* p) { return 2 * (size_t)p->Ns + EXPD_CTL_DOUBLES + 2; }
+
 void pinned_release(double* q, size_t ndoubles) {
     if (!q) return;
     int c = 3;
@@ -159,8 +163,10 @@ void free_plan(expd_plan p) {
     for (auto& g : p->sweep_graph)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (p->loop_graph.exec) cudaGraphExecDestroy(p->loop_graph.exec);
-    pinned_release(p->redhost, 2 * (size_t)p->Ns + EXPD_CTL_DOUBLES + 1);
+    pinned_release(p->redhost, pinned_words(p));
     for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->phase_ev)
+        if (e) cudaEventDestroy(e);
     time_tables_free(p);
     delete p;
 }
@@ -332,6 +338,62 @@ void info_reset(expd_info* info) {
     memset(info, 0, sizeof(*info));
 }
 
+// ---- per-call bookkeeping: phase events, time limit, cancellation ----------
+// A solver call records event 0 at its start, 1 when its iterations start, 2
+// when its output starts and 3 at its end (only when the caller asked for an
+// info report); call_end waits for event 3 and reports the three intervals.
+expd_status call_begin(expd_plan p, expd_info* info, cudaStream_t s) {
+    info_reset(info);
+    p->call_t0 = std::chrono::steady_clock::now();
+    p->call_cancelled = 0;
+    if (!info) return EXPD_OK;
+    for (cudaEvent_t& e : p->phase_ev)
+        if (!e) EXPD_CUDA_TRY(cudaEventCreate(&e));
+    EXPD_CUDA_TRY(cudaEventRecord(p->phase_ev[0], s));
+    return EXPD_OK;
+}
+
+expd_status call_mark(expd_plan p, expd_info* info, int k, cudaStream_t s) {
+    if (info) EXPD_CUDA_TRY(cudaEventRecord(p->phase_ev[k], s));
+    return EXPD_OK;
+}
+
+// Ends a call that returns `result`: phase times into info; a failure to read
+// them only replaces an OK result.
+expd_status call_end(expd_plan p, expd_info* info, cudaStream_t s, expd_status result) {
+    if (!info) return result;
+    cudaError_t e = cudaEventRecord(p->phase_ev[3], s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(p->phase_ev[3]);
+    float t[3] = {0, 0, 0};
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&t[k], p->phase_ev[k], p->phase_ev[k + 1]);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return result == EXPD_OK ? expd_cuda_fail(e, "phase events", __FILE__, __LINE__) : result;
+    }
+    info->ms_setup = t[0];
+    info->ms_iterate = t[1];
+    info->ms_output = t[2];
+    return result;
+}
+
+// Between iterations: EXPD_ERR_CANCELLED when expd_plan_cancel asked for it
+// (the request is consumed), EXPD_ERR_TIMEOUT when the scheme's time limit ran
+// out, else EXPD_OK.
+expd_status poll_stop(expd_plan p) {
+    if (p->cancel_req.load(std::memory_order_acquire) && p->cancel_req.exchange(0)) {
+        if (p->cancel_host) *p->cancel_host = 0;
+        p->call_cancelled = 1;
+        return expd_fail(EXPD_ERR_CANCELLED, "cancelled by expd_plan_cancel");
+    }
+    if (p->time_limit_ms > 0) {
+        const double ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - p->call_t0).count();
+        if (ms > p->time_limit_ms)
+            return expd_fail(EXPD_ERR_TIMEOUT, "time limit of " + std::to_string(p->time_limit_ms) + " ms reached");
+    }
+    return EXPD_OK;
+}
+
 }  // namespace
 
 cudaError_t plan_malloc(expd_plan p, void** ptr, size_t bytes) {
@@ -389,6 +451,8 @@ expd_status expd_cuda_fail(cudaError_t e, const char* what, const char* file, in
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? EXPD_ERR_OOM : EXPD_ERR_CUDA;
 }
+
+void expd_clear_error() { g_err.clear(); }
 
 expd_status expd_fail(expd_status s, const std::string& msg) {
     g_err = msg;
@@ -456,6 +520,14 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
         return expd_fail(EXPD_ERR_INVALID_ARG, "guess must be EXPD_GUESS_LINEAR or EXPD_GUESS_ZERO");
     if (scheme->startup != EXPD_STARTUP_RAMP && scheme->startup != EXPD_STARTUP_GIVEN)
         return expd_fail(EXPD_ERR_INVALID_ARG, "unknown startup mode");
+    if (scheme->kernel_flags & ~(EXPD_KF_TIME_SMEM | EXPD_KF_FFT_RADIX4 | EXPD_KF_DST_FP64))
+        return expd_fail(EXPD_ERR_INVALID_ARG, "unknown kernel_flags bits");
+    if (scheme->nl_form != EXPD_NLF_IF && scheme->nl_form != EXPD_NLF_ETD1)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "nl_form must be EXPD_NLF_IF or EXPD_NLF_ETD1");
+    if (scheme->nl_form == EXPD_NLF_ETD1 && op->nonlin != EXPD_NL_NONE && scheme->order != 1)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "the ETD1 form is a first-order scheme (order 1)");
+    if (!(scheme->time_limit_ms >= 0) || !isfinite(scheme->time_limit_ms))
+        return expd_fail(EXPD_ERR_INVALID_ARG, "time_limit_ms must be finite and >= 0");
     p->ndim = grid->ndim;
     if (p->ndim == 1) {
         p->NX = grid->n[0];
@@ -494,6 +566,25 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     p->startup = scheme->startup;
     p->jacobian = scheme->jacobian;
     p->guess = scheme->guess;
+    p->nl_form = op->nonlin != EXPD_NL_NONE ? scheme->nl_form : EXPD_NLF_IF;
+    p->time_limit_ms = scheme->time_limit_ms;
+    // kernel variants: the scheme's flags, or the environment switches read here
+    // (EXPD_TIME_KERNEL=smem, EXPD_FFT_KERNEL=radix4, EXPD_DST_TC=0)
+    p->kernel_flags = scheme->kernel_flags;
+    {
+        const char* tk = getenv("EXPD_TIME_KERNEL");
+        if (tk && strcmp(tk, "smem") == 0) p->kernel_flags |= EXPD_KF_TIME_SMEM;
+        const char* cf = getenv("EXPD_FFT_KERNEL");
+        if (cf && strcmp(cf, "radix4") == 0) p->kernel_flags |= EXPD_KF_FFT_RADIX4;
+        const char* dt0 = getenv("EXPD_DST_TC");
+        if (dt0 && strcmp(dt0, "0") == 0) p->kernel_flags |= EXPD_KF_DST_FP64;
+        // mixed Krylov refinement threshold (a cycle ends once its residual fell by eta)
+        const char* ke = getenv("EXPD_KRYLOV_ETA");
+        if (ke) {
+            const double v = atof(ke);
+            if (v > 0 && v < 1) p->krylov_eta = v;
+        }
+    }
     for (int q = 1; q <= 6; ++q) bdf(q, p->acoef[q], &p->beta[q]);
     if (p->nonlin != EXPD_NL_NONE) {
         for (int q = 1; q <= p->order; ++q)
@@ -514,12 +605,12 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (ce != cudaSuccess) return expd_cuda_fail(ce, "cudaGetDevice/cudaDeviceGetAttribute", __FILE__, __LINE__);
-    // EXPD_TIME_KERNEL=smem selects the shared-memory time kernel for every window
+    // EXPD_KF_TIME_SMEM selects the shared-memory time kernel for every window
     // (both kernels compute the same sweep; this lets them be compared)
-    const char* tk = getenv("EXPD_TIME_KERNEL");
-    p->no_reg_time = tk && strcmp(tk, "smem") == 0;
-    // EXPD_FFT_KERNEL=radix4 selects the shared-memory radix-4 row and column
+    p->no_reg_time = (p->kernel_flags & EXPD_KF_TIME_SMEM) != 0;
+    // EXPD_KF_FFT_RADIX4 selects the shared-memory radix-4 row and column
     // FFTs for every size (both compute the same transforms)
+    p->no_fft4 = (p->kernel_flags & EXPD_KF_FFT_RADIX4) != 0;
     const char* gr = getenv("EXPD_GRAPHS");
     p->no_graphs = gr && strcmp(gr, "0") == 0;
     // the device-controlled loop is opt-in (EXPD_DEVICE_LOOP=1): on GB300 its
@@ -528,8 +619,6 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     // 256^2 x 64)
     const char* dl = getenv("EXPD_DEVICE_LOOP");
     p->no_device_loop = !(dl && strcmp(dl, "1") == 0);
-    const char* cf = getenv("EXPD_FFT_KERNEL");
-    p->no_fft4 = cf && strcmp(cf, "radix4") == 0;
     return EXPD_OK;
 }
 
@@ -837,6 +926,8 @@ const char* expd_status_string(expd_status s) {
         case EXPD_ERR_DIVERGED: return "diverged";
         case EXPD_ERR_CUDA: return "CUDA error";
         case EXPD_ERR_UNSUPPORTED: return "unsupported";
+        case EXPD_ERR_TIMEOUT: return "timed out";
+        case EXPD_ERR_CANCELLED: return "cancelled";
     }
     return "unknown status";
 }
@@ -1039,13 +1130,18 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
         if (e != cudaSuccess) st = expd_cuda_fail(e, "cudaMemsetAsync(norms)", __FILE__, __LINE__);
     }
     if (st == EXPD_OK) {
-        p->redhost = pinned_acquire(2 * (size_t)p->Ns + EXPD_CTL_DOUBLES + 1);
+        p->redhost = pinned_acquire(pinned_words(p));
         p->phys_slot = reinterpret_cast<double**>(p->redout + nred - 1);
         if (p->redhost) {
             void* d = nullptr;
             const cudaError_t e = cudaHostGetDevicePointer(&d, p->redhost, 0);
             if (e != cudaSuccess) st = expd_cuda_fail(e, "cudaHostGetDevicePointer(norms)", __FILE__, __LINE__);
             p->redhost_dev = static_cast<double*>(d);
+            // the last word: the cancel flag the tensor-core kernel polls
+            const size_t cw = pinned_words(p) - 1;
+            p->cancel_host = reinterpret_cast<volatile int*>(p->redhost + cw);
+            *p->cancel_host = 0;
+            if (p->redhost_dev) p->cancel_dev = reinterpret_cast<const int*>(p->redhost_dev + cw);
         }
         if (!p->redhost) st = expd_fail(EXPD_ERR_OOM, "pinned host memory for the norms");
     }
@@ -1250,9 +1346,10 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     if (!p || !u0 || !U) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, u0 and U are required");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     EXPD_CUDA_TRY(plan_bind_stream(p, s));
-    info_reset(info);
+    expd_status st = call_begin(p, info, s);
+    if (st != EXPD_OK) return st;
     Staging sg;
-    expd_status st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
+    st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
     if (st != EXPD_OK) return st;
     const bool nl = p->nonlin != EXPD_NL_NONE;
     const bool mixed = p->precision == EXPD_PREC_MIXED;
@@ -1384,6 +1481,8 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     int it = 0, it32 = 0;
     expd_status result = EXPD_ERR_NOT_CONVERGED;
     ++p->fp_solves;
+    st = call_mark(p, info, 1, s);
+    if (st != EXPD_OK) return st;
     if (device_loop) {
         const bool two = phase == PH32;
         LoopBody b1{two ? 1 : 0, make_op(two ? PH32 : acc_phase).sout != nullptr ? 1 : 0};
@@ -1466,6 +1565,11 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
             break;
         }
         prev = smax;
+        const expd_status stop = poll_stop(p);
+        if (stop != EXPD_OK) {
+            result = stop;
+            break;
+        }
     }
     if (it > p->max_iter) it = p->max_iter;
     if (phase == PH32) {
@@ -1483,6 +1587,8 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
         info->fp32_iterations = it32;
         info->final_measure = measure;
     }
+    st = call_mark(p, info, 2, s);
+    if (st != EXPD_OK) return st;
     if (phase == PHDD && phys_valid && last_rel <= 1e-4) {
         if (p->order > 1)
             EXPD_CUDA_TRY(cudaMemcpyAsync(sg.U, p->startphys + p->M, (size_t)(p->order - 1) * p->M * sizeof(double),
@@ -1495,7 +1601,7 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     st = stage_out(p, sg, s);
     if (st != EXPD_OK) return st;
     if (result == EXPD_ERR_NOT_CONVERGED) g_err = "max_iter reached before tol";
-    return result;
+    return call_end(p, info, s, result);
 }
 
 // The Krylov block: nvec vectors of eigen_elems doubles, then the dot results
@@ -1572,31 +1678,49 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
     if (p->nonlin != EXPD_NL_NONE) return expd_fail(EXPD_ERR_INVALID_ARG, "GMRES needs a linear problem");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     EXPD_CUDA_TRY(plan_bind_stream(p, s));
-    info_reset(info);
+    expd_status st = call_begin(p, info, s);
+    if (st != EXPD_OK) return st;
     const int m = p->restart;
     const long long n = eigen_elems(p);
+    // mixed precision: the float32 preconditioner inside iterative refinement
+    const bool mixed = p->precision == EXPD_PREC_MIXED;
     // block: V[0..m], c, w, then h/partials
-    {
-        expd_status st = ensure_krylov(p, m + 3);
-        if (st != EXPD_OK) return st;
-    }
+    st = ensure_krylov(p, m + 3);
+    if (st != EXPD_OK) return st;
     double* V = static_cast<double*>(p->gm);
     double* c = V + (size_t)(m + 1) * n;
     double* w = c + n;
     double* h = w + n;  // [128] results + partials
     Staging sg;
-    expd_status st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
+    st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
     if (st != EXPD_OK) return st;
     st = setup_start(p, sg.u0, sg.f, sg.U, s);
+    if (st != EXPD_OK) return st;
+    st = call_mark(p, info, 1, s);
     if (st != EXPD_OK) return st;
     double* x = static_cast<double*>(p->Uh);
     EXPD_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
 
+    // out = P^{-1} R v  (the preconditioned operator of Theorem 3.3)
     auto apply_op = [&](const double* v, double* out) -> expd_status {
         TimeOp op;
         op.X = v;
         op.sigR = 1.0;
         op.precond = 1;
+        op.f32 = mixed;
+        op.out = out;
+        return time_apply(p, op, s);
+    };
+    // out = P^{-1} (f_s - R x): the residual in float64, then preconditioned,
+    // in one pass of the time kernel
+    auto residual_op = [&](double* out) -> expd_status {
+        TimeOp op;
+        op.F = p->Fh;
+        op.f_slices = p->f_slices;
+        op.X = x;
+        op.sigR = -1.0;
+        op.precond = 1;
+        op.f32 = mixed;
         op.out = out;
         return time_apply(p, op, s);
     };
@@ -1613,6 +1737,7 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
         op.F = p->Fh;
         op.f_slices = p->f_slices;
         op.precond = 1;
+        op.f32 = mixed;
         op.out = c;
         st = time_apply(p, op, s);
         if (st != EXPD_OK) return st;
@@ -1627,19 +1752,19 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
     // by at most sqrt(Ns), so GMRES stops at sqrt(Ns) * relres <= tol.
     const double tol_res = p->tol / sqrt((double)p->Ns);
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hh(m + 1), hh2(m + 1), y(m);
-    int total = 0;
+    int total = 0, refinements = 0;
     double relres = 1.0;
     expd_status result = EXPD_ERR_NOT_CONVERGED;
     if (info) info->history[0] = 1.0;
     bool first = true;
-    while (cn > 0 && total < p->max_iter) {
-        // r = c - P^{-1} R x   (x = 0 on the first cycle)
+    while (cn > 0) {
+        // r = P^{-1}(f_s - R x)   (= c on the first cycle, x = 0)
         if (first) {
             EXPD_CUDA_TRY(cudaMemcpyAsync(V, c, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         } else {
-            st = apply_op(x, V);
-            if (st == EXPD_OK) st = gm_axpby(p, n, 1.0, c, -1.0, V, s);
+            st = residual_op(V);
             if (st != EXPD_OK) return st;
+            ++refinements;
         }
         first = false;
         double b2 = 0;
@@ -1647,27 +1772,35 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
         if (st != EXPD_OK) return st;
         const double beta = sqrt(b2);
         relres = beta / cn;
+        if (!(relres == relres)) {
+            result = expd_fail(EXPD_ERR_DIVERGED, "GMRES residual is non-finite");
+            break;
+        }
         if (relres <= tol_res) {
             result = EXPD_OK;
             break;
         }
+        if (total >= p->max_iter) break;
         st = gm_axpby(p, n, 1.0 / beta, V, 0.0, V, s);
         if (st != EXPD_OK) return st;
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
         int jdone = 0;
         bool conv = false;
+        expd_status stop = EXPD_OK;
         for (int j = 0; j < m && total < p->max_iter; ++j) {
             double* vj1 = V + (size_t)(j + 1) * n;
             st = apply_op(V + (size_t)j * n, w);
             if (st != EXPD_OK) return st;
-            // classical Gram-Schmidt with one re-orthogonalisation
+            // classical Gram-Schmidt; float64 preconditioner: one
+            // re-orthogonalisation (the mixed path's operator carries float32
+            // rounding, far above what a second pass would correct)
             st = dots(V, j + 1, w, hh.data());
             if (st == EXPD_OK) st = gm_update(p, V, n, j + 1, h, w, s);
-            if (st == EXPD_OK) st = dots(V, j + 1, w, hh2.data());
-            if (st == EXPD_OK) st = gm_update(p, V, n, j + 1, h, w, s);
+            if (st == EXPD_OK && !mixed) st = dots(V, j + 1, w, hh2.data());
+            if (st == EXPD_OK && !mixed) st = gm_update(p, V, n, j + 1, h, w, s);
             if (st != EXPD_OK) return st;
-            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh2[i];
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + (mixed ? 0.0 : hh2[i]);
             double wn2 = 0;
             st = dots(w, 1, w, &wn2);
             if (st != EXPD_OK) return st;
@@ -1693,10 +1826,15 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
             jdone = j + 1;
             relres = fabs(g[j + 1]) / cn;
             if (info && total < EXPD_MAX_HISTORY) info->history[total] = relres;
-            if (relres <= tol_res) {
+            if (relres <= tol_res || hn == 0) {
                 conv = true;
                 break;
             }
+            // mixed: the cycle ends once its residual fell by eta; the restart
+            // recomputes it in float64 (iterative refinement)
+            if (mixed && fabs(g[j + 1]) <= p->krylov_eta * beta) break;
+            stop = poll_stop(p);
+            if (stop != EXPD_OK) break;
         }
         // x += V y,  H y = g
         for (int i = jdone - 1; i >= 0; --i) {
@@ -1705,11 +1843,19 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
             y[i] = acc / H[(size_t)i * m + i];
         }
         for (int i = 0; i < jdone; ++i) hh[i] = -y[i];
-        EXPD_CUDA_TRY(cudaMemcpyAsync(h, hh.data(), jdone * sizeof(double), cudaMemcpyHostToDevice, s));
-        st = gm_update(p, V, n, jdone, h, x, s);
-        if (st != EXPD_OK) return st;
+        if (jdone > 0) {
+            EXPD_CUDA_TRY(cudaMemcpyAsync(h, hh.data(), jdone * sizeof(double), cudaMemcpyHostToDevice, s));
+            st = gm_update(p, V, n, jdone, h, x, s);
+            if (st != EXPD_OK) return st;
+        }
         EXPD_CUDA_TRY(cudaStreamSynchronize(s));
-        if (conv) {
+        if (stop != EXPD_OK) {
+            result = stop;
+            break;
+        }
+        // float64 preconditioner: the recurrence's residual is the true one;
+        // mixed: convergence is declared only on the recomputed residual
+        if (conv && !mixed) {
             result = EXPD_OK;
             break;
         }
@@ -1718,13 +1864,16 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
     if (info) {
         info->iterations = total;
         info->final_measure = relres;
+        info->refinements = refinements;
     }
+    st = call_mark(p, info, 2, s);
+    if (st != EXPD_OK) return st;
     st = write_solution(p, sg.U, s);
     if (st != EXPD_OK) return st;
     st = stage_out(p, sg, s);
     if (st != EXPD_OK) return st;
     if (result == EXPD_ERR_NOT_CONVERGED) g_err = "max_iter reached before tol";
-    return result;
+    return call_end(p, info, s, result);
 }
 
 expd_status expd_solve_bicgstab(expd_plan p, const double* u0, const double* f, double* U, expd_info* info,
@@ -1733,9 +1882,11 @@ expd_status expd_solve_bicgstab(expd_plan p, const double* u0, const double* f, 
     if (p->nonlin != EXPD_NL_NONE) return expd_fail(EXPD_ERR_INVALID_ARG, "BiCGStab needs a linear problem");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     EXPD_CUDA_TRY(plan_bind_stream(p, s));
-    info_reset(info);
+    expd_status st = call_begin(p, info, s);
+    if (st != EXPD_OK) return st;
     const long long n = eigen_elems(p);
-    expd_status st = ensure_krylov(p, 7);
+    const bool mixed = p->precision == EXPD_PREC_MIXED;
+    st = ensure_krylov(p, 7);
     if (st != EXPD_OK) return st;
     // [rhat][r] and [s][t] adjacent, so one dot kernel gives two products
     double* rhat = static_cast<double*>(p->gm);
@@ -1751,6 +1902,8 @@ expd_status expd_solve_bicgstab(expd_plan p, const double* u0, const double* f, 
     if (st != EXPD_OK) return st;
     st = setup_start(p, sg.u0, sg.f, sg.U, s);
     if (st != EXPD_OK) return st;
+    st = call_mark(p, info, 1, s);
+    if (st != EXPD_OK) return st;
     double* x = static_cast<double*>(p->Uh);
     EXPD_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
     auto apply_op = [&](const double* in, double* out) -> expd_status {  // out = P^{-1} R in
@@ -1758,6 +1911,18 @@ expd_status expd_solve_bicgstab(expd_plan p, const double* u0, const double* f, 
         op.X = in;
         op.sigR = 1.0;
         op.precond = 1;
+        op.f32 = mixed;
+        op.out = out;
+        return time_apply(p, op, s);
+    };
+    auto residual_op = [&](double* out) -> expd_status {  // out = P^{-1}(f_s - R x), residual in float64
+        TimeOp op;
+        op.F = p->Fh;
+        op.f_slices = p->f_slices;
+        op.X = x;
+        op.sigR = -1.0;
+        op.precond = 1;
+        op.f32 = mixed;
         op.out = out;
         return time_apply(p, op, s);
     };
@@ -1778,6 +1943,7 @@ expd_status expd_solve_bicgstab(expd_plan p, const double* u0, const double* f, 
         op.F = p->Fh;
         op.f_slices = p->f_slices;
         op.precond = 1;
+        op.f32 = mixed;
         op.out = c;
         st = time_apply(p, op, s);
     }
@@ -1792,7 +1958,11 @@ expd_status expd_solve_bicgstab(expd_plan p, const double* u0, const double* f, 
     // stop as GMRES does: sqrt(Ns) * ||P^{-1}(f - R v)|| / ||P^{-1} f|| <= tol
     const double tol_res = p->tol / sqrt((double)p->Ns);
     double rho = 1.0, alpha = 1.0, omega = 1.0, relres = 1.0;
-    int it = 0;
+    // mixed: norm of the residual at the last replacement; r is the recomputed
+    // (true) residual right after a replacement
+    double r_ref = cn;
+    bool r_true = true;
+    int it = 0, refinements = 0;
     expd_status result = EXPD_ERR_NOT_CONVERGED;
     if (info) info->history[0] = 1.0;
     while (cn > 0) {
@@ -1800,16 +1970,36 @@ expd_status expd_solve_bicgstab(expd_plan p, const double* u0, const double* f, 
         st = dots(rhat, 2, r, d2);  // (rhat, r), (r, r)
         if (st != EXPD_OK) return st;
         relres = sqrt(d2[1]) / cn;
-        if (it > 0 && info && it < EXPD_MAX_HISTORY) info->history[it] = relres;
+        if (it > 0 && info && it < EXPD_MAX_HISTORY && !r_true) info->history[it] = relres;
         if (!(relres == relres) || relres > 1e12) {
-            result = EXPD_ERR_DIVERGED;
+            result = expd_fail(EXPD_ERR_DIVERGED, "BiCGStab residual non-finite or growing without bound");
             break;
         }
+        // mixed: when the recurrence's residual has fallen by eta since the last
+        // replacement, or claims convergence, replace it by the residual
+        // recomputed in float64 and restart the recurrences from it
+        if (mixed && !r_true && (relres <= tol_res || sqrt(d2[1]) <= p->krylov_eta * r_ref)) {
+            st = residual_op(r);
+            if (st == EXPD_OK) st = copy(r, rhat);
+            if (st == EXPD_OK) EXPD_CUDA_TRY(cudaMemsetAsync(pv, 0, 2 * n * sizeof(double), s));
+            if (st != EXPD_OK) return st;
+            rho = alpha = omega = 1.0;
+            r_true = true;
+            ++refinements;
+            continue;
+        }
+        if (mixed && r_true) r_ref = sqrt(d2[1]);
+        r_true = false;
         if (relres <= tol_res) {
             result = EXPD_OK;
             break;
         }
         if (it >= p->max_iter) break;
+        const expd_status stop = it > 0 ? poll_stop(p) : EXPD_OK;
+        if (stop != EXPD_OK) {
+            result = stop;
+            break;
+        }
         double rho_new = d2[0];
         if (rho_new == 0.0) {  // breakdown: restart the shadow residual from r
             st = copy(r, rhat);
@@ -1845,14 +2035,23 @@ expd_status expd_solve_bicgstab(expd_plan p, const double* u0, const double* f, 
     if (info) {
         info->iterations = it;
         info->final_measure = relres;
+        info->refinements = refinements;
     }
+    st = call_mark(p, info, 2, s);
+    if (st != EXPD_OK) return st;
     st = write_solution(p, sg.U, s);
     if (st != EXPD_OK) return st;
     st = stage_out(p, sg, s);
     if (st != EXPD_OK) return st;
     if (result == EXPD_ERR_NOT_CONVERGED) g_err = "max_iter reached before tol";
-    if (result == EXPD_ERR_DIVERGED) g_err = "BiCGStab residual non-finite or growing without bound";
-    return result;
+    return call_end(p, info, s, result);
+}
+
+expd_status expd_plan_cancel(expd_plan p) {
+    if (!p) return expd_fail(EXPD_ERR_INVALID_ARG, "plan is NULL");
+    p->cancel_req.store(1, std::memory_order_release);
+    if (p->cancel_host) *p->cancel_host = 1;
+    return EXPD_OK;
 }
 
 }  // extern "C"

@@ -86,6 +86,7 @@ struct TcArgs {
     // their products stays within 2^24); gw[q] = i + j of the group's pairs
     unsigned char gstart[33], gw[32];
     int* err;                 // set to 1 when a pipeline wait gave up
+    const volatile int* cancel;  // mapped host word: nonzero asks every wait to give up at once
 };
 
 // ------------------------------------------------------------ PTX helpers ----
@@ -121,15 +122,19 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// Waits for the phase of the given parity; gives up after TC_WAIT_NS or when
-// another role of the CTA has given up (abort != 0, unless ignore_abort).
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort, bool ignore_abort = false) {
+// Waits for the phase of the given parity; gives up after TC_WAIT_NS, when
+// another role of the CTA has given up (abort != 0) or when the host cancels
+// the call (cancel != 0, read from mapped host memory every 1024 tries);
+// ignore_abort (the clean-up waits) heeds neither flag, only the time limit.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort,
+                                       const volatile int* cancel, bool ignore_abort = false) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63) == 0) {
             if (!ignore_abort && *abort) return false;
+            if (!ignore_abort && cancel && (it & 1023) == 0 && *cancel) return false;
             if (globaltimer() - t0 > TC_WAIT_NS) return false;
         }
     }
@@ -368,7 +373,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
                     for (int kb = 0; kb < KB; ++kb, ++it) {
                         const int s = (int)(it % TC_STAGES);
                         const uint32_t ph = (it / TC_STAGES) & 1u;
-                        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) {
+                        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag, a.cancel)) {
                             ok = false;
                             break;
                         }
@@ -387,7 +392,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
             // copies still in flight land before the CTA leaves: the last one
             // issued into each stage completes that stage's phase
             for (uint32_t q = it > (uint32_t)TC_STAGES ? it - TC_STAGES : 0u; q < it; ++q)
-                mbar_wait(full((int)(q % TC_STAGES)), (q / TC_STAGES) & 1u, abort_flag, true);
+                mbar_wait(full((int)(q % TC_STAGES)), (q / TC_STAGES) & 1u, abort_flag, nullptr, true);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -397,7 +402,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
             for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 for (int g = 0; g < a.ngroups && ok; ++g, ++pc) {
                     const int b = (int)(pc % TC_NACC);
-                    if (!mbar_wait(acce(b), ((pc / TC_NACC) & 1u) ^ 1u, abort_flag)) {
+                    if (!mbar_wait(acce(b), ((pc / TC_NACC) & 1u) ^ 1u, abort_flag, a.cancel)) {
                         ok = false;
                         break;
                     }
@@ -407,7 +412,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
                         const bool first = p == a.gstart[g];
                         for (int kb = 0; kb < KB; ++kb, ++it) {
                             const int s = (int)(it % TC_STAGES);
-                            if (!mbar_wait(full(s), (it / TC_STAGES) & 1u, abort_flag)) {
+                            if (!mbar_wait(full(s), (it / TC_STAGES) & 1u, abort_flag, a.cancel)) {
                                 ok = false;
                                 break;
                             }
@@ -430,7 +435,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
             }
             // every MMA issued has completed before TMEM is released
             tc_commit(drain);
-            mbar_wait(drain, 0u, abort_flag, true);
+            mbar_wait(drain, 0u, abort_flag, nullptr, true);
         }
     } else {
         // ---- drain and output (warps 2..9): TMEM lane quarter warp % 4, columns
@@ -447,7 +452,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
                 const int b = (int)(pc % TC_NACC);
                 // every lane waits; the warp goes on only together (the TMEM
                 // loads and stores below are warp-collective)
-                if (!__all_sync(0xffffffffu, mbar_wait(accf(b), (pc / TC_NACC) & 1u, abort_flag))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(accf(b), (pc / TC_NACC) & 1u, abort_flag, a.cancel))) {
                     ok = false;
                     break;
                 }
@@ -567,6 +572,7 @@ expd_status mma_pass(expd_plan p, const uint16_t* A, const int* ea, long long ro
     a.npairs = np;
     a.ngroups = ng;
     a.err = p->tc_err;
+    a.cancel = p->cancel_dev;
     const long long ntiles = (rows / TC_BM) * (N / TC_BN);
     const int grid = (int)std::min<long long>(ntiles, (long long)p->sm_count);
     EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel, TC_SMEM));
@@ -596,8 +602,7 @@ int tc_slices_for(double tol) {
 
 bool dst_tc_eligible(expd_plan p) {
     if (p->bc != EXPD_BC_DIRICHLET || p->fast_dst || p->ndim != 2 || p->precision != EXPD_PREC_MIXED) return false;
-    const char* env = getenv("EXPD_DST_TC");
-    if (env && strcmp(env, "0") == 0) return false;
+    if (p->kernel_flags & EXPD_KF_DST_FP64) return false;
     auto ok = [](int n) { return n % TC_BM == 0 && n <= 1024; };
     return ok(p->NX) && ok(p->NY);
 }
@@ -669,7 +674,14 @@ expd_status dst_tc_check(expd_plan p, cudaStream_t s) {
     EXPD_CUDA_TRY(cudaStreamSynchronize(s));
     if (h) {
         EXPD_CUDA_TRY(cudaMemsetAsync(p->tc_err, 0, sizeof(int), s));
-        return expd_fail(EXPD_ERR_CUDA, "tensor-core DST: a pipeline wait gave up after 2 s (results invalid)");
+        // a wait that gave up because the call was cancelled, or one that ran
+        // out of time; the results are invalid either way
+        if (p->call_cancelled || p->cancel_req.exchange(0)) {
+            if (p->cancel_host) *p->cancel_host = 0;
+            p->call_cancelled = 1;
+            return expd_fail(EXPD_ERR_CANCELLED, "tensor-core DST: cancelled in flight (results invalid)");
+        }
+        return expd_fail(EXPD_ERR_TIMEOUT, "tensor-core DST: a pipeline wait gave up after 2 s (results invalid)");
     }
     return EXPD_OK;
 }

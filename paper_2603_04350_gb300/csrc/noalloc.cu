@@ -10,12 +10,17 @@
 // norm partials of the time kernel -- inside one fixed file-scope device array.
 //
 // The array (EXPD_NOALLOC_SCRATCH_BYTES) lives in every GPU that loads the
-// library until the process exits.  The first call on a device looks up its
-// device address with cudaGetSymbolAddress (host code cannot use the symbol
-// itself: in host code it names a host-side stand-in); make that first call
-// before any stream capture.  Every call shares the array and leaves its contents
-// behind; each call rewrites all of it that it reads, and calls that overlap on
-// the GPU (on different streams or threads) race on it.
+// library until the process exits.  Host code cannot use the symbol itself (in
+// host code it names a host-side stand-in), so a call looks up the array's
+// device address with cudaGetSymbolAddress, with the call's device current:
+// every call on a stream that is not being captured looks it up afresh (so a
+// context torn down and re-created, e.g. after cudaDeviceReset, never leaves a
+// stale address behind), and a call during stream capture, where the lookup
+// may not run, uses the address the last uncaptured call on that device found.
+// So the first call on a device must come before any stream capture.  Every
+// call shares the array and leaves its contents behind; each call rewrites all
+// of it that it reads, and calls that overlap on the GPU (on different streams
+// or threads) race on it.
 #include <math.h>
 
 #include <mutex>
@@ -31,16 +36,24 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 char* g_scratch_addr[kMaxDevices] = {};
 
-expd_status scratch_base(char** base) {
+expd_status scratch_base(cudaStream_t s, char** base) {
     int dev = 0;
     EXPD_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return expd_fail(EXPD_ERR_UNSUPPORTED, "device index out of range");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;  // undecidable: do not call into the runtime's symbol lookup
+    }
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess) return expd_cuda_fail(e, "cudaGetSymbolAddress(scratch)", __FILE__, __LINE__);
         g_scratch_addr[dev] = static_cast<char*>(ptr);
+    } else if (!g_scratch_addr[dev]) {
+        return expd_fail(EXPD_ERR_INVALID_ARG,
+                         "the first allocation-free call on a device must come before any stream capture");
     }
     *base = g_scratch_addr[dev];
     return EXPD_OK;
@@ -195,6 +208,7 @@ __global__ void time_tables_kernel(int Ns, double alpha, int L, int log2L, int b
 extern "C" expd_status expd_precond_apply_noalloc(const expd_grid* grid, const expd_operator* op, double dt, int Nt,
                                                   double alpha, const expd_scheme* scheme, const double* R, double* S,
                                                   void* stream) {
+    expd_clear_error();
     if (!R || !S) return expd_fail(EXPD_ERR_INVALID_ARG, "R and S are required");
     if (!expd_is_device_ptr(R) || !expd_is_device_ptr(S))
         return expd_fail(EXPD_ERR_INVALID_ARG, "R and S must be device pointers (host buffers would need staging)");
@@ -259,7 +273,7 @@ extern "C" expd_status expd_precond_apply_noalloc(const expd_grid* grid, const e
                 return expd_fail(EXPD_ERR_INVALID_ARG,
                                  "problem needs " + std::to_string(cv.used) + " bytes of scratch; the allocation-free "
                                  "entry point holds " + std::to_string((size_t)EXPD_NOALLOC_SCRATCH_BYTES));
-            st = scratch_base(&base);
+            st = scratch_base(s, &base);
             if (st != EXPD_OK) return st;
         }
     }

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -20,6 +22,8 @@
 
 expd_status expd_cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 expd_status expd_fail(expd_status s, const std::string& msg);
+// Clears this thread's expd_last_error() message (at the start of an entry point).
+void expd_clear_error();
 struct expd_plan_s;
 // Validate the problem and fill the plan's scalar fields (no allocation).
 expd_status plan_init_fields(expd_plan_s* p, const expd_grid* grid, const expd_operator* op, double dt, int Nt,
@@ -63,6 +67,9 @@ struct expd_plan_s {
     double alpha = 0;
     int precision = EXPD_PREC_FP64, max_iter = 50, restart = 20, startup = EXPD_STARTUP_RAMP;
     double tol = 1e-8;
+    int kernel_flags = 0;     // EXPD_KF_* (from the scheme and the environment)
+    int nl_form = EXPD_NLF_IF;
+    double time_limit_ms = 0; // 0: no limit
     double acoef[7][7] = {};  // acoef[q][j]: a_j of BDF-q, j = 1..q
     double beta[7] = {};      // beta_q
 
@@ -155,6 +162,16 @@ struct expd_plan_s {
     int no_graphs = 0;            // 1: launch kernel by kernel (EXPD_GRAPHS=0)
     int no_reg_time = 0;          // 1 forces the shared-memory time kernel (tests)
     int no_fft4 = 0;              // 1 forces the radix-4 shared-memory row / column FFTs (tests)
+    // mixed Krylov refinement: a cycle ends once its residual fell by this factor
+    double krylov_eta = 1e-3;
+    // ---- cancellation and time limit (expd_plan_cancel, expd_scheme.time_limit_ms) ----
+    std::atomic<int> cancel_req{0};  // set by expd_plan_cancel, consumed by the call it stops
+    volatile int* cancel_host = nullptr;  // mapped pinned word the tensor-core kernel polls
+    const int* cancel_dev = nullptr;      // the same word as the GPU addresses it
+    int call_cancelled = 0;       // the running call consumed a cancel request
+    std::chrono::steady_clock::time_point call_t0;
+    // ---- per-phase device times of a solver call (expd_info.ms_*) ----
+    cudaEvent_t phase_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // host-pointer staging (lazy)
     double* stage = nullptr;      // [(2*Nt + 1) * M]
     size_t stage_elems = 0;

@@ -17,17 +17,21 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libexpd.so")
 
-OK, ERR_INVALID_ARG, ERR_OOM, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_CUDA, ERR_UNSUPPORTED = range(7)
+(OK, ERR_INVALID_ARG, ERR_OOM, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT,
+ ERR_CANCELLED) = range(9)
 BC_PERIODIC, BC_DIRICHLET = 0, 1
 NL_NONE, NL_ALLEN_CAHN = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 STARTUP_RAMP, STARTUP_GIVEN = 0, 1
 JAC_LAGGED, JAC_MEAN_U0 = 0, 1
 GUESS_LINEAR, GUESS_ZERO = 0, 1
+KF_TIME_SMEM, KF_FFT_RADIX4, KF_DST_FP64 = 1, 2, 4
+NLF_IF, NLF_ETD1 = 0, 1
 MAX_HISTORY = 128
 
 SYMBOLS = ("expd_plan_create", "expd_plan_workspace_bytes", "expd_plan_footprint_bytes", "expd_residual", "expd_precond_apply",
-           "expd_solve_fp", "expd_solve_gmres", "expd_solve_bicgstab", "expd_solve_sequential", "expd_timing_enable", "expd_timing_read", "expd_destroy",
+           "expd_solve_fp", "expd_solve_gmres", "expd_solve_bicgstab", "expd_solve_sequential", "expd_plan_cancel",
+           "expd_timing_enable", "expd_timing_read", "expd_destroy",
            "expd_precond_apply_noalloc",
            "expd_status_string", "expd_last_error", "expd_version")
 (K_TIME, K_FFT_COL, K_FFT_ROW, K_DST, K_GMRES, K_POINTWISE, K_REDUCE, K_TIME32, K_FFT_COL32, K_FFT_ROW32,
@@ -47,18 +51,21 @@ class Operator(C.Structure):
 
 class Scheme(C.Structure):
     _fields_ = [("order", C.c_int), ("precision", C.c_int), ("max_iter", C.c_int), ("tol", C.c_double),
-                ("gmres_restart", C.c_int), ("startup", C.c_int), ("jacobian", C.c_int), ("guess", C.c_int)]
+                ("gmres_restart", C.c_int), ("startup", C.c_int), ("jacobian", C.c_int), ("guess", C.c_int),
+                ("kernel_flags", C.c_int), ("nl_form", C.c_int), ("time_limit_ms", C.c_double)]
 
 
 class Info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("fp32_iterations", C.c_int), ("final_measure", C.c_double),
-                ("contraction", C.c_double), ("history", C.c_double * MAX_HISTORY)]
+                ("contraction", C.c_double), ("history", C.c_double * MAX_HISTORY), ("refinements", C.c_int),
+                ("ms_setup", C.c_double), ("ms_iterate", C.c_double), ("ms_output", C.c_double)]
 
     def as_dict(self):
         k = max(0, min(self.iterations + 1, MAX_HISTORY))
         return {"iterations": self.iterations, "fp32_iterations": self.fp32_iterations,
                 "final_measure": self.final_measure, "contraction": self.contraction,
-                "history": [self.history[i] for i in range(k)]}
+                "history": [self.history[i] for i in range(k)], "refinements": self.refinements,
+                "ms_setup": self.ms_setup, "ms_iterate": self.ms_iterate, "ms_output": self.ms_output}
 
 
 class Timing(C.Structure):
@@ -100,6 +107,7 @@ def lib() -> C.CDLL:
     L.expd_solve_gmres.argtypes = [vp, dp, dp, dp, C.POINTER(Info), vp]
     L.expd_solve_sequential.argtypes = [vp, dp, dp, dp, vp]
     L.expd_solve_bicgstab.argtypes = [vp, dp, dp, dp, C.POINTER(Info), vp]
+    L.expd_plan_cancel.argtypes = [vp]
     L.expd_timing_enable.argtypes = [vp, C.c_int]
     L.expd_timing_read.argtypes = [vp, C.POINTER(Timing), C.c_int]
     L.expd_destroy.argtypes = [vp]
@@ -172,6 +180,9 @@ class PlanSpec:
     jacobian: int = 0
     b: tuple = (0.0, 0.0)
     guess: int = GUESS_LINEAR
+    kernel_flags: int = 0
+    nl_form: int = NLF_IF
+    time_limit_ms: float = 0.0
 
 
 def _structs(spec: PlanSpec):
@@ -183,7 +194,7 @@ def _structs(spec: PlanSpec):
     g.bc = spec.bc
     o = Operator(spec.a, spec.c, spec.nonlin, (C.c_double * 2)(*(tuple(spec.b) + (0.0, 0.0))[:2]))
     s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup, spec.jacobian,
-               spec.guess)
+               spec.guess, spec.kernel_flags, spec.nl_form, spec.time_limit_ms)
     return g, o, s
 
 
@@ -209,15 +220,7 @@ def precond_apply_noalloc(spec: PlanSpec, R, S, stream=None) -> None:
 
 
 def plan_create(spec: PlanSpec, stream=None) -> "Plan":
-    g = Grid()
-    g.ndim = len(spec.n)
-    for d in range(g.ndim):
-        g.n[d] = int(spec.n[d])
-        g.length[d] = float(spec.length[d])
-    g.bc = spec.bc
-    o = Operator(spec.a, spec.c, spec.nonlin, (C.c_double * 2)(*(tuple(spec.b) + (0.0, 0.0))[:2]))
-    s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup, spec.jacobian,
-               spec.guess)
+    g, o, s = _structs(spec)
     h = C.c_void_p()
     _check(lib().expd_plan_create(C.byref(g), C.byref(o), spec.dt, spec.Nt, spec.alpha, C.byref(s),
                                   _stream(stream), C.byref(h)))
@@ -269,6 +272,10 @@ class Plan:
         d["status"] = st
         return d
 
+    def cancel(self) -> None:
+        """expd_plan_cancel: stop the call in flight on this plan (or its next one)."""
+        _check(lib().expd_plan_cancel(self._h))
+
     def solve_sequential(self, u0, f, U, stream=None) -> None:
         """Step the scheme sequentially (float64): the exact all-at-once solution."""
         _check(lib().expd_solve_sequential(self._h, _ptr(u0), _ptr(f), _ptr(U), _stream(stream)))
@@ -301,10 +308,14 @@ class Plan:
 
 def spec_from_problem(p, precision: int = PREC_FP64, max_iter: int = 100, tol: Optional[float] = None,
                       gmres_restart: int = 20, startup: int = STARTUP_RAMP, jacobian: int = 0,
-                      guess: int = GUESS_LINEAR) -> PlanSpec:
+                      guess: int = GUESS_LINEAR, kernel_flags: int = 0, nl_form: Optional[int] = None,
+                      time_limit_ms: float = 0.0) -> PlanSpec:
     """PlanSpec from a paper_2603_04350_gb300.inputs.Problem."""
     return PlanSpec(bc=BC_PERIODIC if p.bc == "periodic" else BC_DIRICHLET, n=tuple(p.n), length=tuple(p.length),
                     a=p.a, c=p.c, nonlin=NL_ALLEN_CAHN if p.nonlin == "allen_cahn" else NL_NONE, dt=p.dt,
                     Nt=p.Nt, alpha=p.alpha, order=p.order, precision=precision, max_iter=max_iter,
                     tol=p.tol if tol is None else tol, gmres_restart=gmres_restart, startup=startup,
-                    jacobian=jacobian, b=tuple(getattr(p, "b", ()) or (0.0, 0.0)), guess=guess)
+                    jacobian=jacobian, b=tuple(getattr(p, "b", ()) or (0.0, 0.0)), guess=guess,
+                    kernel_flags=kernel_flags,
+                    nl_form=(NLF_ETD1 if getattr(p, "nl_form", "if") == "etd1" else NLF_IF) if nl_form is None
+                    else nl_form, time_limit_ms=time_limit_ms)

@@ -26,64 +26,73 @@ def test_knobs_for_each_kind():
 def test_candidates_are_the_product():
     c = A.candidates(AC, expd.PREC_MIXED)
     assert len(c) == 4
-    envs = [e for _, e in c]
-    assert {} in envs and {"EXPD_FFT_KERNEL": "radix4", "EXPD_TIME_KERNEL": "smem"} in envs
-    assert A.candidates(HD, expd.PREC_FP64) == [({}, {})]
+    flags = [f for _, f in c]
+    assert 0 in flags and (expd.KF_FFT_RADIX4 | expd.KF_TIME_SMEM) in flags
+    assert A.candidates(HD, expd.PREC_FP64) == [({}, 0)]
 
 
 def test_tuner_picks_fastest_and_caches():
     calls = []
 
-    def fake(p, prec, solver, env):
-        calls.append(dict(env))
-        return 1.0 + (0.5 if "EXPD_FFT_KERNEL" in env else 0.0) - (0.25 if "EXPD_TIME_KERNEL" in env else 0.0)
+    def fake(p, prec, solver, flags):
+        calls.append(flags)
+        return 1.0 + (0.5 if flags & expd.KF_FFT_RADIX4 else 0.0) - (0.25 if flags & expd.KF_TIME_SMEM else 0.0)
 
     t = A.Tuner(measure=fake)
     assert t.lookup(AC, expd.PREC_MIXED) is None
-    env = t.best(AC, expd.PREC_MIXED)
-    assert env == {"EXPD_TIME_KERNEL": "smem"} and len(calls) == 4
-    assert t.best(AC, expd.PREC_MIXED) == env and len(calls) == 4        # cached
+    flags = t.best(AC, expd.PREC_MIXED)
+    assert flags == expd.KF_TIME_SMEM and len(calls) == 4
+    assert t.best(AC, expd.PREC_MIXED) == flags and len(calls) == 4        # cached
     assert t.lookup(AC.with_(Nt=32), expd.PREC_MIXED) is None             # another shape
     e = t.table[A.shape_key(AC, expd.PREC_MIXED, "fp")]
     assert e["ms"] == 0.75 and len(e["trials"]) == 4 and e["choice"] == {"fft": "four_step", "time": "smem"}
 
 
 def test_table_roundtrip_and_validation(tmp_path):
-    t = A.Tuner(measure=lambda p, prec, solver, env: 2.0 if env else 1.0)
+    t = A.Tuner(measure=lambda p, prec, solver, flags: 2.0 if flags else 1.0)
     t.tune(HD, expd.PREC_MIXED)
     path = os.path.join(tmp_path, "tune.json")
     t.save(path)
     u = A.Tuner(measure=lambda *a: pytest.fail("must not measure"))
     u.load(path)
-    assert u.lookup(HD, expd.PREC_MIXED) == {}
-    with open(path, "w") as fh:
-        fh.write('{"k": {"env": {"LD_PRELOAD": "x"}}}')
-    with pytest.raises(ValueError):
-        u.load(path)
+    assert u.lookup(HD, expd.PREC_MIXED) == 0
+    for bad in ('{"k": {"env": {"LD_PRELOAD": "x"}}}', '{"k": {"flags": 64}}', '{"k": {"flags": true}}'):
+        with open(path, "w") as fh:
+            fh.write(bad)
+        with pytest.raises(ValueError):
+            u.load(path)
 
 
-def test_variant_env_sets_clears_and_restores(monkeypatch):
-    monkeypatch.setenv("EXPD_FFT_KERNEL", "radix4")
-    monkeypatch.delenv("EXPD_DST_TC", raising=False)
-    with A.variant_env({"EXPD_DST_TC": "0"}):
-        assert os.environ.get("EXPD_DST_TC") == "0"
-        assert "EXPD_FFT_KERNEL" not in os.environ
-        # the lock is held while the switches are set
-        assert not A._ENV_LOCK.acquire(blocking=False)
-    assert os.environ.get("EXPD_FFT_KERNEL") == "radix4"
-    assert "EXPD_DST_TC" not in os.environ
+def test_variants_travel_as_plan_flags_not_environment(monkeypatch):
+    # the tuned choice reaches the library through the scheme's kernel_flags
+    # bits of each plan: the process environment is never written, so plans
+    # created concurrently elsewhere are unaffected
+    for k in ("EXPD_FFT_KERNEL", "EXPD_TIME_KERNEL", "EXPD_DST_TC"):
+        monkeypatch.delenv(k, raising=False)
+    spec = expd.spec_from_problem(AC, precision=expd.PREC_MIXED)
+    tuned = A.with_flags(spec, expd.KF_TIME_SMEM | expd.KF_DST_FP64)
+    assert tuned.kernel_flags == expd.KF_TIME_SMEM | expd.KF_DST_FP64
+    assert spec.kernel_flags == 0 and A.with_flags(spec, None).kernel_flags == 0
+    g, o, s = expd._structs(tuned)
+    assert s.kernel_flags == tuned.kernel_flags
+    assert not any(k in os.environ for k in ("EXPD_FFT_KERNEL", "EXPD_TIME_KERNEL", "EXPD_DST_TC"))
 
 
-def test_variant_env_serialises_threads():
-    seen = []
+def test_tuner_is_thread_safe():
+    t = A.Tuner(measure=lambda p, prec, solver, flags: 1.0 + flags)
+    errs = []
 
-    def worker(v):
-        with A.variant_env({"EXPD_TIME_KERNEL": v}):
-            seen.append(os.environ.get("EXPD_TIME_KERNEL") == v)
+    def worker(i):
+        try:
+            q = AC.with_(Nt=16 + (i % 4))
+            t.tune(q, expd.PREC_MIXED)
+            assert t.lookup(q, expd.PREC_MIXED) is not None
+        except Exception as e:  # pragma: no cover - reported below
+            errs.append(e)
 
-    ts = [threading.Thread(target=worker, args=("smem" if i % 2 else "reg",)) for i in range(16)]
+    ts = [threading.Thread(target=worker, args=(i,)) for i in range(16)]
     for th in ts:
         th.start()
     for th in ts:
         th.join()
-    assert all(seen) and len(seen) == 16
+    assert not errs and len(t.table) == 4

@@ -128,3 +128,28 @@ def test_tc_heat_dirichlet_1024_full_mixed_gmres(expd):
     assert cls["dst_tc"]["count"] > 0 and cls["dst"]["count"] == 0, cls
     ref = O.sequential_solve(O.spec_of(p), u0, f)[1:]
     assert O.rel_error(host(U), ref) < p.tol, info
+
+
+def test_tc_cancel_in_flight_gives_up_waits_and_gpu_stays_usable(expd):
+    # Failure detection without a GPU fault: a cancel request set before the
+    # solve makes the tensor-core kernel's pipeline waits give up at once (the
+    # kernel waits, with a limit, for its own copies and MMAs, frees TMEM and
+    # records the give-up); the call returns EXPD_ERR_CANCELLED, and the next
+    # solve on the same plan runs normally and matches the oracle.
+    p = TC_CASES[1]
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(17)
+    u0 = rng.standard_normal(p.n)
+    f = rng.standard_normal((p.Nt,) + p.n)
+    ref = O.sequential_solve(sp, u0, f)[1:]
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-10, max_iter=100)) as plan:
+        plan.timing_enable(True)
+        plan.cancel()
+        with pytest.raises(expd.ExpdError) as ei:
+            plan.solve_gmres(dev(u0), dev(f), U)
+        assert ei.value.status == expd.ERR_CANCELLED
+        assert _counts(plan)["dst_tc"]["count"] > 0
+        plan.solve_gmres(dev(u0), dev(f), U)
+        assert _counts(plan)["dst_tc"]["count"] > 0
+    assert O.rel_error(host(U), ref) < 1e-9

@@ -41,6 +41,30 @@ def relmax(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
+def slice_relmax(U, ref):
+    """Element-wise error of every time slice relative to that slice's own
+    largest value, maximised over the slices: no single grid point of any
+    slice may be off by more than the bar it is held to.
+
+    A solve stopped at the workload's tolerance targets Sec. 7's norm
+    max_n ||e_n||_2 / max_n ||u_n||_2; a grid-point error spread like noise
+    over the slice exceeds its slice's L2 ratio by the field's peak-to-RMS
+    factor (measured up to about 4 on the Allen-Cahn fields), so at the
+    workload tolerance the element-wise bar is ELEMENTWISE_FACTOR * tol.  Runs
+    at the float64 parity bar (solver tol 1e-12 or below) are held to 1e-10
+    element-wise as well."""
+    d = np.abs(U - ref).reshape(U.shape[0], -1).max(axis=1)
+    r = np.abs(ref).reshape(ref.shape[0], -1).max(axis=1)
+    return float((d / np.maximum(r, 1e-300)).max())
+
+
+ELEMENTWISE_FACTOR = 10.0
+
+
+def elementwise_bar(tight, tol):
+    return 1e-10 if tight else ELEMENTWISE_FACTOR * tol
+
+
 def P(name, bc, n, order, nonlin="none", Nt=None, alpha=1e-2, a=None, c=0.1, dt=0.01, forcing=False, b=()):
     length = tuple(2 * math.pi if bc == "periodic" else 1.0 for _ in n)
     if a is None:
@@ -258,6 +282,16 @@ def solve_full(expd, p, precision, solver=None, tol=None):
     return u0, f, host(U), info
 
 
+_REF = {}
+
+
+def sequential_ref(p, u0, f):
+    """The oracle's sequential solution of a full-size workload, computed once per module."""
+    if p.name not in _REF:
+        _REF[p.name] = O.sequential_solve(O.spec_of(p), u0, f)[1:]
+    return _REF[p.name]
+
+
 def test_heat1d_full_exact_solution(expd):
     p = I.HEAT1D
     u0, f, U8, info8 = solve_full(expd, p, expd.PREC_FP64)          # the workload's tol 1e-8
@@ -269,7 +303,10 @@ def test_heat1d_full_exact_solution(expd):
                           / k**2 for k in range(1, 17)) for n in range(p.Nt)])
     assert O.rel_error(U8, exact) < p.tol
     assert O.rel_error(U, exact) < 1e-10
-    assert O.rel_error(U, O.sequential_solve(O.spec_of(p), u0)[1:]) < 1e-10
+    seq = O.sequential_solve(O.spec_of(p), u0)[1:]
+    assert O.rel_error(U, seq) < 1e-10
+    assert slice_relmax(U, seq) < 1e-10
+    assert slice_relmax(U8, seq) < elementwise_bar(False, p.tol)
     assert info["iterations"] <= 8
 
 
@@ -279,23 +316,109 @@ def test_allen_cahn_256_full(expd, prec):
     tight = prec == "fp64_tight"
     u0, f, U, info = solve_full(expd, p, expd.PREC_MIXED if prec == "mixed" else expd.PREC_FP64,
                                 tol=1e-13 if tight else None)
-    ref = O.sequential_solve(O.spec_of(p), u0)[1:]
-    assert O.rel_error(U, ref) < (1e-10 if tight else p.tol), info
+    ref = sequential_ref(p, u0, None)
+    bar = 1e-10 if tight else p.tol
+    assert O.rel_error(U, ref) < bar, info
+    assert slice_relmax(U, ref) < elementwise_bar(tight, p.tol), info
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+# The 512^2 x 256 order-6 Allen-Cahn workload: its tolerance 1e-8 on both
+# paths, and the float64 path held to the 1e-10 parity bar at solver tol 1e-12.
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp64_tight"])
 def test_allen_cahn_512_order6_full(expd, prec):
     p = I.ALLEN_CAHN_512_S6
-    u0, f, U, info = solve_full(expd, p, expd.PREC_FP64 if prec == "fp64" else expd.PREC_MIXED)
-    ref = O.sequential_solve(O.spec_of(p), u0)[1:]
-    assert O.rel_error(U, ref) < p.tol, info
+    tight = prec == "fp64_tight"
+    u0, f, U, info = solve_full(expd, p, expd.PREC_MIXED if prec == "mixed" else expd.PREC_FP64,
+                                tol=1e-12 if tight else None)
+    ref = sequential_ref(p, u0, None)
+    bar = 1e-10 if tight else p.tol
+    assert O.rel_error(U, ref) < bar, info
+    assert slice_relmax(U, ref) < elementwise_bar(tight, p.tol), info
 
 
-def test_heat_dirichlet_1024_full_gmres(expd):
+# The 1024^2 x 128 Dirichlet heat workload (s = 2, GMRES or BiCGStab, tol 1e-9):
+# the float64 path (float64 dense sine products and preconditioner) at the
+# workload's tolerance and at the 1e-10 parity bar (solver tol 1e-12), and the
+# mixed path (tensor-core sine transforms, float32 preconditioner inside
+# float64 residual refinement) at the workload's tolerance.
+@pytest.mark.parametrize("case", ["fp64_gmres", "fp64_tight_gmres", "mixed_gmres", "mixed_bicgstab"])
+def test_heat_dirichlet_1024_full(expd, case):
     p = I.HEAT_DIRICHLET_1024
-    u0, f, U, info = solve_full(expd, p, expd.PREC_FP64)
+    tight = "tight" in case
+    prec = expd.PREC_MIXED if case.startswith("mixed") else expd.PREC_FP64
+    solver = "bicgstab" if case.endswith("bicgstab") else "gmres"
+    u0, f = I.make_inputs(p)
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, precision=prec, max_iter=200,
+                                                 tol=1e-12 if tight else None)) as plan:
+        fn = plan.solve_bicgstab if solver == "bicgstab" else plan.solve_gmres
+        info = fn(dev(u0), dev(f), U)
+    Uh = host(U)
+    ref = sequential_ref(p, u0, f)
+    bar = 1e-10 if tight else p.tol
+    assert O.rel_error(Uh, ref) < bar, info
+    assert slice_relmax(Uh, ref) < elementwise_bar(tight, p.tol), info
+    if prec == expd.PREC_MIXED:
+        assert info["refinements"] >= 1, info
+
+
+@pytest.mark.parametrize("solver", ["gmres", "bicgstab"])
+@pytest.mark.parametrize("p", [c for c in CASES if c.nonlin == "none"], ids=[c.name for c in CASES if c.nonlin == "none"])
+def test_mixed_krylov_refinement_reaches_float64_accuracy(expd, p, solver):
+    # the float32 preconditioner's rounding (about eps32/alpha) limits only how
+    # fast the refinement restarts contract: the solution reaches the float64
+    # parity bar against sequential stepping
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(14)
+    u0 = rng.standard_normal(p.n)
+    f = rng.standard_normal((p.Nt,) + p.n)
+    ref = O.sequential_solve(sp, u0, f)[1:]
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-12, max_iter=400)) as plan:
+        fn = plan.solve_bicgstab if solver == "bicgstab" else plan.solve_gmres
+        info = fn(dev(u0), dev(f), U)
+    Uh = host(U)
+    assert O.rel_error(Uh, ref) < 1e-10, info
+    assert slice_relmax(Uh, ref) < 1e-10, info
+    assert info["refinements"] >= 1, info
+    assert info["final_measure"] <= 1e-12 / math.sqrt(p.Ns), info
+
+
+def test_info_phase_times(expd):
+    p = CASES[6]
+    rng = np.random.default_rng(15)
+    u0 = rng.standard_normal(p.n)
+    f = rng.standard_normal((p.Nt,) + p.n)
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, tol=1e-12)) as plan:
+        for fn in (plan.solve_fp, plan.solve_gmres, plan.solve_bicgstab):
+            info = fn(dev(u0), dev(f), U)
+            assert info["ms_setup"] > 0 and info["ms_iterate"] > 0 and info["ms_output"] > 0, info
+
+
+def test_time_limit_and_cancel_status(expd):
+    # a time limit that has run out stops the solve between iterations with
+    # EXPD_ERR_TIMEOUT; expd_plan_cancel stops the next solve with
+    # EXPD_ERR_CANCELLED (the request is consumed: the solve after it succeeds)
+    p = CASES[0].with_(alpha=0.3)
+    rng = np.random.default_rng(16)
+    u0 = rng.standard_normal(p.n)
+    f = rng.standard_normal((p.Nt,) + p.n)
     ref = O.sequential_solve(O.spec_of(p), u0, f)[1:]
-    assert O.rel_error(U, ref) < p.tol, info
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, tol=1e-13, max_iter=400, time_limit_ms=1e-6)) as plan:
+        for fn in (plan.solve_fp, plan.solve_gmres, plan.solve_bicgstab):
+            with pytest.raises(expd.ExpdError) as ei:
+                fn(dev(u0), dev(f), U)
+            assert ei.value.status == expd.ERR_TIMEOUT
+    with expd.plan_create(expd.spec_from_problem(p, tol=1e-13, max_iter=400)) as plan:
+        for fn in (plan.solve_fp, plan.solve_gmres, plan.solve_bicgstab):
+            plan.cancel()
+            with pytest.raises(expd.ExpdError) as ei:
+                fn(dev(u0), dev(f), U)
+            assert ei.value.status == expd.ERR_CANCELLED
+            fn(dev(u0), dev(f), U)
+            assert O.rel_error(host(U), ref) < 1e-10
 
 
 def test_footprint_matches_allocation(expd):
