@@ -63,6 +63,7 @@ class Spec:
     alpha: float
     order: int                   # s in 1..6
     b: Tuple[float, ...] = ()    # advection velocity: L = a*Lap - b.grad - c (periodic only)
+    nl_form: str = "if"          # "if" (integrating factor, Eq. (6.1)) | "etd1" (see etd1_step)
 
     @property
     def ndim(self):
@@ -76,7 +77,7 @@ class Spec:
 def spec_of(p) -> Spec:
     """Build a Spec from any object with the same attribute names."""
     return Spec(p.bc, tuple(p.n), tuple(p.length), p.a, p.c, p.nonlin, p.dt, p.Nt,
-                p.alpha, p.order, tuple(getattr(p, "b", ()) or ()))
+                p.alpha, p.order, tuple(getattr(p, "b", ()) or ()), getattr(p, "nl_form", "if"))
 
 
 def has_advection(sp: Spec) -> bool:
@@ -179,6 +180,40 @@ def apply_A_power(sp: Spec, u: np.ndarray, j: int) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
+# phi_1 and the first-order exponential time differencing (ETD1) step.
+# Sec. 6 names an ETD-based treatment of the nonlinear term as the
+# alternative to the integrating factor it develops; ETD1 is its first-order
+# member: u_n = A u_{n-1} + dt phi_1(dt L_h) N(u_{n-1}), phi_1(z) = (e^z - 1)/z.
+# ---------------------------------------------------------------------------
+def phi1(z: np.ndarray) -> np.ndarray:
+    """phi_1(z) = (e^z - 1)/z, phi_1(0) = 1; expm1 keeps small |z| accurate."""
+    z = np.asarray(z)
+    out = np.ones(z.shape, dtype=np.result_type(z, np.float64))
+    nz = z != 0
+    out[nz] = np.expm1(z[nz]) / z[nz]
+    return out
+
+
+def apply_phi1(sp: Spec, u: np.ndarray) -> np.ndarray:
+    """dt phi_1(dt L_h) u, applied in L_h's eigenbasis."""
+    mu = spatial_eigenvalues(sp)
+    out = from_eigen(sp, sp.dt * phi1(sp.dt * mu) * to_eigen(sp, u))
+    return out if np.iscomplexobj(u) else out.real
+
+
+def etd1_step(sp: Spec, u_prev: np.ndarray) -> np.ndarray:
+    """u_n = A u_{n-1} + dt phi_1(dt L_h) N(u_{n-1}) (explicit in N)."""
+    return apply_A_power(sp, u_prev, 1) + apply_phi1(sp, nonlinearity(sp, u_prev))
+
+
+def _check_etd1(sp: Spec, f) -> None:
+    if sp.order != 1:
+        raise ValueError("ETD1 is a first-order scheme (order 1)")
+    if f is not None:
+        raise ValueError("the ETD1 form takes no source term")
+
+
+# ---------------------------------------------------------------------------
 # Nonlinearity and the pointwise implicit solve of the IF scheme (Eq. (6.1)).
 # ---------------------------------------------------------------------------
 def nonlinearity(sp: Spec, u: np.ndarray) -> np.ndarray:
@@ -234,6 +269,11 @@ def sequential_solve(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None,
     u_n - beta dt N(u_n) = sum_j a_j A^j u_{n-j} + beta dt f(t_n)."""
     U = np.zeros((sp.Nt + 1,) + sp.n)
     U[0] = u0
+    if sp.nl_form == "etd1" and sp.nonlin != "none":
+        _check_etd1(sp, f)
+        for n in range(1, sp.Nt + 1):
+            U[n] = etd1_step(sp, U[n - 1])
+        return U
     first = 1
     if U_start is not None:
         U[: sp.order] = U_start
@@ -274,7 +314,15 @@ def rhs_known(sp: Spec, U_start: np.ndarray, f: Optional[np.ndarray]) -> np.ndar
         for j in range(1, s + 1):
             if n - j < s:
                 b[i] += a[j - 1] * apply_A_power(sp, U_start[n - j], j)
+    if is_etd1(sp):
+        # ETD1: row 0 also carries the known dt phi_1(dt L_h) N(u_0)
+        _check_etd1(sp, f)
+        b[0] += apply_phi1(sp, nonlinearity(sp, U_start[0]))
     return b
+
+
+def is_etd1(sp: Spec) -> bool:
+    return sp.nl_form == "etd1" and sp.nonlin != "none"
 
 
 def apply_R(sp: Spec, V: np.ndarray) -> np.ndarray:
@@ -291,7 +339,13 @@ def apply_R(sp: Spec, V: np.ndarray) -> np.ndarray:
 
 def residual(sp: Spec, V: np.ndarray, b: np.ndarray) -> np.ndarray:
     """r = f_s + beta dt N(v) - R_s v (Eq. (3.2); the lagged nonlinear term of
-    Eq. (7.4) enters with the current iterate)."""
+    Eq. (7.4) enters with the current iterate).  ETD1: row i >= 1 carries
+    dt phi_1(dt L_h) N(v_{i-1}) instead (the previous slice, explicit)."""
+    if is_etd1(sp):
+        r = b - apply_R(sp, V)
+        for i in range(1, sp.Ns):
+            r[i] += apply_phi1(sp, nonlinearity(sp, V[i - 1]))
+        return r
     _, beta = bdf_float(sp.order)
     return b + beta * sp.dt * nonlinearity(sp, V) - apply_R(sp, V)
 
@@ -622,6 +676,18 @@ def dense_A(sp: Spec) -> np.ndarray:
     return scipy.linalg.expm(sp.dt * dense_Lh(sp))
 
 
+def dense_phi1(sp: Spec) -> np.ndarray:
+    """dt phi_1(dt L_h) from one expm of the augmented matrix
+    [[dt L_h, I], [0, 0]], whose top-right block is sum_k (dt L_h)^k/(k+1)!
+    = phi_1(dt L_h): independent of the eigen-symbol path."""
+    Z = sp.dt * dense_Lh(sp)
+    M = Z.shape[0]
+    aug = np.zeros((2 * M, 2 * M))
+    aug[:M, :M] = Z
+    aug[:M, M:] = np.eye(M)
+    return sp.dt * scipy.linalg.expm(aug)[:M, M:]
+
+
 def shift_matrix(N: int, j: int, alpha: float = 0.0) -> np.ndarray:
     """C_j (alpha = 0) or C_j^alpha: ones where row - col = j+1, and alpha on
     the wrap-around entries row - col = j+1-N (top-right corner).
@@ -676,6 +742,8 @@ def dense_solve(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None) -> np.
     a, _ = bdf_float(sp.order)
     A = dense_A(sp)
     M = A.shape[0]
+    if is_etd1(sp):
+        return _dense_solve_etd1(sp, u0, f, A)
     # dense startup ramp u_1..u_{s-1}
     Us = [u0.ravel().copy()]
     for n in range(1, sp.order):
@@ -700,6 +768,30 @@ def dense_solve(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None) -> np.
             if np.max(np.abs(dv)) < 1e-15:
                 break
     return assemble(sp, U_start, v.reshape((sp.Ns,) + sp.n))
+
+
+def _dense_solve_etd1(sp: Spec, u0: np.ndarray, f, A: np.ndarray) -> np.ndarray:
+    """ETD1 as one dense all-at-once system: R_1 v - (C_0 (x) Phi) N(v) = b
+    with b_0 = A u_0 + Phi N(u_0), Phi = dt phi_1(dt L_h) from dense_phi1,
+    solved by Newton with the dense Jacobian from v = 0."""
+    _check_etd1(sp, f)
+    Phi = dense_phi1(sp)
+    M = A.shape[0]
+    Ns = sp.Ns
+    R = dense_R(sp)
+    S = np.kron(shift_matrix(Ns, 0), Phi)
+    u0v = u0.ravel()
+    b = np.zeros(Ns * M)
+    b[:M] = A @ u0v + Phi @ (u0v - u0v**3)
+    v = np.zeros(Ns * M)
+    for _ in range(60):
+        F = R @ v - S @ (v - v**3) - b
+        J = R - S @ np.diag(1.0 - 3.0 * v**2)
+        dv = np.linalg.solve(J, F)
+        v = v - dv
+        if np.max(np.abs(dv)) < 1e-15:
+            break
+    return assemble(sp, u0[None], v.reshape((Ns,) + sp.n))
 
 
 def _dense_pointwise(sp: Spec, w: np.ndarray, bdt: float) -> np.ndarray:

@@ -418,3 +418,73 @@ def check_linear_guess_is_homogeneous_solution():
         V = O.linear_guess(sp, U_start)
         worst = max(worst, O.rel_error(V, ref[sp.order:]))
     return worst
+
+
+# --- ETD1 (phi_1) ------------------------------------------------------------
+def etd_spec(bc="periodic", n=(8,), Nt=6, a=0.3, c=0.1, dt=0.05, alpha=0.05):
+    sp = spec(bc, n, a=a, c=c, nonlin="allen_cahn", dt=dt, Nt=Nt, alpha=alpha, order=1)
+    return O.Spec(sp.bc, sp.n, sp.length, sp.a, sp.c, sp.nonlin, sp.dt, sp.Nt, sp.alpha, sp.order, (), "etd1")
+
+
+def check_phi1_scalar():
+    """phi_1(z) = (e^z - 1)/z against a 40-digit evaluation (decimal), with
+    phi_1(0) = 1, over arguments from -700 to 1 including tiny ones."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 40
+    zs = np.array([-700.0, -50.0, -3.0, -1.0, -1e-3, -1e-9, -1e-300, 0.0, 1e-12, 1e-4, 0.5, 1.0])
+    got = O.phi1(zs)
+    worst = 0.0
+    for z, g in zip(zs, got):
+        dz = Decimal(float(z))
+        if abs(z) < 1e-20:
+            want = 1 + dz / 2          # the series: 1 + z/2 + z^2/6 + ...
+        else:
+            want = (dz.exp() - 1) / dz
+        worst = max(worst, abs(float((Decimal(float(g)) - want) / want)))
+    return worst
+
+
+def check_phi1_vs_dense(sp, seed=12):
+    """dt phi_1(dt L_h) u by the eigen-symbol path against the top-right block
+    of the dense expm of [[dt L_h, I], [0, 0]]."""
+    u = rng_field(sp, seed)
+    ref = (O.dense_phi1(sp) @ u.ravel()).reshape(sp.n)
+    return np.abs(O.apply_phi1(sp, u) - ref).max() / np.abs(ref).max()
+
+
+def check_etd1_sequential_vs_dense(sp, seed=13):
+    """ETD1 stepping (eigen symbols) against the dense all-at-once system
+    R_1 v - (C_0 (x) Phi) N(v) = b solved by Newton with dense expm operators."""
+    u0 = 0.6 * np.tanh(rng_field(sp, seed))
+    U = O.sequential_solve(sp, u0)
+    D = O.dense_solve(sp, u0)
+    return np.abs(U - D).max() / np.abs(D).max()
+
+
+def check_etd1_order(T=0.4, n=16, a=0.05):
+    """ETD1 on the semi-discrete 1D periodic Allen-Cahn system against
+    scipy's DOP853 at tolerance 1e-12 (dense L_h): the observed convergence
+    order from Nt = 40 -> 80 (must be ~ 1)."""
+    import scipy.integrate
+    x = np.arange(n) * 2 * math.pi / n
+    u0 = 0.5 * np.sin(x) + 0.2 * np.cos(2 * x)
+    base = O.Spec("periodic", (n,), (2 * math.pi,), a, 0.0, "allen_cahn", T / 40, 40, 1e-3, 1, (), "etd1")
+    L = O.dense_Lh(base)
+    sol = scipy.integrate.solve_ivp(lambda t, u: L @ u + u - u**3, (0.0, T), u0, method="DOP853",
+                                    rtol=1e-12, atol=1e-14)
+    ref = sol.y[:, -1]
+    errs = []
+    for Nt in (40, 80):
+        sp = O.Spec("periodic", (n,), (2 * math.pi,), a, 0.0, "allen_cahn", T / Nt, Nt, 1e-3, 1, (), "etd1")
+        U = O.sequential_solve(sp, u0)
+        errs.append(np.abs(U[-1] - ref).max())
+    return math.log2(errs[0] / errs[1])
+
+
+def check_etd1_richardson_reaches_sequential(sp, seed=14, iters=80):
+    """The lagged Exp-ParaDiag fixed point of the ETD1 system (residual with
+    N of the previous slice) reaches the sequential ETD1 solution."""
+    u0 = 0.6 * np.tanh(rng_field(sp, seed))
+    ref = O.sequential_solve(sp, u0)
+    res = O.richardson(sp, u0, None, max_iter=iters, tol=1e-15)
+    return O.rel_error(res.U[1:], ref[1:])

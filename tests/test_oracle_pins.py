@@ -312,3 +312,34 @@ def test_linear_guess_reaches_the_same_fixed_point_one_sweep_sooner():
     assert O.rel_error(rl.U[1:], rz.U[1:]) < 1e-12
     for k in range(1, 5):
         assert rl.history[k - 1] < 3.0 * rz.history[k]
+
+
+# ------------------------------------------------------------------- ETD1 --
+# u_n = A u_{n-1} + dt phi_1(dt L_h) N(u_{n-1}), the first-order ETD form of
+# the nonlinear term that Sec. 6 names beside its integrating-factor form.
+def test_phi1_scalar_against_high_precision():
+    assert C.check_phi1_scalar() < 4e-16
+
+
+@pytest.mark.parametrize("sp", [C.etd_spec("periodic", (8,)), C.etd_spec("dirichlet", (7,)),
+                                C.etd_spec("periodic", (4, 6)), C.etd_spec("dirichlet", (5, 4))],
+                         ids=["p1d", "d1d", "p2d", "d2d"])
+def test_phi1_matches_dense_augmented_expm(sp):
+    assert C.check_phi1_vs_dense(sp) < 1e-12
+
+
+@pytest.mark.parametrize("sp", [C.etd_spec("periodic", (8,)), C.etd_spec("dirichlet", (5, 4), Nt=5)],
+                         ids=["p1d", "d2d"])
+def test_etd1_sequential_equals_dense_all_at_once(sp):
+    assert C.check_etd1_sequential_vs_dense(sp) < 1e-12
+
+
+def test_etd1_first_order_convergence():
+    p = C.check_etd1_order()
+    assert abs(p - 1.0) < 0.1, p
+
+
+@pytest.mark.parametrize("sp", [C.etd_spec("periodic", (8,), Nt=10), C.etd_spec("dirichlet", (6, 5), Nt=8)],
+                         ids=["p1d", "d2d"])
+def test_etd1_richardson_reaches_sequential(sp):
+    assert C.check_etd1_richardson_reaches_sequential(sp) < 1e-12

@@ -178,3 +178,39 @@ def test_planted_linear_guess_power_is_caught(monkeypatch):
         return np.stack([E.apply_A_power(sp, u_last, k) for k in range(sp.Ns)])
     patch(monkeypatch, "linear_guess", linear_guess)
     assert C.check_linear_guess_is_homogeneous_solution() > 1e-6
+
+
+# ------------------------------------------------------------------- ETD1 --
+ETD_P = C.etd_spec("periodic", (8,), Nt=10)
+ETD_D = C.etd_spec("dirichlet", (5, 4), Nt=5)
+
+
+@pytest.mark.parametrize("kind", ["phi_is_one", "no_dt"])
+def test_planted_phi1_mistakes_are_caught(monkeypatch, kind):
+    def apply_phi1(sp, u):
+        mu = E.spatial_eigenvalues(sp)
+        sym = np.ones_like(mu) if kind == "phi_is_one" else E.phi1(sp.dt * mu)
+        scale = sp.dt if kind == "phi_is_one" else 1.0
+        return E.from_eigen(sp, scale * sym * E.to_eigen(sp, u)).real
+    patch(monkeypatch, "apply_phi1", apply_phi1)
+    assert max(C.check_phi1_vs_dense(ETD_P), C.check_phi1_vs_dense(ETD_D)) > 1e-3
+
+
+def test_planted_etd1_nonlinearity_at_the_propagated_state_is_caught(monkeypatch):
+    def etd1_step(sp, u_prev):
+        w = E.apply_A_power(sp, u_prev, 1)
+        return w + E.apply_phi1(sp, E.nonlinearity(sp, w))     # N(A u) instead of N(u)
+    patch(monkeypatch, "etd1_step", etd1_step)
+    assert C.check_etd1_sequential_vs_dense(ETD_P) > 1e-6
+
+
+def test_planted_etd1_residual_on_the_same_slice_is_caught(monkeypatch):
+    orig = E.residual
+
+    def residual(sp, V, b):
+        r = b - E.apply_R(sp, V)
+        for i in range(1, sp.Ns):
+            r[i] += E.apply_phi1(sp, E.nonlinearity(sp, V[i]))  # slice i instead of i - 1
+        return r if E.is_etd1(sp) else orig(sp, V, b)
+    patch(monkeypatch, "residual", residual)
+    assert C.check_etd1_richardson_reaches_sequential(ETD_P) > 1e-6
