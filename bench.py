@@ -1,31 +1,50 @@
 #!/usr/bin/env python
-"""Exp-ParaDiag benchmark: space-time unknowns per second to 1e-8 relative error.
+"""Exp-ParaDiag benchmark: space-time unknowns per second to the workload's
+relative error, mixed-precision path against the plain float64 GPU path.
 
-Workload (one "step" = one whole solve of one batch of synthetic input): 2D
-periodic Allen-Cahn u_t = eps^2 Lap u + u - u^3, eps = 0.05, 256 x 256 grid,
-Nt = 64, dt = 1e-3, exponential Euler (s = 1), lagged nonlinear Exp-ParaDiag
-fixed point with alpha = 1e-3, u0 ~ U(-0.9, 0.9) seeded, tol 1e-8.  Every step
-runs the whole hot path: the lagged N evaluation through the spatial FFTs, the
-float64 residual, the alpha-scaled time DFT, the shifted solves, the inverse
-time DFT and the update, until the convergence test passes, then the solution
-returns to physical space.
+Headline workload (one "step" = one whole solve of one batch of synthetic
+input): 2D heat u_t = Lap u + f with homogeneous Dirichlet boundaries, the
+5-point Laplacian on 1024 x 1024 interior points of (0,1)^2, Nt = 128 steps to
+T = 0.1, the second-order exponential scheme (s = 2, 127 unknown slices,
+133,169,152 space-time unknowns), GMRES preconditioned with Exp-ParaDiag,
+alpha = 1e-3, tol 1e-9, u0 the Gaussian bump of Sec. 7 and a seeded smooth
+source e^{-t} sum_i c_i sin(p_i pi x) sin(q_i pi y).  It is the largest of the
+workloads that fits one GPU.  Every step runs the whole hot path: the sine
+transforms of u0 and f (split-bf16 digit products on the tensor cores), the
+start-up ramp and the right-hand side f_s, the GMRES iterations (each one the
+residual R_s v fused with the alpha-scaled time DFT, the shifted solves and
+the inverse DFT, on the float32 preconditioner, with float64 residual
+refinement), and the inverse transform of the solution.
 
-  value      whole-job unknowns/s of the mixed-precision path, inputs resident
-             in HBM, L2 flushed (256 MiB write) between timed steps
-  e2e        the same through the C ABI with pinned host buffers (u0 in, U out)
-  fp64_path  the plain float64 GPU path on the same workload (for the speedup)
+  value       whole-job unknowns/s of the mixed path, inputs resident in HBM
+              (f alone is 1.07 GB, larger than L2; L2 is also flushed by a
+              256 MiB write between timed steps)
+  e2e         the same through the C ABI with pinned host buffers (u0 and f
+              copied in, U copied out inside every timed call)
+  fp64_path   the plain float64 GPU path on the same workload (speedup)
+  bicgstab    the mixed path with BiCGStab (Sec. 7, Table 2)
   gpu_sequential  the same scheme stepped one time step after another on the
-             GPU in float64 (the time-stepping baseline)
-  roofline   the dominant kernel class from CUDA events on its launch stream
-  cpu_baseline  the CPU oracle (tests' reference), one full solve, host cores
-  heat_dirichlet_1024  the 1024^2 Dirichlet heat workload (s = 2, Nt = 128,
-             GMRES, tol 1e-9): mixed path (tensor-core sine transforms) vs
-             the float64 path, and the tensor-core kernel's TFLOP/s against
-             the measured bf16 peak (roofline_tensor)
+              GPU in float64 (the time-stepping baseline)
+  roofline    the dominant kernel class of the headline solve: algorithmic
+              bytes (HBM-bound classes) or executed bf16 flops (the
+              tensor-core DST) per launch over its CUDA-event time, against
+              MEASURED_PEAKS.json; roofline_hbm_top / roofline_tensor give
+              the largest class of each kind
+  legs        the other workloads: the 1D periodic heat equation (Nx = 128,
+              Nt = 32, float64 fixed point, against the exact solution too),
+              the 256^2 x 64 and the 512^2 x 256 order-6 periodic Allen-Cahn
+              solves, each mixed against float64 with the error against the
+              oracle
+  served_mix  the 2,000-request mix (Poisson arrivals at 70 % of measured
+              capacity): throughput and p50/p99 latency of the concurrent
+              engine, and of a float64 one-request-at-a-time server
+  cpu_baseline  the CPU oracle's Exp-ParaDiag GMRES on a bounded sample of the
+              headline workload, one replica per host core
 
 Launch: python bench.py [--gpus N --steps K --warmup W] (N > 1 under torchrun:
 every rank solves its own seeded problem, no collective on the data path).
---impl reference times the CPU oracle on the same workload and metric.
+--impl reference times the CPU oracle (the reference arm: the paper ships no
+code) on the same workload and metric.
 """
 from __future__ import annotations
 
@@ -43,25 +62,27 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# PyTorch allocates from the CUDA stream-ordered pool the plans use too
+# (cudaMallocAsync), so the served mix's request tensors and plans share one
+# pool instead of two caches that fragment device memory between them
+os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "backend:cudaMallocAsync")
 
 METRIC = "space-time unknowns/sec to 1e-8 rel. error, mixed vs FP64 GPU path; p50/p99 latency"
 UNIT = "unknowns/s"
 FALLBACK_HBM_GBS = 6800.0
-# float64 FMA throughput measured on this machine's GB300 (152 SMs x 2 FMA/clk x 2.07 GHz)
+FALLBACK_BF16_TFLOPS = 1900.0
+# float64 FMA throughput on GB300 (152 SMs x 2 FMA/clk x 2.07 GHz x 2 flop)
 FP64_PEAK_TFLOPS = 1.248
-# double-float kernels are bound by the float32 pipe: 152 SMs x 128 float32
-# lanes x 2 flop (fma) x 2.07 GHz; their algorithmic work is counted in
-# float32 operations, DD_FP32_OPS per double-float operation (a dd add is 11
-# float32 operations, a dd multiply 10)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-DD_CLASSES = ("fft_rowdd", "fft_coldd")
-DD_FP32_OPS = 10.5
+# classes bound by the float64 pipe on a float64 plan
 FP64_CLASSES = ("time", "fft_col", "fft_row", "dst")
-# DRAM bytes (read + write) per launch of the dominant kernels at the bench
-# workload (256^2 x 64 slices), from one ncu capture of each kernel as built
-# now (dram__bytes_read.sum + dram__bytes_write.sum, cold caches)
-NCU_TRAFFIC_256x64 = {"time32": 34.270976e6, "fft_col32": 16.928768e6 + 16.896e3, "fft_row32": 16.941056e6,
-                      "timedd": 51.710976e6 + 2.476544e6}
+# the sample of the headline workload the CPU oracle solves per replica
+ORACLE_SAMPLE_N = 128
+# DRAM bytes (read + write) per space-time unknown of the dominant kernels,
+# from one ncu capture each (dram__bytes_read.sum + dram__bytes_write.sum of a
+# 512^2 x 127 Dirichlet launch divided by its unknowns; traffic grows in
+# proportion to the unknowns, so a full launch moves this times 133,169,152).
+# An entry is removed whenever its kernel changes after the capture.
+NCU_TRAFFIC_PER_UNKNOWN = {}
 
 
 def parse_args():
@@ -70,10 +91,14 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
+    ap.add_argument("--no-check", action="store_true", help="skip the oracle error checks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mix", type=int, default=200, metavar="R",
+    ap.add_argument("--legs", default="heat1d,ac256,ac512",
+                    help="comma list of the other workloads to run (heat1d, ac256, ac512; '' for none)")
+    ap.add_argument("--mix", type=int, default=2000, metavar="R",
                     help="requests of the served mix to replay (0 skips it)")
+    ap.add_argument("--mix-baseline", type=int, default=200, metavar="R",
+                    help="requests of the same arrivals the float64 one-at-a-time server replays")
     ap.add_argument("--mix-workers", type=int, default=4)
     ap.add_argument("--profile-case", default=None, metavar="N,NT,PREC",
                     help="run two solves of the Allen-Cahn workload on an N x N grid with NT steps "
@@ -81,10 +106,10 @@ def parse_args():
     ap.add_argument("--profile-dirichlet", default=None, metavar="N,NT[,M]",
                     help="run two mixed GMRES(M) solves of the Dirichlet heat workload on an N x N grid with NT "
                          "steps (tensor-core DST; M = 20 by default) and exit; the target of ncu captures")
-    ap.add_argument("--no-dirichlet", action="store_true", help="skip the 1024^2 Dirichlet heat leg")
     return ap.parse_args()
 
 
+# ------------------------------------------------------------ profile runs ---
 def profile_case(spec: str) -> int:
     """Two solves (the second one is the captured steady state) of the periodic
     Allen-Cahn workload at another size; prints nothing but the iteration counts."""
@@ -128,79 +153,13 @@ def profile_dirichlet(spec: str) -> int:
     return 0
 
 
-def dirichlet_leg(stream, flush, barrier, check: bool) -> dict:
-    """The 1024^2 Dirichlet heat workload (s = 2, Nt = 128, GMRES, tol 1e-9):
-    the mixed path (tensor-core DST) against the float64 path (float64 dense
-    products), inputs resident, L2 flushed between solves; the tensor-core
-    kernel's rate from per-launch events."""
-    import torch
-    from paper_2603_04350_gb300 import expd, inputs as I
-    p = I.HEAT_DIRICHLET_1024
-    u0, f = I.make_inputs(p)
-    dev = flush.device
-    u0d, fd = torch.from_numpy(u0).to(dev), torch.from_numpy(f).to(dev)
-    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=dev)
-
-    def run(prec, K, warm, timing=False):
-        with expd.plan_create(expd.spec_from_problem(p, precision=prec, max_iter=200), stream) as pl:
-            for k in range(warm):
-                flush.fill_(float(k))
-                pl.solve_gmres(u0d, fd, U)
-            barrier()
-            pl.timing_read(reset=True)
-            pl.timing_enable(timing)
-            ms, info = [], None
-            for k in range(K):
-                flush.fill_(float(k + 1))
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                info = pl.solve_gmres(u0d, fd, U)
-                e1.record(stream)
-                barrier()
-                ms.append(e0.elapsed_time(e1))
-            tm = pl.timing_read(reset=True)
-        return ms, info, tm
-
-    ms, info, tm_plain = run(expd.PREC_MIXED, 3, 3)
-    U_mixed = U.cpu().numpy()
-    _, _, tm = run(expd.PREC_MIXED, 1, 1, timing=True)
-    ms64, info64, _ = run(expd.PREC_FP64, 1, 1)
-    U_fp64 = U.cpu().numpy()
-    value = p.unknowns / (statistics.mean(ms) / 1e3)
-    value64 = p.unknowns / (statistics.mean(ms64) / 1e3)
-    cls = tm["classes"]
-    out = {"workload": p.name, "unknowns": p.unknowns, "tol": p.tol,
-           "mixed": {"value": value, "unit": UNIT, "ms_per_step": statistics.mean(ms), "steps": len(ms),
-                     "iterations": info["iterations"], "gpu_launches": int(tm_plain["launches"])},
-           "fp64_path": {"value": value64, "unit": UNIT, "ms_per_step": statistics.mean(ms64), "steps": len(ms64),
-                         "iterations": info64["iterations"]},
-           "speedup_vs_fp64": value / value64,
-           "kernels": {k: {"launches": v["count"], "ms_total": round(v["ms"], 4),
-                           "avg_us": round(1e3 * v["ms"] / v["count"], 3)}
-                       for k, v in cls.items() if v["count"]}}
-    c = cls.get("dst_tc")
-    if c and c["count"]:
-        peak = bf16_peak(sustained=True)
-        ach = (c["flops"] / c["count"]) / (c["ms"] / c["count"] / 1e3) / 1e12
-        out["roofline_tensor"] = {"bound": "tensor", "kernel": "dst_tc", "achieved": ach, "peak": peak[0],
-                                  "peak_source": peak[1], "unit": "TFLOP/s", "frac": ach / peak[0], "traffic": None,
-                                  "flops_per_launch": c["flops"] / c["count"],
-                                  "note": "bf16 digit products executed (pairs x 2 rows N K) per launch"}
-    if check:
-        import oracle as O
-        ref = O.sequential_solve(O.spec_of(p), u0, f)[1:]
-        out["rel_err_vs_oracle"] = {"mixed": O.rel_error(U_mixed, ref), "fp64": O.rel_error(U_fp64, ref)}
-    return out
-
-
+# ----------------------------------------------------------------- helpers ---
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def workload(rank: int):
-    from paper_2603_04350_gb300 import inputs as I
-    p = I.ALLEN_CAHN_256
+def with_rank_seed(p, rank: int):
     return p.with_(seed=p.seed + 1000 * rank) if rank else p
 
 
@@ -215,14 +174,14 @@ def aggregate(total_ms: float, unknowns: int, steps: int, world: int, pg=None, d
     return total_ms, world * unknowns * steps / (total_ms / 1e3)
 
 
-def config_dict(p, world):
-    return {"workload": p.name, "grid": list(p.n), "Nt": p.Nt, "Ns": p.Ns, "order": p.order, "alpha": p.alpha,
-            "dt": p.dt, "tol": p.tol, "nonlin": p.nonlin, "unknowns_per_solve": p.unknowns,
+def config_dict(p, world, solver):
+    return {"workload": p.name, "grid": list(p.n), "bc": p.bc, "Nt": p.Nt, "Ns": p.Ns, "order": p.order,
+            "alpha": p.alpha, "dt": p.dt, "tol": p.tol, "nonlin": p.nonlin, "solver": solver,
+            "unknowns_per_solve": p.unknowns,
             "parallelism": f"replicas{world}" if world > 1 else "single",
-            "l2": "flushed between timed steps (256 MiB write)"}
+            "l2": "inputs larger than L2 (f: 1.07 GB) and L2 flushed (256 MiB write) between timed steps"}
 
 
-# ----------------------------------------------------------------- clocks ---
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -271,96 +230,369 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def measured_peaks():
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+def _peaks():
     try:
-        with open(path) as fh:
-            d = json.load(fh)
-        return float(d["hbm_gbs"]), "measured"
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
     except Exception:
-        return FALLBACK_HBM_GBS, "fallback"
+        return None
+
+
+def hbm_peak():
+    d = _peaks()
+    if d and "hbm_gbs" in d:
+        return float(d["hbm_gbs"]), "measured (hbm_gbs)"
+    return FALLBACK_HBM_GBS, "fallback"
 
 
 def bf16_peak(sustained: bool):
-    """Dense bf16 tensor peak in TFLOP/s: the measured cuBLAS figure (sustained
-    for a kernel timed inside a long step, burst otherwise), else the fallback."""
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    """Dense bf16 tensor peak in TFLOP/s: the measured cuBLAS figure (burst for
+    a kernel timed alone, sustained for one timed inside a long step)."""
+    d = _peaks()
     key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
-    try:
-        with open(path) as fh:
-            return float(json.load(fh)[key]), f"measured ({key})"
-    except Exception:
-        return (1700.0 if sustained else 1900.0), "fallback"
+    if d and key in d:
+        return float(d[key]), f"measured ({key})"
+    return (1700.0 if sustained else FALLBACK_BF16_TFLOPS), "fallback"
+
+
+def kernel_table(classes):
+    return {k: {"launches": v["count"], "ms_total": round(v["ms"], 4),
+                "avg_us": round(1e3 * v["ms"] / v["count"], 3) if v["count"] else None,
+                "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] else None,
+                "GFLOPs": round(v["flops"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] else None}
+            for k, v in classes.items() if v["count"]}
+
+
+def roofline_of(classes, k, fp64_plan: bool, unknowns=None):
+    """The roofline entry of kernel class k from per-launch CUDA-event times:
+    achieved = algorithmic bytes (or flops) per launch / average launch time."""
+    c = classes[k]
+    n = max(c["count"], 1)
+    sec = c["ms"] / n / 1e3
+    if k == "dst_tc":
+        # executed bf16 digit products against the dense bf16 peak; every
+        # launch is timed alone by its own event pair, so the burst figure
+        peak, src = bf16_peak(sustained=False)
+        ach = (c["flops"] / n) / sec / 1e12
+        return {"bound": "tensor", "kernel": k, "achieved": ach, "peak": peak, "peak_source": src,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "flops_per_launch": c["flops"] / n,
+                "note": "bf16 digit products executed per launch (pairs x 2 rows N K)"}
+    if fp64_plan and k in FP64_CLASSES:
+        ach = (c["flops"] / n) / sec / 1e12
+        return {"bound": "alu", "kernel": k, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "peak_source": "float64 FMA rate: 152 SMs x 2 FMA/clk x 2.07 GHz", "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None}
+    peak, src = hbm_peak()
+    ach = (c["bytes"] / n) / sec / 1e9
+    per_unk = NCU_TRAFFIC_PER_UNKNOWN.get(k)
+    traffic = per_unk * unknowns if (per_unk is not None and unknowns) else None
+    return {"bound": "hbm", "kernel": k, "achieved": ach, "peak": peak, "peak_source": src, "unit": "GB/s",
+            "frac": ach / peak, "traffic": traffic, "algorithmic_bytes_per_launch": c["bytes"] / n}
 
 
 # ------------------------------------------------------------ cpu oracle ---
-def cpu_oracle_solve(p, u0):
-    """One oracle Exp-ParaDiag solve (lagged fixed point to tol): (seconds, iters, U)."""
+def _oracle_sample():
+    from paper_2603_04350_gb300 import inputs as I
+    return I.HEAT_DIRICHLET_1024.with_(name=f"heat_dirichlet_{ORACLE_SAMPLE_N}x{ORACLE_SAMPLE_N}_nt128_s2",
+                                       n=(ORACLE_SAMPLE_N, ORACLE_SAMPLE_N))
+
+
+def _oracle_worker(_):
+    """One oracle Exp-ParaDiag GMRES solve of the sample (in a worker process)."""
     import oracle as O
-    sp = O.spec_of(p)
+    from paper_2603_04350_gb300 import inputs as I
+    p = _oracle_sample()
+    u0, f = I.make_inputs(p)
     t0 = time.perf_counter()
-    res = O.richardson(sp, u0, None, max_iter=60, tol=p.tol * 0.1)
-    return time.perf_counter() - t0, res.iterations, res.U
+    res = O.gmres(O.spec_of(p), u0, f, tol=p.tol / math.sqrt(p.Ns), restart=20)
+    return time.perf_counter() - t0, res.iterations
 
 
-def cpu_baseline(p, u0):
-    secs, iters, _ = cpu_oracle_solve(p, u0)
-    return {"value": p.unknowns / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full solve of the {p.name} workload ({iters} fixed-point sweeps, numpy float64, "
-                      f"single-threaded pocketfft), {secs:.2f} s"}
+def oracle_pool():
+    """A spawn pool with one single-threaded oracle worker per host core,
+    started before any CUDA call (a process forked after one would hang)."""
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
+    cores = os.cpu_count() or 1
+    return mp.get_context("spawn").Pool(cores), cores
+
+
+def cpu_baseline(pool, cores, rounds=1):
+    """The oracle on every host core: `cores` independent replicas of the
+    sample solved at once, `rounds` times; unknowns of all replicas / wall time."""
+    p = _oracle_sample()
+    t0 = time.perf_counter()
+    res = []
+    for _ in range(rounds):
+        res = pool.map(_oracle_worker, range(cores))
+    wall = time.perf_counter() - t0
+    value = cores * rounds * p.unknowns / wall
+    per = statistics.mean(t for t, _ in res)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the headline workload at {ORACLE_SAMPLE_N}^2 interior points (same Nt = 128, s = 2, "
+                      f"alpha, tol, source): numpy float64 Exp-ParaDiag GMRES ({res[0][1]} iterations), one "
+                      f"single-threaded replica per core, {rounds} round(s), {wall:.1f} s wall, {per:.1f} s per solve",
+            "wall_s": wall}
 
 
 def run_reference(args):
+    """The reference arm: the oracle (the paper ships no code) on the host
+    cores, every step one round of replicas of the bounded sample."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    from paper_2603_04350_gb300 import inputs as I
-    p = workload(0)
-    u0 = I.make_u0(p)
+    pool, cores = oracle_pool()
+    p = _oracle_sample()
     times = []
     for k in range(args.warmup + args.steps):
-        secs, iters, _ = cpu_oracle_solve(p, u0)
+        t0 = time.perf_counter()
+        pool.map(_oracle_worker, range(cores))
         if k >= args.warmup:
-            times.append(secs)
-    # bounded: the reference arm's step is the full solve (~8 s on one core); K and W are
-    # capped so the run ends within minutes
+            times.append(time.perf_counter() - t0)
+    pool.close()
     total = sum(times)
-    value = p.unknowns * len(times) / total
+    value = cores * p.unknowns * len(times) / total
+    from paper_2603_04350_gb300 import inputs as I
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": len(times),
             "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": config_dict(p, 1),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{len(times)} full solves of {p.name} on the host, numpy float64"},
+            "config": config_dict(I.HEAT_DIRICHLET_1024, 1, "gmres"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"every step: {cores} single-threaded replicas (one per core) of the "
+                                       f"headline workload at {ORACLE_SAMPLE_N}^2 interior points, numpy float64 "
+                                       "Exp-ParaDiag GMRES"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
 # ------------------------------------------------------------------ GPU arm ---
-def served_mix(count: int, workers: int, local: int) -> dict:
+class Runner:
+    """Timed whole solves on one stream: CUDA events around every solve, a
+    256 MiB L2 flush between them, optional per-launch event timing."""
+
+    def __init__(self, torch, stream, flush, barrier):
+        self.torch, self.stream, self.flush, self.barrier = torch, stream, flush, barrier
+
+    def steps(self, plan, solver, u0, f, U, K, warm, timing=False):
+        torch = self.torch
+        fn = {"fp": plan.solve_fp, "gmres": plan.solve_gmres, "bicgstab": plan.solve_bicgstab,
+              "sequential": plan.solve_sequential}[solver]
+        for k in range(warm):
+            self.flush.fill_(float(k))
+            fn(u0, f, U)
+        self.barrier()
+        plan.timing_read(reset=True)
+        plan.timing_enable(timing)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        infos = []
+        self.barrier()
+        for k in range(K):
+            self.flush.fill_(float(k + 1))
+            starts[k].record(self.stream)
+            infos.append(fn(u0, f, U))
+            ends[k].record(self.stream)
+        self.barrier()
+        ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        tm = plan.timing_read(reset=True)
+        plan.timing_enable(False)
+        return ms, infos, tm
+
+
+def oracle_ref(p, u0, f):
+    import oracle as O
+    return O.sequential_solve(O.spec_of(p), u0, f)[1:]
+
+
+def errs(U, ref):
+    """Sec. 7's error norm and the largest grid-point error of any slice
+    relative to that slice's largest value."""
+    import oracle as O
+    d = np.abs(U - ref).reshape(U.shape[0], -1).max(axis=1)
+    r = np.abs(ref).reshape(ref.shape[0], -1).max(axis=1)
+    return {"rel_error": O.rel_error(U, ref), "slice_elementwise": float((d / np.maximum(r, 1e-300)).max())}
+
+
+def headline(args, run, dev, stream, world, pg, rank, check, clocks):
+    torch = run.torch
+    from paper_2603_04350_gb300 import expd, inputs as I
+    p = with_rank_seed(I.HEAT_DIRICHLET_1024, rank)
+    u0, f = I.make_inputs(p)
+    u0d, fd = torch.from_numpy(u0).to(dev), torch.from_numpy(f).to(dev)
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=dev)
+    spec = expd.spec_from_problem(p, precision=expd.PREC_MIXED, max_iter=200)
+    with expd.plan_create(spec, stream) as plan:
+        clocks.start()
+        ms, infos, tm_plain = run.steps(plan, "gmres", u0d, fd, U, args.steps, args.warmup)
+        clk = clocks.stop()
+        U_mixed = U.cpu().numpy()
+        total_ms, value = aggregate(sum(ms), p.unknowns, args.steps, world, pg, dev)
+        # the same solves with an event pair around every kernel launch: per-kernel
+        # durations for the roofline and the kernel table (not the headline run)
+        ms_ev, _, tm = run.steps(plan, "gmres", u0d, fd, U, 2, 0, timing=True)
+        # end to end through the C ABI: pinned host u0, f in and U out inside the call
+        u0_h = torch.from_numpy(u0).pin_memory()
+        f_h = torch.from_numpy(f).pin_memory()
+        U_h = torch.empty((p.Nt,) + p.n, dtype=torch.float64).pin_memory()
+        plan.solve_gmres(u0_h, f_h, U_h)
+        run.barrier()
+        e2e_t = []
+        for k in range(max(3, args.steps // 2)):
+            run.flush.fill_(float(k))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan.solve_gmres(u0_h, f_h, U_h)     # returns after U is in host memory
+            e2e_t.append(time.perf_counter() - t0)
+        e2e_value = world * p.unknowns / statistics.mean(e2e_t)
+        U_e2e = U_h.numpy().copy()
+    # BiCGStab on the same mixed path
+    with expd.plan_create(spec, stream) as plan:
+        ms_bi, infos_bi, _ = run.steps(plan, "bicgstab", u0d, fd, U, 3, 1)
+        U_bi = U.cpu().numpy()
+    # the plain float64 path and float64 sequential stepping
+    spec64 = expd.spec_from_problem(p, precision=expd.PREC_FP64, max_iter=200)
+    with expd.plan_create(spec64, stream) as plan:
+        ms64, infos64, _ = run.steps(plan, "gmres", u0d, fd, U, 2, 1)
+        U_fp64 = U.cpu().numpy()
+        ms_seq, _, _ = run.steps(plan, "sequential", u0d, fd, U, 2, 1)
+        U_seq = U.cpu().numpy()
+    value64 = p.unknowns / (statistics.mean(ms64) / 1e3)
+    value_seq = p.unknowns / (statistics.mean(ms_seq) / 1e3)
+    classes = tm["classes"]
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    mem = [k for k in classes if classes[k]["count"] and k != "dst_tc"]
+    info = infos[-1]
+    out = {
+        "value": value, "ms_per_step": total_ms / args.steps, "config": config_dict(p, world, "gmres"),
+        "iterations": info["iterations"], "refinements": info["refinements"],
+        "residual_history": info["history"],
+        "phase_ms": {"setup": info["ms_setup"], "iterate": info["ms_iterate"], "output": info["ms_output"]},
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+        "ms_per_step_with_kernel_events": statistics.mean(ms_ev),
+        "fp64_path": {"value": value64, "ms_per_step": statistics.mean(ms64),
+                      "iterations": infos64[-1]["iterations"]},
+        "speedup_vs_fp64": value / (world * value64),
+        "bicgstab": {"value": p.unknowns / (statistics.mean(ms_bi) / 1e3), "ms_per_step": statistics.mean(ms_bi),
+                     "iterations": infos_bi[-1]["iterations"], "refinements": infos_bi[-1]["refinements"]},
+        "gpu_sequential": {"value": value_seq, "ms_per_step": statistics.mean(ms_seq),
+                           "note": "float64 IF-BDF2 stepping in the eigenbasis, one time step after another"},
+        "speedup_vs_gpu_sequential": value / (world * value_seq),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(u0.nbytes + f.nbytes),
+                "d2h_bytes_per_step": int(U_h.numel() * 8)},
+        "gpu_launches": int(tm_plain["launches"]),
+        "roofline": roofline_of(classes, dom, fp64_plan=False, unknowns=p.unknowns),
+        "roofline_hbm_top": roofline_of(classes, max(mem, key=lambda k: classes[k]["ms"]), False, p.unknowns)
+        if mem else None,
+        "roofline_tensor": roofline_of(classes, "dst_tc", False) if classes.get("dst_tc", {}).get("count") else None,
+        "kernels": kernel_table(classes),
+    }
+    if clk:
+        out["clocks"] = clk
+    if check:
+        ref = oracle_ref(p, u0, f)
+        out["rel_err_vs_oracle"] = {"mixed": errs(U_mixed, ref), "e2e": errs(U_e2e, ref),
+                                    "bicgstab": errs(U_bi, ref), "fp64": errs(U_fp64, ref),
+                                    "gpu_sequential": errs(U_seq, ref)}
+    return out
+
+
+def leg(run, dev, stream, p, solver, variants, K, warm, check, exact=None):
+    """One workload on each (name, precision, scheme options) variant: value,
+    time per solve, iterations, the dominant kernel's roofline, the error
+    against the oracle (and against an exact solution when one is given)."""
+    torch = run.torch
+    from paper_2603_04350_gb300 import expd, inputs as I
+    u0, f = I.make_inputs(p)
+    u0d = torch.from_numpy(u0).to(dev)
+    fd = None if f is None else torch.from_numpy(f).to(dev)
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=dev)
+    out = {"workload": p.name, "unknowns": p.unknowns, "tol": p.tol, "solver": solver}
+    ref = oracle_ref(p, u0, f) if check else None
+    for name, prec, kw, slv in variants:
+        with expd.plan_create(expd.spec_from_problem(p, precision=prec, max_iter=200, **kw), stream) as plan:
+            ms, infos, _ = run.steps(plan, slv, u0d, fd, U, K, warm)
+            _, _, tm = run.steps(plan, slv, u0d, fd, U, 1, 0, timing=True)
+            Uh = U.cpu().numpy()
+        cls = tm["classes"]
+        dom = max(cls, key=lambda k: cls[k]["ms"])
+        d = {"value": p.unknowns / (statistics.mean(ms) / 1e3), "ms_per_step": statistics.mean(ms),
+             "launches_per_solve": int(tm["launches"]),
+             "dominant_kernel": roofline_of(cls, dom, fp64_plan=(prec == expd.PREC_FP64), unknowns=p.unknowns)}
+        if infos[-1] is not None:
+            d["iterations"] = infos[-1]["iterations"]
+            d["fp32_iterations"] = infos[-1]["fp32_iterations"]
+        if ref is not None:
+            d["rel_err_vs_oracle"] = errs(Uh, ref)
+        if exact is not None:
+            d["rel_err_vs_exact"] = errs(Uh, exact)
+        out[name] = d
+    if "mixed" in out and "fp64" in out:
+        out["speedup_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def heat1d_exact(p):
+    """The exact solution of the 1D periodic heat workload: the spectral
+    exponential Euler step reproduces e^{-k^2 t} on each Fourier mode."""
+    from paper_2603_04350_gb300 import inputs as I
+    x = I.grid_coords(p)[0]
+    rng = np.random.default_rng(p.seed)
+    ak, bk = rng.standard_normal(16), rng.standard_normal(16)
+    return np.array([sum(math.exp(-k * k * (n + 1) * p.dt) * (ak[k - 1] * np.cos(k * x) + bk[k - 1] * np.sin(k * x))
+                         / k ** 2 for k in range(1, 17)) for n in range(p.Nt)])
+
+
+def other_legs(args, run, dev, stream, check):
+    from paper_2603_04350_gb300 import expd, inputs as I
+    names = [s for s in args.legs.split(",") if s]
+    out = {}
+    both = [("fp64", expd.PREC_FP64, {}, "fp"), ("mixed", expd.PREC_MIXED, {}, "fp")]
+    if "heat1d" in names:
+        p = I.HEAT1D
+        out[p.name] = leg(run, dev, stream, p, "fp", both, 20, 3, check, exact=heat1d_exact(p))
+    if "ac256" in names:
+        p = I.ALLEN_CAHN_256
+        out[p.name] = leg(run, dev, stream, p, "fp",
+                          both + [("mixed_mean_jacobian", expd.PREC_MIXED, {"jacobian": expd.JAC_MEAN_U0}, "fp"),
+                                  ("gpu_sequential", expd.PREC_FP64, {}, "sequential")], 10, 3, check)
+    if "ac512" in names:
+        p = I.ALLEN_CAHN_512_S6
+        out[p.name] = leg(run, dev, stream, p, "fp", both, 3, 1, check)
+    return out
+
+
+def served_mix(count: int, base_count: int, workers: int, local: int) -> dict:
     """The served mix: heterogeneous requests (kind, grid, Nt, order drawn per
     request, seed 5) replayed with Poisson arrivals at 70 % of the engine's
     measured capacity; latency from arrival to result on the device.  Baseline:
-    the float64 path serving one request at a time, first come first served."""
+    the float64 path serving one request at a time, first come first served,
+    on the first base_count requests of the same arrivals."""
     from paper_2603_04350_gb300 import expd, inputs as I, serve
     reqs = I.served_mix(count=count, seed=5)
     eng = serve.Engine(device=local, workers=workers, precision=expd.PREC_MIXED)
-    eng.run(reqs[: min(8, count)], realtime=False)                 # warm-up: plans, kernels
+    eng.run(reqs[: min(16, count)], realtime=False)               # warm-up: plans, kernels
     t0 = time.perf_counter()
-    recs = eng.run(reqs, realtime=False)                          # all queued at t = 0
+    eng.run(reqs, realtime=False)                                  # all queued at t = 0
     cap_span = time.perf_counter() - t0
     capacity = count / cap_span
     rate = 0.7 * capacity
     timed = serve.with_rate(reqs, rate, seed=5)
     recs = eng.run(timed, realtime=True)
     mixed = serve.summary(recs)
-    base = serve.summary(serve.run_one_at_a_time(timed, device=local, precision=expd.PREC_FP64))
+    nb = min(base_count, count)
+    base = serve.summary(serve.run_one_at_a_time(timed[:nb], device=local, precision=expd.PREC_FP64))
+    mixed_first = serve.summary([r for r in recs if r.rid < nb])
     return {"requests": count, "seed": 5, "workers": workers, "capacity_req_per_s": capacity,
-            "rate_per_s": rate, "mixed_concurrent": mixed, "fp64_one_at_a_time": base,
+            "rate_per_s": rate, "mixed_concurrent": mixed,
+            "mixed_concurrent_first_requests": dict(mixed_first, requests_counted=nb),
+            "fp64_one_at_a_time": dict(base, requests_replayed=nb),
             "errors": eng.errors[:5], "oom_retries": eng.retries,
-            "note": "grids {64..1024}^2 (Dirichlet: g-1 interior points), Nt {16..256}, s {1,2,6}, "
-                    "kind {Allen-Cahn periodic, heat Dirichlet}; inputs generated on the device"}
+            "note": "grids {64..1024}^2, Nt {16..256}, s {1,2,6}, kind {Allen-Cahn periodic (fixed point, tol 1e-8), "
+                    "heat Dirichlet (g x g interior points, GMRES, tol 1e-9)}; the float64 server replays the first "
+                    f"{nb} requests of the same arrivals"}
 
 
 def main():
@@ -370,16 +602,15 @@ def main():
     if args.profile_dirichlet:
         return profile_dirichlet(args.profile_dirichlet)
     if args.impl == "reference":
-        args.steps = min(args.steps, 4)
-        args.warmup = min(args.warmup, 1)
         return run_reference(args)
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local = dist_env()
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    pool, cores = oracle_pool() if want_cpu else (None, 0)   # before the first CUDA call
     import torch
     import __graft_entry__ as g
     g.build()
-    from paper_2603_04350_gb300 import expd, inputs as I
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -394,177 +625,26 @@ def main():
             pg.barrier()
         torch.cuda.synchronize()
 
-    p = workload(rank)
-    u0 = I.make_u0(p)
-    u0_d = torch.from_numpy(u0).to(dev)
-    U_d = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     # a stream of its own (the legacy default stream cannot hold CUDA graphs)
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
+    run = Runner(torch, stream, flush, barrier)
+    check = rank == 0 and not args.no_check
+    h = headline(args, run, dev, stream, world, pg, rank, check, ClockSampler(local))
 
-    plan = expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, max_iter=100), stream)
-    plan64 = expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_FP64, max_iter=100), stream)
-
-    def timed_steps(pl, K, warm, timing=False):
-        infos = []
-        for k in range(warm):
-            flush.fill_(float(k))
-            pl.solve_fp(u0_d, None, U_d)
-        barrier()
-        pl.timing_read(reset=True)
-        if timing:
-            pl.timing_enable(True)
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-        barrier()
-        for k in range(K):
-            flush.fill_(float(k + 1))
-            starts[k].record(stream)
-            infos.append(pl.solve_fp(u0_d, None, U_d))
-            ends[k].record(stream)
-        barrier()
-        ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-        tm = pl.timing_read(reset=True)
-        pl.timing_enable(False)
-        return ms, infos, tm
-
-    # ---- mixed path: the headline (CUDA events around each solve only) ----
-    clocks = ClockSampler(local)
-    clocks.start()
-    ms, infos, tm_plain = timed_steps(plan, args.steps, args.warmup, timing=False)
-    clk = clocks.stop()
-    U_mixed = U_d.cpu().numpy()
-    total_ms, value = aggregate(sum(ms), p.unknowns, args.steps, world, pg, dev)
-
-    # the same loop with an event pair around every kernel launch: per-kernel
-    # durations for the roofline and the kernel table (the event records add
-    # host and device overhead, so this run is not the headline)
-    ms_ev, _, tm = timed_steps(plan, args.steps, 1, timing=True)
-
-    # ---- inexact Newton variant (mean Jacobian at u0), mixed path ----
-    plan_nt = expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, max_iter=100,
-                                                      jacobian=expd.JAC_MEAN_U0), stream)
-    ms_nt, infos_nt, _ = timed_steps(plan_nt, args.steps, 3, timing=False)
-    U_nt = U_d.cpu().numpy()
-    value_nt = p.unknowns / (statistics.mean(ms_nt) / 1e3)
-    plan_nt.destroy()
-
-    # ---- plain float64 path ----
-    K64 = max(3, args.steps // 2)
-    ms64, infos64, _ = timed_steps(plan64, K64, 3, timing=False)
-    U_fp64 = U_d.cpu().numpy()
-    value64 = p.unknowns / (statistics.mean(ms64) / 1e3)
-
-    # ---- the same scheme stepped sequentially on the GPU (float64): the
-    # time-stepping baseline that parallel-in-time has to beat ----
-    for k in range(3):
-        flush.fill_(float(k))
-        plan64.solve_sequential(u0_d, None, U_d)
-    barrier()
-    ms_seq = []
-    for k in range(K64):
-        flush.fill_(float(k + 1))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        plan64.solve_sequential(u0_d, None, U_d)
-        e1.record(stream)
-        barrier()
-        ms_seq.append(e0.elapsed_time(e1))
-    U_seq = U_d.cpu().numpy()
-    value_seq = p.unknowns / (statistics.mean(ms_seq) / 1e3)
-
-    # ---- end to end through the C ABI with pinned host buffers ----
-    u0_h = torch.from_numpy(u0).pin_memory()
-    U_h = torch.empty((p.Nt,) + p.n, dtype=torch.float64).pin_memory()
-    for _ in range(2):
-        plan.solve_fp(u0_h, None, U_h)
-    barrier()
-    e2e_t = []
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        plan.solve_fp(u0_h, None, U_h)          # copies in and out inside the call
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_value = world * p.unknowns / statistics.mean(e2e_t)
-
-    # ---- roofline of the dominant kernel class ----
-    peak, peak_src = measured_peaks()
-    classes = tm["classes"]
-    dom = max(classes, key=lambda k: classes[k]["ms"])
-    c = classes[dom]
-
-    def hbm_roof(k):
-        ck = classes[k]
-        ach = (ck["bytes"] / ck["count"]) / (ck["ms"] / ck["count"] / 1e3) / 1e9 if ck["count"] else 0.0
-        traffic = NCU_TRAFFIC_256x64.get(k) if p.n == (256, 256) and p.Nt == 64 else None
-        return {"bound": "hbm", "kernel": k, "achieved": ach, "peak": peak, "peak_source": peak_src,
-                "unit": "GB/s", "frac": ach / peak, "traffic": traffic,
-                "algorithmic_bytes_per_launch": ck["bytes"] / ck["count"] if ck["count"] else None}
-
-    if dom in DD_CLASSES:
-        achieved = DD_FP32_OPS * (c["flops"] / c["count"]) / (c["ms"] / c["count"] / 1e3) / 1e12 if c["count"] else 0.0
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "peak_source": "derived: 152 SMs x 128 float32 lanes x 2 flop x 2.07 GHz (double-float arithmetic "
-                               f"counted as {DD_FP32_OPS} float32 operations per operation)",
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None}
-    elif dom in FP64_CLASSES:
-        # float64 kernels are bound by the float64 pipe on GB300 (1/58 of float32)
-        achieved = (c["flops"] / c["count"]) / (c["ms"] / c["count"] / 1e3) / 1e12 if c["count"] else 0.0
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "peak_source": "measured float64 FMA throughput (2 FMA/clk/SM at 2.07 GHz)", "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None}
-    else:
-        roof = hbm_roof(dom)
-    # the largest memory-bound class, whatever dominates
-    mem = [k for k in classes if k not in DD_CLASSES and k not in FP64_CLASSES and classes[k]["count"]]
-    roof_hbm_top = hbm_roof(max(mem, key=lambda k: classes[k]["ms"])) if mem else None
-    kernels = {k: {"launches": v["count"], "ms_total": round(v["ms"], 4),
-                   "avg_us": round(1e3 * v["ms"] / v["count"], 3) if v["count"] else None,
-                   "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] else None,
-                   "GFLOPs": round(v["flops"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] else None}
-               for k, v in classes.items() if v["count"]}
-
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-           "config": config_dict(p, world),
-           "iterations": infos[-1]["iterations"], "fp32_iterations": infos[-1]["fp32_iterations"],
-           "error_estimate_history": infos[-1]["history"],
-           "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
-           "ms_per_step_with_kernel_events": statistics.mean(ms_ev),
-           "fp64_path": {"value": value64, "ms_per_step": statistics.mean(ms64),
-                         "iterations": infos64[-1]["iterations"]},
-           "speedup_vs_fp64": value / (world * value64),
-           "mean_jacobian_variant": {"value": value_nt, "ms_per_step": statistics.mean(ms_nt),
-                                     "iterations": infos_nt[-1]["iterations"],
-                                     "fp32_iterations": infos_nt[-1]["fp32_iterations"],
-                                     "note": "preconditioner shifted by beta dt mean N'(u0) (inexact Newton)"},
-           "gpu_sequential": {"value": value_seq, "ms_per_step": statistics.mean(ms_seq),
-                              "note": "float64 IF-BDF stepping, one time step after another"},
-           "speedup_vs_gpu_sequential": value / (world * value_seq),
-           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(u0.nbytes),
-                   "d2h_bytes_per_step": int(U_h.numel() * 8)},
-           "gpu_launches": int(tm_plain["launches"]),
-           "roofline": roof, "roofline_hbm_top": roof_hbm_top,
-           "kernels": kernels}
-    if clk:
-        out["clocks"] = clk
-    if rank == 0 and not args.no_check:
-        import oracle as O
-        ref = O.sequential_solve(O.spec_of(p), u0)[1:]
-        out["rel_err_vs_oracle"] = {"mixed": O.rel_error(U_mixed, ref), "fp64": O.rel_error(U_fp64, ref),
-                                    "gpu_sequential": O.rel_error(U_seq, ref),
-                                    "mean_jacobian_variant": O.rel_error(U_nt, ref)}
-    if not args.no_dirichlet:
-        out["heat_dirichlet_1024"] = dirichlet_leg(stream, flush, barrier, rank == 0 and not args.no_check)
-    if args.mix > 0:
-        out["served_mix"] = served_mix(args.mix, args.mix_workers, local)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(p, u0)
-    plan.destroy()
-    plan64.destroy()
+    out = {"metric": METRIC, "value": h.pop("value"), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": h.pop("ms_per_step"), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32+bf16", "data": "synthetic",
+           "config": h.pop("config")}
+    out.update(h)
+    if rank == 0:
+        out["legs"] = other_legs(args, run, dev, stream, check)
+        if args.mix > 0:
+            out["served_mix"] = served_mix(args.mix, args.mix_baseline, args.mix_workers, local)
+    if want_cpu:
+        out["cpu_baseline"] = cpu_baseline(pool, cores)
+        pool.close()
     if rank == 0:
         print(json.dumps(out))
     if pg is not None:

@@ -155,7 +155,7 @@ expd_status upload_vec(expd_plan p, T** dptr, const std::vector<T>& h, const cha
 
 void free_plan(expd_plan p) {
     if (!p) return;
-    void* bufs[] = {p->E,    p->C64,  p->C32, p->Cdd, p->Wxdd, p->Wydd, p->gamdd, p->oscdd, p->Wx64, p->Wx32,   p->Wy64,    p->Wy32,    p->Sx,        p->Sy, p->Dtx, p->Dty,
+    void* bufs[] = {p->E,    p->PHI64, p->PHI32, p->PHIdd, p->C64,  p->C32, p->Cdd, p->Wxdd, p->Wydd, p->gamdd, p->oscdd, p->Wx64, p->Wx32,   p->Wy64,    p->Wy32,    p->Sx,        p->Sy, p->Dtx, p->Dty,
                     p->Uh,   p->Fh,   p->Sh,     p->fh,      p->NL64,    p->NL32,      p->work64,
                     p->work32, p->startphys, p->partial, p->redout, p->stage, p->gm, p->U32, p->F32,
                     p->tc_S, p->tc_pack, p->tc_ex};
@@ -288,7 +288,17 @@ expd_status setup_start(expd_plan p, const double* u0, const double* f, const do
         }
         if (st != EXPD_OK) return st;
     }
-    return assemble_rhs(p, f ? p->fh : nullptr, s, F32, fh_dd);
+    // ETD1: row 0 of f_s gains dt phi_1(dt L) N(u_0); N(u_0) goes through slice
+    // 1 of the N buffer (physical scratch) into its slice 0 (eigen)
+    const void* nl0 = nullptr;
+    if (p->nl_form == EXPD_NLF_ETD1) {
+        double* phys = static_cast<double*>(eig_slice(p, p->NL64, 1));
+        st = nonlinearity_eval_phys(p, p->startphys, phys, (long long)M, s);
+        if (st == EXPD_OK) st = fwd(phys, p->NL64, 1);
+        if (st != EXPD_OK) return st;
+        nl0 = p->NL64;
+    }
+    return assemble_rhs(p, f ? p->fh : nullptr, s, F32, fh_dd, nl0);
 }
 
 // out = {sqrt(max_n ||s_n||^2), sqrt(max_n ||x_n||^2), sum_n ||s_n||^2, sum_n ||x_n||^2}
@@ -554,6 +564,11 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     p->adv = p->bx != 0.0 || p->by != 0.0;
     if (p->adv && grid->bc != EXPD_BC_PERIODIC)
         return expd_fail(EXPD_ERR_INVALID_ARG, "advection needs a periodic grid (the sine basis does not diagonalise it)");
+    if (op->nonlin != EXPD_NL_NONE && scheme->nl_form == EXPD_NLF_ETD1) {
+        if (p->adv) return expd_fail(EXPD_ERR_UNSUPPORTED, "the ETD1 form takes real symbols (no advection)");
+        if (scheme->jacobian == EXPD_JAC_MEAN_U0)
+            return expd_fail(EXPD_ERR_INVALID_ARG, "the mean-Jacobian preconditioner is defined for the IF form only");
+    }
     p->dt = dt;
     p->Nt = Nt;
     p->order = scheme->order;
@@ -611,6 +626,10 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     // EXPD_KF_FFT_RADIX4 selects the shared-memory radix-4 row and column
     // FFTs for every size (both compute the same transforms)
     p->no_fft4 = (p->kernel_flags & EXPD_KF_FFT_RADIX4) != 0;
+    // EXPD_TIME_REAL=0: real (Dirichlet) columns take the generic shared-memory
+    // kernel instead of the real-column one (both compute the same; tests)
+    const char* tr = getenv("EXPD_TIME_REAL");
+    p->no_real_time = tr && strcmp(tr, "0") == 0;
     const char* gr = getenv("EXPD_GRAPHS");
     p->no_graphs = gr && strcmp(gr, "0") == 0;
     // the device-controlled loop is opt-in (EXPD_DEVICE_LOOP=1): on GB300 its
@@ -1021,6 +1040,46 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
             p->Cdd = dptr;
         }
     }
+    // ---- ETD1: dt phi_1(dt mu_m), phi_1(z) = expm1(z)/z, phi_1(0) = 1 ----
+    if (st == EXPD_OK && p->nl_form == EXPD_NLF_ETD1) {
+        std::vector<double> ph((size_t)p->Mcol);
+        std::vector<float> ph32((size_t)p->Mcol);
+        std::vector<float2> phdd((size_t)p->Mcol);
+        for (long long m = 0; m < p->Mcol; ++m) {
+            const int kx = (int)(m % p->KX), ky = (int)(m / p->KX);
+            double mu = -p->c;
+            if (p->bc == EXPD_BC_PERIODIC) {
+                const double wx = 2.0 * M_PI * kx / p->LX;
+                mu -= p->a * wx * wx;
+                if (p->ndim == 2) {
+                    const int kyf = ky <= p->NY / 2 ? ky : ky - p->NY;
+                    const double wy = 2.0 * M_PI * kyf / p->LY;
+                    mu -= p->a * wy * wy;
+                }
+            } else {
+                const double hx = p->LX / (p->NX + 1);
+                const double sx = sin(M_PI * (kx + 1) * hx / (2.0 * p->LX));
+                mu -= p->a * (4.0 / (hx * hx)) * sx * sx;
+                if (p->ndim == 2) {
+                    const double hy = p->LY / (p->NY + 1);
+                    const double sy = sin(M_PI * (ky + 1) * hy / (2.0 * p->LY));
+                    mu -= p->a * (4.0 / (hy * hy)) * sy * sy;
+                }
+            }
+            const double z = dt * mu;
+            ph[m] = dt * (z == 0.0 ? 1.0 : std::expm1(z) / z);
+            ph32[m] = (float)ph[m];
+            const float2_pair d = split_dd(ph[m]);
+            phdd[m] = make_float2(d.hi, d.lo);
+        }
+        st = upload_vec(p, &p->PHI64, ph, "phi_1 table", s);
+        if (st == EXPD_OK) st = upload_vec(p, &p->PHI32, ph32, "phi_1 table (float32)", s);
+        if (st == EXPD_OK && p->precision == EXPD_PREC_MIXED && p->bc == EXPD_BC_PERIODIC) {
+            float2* dptr = nullptr;
+            st = upload_vec(p, &dptr, phdd, "phi_1 table (double-float)", s);
+            p->PHIdd = dptr;
+        }
+    }
     // ---- spatial transform tables ----
     if (st == EXPD_OK && p->bc == EXPD_BC_PERIODIC) {
         std::vector<double2> w64(p->NX / 2 + 1);
@@ -1170,6 +1229,7 @@ expd_status expd_plan_footprint_bytes(const expd_grid* grid, const expd_operator
     const size_t cw = p->adv ? 2 : 1;                                      // complex tables with advection
     b += cw * (Mcol * 8 + ord * Mcol * 8 + ord * Mcol * 4);                 // E, C64, C32
     if (mixed && per) b += cw * ord * Mcol * 8;                             // Cdd
+    if (p->nl_form == EXPD_NLF_ETD1) b += Mcol * (8 + 4) + (mixed && per ? Mcol * 8 : 0);  // PHI64, PHI32, PHIdd
     if (per) {
         b += (size_t)(p->NX / 2 + 1) * (16 + 8);                            // Wx64, Wx32
         if (p->ndim == 2) b += (size_t)std::max(1, p->NY / 2) * (16 + 8);  // Wy64, Wy32
@@ -1258,6 +1318,7 @@ expd_status expd_destroy(expd_plan p) {
 expd_status expd_residual(expd_plan p, const double* u0, const double* f, const double* U, double* R,
                           void* stream) {
     if (!p || !u0 || !U || !R) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, u0, U and R are required");
+    if (f && p->nl_form == EXPD_NLF_ETD1) return expd_fail(EXPD_ERR_INVALID_ARG, "the ETD1 form takes no source term");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     EXPD_CUDA_TRY(plan_bind_stream(p, s));
     const size_t M = (size_t)p->M;
@@ -1288,9 +1349,11 @@ expd_status expd_residual(expd_plan p, const double* u0, const double* f, const 
     op.out = p->Fh;  // in-place per tile: each tile is loaded before it is written
     if (p->nonlin != EXPD_NL_NONE) {
         st = nonlinear_eval(p, p->Uh, p->NL64, 0, s);
+        // ETD1: dt phi_1(dt L) N of the previous slice
+        if (st == EXPD_OK && p->nl_form == EXPD_NLF_ETD1) st = etd_shift(p, p->NL64, 0, s);
         if (st != EXPD_OK) return st;
         op.NL = p->NL64;
-        op.bdt = p->beta[p->order] * p->dt;
+        op.bdt = p->nl_form == EXPD_NLF_ETD1 ? 1.0 : p->beta[p->order] * p->dt;
     }
     st = time_apply(p, op, s);
     if (st != EXPD_OK) return st;
@@ -1344,6 +1407,7 @@ expd_status expd_precond_apply(expd_plan p, const double* R, double* S, void* st
 expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double* U, expd_info* info,
                           void* stream) {
     if (!p || !u0 || !U) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, u0 and U are required");
+    if (f && p->nl_form == EXPD_NLF_ETD1) return expd_fail(EXPD_ERR_INVALID_ARG, "the ETD1 form takes no source term");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     EXPD_CUDA_TRY(plan_bind_stream(p, s));
     expd_status st = call_begin(p, info, s);
@@ -1352,6 +1416,7 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
     if (st != EXPD_OK) return st;
     const bool nl = p->nonlin != EXPD_NL_NONE;
+    const bool etd = nl && p->nl_form == EXPD_NLF_ETD1;
     const bool mixed = p->precision == EXPD_PREC_MIXED;
     // the mixed path's right-hand side comes out of its assembly in float32
     // and, for the double-float phase, as double-float pairs
@@ -1460,9 +1525,11 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
                 NL = p->NL64;
                 r = nonlinear_eval(p, o.X, NL, 0, s, 0);
             }
+            // ETD1: dt phi_1(dt L) N of the previous slice, in the phase's storage
+            if (r == EXPD_OK && etd) r = etd_shift(p, NL, ph == PH32 ? 1 : ph == PHDD ? 2 : 0, s);
             if (r != EXPD_OK) return r;
             o.NL = NL;
-            o.bdt = p->beta[p->order] * p->dt;
+            o.bdt = etd ? 1.0 : p->beta[p->order] * p->dt;
         }
         r = time_apply(p, o, s);
         if (r == EXPD_OK) r = time_reduce(p, s);
@@ -1624,6 +1691,7 @@ static expd_status ensure_krylov(expd_plan p, int nvec) {
 
 expd_status expd_solve_sequential(expd_plan p, const double* u0, const double* f, double* U, void* stream) {
     if (!p || !u0 || !U) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, u0 and U are required");
+    if (f && p->nl_form == EXPD_NLF_ETD1) return expd_fail(EXPD_ERR_INVALID_ARG, "the ETD1 form takes no source term");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     EXPD_CUDA_TRY(plan_bind_stream(p, s));
     Staging sg;
@@ -1642,6 +1710,16 @@ expd_status expd_solve_sequential(expd_plan p, const double* u0, const double* f
     const double bdt = p->beta[so] * p->dt;
     auto steps = [&]() -> expd_status {
         expd_status r = EXPD_OK;
+        if (nl && p->nl_form == EXPD_NLF_ETD1) {
+            // ETD1: u_n = A u_{n-1} + dt phi_1(dt L) N(u_{n-1})
+            for (int n = 1; n <= p->Nt && r == EXPD_OK; ++n) {
+                r = spatial_inverse64(p, slice(n - 1), phys, 1, s);
+                if (r == EXPD_OK) r = nonlinearity_eval_phys(p, phys, phys, M, s);
+                if (r == EXPD_OK) r = spatial_forward64(p, phys, tmp, 1, s);
+                if (r == EXPD_OK) r = etd_step(p, slice(n), slice(n - 1), tmp, s);
+            }
+            return r;
+        }
         for (int n = so; n <= p->Nt && r == EXPD_OK; ++n) {
             // IF-BDF-s step: w = sum_j a_j A^j u_{n-j} + beta_s dt f(t_n), then
             // u_n = w (linear) or u_n - beta_s dt N(u_n) = w pointwise (Eq. (7.3))

@@ -123,10 +123,19 @@ EXPD_HD T2 cmul_quarter(T2 a, int sign) {
 // i + 2 (i >> 3).  The radix-4 passes touch elements 0, 1, 8, 9, 16, 17, ...
 // from consecutive lanes; unpadded, a quarter-warp's eight 16-byte accesses
 // then fall on two bank groups (4-way conflicts), padded on eight.
+// Shared-memory index maps of the warp FFT buffers.  PAD 1: two 16-byte slots
+// of padding per eight elements (16-byte elements).  PAD 2: an XOR swizzle of
+// the low four index bits by bits 4-5, i ^ 5 ((i >> 4) & 3), a bijection on
+// every aligned block of 16 elements that keeps all radix-4 passes and the
+// natural-order sweeps of lengths 64..1024 free of bank conflicts for 8-byte
+// elements (at most two-way for 16-byte ones).
 template <int PAD>
-EXPD_HD int padi(int i) { return PAD ? i + ((i >> 3) << 1) : i; }
+EXPD_HD int padi(int i) {
+    if (PAD == 2) return i ^ (5 * ((i >> 4) & 3));
+    return PAD ? i + ((i >> 3) << 1) : i;
+}
 template <int PAD>
-EXPD_HD int padded_len(int n) { return PAD ? n + ((n >> 3) << 1) : n; }
+EXPD_HD int padded_len(int n) { return PAD == 1 ? n + ((n >> 3) << 1) : n; }
 
 // Decimation in time: x in bit-reversed order -> X in natural order.
 template <typename T2, int PAD = 0>

@@ -53,6 +53,29 @@ EXPD_HD float f32_rn_from_f64(double v) {
     return f32_from_bits(u);
 }
 
+// Exact float -> double by integer operations (every float is a double):
+// normal values rebias the exponent and widen the fraction; zeros,
+// subnormals, infinities and NaN take the ordinary conversion.
+EXPD_HD double f64_from_f32(float f) {
+#ifdef __CUDA_ARCH__
+    const unsigned u = __float_as_uint(f);
+#else
+    unsigned u;
+    memcpy(&u, &f, 4);
+#endif
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double d;
+    memcpy(&d, &b, 8);
+    return d;
+#endif
+}
+
 struct dd;
 EXPD_HD dd dd_from_f64(double v);
 

@@ -82,6 +82,9 @@ struct expd_plan_s {
 
     // ---- tables ---------------------------------------------------------------
     double* E = nullptr;       // [Mcol] exp(dt mu_m)
+    double* PHI64 = nullptr;   // ETD1: [Mcol] dt phi_1(dt mu_m), phi_1(z) = (e^z - 1)/z
+    float* PHI32 = nullptr;    // the same in float32
+    void* PHIdd = nullptr;     // the same as double-float (mixed periodic plans)
     double* C64 = nullptr;     // [order][Mcol] a_j exp(j dt mu_m), j = 1..order (time-kernel coefficients)
     float* C32 = nullptr;      // the same in float32
     double2* Wx64 = nullptr;   // [NX/2+1] e^{-2 pi i k/NX}
@@ -161,6 +164,7 @@ struct expd_plan_s {
     long long fp_solves = 0;      // fixed-point solves run on this plan
     int no_graphs = 0;            // 1: launch kernel by kernel (EXPD_GRAPHS=0)
     int no_reg_time = 0;          // 1 forces the shared-memory time kernel (tests)
+    int no_real_time = 0;         // 1: real columns take the generic kernel (EXPD_TIME_REAL=0, tests)
     int no_fft4 = 0;              // 1 forces the radix-4 shared-memory row / column FFTs (tests)
     // mixed Krylov refinement: a cycle ends once its residual fell by this factor
     double krylov_eta = 1e-3;
@@ -260,8 +264,17 @@ expd_status eigen_combine(expd_plan p, void* out, const void* const* in, const d
 // f_s: Fh[i] = bdt f^(s+i) + sum_{j: s+i-j<s} a_j E^j Sh[s+i-j]
 // *out_dev = sum of x[i]^2 (deterministic); scratch holds 64 doubles
 expd_status sum_squares(expd_plan p, const double* x, long long n, double* out_dev, double* scratch, cudaStream_t s);
-// F32 (optional): also the float32 copy; fh_dd: Fh stored as double-float pairs
-expd_status assemble_rhs(expd_plan p, const void* fh, cudaStream_t s, float* F32 = nullptr, int fh_dd = 0);
+// F32 (optional): also the float32 copy; fh_dd: Fh stored as double-float pairs;
+// nl0 (ETD1): N(u_0) in the eigenbasis, whose phi-scaled value row 0 gains
+expd_status assemble_rhs(expd_plan p, const void* fh, cudaStream_t s, float* F32 = nullptr, int fh_dd = 0,
+                         const void* nl0 = nullptr);
+// ETD1: NL_n <- dt phi_1(dt mu) NL_{n-1}, NL_0 <- 0, in place (kind 0 float64,
+// 1 float32, 2 double-float storage)
+expd_status etd_shift(expd_plan p, void* NL, int kind, cudaStream_t s);
+// ETD1 step: out = E prev + dt phi_1(dt mu) nl (float64 eigen slices)
+expd_status etd_step(expd_plan p, void* out, const void* prev, const void* nl, cudaStream_t s);
+// out = N(u) pointwise (physical float64)
+expd_status nonlinearity_eval_phys(expd_plan p, const double* u, double* out, long long n, cudaStream_t s);
 
 // ---- tensor-core DST (dst_tc.cu) ----------------------------------------------
 // The mixed path on a 2D Dirichlet grid with both sizes multiples of 128 up to

@@ -239,6 +239,24 @@ static void test_column(int Ns, int order, double E, double alpha, double tol, s
         pscale = std::max(pscale, std::max(std::fabs(r1[n]), std::fabs(r2[n])));
     }
     check(sizeof(T) == 8 ? "precond_column_pair double" : "precond_column_pair float", perr / pscale, tol, Ns, order);
+
+    // the same pair solve on the swizzled buffer layout (padi<2>) of the
+    // real-column kernel: identical values at every logical position
+    std::vector<T2> wsw(t.L);
+    for (int i = 0; i < t.L; ++i) wsw[padi<2>(i)] = to_dev<T2, T>(wp)[i];
+    const double ss = precond_column_pair<T, T2, 2>(wsw.data(), Ns, t.L, t.log2L, t.bluestein, twd.data(), lamd.data(),
+                                                    t.bluestein ? chd.data() : nullptr,
+                                                    t.bluestein ? bpd.data() : nullptr,
+                                                    t.bluestein ? bmd.data() : nullptr, cjT, cj2, order, 0, 1);
+    double serr = 0;
+    for (int n = 0; n < Ns; ++n) {
+        const int pos = t.bluestein ? n : bitrev(n, t.log2L);
+        const T2 a = wsw[padi<2>(pos)], b = wpd[pos];
+        serr = std::max(serr, std::max(std::fabs((double)a.x * ss - (double)b.x * sp),
+                                       std::fabs((double)a.y * ss - (double)b.y * sp)));
+    }
+    check(sizeof(T) == 8 ? "precond_column_pair swizzled double" : "precond_column_pair swizzled float",
+          serr / pscale, 0.0, Ns, order);  // the same operations in the same order: bit-identical
 }
 
 // The integer-path conversions against the hardware ones: round to nearest
@@ -263,6 +281,18 @@ static void test_conversions(std::mt19937_64& rng) {
     const double specials[] = {0.0, -0.0, 1.0, -1.0, 3.0e38, -3.4e38, 1e-40, 1e300};
     for (double v : specials)
         if (f32_rn_from_f64(v) != (float)v) ++bad;
+    // exact float -> double widening: every float, specials included
+    std::uniform_int_distribution<unsigned> bits32(0u, 0xffffffffu);
+    for (int i = 0; i < 400000; ++i) {
+        unsigned u = bits32(rng);
+        float f;
+        memcpy(&f, &u, 4);
+        const double a = f64_from_f32(f), b = (double)f;
+        if (!(a == b || (a != a && b != b)) || (a == 0.0 && std::signbit(a) != std::signbit(b))) ++bad;
+    }
+    const float fspec[] = {0.0f, -0.0f, 1.0f, -1.0f, 3.4e38f, 1e-40f, -1e-45f, INFINITY, -INFINITY};
+    for (float f : fspec)
+        if (f64_from_f32(f) != (double)f) ++bad;
     const dd n = dd_from_f64(NAN);
     if (!(n.hi != n.hi)) ++bad;
     const dd z = dd_from_f64(0.0);

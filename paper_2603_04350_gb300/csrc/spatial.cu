@@ -224,6 +224,42 @@ __global__ void nl_pointwise_kernel(double* __restrict__ u, long long n, int non
     }
 }
 
+// ---- ETD1 (first-order exponential time differencing, phi_1) ----
+// N of the unknown slices moved one slice later and scaled per mode:
+// NL_n <- phi_m NL_{n-1} for n = Ns-1 .. 1, NL_0 <- 0 (row 0's N(u_0) term is
+// in the right-hand side).  In place: one thread per scalar element walks its
+// slices downward (every old value is read before it is overwritten),
+// coalesced across the elements.  T: float64, float32 or double-float storage.
+template <typename T, typename P>
+__global__ void etd_shift_kernel(T* __restrict__ NL, const P* __restrict__ phi, long long nelem, int eshift, int Ns) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nelem;
+         e += (long long)gridDim.x * blockDim.x) {
+        const P ph = phi[e >> eshift];
+        for (int n = Ns - 1; n >= 1; --n) NL[(long long)n * nelem + e] = ph * NL[(long long)(n - 1) * nelem + e];
+        NL[e] = T(0.0f);
+    }
+}
+
+// ETD1 step in the eigenbasis: out = E_m prev + phi_m nl (float64)
+__global__ void etd_step_kernel(double* __restrict__ out, const double* __restrict__ prev,
+                                const double* __restrict__ nl, const double* __restrict__ E,
+                                const double* __restrict__ phi, long long nelem, int eshift) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nelem;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long m = e >> eshift;
+        out[e] = fma(E[m], prev[e], phi[m] * nl[e]);
+    }
+}
+
+// out = N(u) pointwise (float64 physical values)
+__global__ void nl_eval_kernel(const double* __restrict__ u, double* __restrict__ out, long long n, int nonlin) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double x = u[i];
+        out[i] = (nonlin == EXPD_NL_ALLEN_CAHN) ? x - x * x * x : 0.0;
+    }
+}
+
 __global__ void f64_to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         out[i] = (float)in[i];
@@ -315,6 +351,8 @@ struct RhsArgs {
     double bdt;
     long long nelem;
     int eshift, s, Ns;
+    const double* nl0;  // ETD1: N(u_0) transformed ([nelem]); row 0 gains phi_m N(u_0)
+    const double* phi;  // ETD1: dt phi_1(dt mu_m) per mode
 };
 
 // Initial iterate X_k[m] = E_m^(k+1) S[m], k < Ns: one thread per mode walks
@@ -379,6 +417,7 @@ __global__ void rhs_kernel(RhsArgs r) {
                 if (n - j < r.s) acc += cmul_elem(r.a[j] * pr, r.a[j] * pi, r.Sh + (long long)(n - j) * r.nelem, e);
             }
         }
+        if (i == 0 && r.nl0) acc = fma(r.phi[e >> r.eshift], r.nl0[e], acc);
         if (r.F32) r.F32[idx] = f32_rn_from_f64(acc);
         if (r.fh_dd) reinterpret_cast<dd*>(r.Fh)[idx] = dd_from_f64(acc);
         else r.Fh[idx] = acc;
@@ -1354,6 +1393,40 @@ expd_status pointwise_solve(expd_plan p, const double* w, double* u, long long n
     return EXPD_OK;
 }
 
+expd_status etd_shift(expd_plan p, void* NL, int kind, cudaStream_t s) {
+    const int eshift = p->realcol ? 0 : 1;
+    const long long nelem = p->Mcol << eshift;
+    const double esz = kind == 1 ? 4.0 : 8.0;
+    KProf kp(p, s, EXPD_K_POINTWISE, 2.0 * esz * nelem * (p->Ns - 1), (double)nelem * p->Ns);
+    const int grid = (int)std::min<long long>((nelem + 255) / 256, (long long)p->sm_count * 16);
+    if (kind == 0)
+        etd_shift_kernel<double, double><<<grid, 256, 0, s>>>(static_cast<double*>(NL), p->PHI64, nelem, eshift, p->Ns);
+    else if (kind == 1)
+        etd_shift_kernel<float, float><<<grid, 256, 0, s>>>(static_cast<float*>(NL), p->PHI32, nelem, eshift, p->Ns);
+    else
+        etd_shift_kernel<dd, dd><<<grid, 256, 0, s>>>(static_cast<dd*>(NL), static_cast<const dd*>(p->PHIdd), nelem,
+                                                      eshift, p->Ns);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+expd_status etd_step(expd_plan p, void* out, const void* prev, const void* nl, cudaStream_t s) {
+    const int eshift = p->realcol ? 0 : 1;
+    const long long nelem = p->Mcol << eshift;
+    KProf kp(p, s, EXPD_K_POINTWISE, 24.0 * nelem, 3.0 * nelem);
+    etd_step_kernel<<<grid_for(nelem, 256), 256, 0, s>>>(static_cast<double*>(out), static_cast<const double*>(prev),
+                                                        static_cast<const double*>(nl), p->E, p->PHI64, nelem, eshift);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+expd_status nonlinearity_eval_phys(expd_plan p, const double* u, double* out, long long n, cudaStream_t s) {
+    KProf kp(p, s, EXPD_K_POINTWISE, 16.0 * n, 3.0 * n);
+    nl_eval_kernel<<<grid_for(n, 256), 256, 0, s>>>(u, out, n, p->nonlin);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
 expd_status eigen_combine(expd_plan p, void* out, const void* const* in, const double* coef, int q,
                           const void* src, double g, cudaStream_t s) {
     CombineArgs a;
@@ -1397,8 +1470,10 @@ expd_status linear_guess(expd_plan p, void* X, int x32, cudaStream_t s) {
     return EXPD_OK;
 }
 
-expd_status assemble_rhs(expd_plan p, const void* fh, cudaStream_t s, float* F32, int fh_dd) {
+expd_status assemble_rhs(expd_plan p, const void* fh, cudaStream_t s, float* F32, int fh_dd, const void* nl0) {
     RhsArgs r;
+    r.nl0 = static_cast<const double*>(nl0);
+    r.phi = p->PHI64;
     r.fh = static_cast<const double*>(fh);
     r.Sh = static_cast<const double*>(p->Sh);
     r.Fh = static_cast<double*>(p->Fh);

@@ -31,6 +31,9 @@ struct TimeArgs {
     int KX, NX, realcol;
     const void* gam;  // [Ns] in the storage precision ST
     const void* osc;  // [Ns] in the storage precision ST
+    const float* gam32;  // [Ns] float32 copies (residuals formed in float32)
+    const float* osc32;
+    int norms;        // accumulate the per-slice norm partials (the fixed point's stopping test)
     const void* lam;  // PT2 tables
     const void* tw;
     const void* chirp;

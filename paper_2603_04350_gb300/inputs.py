@@ -58,6 +58,7 @@ class Problem:
     u0_range: Tuple[float, float] = (-0.9, 0.9)
     u0_lowpass: Optional[int] = None
     b: Tuple[float, ...] = ()   # advection velocity per axis (periodic): L = a*Lap - b.grad - c
+    nl_form: str = "if"         # nonlinear term: "if" (integrating factor) or "etd1" (order 1, no source)
 
     @property
     def ndim(self) -> int:
@@ -212,10 +213,11 @@ def served_mix(count: int = 2000, seed: int = 5, rate_per_s: float = 100.0,
                grids=(64, 128, 256, 512, 1024), nts=(16, 32, 64, 128, 256), orders=(1, 2, 6)):
     """Requests with Poisson arrivals; kind, grid, Nt and order drawn uniformly.
 
-    Heat requests are Dirichlet (the Dirichlet workload's parameters with the
-    drawn sizes; a grid of g intervals per side, i.e. g - 1 interior points
-    and h = 1/g); Allen-Cahn requests are periodic (the 256^2 workload's
-    parameters with the drawn sizes)."""
+    Heat requests are Dirichlet: the 1024^2 Dirichlet workload's parameters
+    (GMRES, tol 1e-9, the smooth source) with the drawn sizes, a grid g^2 being
+    g x g interior points as in that workload; Allen-Cahn requests are
+    periodic (the 256^2 workload's parameters with the drawn sizes, fixed
+    point, tol 1e-8)."""
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate_per_s, size=count)
     t = np.cumsum(gaps)
@@ -228,8 +230,8 @@ def served_mix(count: int = 2000, seed: int = 5, rate_per_s: float = 100.0,
         rseed = int(rng.integers(0, 2**31 - 1))
         if kind == 0:
             base = HEAT_DIRICHLET_1024
-            prob = base.with_(name=f"req{i}_heat_{g}_{nt}_{s}", n=(g - 1, g - 1), Nt=nt, dt=0.1 / nt,
-                              order=s, seed=rseed, solver="fp", tol=1e-8)
+            prob = base.with_(name=f"req{i}_heat_{g}_{nt}_{s}", n=(g, g), Nt=nt, dt=0.1 / nt,
+                              order=s, seed=rseed)
         else:
             base = ALLEN_CAHN_256
             prob = base.with_(name=f"req{i}_ac_{g}_{nt}_{s}", n=(g, g), Nt=nt, order=s,

@@ -53,8 +53,15 @@ class Record:
         return self.end - self.arrival
 
 
+# GMRES restart length of served requests: the mixed path's refinement ends a
+# cycle after one or two iterations, and every basis vector of a 1024^2 x 255
+# request is 2.1 GB, so the engine keeps 4 (7 vectors with the two work
+# vectors; the workload default of 20 holds 23)
+SERVE_GMRES_RESTART = 4
+
+
 def _spec(p: I.Problem, precision: int, max_iter: int) -> expd.PlanSpec:
-    return expd.spec_from_problem(p, precision=precision, max_iter=max_iter)
+    return expd.spec_from_problem(p, precision=precision, max_iter=max_iter, gmres_restart=SERVE_GMRES_RESTART)
 
 
 def _key(spec: expd.PlanSpec):
@@ -100,6 +107,10 @@ class Admission:
     def push(self, item, need: int) -> None:
         self.queue.append((item, int(need)))
 
+    def push_front(self, item, need: int) -> None:
+        """Re-queue a request that has to wait (ahead of every later arrival)."""
+        self.queue.insert(0, (item, int(need)))
+
     def take(self):
         for i, (item, need) in enumerate(self.queue):
             if self.in_use + self.cached + need <= self.budget or (self.in_use == 0 and self.cached == 0):
@@ -133,6 +144,7 @@ class Engine:
         self._adm = Admission(self.budget)
         self._closed = False
         self.records: List[Record] = []
+        self._alone: set = set()      # workers retrying a request alone after running out of memory
         self.errors: List[str] = []
         self.results: dict = {}
         self.keep_results = False
@@ -147,6 +159,16 @@ class Engine:
             with self._cv:
                 got = None
                 while True:
+                    # a worker retrying alone after running out of memory: hand
+                    # back every cached plan and take nothing new until it is done
+                    if self._alone - {wid}:
+                        while cache:
+                            _, (pl, b) = cache.popitem(last=False)
+                            pl.destroy()
+                            self._adm.cached -= b
+                        self._cv.notify_all()
+                        self._cv.wait(timeout=0.05)
+                        continue
                     got = self._adm.take()
                     if got is not None or (self._closed and not self._adm.queue):
                         break
@@ -164,6 +186,7 @@ class Engine:
             status, iters = expd.OK, 0
             spec = _spec(p, self.precision, self.max_iter)
             key = _key(spec)
+            requeue = False
             for attempt in range(3):
                 plan = None
                 status = expd.OK
@@ -208,18 +231,53 @@ class Engine:
                         self.errors.append(f"{p.name}: {e}")
                         break
                     # device memory held outside the budget (PyTorch's cache of
-                    # earlier inputs, this worker's cached plans): release and retry
+                    # earlier inputs, cached plans): release this worker's plans
+                    # and retry; the last retry waits until this request is the
+                    # only one running and every cached plan is gone, so a
+                    # request that fits the device alone always completes
                     with self._cv:
                         while cache:
                             _, (pl, b) = cache.popitem(last=False)
                             pl.destroy()
                             self._adm.cached -= b
+                        if attempt == 1:
+                            if self._alone:
+                                # another worker is already retrying alone: hand the
+                                # request back to the head of the queue
+                                requeue = True
+                            else:
+                                self._alone.add(wid)
+                                while self._adm.in_use > need or self._adm.cached > 0:
+                                    self._cv.notify_all()
+                                    self._cv.wait(timeout=0.05)
+                    if requeue:
+                        break
+                    # only this worker's stream is synchronised: another worker
+                    # may be capturing a CUDA graph, which a device-wide
+                    # synchronisation (or a free that implies one) would break
                     stream.synchronize()
-                    torch.cuda.empty_cache()
+                    try:
+                        torch.cuda.empty_cache()
+                    except RuntimeError:
+                        pass
                     self.retries += 1
+                except Exception as e:  # any other failure: recorded, never lost
+                    status = expd.ERR_CUDA
+                    self.errors.append(f"{p.name}: {type(e).__name__}: {e}")
+                    if plan is not None:
+                        try:
+                            plan.destroy()
+                        except Exception:
+                            pass
+                    break
             end = time.perf_counter() - t0
             with self._cv:
+                self._alone.discard(wid)
                 self._adm.done(need)
+                if requeue:
+                    self._adm.push_front((arrival, rid, p), need)
+                    self._cv.notify_all()
+                    continue
                 self.records.append(Record(rid, p.name, arrival, start, end, p.unknowns, iters, status,
                                            self.precision))
                 self._cv.notify_all()
@@ -275,15 +333,18 @@ def summary(records: List[Record], wall: Optional[float] = None) -> dict:
 
 
 def run_one_at_a_time(requests: List[I.Request], device: int = 0, precision: int = expd.PREC_FP64,
-                      max_iter: int = 200, cache_plans: int = 4) -> List[Record]:
+                      max_iter: int = 200, cache_plans: int = 4, cache_bytes: Optional[int] = None) -> List[Record]:
     """Baseline server: one request at a time, first come first served.
 
     Each request is solved alone (plan, inputs, solve, synchronise) to measure
     its service time (plans are reused across equal requests, up to
-    `cache_plans` of them, as the engine does); a single-server FIFO queue then gives start_i =
-    max(arrival_i, end_{i-1}) and end_i = start_i + service_i, which is exactly
-    what a one-at-a-time server does with these arrivals."""
+    `cache_plans` of them and `cache_bytes` of device memory -- half the free
+    memory by default -- as the engine does); a single-server FIFO queue then
+    gives start_i = max(arrival_i, end_{i-1}) and end_i = start_i + service_i,
+    which is exactly what a one-at-a-time server does with these arrivals."""
     dev = torch.device("cuda", device)
+    if cache_bytes is None:
+        cache_bytes = int(0.5 * torch.cuda.mem_get_info(dev)[0])
     out = []
     prev_end = 0.0
     cache: "collections.OrderedDict" = collections.OrderedDict()   # the same plan reuse as the engine
@@ -293,7 +354,12 @@ def run_one_at_a_time(requests: List[I.Request], device: int = 0, precision: int
         t0 = time.perf_counter()
         spec = _spec(p, precision, max_iter)
         key = _key(spec)
-        plan = cache.pop(key, None) or expd.plan_create(spec)
+        plan = cache.pop(key, None)
+        if plan is None:
+            need = request_bytes(p, precision, max_iter)
+            while cache and sum(pl.workspace_bytes() for pl in cache.values()) + need > cache_bytes:
+                cache.popitem(last=False)[1].destroy()
+            plan = expd.plan_create(spec)
         u0, f = device_inputs(p, dev, torch.cuda.current_stream())
         U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=dev)
         fn = plan.solve_gmres if p.solver == "gmres" else plan.solve_fp

@@ -847,3 +847,129 @@ def test_graph_sequential_stepping_matches_direct(expd, p):
             plan.solve_sequential(dev(u0), fd, U, stream=side)
             side.synchronize()
             assert np.array_equal(U.cpu().numpy(), ref), k
+
+
+# ----------------------------------------------- real-column time kernel --
+# Dirichlet grids run a real-column kernel (16 columns per CTA, two per warp,
+# swizzled FFT buffers, float32 combination for operator applications on the
+# mixed path); EXPD_TIME_REAL=0 selects the generic kernel.  Both compute the
+# same operations: the preconditioner and the residual agree to the oracle's
+# tolerance of their precision, and the Krylov solves reach the float64 bar.
+REAL_CASES = [c for c in CASES if c.bc == "dirichlet"] + [
+    P("d2d_blue127", "dirichlet", (19, 13), 2, Nt=128, alpha=1e-3, dt=1e-3),   # Ns = 127: Bluestein L = 256
+    P("d2d_pow2_32", "dirichlet", (17, 9), 1, Nt=32),                            # Ns = 32: radix-2
+]
+
+
+@pytest.mark.parametrize("p", REAL_CASES, ids=[p.name for p in REAL_CASES])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_real_time_kernel_matches_generic_and_oracle(expd, p, prec, monkeypatch):
+    sp = O.spec_of(p)
+    r = rand_field(p, (p.Ns,), 23)
+    ref = O.precond_apply(sp, r)
+    precision = expd.PREC_FP64 if prec == "fp64" else expd.PREC_MIXED
+    outs = {}
+    for kind in ("real", "generic"):
+        if kind == "generic":
+            monkeypatch.setenv("EXPD_TIME_REAL", "0")
+        else:
+            monkeypatch.delenv("EXPD_TIME_REAL", raising=False)
+        S = torch.empty_like(dev(r))
+        with expd.plan_create(expd.spec_from_problem(p, precision=precision)) as plan:
+            plan.precond_apply(dev(r), S)
+        outs[kind] = host(S)
+    bound = 1e-11 if prec == "fp64" else 6e-8 * 16 / p.alpha
+    assert relmax(outs["real"], ref) < bound
+    assert relmax(outs["generic"], ref) < bound
+    assert relmax(outs["real"], outs["generic"]) < bound
+    if p.nonlin == "none":
+        rng = np.random.default_rng(24)
+        u0 = rng.standard_normal(p.n)
+        f = rng.standard_normal((p.Nt,) + p.n)
+        seq = O.sequential_solve(sp, u0, f)[1:]
+        monkeypatch.delenv("EXPD_TIME_REAL", raising=False)
+        U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+        with expd.plan_create(expd.spec_from_problem(p, precision=precision, tol=1e-12, max_iter=400)) as plan:
+            for fn in (plan.solve_gmres, plan.solve_bicgstab, plan.solve_fp):
+                info = fn(dev(u0), dev(f), U)
+                assert O.rel_error(host(U), seq) < 1e-10, (fn.__name__, info)
+
+
+# ------------------------------------------------------------------- ETD1 --
+# u_n = A u_{n-1} + dt phi_1(dt L) N(u_{n-1}) (nl_form = EXPD_NLF_ETD1): the
+# phi_1 tables, the one-slice shift of the transformed N, the phi_1 N(u_0)
+# term of the right-hand side and the ETD sequential step, against the oracle.
+ETD_CASES = [
+    P("etd_p2d_ns16", "periodic", (16, 32), 1, nonlin="allen_cahn", a=0.01, c=0.0, dt=1e-3, Nt=16,
+      alpha=1e-3).with_(nl_form="etd1"),                                      # register kernel (mixed)
+    P("etd_p2d_ns20", "periodic", (32, 16), 1, nonlin="allen_cahn", a=0.01, c=0.1, dt=2e-3, Nt=20,
+      alpha=1e-3).with_(nl_form="etd1"),                                      # Bluestein window
+    P("etd_d2d", "dirichlet", (9, 12), 1, nonlin="allen_cahn", a=0.01, c=0.0, dt=1e-3, Nt=12,
+      alpha=1e-3).with_(nl_form="etd1"),
+    P("etd_p1d", "periodic", (64,), 1, nonlin="allen_cahn", a=0.05, c=0.0, dt=5e-3, Nt=24,
+      alpha=1e-2).with_(nl_form="etd1"),
+]
+ETD_IDS = [p.name for p in ETD_CASES]
+
+
+@pytest.mark.parametrize("guess", GUESSES)
+@pytest.mark.parametrize("p", ETD_CASES, ids=ETD_IDS)
+def test_etd1_richardson_iterates_match_oracle(expd, p, guess):
+    sp = O.spec_of(p)
+    assert sp.nl_form == "etd1"
+    u0 = np.random.default_rng(31).uniform(-0.8, 0.8, p.n)
+    for k in (1, 2, 3):
+        ref = O.richardson(sp, u0, None, max_iter=k, init=guess).U[1:]
+        U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+        spec = expd.spec_from_problem(p, tol=1e-300, max_iter=k, guess=guess_code(expd, guess))
+        assert spec.nl_form == expd.NLF_ETD1
+        with expd.plan_create(spec) as plan:
+            info = plan.solve_fp(dev(u0), None, U, allow_not_converged=True)
+        assert info["iterations"] == k
+        assert O.rel_error(host(U), ref) < 1e-12, (k, guess)
+
+
+@pytest.mark.parametrize("p", ETD_CASES, ids=ETD_IDS)
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_etd1_solve_and_stepper_match_sequential(expd, p, prec):
+    sp = O.spec_of(p)
+    u0 = np.random.default_rng(32).uniform(-0.8, 0.8, p.n)
+    ref = O.sequential_solve(sp, u0)[1:]
+    precision = expd.PREC_FP64 if prec == "fp64" else expd.PREC_MIXED
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, precision=precision, tol=1e-12, max_iter=200)) as plan:
+        info = plan.solve_fp(dev(u0), None, U)
+        assert O.rel_error(host(U), ref) < 1e-10, info
+        assert slice_relmax(host(U), ref) < 1e-10, info
+        plan.solve_sequential(dev(u0), None, U)
+        assert O.rel_error(host(U), ref) < 1e-12
+
+
+@pytest.mark.parametrize("p", ETD_CASES, ids=ETD_IDS)
+def test_etd1_residual_matches_oracle(expd, p):
+    sp = O.spec_of(p)
+    rng = np.random.default_rng(33)
+    u0 = 0.5 * rng.uniform(-1, 1, p.n)
+    U = 0.5 * rng.uniform(-1, 1, (p.Nt,) + p.n)
+    ref = O.residual(sp, U, O.rhs_known(sp, u0[None], None))
+    R = torch.empty((p.Ns,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p)) as plan:
+        plan.residual(dev(u0), None, dev(U), R)
+    assert relmax(host(R), ref) < 1e-11
+
+
+def test_etd1_argument_checks(expd):
+    p = ETD_CASES[0]
+    with pytest.raises(expd.ExpdError) as ei:
+        expd.plan_create(expd.spec_from_problem(p.with_(order=2, Nt=17)))
+    assert ei.value.status == expd.ERR_INVALID_ARG
+    with pytest.raises(expd.ExpdError) as ei:
+        expd.plan_create(expd.spec_from_problem(p, jacobian=expd.JAC_MEAN_U0))
+    assert ei.value.status == expd.ERR_INVALID_ARG
+    u0 = np.zeros(p.n)
+    f = np.zeros((p.Nt,) + p.n)
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p)) as plan:
+        with pytest.raises(expd.ExpdError) as ei:
+            plan.solve_fp(dev(u0), dev(f), U)
+        assert ei.value.status == expd.ERR_INVALID_ARG

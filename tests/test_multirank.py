@@ -20,11 +20,12 @@ def _rank_main(rank, world, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
     from paper_2603_04350_gb300 import inputs as I
-    p = bench.workload(rank)
+    p = bench.with_rank_seed(I.HEAT_DIRICHLET_1024, rank)
     local_ms = 10.0 + 5.0 * rank                     # rank 1 is the slowest
     total_ms, value = bench.aggregate(local_ms, p.unknowns, 4, world, dist, torch.device("cpu"))
     u0 = I.make_u0(p)
-    out[rank] = (total_ms, value, p.seed, p.n, float(u0[0, 0]))
+    f = I.make_forcing(p.with_(Nt=2))
+    out[rank] = (total_ms, value, p.seed, p.n, float(f[1].sum()))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -35,8 +36,8 @@ def test_two_rank_replicas_take_the_max_and_count_all_units():
         out = m.dict()
         mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
-    import bench
-    p = bench.workload(0)
+    from paper_2603_04350_gb300 import inputs as I
+    p = I.HEAT_DIRICHLET_1024
     for r in range(world):
         total_ms, value, seed, n, _ = res[r]
         assert total_ms == 15.0                                   # max over ranks

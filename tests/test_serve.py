@@ -24,7 +24,9 @@ def test_mix_recipe():
         assert p.Ns >= p.order + 1
         if p.bc == I.DIRICHLET:
             n = p.n[0]
-            assert ((n + 1) & n) == 0 and p.forcing and p.nonlin == I.NL_NONE   # g - 1 interior points
+            # g x g interior points, the 1024^2 Dirichlet workload's solver and tolerance
+            assert n in (64, 128, 256, 512, 1024) and p.n[1] == n
+            assert p.forcing and p.nonlin == I.NL_NONE and p.solver == "gmres" and p.tol == 1e-9
         else:
             assert p.nonlin == I.NL_ALLEN_CAHN and (p.n[0] & (p.n[0] - 1)) == 0
     assert len({r.problem.seed for r in reqs}) == 400
@@ -85,3 +87,11 @@ def test_admission_never_exceeds_budget_random():
         assert a.in_use <= 1000 or len(running) == 1
         if running and rng.random() < 0.5:
             a.done(running.pop(int(rng.integers(0, len(running)))))
+
+
+def test_admission_push_front_goes_first():
+    serve = _serve()
+    a = serve.Admission(100)
+    a.push("late", 10)
+    a.push_front("retry", 10)
+    assert a.take() == ("retry", 10) and a.take() == ("late", 10)
