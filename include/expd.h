@@ -116,7 +116,7 @@ typedef struct {
  *               sine transforms (Sec. 3.1, the eigenbasis of L_h) run on the
  *               tensor cores as split-bf16 products: every row cut into k
  *               7-bit digits, the digit products summed exactly in float32,
- *               the pairs in double-float, k = ceil((6 - log2 tol) / 7) in
+ *               the pairs in double-float, k = ceil((3 - log2 tol) / 7) in
  *               3..7, relative error about 2^(-7k).  A pipeline wait of that
  *               kernel that gives up (after 2 s, or at once when the plan is
  *               cancelled) makes the call return EXPD_ERR_TIMEOUT, or

@@ -1809,13 +1809,178 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
         EXPD_CUDA_TRY(cudaStreamSynchronize(s));
         return EXPD_OK;
     };
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hh(m + 1), hh2(m + 1), y(m);
+    // The relative preconditioned residual bounds the global relative error
+    // (the eigenvalues of P^{-1}R lie within alpha/(1-alpha) of 1, Lemma 3.4);
+    // the per-slice maximum of Sec. 7's error norm can exceed the global ratio
+    // by at most sqrt(Ns), so GMRES stops at sqrt(Ns) * relres <= tol.
+    const double tol_res = p->tol / sqrt((double)p->Ns);
+    int total = 0, refinements = 0;
+    double relres = 1.0, cn = 0.0;
+    expd_status result = EXPD_ERR_NOT_CONVERGED;
+    if (info) info->history[0] = 1.0;
+    if (mixed) {
+        // ---- float32 preconditioner, float64 residual refinement ----
+        // The basis vectors are kept unnormalised: V_j = sc[j] v_j with the
+        // orthonormal v_j, so the operator applies to V_j directly (it is
+        // linear) and no pass rescales a vector.  On Dirichlet grids the time
+        // kernel returns ||w||^2 and <V_j, w> of its output w = P^{-1} R V_j
+        // (and ||out||^2 of a residual) from its epilogue; the norm of the
+        // orthogonal part then follows from those exact dots of the same w,
+        // ||w/sc_j - sum_i h_ij v_i||^2 = ||w||^2/sc_j^2 - sum_i h_ij^2, and the
+        // next basis vector is formed only when the cycle continues.
+        auto launch = [&](const double* X, const void* F, double sigR, double* out) -> expd_status {
+            TimeOp op;
+            op.X = X;
+            op.F = F;
+            op.f_slices = p->f_slices;
+            op.sigR = sigR;
+            op.precond = 1;
+            op.f32 = 1;
+            op.out = out;
+            op.dots = 1;
+            return time_apply(p, op, s);
+        };
+        // (||out||^2, <X, out>) of the last launch: fused partials, or dot passes
+        auto out_dots = [&](const double* X, const double* out, double* oo, double* xo) -> expd_status {
+            if (p->dots_fused) {
+                expd_status r = time_reduce(p, s);
+                if (r != EXPD_OK) return r;
+                double nr[4];
+                r = read_reduced_norms(p, s, nr);
+                *oo = nr[2];
+                *xo = nr[3];
+                return r;
+            }
+            expd_status r = dots(out, 1, out, oo);
+            if (r == EXPD_OK && X) r = dots(X, 1, out, xo);
+            return r;
+        };
+        std::vector<double> sc(m + 1), hcol(m + 1), coef(m + 1);
+        // c = P^{-1} f_s, the first cycle's residual (x = 0), into V_0
+        st = launch(nullptr, p->Fh, 0.0, V);
+        if (st != EXPD_OK) return st;
+        double cn2 = 0, unused = 0;
+        st = out_dots(nullptr, V, &cn2, &unused);
+        if (st != EXPD_OK) return st;
+        cn = sqrt(cn2);
+        double beta = cn;
+        bool first = true;
+        while (cn > 0) {
+            if (!first) {
+                // r = P^{-1}(f_s - R x): the residual in float64, then preconditioned
+                st = launch(x, p->Fh, -1.0, V);
+                double b2 = 0;
+                if (st == EXPD_OK) st = out_dots(x, V, &b2, &unused);
+                if (st != EXPD_OK) return st;
+                beta = sqrt(b2);
+                ++refinements;
+            }
+            first = false;
+            relres = beta / cn;
+            if (!(relres == relres)) {
+                result = expd_fail(EXPD_ERR_DIVERGED, "GMRES residual is non-finite");
+                break;
+            }
+            if (relres <= tol_res) {
+                result = EXPD_OK;
+                break;
+            }
+            if (total >= p->max_iter) break;
+            std::fill(g.begin(), g.end(), 0.0);
+            g[0] = beta;
+            sc[0] = beta;
+            int jdone = 0;
+            expd_status stop = EXPD_OK;
+            for (int j = 0; j < m; ++j) {
+                double* w = V + (size_t)(j + 1) * n;
+                st = launch(V + (size_t)j * n, nullptr, 1.0, w);
+                if (st != EXPD_OK) return st;
+                double ww = 0, dj = 0;
+                if (p->dots_fused) {
+                    st = out_dots(V + (size_t)j * n, w, &ww, &dj);
+                    if (st == EXPD_OK && j > 0) st = dots(V, j, w, hh.data());  // <V_i, w>, i < j
+                } else {
+                    st = dots(V, j + 1, w, hh.data());
+                    if (st == EXPD_OK) st = dots(w, 1, w, &ww);
+                    dj = hh[j];
+                }
+                if (st != EXPD_OK) return st;
+                hh[j] = dj;
+                const double wn = ww / (sc[j] * sc[j]);
+                double orth = wn;
+                for (int i = 0; i <= j; ++i) {
+                    hcol[i] = hh[i] / (sc[i] * sc[j]);
+                    H[(size_t)i * m + j] = hcol[i];
+                    orth -= hcol[i] * hcol[i];
+                }
+                // the fused partials come from float32 products: below 2^-20 of
+                // ||w||^2 the difference is rounding, so the orthogonal part is
+                // taken at that resolution (the cycle then ends and the
+                // recomputed float64 residual tells the truth)
+                const double floor2 = p->dots_fused ? wn * 0x1p-20 : 0.0;
+                const double hn = sqrt(orth > floor2 ? orth : floor2);
+                H[(size_t)(j + 1) * m + j] = hn;
+                for (int i = 0; i < j; ++i) {
+                    const double t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
+                    H[(size_t)(i + 1) * m + j] = -sn[i] * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
+                    H[(size_t)i * m + j] = t;
+                }
+                const double den = hypot(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j]);
+                cs[j] = H[(size_t)j * m + j] / den;
+                sn[j] = H[(size_t)(j + 1) * m + j] / den;
+                H[(size_t)j * m + j] = den;
+                H[(size_t)(j + 1) * m + j] = 0.0;
+                g[j + 1] = -sn[j] * g[j];
+                g[j] = cs[j] * g[j];
+                ++total;
+                jdone = j + 1;
+                relres = fabs(g[j + 1]) / cn;
+                if (info && total < EXPD_MAX_HISTORY) info->history[total] = relres;
+                // the cycle ends once its residual fell by eta or claims
+                // convergence; the restart recomputes it in float64
+                if (relres <= tol_res || hn == 0 || fabs(g[j + 1]) <= p->krylov_eta * beta || j + 1 == m ||
+                    total >= p->max_iter)
+                    break;
+                stop = poll_stop(p);
+                if (stop != EXPD_OK) break;
+                // V_{j+1} = (w - sum_i hcol_i (sc_j / sc_i) V_i) / (sc_j hn), of norm ~1
+                for (int i = 0; i <= j; ++i) coef[i] = hcol[i] * sc[j] / sc[i];
+                EXPD_CUDA_TRY(cudaMemcpyAsync(h + 64, coef.data(), (j + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+                st = gm_update_norm(p, V, n, j + 1, h + 64, 1.0 / (sc[j] * hn), w, h, s);
+                double nn = 0;
+                if (st == EXPD_OK) {
+                    EXPD_CUDA_TRY(cudaMemcpyAsync(&nn, h, sizeof(double), cudaMemcpyDeviceToHost, s));
+                    EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+                }
+                if (st != EXPD_OK) return st;
+                sc[j + 1] = sqrt(nn);
+            }
+            // x += sum_i y_i v_i = sum_i (y_i / sc_i) V_i,  H y = g
+            for (int i = jdone - 1; i >= 0; --i) {
+                double acc = g[i];
+                for (int k = i + 1; k < jdone; ++k) acc -= H[(size_t)i * m + k] * y[k];
+                y[i] = acc / H[(size_t)i * m + i];
+            }
+            for (int i = 0; i < jdone; ++i) hh[i] = -y[i] / sc[i];
+            if (jdone > 0) {
+                EXPD_CUDA_TRY(cudaMemcpyAsync(h, hh.data(), jdone * sizeof(double), cudaMemcpyHostToDevice, s));
+                st = gm_update(p, V, n, jdone, h, x, s);
+                if (st != EXPD_OK) return st;
+            }
+            if (stop != EXPD_OK) {
+                EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+                result = stop;
+                break;
+            }
+        }
+    } else {
     // c = P^{-1} f_s
     {
         TimeOp op;
         op.F = p->Fh;
         op.f_slices = p->f_slices;
         op.precond = 1;
-        op.f32 = mixed;
         op.out = c;
         st = time_apply(p, op, s);
         if (st != EXPD_OK) return st;
@@ -1823,17 +1988,7 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
     double cn2 = 0;
     st = dots(c, 1, c, &cn2);
     if (st != EXPD_OK) return st;
-    const double cn = sqrt(cn2);
-    // The relative preconditioned residual bounds the global relative error
-    // (the eigenvalues of P^{-1}R lie within alpha/(1-alpha) of 1, Lemma 3.4);
-    // the per-slice maximum of Sec. 7's error norm can exceed the global ratio
-    // by at most sqrt(Ns), so GMRES stops at sqrt(Ns) * relres <= tol.
-    const double tol_res = p->tol / sqrt((double)p->Ns);
-    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hh(m + 1), hh2(m + 1), y(m);
-    int total = 0, refinements = 0;
-    double relres = 1.0;
-    expd_status result = EXPD_ERR_NOT_CONVERGED;
-    if (info) info->history[0] = 1.0;
+    cn = sqrt(cn2);
     bool first = true;
     while (cn > 0) {
         // r = P^{-1}(f_s - R x)   (= c on the first cycle, x = 0)
@@ -1842,7 +1997,6 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
         } else {
             st = residual_op(V);
             if (st != EXPD_OK) return st;
-            ++refinements;
         }
         first = false;
         double b2 = 0;
@@ -1870,15 +2024,13 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
             double* vj1 = V + (size_t)(j + 1) * n;
             st = apply_op(V + (size_t)j * n, w);
             if (st != EXPD_OK) return st;
-            // classical Gram-Schmidt; float64 preconditioner: one
-            // re-orthogonalisation (the mixed path's operator carries float32
-            // rounding, far above what a second pass would correct)
+            // classical Gram-Schmidt with one re-orthogonalisation
             st = dots(V, j + 1, w, hh.data());
             if (st == EXPD_OK) st = gm_update(p, V, n, j + 1, h, w, s);
-            if (st == EXPD_OK && !mixed) st = dots(V, j + 1, w, hh2.data());
-            if (st == EXPD_OK && !mixed) st = gm_update(p, V, n, j + 1, h, w, s);
+            if (st == EXPD_OK) st = dots(V, j + 1, w, hh2.data());
+            if (st == EXPD_OK) st = gm_update(p, V, n, j + 1, h, w, s);
             if (st != EXPD_OK) return st;
-            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + (mixed ? 0.0 : hh2[i]);
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh2[i];
             double wn2 = 0;
             st = dots(w, 1, w, &wn2);
             if (st != EXPD_OK) return st;
@@ -1908,9 +2060,6 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
                 conv = true;
                 break;
             }
-            // mixed: the cycle ends once its residual fell by eta; the restart
-            // recomputes it in float64 (iterative refinement)
-            if (mixed && fabs(g[j + 1]) <= p->krylov_eta * beta) break;
             stop = poll_stop(p);
             if (stop != EXPD_OK) break;
         }
@@ -1931,12 +2080,12 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
             result = stop;
             break;
         }
-        // float64 preconditioner: the recurrence's residual is the true one;
-        // mixed: convergence is declared only on the recomputed residual
-        if (conv && !mixed) {
+        // float64 preconditioner: the recurrence's residual is the true one
+        if (conv) {
             result = EXPD_OK;
             break;
         }
+    }
     }
     if (cn == 0) result = EXPD_OK;
     if (info) {

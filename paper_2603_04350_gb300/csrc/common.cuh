@@ -217,6 +217,102 @@ EXPD_HD void fft_dif(T2* x, int log2n, const T2* tw, int ts, int sign, int lane,
     }
 }
 
+// The same radix-4 passes for one warp of 32 lanes with the length known at
+// compile time (LOG2N) and the direction a template parameter: every pass and
+// lane loop unrolls and the strides, spans and twiddle steps become constants.
+// The arithmetic, and its order, is that of fft_dif / fft_dit.
+template <typename T2, int PAD, int LOG2N, int SIGN>
+EXPD_HD void wfft_dif(T2* x, const T2* tw, int lane) {
+    constexpr int n = 1 << LOG2N;
+#pragma unroll
+    for (int s = LOG2N - 1; s >= 1; s -= 2) {
+        const int h = 1 << (s - 1);
+        const int t4 = n >> (s + 1);
+        const int t2 = n >> s;
+#pragma unroll 2
+        for (int g0 = 0; g0 < (n >> 2); g0 += 32) {
+            const int g = g0 + lane;
+            if ((n >> 2) >= 32 || g < (n >> 2)) {
+                const int k = g & (h - 1);
+                const int i = ((g >> (s - 1)) << (s + 1)) + k;
+                T2 w2 = tw[k * t2], w4 = tw[k * t4];
+                if (SIGN > 0) {
+                    w2.y = -w2.y;
+                    w4.y = -w4.y;
+                }
+                const T2 x0 = x[padi<PAD>(i)], x1 = x[padi<PAD>(i + h)], x2 = x[padi<PAD>(i + 2 * h)],
+                         x3 = x[padi<PAD>(i + 3 * h)];
+                const T2 a0 = cadd(x0, x2), a1 = cadd(x1, x3);
+                const T2 a2 = cmul(csub(x0, x2), w4);
+                const T2 a3 = cmul_quarter(cmul(csub(x1, x3), w4), SIGN);
+                x[padi<PAD>(i)] = cadd(a0, a1);
+                x[padi<PAD>(i + h)] = cmul(csub(a0, a1), w2);
+                x[padi<PAD>(i + 2 * h)] = cadd(a2, a3);
+                x[padi<PAD>(i + 3 * h)] = cmul(csub(a2, a3), w2);
+            }
+        }
+        EXPD_SYNCWARP();
+    }
+    if (LOG2N & 1) {
+#pragma unroll
+        for (int b0 = 0; b0 < (n >> 1); b0 += 32) {
+            const int b = b0 + lane;
+            if ((n >> 1) >= 32 || b < (n >> 1)) {
+                const T2 u = x[padi<PAD>(2 * b)], v = x[padi<PAD>(2 * b + 1)];
+                x[padi<PAD>(2 * b)] = cadd(u, v);
+                x[padi<PAD>(2 * b + 1)] = csub(u, v);
+            }
+        }
+        EXPD_SYNCWARP();
+    }
+}
+
+template <typename T2, int PAD, int LOG2N, int SIGN>
+EXPD_HD void wfft_dit(T2* x, const T2* tw, int lane) {
+    constexpr int n = 1 << LOG2N;
+    if (LOG2N & 1) {
+#pragma unroll
+        for (int b0 = 0; b0 < (n >> 1); b0 += 32) {
+            const int b = b0 + lane;
+            if ((n >> 1) >= 32 || b < (n >> 1)) {
+                const T2 u = x[padi<PAD>(2 * b)], v = x[padi<PAD>(2 * b + 1)];
+                x[padi<PAD>(2 * b)] = cadd(u, v);
+                x[padi<PAD>(2 * b + 1)] = csub(u, v);
+            }
+        }
+        EXPD_SYNCWARP();
+    }
+#pragma unroll
+    for (int s = (LOG2N & 1); s < LOG2N; s += 2) {
+        const int h = 1 << s;
+        const int t2 = n >> (s + 1);
+        const int t4 = n >> (s + 2);
+#pragma unroll 2
+        for (int g0 = 0; g0 < (n >> 2); g0 += 32) {
+            const int g = g0 + lane;
+            if ((n >> 2) >= 32 || g < (n >> 2)) {
+                const int k = g & (h - 1);
+                const int i = ((g >> s) << (s + 2)) + k;
+                T2 w2 = tw[k * t2], w4 = tw[k * t4];
+                if (SIGN > 0) {
+                    w2.y = -w2.y;
+                    w4.y = -w4.y;
+                }
+                const T2 x0 = x[padi<PAD>(i)], x1 = cmul(x[padi<PAD>(i + h)], w2);
+                const T2 x2 = x[padi<PAD>(i + 2 * h)], x3 = cmul(x[padi<PAD>(i + 3 * h)], w2);
+                const T2 a0 = cadd(x0, x1), a1 = csub(x0, x1);
+                const T2 a2 = cmul(cadd(x2, x3), w4);
+                const T2 a3 = cmul_quarter(cmul(csub(x2, x3), w4), SIGN);
+                x[padi<PAD>(i)] = cadd(a0, a2);
+                x[padi<PAD>(i + 2 * h)] = csub(a0, a2);
+                x[padi<PAD>(i + h)] = cadd(a1, a3);
+                x[padi<PAD>(i + 3 * h)] = csub(a1, a3);
+            }
+        }
+        EXPD_SYNCWARP();
+    }
+}
+
 // ---- coefficient helpers: real a_j E^j (diffusion) or complex (advection) ----
 // acc + c, and r - c x, for a real or a complex coefficient c
 EXPD_HD float2 acc_add(float2 a, float c) { return make_float2(a.x + c, a.y); }

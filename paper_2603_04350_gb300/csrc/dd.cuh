@@ -45,6 +45,7 @@ EXPD_HD float f32_from_bits(unsigned u) {
 EXPD_HD float f32_rn_from_f64(double v) {
     const unsigned long long b = f64_bits(v);
     const int e = (int)((b >> 52) & 0x7ff);
+    if ((b << 1) == 0ull) return f32_from_bits((unsigned)(b >> 63) << 31);  // signed zero
     if (e < 897 || e > 1150) return (float)v;  // outside float's normal range
     const unsigned long long m = b & 0xfffffffffffffULL;
     unsigned u = ((unsigned)(b >> 63) << 31) | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29);
@@ -54,8 +55,9 @@ EXPD_HD float f32_rn_from_f64(double v) {
 }
 
 // Exact float -> double by integer operations (every float is a double):
-// normal values rebias the exponent and widen the fraction; zeros,
-// subnormals, infinities and NaN take the ordinary conversion.
+// normal values rebias the exponent and widen the fraction, subnormals are
+// normalised by their leading-zero count, zeros keep their sign; infinities
+// and NaN take the ordinary conversion.
 EXPD_HD double f64_from_f32(float f) {
 #ifdef __CUDA_ARCH__
     const unsigned u = __float_as_uint(f);
@@ -64,9 +66,27 @@ EXPD_HD double f64_from_f32(float f) {
     memcpy(&u, &f, 4);
 #endif
     const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)f;
-    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
-                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    const unsigned m = u & 0x7fffffu;
+    unsigned long long b;
+    if (e == 0u) {
+        if (m == 0u) {
+            b = (unsigned long long)(u >> 31) << 63;  // signed zero
+        } else {
+            // subnormal: m 2^-149 = 1.f 2^(22 - z - 149), z leading zeros of m in 23 bits
+#ifdef __CUDA_ARCH__
+            const int z = __clz(m) - 9;
+#else
+            const int z = __builtin_clz(m) - 9;
+#endif
+            b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(896 - z) << 52) |
+                ((unsigned long long)((m << (z + 1)) & 0x7fffffu) << 29);
+        }
+    } else if (e == 0xffu) {
+        return (double)f;  // infinity, NaN
+    } else {
+        b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
+            ((unsigned long long)m << 29);
+    }
 #ifdef __CUDA_ARCH__
     return __longlong_as_double((long long)b);
 #else
@@ -74,6 +94,23 @@ EXPD_HD double f64_from_f32(float f) {
     memcpy(&d, &b, 8);
     return d;
 #endif
+}
+
+// The same with magnitudes below float's normal range (|v| < 2^-126) flushed
+// to signed zero, all by integer operations: the input conversion of the
+// float32 preconditioner, whose float32 transforms hold values relative to
+// the largest one, far above 2^-126 (finite values above float's range take the
+// hardware conversion, to infinity).
+EXPD_HD float f32_ftz_from_f64(double v) {
+    const unsigned long long b = f64_bits(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 897) return f32_from_bits((unsigned)(b >> 63) << 31);
+    if (e > 1150) return (float)v;
+    const unsigned long long m = b & 0xfffffffffffffULL;
+    unsigned u = ((unsigned)(b >> 63) << 31) | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29);
+    const unsigned long long tail = m & 0x1fffffffULL;
+    if (tail > 0x10000000ULL || (tail == 0x10000000ULL && (u & 1u))) ++u;
+    return f32_from_bits(u);
 }
 
 struct dd;

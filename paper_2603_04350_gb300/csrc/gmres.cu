@@ -5,6 +5,8 @@
 // mode with 0 < kx < NX/2 stands for itself and its conjugate and weighs 2
 // (Parseval), so GMRES in the eigenbasis reproduces physical-space GMRES.
 // Reductions are two-level with a fixed grid and fixed order (deterministic).
+#include <algorithm>
+
 #include "common.cuh"
 #include "plan.h"
 
@@ -21,31 +23,77 @@ __device__ __forceinline__ double elem_weight(long long e, long long Mcol, int K
     return (kx == 0 || 2 * kx == NX) ? 1.0 : 2.0;
 }
 
-// partial[i][block] = sum over this block's elements of w_e V_i[e] x[e]
-__global__ void __launch_bounds__(GM_THREADS) dots_kernel(const double* __restrict__ V, long long ld, int k,
+// partial[i][block] = sum over this block's elements of w_e V_i[e] x[e], for
+// the K (compile-time) vectors V_0..V_{K-1}: x is read once for all of them,
+// the elements visited in a fixed order (deterministic).
+constexpr int GM_DOTS = 8;
+
+template <int K>
+__global__ void __launch_bounds__(GM_THREADS) dots_kernel(const double* __restrict__ V, long long ld,
                                                           const double* __restrict__ x, long long n,
                                                           long long Mcol, int KX, int NX, int realcol,
                                                           double* __restrict__ partial) {
-    __shared__ double red[GM_THREADS / 32];
+    __shared__ double red[K][GM_THREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = 0; i < k; ++i) {
-        double acc = 0.0;
-        for (long long base = (long long)blockIdx.x * GM_CHUNK; base < n; base += (long long)gridDim.x * GM_CHUNK) {
+    double acc[K];
 #pragma unroll
-            for (int t = 0; t < GM_PER_THREAD; ++t) {
-                const long long e = base + t * GM_THREADS + threadIdx.x;
-                if (e < n) acc = fma(elem_weight(e, Mcol, KX, NX, realcol) * V[(long long)i * ld + e], x[e], acc);
+    for (int i = 0; i < K; ++i) acc[i] = 0.0;
+    for (long long base = (long long)blockIdx.x * GM_CHUNK; base < n; base += (long long)gridDim.x * GM_CHUNK) {
+#pragma unroll
+        for (int t = 0; t < GM_PER_THREAD; ++t) {
+            const long long e = base + t * GM_THREADS + threadIdx.x;
+            if (e < n) {
+                const double xe = elem_weight(e, Mcol, KX, NX, realcol) * x[e];
+#pragma unroll
+                for (int i = 0; i < K; ++i) acc[i] = fma(V[(long long)i * ld + e], xe, acc[i]);
             }
         }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) red[warp] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int w = 0; w < GM_THREADS / 32; ++w) s += red[w];
-            partial[(long long)i * gridDim.x + blockIdx.x] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        double a = acc[i];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) red[i][warp] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double t = 0.0;
+        for (int w = 0; w < GM_THREADS / 32; ++w) t += red[threadIdx.x][w];
+        partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// w = scale (w - sum_{i<k} c[i] V_i), partial[block] = sum of w_e (new w)^2
+// over this block's elements (fixed order): the next Krylov basis vector and
+// its norm in one pass.
+__global__ void __launch_bounds__(GM_THREADS) update_norm_kernel(const double* __restrict__ V, long long ld, int k,
+                                                                 const double* __restrict__ c, double scale,
+                                                                 double* __restrict__ w, long long n, long long Mcol,
+                                                                 int KX, int NX, int realcol,
+                                                                 double* __restrict__ partial) {
+    __shared__ double red[GM_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double acc = 0.0;
+    for (long long base = (long long)blockIdx.x * GM_CHUNK; base < n; base += (long long)gridDim.x * GM_CHUNK) {
+#pragma unroll
+        for (int t = 0; t < GM_PER_THREAD; ++t) {
+            const long long e = base + t * GM_THREADS + threadIdx.x;
+            if (e < n) {
+                double v = w[e];
+                for (int i = 0; i < k; ++i) v = fma(-c[i], V[(long long)i * ld + e], v);
+                v *= scale;
+                w[e] = v;
+                acc = fma(elem_weight(e, Mcol, KX, NX, realcol) * v, v, acc);
+            }
         }
-        __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < GM_THREADS / 32; ++q) t += red[q];
+        partial[blockIdx.x] = t;
     }
 }
 
@@ -89,10 +137,44 @@ expd_status gm_dots(expd_plan p, const double* V, long long ld, int k, const dou
     const long long n = eigen_elems(p);
     const int grid = p->sm_count * 4;
     double* partial = h_dev + 128;  // caller reserves 128 + 65 * grid doubles
-    KProf kp(p, s, EXPD_K_GMRES, 8.0 * (k + 1) * (double)n, 3.0 * k * (double)n);
-    dots_kernel<<<grid, GM_THREADS, 0, s>>>(V, ld, k, w, n, p->Mcol, p->KX, p->NX, p->realcol, partial);
-    EXPD_CUDA_TRY(cudaGetLastError());
+    KProf kp(p, s, EXPD_K_GMRES, 8.0 * (k + (k + GM_DOTS - 1) / GM_DOTS) * (double)n, 3.0 * k * (double)n);
+    // chunks of up to GM_DOTS vectors per pass of x
+    for (int i0 = 0; i0 < k; i0 += GM_DOTS) {
+        const int kk = std::min(GM_DOTS, k - i0);
+        const double* Vc = V + (long long)i0 * ld;
+        double* pc = partial + (long long)i0 * grid;
+        switch (kk) {
+#define EXPD_DOTS_CASE(K)                                                                                      \
+    case K:                                                                                                    \
+        dots_kernel<K><<<grid, GM_THREADS, 0, s>>>(Vc, ld, w, n, p->Mcol, p->KX, p->NX, p->realcol, pc);     \
+        break;
+            EXPD_DOTS_CASE(1)
+            EXPD_DOTS_CASE(2)
+            EXPD_DOTS_CASE(3)
+            EXPD_DOTS_CASE(4)
+            EXPD_DOTS_CASE(5)
+            EXPD_DOTS_CASE(6)
+            EXPD_DOTS_CASE(7)
+            EXPD_DOTS_CASE(8)
+#undef EXPD_DOTS_CASE
+        }
+        EXPD_CUDA_TRY(cudaGetLastError());
+    }
     dots_final<<<k, 256, 0, s>>>(partial, grid, k, h_dev);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+expd_status gm_update_norm(expd_plan p, const double* V, long long ld, int k, const double* c_dev, double scale,
+                           double* w, double* h_dev, cudaStream_t s) {
+    const long long n = eigen_elems(p);
+    const int grid = p->sm_count * 4;
+    double* partial = h_dev + 128;
+    KProf kp(p, s, EXPD_K_GMRES, 8.0 * (k + 2) * (double)n, (2.0 * k + 3.0) * (double)n);
+    update_norm_kernel<<<grid, GM_THREADS, 0, s>>>(V, ld, k, c_dev, scale, w, n, p->Mcol, p->KX, p->NX, p->realcol,
+                                                   partial);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    dots_final<<<1, 256, 0, s>>>(partial, grid, 1, h_dev);
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }

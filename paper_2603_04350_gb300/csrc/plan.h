@@ -132,6 +132,7 @@ struct expd_plan_s {
     int time_grid = 0;            // CTAs of the time kernel (multiple of SM count)
     int partial_cap = 0;          // CTAs the partial-norm buffer has room for
     int time_grid_used = 0;       // CTAs of the last time-kernel launch (for the reduction)
+    int dots_fused = 0;           // the last time-kernel launch produced the requested Krylov partials
     int jacobian = 0;             // EXPD_JAC_*
     int guess = 0;                // EXPD_GUESS_*: the fixed point's initial iterate
     int f_slices = 0;             // leading slices of the right-hand side Fh / F32 that can be nonzero
@@ -307,6 +308,8 @@ struct TimeOp {
     int stdd = 0;              // X, F, NL, out and the residual arithmetic in double-float
     const void* X32 = nullptr; // double-float accumulation: read the iterate from this float32 array
                                // (exact in double-float) and write X + s to X (register kernel)
+    int dots = 0;              // Krylov: per-slice partials (||out||^2, <X, out>) for time_reduce,
+                               // where the kernel taken supports them (p->dots_fused tells)
 };
 expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s);
 // The register time kernel serves this plan's window (Ns in {16, 32, 64}).
@@ -326,6 +329,9 @@ expd_status gm_dots(expd_plan p, const double* V, long long ld, int k, const dou
 // w -= sum_i h[i] V_i
 expd_status gm_update(expd_plan p, const double* V, long long ld, int k, const double* h_dev, double* w,
                       cudaStream_t s);
+// w = scale (w - sum_i c[i] V_i) and h_dev[0] = the weighted ||w||^2 of the result, in one pass
+expd_status gm_update_norm(expd_plan p, const double* V, long long ld, int k, const double* c_dev, double scale,
+                           double* w, double* h_dev, cudaStream_t s);
 // y = a*x + b*y  (plain elementwise)
 expd_status gm_axpby(expd_plan p, long long n, double a, const double* x, double b, double* y, cudaStream_t s);
 long long eigen_elems(expd_plan p);  // doubles per space-time eigen vector

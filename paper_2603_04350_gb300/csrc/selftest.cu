@@ -290,6 +290,18 @@ static void test_conversions(std::mt19937_64& rng) {
         const double a = f64_from_f32(f), b = (double)f;
         if (!(a == b || (a != a && b != b)) || (a == 0.0 && std::signbit(a) != std::signbit(b))) ++bad;
     }
+    // the flushing variant: the rounding of the hardware conversion on float's
+    // normal range, signed zero below it
+    for (int i = 0; i < 200000; ++i) {
+        double v = ldexp(frac(rng), ex(rng));
+        if (i & 1) v = -v;
+        const float a = f32_ftz_from_f64(v);
+        const float want = fabs(v) < ldexp(1.0, -126) ? (v < 0 ? -0.0f : 0.0f) : (float)v;
+        if (a != want || std::signbit(a) != std::signbit(want)) ++bad;
+    }
+    if (f32_ftz_from_f64(-0.0) != 0.0f || !std::signbit(f32_ftz_from_f64(-0.0)) || f32_rn_from_f64(-0.0) != 0.0f ||
+        !std::signbit(f32_rn_from_f64(-0.0)))
+        ++bad;
     const float fspec[] = {0.0f, -0.0f, 1.0f, -1.0f, 3.4e38f, 1e-40f, -1e-45f, INFINITY, -INFINITY};
     for (float f : fspec)
         if (f64_from_f32(f) != (double)f) ++bad;

@@ -33,7 +33,8 @@ struct TimeArgs {
     const void* osc;  // [Ns] in the storage precision ST
     const float* gam32;  // [Ns] float32 copies (residuals formed in float32)
     const float* osc32;
-    int norms;        // accumulate the per-slice norm partials (the fixed point's stopping test)
+    int norms;        // per-slice partials: 0 none, 1 (||s||^2, ||X + s||^2) for the fixed point,
+                      // 2 (||out||^2, <X, out>) for the Krylov solvers
     const void* lam;  // PT2 tables
     const void* tw;
     const void* chirp;
@@ -100,6 +101,22 @@ __device__ __forceinline__ dd coef<dd>(const TimeArgs& A, int j, long long m) {
     return A.Cdd[(long long)(j - 1) * A.Mcol + m];
 }
 
+// Asynchronous global -> shared copy of one element (4, 8 or 16 bytes); a
+// source size of 0 fills the destination with zeros (columns past the end).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? BYTES : 0;
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(BYTES), "r"(n)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <typename ST>
 __device__ __forceinline__ ST mode_weight(long long m, int KX, int NX, int realcol) {
     if (realcol) return (ST)1;
@@ -113,3 +130,7 @@ __device__ __forceinline__ ST mode_weight(long long m, int KX, int NX, int realc
 // with the float32 preconditioner; st = 1 for float32 storage, 2 for
 // double-float, 0 for float64.
 expd_status time_reg_launch(expd_plan p, expd_time::TimeArgs& a, int st, cudaStream_t s);
+
+// Real-column time kernel (Dirichlet grids; time_real.cu): float32 (f32 = 1)
+// or float64 preconditioner, float32 (st32 = 1) or float64 storage.
+expd_status time_real_launch(expd_plan p, expd_time::TimeArgs& a, int f32, int st32, cudaStream_t s);

@@ -17,7 +17,7 @@
 
 // Step (a): on exit w[k] holds Y_k (radix-2) or L Y_k (Bluestein), natural order.
 // PAD selects the buffer's index map (padi): every access to w goes through it.
-template <typename PT, typename PT2, int PAD = 0>
+template <typename PT, typename PT2, int PAD = 0, int LOG2L = 0>
 EXPD_HD void precond_step_a(PT2* w, int Ns, int L, int log2L, int bluestein, const PT2* tw, const PT2* chirp,
                             const PT2* bp, int lane, int nlanes) {
     if (bluestein) {
@@ -26,14 +26,17 @@ EXPD_HD void precond_step_a(PT2* w, int Ns, int L, int log2L, int bluestein, con
         EXPD_SYNCWARP();
         // Step (a) by chirp-z: Y_k = c_k sum_n (y_n c_n) conj(c_{k-n}),
         // the convolution as FFT_L^{-1}(FFT_L(.) * FFT_L(kernel)).
-        fft_dif<PT2, PAD>(w, log2L, tw, 1, -1, lane, nlanes);
+        if constexpr (LOG2L > 0) wfft_dif<PT2, PAD, LOG2L, -1>(w, tw, lane);
+        else fft_dif<PT2, PAD>(w, log2L, tw, 1, -1, lane, nlanes);
         for (int k = lane; k < L; k += nlanes) w[padi<PAD>(k)] = cmul(w[padi<PAD>(k)], bp[k]);
         EXPD_SYNCWARP();
-        fft_dit<PT2, PAD>(w, log2L, tw, 1, +1, lane, nlanes);
+        if constexpr (LOG2L > 0) wfft_dit<PT2, PAD, LOG2L, +1>(w, tw, lane);
+        else fft_dit<PT2, PAD>(w, log2L, tw, 1, +1, lane, nlanes);
         for (int k = lane; k < Ns; k += nlanes) w[padi<PAD>(k)] = cmul(w[padi<PAD>(k)], chirp[k]);  // = L * Y_k
         EXPD_SYNCWARP();
     } else {
-        fft_dit<PT2, PAD>(w, log2L, tw, 1, +1, lane, nlanes);  // natural Y_k
+        if constexpr (LOG2L > 0) wfft_dit<PT2, PAD, LOG2L, +1>(w, tw, lane);  // natural Y_k
+        else fft_dit<PT2, PAD>(w, log2L, tw, 1, +1, lane, nlanes);
     }
 }
 
@@ -55,18 +58,20 @@ EXPD_HD PT2 precond_divisor(PT2 lk, const CJ* cp, int order, PT one) {
 
 // Step (c) from Z_k in natural order (Bluestein: already times conj(c_k));
 // returns the output scale.
-template <typename PT, typename PT2, int PAD = 0>
+template <typename PT, typename PT2, int PAD = 0, int LOG2L = 0>
 EXPD_HD double precond_step_c(PT2* w, int Ns, int L, int log2L, int bluestein, const PT2* tw, const PT2* chirp,
                               const PT2* bm, int lane, int nlanes) {
     if (bluestein)
         for (int k = Ns + lane; k < L; k += nlanes) w[padi<PAD>(k)] = c2((PT)0, (PT)0);
     EXPD_SYNCWARP();
     // Step (c): z_n = sum_k Z_k e^{-2 pi i kn/Ns}
-    fft_dif<PT2, PAD>(w, log2L, tw, 1, -1, lane, nlanes);
+    if constexpr (LOG2L > 0) wfft_dif<PT2, PAD, LOG2L, -1>(w, tw, lane);
+    else fft_dif<PT2, PAD>(w, log2L, tw, 1, -1, lane, nlanes);
     if (!bluestein) return 1.0 / Ns;  // bit-reversed output
     for (int k = lane; k < L; k += nlanes) w[padi<PAD>(k)] = cmul(w[padi<PAD>(k)], bm[k]);
     EXPD_SYNCWARP();
-    fft_dit<PT2, PAD>(w, log2L, tw, 1, +1, lane, nlanes);
+    if constexpr (LOG2L > 0) wfft_dit<PT2, PAD, LOG2L, +1>(w, tw, lane);
+    else fft_dit<PT2, PAD>(w, log2L, tw, 1, +1, lane, nlanes);
     for (int n = lane; n < Ns; n += nlanes) w[padi<PAD>(n)] = cmulc(w[padi<PAD>(n)], chirp[n]);
     EXPD_SYNCWARP();
     return 1.0 / ((double)L * (double)L * (double)Ns);
@@ -97,11 +102,11 @@ EXPD_HD double precond_column(PT2* w, int Ns, int L, int log2L, int bluestein, c
 // with W = DFT(y1 + i y2): Y1_k = (W_k + conj(W_{Ns-k})) / 2,
 // Y2_k = (W_k - conj(W_{Ns-k})) / 2i, and Z1 + i Z2 goes into step (c).  One
 // lane handles k and Ns - k together.  Two columns for the FFT work of one.
-template <typename PT, typename PT2, int PAD = 0>
+template <typename PT, typename PT2, int PAD = 0, int LOG2L = 0>
 EXPD_HD double precond_column_pair(PT2* w, int Ns, int L, int log2L, int bluestein, const PT2* tw, const PT2* lam,
                                    const PT2* chirp, const PT2* bp, const PT2* bm, const PT* cj1, const PT* cj2,
                                    int order, int lane, int nlanes, PT one = (PT)1) {
-    precond_step_a<PT, PT2, PAD>(w, Ns, L, log2L, bluestein, tw, chirp, bp, lane, nlanes);
+    precond_step_a<PT, PT2, PAD, LOG2L>(w, Ns, L, log2L, bluestein, tw, chirp, bp, lane, nlanes);
     PT c1[7], c2v[7];
 #pragma unroll
     for (int j = 1; j <= 6; ++j) {
@@ -125,7 +130,7 @@ EXPD_HD double precond_column_pair(PT2* w, int Ns, int L, int log2L, int blueste
         w[padi<PAD>(k)] = wk;
         if (kk != k) w[padi<PAD>(kk)] = wkk;
     }
-    return precond_step_c<PT, PT2, PAD>(w, Ns, L, log2L, bluestein, tw, chirp, bm, lane, nlanes);
+    return precond_step_c<PT, PT2, PAD, LOG2L>(w, Ns, L, log2L, bluestein, tw, chirp, bm, lane, nlanes);
 }
 
 #ifndef __CUDACC_RTC__

@@ -248,268 +248,6 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel(TimeArgs A
         A.partial[(size_t)n * gridDim.x + blockIdx.x] = make_double2((double)sAcc[n].x, (double)sAcc[n].y);
 }
 
-// Real time columns (Dirichlet grids).  A CTA owns a tile of TR = 16
-// consecutive modes and every one of its 8 warps solves two of them as one
-// complex column (precond_column_pair: the FFT work of one column for two).
-// The tile is stored real, [TR][P] with an odd column stride P, so the
-// coalesced row-wise loads and stores (a warp covers 128-byte row segments of
-// two slices) and the per-column sweeps are both free of bank conflicts; the
-// FFT buffers use the swizzled index map padi<2>.  An operator application
-// without right-hand side and N (R_s X for the Krylov solvers) forms its
-// residual combination in the preconditioner's precision when that is float32
-// (the combination is rounded to float32 before Step (a) in any case); with a
-// right-hand side (the residual the fixed point and the refinement rely on) it
-// stays in the storage precision ST.  Norm partials only when A.norms.
-constexpr int TIME_REAL_COLS = 2 * EXPD_TIME_COLS;
-
-// Byte offsets of the real kernel's shared-memory regions, each 16-byte aligned
-// (the host sizes the launch with the same struct).
-template <typename PT, typename ST>
-struct RealSmem {
-    size_t w, tw, lam, chirp, bp, bm, acc, x, r, gam, gamf, total;
-    EXPD_HD static size_t up16(size_t b) { return (b + 15) & ~(size_t)15; }
-    EXPD_HD RealSmem(int Ns, int L, int bluestein, int norms) {
-        const size_t c = sizeof(typename cplx<PT>::t);
-        const int P = Ns | 1;
-        size_t o = 0;
-        w = o;     o = up16(o + (size_t)EXPD_TIME_COLS * L * c);
-        tw = o;    o = up16(o + (size_t)((L >> 1) + 1) * c);
-        lam = o;   o = up16(o + (size_t)Ns * c);
-        chirp = o; o = up16(o + (bluestein ? (size_t)Ns * c : 0));
-        bp = o;    o = up16(o + (bluestein ? (size_t)L * c : 0));
-        bm = o;    o = up16(o + (bluestein ? (size_t)L * c : 0));
-        acc = o;   o = up16(o + (norms ? (size_t)Ns * 16 : 0));
-        x = o;     o = up16(o + (size_t)TIME_REAL_COLS * P * sizeof(ST));
-        r = o;     o = up16(o + (size_t)TIME_REAL_COLS * P * sizeof(ST));
-        gam = o;   o = up16(o + 2 * (size_t)Ns * sizeof(ST));
-        gamf = o;  o = up16(o + 2 * (size_t)Ns * sizeof(float));
-        total = o;
-    }
-};
-
-template <typename PT, typename ST>
-__global__ void __launch_bounds__(32 * EXPD_TIME_COLS, 3) time_kernel_real(TimeArgs A) {
-    typedef typename cplx<PT>::t PT2;
-    constexpr int TR = TIME_REAL_COLS;
-    const int Ns = A.Ns, L = A.L;
-    const int P = Ns | 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const RealSmem<PT, ST> lay(Ns, L, A.bluestein, A.norms);
-    PT2* sW = reinterpret_cast<PT2*>(smem_raw + lay.w);          // [NW][L]
-    PT2* tw = reinterpret_cast<PT2*>(smem_raw + lay.tw);         // [L/2]
-    PT2* lam = reinterpret_cast<PT2*>(smem_raw + lay.lam);       // [Ns]
-    PT2* chirp = reinterpret_cast<PT2*>(smem_raw + lay.chirp);   // [Ns]  (Bluestein)
-    PT2* bp = reinterpret_cast<PT2*>(smem_raw + lay.bp);         // [L]   (Bluestein)
-    PT2* bm = reinterpret_cast<PT2*>(smem_raw + lay.bm);         // [L]   (Bluestein)
-    double2* sAcc = reinterpret_cast<double2*>(smem_raw + lay.acc);  // [Ns] (norms)
-    ST* sX = reinterpret_cast<ST*>(smem_raw + lay.x);            // [TR][P]
-    ST* sR = reinterpret_cast<ST*>(smem_raw + lay.r);            // [TR][P]
-    ST* gam = reinterpret_cast<ST*>(smem_raw + lay.gam);         // [Ns]
-    ST* osc = gam + Ns;                                          // [Ns]
-    float* gamf = reinterpret_cast<float*>(smem_raw + lay.gamf); // [Ns]
-    float* oscf = gamf + Ns;                                     // [Ns]
-
-    const int tid = threadIdx.x, nth = blockDim.x;
-    for (int i = tid; i < (L >> 1); i += nth) tw[i] = static_cast<const PT2*>(A.tw)[i];
-    for (int i = tid; i < Ns; i += nth) {
-        lam[i] = static_cast<const PT2*>(A.lam)[i];
-        gam[i] = static_cast<const ST*>(A.gam)[i];
-        osc[i] = static_cast<const ST*>(A.osc)[i];
-        gamf[i] = A.gam32[i];
-        oscf[i] = A.osc32[i];
-        if (A.norms) sAcc[i] = make_double2(0.0, 0.0);
-        if (A.bluestein) chirp[i] = static_cast<const PT2*>(A.chirp)[i];
-    }
-    if (A.bluestein)
-        for (int i = tid; i < L; i += nth) {
-            bp[i] = static_cast<const PT2*>(A.bplus)[i];
-            bm[i] = static_cast<const PT2*>(A.bminus)[i];
-        }
-    pdl_wait();
-    __syncthreads();
-
-    const int lane = tid & 31, warp = tid >> 5;
-    const long long Mcol = A.Mcol;
-    const ST bdt = (ST)A.bdt, sigR = (ST)A.sigR;
-    const ST* X = static_cast<const ST*>(A.X);
-    const ST* F = static_cast<const ST*>(A.F);
-    // float32 combination: preconditioner in float32, no right-hand side, no N
-    const bool lowq = std::is_same<PT, float>::value && !A.F && !A.NL;
-    const PT one = (PT)(1.0 - A.dshift);
-    for (long long tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
-        const long long m0 = tile * TR;
-        // ---- coalesced load of the tile ----
-        for (int idx = tid; idx < Ns * TR; idx += nth) {
-            const int n = idx / TR, c = idx - n * TR;
-            const long long m = m0 + c;
-            ST x = (ST)0, r = (ST)0;
-            if (m < Mcol) {
-                const long long g = (long long)n * Mcol + m;
-                if (X) x = X[g];
-                if (F && n < A.f_slices) r = F[g];
-                if (A.NL) r = fma(bdt, ldnl<ST, true>(A.NL, g, A.nl_f32).x, r);
-            }
-            if (lowq) {
-                // the float32 combination reads the iterate once converted
-                // (integer rounding of the binary64 encoding, off the float64 pipe)
-                reinterpret_cast<float*>(sX)[c * P + n] = f32_rn_from_f64((double)x);
-            } else {
-                sX[c * P + n] = x;
-                sR[c * P + n] = r;
-            }
-        }
-        __syncthreads();
-
-        // ---- two columns per warp ----
-        const int ca = 2 * warp;
-        const long long ma = m0 + ca, mb = ma + 1;
-        if (ma < Mcol && A.precond) {
-            const bool hasb = mb < Mcol;
-            ST csa[7], csb[7];
-            PT cpa[7], cpb[7];
-            csa[0] = csb[0] = (ST)0;
-            cpa[0] = cpb[0] = (PT)0;
-#pragma unroll
-            for (int j = 1; j <= 6; ++j) {
-                csa[j] = j <= A.order ? coef<ST>(A, j, ma) : (ST)0;
-                cpa[j] = j <= A.order ? coef<PT>(A, j, ma) : (PT)0;
-                csb[j] = j <= A.order && hasb ? coef<ST>(A, j, mb) : csa[j];
-                cpb[j] = j <= A.order && hasb ? coef<PT>(A, j, mb) : cpa[j];
-            }
-            PT2* w = sW + (size_t)warp * L;
-            const ST* xa = sX + (size_t)ca * P;
-            const ST* xb = xa + P;
-            ST* ra = sR + (size_t)ca * P;
-            ST* rb = ra + P;
-            const int pos_shift = A.bluestein ? 0 : 1;  // radix-2 windows take bit-reversed positions
-            for (int n = lane; n < Ns; n += 32) {
-                const int pos = padi<2>(pos_shift ? (int)bitrev(n, A.log2L) : n);
-                if (lowq) {
-                    // q = sigR (X_n - sum_j c_j X_{n-j}) in float32 (coefficients in
-                    // the preconditioner's table)
-                    const float* xfa = reinterpret_cast<const float*>(sX) + (size_t)ca * P;
-                    const float* xfb = xfa + P;
-                    float qa = xfa[n], qb = hasb ? xfb[n] : 0.0f;
-#pragma unroll
-                    for (int j = 1; j <= 6; ++j) {
-                        if (j <= A.order && j <= n) {
-                            qa = fmaf(-(float)cpa[j], xfa[n - j], qa);
-                            if (hasb) qb = fmaf(-(float)cpb[j], xfb[n - j], qb);
-                        }
-                    }
-                    const float sg = (float)A.sigR * gamf[n];
-                    w[pos] = cvt2<PT2>(make_float2(qa * sg, qb * sg));
-                } else {
-                    ST qa = ra[n], qb = hasb ? rb[n] : (ST)0;
-                    if (X) {
-                        ST rxa = xa[n], rxb = hasb ? xb[n] : (ST)0;
-#pragma unroll
-                        for (int j = 1; j <= 6; ++j) {
-                            if (j <= A.order && j <= n) {
-                                rxa = fma(-csa[j], xa[n - j], rxa);
-                                if (hasb) rxb = fma(-csb[j], xb[n - j], rxb);
-                            }
-                        }
-                        qa = fma(sigR, rxa, qa);
-                        qb = fma(sigR, rxb, qb);
-                    }
-                    if constexpr (std::is_same<PT, float>::value) {
-                        // the accurate combination rounded to float32, then Gamma_alpha in float32
-                        w[pos] = make_float2(f32_rn_from_f64((double)qa) * gamf[n], f32_rn_from_f64((double)qb) * gamf[n]);
-                    } else {
-                        w[pos] = cvt2<PT2>(c2(qa * gam[n], qb * gam[n]));
-                    }
-                }
-            }
-            EXPD_SYNCWARP();
-            precond_column_pair<PT, PT2, 2>(w, Ns, L, A.log2L, A.bluestein, tw, lam, chirp, bp, bm, cpa, cpb, A.order,
-                                            lane, 32, one);
-            for (int n = lane; n < Ns; n += 32) {
-                const PT2 v = w[padi<2>(pos_shift ? (int)bitrev(n, A.log2L) : n)];
-                if constexpr (std::is_same<PT, float>::value) {
-                    // output scale in float32, widened exactly by integer operations
-                    const float sa = v.x * oscf[n], sb = v.y * oscf[n];
-                    if constexpr (std::is_same<ST, double>::value) {
-                        ra[n] = f64_from_f32(sa);
-                        if (hasb) rb[n] = f64_from_f32(sb);
-                    } else {
-                        ra[n] = (ST)sa;
-                        if (hasb) rb[n] = (ST)sb;
-                    }
-                } else {
-                    ra[n] = (ST)v.x * osc[n];
-                    if (hasb) rb[n] = (ST)v.y * osc[n];
-                }
-            }
-        } else if (ma < Mcol) {
-            // no preconditioner: out = F + bdt N + sigR R_s X in ST
-            const bool hasb = mb < Mcol;
-            for (int c = ca; c < ca + 2 && (c == ca || hasb); ++c) {
-                const long long mc = m0 + c;
-                ST cs[7];
-#pragma unroll
-                for (int j = 1; j <= 6; ++j) cs[j] = j <= A.order ? coef<ST>(A, j, mc) : (ST)0;
-                const ST* xc = sX + (size_t)c * P;
-                ST* rc = sR + (size_t)c * P;
-                for (int n = lane; n < Ns; n += 32) {
-                    ST q = rc[n];
-                    if (X) {
-                        ST rx = xc[n];
-#pragma unroll
-                        for (int j = 1; j <= 6; ++j)
-                            if (j <= A.order && j <= n) rx = fma(-cs[j], xc[n - j], rx);
-                        q = fma(sigR, rx, q);
-                    }
-                    rc[n] = q;
-                }
-            }
-        }
-        __syncthreads();
-
-        // ---- coalesced write-back; per-element norm terms into sR / sX ----
-        for (int idx = tid; idx < Ns * TR; idx += nth) {
-            const int n = idx / TR, c = idx - n * TR;
-            const long long mm = m0 + c;
-            ST e_r = (ST)0, e_x = (ST)0;
-            if (mm < Mcol) {
-                const long long g = (long long)n * Mcol + mm;
-                const ST res = sR[c * P + n];
-                if (A.accum) {
-                    const ST xn = sX[c * P + n] + res;
-                    const_cast<ST*>(X)[g] = xn;
-                    if (A.sout) static_cast<float*>(A.sout)[g] = (float)res;
-                    if (A.norms) {
-                        e_r = res * res;
-                        e_x = xn * xn;
-                    }
-                } else {
-                    static_cast<ST*>(A.out)[g] = res;
-                    if (A.norms) e_r = res * res;
-                }
-            }
-            if (A.norms) {
-                sR[c * P + n] = e_r;
-                sX[c * P + n] = e_x;
-            }
-        }
-        __syncthreads();
-        if (A.norms) {
-            for (int n = tid; n < Ns; n += nth) {
-                ST a = (ST)0, b = (ST)0;
-                for (int c = 0; c < TR; ++c) {
-                    a += sR[c * P + n];
-                    b += sX[c * P + n];
-                }
-                sAcc[n].x += (double)a;
-                sAcc[n].y += (double)b;
-            }
-            __syncthreads();
-        }
-    }
-    if (A.norms)
-        for (int n = tid; n < Ns; n += nth) A.partial[(size_t)n * gridDim.x + blockIdx.x] = sAcc[n];
-}
-
 // Per-slice totals over the time kernel's CTAs: block n sums slice n's
 // partials in a fixed order (four independent strided accumulators per thread,
 // a shuffle tree, then the warps in order), so the totals are deterministic.
@@ -594,48 +332,6 @@ expd_status launch_time(expd_plan p, TimeArgs& a, cudaStream_t s) {
     KProf kp(p, s, cls, per * p->Ns * (double)p->Mcol, fl_col * (double)p->Mcol);
     EXPD_CUDA_TRY(launch_pdl(kern, dim3(p->time_grid), dim3(32 * EXPD_TIME_COLS), smem, s, a));
     p->time_grid_used = p->time_grid;
-    return EXPD_OK;
-}
-
-// Real columns (Dirichlet) with float64 or float32 storage (double-float
-// storage keeps the generic kernel).
-template <typename PT, typename ST>
-expd_status launch_time_real(expd_plan p, TimeArgs& a, cudaStream_t s) {
-    const TimeTables& t = std::is_same<PT, float>::value ? p->t32 : p->t64;
-    const TimeTables& ts = std::is_same<ST, float>::value ? p->t32 : p->t64;
-    a.gam = ts.gam;
-    a.osc = ts.osc;
-    a.gam32 = static_cast<const float*>(p->t32.gam);
-    a.osc32 = static_cast<const float*>(p->t32.osc);
-    a.lam = t.lam;
-    a.tw = t.tw;
-    a.chirp = t.chirp;
-    a.bplus = t.bplus;
-    a.bminus = t.bminus;
-    a.L = t.L;
-    a.log2L = t.log2L;
-    a.bluestein = t.bluestein;
-    a.ntiles = (p->Mcol + TIME_REAL_COLS - 1) / TIME_REAL_COLS;
-    const size_t smem = RealSmem<PT, ST>(p->Ns, t.L, t.bluestein, a.norms).total;
-    auto kern = time_kernel_real<PT, ST>;
-    EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
-    int per_sm = 1;
-    EXPD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * EXPD_TIME_COLS, smem));
-    long long grid = (long long)p->sm_count * std::max(per_sm, 1);
-    grid = std::min<long long>(grid, std::max<long long>(a.ntiles, 1));
-    if (a.norms) grid = std::min<long long>(grid, p->partial_cap);
-    const double esz = sizeof(ST);
-    const double nlsz = a.nl_f32 ? 4.0 : 8.0;
-    const double ffrac = (double)a.f_slices / p->Ns;
-    const double per = (a.X ? esz : 0.0) + (a.F ? esz * ffrac : 0.0) + (a.NL ? nlsz : 0.0) + esz +
-                       (a.accum && a.sout ? 4.0 : 0.0);
-    const double lg = (double)t.log2L;
-    const double fl_col = (a.precond ? (t.bluestein ? 4.0 : 2.0) * 5.0 * t.L * lg / 2.0 + 8.0 * p->order * p->Ns : 0.0) +
-                          2.0 * p->order * p->Ns;
-    const int cls = sizeof(ST) == 4 ? EXPD_K_TIME32 : EXPD_K_TIME;
-    KProf kp(p, s, cls, per * p->Ns * (double)p->Mcol, fl_col * (double)p->Mcol);
-    EXPD_CUDA_TRY(launch_pdl(kern, dim3((unsigned)grid), dim3(32 * EXPD_TIME_COLS), smem, s, a));
-    p->time_grid_used = (int)grid;
     return EXPD_OK;
 }
 
@@ -769,7 +465,14 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s) {
     a.X32 = op.X32;
     a.dshift = op.dshift;
     a.f_slices = op.f_slices < 0 ? p->Ns : op.f_slices;
-    a.norms = op.accum;
+    a.norms = op.accum ? 1 : 0;
+    p->dots_fused = 0;
+    // the Krylov partials come from the real-column kernel (Dirichlet grids)
+    // (float32 preconditioner on float64 storage: its scratch layout, time_real.cu)
+    if (op.dots && !op.accum && op.precond && op.f32 && !op.st32 && p->realcol && !op.stdd && !p->no_real_time) {
+        a.norms = 2;
+        p->dots_fused = 1;
+    }
     // power-of-two windows up to 64 with the float32 preconditioner: register kernel
     const bool reg = op.precond && op.f32 && (p->Ns == 16 || p->Ns == 32 || p->Ns == 64) && !p->no_reg_time;
     // (double-float storage included: with the right-hand side staged only on
@@ -788,9 +491,9 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s) {
         if (op.st32) {
             if (!op.f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 storage needs the float32 preconditioner");
             if (op.NL && !op.nl_f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 storage needs float32 N");
-            return launch_time_real<float, float>(p, a, s);
+            return time_real_launch(p, a, 1, 1, s);
         }
-        return op.f32 ? launch_time_real<float, double>(p, a, s) : launch_time_real<double, double>(p, a, s);
+        return time_real_launch(p, a, op.f32 ? 1 : 0, 0, s);
     }
     if (op.stdd) {
         if (!op.f32) return expd_fail(EXPD_ERR_INVALID_ARG, "double-float storage needs the float32 preconditioner");

@@ -54,22 +54,6 @@ __device__ __forceinline__ dd shfl_c(dd v, int lane) {
 __device__ __forceinline__ dd2 shfl_c(dd2 v, int lane) { return c2(shfl_c(v.x, lane), shfl_c(v.y, lane)); }
 
 
-// Asynchronous global -> shared copy of one element (4, 8 or 16 bytes); a
-// source size of 0 fills the destination with zeros (columns past the end).
-template <int BYTES>
-__device__ __forceinline__ void cp_async_elem(void* dst, const void* src, bool valid) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    const int n = valid ? BYTES : 0;
-    if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(BYTES), "r"(n)
-                     : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
 // Columns of the register kernel for a fixed order ORD (1..6), or ORD = 0 for
 // the plan's order read at run time (at most 6).  ADV: complex a_j E^j
 // (advection); otherwise real.
