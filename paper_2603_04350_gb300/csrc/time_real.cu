@@ -38,6 +38,133 @@ using namespace expd_time;
 // by asynchronous copies, all of a thread's elements in flight at once.
 constexpr int TIME_REAL_COLS = 2 * EXPD_TIME_COLS;
 
+// Bluestein passes of the real kernel (one warp, length 2^LOG2N, the
+// swizzled buffer map padi<2>), with the pointwise steps of precond_step_a /
+// precond_step_c folded in.  A Bluestein input is zero from Ns <= L/2 on, so
+// the first DIF pass reads only the lower half; the kernel spectrum (bp or bm,
+// stored in the DIF's bit-reversed output order) multiplies the last DIF
+// pass's results; the last DIT pass stores only the lower half, the outputs
+// k < Ns the solve reads.  The operations on the values kept, and their order,
+// are those of fft_dif / fft_dit and the separate sweeps.
+template <typename T2, int LOG2N, int SIGN>
+__device__ __forceinline__ void bl_dif(T2* x, const T2* tw, const T2* tab, int lane) {
+    constexpr int n = 1 << LOG2N;
+    static_assert(LOG2N >= 6, "a warp of 32 lanes covers the radix-2 passes; the first pass is not the last");
+    {  // first pass: span n/4, inputs x[i + n/2], x[i + 3n/4] are zero
+        constexpr int h = n >> 2;
+#pragma unroll 2
+        for (int g0 = 0; g0 < h; g0 += 32) {
+            const int i = g0 + lane;
+            if (h < 32 && i >= h) break;
+            T2 w2 = tw[i * 2], w4 = tw[i];
+            if (SIGN > 0) {
+                w2.y = -w2.y;
+                w4.y = -w4.y;
+            }
+            const T2 x0 = x[padi<2>(i)], x1 = x[padi<2>(i + h)];
+            const T2 a2 = cmul(x0, w4);
+            const T2 a3 = cmul_quarter(cmul(x1, w4), SIGN);
+            x[padi<2>(i)] = cadd(x0, x1);
+            x[padi<2>(i + h)] = cmul(csub(x0, x1), w2);
+            x[padi<2>(i + 2 * h)] = cadd(a2, a3);
+            x[padi<2>(i + 3 * h)] = cmul(csub(a2, a3), w2);
+        }
+        EXPD_SYNCWARP();
+    }
+#pragma unroll
+    for (int s = LOG2N - 3; s >= 1; s -= 2) {
+        const int h = 1 << (s - 1);
+        const int t4 = n >> (s + 1);
+        const int t2 = n >> s;
+        const bool last = (s == 1);  // (LOG2N even: the last pass, spans 1)
+#pragma unroll 2
+        for (int g0 = 0; g0 < (n >> 2); g0 += 32) {
+            const int g = g0 + lane;
+            if ((n >> 2) < 32 && g >= (n >> 2)) break;
+            const int k = g & (h - 1);
+            const int i = ((g >> (s - 1)) << (s + 1)) + k;
+            T2 w2 = tw[k * t2], w4 = tw[k * t4];
+            if (SIGN > 0) {
+                w2.y = -w2.y;
+                w4.y = -w4.y;
+            }
+            const T2 x0 = x[padi<2>(i)], x1 = x[padi<2>(i + h)], x2 = x[padi<2>(i + 2 * h)],
+                     x3 = x[padi<2>(i + 3 * h)];
+            const T2 a0 = cadd(x0, x2), a1 = cadd(x1, x3);
+            const T2 a2 = cmul(csub(x0, x2), w4);
+            const T2 a3 = cmul_quarter(cmul(csub(x1, x3), w4), SIGN);
+            T2 o0 = cadd(a0, a1), o1 = cmul(csub(a0, a1), w2), o2 = cadd(a2, a3), o3 = cmul(csub(a2, a3), w2);
+            if (last) {
+                o0 = cmul(o0, tab[i]);
+                o1 = cmul(o1, tab[i + h]);
+                o2 = cmul(o2, tab[i + 2 * h]);
+                o3 = cmul(o3, tab[i + 3 * h]);
+            }
+            x[padi<2>(i)] = o0;
+            x[padi<2>(i + h)] = o1;
+            x[padi<2>(i + 2 * h)] = o2;
+            x[padi<2>(i + 3 * h)] = o3;
+        }
+        EXPD_SYNCWARP();
+    }
+    if (LOG2N & 1) {  // the last pass is radix 2
+#pragma unroll 2
+        for (int b0 = 0; b0 < (n >> 1); b0 += 32) {
+            const int b = b0 + lane;
+            const T2 u = x[padi<2>(2 * b)], v = x[padi<2>(2 * b + 1)];
+            x[padi<2>(2 * b)] = cmul(cadd(u, v), tab[2 * b]);
+            x[padi<2>(2 * b + 1)] = cmul(csub(u, v), tab[2 * b + 1]);
+        }
+        EXPD_SYNCWARP();
+    }
+}
+
+template <typename T2, int LOG2N, int SIGN>
+__device__ __forceinline__ void bl_dit(T2* x, const T2* tw, int lane) {
+    constexpr int n = 1 << LOG2N;
+    if (LOG2N & 1) {
+#pragma unroll 2
+        for (int b0 = 0; b0 < (n >> 1); b0 += 32) {
+            const int b = b0 + lane;
+            const T2 u = x[padi<2>(2 * b)], v = x[padi<2>(2 * b + 1)];
+            x[padi<2>(2 * b)] = cadd(u, v);
+            x[padi<2>(2 * b + 1)] = csub(u, v);
+        }
+        EXPD_SYNCWARP();
+    }
+#pragma unroll
+    for (int s = (LOG2N & 1); s < LOG2N; s += 2) {
+        const int h = 1 << s;
+        const int t2 = n >> (s + 1);
+        const int t4 = n >> (s + 2);
+        const bool last = (s == LOG2N - 2);  // span n/4: only outputs below n/2 are kept
+#pragma unroll 2
+        for (int g0 = 0; g0 < (n >> 2); g0 += 32) {
+            const int g = g0 + lane;
+            if ((n >> 2) < 32 && g >= (n >> 2)) break;
+            const int k = g & (h - 1);
+            const int i = ((g >> s) << (s + 2)) + k;
+            T2 w2 = tw[k * t2], w4 = tw[k * t4];
+            if (SIGN > 0) {
+                w2.y = -w2.y;
+                w4.y = -w4.y;
+            }
+            const T2 x0 = x[padi<2>(i)], x1 = cmul(x[padi<2>(i + h)], w2);
+            const T2 x2 = x[padi<2>(i + 2 * h)], x3 = cmul(x[padi<2>(i + 3 * h)], w2);
+            const T2 a0 = cadd(x0, x1), a1 = csub(x0, x1);
+            const T2 a2 = cmul(cadd(x2, x3), w4);
+            const T2 a3 = cmul_quarter(cmul(csub(x2, x3), w4), SIGN);
+            x[padi<2>(i)] = cadd(a0, a2);
+            x[padi<2>(i + h)] = cadd(a1, a3);
+            if (!last) {
+                x[padi<2>(i + 2 * h)] = csub(a0, a2);
+                x[padi<2>(i + 3 * h)] = csub(a1, a3);
+            }
+        }
+        EXPD_SYNCWARP();
+    }
+}
+
 // Byte offsets of the real kernel's shared-memory regions, each 16-byte aligned
 // (the host sizes the launch with the same struct).
 template <typename PT, typename ST>
@@ -174,8 +301,12 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, sizeof(PT) == 8 ? 2 : 3) 
             ST* ra = (lowq ? sX : sR) + (size_t)ca * P;
             ST* rb = ra + P;
             const int pos_shift = A.bluestein ? 0 : 1;  // radix-2 windows take bit-reversed positions
+            // Bluestein windows at a compile-time length: the pointwise chirp
+            // and kernel-spectrum steps fold into the FFT passes (bl_dif / bl_dit)
+            const bool fold = LOG2L > 0 && A.bluestein;
             for (int n = lane; n < Ns; n += 32) {
                 const int pos = padi<2>(pos_shift ? (int)bitrev(n, A.log2L) : n);
+                PT2 val;
                 if (lowq) {
                     // q = sigR (X_n - sum_j c_j X_{n-j}) in float32 (coefficients in
                     // the preconditioner's table)
@@ -190,7 +321,7 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, sizeof(PT) == 8 ? 2 : 3) 
                         }
                     }
                     const float sg = (float)A.sigR * gamf[n];
-                    w[pos] = cvt2<PT2>(make_float2(qa * sg, qb * sg));
+                    val = cvt2<PT2>(make_float2(qa * sg, qb * sg));
                 } else {
                     ST qa = qra[n], qb = hasb ? qrb[n] : (ST)0;
                     if (X) {
@@ -207,17 +338,59 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, sizeof(PT) == 8 ? 2 : 3) 
                     }
                     if constexpr (std::is_same<PT, float>::value) {
                         // the accurate combination rounded to float32, then Gamma_alpha in float32
-                        w[pos] = make_float2(f32_ftz_from_f64((double)qa) * gamf[n], f32_ftz_from_f64((double)qb) * gamf[n]);
+                        val = make_float2(f32_ftz_from_f64((double)qa) * gamf[n], f32_ftz_from_f64((double)qb) * gamf[n]);
                     } else {
-                        w[pos] = cvt2<PT2>(c2(qa * gam[n], qb * gam[n]));
+                        val = cvt2<PT2>(c2(qa * gam[n], qb * gam[n]));
                     }
                 }
+                w[pos] = fold ? cmul(val, chirp[n]) : val;
             }
-            EXPD_SYNCWARP();
-            precond_column_pair<PT, PT2, 2, LOG2L>(w, Ns, L, A.log2L, A.bluestein, tw, lam, chirp, bp, bm, cpa, cpb, A.order,
-                                            lane, 32, one);
+            if (fold) {
+                const int half = L >> 1;
+                for (int k = Ns + lane; k < half; k += 32) w[padi<2>(k)] = c2((PT)0, (PT)0);
+                EXPD_SYNCWARP();
+                // Step (a): chirp-z convolution; on exit w[k] c_k = L Y_k for k < Ns
+                if constexpr (LOG2L > 0) {
+                    bl_dif<PT2, LOG2L, -1>(w, tw, bp, lane);
+                    bl_dit<PT2, LOG2L, +1>(w, tw, lane);
+                }
+                // Step (b) on two real columns at once (precond_column_pair), the
+                // Step (a) output chirp folded into the reads and Step (c)'s input
+                // chirp into the writes
+                PT c1[7], c2v[7];
+#pragma unroll
+                for (int j = 1; j <= 6; ++j) {
+                    c1[j] = j <= A.order ? cpa[j] : (PT)0;
+                    c2v[j] = j <= A.order ? cpb[j] : (PT)0;
+                }
+                const PT hf = (PT)0.5;
+                for (int k = lane; k <= Ns / 2; k += 32) {
+                    const int kk = k == 0 ? 0 : Ns - k;
+                    const PT2 av = cmul(w[padi<2>(k)], chirp[k]), bv = cmul(w[padi<2>(kk)], chirp[kk]);
+                    const PT2 y1 = c2(hf * (av.x + bv.x), hf * (av.y - bv.y));
+                    const PT2 y2 = c2(hf * (av.y + bv.y), hf * (bv.x - av.x));
+                    const PT2 z1 = cdiv(y1, precond_divisor<PT, PT2, PT>(lam[k], c1, A.order, one));
+                    const PT2 z2 = cdiv(y2, precond_divisor<PT, PT2, PT>(lam[k], c2v, A.order, one));
+                    const PT2 wk = cmulc(c2(z1.x - z2.y, z1.y + z2.x), chirp[k]);
+                    const PT2 wkk = cmulc(c2(z1.x + z2.y, z2.x - z1.y), chirp[kk]);
+                    w[padi<2>(k)] = wk;
+                    if (kk != k) w[padi<2>(kk)] = wkk;
+                }
+                for (int k = Ns + lane; k < half; k += 32) w[padi<2>(k)] = c2((PT)0, (PT)0);
+                EXPD_SYNCWARP();
+                // Step (c): the inverse DFT by chirp-z; the output chirp below
+                if constexpr (LOG2L > 0) {
+                    bl_dif<PT2, LOG2L, -1>(w, tw, bm, lane);
+                    bl_dit<PT2, LOG2L, +1>(w, tw, lane);
+                }
+            } else {
+                EXPD_SYNCWARP();
+                precond_column_pair<PT, PT2, 2, LOG2L>(w, Ns, L, A.log2L, A.bluestein, tw, lam, chirp, bp, bm, cpa, cpb,
+                                                       A.order, lane, 32, one);
+            }
             for (int n = lane; n < Ns; n += 32) {
-                const PT2 v = w[padi<2>(pos_shift ? (int)bitrev(n, A.log2L) : n)];
+                PT2 v = w[padi<2>(pos_shift ? (int)bitrev(n, A.log2L) : n)];
+                if (fold) v = cmulc(v, chirp[n]);
                 if constexpr (std::is_same<PT, float>::value) {
                     // output scale in float32, widened exactly by integer operations
                     const float sa = v.x * oscf[n], sb = v.y * oscf[n];

@@ -858,6 +858,13 @@ def test_graph_sequential_stepping_matches_direct(expd, p):
 REAL_CASES = [c for c in CASES if c.bc == "dirichlet"] + [
     P("d2d_blue127", "dirichlet", (19, 13), 2, Nt=128, alpha=1e-3, dt=1e-3),   # Ns = 127: Bluestein L = 256
     P("d2d_pow2_32", "dirichlet", (17, 9), 1, Nt=32),                            # Ns = 32: radix-2
+    # the compile-time Bluestein lengths (the pointwise steps folded into the
+    # passes): L = 64, 128, 512, odd and even log2 L; a compile-time radix-2
+    # window (L = Ns = 256)
+    P("d2d_blue20", "dirichlet", (9, 7), 2, Nt=21, alpha=1e-3, dt=1e-3),       # Ns = 20: L = 64
+    P("d2d_blue45", "dirichlet", (7, 9), 6, Nt=50, alpha=1e-3, dt=1e-3),       # Ns = 45: L = 128
+    P("d2d_blue200", "dirichlet", (5, 7), 1, Nt=200, alpha=1e-3, dt=1e-3),     # Ns = 200: L = 512
+    P("d2d_pow2_256", "dirichlet", (6, 5), 2, Nt=257, alpha=1e-3, dt=1e-3),    # Ns = 256: radix-2 at L = 256
 ]
 
 
