@@ -100,9 +100,10 @@ def parse_args():
     ap.add_argument("--mix-baseline", type=int, default=200, metavar="R",
                     help="requests of the same arrivals the float64 one-at-a-time server replays")
     ap.add_argument("--mix-workers", type=int, default=4)
-    ap.add_argument("--profile-case", default=None, metavar="N,NT,PREC",
+    ap.add_argument("--profile-case", default=None, metavar="N,NT,PREC[,S]",
                     help="run two solves of the Allen-Cahn workload on an N x N grid with NT steps "
-                         "(PREC mixed|fp64) and exit; the target of ncu captures")
+                         "(PREC mixed|fp64, order S: 1 with the 256^2 workload's parameters, 6 with the "
+                         "512^2 one's) and exit; the target of ncu captures")
     ap.add_argument("--profile-dirichlet", default=None, metavar="N,NT[,M]",
                     help="run two mixed GMRES(M) solves of the Dirichlet heat workload on an N x N grid with NT "
                          "steps (tensor-core DST; M = 20 by default) and exit; the target of ncu captures")
@@ -120,7 +121,9 @@ def profile_case(spec: str) -> int:
     parts = spec.split(",")
     n, nt = int(parts[0]), int(parts[1])
     prec = expd.PREC_FP64 if len(parts) > 2 and parts[2] == "fp64" else expd.PREC_MIXED
-    p = I.ALLEN_CAHN_256.with_(n=(n, n), Nt=nt)
+    order = int(parts[3]) if len(parts) > 3 else 1
+    base = I.ALLEN_CAHN_512_S6 if order == 6 else I.ALLEN_CAHN_256.with_(order=order)
+    p = base.with_(n=(n, n), Nt=nt)
     u0 = torch.from_numpy(I.make_u0(p)).cuda()
     U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device="cuda")
     with expd.plan_create(expd.spec_from_problem(p, precision=prec)) as plan:

@@ -20,8 +20,7 @@ Parabolic PDEs" (arXiv 2603.04350) computes:
   * dense brute-force versions of all of the above for tiny sizes (explicit
     L_h, scipy's expm, explicit C_j^alpha matrices, LU solves).
 
-Readings taken where the paper is silent (each is also listed in the design
-notes): the source f enters row n as beta_s*dt*f(t_n) and the nonlinear term as
+Readings taken where the paper is silent: the source f enters row n as beta_s*dt*f(t_n) and the nonlinear term as
 beta_s*dt*N(u_n) (implicit, integrating factor); the startup values
 u_1..u_{s-1} come from the IF-BDF_j ramp j = 1..s-1; C_j^alpha = (C_0^alpha)^(j+1)
 (the printed entry lists of Sec. 5 are garbled); the periodic L_h is the

@@ -141,6 +141,13 @@ expd_status dalloc(expd_plan p, void** ptr, size_t bytes, const char* what) {
                                             std::to_string(bytes) + " bytes): " + cudaGetErrorString(e));
     }
     p->bytes += bytes;
+    // debugging aid: all-ones bytes are a NaN in every floating type, so a
+    // read of a buffer before it is written turns the result non-finite
+    if (p->poison) {
+        e = cudaMemsetAsync(*ptr, 0xFF, bytes, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+        if (e != cudaSuccess) return expd_cuda_fail(e, "cudaMemsetAsync(poison)", __FILE__, __LINE__);
+    }
     return EXPD_OK;
 }
 
@@ -632,6 +639,8 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     p->no_real_time = tr && strcmp(tr, "0") == 0;
     const char* gr = getenv("EXPD_GRAPHS");
     p->no_graphs = gr && strcmp(gr, "0") == 0;
+    const char* po = getenv("EXPD_POISON");
+    p->poison = po && strcmp(po, "1") == 0;
     // the device-controlled loop is opt-in (EXPD_DEVICE_LOOP=1): on GB300 its
     // while-node iterations measured slower than host round trips that read
     // the norms from mapped memory (0.624 against 0.594 ms per solve on

@@ -122,9 +122,11 @@ __global__ void update_kernel(const double* __restrict__ V, long long ld, int k,
     }
 }
 
+// y = a x + b y; with b = 0, y is output only (it is not read: 0 * y would be
+// NaN where y holds a non-finite value left by an earlier use of the buffer)
 __global__ void axpby_kernel(long long n, double a, const double* x, double b, double* y) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-        y[e] = fma(a, x[e], b * y[e]);
+        y[e] = b == 0.0 ? a * x[e] : fma(a, x[e], b * y[e]);
 }
 
 }  // namespace

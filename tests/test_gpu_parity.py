@@ -3,7 +3,8 @@
 Tolerances: the float64 path must match the oracle to 1e-11 relative (the
 stated 1e-10 bar with margin) on every element; float32-preconditioner (mixed)
 operations that are not refined are held to the float32 bound eps32/alpha
-derived in the design notes; solves of either precision must meet the
+(float32 rounding in the scaled time DFT, amplified at most 1/alpha by the
+Gamma_alpha^-1 scaling of Eq. (3.3)); solves of either precision must meet the
 workload's tolerance in the L^inf(0,T;L^2) relative error of Sec. 7.
 """
 import math
