@@ -16,11 +16,16 @@ Parabolic PDEs" (arXiv 2603.04350) computes:
   * the three-step preconditioner solve (Eq. (3.3), Eq. (4.5));
   * the preconditioned Richardson iteration (Eq. (3.2), (4.4)) and its lagged
     nonlinear form (Eqs. (7.3)-(7.4));
-  * left-preconditioned GMRES (Sec. 3.2, Theorem 3.3);
+  * left-preconditioned GMRES (Sec. 3.2, Theorem 3.3) and BiCGStab;
+  * complex states for complex a and c, the Schrodinger equation of Sec. 7
+    (a = i, c = 2i or 200i): complex arithmetic throughout, GMRES with the
+    Hermitian inner product and complex Givens rotations;
   * dense brute-force versions of all of the above for tiny sizes (explicit
     L_h, scipy's expm, explicit C_j^alpha matrices, LU solves).
 
-Readings taken where the paper is silent: the source f enters row n as beta_s*dt*f(t_n) and the nonlinear term as
+Readings taken where the paper is silent: GMRES on a complex state is complex
+GMRES (the paper's Schrodinger runs converge in one and three iterations,
+which real GMRES on the real and imaginary parts does not reproduce); the source f enters row n as beta_s*dt*f(t_n) and the nonlinear term as
 beta_s*dt*N(u_n) (implicit, integrating factor); the startup values
 u_1..u_{s-1} come from the IF-BDF_j ramp j = 1..s-1; C_j^alpha = (C_0^alpha)^(j+1)
 (the printed entry lists of Sec. 5 are garbled); the periodic L_h is the
@@ -54,8 +59,8 @@ class Spec:
     bc: str                      # "periodic" | "dirichlet"
     n: Tuple[int, ...]           # grid points per dimension
     length: Tuple[float, ...]    # domain length per dimension
-    a: float                     # L = a*Lap - c   (Eq. (1.2))
-    c: float
+    a: complex                   # L = a*Lap - c   (Eq. (1.2)); a = i, c = 2i: Schrodinger (Sec. 7)
+    c: complex
     nonlin: str                  # "none" | "allen_cahn"
     dt: float
     Nt: int
@@ -63,6 +68,7 @@ class Spec:
     order: int                   # s in 1..6
     b: Tuple[float, ...] = ()    # advection velocity: L = a*Lap - b.grad - c (periodic only)
     nl_form: str = "if"          # "if" (integrating factor, Eq. (6.1)) | "etd1" (see etd1_step)
+    complex_state: bool = False  # u, f and the solution are complex (Schrodinger-type L, Sec. 7)
 
     @property
     def ndim(self):
@@ -76,7 +82,19 @@ class Spec:
 def spec_of(p) -> Spec:
     """Build a Spec from any object with the same attribute names."""
     return Spec(p.bc, tuple(p.n), tuple(p.length), p.a, p.c, p.nonlin, p.dt, p.Nt,
-                p.alpha, p.order, tuple(getattr(p, "b", ()) or ()), getattr(p, "nl_form", "if"))
+                p.alpha, p.order, tuple(getattr(p, "b", ()) or ()), getattr(p, "nl_form", "if"),
+                bool(getattr(p, "complex_state", False)))
+
+
+def state_dtype(sp: Spec):
+    """float64 for a real state; complex128 when the state is complex, as for
+    the Schrodinger equation u_t = i Lap u - c u of Sec. 7 (a = i, c = 2i or
+    200i), whose solution is complex even from a real u_0."""
+    if not sp.complex_state and (np.imag(sp.a) != 0 or np.imag(sp.c) != 0):
+        raise ValueError("a complex a or c needs complex_state=True")
+    if sp.complex_state and sp.nonlin != "none":
+        raise ValueError("a complex state is defined for linear problems only")
+    return np.complex128 if sp.complex_state else np.float64
 
 
 def has_advection(sp: Spec) -> bool:
@@ -175,7 +193,7 @@ def apply_A_power(sp: Spec, u: np.ndarray, j: int) -> np.ndarray:
     """A^j u with A = exp(dt L_h) (Eq. (2.2)), applied in L_h's eigenbasis."""
     mu = spatial_eigenvalues(sp)
     out = from_eigen(sp, np.exp(j * sp.dt * mu) * to_eigen(sp, u))
-    return out if np.iscomplexobj(u) else out.real
+    return out if (np.iscomplexobj(u) or sp.complex_state) else out.real
 
 
 # ---------------------------------------------------------------------------
@@ -249,7 +267,7 @@ def pointwise_implicit_solve(sp: Spec, w: np.ndarray, bdt: float) -> np.ndarray:
 def step_rhs(sp: Spec, U: np.ndarray, n: int, q: int, f: Optional[np.ndarray]) -> np.ndarray:
     """w_n = sum_{j=1..q} a_j A^j u_{n-j} + beta_q dt f(t_n) of BDF-q."""
     a, beta = bdf_float(q)
-    w = np.zeros(sp.n)
+    w = np.zeros(sp.n, dtype=state_dtype(sp))
     for j in range(1, q + 1):
         w += a[j - 1] * apply_A_power(sp, U[n - j], j)
     if f is not None:
@@ -266,7 +284,7 @@ def sequential_solve(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None,
     taken from U_start (shape (s, *n), U_start[0] = u0) when supplied, else
     from the ramp that steps u_n with BDF-n.  Each step solves
     u_n - beta dt N(u_n) = sum_j a_j A^j u_{n-j} + beta dt f(t_n)."""
-    U = np.zeros((sp.Nt + 1,) + sp.n)
+    U = np.zeros((sp.Nt + 1,) + sp.n, dtype=state_dtype(sp))
     U[0] = u0
     if sp.nl_form == "etd1" and sp.nonlin != "none":
         _check_etd1(sp, f)
@@ -289,7 +307,7 @@ def startup_values(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None,
                    U_start: Optional[np.ndarray] = None) -> np.ndarray:
     """u_0..u_{s-1}: the given values, or u0 and the sequential ramp."""
     if U_start is not None:
-        return np.array(U_start, dtype=float).reshape((sp.order,) + sp.n)
+        return np.array(U_start, dtype=state_dtype(sp)).reshape((sp.order,) + sp.n)
     short = dataclasses.replace(sp, Nt=sp.order - 1)
     if sp.order == 1:
         return u0[None].copy()
@@ -305,7 +323,7 @@ def rhs_known(sp: Spec, U_start: np.ndarray, f: Optional[np.ndarray]) -> np.ndar
     n-j < s (the printed f_2 .. f_6) plus beta_s dt f(t_n)."""
     s = sp.order
     a, beta = bdf_float(s)
-    b = np.zeros((sp.Ns,) + sp.n)
+    b = np.zeros((sp.Ns,) + sp.n, dtype=state_dtype(sp))
     for i in range(sp.Ns):
         n = s + i
         if f is not None:
@@ -406,7 +424,7 @@ def precond_apply(sp: Spec, r: np.ndarray, shift: float = 0.0) -> np.ndarray:
         Sb[n] = from_eigen(sp, to_eigen(sp, Sa[n]) / d)
     # Step (c)
     s = np.fft.fft(Sb, axis=0) / np.sqrt(Ns) / gam
-    return s.real
+    return s if sp.complex_state else s.real
 
 
 # ---------------------------------------------------------------------------
@@ -421,7 +439,7 @@ class SolveResult:
 
 
 def assemble(sp: Spec, U_start: np.ndarray, V: np.ndarray) -> np.ndarray:
-    U = np.zeros((sp.Nt + 1,) + sp.n)
+    U = np.zeros((sp.Nt + 1,) + sp.n, dtype=state_dtype(sp))
     U[: sp.order] = U_start
     U[sp.order:] = V
     return U
@@ -458,7 +476,7 @@ def richardson(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None,
     elif init == "linear":
         V = linear_guess(sp, U_start)
     elif init == "zero":
-        V = np.zeros((sp.Ns,) + sp.n)
+        V = np.zeros((sp.Ns,) + sp.n, dtype=state_dtype(sp))
     else:
         raise ValueError(f"unknown initial guess {init!r}")
     hist, its = [], []
@@ -466,8 +484,8 @@ def richardson(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None,
     for k in range(1, max_iter + 1):
         s = precond_apply(sp, residual(sp, V, b), shift)
         V = V + s
-        sn = np.sqrt((s.reshape(sp.Ns, -1) ** 2).sum(1)).max()
-        vn = np.sqrt((V.reshape(sp.Ns, -1) ** 2).sum(1)).max()
+        sn = np.sqrt((np.abs(s.reshape(sp.Ns, -1)) ** 2).sum(1)).max()
+        vn = np.sqrt((np.abs(V.reshape(sp.Ns, -1)) ** 2).sum(1)).max()
         hist.append(sn / vn if vn > 0 else 0.0)
         if keep_iterates:
             its.append(V.copy())
@@ -482,12 +500,19 @@ def gmres(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None, tol: float =
     """Left-preconditioned restarted GMRES(m) with modified Gram-Schmidt on
     P_alpha^{-1} R_s v = P_alpha^{-1} f_s (Sec. 3.2, Theorem 3.3), v^0 = 0.
     Stops when ||P^{-1}(f_s - R_s v)|| <= tol * ||P^{-1} f_s||.
-    history[k] is that relative preconditioned residual after k iterations."""
+    history[k] is that relative preconditioned residual after k iterations.
+
+    A complex state runs complex GMRES: the Hermitian inner product
+    <v, w> = sum conj(v) w, complex Hessenberg entries and complex Givens
+    rotations G = [[conj(c), s], [-s, c]] with |c|^2 + s^2 = 1 and s real
+    (the subdiagonal entry is a norm); on real data every step reduces to
+    the real algorithm."""
     if sp.nonlin != "none":
         raise ValueError("GMRES is for linear problems")
     U_start = startup_values(sp, u0, f, U_start)
     b = rhs_known(sp, U_start, f)
     shape = (sp.Ns,) + sp.n
+    dt_ = state_dtype(sp)
 
     def op(x):
         return precond_apply(sp, apply_R(sp, x.reshape(shape))).ravel()
@@ -505,31 +530,31 @@ def gmres(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None, tol: float =
         if beta <= tol * cn:
             break
         m = restart
-        Vb = np.zeros((m + 1, c.size))
-        H = np.zeros((m + 1, m))
-        cs, sn = np.zeros(m), np.zeros(m)
-        g = np.zeros(m + 1)
+        Vb = np.zeros((m + 1, c.size), dtype=dt_)
+        H = np.zeros((m + 1, m), dtype=dt_)
+        cs, sn = np.zeros(m, dtype=dt_), np.zeros(m)
+        g = np.zeros(m + 1, dtype=dt_)
         g[0] = beta
         Vb[0] = r / beta
         j_done = 0
         for j in range(m):
             w = op(Vb[j])
             for i in range(j + 1):                      # modified Gram-Schmidt
-                H[i, j] = np.dot(w, Vb[i])
+                H[i, j] = np.vdot(Vb[i], w)
                 w = w - H[i, j] * Vb[i]
             H[j + 1, j] = np.linalg.norm(w)
-            if H[j + 1, j] > 0:
+            if H[j + 1, j] != 0:
                 Vb[j + 1] = w / H[j + 1, j]
             for i in range(j):                          # previous Givens rotations
-                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                t = np.conj(cs[i]) * H[i, j] + sn[i] * H[i + 1, j]
                 H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
                 H[i, j] = t
-            den = math.hypot(H[j, j], H[j + 1, j])
-            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            den = math.hypot(abs(H[j, j]), abs(H[j + 1, j]))
+            cs[j], sn[j] = H[j, j] / den, abs(H[j + 1, j]) / den
             H[j, j] = den
             H[j + 1, j] = 0.0
             g[j + 1] = -sn[j] * g[j]
-            g[j] = cs[j] * g[j]
+            g[j] = np.conj(cs[j]) * g[j]
             total += 1
             j_done = j + 1
             hist.append(abs(g[j + 1]) / cn)
@@ -543,10 +568,11 @@ def gmres(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None, tol: float =
 
 
 def bicgstab_solve(matvec, b: np.ndarray, tol: float, max_iter: int):
-    """BiCGStab (van der Vorst, 1992) for matvec(x) = b from x = 0, in plain
-    float64: the BiCG direction step followed by a one-dimensional minimal
-    residual step each iteration.  Stops when ||r_k|| <= tol ||b||; on a
-    breakdown (rho exactly zero) it restarts the shadow residual rhat = r.
+    """BiCGStab (van der Vorst, 1992) for matvec(x) = b from x = 0: the BiCG
+    direction step followed by a one-dimensional minimal residual step each
+    iteration, with the Hermitian products <u, v> = sum conj(u) v (plain dot
+    products on real data).  Stops when ||r_k|| <= tol ||b||; on a breakdown
+    (rho exactly zero) it restarts the shadow residual rhat = r.
     Returns (x, history of ||r_k|| / ||b||)."""
     bn = np.linalg.norm(b)
     x = np.zeros_like(b)
@@ -559,21 +585,21 @@ def bicgstab_solve(matvec, b: np.ndarray, tol: float, max_iter: int):
     v = np.zeros_like(b)
     p = np.zeros_like(b)
     for _ in range(max_iter):
-        rho_new = float(np.dot(rhat, r))
+        rho_new = np.vdot(rhat, r)
         if rho_new == 0.0:                     # breakdown: restart the shadow residual
             rhat = r.copy()
             rho, alpha, omega = 1.0, 1.0, 1.0
             v[:] = 0.0
             p[:] = 0.0
-            rho_new = float(np.dot(rhat, r))
+            rho_new = np.vdot(rhat, r)
         beta = (rho_new / rho) * (alpha / omega)
         p = r + beta * (p - omega * v)
         v = matvec(p)
-        alpha = rho_new / float(np.dot(rhat, v))
+        alpha = rho_new / np.vdot(rhat, v)
         s = r - alpha * v
         t = matvec(s)
-        tt = float(np.dot(t, t))
-        omega = float(np.dot(t, s)) / tt if tt > 0 else 0.0
+        tt = np.vdot(t, t).real
+        omega = np.vdot(t, s) / tt if tt > 0 else 0.0
         x = x + alpha * p + omega * s
         r = s - omega * t
         rho = rho_new
@@ -606,8 +632,8 @@ def bicgstab(sp: Spec, u0: np.ndarray, f: Optional[np.ndarray] = None, tol: floa
 # ---------------------------------------------------------------------------
 def rel_error(U: np.ndarray, Uref: np.ndarray) -> float:
     """max_n ||u_n - u_n^ref||_2 / max_n ||u_n^ref||_2 over the given slices."""
-    d = (U - Uref).reshape(U.shape[0], -1)
-    r = Uref.reshape(Uref.shape[0], -1)
+    d = np.abs(U - Uref).reshape(U.shape[0], -1)
+    r = np.abs(Uref).reshape(Uref.shape[0], -1)
     return float(np.sqrt((d**2).sum(1)).max() / np.sqrt((r**2).sum(1)).max())
 
 
@@ -709,8 +735,8 @@ def dense_R(sp: Spec, alpha: float = 0.0) -> np.ndarray:
     A = dense_A(sp)
     M = A.shape[0]
     Ns = sp.Ns
-    R = np.eye(Ns * M)
-    Aj = np.eye(M)
+    R = np.eye(Ns * M, dtype=A.dtype)
+    Aj = np.eye(M, dtype=A.dtype)
     for j in range(1, sp.order + 1):
         Aj = Aj @ A
         R -= a[j - 1] * np.kron(shift_matrix(Ns, j - 1, alpha), Aj)
@@ -723,7 +749,7 @@ def dense_rhs(sp: Spec, U_start: np.ndarray, f: Optional[np.ndarray]) -> np.ndar
     A = dense_A(sp)
     s = sp.order
     M = A.shape[0]
-    b = np.zeros((sp.Ns, M))
+    b = np.zeros((sp.Ns, M), dtype=np.result_type(A, U_start, state_dtype(sp)))
     for i in range(sp.Ns):
         n = s + i
         if f is not None:

@@ -32,7 +32,9 @@ class Problem:
     n       grid points per dimension (periodic) or interior points (Dirichlet)
     length  domain length per dimension; periodic grid x_j = j*L/n,
             Dirichlet grid x_j = j*L/(n+1), j = 1..n
-    a, c    L = a*Lap - c  (Sec. 1, Eq. (1.2)); b adds advection -b.grad
+    a, c    L = a*Lap - c  (Sec. 1, Eq. (1.2)); b adds advection -b.grad; a and c
+            may be complex (the Schrodinger equation of Sec. 7: a = i, c = 2i
+            or 200i), which needs complex_state
     nonlin  N(u): "none" or "allen_cahn" (N(u) = u - u^3)
     dt, Nt  time step and number of steps; the window is T = Nt*dt
     alpha   the alpha-circulant parameter (Sec. 2)
@@ -59,6 +61,7 @@ class Problem:
     u0_lowpass: Optional[int] = None
     b: Tuple[float, ...] = ()   # advection velocity per axis (periodic): L = a*Lap - b.grad - c
     nl_form: str = "if"         # nonlinear term: "if" (integrating factor) or "etd1" (order 1, no source)
+    complex_state: bool = False  # u0, f and the solution are complex128
 
     @property
     def ndim(self) -> int:
@@ -104,7 +107,26 @@ ALLEN_CAHN_512_S6 = Problem(
     a=0.02 ** 2, c=0.0, nonlin=NL_ALLEN_CAHN, dt=1e-3, Nt=256, alpha=1e-3, order=6, tol=1e-8,
     solver="fp", seed=4, u0_kind="uniform", u0_range=(-1.0, 1.0), u0_lowpass=32,
 )
-WORKLOADS = {p.name: p for p in (HEAT1D, ALLEN_CAHN_256, HEAT_DIRICHLET_1024, ALLEN_CAHN_512_S6)}
+# The Schrodinger equation u_t = i Lap u - c u of Sec. 7 (a = i), homogeneous
+# Dirichlet conditions on the unit interval / square, alpha = alpha_opt =
+# 1/5120 (the table of optimised alpha in Sec. 7), GMRES.  1D: h = 1/128
+# (127 interior points), dt = 0.01, c = 2i, u_0 = sin(pi x), first order,
+# T = 2.  2D: h = 1/40 (39^2 interior points), dt = 0.05, c = 200i, BDF2,
+# the Gaussian wave packet u_0 = exp(-|x - 1/2|^2/(2 mu^2)) exp(-5i (x - 1/2)),
+# mu = 0.05, T = 4.  The paper stops at an error of 1e-10 (Sec. 7).
+ALPHA_OPT = 1.0 / 5120.0
+SCHRODINGER_1D = Problem(
+    name="schrodinger_dirichlet_127_nt200_s1", bc=DIRICHLET, n=(127,), length=(1.0,),
+    a=1j, c=2j, nonlin=NL_NONE, dt=0.01, Nt=200, alpha=ALPHA_OPT, order=1, tol=1e-10,
+    solver="gmres", seed=6, u0_kind="sine_mode", complex_state=True,
+)
+SCHRODINGER_2D = Problem(
+    name="schrodinger_dirichlet_39x39_nt80_s2", bc=DIRICHLET, n=(39, 39), length=(1.0, 1.0),
+    a=1j, c=200j, nonlin=NL_NONE, dt=0.05, Nt=80, alpha=ALPHA_OPT, order=2, tol=1e-10,
+    solver="gmres", seed=7, u0_kind="wave_packet", complex_state=True,
+)
+WORKLOADS = {p.name: p for p in (HEAT1D, ALLEN_CAHN_256, HEAT_DIRICHLET_1024, ALLEN_CAHN_512_S6,
+                                 SCHRODINGER_1D, SCHRODINGER_2D)}
 
 
 def grid_coords(p: Problem):
@@ -119,7 +141,12 @@ def grid_coords(p: Problem):
 
 
 def make_u0(p: Problem) -> np.ndarray:
-    """Seeded initial state of shape p.n (float64)."""
+    """Seeded initial state of shape p.n (float64; complex128 for complex states)."""
+    u = _make_u0(p)
+    return u.astype(np.complex128) if p.complex_state else u
+
+
+def _make_u0(p: Problem) -> np.ndarray:
     rng = np.random.default_rng(p.seed)
     xs = grid_coords(p)
     if p.u0_kind == "fourier16":
@@ -150,6 +177,15 @@ def make_u0(p: Problem) -> np.ndarray:
         return u
     if p.u0_kind == "constant":
         return np.full(p.n, p.u0_range[0])
+    if p.u0_kind == "wave_packet":
+        # Gaussian of width mu = 0.05 centred in the domain, carrying the
+        # phase exp(-5i (x - L_x/2)) along the first axis
+        grids = np.meshgrid(*xs, indexing="ij")
+        r2 = sum((g - 0.5 * L) ** 2 for g, L in zip(grids, p.length))
+        mu = 0.05
+        return np.exp(-r2 / (2.0 * mu * mu)) * np.exp(-5j * (grids[0] - 0.5 * p.length[0]))
+    if p.u0_kind == "random_complex":
+        return rng.standard_normal(p.n) + 1j * rng.standard_normal(p.n)
     raise ValueError(p.u0_kind)
 
 
@@ -191,7 +227,8 @@ def make_forcing(p: Problem) -> Optional[np.ndarray]:
             term = term * np.sin(pq[i, d] * math.pi * gd / p.length[d])
         g += term
     t = np.arange(1, p.Nt + 1) * p.dt
-    return np.exp(-t).reshape((-1,) + (1,) * p.ndim) * g[None]
+    f = np.exp(-t).reshape((-1,) + (1,) * p.ndim) * g[None]
+    return f.astype(np.complex128) if p.complex_state else f
 
 
 def make_inputs(p: Problem):

@@ -488,3 +488,91 @@ def check_etd1_richardson_reaches_sequential(sp, seed=14, iters=80):
     ref = O.sequential_solve(sp, u0)
     res = O.richardson(sp, u0, None, max_iter=iters, tol=1e-15)
     return O.rel_error(res.U[1:], ref[1:])
+
+
+# --- complex states: the Schrodinger equation of Sec. 7 --------------------
+def se_spec(bc="dirichlet", n=(7,), a=1j, c=2j, Nt=8, order=1, alpha=0.05, dt=0.05, length=None):
+    if length is None:
+        length = tuple(2 * math.pi if bc == "periodic" else 1.0 for _ in n)
+    return O.Spec(bc, tuple(n), tuple(length), a, c, "none", dt, Nt, alpha, order, complex_state=True)
+
+
+def rng_complex(sp, seed, lead=()):
+    rng = np.random.default_rng(seed)
+    shape = tuple(lead) + sp.n
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def check_complex_A_vs_dense(sp, seed=20):
+    """A^j u for a complex state and complex a, c: eigen-symbol path against
+    the dense expm of the explicit complex L_h (j = 1..3)."""
+    A = O.dense_A(sp)
+    u = rng_complex(sp, seed)
+    worst, Aj = 0.0, np.eye(A.shape[0], dtype=complex)
+    for j in range(1, 4):
+        Aj = Aj @ A
+        ref = (Aj @ u.ravel()).reshape(sp.n)
+        worst = max(worst, np.abs(O.apply_A_power(sp, u, j) - ref).max() / np.abs(ref).max())
+    return worst
+
+
+def check_complex_precond_vs_dense(sp, seed=21):
+    r = rng_complex(sp, seed, (sp.Ns,))
+    ref = O.dense_precond_apply(sp, r)
+    return np.abs(O.precond_apply(sp, r) - ref).max() / np.abs(ref).max()
+
+
+def check_complex_sequential_vs_dense(sp, seed=22):
+    u0 = rng_complex(sp, seed)
+    f = rng_complex(sp, seed + 1, (sp.Nt,))
+    return O.rel_error(O.sequential_solve(sp, u0, f)[1:], O.dense_solve(sp, u0, f)[1:])
+
+
+def check_schrodinger_sine_mode(n=15, Nt=12, dt=0.01, c=2j):
+    """u_0 = sin(pi x) is the first eigenvector of the 3-point Dirichlet
+    Laplacian (eigenvalue -(4/h^2) sin^2(pi h/2)); with a = i the first-order
+    scheme gives u_n = exp(n dt (i lambda_1 - c)) u_0 exactly.  Max deviation."""
+    sp = se_spec("dirichlet", (n,), 1j, c, Nt, 1, dt=dt)
+    x = np.arange(1, n + 1) / (n + 1)
+    u0 = np.sin(np.pi * x).astype(complex)
+    h = 1.0 / (n + 1)
+    lam1 = -(4.0 / h**2) * math.sin(math.pi * h / 2) ** 2
+    mu = 1j * lam1 - c
+    want = np.array([np.exp(k * dt * mu) * u0 for k in range(Nt + 1)])
+    return np.abs(O.sequential_solve(sp, u0) - want).max()
+
+
+def check_unitary_norm(sp, seed=23):
+    """Purely imaginary a and c make A = exp(dt L_h) unitary, and every BDF-s
+    step of a homogeneous problem reproduces u_n = A^n u_0 (the a_j sum to 1);
+    max_n | ||u_n|| / ||u_0|| - 1 |."""
+    u0 = rng_complex(sp, seed)
+    U = O.sequential_solve(sp, u0)
+    nrm = np.sqrt((np.abs(U.reshape(U.shape[0], -1)) ** 2).sum(1))
+    return float(np.abs(nrm / nrm[0] - 1.0).max())
+
+
+def schrodinger_gmres_errors(p, iters):
+    """Errors (Sec. 7's norm) vs sequential stepping after k = 1..iters GMRES
+    iterations on a Schrodinger workload."""
+    from paper_2603_04350_gb300 import inputs as I
+    sp = O.spec_of(p)
+    u0, f = I.make_inputs(p)
+    seq = O.sequential_solve(sp, u0, f)
+    return [O.rel_error(O.gmres(sp, u0, f, tol=0.0, restart=20, max_iter=k).U[1:], seq[1:])
+            for k in range(1, iters + 1)]
+
+
+def check_complex_gmres_vs_dense(sp, seed=24):
+    """Complex GMRES solution vs the dense LU solution."""
+    u0 = rng_complex(sp, seed)
+    f = rng_complex(sp, seed + 1, (sp.Nt,))
+    res = O.gmres(sp, u0, f, tol=1e-13, restart=50, max_iter=100)
+    return O.rel_error(res.U[1:], O.dense_solve(sp, u0, f)[1:]), res
+
+
+def check_complex_bicgstab_vs_dense(sp, seed=25):
+    u0 = rng_complex(sp, seed)
+    f = rng_complex(sp, seed + 1, (sp.Nt,))
+    res = O.bicgstab(sp, u0, f, tol=1e-13, max_iter=100)
+    return O.rel_error(res.U[1:], O.dense_solve(sp, u0, f)[1:]), res

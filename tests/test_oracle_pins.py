@@ -343,3 +343,77 @@ def test_etd1_first_order_convergence():
                          ids=["p1d", "d2d"])
 def test_etd1_richardson_reaches_sequential(sp):
     assert C.check_etd1_richardson_reaches_sequential(sp) < 1e-12
+
+
+# --------------------------------------------------- complex states (Sec. 7) --
+SE_SPECS = [
+    C.se_spec("dirichlet", (7,), 1j, 2j, Nt=8, order=1),
+    C.se_spec("dirichlet", (3, 4), 1j, 200j, Nt=9, order=2, dt=0.05),
+    C.se_spec("dirichlet", (5,), 0.3 + 1j, 0.1 + 2j, Nt=14, order=6, dt=0.02),
+    C.se_spec("periodic", (8,), 1j, 2j, Nt=8, order=1),
+    C.se_spec("periodic", (4, 6), 0.05 + 1j, 1j, Nt=9, order=2, length=(1.0, 1.5)),
+]
+SE_IDS = ["d1_s1", "d2_s2_c200i", "d1_s6_mixed", "p1_s1", "p2_s2"]
+
+
+@pytest.mark.parametrize("sp", SE_SPECS, ids=SE_IDS)
+def test_complex_A_matches_dense_expm(sp):
+    assert C.check_complex_A_vs_dense(sp) < 1e-12
+
+
+@pytest.mark.parametrize("sp", SE_SPECS, ids=SE_IDS)
+def test_complex_precond_matches_dense(sp):
+    assert C.check_complex_precond_vs_dense(sp) < 1e-11
+
+
+@pytest.mark.parametrize("sp", SE_SPECS, ids=SE_IDS)
+def test_complex_sequential_matches_dense(sp):
+    assert C.check_complex_sequential_vs_dense(sp) < 1e-11
+
+
+def test_schrodinger_sine_mode_closed_form():
+    assert C.check_schrodinger_sine_mode() < 1e-13
+
+
+@pytest.mark.parametrize("sp", [C.se_spec("dirichlet", (9,), 1j, 2j, Nt=12, order=1),
+                                C.se_spec("dirichlet", (3, 3), 1j, 200j, Nt=12, order=2),
+                                C.se_spec("periodic", (8,), 1j, 0.5j, Nt=12, order=6, dt=0.01)],
+                         ids=["d_s1", "d2_s2", "p_s6"])
+def test_unitary_propagator_keeps_norm(sp):
+    assert C.check_unitary_norm(sp) < 1e-12
+
+
+@pytest.mark.parametrize("sp", SE_SPECS[:3], ids=SE_IDS[:3])
+def test_complex_gmres_matches_dense(sp):
+    err, res = C.check_complex_gmres_vs_dense(sp)
+    assert err < 1e-11
+    assert res.history[-1] < 1e-13
+
+
+@pytest.mark.parametrize("sp", SE_SPECS[:3], ids=SE_IDS[:3])
+def test_complex_bicgstab_matches_dense(sp):
+    err, _ = C.check_complex_bicgstab_vs_dense(sp)
+    assert err < 1e-11
+
+
+@pytest.mark.parametrize("Nt", (50, 100, 200))
+def test_schrodinger_1d_gmres_one_iteration(Nt):
+    # Sec. 7: GMRES with the Exp-ParaDiag preconditioner converges in one
+    # iteration on the 1D Schrodinger equation (h = 1/128, dt = 0.01,
+    # alpha_opt, u_0 = sin(pi x)) for every window length: u_0 is an
+    # eigenvector of L_h, so the first residual is an eigenvector of the
+    # preconditioned operator (complex GMRES; a real GMRES on the real and
+    # imaginary parts would need two steps)
+    from paper_2603_04350_gb300 import inputs as I
+    errs = C.schrodinger_gmres_errors(I.SCHRODINGER_1D.with_(Nt=Nt), 1)
+    assert errs[0] < 1e-10
+
+
+@pytest.mark.parametrize("Nt", (20, 80))
+def test_schrodinger_2d_gmres_three_iterations(Nt):
+    # Sec. 7: BDF2 GMRES on the 2D Schrodinger equation (h = 1/40, dt = 0.05,
+    # c = 200i, the Gaussian wave packet) reaches the 1e-10 error in three
+    # iterations whatever the window length
+    from paper_2603_04350_gb300 import inputs as I
+    errs = C.schrodinger_gmres_errors(I.SCHRODINGER_2D.with_(Nt=Nt), 3)
+    assert errs[1] > 1e-10 and errs[2] < 1e-10

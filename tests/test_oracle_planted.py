@@ -214,3 +214,49 @@ def test_planted_etd1_residual_on_the_same_slice_is_caught(monkeypatch):
         return r if E.is_etd1(sp) else orig(sp, V, b)
     patch(monkeypatch, "residual", residual)
     assert C.check_etd1_richardson_reaches_sequential(ETD_P) > 1e-6
+
+
+# ------------------------------------------------------------ complex states --
+def _patched_source(monkeypatch, name, old, new):
+    """Plant a mistake by editing one line of an oracle function's source."""
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(getattr(E, name)))
+    assert old in src
+    ns = dict(vars(E))
+    exec(compile(src.replace(old, new), E.__file__, "exec"), ns)
+    patch(monkeypatch, name, ns[name])
+
+
+SE_D1 = C.se_spec("dirichlet", (7,), 1j, 2j, Nt=8, order=1)
+SE_D2 = C.se_spec("dirichlet", (3, 4), 1j, 200j, Nt=9, order=2)
+
+
+def test_planted_unconjugated_gmres_product_is_caught(monkeypatch):
+    # the bilinear sum v w in place of the Hermitian sum conj(v) w
+    _patched_source(monkeypatch, "gmres", "H[i, j] = np.vdot(Vb[i], w)", "H[i, j] = np.dot(Vb[i], w)")
+    err, _ = C.check_complex_gmres_vs_dense(SE_D2)
+    assert err > 1e-6
+
+
+def test_planted_real_gmres_coefficients_are_caught(monkeypatch):
+    # GMRES on the real and imaginary parts as a real vector (real projection
+    # coefficients): correct in the limit, but no longer one iteration on the
+    # 1D Schrodinger problem of Sec. 7
+    _patched_source(monkeypatch, "gmres", "H[i, j] = np.vdot(Vb[i], w)", "H[i, j] = np.vdot(Vb[i], w).real")
+    from paper_2603_04350_gb300 import inputs as I
+    assert C.schrodinger_gmres_errors(I.SCHRODINGER_1D.with_(Nt=50), 1)[0] > 1e-6
+
+
+def test_planted_real_part_of_complex_preconditioner_is_caught(monkeypatch):
+    _patched_source(monkeypatch, "precond_apply", "return s if sp.complex_state else s.real", "return s.real")
+    assert C.check_complex_precond_vs_dense(SE_D1) > 1e-3
+
+
+def test_planted_conjugated_symbol_is_caught(monkeypatch):
+    orig = E.spatial_eigenvalues
+
+    def spatial_eigenvalues(sp):
+        return np.conj(orig(sp))
+    patch(monkeypatch, "spatial_eigenvalues", spatial_eigenvalues)
+    assert C.check_schrodinger_sine_mode() > 1e-3
