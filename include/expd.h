@@ -84,12 +84,25 @@ typedef struct {
  * nonlinearity N.  b[d] is the velocity along grid axis d (the axis of n[d]);
  * advection needs a periodic grid: its spectral first derivative gives the
  * complex symbol -a|k|^2 - i b.k - c (the Nyquist wavenumber's first-derivative
- * symbol is 0, so real fields stay real).  b = {0, 0} for pure diffusion. */
+ * symbol is 0, so real fields stay real).  b = {0, 0} for pure diffusion.
+ *
+ * Complex states (the Schrodinger equation of Sec. 7: a = i, c = 2i or 200i):
+ * with complex_state = 1 the coefficients are a + i a_im and c + i c_im, and
+ * every state array of the calls below (u0, f, U, R, S) holds complex values,
+ * interleaved (re, im) doubles -- the layout of C99 double _Complex and of
+ * complex128 tensors -- so an array of k slices holds 2 k M doubles.  A complex
+ * state needs nonlin = EXPD_NL_NONE and the float64 precision (other cases
+ * return EXPD_ERR_UNSUPPORTED); GMRES then runs in complex arithmetic
+ * (Hermitian inner product, complex Givens rotations).  With complex_state = 0,
+ * a_im and c_im must be 0. */
 typedef struct {
     double a;
     double c;
     int nonlin;                 /* EXPD_NL_*                                           */
     double b[2];
+    double a_im;                /* imaginary part of a (complex_state only)            */
+    double c_im;                /* imaginary part of c (complex_state only)            */
+    int complex_state;          /* 0: real arrays, 1: complex (interleaved) arrays     */
 } expd_operator;
 
 /* Scheme and solver controls.

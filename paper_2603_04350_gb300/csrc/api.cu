@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <complex>
 #include <mutex>
 #include <cstdint>
 #include <string>
@@ -122,6 +123,14 @@ double* pinned_acquire(size_t ndoubles) {
 // spare, and the cancel flag
 size_t pinned_words(const expd_plan_s* p) { return 2 * (size_t)p->Ns + EXPD_CTL_DOUBLES + 2; }
 
+// Spatial-transform scratch: one complex value per mode and slice; a complex
+// state on a Dirichlet grid splits chunks of max(1, Ns/4) slices into real
+// and imaginary parts and needs 8 M doubles per slice of a chunk.
+size_t work64_bytes(const expd_plan_s* p) {
+    const size_t slices = (p->cplx && p->bc == EXPD_BC_DIRICHLET) ? (size_t)std::max(p->Ns, 4) : (size_t)p->Ns;
+    return slices * p->NY * p->KX * sizeof(double2);
+}
+
 void pinned_release(double* q, size_t ndoubles) {
     if (!q) return;
     int c = 3;
@@ -189,7 +198,7 @@ struct Staging {
 
 expd_status ensure_stage(expd_plan p) {
     if (p->stage) return EXPD_OK;
-    p->stage_elems = (size_t)(2 * p->Nt + 1) * p->M;
+    p->stage_elems = (size_t)(2 * p->Nt + 1) * p->Mp;
     return dalloc(p, reinterpret_cast<void**>(&p->stage), p->stage_elems * sizeof(double), "staging");
 }
 
@@ -203,7 +212,7 @@ expd_status stage_in(expd_plan p, const double* u0, const double* f, double* U, 
         expd_status r = ensure_stage(p);
         if (r != EXPD_OK) return r;
     }
-    const size_t M = (size_t)p->M;
+    const size_t M = (size_t)p->Mp;
     st.u0 = u0;
     st.f = f;
     st.U = U;
@@ -227,7 +236,7 @@ expd_status stage_in(expd_plan p, const double* u0, const double* f, double* U, 
 
 expd_status stage_out(expd_plan p, const Staging& st, cudaStream_t s) {
     if (st.U_host)
-        EXPD_CUDA_TRY(cudaMemcpyAsync(st.U_host, st.U, st.U_slices * (size_t)p->M * sizeof(double),
+        EXPD_CUDA_TRY(cudaMemcpyAsync(st.U_host, st.U, st.U_slices * (size_t)p->Mp * sizeof(double),
                                       cudaMemcpyDeviceToHost, s));
     if (st.U_host) EXPD_CUDA_TRY(cudaStreamSynchronize(s));
     return EXPD_OK;
@@ -242,7 +251,7 @@ void* eig_slice(expd_plan p, void* base, long long n) {
 // when f is given, and the assembled right-hand side Fh.
 expd_status setup_start(expd_plan p, const double* u0, const double* f, const double* Ugiven, cudaStream_t s,
                         float* F32 = nullptr, int fh_dd = 0) {
-    const size_t M = (size_t)p->M;
+    const size_t M = (size_t)p->Mp;
     const int so = p->order;
     // the mixed path transforms its data with double-float arithmetic (2^-48
     // roundoff, far below any tolerance it is run at) on the float32 pipes
@@ -333,7 +342,7 @@ expd_status read_reduced_norms(expd_plan p, cudaStream_t s, double out[4]) {
 // U output: u_1..u_{s-1} from the startup values, u_s..u_Nt from Uh.
 // Uh holds double-float values when uh_dd (the mixed path's accurate phase).
 expd_status write_solution(expd_plan p, double* U, cudaStream_t s, bool uh_dd = false) {
-    const size_t M = (size_t)p->M;
+    const size_t M = (size_t)p->Mp;
     if (p->order > 1)
         EXPD_CUDA_TRY(cudaMemcpyAsync(U, p->startphys + M, (size_t)(p->order - 1) * M * sizeof(double),
                                       cudaMemcpyDeviceToDevice, s));
@@ -523,7 +532,16 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
         return expd_fail(EXPD_ERR_UNSUPPORTED, "Nt - order + 1 exceeds 512 unknown slices");
     if (op->nonlin != EXPD_NL_NONE && op->nonlin != EXPD_NL_ALLEN_CAHN)
         return expd_fail(EXPD_ERR_INVALID_ARG, "unknown nonlinearity");
-    if (!isfinite(op->a) || !isfinite(op->c)) return expd_fail(EXPD_ERR_INVALID_ARG, "a and c must be finite");
+    if (!isfinite(op->a) || !isfinite(op->c) || !isfinite(op->a_im) || !isfinite(op->c_im))
+        return expd_fail(EXPD_ERR_INVALID_ARG, "a and c must be finite");
+    if (op->complex_state != 0 && op->complex_state != 1)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "complex_state must be 0 or 1");
+    if (!op->complex_state && (op->a_im != 0.0 || op->c_im != 0.0))
+        return expd_fail(EXPD_ERR_INVALID_ARG, "a complex a or c needs complex_state = 1");
+    if (op->complex_state && op->nonlin != EXPD_NL_NONE)
+        return expd_fail(EXPD_ERR_UNSUPPORTED, "complex states are built for linear problems");
+    if (op->complex_state && scheme->precision != EXPD_PREC_FP64)
+        return expd_fail(EXPD_ERR_UNSUPPORTED, "complex states run in the float64 precision");
     if (scheme->precision != EXPD_PREC_FP64 && scheme->precision != EXPD_PREC_MIXED)
         return expd_fail(EXPD_ERR_INVALID_ARG, "unknown precision");
     if (scheme->max_iter < 1 || scheme->max_iter > 100000)
@@ -560,6 +578,9 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     p->bc = grid->bc;
     p->a = op->a;
     p->c = op->c;
+    p->a_im = op->a_im;
+    p->c_im = op->c_im;
+    p->cplx = op->complex_state;
     p->nonlin = op->nonlin;
     if (!isfinite(op->b[0]) || !isfinite(op->b[1])) return expd_fail(EXPD_ERR_INVALID_ARG, "b must be finite");
     if (grid->ndim == 1) {
@@ -568,9 +589,11 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
         p->by = op->b[0];  // axis 0 is the slow (NY) axis
         p->bx = op->b[1];
     }
-    p->adv = p->bx != 0.0 || p->by != 0.0;
-    if (p->adv && grid->bc != EXPD_BC_PERIODIC)
+    const bool velocity = p->bx != 0.0 || p->by != 0.0;
+    if (velocity && grid->bc != EXPD_BC_PERIODIC)
         return expd_fail(EXPD_ERR_INVALID_ARG, "advection needs a periodic grid (the sine basis does not diagonalise it)");
+    // complex E and coefficient tables whenever the symbol is complex
+    p->adv = velocity || p->a_im != 0.0 || p->c_im != 0.0;
     if (op->nonlin != EXPD_NL_NONE && scheme->nl_form == EXPD_NLF_ETD1) {
         if (p->adv) return expd_fail(EXPD_ERR_UNSUPPORTED, "the ETD1 form takes real symbols (no advection)");
         if (scheme->jacobian == EXPD_JAC_MEAN_U0)
@@ -613,8 +636,12 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
             if (!(p->beta[q] * dt < 1.0)) return expd_fail(EXPD_ERR_INVALID_ARG, "nonlinear problems need beta_s*dt < 1");
     }
     p->M = (long long)p->NX * p->NY;
-    p->realcol = p->bc == EXPD_BC_DIRICHLET;
-    p->KX = p->realcol ? p->NX : p->NX / 2 + 1;
+    p->Mp = p->M * (p->cplx ? 2 : 1);
+    // a real state on a Dirichlet grid has real sine coefficients; a complex
+    // state keeps every mode (the full spectrum on a periodic grid: no
+    // conjugate symmetry halves it)
+    p->realcol = p->bc == EXPD_BC_DIRICHLET && !p->cplx;
+    p->KX = (p->bc == EXPD_BC_DIRICHLET || p->cplx) ? p->NX : p->NX / 2 + 1;
     p->Mcol = (long long)p->NY * p->KX;
     p->esz = p->realcol ? sizeof(double) : sizeof(double2);
     if (p->bc == EXPD_BC_DIRICHLET) {
@@ -993,27 +1020,33 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
         for (long long m = 0; m < p->Mcol; ++m) {
             const int kx = (int)(m % p->KX);
             const int ky = (int)(m / p->KX);
-            double mu = -p->c, nu = 0.0;  // symbol mu + i nu
+            // symbol mu + i nu = (a + i a_im) lap_m - i b.k - (c + i c_im), lap_m
+            // the Laplacian's eigenvalue on mode m
+            double lap = 0.0, nu = -p->c_im;
             if (p->bc == EXPD_BC_PERIODIC) {
-                const double wx = 2.0 * M_PI * kx / p->LX;
-                mu -= p->a * wx * wx;
+                // signed wavenumber (a complex state stores the full spectrum)
+                const int kxf = kx <= p->NX / 2 ? kx : kx - p->NX;
+                const double wx = 2.0 * M_PI * kxf / p->LX;
+                lap -= wx * wx;
                 if (2 * kx != p->NX) nu -= p->bx * wx;  // first derivative: 0 at the Nyquist wavenumber
                 if (p->ndim == 2) {
                     const int kyf = ky <= p->NY / 2 ? ky : ky - p->NY;
                     const double wy = 2.0 * M_PI * kyf / p->LY;
-                    mu -= p->a * wy * wy;
+                    lap -= wy * wy;
                     if (2 * ky != p->NY) nu -= p->by * wy;
                 }
             } else {
                 const double hx = p->LX / (p->NX + 1);
                 const double sx = sin(M_PI * (kx + 1) * hx / (2.0 * p->LX));
-                mu -= p->a * (4.0 / (hx * hx)) * sx * sx;
+                lap -= (4.0 / (hx * hx)) * sx * sx;
                 if (p->ndim == 2) {
                     const double hy = p->LY / (p->NY + 1);
                     const double sy = sin(M_PI * (ky + 1) * hy / (2.0 * p->LY));
-                    mu -= p->a * (4.0 / (hy * hy)) * sy * sy;
+                    lap -= (4.0 / (hy * hy)) * sy * sy;
                 }
             }
+            const double mu = p->a * lap - p->c;
+            nu += p->a_im * lap;
             if (!p->adv) {
                 E[m] = exp(dt * mu);
                 for (int j = 1; j <= p->order; ++j) {
@@ -1173,9 +1206,9 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
     if (st == EXPD_OK) st = dalloc(p, &p->Fh, vec, "right-hand side");
     if (st == EXPD_OK) st = dalloc(p, &p->Sh, (size_t)p->order * p->Mcol * p->esz, "startup (eigen)");
     if (st == EXPD_OK)
-        st = dalloc(p, reinterpret_cast<void**>(&p->startphys), (size_t)p->order * p->M * sizeof(double),
+        st = dalloc(p, reinterpret_cast<void**>(&p->startphys), (size_t)p->order * p->Mp * sizeof(double),
                     "startup (physical)");
-    const size_t work = (size_t)p->Ns * p->NY * p->KX * sizeof(double2);
+    const size_t work = work64_bytes(p);
     if (st == EXPD_OK) st = dalloc(p, &p->work64, work, "work64");
     if (st == EXPD_OK && p->nonlin != EXPD_NL_NONE) {
         st = dalloc(p, &p->NL64, vec, "N (float64)");
@@ -1255,8 +1288,8 @@ expd_status expd_plan_footprint_bytes(const expd_grid* grid, const expd_operator
         if (p->ndim == 2) b += (size_t)p->NY * p->NY * 8;
         if (p->tc_dst) b += dst_tc_bytes(p);                                // tensor-core DST digits
     }
-    b += 2 * vec + ord * Mcol * p->esz + ord * (size_t)p->M * 8;            // Uh, Fh, Sh, startphys
-    b += Ns * p->NY * p->KX * 16;                                           // work64
+    b += 2 * vec + ord * Mcol * p->esz + ord * (size_t)p->Mp * 8;            // Uh, Fh, Sh, startphys
+    b += work64_bytes(p);                                                   // work64
     if (nl) {
         b += vec;
         if (mixed && per) b += Ns * Mcol * 8 + Ns * p->NY * p->KX * 8;      // NL32, work32
@@ -1274,10 +1307,11 @@ expd_status expd_plan_footprint_bytes(const expd_grid* grid, const expd_operator
     if (st != EXPD_OK) return st;
     b += (size_t)std::max(grid_t, p->sm_count * 8) * Ns * 16;              // norm partials
     if (flags & EXPD_FOOTPRINT_SOURCE) b += (size_t)p->Nt * Mcol * p->esz;
-    if (flags & EXPD_FOOTPRINT_HOST) b += (size_t)(2 * p->Nt + 1) * p->M * 8;
+    if (flags & EXPD_FOOTPRINT_HOST) b += (size_t)(2 * p->Nt + 1) * p->Mp * 8;
     if (flags & EXPD_FOOTPRINT_GMRES) {
         const size_t n = (size_t)eigen_elems(p);
-        b += (size_t)std::max(p->restart + 3, 7) * n * 8 + (128 + 65 * (size_t)p->sm_count * 4) * 8;
+        const size_t grid = (size_t)p->sm_count * 4;
+        b += (size_t)std::max(p->restart + 3, 7) * n * 8 + (p->cplx ? 256 + 131 * grid : 128 + 65 * grid) * 8;
     }
     *bytes = b;
     return EXPD_OK;
@@ -1330,7 +1364,7 @@ expd_status expd_residual(expd_plan p, const double* u0, const double* f, const 
     if (f && p->nl_form == EXPD_NLF_ETD1) return expd_fail(EXPD_ERR_INVALID_ARG, "the ETD1 form takes no source term");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     EXPD_CUDA_TRY(plan_bind_stream(p, s));
-    const size_t M = (size_t)p->M;
+    const size_t M = (size_t)p->Mp;
     Staging sg;
     expd_status st = stage_in(p, u0, f, const_cast<double*>(U), p->Nt, true, sg, s);
     if (st != EXPD_OK) return st;
@@ -1380,7 +1414,7 @@ expd_status expd_precond_apply(expd_plan p, const double* R, double* S, void* st
     if (!p || !R || !S) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, R and S are required");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     EXPD_CUDA_TRY(plan_bind_stream(p, s));
-    const size_t M = (size_t)p->M;
+    const size_t M = (size_t)p->Mp;
     const size_t bytes = (size_t)p->Ns * M * sizeof(double);
     const double* Rd = R;
     double* Sd = S;
@@ -1496,7 +1530,7 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
         const double nbar = 1.0 - 3.0 * p->redhost[0] / (double)p->M;
         dshift = p->beta[p->order] * p->dt * nbar;
     }
-    double* phys_out = sg.U + (size_t)(p->order - 1) * p->M;
+    double* phys_out = sg.U + (size_t)(p->order - 1) * p->Mp;
     const bool fast_out = use_dd && nl && inverse32_accum_supported(p);
     // the time operator of a sweep of phase ph (first: the first double-float
     // sweep reading the float32 iterate)
@@ -1667,7 +1701,7 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     if (st != EXPD_OK) return st;
     if (phase == PHDD && phys_valid && last_rel <= 1e-4) {
         if (p->order > 1)
-            EXPD_CUDA_TRY(cudaMemcpyAsync(sg.U, p->startphys + p->M, (size_t)(p->order - 1) * p->M * sizeof(double),
+            EXPD_CUDA_TRY(cudaMemcpyAsync(sg.U, p->startphys + p->Mp, (size_t)(p->order - 1) * p->Mp * sizeof(double),
                                           cudaMemcpyDeviceToDevice, s));
         st = spatial_inverse32_accum(p, p->U32, phys_out, s);
     } else {
@@ -1682,7 +1716,11 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
 
 // The Krylov block: nvec vectors of eigen_elems doubles, then the dot results
 // and partials (128 + 65 x dots grid doubles).
-static size_t krylov_hblock(expd_plan p) { return 128 + 65 * (size_t)(p->sm_count * 4); }
+// results and per-block partials of the Krylov dot products: up to 65 results
+// (128 slots; 256 and twice the partials for a complex state's re/im pairs)
+static size_t krylov_hblock(expd_plan p) {
+    return p->cplx ? 256 + 131 * (size_t)(p->sm_count * 4) : 128 + 65 * (size_t)(p->sm_count * 4);
+}
 
 static expd_status ensure_krylov(expd_plan p, int nvec) {
     const size_t n = (size_t)eigen_elems(p);
@@ -1983,6 +2021,141 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
                 break;
             }
         }
+    } else if (p->cplx) {
+        // ---- complex state: complex GMRES (float64) ----
+        // The Hermitian inner product <v, w> = sum conj(v) w (its real part is
+        // the plain dot product of the interleaved arrays), complex Hessenberg
+        // entries, classical Gram-Schmidt with one re-orthogonalisation and
+        // complex Givens rotations G = [[conj(c), s], [-s, c]], |c|^2 + s^2 = 1
+        // with s real (the subdiagonal entry is a norm).
+        typedef std::complex<double> cd;
+        std::vector<double> tbuf(2 * (size_t)(m + 1));
+        auto cdots = [&](const double* Vb, int k, const double* vec, cd* out) -> expd_status {
+            expd_status r = gm_cdots(p, Vb, n, k, vec, h, s);
+            if (r != EXPD_OK) return r;
+            EXPD_CUDA_TRY(cudaMemcpyAsync(tbuf.data(), h, 2 * (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, s));
+            EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+            for (int i = 0; i < k; ++i) out[i] = cd(tbuf[2 * i], tbuf[2 * i + 1]);
+            return EXPD_OK;
+        };
+        // x -= sum_i coef_i V_i
+        auto cupdate = [&](const double* Vb, int k, const cd* coef, double* xv) -> expd_status {
+            for (int i = 0; i < k; ++i) {
+                tbuf[2 * i] = coef[i].real();
+                tbuf[2 * i + 1] = coef[i].imag();
+            }
+            EXPD_CUDA_TRY(cudaMemcpyAsync(h, tbuf.data(), 2 * (size_t)k * sizeof(double), cudaMemcpyHostToDevice, s));
+            return gm_cupdate(p, Vb, n, k, h, xv, s);
+        };
+        {
+            TimeOp op;
+            op.F = p->Fh;
+            op.f_slices = p->f_slices;
+            op.precond = 1;
+            op.out = c;
+            st = time_apply(p, op, s);
+            if (st != EXPD_OK) return st;
+        }
+        double cn2 = 0;
+        st = dots(c, 1, c, &cn2);
+        if (st != EXPD_OK) return st;
+        cn = sqrt(cn2);
+        std::vector<cd> Hc((size_t)(m + 1) * m), csc(m), gc(m + 1), h1(m + 1), h2(m + 1), yc(m);
+        std::vector<double> snc(m);
+        bool first = true;
+        while (cn > 0) {
+            if (first) {
+                EXPD_CUDA_TRY(cudaMemcpyAsync(V, c, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            } else {
+                st = residual_op(V);
+                if (st != EXPD_OK) return st;
+            }
+            first = false;
+            double b2 = 0;
+            st = dots(V, 1, V, &b2);
+            if (st != EXPD_OK) return st;
+            const double beta = sqrt(b2);
+            relres = beta / cn;
+            if (!(relres == relres)) {
+                result = expd_fail(EXPD_ERR_DIVERGED, "GMRES residual is non-finite");
+                break;
+            }
+            if (relres <= tol_res) {
+                result = EXPD_OK;
+                break;
+            }
+            if (total >= p->max_iter) break;
+            st = gm_axpby(p, n, 1.0 / beta, V, 0.0, V, s);
+            if (st != EXPD_OK) return st;
+            std::fill(gc.begin(), gc.end(), cd(0.0));
+            gc[0] = beta;
+            int jdone = 0;
+            bool conv = false;
+            expd_status stop = EXPD_OK;
+            for (int j = 0; j < m && total < p->max_iter; ++j) {
+                double* vj1 = V + (size_t)(j + 1) * n;
+                st = apply_op(V + (size_t)j * n, w);
+                if (st != EXPD_OK) return st;
+                st = cdots(V, j + 1, w, h1.data());
+                if (st == EXPD_OK) st = cupdate(V, j + 1, h1.data(), w);
+                if (st == EXPD_OK) st = cdots(V, j + 1, w, h2.data());
+                if (st == EXPD_OK) st = cupdate(V, j + 1, h2.data(), w);
+                if (st != EXPD_OK) return st;
+                for (int i = 0; i <= j; ++i) Hc[(size_t)i * m + j] = h1[i] + h2[i];
+                double wn2 = 0;
+                st = dots(w, 1, w, &wn2);
+                if (st != EXPD_OK) return st;
+                const double hn = sqrt(wn2);
+                Hc[(size_t)(j + 1) * m + j] = hn;
+                if (hn > 0) {
+                    st = gm_axpby(p, n, 1.0 / hn, w, 0.0, vj1, s);
+                    if (st != EXPD_OK) return st;
+                }
+                for (int i = 0; i < j; ++i) {
+                    const cd a0 = Hc[(size_t)i * m + j], a1 = Hc[(size_t)(i + 1) * m + j];
+                    Hc[(size_t)i * m + j] = std::conj(csc[i]) * a0 + snc[i] * a1;
+                    Hc[(size_t)(i + 1) * m + j] = -snc[i] * a0 + csc[i] * a1;
+                }
+                const cd hjj = Hc[(size_t)j * m + j];
+                const double den = hypot(std::abs(hjj), hn);
+                csc[j] = hjj / den;
+                snc[j] = hn / den;
+                Hc[(size_t)j * m + j] = den;
+                Hc[(size_t)(j + 1) * m + j] = 0.0;
+                gc[j + 1] = -snc[j] * gc[j];
+                gc[j] = std::conj(csc[j]) * gc[j];
+                ++total;
+                jdone = j + 1;
+                relres = std::abs(gc[j + 1]) / cn;
+                if (info && total < EXPD_MAX_HISTORY) info->history[total] = relres;
+                if (relres <= tol_res || hn == 0) {
+                    conv = true;
+                    break;
+                }
+                stop = poll_stop(p);
+                if (stop != EXPD_OK) break;
+            }
+            // x += V y,  H y = g (back substitution); the update subtracts -y
+            for (int i = jdone - 1; i >= 0; --i) {
+                cd acc = gc[i];
+                for (int k = i + 1; k < jdone; ++k) acc -= Hc[(size_t)i * m + k] * yc[k];
+                yc[i] = acc / Hc[(size_t)i * m + i];
+            }
+            for (int i = 0; i < jdone; ++i) h1[i] = -yc[i];
+            if (jdone > 0) {
+                st = cupdate(V, jdone, h1.data(), x);
+                if (st != EXPD_OK) return st;
+            }
+            EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+            if (stop != EXPD_OK) {
+                result = stop;
+                break;
+            }
+            if (conv) {
+                result = EXPD_OK;
+                break;
+            }
+        }
     } else {
     // c = P^{-1} f_s
     {
@@ -2116,6 +2289,7 @@ expd_status expd_solve_bicgstab(expd_plan p, const double* u0, const double* f, 
                                 void* stream) {
     if (!p || !u0 || !U) return expd_fail(EXPD_ERR_INVALID_ARG, "plan, u0 and U are required");
     if (p->nonlin != EXPD_NL_NONE) return expd_fail(EXPD_ERR_INVALID_ARG, "BiCGStab needs a linear problem");
+    if (p->cplx) return expd_fail(EXPD_ERR_UNSUPPORTED, "BiCGStab takes real states (complex states: GMRES)");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     EXPD_CUDA_TRY(plan_bind_stream(p, s));
     expd_status st = call_begin(p, info, s);

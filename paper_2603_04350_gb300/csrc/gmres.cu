@@ -17,7 +17,7 @@ constexpr int GM_PER_THREAD = 4;
 constexpr int GM_CHUNK = GM_THREADS * GM_PER_THREAD;
 
 __device__ __forceinline__ double elem_weight(long long e, long long Mcol, int KX, int NX, int realcol) {
-    if (realcol) return 1.0;
+    if (realcol || KX == NX) return 1.0;  // real columns, or a complex state's full spectrum
     const long long m = (e >> 1) % Mcol;
     const int kx = (int)(m % KX);
     return (kx == 0 || 2 * kx == NX) ? 1.0 : 2.0;
@@ -129,6 +129,69 @@ __global__ void axpby_kernel(long long n, double a, const double* x, double b, d
         y[e] = b == 0.0 ? a * x[e] : fma(a, x[e], b * y[e]);
 }
 
+// Complex states: partial[2i][block] and partial[2i+1][block] = real and
+// imaginary parts of this block's share of <V_i, x> = sum conj(V_i) x over
+// the complex elements (interleaved re, im doubles), fixed order.
+template <int K>
+__global__ void __launch_bounds__(GM_THREADS) cdots_kernel(const double2* __restrict__ V, long long ld2,
+                                                           const double2* __restrict__ x, long long n2,
+                                                           double* __restrict__ partial) {
+    __shared__ double red[2 * K][GM_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double re[K], im[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) re[i] = im[i] = 0.0;
+    for (long long base = (long long)blockIdx.x * GM_CHUNK; base < n2; base += (long long)gridDim.x * GM_CHUNK) {
+#pragma unroll
+        for (int t = 0; t < GM_PER_THREAD; ++t) {
+            const long long e = base + t * GM_THREADS + threadIdx.x;
+            if (e < n2) {
+                const double2 xe = x[e];
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    const double2 v = V[(long long)i * ld2 + e];
+                    re[i] = fma(v.x, xe.x, fma(v.y, xe.y, re[i]));
+                    im[i] = fma(v.x, xe.y, fma(-v.y, xe.x, im[i]));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        double a = re[i], b = im[i];
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) {
+            red[2 * i][warp] = a;
+            red[2 * i + 1][warp] = b;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * K) {
+        double t = 0.0;
+        for (int w = 0; w < GM_THREADS / 32; ++w) t += red[threadIdx.x][w];
+        partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// x -= sum_{i<k} h_i V_i with complex h_i = (h[2i], h[2i+1])
+__global__ void cupdate_kernel(const double2* __restrict__ V, long long ld2, int k, const double* __restrict__ h,
+                               double2* __restrict__ x, long long n2) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n2;
+         e += (long long)gridDim.x * blockDim.x) {
+        double2 acc = x[e];
+        for (int i = 0; i < k; ++i) {
+            const double2 v = V[(long long)i * ld2 + e];
+            const double hr = h[2 * i], hi = h[2 * i + 1];
+            acc.x = fma(-hr, v.x, fma(hi, v.y, acc.x));
+            acc.y = fma(-hr, v.y, fma(-hi, v.x, acc.y));
+        }
+        x[e] = acc;
+    }
+}
+
 }  // namespace
 
 long long eigen_elems(expd_plan p) { return (long long)p->Ns * p->Mcol * (p->realcol ? 1 : 2); }
@@ -193,6 +256,52 @@ expd_status gm_update(expd_plan p, const double* V, long long ld, int k, const d
 expd_status gm_axpby(expd_plan p, long long n, double a, const double* x, double b, double* y, cudaStream_t s) {
     KProf kp(p, s, EXPD_K_GMRES, 24.0 * (double)n, 3.0 * (double)n);
     axpby_kernel<<<p->sm_count * 8, 256, 0, s>>>(n, a, x, b, y);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+// Complex states: h_dev[2i], h_dev[2i+1] = <V_i, w> = sum conj(V_i) w for
+// i < k (k <= 65); per-block partials after the 256 result slots.
+expd_status gm_cdots(expd_plan p, const double* V, long long ld, int k, const double* w, double* h_dev,
+                     cudaStream_t s) {
+    const long long n2 = eigen_elems(p) / 2;
+    const int grid = p->sm_count * 4;
+    double* partial = h_dev + 256;  // caller reserves 256 + 131 * grid doubles
+    KProf kp(p, s, EXPD_K_GMRES, 16.0 * (k + (k + GM_DOTS - 1) / GM_DOTS) * (double)n2, 8.0 * k * (double)n2);
+    const double2* V2 = reinterpret_cast<const double2*>(V);
+    const double2* w2 = reinterpret_cast<const double2*>(w);
+    for (int i0 = 0; i0 < k; i0 += GM_DOTS) {
+        const int kk = std::min(GM_DOTS, k - i0);
+        const double2* Vc = V2 + (long long)i0 * (ld / 2);
+        double* pc = partial + 2LL * i0 * grid;
+        switch (kk) {
+#define EXPD_CDOTS_CASE(K)                                                                 \
+    case K:                                                                                \
+        cdots_kernel<K><<<grid, GM_THREADS, 0, s>>>(Vc, ld / 2, w2, n2, pc);               \
+        break;
+            EXPD_CDOTS_CASE(1)
+            EXPD_CDOTS_CASE(2)
+            EXPD_CDOTS_CASE(3)
+            EXPD_CDOTS_CASE(4)
+            EXPD_CDOTS_CASE(5)
+            EXPD_CDOTS_CASE(6)
+            EXPD_CDOTS_CASE(7)
+            EXPD_CDOTS_CASE(8)
+#undef EXPD_CDOTS_CASE
+        }
+        EXPD_CUDA_TRY(cudaGetLastError());
+    }
+    dots_final<<<2 * k, 256, 0, s>>>(partial, grid, 2 * k, h_dev);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+expd_status gm_cupdate(expd_plan p, const double* V, long long ld, int k, const double* h_dev, double* x,
+                       cudaStream_t s) {
+    const long long n2 = eigen_elems(p) / 2;
+    KProf kp(p, s, EXPD_K_GMRES, 16.0 * (k + 2) * (double)n2, 8.0 * k * (double)n2);
+    cupdate_kernel<<<p->sm_count * 8, 256, 0, s>>>(reinterpret_cast<const double2*>(V), ld / 2, k, h_dev,
+                                                   reinterpret_cast<double2*>(x), n2);
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }

@@ -59,8 +59,10 @@ struct expd_plan_s {
     int bc = EXPD_BC_PERIODIC;
     double LX = 1, LY = 1;
     double a = 0, c = 0;
+    double a_im = 0, c_im = 0;  // imaginary parts of a and c (complex states)
+    int cplx = 0;           // complex state: interleaved complex physical slices, full spectrum
     double bx = 0, by = 0;  // advection velocity along NX / NY
-    int adv = 0;            // advection present: complex symbol, complex E and coefficient tables
+    int adv = 0;            // complex symbol (advection, or imaginary a or c): complex E and coefficient tables
     int nonlin = EXPD_NL_NONE;
     double dt = 0;
     int Nt = 0, order = 1, Ns = 0;
@@ -75,9 +77,10 @@ struct expd_plan_s {
 
     // ---- layout -------------------------------------------------------------
     long long M = 0;     // physical points per slice
-    int KX = 0;          // periodic: NX/2+1 complex per row; Dirichlet: NX real per row
+    long long Mp = 0;    // doubles per physical slice: M, or 2 M for a complex state
+    int KX = 0;          // periodic: NX/2+1 complex per row; Dirichlet or complex state: NX per row
     long long Mcol = 0;  // time columns per slice (complex modes or real modes)
-    int realcol = 0;     // 1 for Dirichlet (real eigen-coefficients)
+    int realcol = 0;     // 1 for Dirichlet grids with a real state (real eigen-coefficients)
     size_t esz = 16;     // bytes per eigen element (16 complex, 8 real)
 
     // ---- tables ---------------------------------------------------------------
@@ -335,4 +338,9 @@ expd_status gm_update_norm(expd_plan p, const double* V, long long ld, int k, co
                            double* w, double* h_dev, cudaStream_t s);
 // y = a*x + b*y  (plain elementwise)
 expd_status gm_axpby(expd_plan p, long long n, double a, const double* x, double b, double* y, cudaStream_t s);
+// complex states: Hermitian dot products (re, im pairs) and complex multi-axpy
+expd_status gm_cdots(expd_plan p, const double* V, long long ld, int k, const double* w, double* h_dev,
+                     cudaStream_t s);
+expd_status gm_cupdate(expd_plan p, const double* V, long long ld, int k, const double* h_dev, double* x,
+                       cudaStream_t s);
 long long eigen_elems(expd_plan p);  // doubles per space-time eigen vector

@@ -1146,10 +1146,130 @@ expd_status dst2(expd_plan p, const double* X, double* Y, int ns, double* tmp, c
     return dgemm(p, p->Sy, NY, 0, tmp, NX, (long long)NY * NX, Y, NX, (long long)NY * NX, NY, NX, NY, ns, s);
 }
 
+// Complex-to-complex FFT along contiguous rows of length n (a power of two),
+// for complex states on periodic grids: one warp per row, its length-n buffer
+// in shared memory (loaded in bit-reversed order), sign -1 forward and +1
+// inverse, the output scaled by `scale`.  A warp reads its whole row before
+// writing it, so in == out is allowed.
+__global__ void __launch_bounds__(128) crow_kernel(const double2* __restrict__ in, double2* __restrict__ out,
+                                                   long long rows, int n, int log2n,
+                                                   const double2* __restrict__ tw, int sign, double scale) {
+    extern __shared__ double2 cbuf[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    double2* z = cbuf + (size_t)warp * n;
+    for (long long r = (long long)blockIdx.x * nw + warp; r < rows; r += (long long)gridDim.x * nw) {
+        const double2* x = in + r * n;
+        for (int j = lane; j < n; j += 32) z[bitrev((unsigned)j, log2n)] = x[j];
+        __syncwarp();
+        fft_dit(z, log2n, tw, 1, sign, lane, 32);
+        double2* y = out + r * n;
+        for (int k = lane; k < n; k += 32) y[k] = cscale(z[k], scale);
+        __syncwarp();
+    }
+}
+
+expd_status crow(expd_plan p, const double2* in, double2* out, long long rows, int sign, double scale,
+                 cudaStream_t s) {
+    const int n = p->NX, log2n = ilog2(n);
+    const int warps = std::max(1, std::min(4, 65536 / (n * 16)));
+    const size_t smem = (size_t)warps * n * sizeof(double2);
+    const long long grid = std::max(1LL, std::min<long long>((rows + warps - 1) / warps, (long long)p->sm_count * 32));
+    EXPD_CUDA_TRY(smem_allow((const void*)crow_kernel, smem));
+    KProf kp(p, s, EXPD_K_FFT_ROW, 32.0 * rows * n, 5.0 * n * log2n * (double)rows);
+    crow_kernel<<<(int)grid, 32 * warps, smem, s>>>(in, out, rows, n, log2n, p->Wx64, sign, scale);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+// A complex slice of M values as two real slices (real part, then imaginary
+// part), and back: the real sine transform then acts on both parts alike.
+__global__ void split_complex_kernel(const double2* __restrict__ in, double* __restrict__ out, long long M,
+                                     long long total) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long sl = i / M, e = i - sl * M;
+        const double2 v = in[i];
+        out[2 * sl * M + e] = v.x;
+        out[(2 * sl + 1) * M + e] = v.y;
+    }
+}
+
+__global__ void join_complex_kernel(const double* __restrict__ in, double2* __restrict__ out, long long M,
+                                    long long total) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long sl = i / M, e = i - sl * M;
+        out[i] = make_double2(in[2 * sl * M + e], in[(2 * sl + 1) * M + e]);
+    }
+}
+
+// Complex states (float64): forward (dir = -1) or inverse (dir = +1) spatial
+// transform of nslices complex slices.  Periodic grids: complex FFTs along
+// rows and columns, the full spectrum.  Dirichlet grids: split, the real
+// orthonormal sine transform of the 2 ns real slices (its own inverse), join.
+expd_status spatial_complex64(expd_plan p, const double* in, double* out, int nslices, int dir, cudaStream_t s) {
+    const long long M = p->M;
+    if (p->bc == EXPD_BC_PERIODIC) {
+        const int chunk = p->Ns;
+        for (int b0 = 0; b0 < nslices; b0 += chunk) {
+            const int ns = std::min(chunk, nslices - b0);
+            const double2* x = reinterpret_cast<const double2*>(in) + (long long)b0 * M;
+            double2* y = reinterpret_cast<double2*>(out) + (long long)b0 * M;
+            double2* w = static_cast<double2*>(p->work64);
+            expd_status st;
+            if (dir < 0) {
+                if (p->ndim == 1) {
+                    st = crow(p, x, y, ns, -1, 1.0, s);
+                } else {
+                    st = crow(p, x, w, (long long)ns * p->NY, -1, 1.0, s);
+                    if (st == EXPD_OK) st = launch_col<double, double2, double2>(p, w, y, ns, -1, 1.0, s);
+                }
+            } else {
+                const double sx = 1.0 / p->NX;
+                if (p->ndim == 1) {
+                    st = crow(p, x, y, ns, +1, sx, s);
+                } else {
+                    st = launch_col<double, double2, double2>(p, x, w, ns, +1, 1.0 / p->NY, s);
+                    if (st == EXPD_OK) st = crow(p, w, y, (long long)ns * p->NY, +1, sx, s);
+                }
+            }
+            if (st != EXPD_OK) return st;
+        }
+        return EXPD_OK;
+    }
+    // work64 holds 2 max(Ns, 4) M doubles: the split slices, the transformed
+    // ones and the sine transform's scratch, 8 M doubles per complex slice
+    const int chunk = std::max(1, p->Ns / 4);
+    double* P = static_cast<double*>(p->work64);
+    double* Q = P + 2LL * chunk * M;
+    double* tmp = Q + 2LL * chunk * M;
+    for (int b0 = 0; b0 < nslices; b0 += chunk) {
+        const int ns = std::min(chunk, nslices - b0);
+        const long long total = (long long)ns * M;
+        const int blocks = grid_for(total, 256);
+        {
+            KProf kp(p, s, EXPD_K_POINTWISE, 32.0 * total, 0.0);
+            split_complex_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const double2*>(in) + (long long)b0 * M, P,
+                                                        M, total);
+            EXPD_CUDA_TRY(cudaGetLastError());
+        }
+        expd_status st = dst2(p, P, Q, 2 * ns, tmp, s);
+        if (st != EXPD_OK) return st;
+        {
+            KProf kp(p, s, EXPD_K_POINTWISE, 32.0 * total, 0.0);
+            join_complex_kernel<<<blocks, 256, 0, s>>>(Q, reinterpret_cast<double2*>(out) + (long long)b0 * M, M,
+                                                       total);
+            EXPD_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    return EXPD_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ launchers ----
 expd_status spatial_forward64(expd_plan p, const double* phys, void* eig, int nslices, cudaStream_t s) {
+    if (p->cplx) return spatial_complex64(p, phys, static_cast<double*>(eig), nslices, -1, s);
     const int chunk = p->Ns;
     for (int b0 = 0; b0 < nslices; b0 += chunk) {
         const int ns = std::min(chunk, nslices - b0);
@@ -1174,6 +1294,7 @@ expd_status spatial_forward64(expd_plan p, const double* phys, void* eig, int ns
 }
 
 expd_status spatial_inverse64(expd_plan p, const void* eig, double* phys, int nslices, cudaStream_t s) {
+    if (p->cplx) return spatial_complex64(p, static_cast<const double*>(eig), phys, nslices, +1, s);
     const int chunk = p->Ns;
     for (int b0 = 0; b0 < nslices; b0 += chunk) {
         const int ns = std::min(chunk, nslices - b0);

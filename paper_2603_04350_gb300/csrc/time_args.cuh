@@ -119,7 +119,9 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 template <typename ST>
 __device__ __forceinline__ ST mode_weight(long long m, int KX, int NX, int realcol) {
-    if (realcol) return (ST)1;
+    // real columns, or the full spectrum of a complex state (KX = NX): every
+    // mode stands for itself
+    if (realcol || KX == NX) return (ST)1;
     const int kx = (int)(m % KX);
     return (kx == 0 || 2 * kx == NX) ? (ST)1 : (ST)2;
 }

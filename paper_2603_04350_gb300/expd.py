@@ -46,7 +46,8 @@ class Grid(C.Structure):
 
 
 class Operator(C.Structure):
-    _fields_ = [("a", C.c_double), ("c", C.c_double), ("nonlin", C.c_int), ("b", C.c_double * 2)]
+    _fields_ = [("a", C.c_double), ("c", C.c_double), ("nonlin", C.c_int), ("b", C.c_double * 2),
+                ("a_im", C.c_double), ("c_im", C.c_double), ("complex_state", C.c_int)]
 
 
 class Scheme(C.Structure):
@@ -130,18 +131,21 @@ def _check(status: int, allow=(OK,)) -> int:
     return status
 
 
-def _ptr(x) -> Optional[int]:
-    """Data pointer of a float64 C-contiguous torch tensor or numpy array."""
+def _ptr(x, cplx: bool = False) -> Optional[int]:
+    """Data pointer of a C-contiguous torch tensor or numpy array: float64, or
+    complex128 (interleaved re, im doubles) for a plan with a complex state."""
     if x is None:
         return None
     if isinstance(x, np.ndarray):
-        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
-            raise ValueError("arrays must be float64 and C-contiguous")
+        want = np.complex128 if cplx else np.float64
+        if x.dtype != want or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"arrays must be {np.dtype(want).name} and C-contiguous")
         return x.ctypes.data
     import torch
     if isinstance(x, torch.Tensor):
-        if x.dtype != torch.float64 or not x.is_contiguous():
-            raise ValueError("tensors must be float64 and contiguous")
+        want = torch.complex128 if cplx else torch.float64
+        if x.dtype != want or not x.is_contiguous():
+            raise ValueError(f"tensors must be {want} and contiguous")
         return x.data_ptr()
     raise TypeError(f"unsupported array type {type(x)}")
 
@@ -183,6 +187,7 @@ class PlanSpec:
     kernel_flags: int = 0
     nl_form: int = NLF_IF
     time_limit_ms: float = 0.0
+    complex_state: bool = False   # complex a, c and complex128 state arrays
 
 
 def _structs(spec: PlanSpec):
@@ -192,7 +197,9 @@ def _structs(spec: PlanSpec):
         g.n[d] = int(spec.n[d])
         g.length[d] = float(spec.length[d])
     g.bc = spec.bc
-    o = Operator(spec.a, spec.c, spec.nonlin, (C.c_double * 2)(*(tuple(spec.b) + (0.0, 0.0))[:2]))
+    a, c = complex(spec.a), complex(spec.c)
+    o = Operator(a.real, c.real, spec.nonlin, (C.c_double * 2)(*(tuple(spec.b) + (0.0, 0.0))[:2]),
+                 a.imag, c.imag, 1 if spec.complex_state else 0)
     s = Scheme(spec.order, spec.precision, spec.max_iter, spec.tol, spec.gmres_restart, spec.startup, spec.jacobian,
                spec.guess, spec.kernel_flags, spec.nl_form, spec.time_limit_ms)
     return g, o, s
@@ -234,6 +241,10 @@ class Plan:
         self._h = handle
         self.spec = spec
         self.Ns = spec.Nt - spec.order + 1
+        self._c = bool(spec.complex_state)
+
+    def _p(self, x):
+        return _ptr(x, self._c)
 
     def workspace_bytes(self) -> int:
         b = C.c_size_t()
@@ -241,15 +252,16 @@ class Plan:
         return b.value
 
     def residual(self, u0, f, U, R, stream=None) -> None:
-        _check(lib().expd_residual(self._h, _ptr(u0), _ptr(f), _ptr(U), _ptr(R), _stream(stream)))
+        _check(lib().expd_residual(self._h, self._p(u0), self._p(f), self._p(U), self._p(R), _stream(stream)))
 
     def precond_apply(self, R, S, stream=None) -> None:
-        _check(lib().expd_precond_apply(self._h, _ptr(R), _ptr(S), _stream(stream)))
+        _check(lib().expd_precond_apply(self._h, self._p(R), self._p(S), _stream(stream)))
 
     def solve_fp(self, u0, f, U, stream=None, allow_not_converged=False) -> dict:
         info = Info()
         allow = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
-        st = _check(lib().expd_solve_fp(self._h, _ptr(u0), _ptr(f), _ptr(U), C.byref(info), _stream(stream)), allow)
+        st = _check(lib().expd_solve_fp(self._h, self._p(u0), self._p(f), self._p(U), C.byref(info), _stream(stream)),
+                    allow)
         d = info.as_dict()
         d["status"] = st
         return d
@@ -257,7 +269,8 @@ class Plan:
     def solve_gmres(self, u0, f, U, stream=None, allow_not_converged=False) -> dict:
         info = Info()
         allow = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
-        st = _check(lib().expd_solve_gmres(self._h, _ptr(u0), _ptr(f), _ptr(U), C.byref(info), _stream(stream)),
+        st = _check(lib().expd_solve_gmres(self._h, self._p(u0), self._p(f), self._p(U), C.byref(info),
+                                           _stream(stream)),
                     allow)
         d = info.as_dict()
         d["status"] = st
@@ -266,7 +279,8 @@ class Plan:
     def solve_bicgstab(self, u0, f, U, stream=None, allow_not_converged=False) -> dict:
         info = Info()
         allow = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
-        st = _check(lib().expd_solve_bicgstab(self._h, _ptr(u0), _ptr(f), _ptr(U), C.byref(info), _stream(stream)),
+        st = _check(lib().expd_solve_bicgstab(self._h, self._p(u0), self._p(f), self._p(U), C.byref(info),
+                                              _stream(stream)),
                     allow)
         d = info.as_dict()
         d["status"] = st
@@ -278,7 +292,7 @@ class Plan:
 
     def solve_sequential(self, u0, f, U, stream=None) -> None:
         """Step the scheme sequentially (float64): the exact all-at-once solution."""
-        _check(lib().expd_solve_sequential(self._h, _ptr(u0), _ptr(f), _ptr(U), _stream(stream)))
+        _check(lib().expd_solve_sequential(self._h, self._p(u0), self._p(f), self._p(U), _stream(stream)))
 
     def timing_enable(self, enable: bool = True) -> None:
         _check(lib().expd_timing_enable(self._h, 1 if enable else 0))
@@ -318,4 +332,5 @@ def spec_from_problem(p, precision: int = PREC_FP64, max_iter: int = 100, tol: O
                     jacobian=jacobian, b=tuple(getattr(p, "b", ()) or (0.0, 0.0)), guess=guess,
                     kernel_flags=kernel_flags,
                     nl_form=(NLF_ETD1 if getattr(p, "nl_form", "if") == "etd1" else NLF_IF) if nl_form is None
-                    else nl_form, time_limit_ms=time_limit_ms)
+                    else nl_form, time_limit_ms=time_limit_ms,
+                    complex_state=bool(getattr(p, "complex_state", False)))

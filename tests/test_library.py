@@ -84,6 +84,8 @@ def test_plan_create_rejects_too_long_windows_without_touching_the_gpu(expd):
     (dict(bc=1, n=(7, 7), b=(0.5, 0.0)), "advection needs a periodic grid"),
     (dict(jacobian=5), "jacobian"),
     (dict(guess=2), "guess"),
+    (dict(a=0.01 + 1j), "complex_state"),
+    (dict(c=2j), "complex_state"),
 ])
 def test_plan_create_rejects_bad_arguments_without_touching_the_gpu(expd, kw, msg):
     spec = _spec(expd, **kw)
@@ -99,6 +101,16 @@ def test_plan_create_rejects_bad_arguments_without_touching_the_gpu(expd, kw, ms
         expd.plan_create(spec)
     assert ei.value.status == expd.ERR_INVALID_ARG
     assert msg in str(ei.value)
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(a=1j, c=2j, complex_state=True, precision=1), "float64"),
+    (dict(a=1j, complex_state=True, nonlin=1), "linear"),
+])
+def test_plan_create_rejects_unbuilt_complex_state_cases_without_touching_the_gpu(expd, kw, msg):
+    with pytest.raises(expd.ExpdError) as ei:
+        expd.plan_create(_spec(expd, **kw))
+    assert ei.value.status == expd.ERR_UNSUPPORTED and msg in str(ei.value)
 
 
 def test_every_entry_point_has_declared_argument_types(expd):
