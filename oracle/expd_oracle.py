@@ -17,6 +17,8 @@ Parabolic PDEs" (arXiv 2603.04350) computes:
   * the preconditioned Richardson iteration (Eq. (3.2), (4.4)) and its lagged
     nonlinear form (Eqs. (7.3)-(7.4));
   * left-preconditioned GMRES (Sec. 3.2, Theorem 3.3) and BiCGStab;
+  * periodic (spectral), Dirichlet (DST-I) and Neumann (cell-centred, DCT-II)
+    grids, the Neumann one for the Allen-Cahn experiment of Sec. 7;
   * complex states for complex a and c, the Schrodinger equation of Sec. 7
     (a = i, c = 2i or 200i): complex arithmetic throughout, GMRES with the
     Hermitian inner product and complex Givens rotations;
@@ -29,7 +31,9 @@ which real GMRES on the real and imaginary parts does not reproduce); the source
 beta_s*dt*N(u_n) (implicit, integrating factor); the startup values
 u_1..u_{s-1} come from the IF-BDF_j ramp j = 1..s-1; C_j^alpha = (C_0^alpha)^(j+1)
 (the printed entry lists of Sec. 5 are garbled); the periodic L_h is the
-spectral Laplacian with the Nyquist mode's symbol -a*(pi*n/L)^2.
+spectral Laplacian with the Nyquist mode's symbol -a*(pi*n/L)^2; the Neumann
+L_h is the 3-point Laplacian on cell centres with mirrored ghost values (the
+paper names the boundary condition, not its discretisation).
 
 Parity status: every function here is pinned by tests/test_oracle_pins.py
 against closed forms, the paper's printed coefficients and spectra, and dense
@@ -49,6 +53,7 @@ import scipy.linalg
 
 PERIODIC = "periodic"
 DIRICHLET = "dirichlet"
+NEUMANN = "neumann"
 
 
 # ---------------------------------------------------------------------------
@@ -56,7 +61,7 @@ DIRICHLET = "dirichlet"
 # ---------------------------------------------------------------------------
 @dataclass(frozen=True)
 class Spec:
-    bc: str                      # "periodic" | "dirichlet"
+    bc: str                      # "periodic" | "dirichlet" | "neumann"
     n: Tuple[int, ...]           # grid points per dimension
     length: Tuple[float, ...]    # domain length per dimension
     a: complex                   # L = a*Lap - c   (Eq. (1.2)); a = i, c = 2i: Schrodinger (Sec. 7)
@@ -136,6 +141,11 @@ def spatial_eigenvalues(sp: Spec) -> np.ndarray:
     Dirichlet: 3-point (1D) / 5-point (2D) finite differences on n interior
     points, h = L/(n+1): mu = -a*sum_d (4/h^2) sin^2(pi k_d h/(2 L_d)) - c,
     k_d = 1..n, eigenvectors sin(pi k_d x/L_d) (the DST-I basis).
+    Neumann (the Allen-Cahn experiment of Sec. 7 with du/dn = 0): the same
+    finite differences on the n cell centres x_j = (j - 1/2) h, h = L/n, with
+    the boundary condition imposed by mirroring (u_0 = u_1, u_{n+1} = u_n):
+    mu = -a*sum_d (4/h^2) sin^2(pi k_d/(2 n_d)) - c, k_d = 0..n-1,
+    eigenvectors cos(pi k_d (j - 1/2)/n_d) (the DCT-II basis).
     Advection (periodic, the advection-diffusion operator of Sec. 7 and
     Remark 3.7): the spectral first derivative adds -i sum_d b_d (2 pi k_d/L_d)
     with the Nyquist wavenumber's first-derivative symbol 0 (so real fields
@@ -149,6 +159,10 @@ def spatial_eigenvalues(sp: Spec) -> np.ndarray:
             if n % 2 == 0:
                 k1[n // 2] = 0.0
             adv.append(2.0 * np.pi * k1 / L * (sp.b[d] if d < len(sp.b) else 0.0))
+        elif sp.bc == NEUMANN:
+            h = L / n
+            k = np.arange(n)
+            parts.append(-(4.0 / h**2) * np.sin(np.pi * k / (2.0 * n)) ** 2)
         else:
             h = L / (n + 1)
             k = np.arange(1, n + 1)
@@ -168,10 +182,16 @@ def _axes(sp: Spec, x: np.ndarray):
 
 def to_eigen(sp: Spec, u: np.ndarray) -> np.ndarray:
     """Coefficients of u in L_h's eigenbasis (last ndim axes): unnormalised
-    DFT for periodic grids, orthonormal DST-I for Dirichlet grids."""
+    DFT for periodic grids, orthonormal DST-I for Dirichlet grids, orthonormal
+    DCT-II for Neumann grids."""
     ax = _axes(sp, u)
     if sp.bc == PERIODIC:
         return np.fft.fftn(u, axes=ax)
+    if sp.bc == NEUMANN:
+        if np.iscomplexobj(u):
+            return (scipy.fft.dctn(u.real, type=2, axes=ax, norm="ortho")
+                    + 1j * scipy.fft.dctn(u.imag, type=2, axes=ax, norm="ortho"))
+        return scipy.fft.dctn(u, type=2, axes=ax, norm="ortho")
     if np.iscomplexobj(u):
         return (scipy.fft.dstn(u.real, type=1, axes=ax, norm="ortho")
                 + 1j * scipy.fft.dstn(u.imag, type=1, axes=ax, norm="ortho"))
@@ -183,6 +203,11 @@ def from_eigen(sp: Spec, uh: np.ndarray) -> np.ndarray:
     ax = _axes(sp, uh)
     if sp.bc == PERIODIC:
         return np.fft.ifftn(uh, axes=ax)
+    if sp.bc == NEUMANN:
+        if np.iscomplexobj(uh):
+            return (scipy.fft.idctn(uh.real, type=2, axes=ax, norm="ortho")
+                    + 1j * scipy.fft.idctn(uh.imag, type=2, axes=ax, norm="ortho"))
+        return scipy.fft.idctn(uh, type=2, axes=ax, norm="ortho")
     if np.iscomplexobj(uh):
         return (scipy.fft.idstn(uh.real, type=1, axes=ax, norm="ortho")
                 + 1j * scipy.fft.idstn(uh.imag, type=1, axes=ax, norm="ortho"))
@@ -644,7 +669,10 @@ def dense_laplacian_1d(bc: str, n: int, L: float) -> np.ndarray:
     """Periodic: the spectral second-derivative matrix of the periodic sinc
     interpolant (even n): -pi^2/(3h^2) - 1/6 on the diagonal and
     -(-1)^j / (2 sin^2(j h/2)) off it, for the grid spacing h = 2 pi/n, scaled
-    to length L.  Dirichlet: tridiag(1, -2, 1)/h^2 with h = L/(n+1)."""
+    to length L.  Dirichlet: tridiag(1, -2, 1)/h^2 with h = L/(n+1).  Neumann:
+    the same on n cell centres, h = L/n, with the mirrored ghost values
+    u_0 = u_1 and u_{n+1} = u_n folding the outer couplings onto the first
+    and last diagonal entries (-1/h^2)."""
     if bc == PERIODIC:
         if n % 2:
             raise ValueError("even n only")
@@ -654,9 +682,12 @@ def dense_laplacian_1d(bc: str, n: int, L: float) -> np.ndarray:
         j = np.arange(1, n)
         col[1:] = -((-1.0) ** j) / (2.0 * np.sin(j * h / 2.0) ** 2)
         return scipy.linalg.toeplitz(col) * (2.0 * np.pi / L) ** 2
-    h = L / (n + 1)
-    return (np.diag(-2.0 * np.ones(n)) + np.diag(np.ones(n - 1), 1)
-            + np.diag(np.ones(n - 1), -1)) / h**2
+    h = L / n if bc == NEUMANN else L / (n + 1)
+    T = np.diag(-2.0 * np.ones(n)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1)
+    if bc == NEUMANN:
+        T[0, 0] += 1.0
+        T[-1, -1] += 1.0
+    return T / h**2
 
 
 def dense_derivative_1d(n: int, L: float) -> np.ndarray:

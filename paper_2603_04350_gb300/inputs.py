@@ -21,6 +21,7 @@ import numpy as np
 
 PERIODIC = "periodic"
 DIRICHLET = "dirichlet"
+NEUMANN = "neumann"
 NL_NONE = "none"
 NL_ALLEN_CAHN = "allen_cahn"
 
@@ -29,9 +30,11 @@ NL_ALLEN_CAHN = "allen_cahn"
 class Problem:
     """Parameters of one all-at-once solve.
 
-    n       grid points per dimension (periodic) or interior points (Dirichlet)
+    n       grid points per dimension (periodic), interior points (Dirichlet)
+            or cells (Neumann)
     length  domain length per dimension; periodic grid x_j = j*L/n,
-            Dirichlet grid x_j = j*L/(n+1), j = 1..n
+            Dirichlet grid x_j = j*L/(n+1), j = 1..n, Neumann cell centres
+            x_j = (j - 1/2) L/n
     a, c    L = a*Lap - c  (Sec. 1, Eq. (1.2)); b adds advection -b.grad; a and c
             may be complex (the Schrodinger equation of Sec. 7: a = i, c = 2i
             or 200i), which needs complex_state
@@ -135,6 +138,8 @@ def grid_coords(p: Problem):
     for n, L in zip(p.n, p.length):
         if p.bc == PERIODIC:
             out.append(np.arange(n) * (L / n))
+        elif p.bc == NEUMANN:
+            out.append((np.arange(n) + 0.5) * (L / n))       # cell centres
         else:
             out.append(np.arange(1, n + 1) * (L / (n + 1)))
     return out

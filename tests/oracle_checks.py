@@ -576,3 +576,54 @@ def check_complex_bicgstab_vs_dense(sp, seed=25):
     f = rng_complex(sp, seed + 1, (sp.Nt,))
     res = O.bicgstab(sp, u0, f, tol=1e-13, max_iter=100)
     return O.rel_error(res.U[1:], O.dense_solve(sp, u0, f)[1:]), res
+
+
+# --- Neumann grids (DCT-II eigenbasis; the Allen-Cahn experiment of Sec. 7) --
+def neu_spec(n=(8,), a=0.3, c=0.1, nonlin="none", Nt=9, order=1, alpha=0.05, dt=0.05):
+    return O.Spec("neumann", tuple(n), tuple(1.0 for _ in n), a, c, nonlin, dt, Nt, alpha, order)
+
+
+def check_neumann_mass(n=(12,), Nt=10, order=2):
+    """With c = 0 and no source the mirrored boundary lets nothing out: the
+    cell sum sum_j u_n,j (the k = 0 mode, symbol 0) is conserved.  Max
+    relative drift."""
+    sp = neu_spec(n, a=0.7, c=0.0, Nt=Nt, order=order, dt=0.01)
+    u0 = np.random.default_rng(30).uniform(-1, 1, sp.n) + 0.3
+    U = O.sequential_solve(sp, u0)
+    m = U.reshape(U.shape[0], -1).sum(1)
+    return float(np.abs(m / m[0] - 1.0).max())
+
+
+def check_neumann_cosine_mode(n=16, k=2, Nt=8, a=0.7, c=0.2, dt=0.01):
+    """cos(k pi x_j) at the cell centres is an eigenvector of the Neumann
+    3-point Laplacian with eigenvalue -(4/h^2) sin^2(k pi/(2n)); the first-order
+    scheme multiplies it by exp(dt mu) per step.  Max deviation."""
+    sp = neu_spec((n,), a, c, Nt=Nt, order=1, dt=dt)
+    x = (np.arange(n) + 0.5) / n
+    u0 = np.cos(k * np.pi * x)
+    h = 1.0 / n
+    mu = -a * (4.0 / h**2) * math.sin(k * math.pi / (2 * n)) ** 2 - c
+    want = np.array([math.exp(j * dt * mu) * u0 for j in range(Nt + 1)])
+    return np.abs(O.sequential_solve(sp, u0) - want).max()
+
+
+def neumann_allen_cahn_errors(order, n=256, T=0.1, steps=(25, 50, 100, 200), eps=0.01):
+    """The Neumann Allen-Cahn problem of Sec. 7: u_t = eps^2 u_xx - (u^3 - u)
+    + s_f on (0, 1), du/dn = 0, eps = 0.01, the source chosen so that
+    u = 0.5 e^{-t} cos(2 pi x) is the exact solution
+    (s_f = u (4 pi^2 eps^2 - 2) + u^3); Sec. 7's error of the sequential
+    IF-BDF-s solution at each step count."""
+    out = []
+    for Nt in steps:
+        dt = T / Nt
+        sp = O.Spec("neumann", (n,), (1.0,), eps**2, 0.0, "allen_cahn", dt, Nt, 1e-3, order)
+        x = (np.arange(n) + 0.5) / n
+
+        def ue(t):
+            return 0.5 * np.exp(-t) * np.cos(2 * np.pi * x)
+        f = np.array([ue((k + 1) * dt) * (4 * np.pi**2 * eps**2 - 2) + ue((k + 1) * dt) ** 3
+                      for k in range(Nt)])
+        U = O.sequential_solve(sp, ue(0.0), f)
+        ex = np.array([ue(k * dt) for k in range(Nt + 1)])
+        out.append(O.rel_error(U[1:], ex[1:]))
+    return out

@@ -417,3 +417,57 @@ def test_schrodinger_2d_gmres_three_iterations(Nt):
     from paper_2603_04350_gb300 import inputs as I
     errs = C.schrodinger_gmres_errors(I.SCHRODINGER_2D.with_(Nt=Nt), 3)
     assert errs[1] > 1e-10 and errs[2] < 1e-10
+
+
+# ------------------------------------------------------- Neumann grids (Sec. 7) --
+NEU_SPECS = [
+    C.neu_spec((8,), order=1),
+    C.neu_spec((5, 6), order=2),
+    C.neu_spec((7,), order=6, Nt=14, dt=0.02),
+    C.neu_spec((6, 5), a=0.01, c=0.0, nonlin="allen_cahn", order=2, dt=0.02),
+]
+NEU_IDS = ["n1_s1", "n2_s2", "n1_s6", "n2_ac_s2"]
+
+
+@pytest.mark.parametrize("sp", NEU_SPECS, ids=NEU_IDS)
+def test_neumann_A_matches_dense_expm(sp):
+    assert C.check_A_vs_dense(sp) < 1e-12
+
+
+@pytest.mark.parametrize("sp", NEU_SPECS, ids=NEU_IDS)
+def test_neumann_precond_and_R_match_dense(sp):
+    assert C.check_precond_vs_dense(sp) < 1e-11
+    assert C.check_apply_R_vs_dense(sp) < 1e-12
+
+
+@pytest.mark.parametrize("sp", NEU_SPECS, ids=NEU_IDS)
+def test_neumann_sequential_matches_dense(sp):
+    assert C.check_sequential_vs_dense(sp) < 1e-11
+
+
+def test_neumann_mass_conservation():
+    assert C.check_neumann_mass() < 1e-13
+
+
+def test_neumann_cosine_mode_closed_form():
+    assert C.check_neumann_cosine_mode() < 1e-13
+
+
+@pytest.mark.parametrize("order,ratio", [(1, 2.0), (2, 4.0)])
+def test_neumann_allen_cahn_exact_solution_order(order, ratio):
+    # Sec. 7's Neumann Allen-Cahn problem with a manufactured exact solution:
+    # halving dt divides the error by 2 (s = 1) and about 4 (s = 2)
+    errs = C.neumann_allen_cahn_errors(order, steps=(25, 50, 100))
+    rates = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert errs[0] < 3e-4
+    assert all(abs(r - ratio) < 0.15 * ratio for r in rates)
+
+
+def test_neumann_gmres_and_richardson_reach_dense():
+    sp = C.neu_spec((5, 4), order=2, Nt=10, alpha=0.05)
+    rng = np.random.default_rng(31)
+    u0 = rng.standard_normal(sp.n)
+    f = rng.standard_normal((sp.Nt,) + sp.n)
+    ref = O.dense_solve(sp, u0, f)[1:]
+    assert O.rel_error(O.gmres(sp, u0, f, tol=1e-13).U[1:], ref) < 1e-11
+    assert O.rel_error(O.richardson(sp, u0, f, max_iter=60, tol=1e-14).U[1:], ref) < 1e-11

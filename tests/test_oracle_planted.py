@@ -260,3 +260,16 @@ def test_planted_conjugated_symbol_is_caught(monkeypatch):
         return np.conj(orig(sp))
     patch(monkeypatch, "spatial_eigenvalues", spatial_eigenvalues)
     assert C.check_schrodinger_sine_mode() > 1e-3
+
+
+def test_planted_neumann_dirichlet_index_is_caught(monkeypatch):
+    # the Neumann symbol evaluated at k + 1 (the Dirichlet sine index)
+    _patched_source(monkeypatch, "spatial_eigenvalues", "k = np.arange(n)\n", "k = np.arange(1, n + 1)\n")
+    assert C.check_A_vs_dense(C.neu_spec((8,))) > 1e-3
+
+
+def test_planted_neumann_wrong_cosine_transform_is_caught(monkeypatch):
+    # the DCT-I in place of the DCT-II (vertex instead of cell-centred basis)
+    _patched_source(monkeypatch, "to_eigen", 'return scipy.fft.dctn(u, type=2, axes=ax, norm="ortho")',
+                    'return scipy.fft.dctn(u, type=1, axes=ax, norm="ortho")')
+    assert C.check_A_vs_dense(C.neu_spec((8,))) > 1e-3
