@@ -66,7 +66,13 @@ typedef enum {
     EXPD_ERR_CANCELLED = 8      /* expd_plan_cancel stopped the call                    */
 } expd_status;
 
-enum { EXPD_BC_PERIODIC = 0, EXPD_BC_DIRICHLET = 1 };
+/* Boundary conditions and the eigenbasis of L_h they give (Sec. 2 after
+ * Eq. (2.7); the Neumann Allen-Cahn experiment of Sec. 7):
+ *  PERIODIC   n points x_j = j L/n, spectral Laplacian, the DFT;
+ *  DIRICHLET  n interior points x_j = j L/(n+1), 3/5-point Laplacian, the DST-I;
+ *  NEUMANN    n cell centres x_j = (j - 1/2) L/n, 3/5-point Laplacian with
+ *             mirrored ghost values (zero normal derivative), the DCT-II. */
+enum { EXPD_BC_PERIODIC = 0, EXPD_BC_DIRICHLET = 1, EXPD_BC_NEUMANN = 2 };
 enum { EXPD_NL_NONE = 0, EXPD_NL_ALLEN_CAHN = 1 };      /* N(u) = 0 or u - u^3          */
 enum { EXPD_PREC_FP64 = 0, EXPD_PREC_MIXED = 1 };
 enum { EXPD_STARTUP_RAMP = 0, EXPD_STARTUP_GIVEN = 1 };

@@ -126,8 +126,26 @@ size_t pinned_words(const expd_plan_s* p) { return 2 * (size_t)p->Ns + EXPD_CTL_
 // Spatial-transform scratch: one complex value per mode and slice; a complex
 // state on a Dirichlet grid splits chunks of max(1, Ns/4) slices into real
 // and imaginary parts and needs 8 M doubles per slice of a chunk.
+// Eigenvalue of the 3-point (1D) / 5-point (2D) Laplacian on mode (kx, ky):
+// Dirichlet -(4/h^2) sin^2(pi (k+1) h/(2L)) with h = L/(n+1) (sine modes
+// k + 1 = 1..n); Neumann -(4/h^2) sin^2(pi k/(2n)) with h = L/n (cosine modes
+// k = 0..n-1 on the cell centres).
+double fd_laplacian_symbol(const expd_plan_s* p, int kx, int ky) {
+    auto one = [&](int k, int n, double L) {
+        if (p->bc == EXPD_BC_NEUMANN) {
+            const double h = L / n, sn = sin(M_PI * k / (2.0 * n));
+            return -(4.0 / (h * h)) * sn * sn;
+        }
+        const double h = L / (n + 1), sn = sin(M_PI * (k + 1) * h / (2.0 * L));
+        return -(4.0 / (h * h)) * sn * sn;
+    };
+    double lap = one(kx, p->NX, p->LX);
+    if (p->ndim == 2) lap += one(ky, p->NY, p->LY);
+    return lap;
+}
+
 size_t work64_bytes(const expd_plan_s* p) {
-    const size_t slices = (p->cplx && p->bc == EXPD_BC_DIRICHLET) ? (size_t)std::max(p->Ns, 4) : (size_t)p->Ns;
+    const size_t slices = (p->cplx && p->bc != EXPD_BC_PERIODIC) ? (size_t)std::max(p->Ns, 4) : (size_t)p->Ns;
     return slices * p->NY * p->KX * sizeof(double2);
 }
 
@@ -171,7 +189,7 @@ expd_status upload_vec(expd_plan p, T** dptr, const std::vector<T>& h, const cha
 
 void free_plan(expd_plan p) {
     if (!p) return;
-    void* bufs[] = {p->E,    p->PHI64, p->PHI32, p->PHIdd, p->C64,  p->C32, p->Cdd, p->Wxdd, p->Wydd, p->gamdd, p->oscdd, p->Wx64, p->Wx32,   p->Wy64,    p->Wy32,    p->Sx,        p->Sy, p->Dtx, p->Dty,
+    void* bufs[] = {p->E,    p->PHI64, p->PHI32, p->PHIdd, p->C64,  p->C32, p->Cdd, p->Wxdd, p->Wydd, p->gamdd, p->oscdd, p->Wx64, p->Wx32,   p->Wy64,    p->Wy32,    p->Sx,        p->Sy, p->SxT, p->SyT, p->Dtx, p->Dty,
                     p->Uh,   p->Fh,   p->Sh,     p->fh,      p->NL64,    p->NL32,      p->work64,
                     p->work32, p->startphys, p->partial, p->redout, p->stage, p->gm, p->U32, p->F32,
                     p->tc_S, p->tc_pack, p->tc_ex};
@@ -512,14 +530,16 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
                              double alpha, const expd_scheme* scheme) {
     if (!grid || !op || !scheme) return expd_fail(EXPD_ERR_INVALID_ARG, "grid, operator and scheme are required");
     if (grid->ndim != 1 && grid->ndim != 2) return expd_fail(EXPD_ERR_INVALID_ARG, "ndim must be 1 or 2");
-    if (grid->bc != EXPD_BC_PERIODIC && grid->bc != EXPD_BC_DIRICHLET)
-        return expd_fail(EXPD_ERR_INVALID_ARG, "bc must be EXPD_BC_PERIODIC or EXPD_BC_DIRICHLET");
+    if (grid->bc != EXPD_BC_PERIODIC && grid->bc != EXPD_BC_DIRICHLET && grid->bc != EXPD_BC_NEUMANN)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "bc must be EXPD_BC_PERIODIC, EXPD_BC_DIRICHLET or EXPD_BC_NEUMANN");
     for (int d = 0; d < grid->ndim; ++d) {
         const int n = grid->n[d];
         if (grid->bc == EXPD_BC_PERIODIC && (!is_pow2(n) || n < 8 || n > EXPD_MAX_PERIODIC_N))
             return expd_fail(EXPD_ERR_INVALID_ARG, "periodic grid sizes must be powers of two in [8, 4096]");
         if (grid->bc == EXPD_BC_DIRICHLET && (n < 2 || n > EXPD_MAX_DIRICHLET_N))
             return expd_fail(EXPD_ERR_INVALID_ARG, "Dirichlet grid sizes must be in [2, 4096]");
+        if (grid->bc == EXPD_BC_NEUMANN && (n < 2 || n > EXPD_MAX_DIRICHLET_N))
+            return expd_fail(EXPD_ERR_INVALID_ARG, "Neumann grid sizes must be in [2, 4096]");
         if (!(grid->length[d] > 0) || !isfinite(grid->length[d]))
             return expd_fail(EXPD_ERR_INVALID_ARG, "domain lengths must be positive");
     }
@@ -640,8 +660,8 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     // a real state on a Dirichlet grid has real sine coefficients; a complex
     // state keeps every mode (the full spectrum on a periodic grid: no
     // conjugate symmetry halves it)
-    p->realcol = p->bc == EXPD_BC_DIRICHLET && !p->cplx;
-    p->KX = (p->bc == EXPD_BC_DIRICHLET || p->cplx) ? p->NX : p->NX / 2 + 1;
+    p->realcol = p->bc != EXPD_BC_PERIODIC && !p->cplx;
+    p->KX = (p->bc != EXPD_BC_PERIODIC || p->cplx) ? p->NX : p->NX / 2 + 1;
     p->Mcol = (long long)p->NY * p->KX;
     p->esz = p->realcol ? sizeof(double) : sizeof(double2);
     if (p->bc == EXPD_BC_DIRICHLET) {
@@ -1036,14 +1056,7 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
                     if (2 * ky != p->NY) nu -= p->by * wy;
                 }
             } else {
-                const double hx = p->LX / (p->NX + 1);
-                const double sx = sin(M_PI * (kx + 1) * hx / (2.0 * p->LX));
-                lap -= (4.0 / (hx * hx)) * sx * sx;
-                if (p->ndim == 2) {
-                    const double hy = p->LY / (p->NY + 1);
-                    const double sy = sin(M_PI * (ky + 1) * hy / (2.0 * p->LY));
-                    lap -= (4.0 / (hy * hy)) * sy * sy;
-                }
+                lap = fd_laplacian_symbol(p, kx, ky);
             }
             const double mu = p->a * lap - p->c;
             nu += p->a_im * lap;
@@ -1099,14 +1112,7 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
                     mu -= p->a * wy * wy;
                 }
             } else {
-                const double hx = p->LX / (p->NX + 1);
-                const double sx = sin(M_PI * (kx + 1) * hx / (2.0 * p->LX));
-                mu -= p->a * (4.0 / (hx * hx)) * sx * sx;
-                if (p->ndim == 2) {
-                    const double hy = p->LY / (p->NY + 1);
-                    const double sy = sin(M_PI * (ky + 1) * hy / (2.0 * p->LY));
-                    mu -= p->a * (4.0 / (hy * hy)) * sy * sy;
-                }
+                mu += p->a * fd_laplacian_symbol(p, kx, ky);
             }
             const double z = dt * mu;
             ph[m] = dt * (z == 0.0 ? 1.0 : std::expm1(z) / z);
@@ -1199,6 +1205,29 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
             st = upload_vec(p, d == 0 ? &p->Sx : &p->Sy, S, "DST matrix", s);
         }
         if (st == EXPD_OK && p->tc_dst) st = dst_tc_setup(p, s);
+    } else if (st == EXPD_OK && p->bc == EXPD_BC_NEUMANN) {
+        // orthonormal DCT-II C[k][j] = w_k cos(pi k (2j + 1)/(2n)), w_0 = sqrt(1/n),
+        // w_k = sqrt(2/n): forward Y = C_y X C_x^T, inverse X = C_y^T Y C_x.
+        // Sx = C_x^T and SxT = C_x are the right operands of the two
+        // directions, Sy = C_y and SyT = C_y^T the left ones
+        for (int d = 0; d < p->ndim && st == EXPD_OK; ++d) {
+            const int n = d == 0 ? p->NX : p->NY;
+            std::vector<double> Cm((size_t)n * n), Ct((size_t)n * n);
+            for (int k = 0; k < n; ++k)
+                for (int j = 0; j < n; ++j) {
+                    const long long r = ((long long)k * (2 * j + 1)) % (4LL * n);  // angle pi r/(2n)
+                    const double v = sqrt((k == 0 ? 1.0 : 2.0) / n) * cos(M_PI * (double)r / (2.0 * n));
+                    Cm[(size_t)k * n + j] = v;
+                    Ct[(size_t)j * n + k] = v;
+                }
+            if (d == 0) {
+                st = upload_vec(p, &p->Sx, Ct, "DCT matrix", s);
+                if (st == EXPD_OK) st = upload_vec(p, &p->SxT, Cm, "DCT matrix (inverse)", s);
+            } else {
+                st = upload_vec(p, &p->Sy, Cm, "DCT matrix", s);
+                if (st == EXPD_OK) st = upload_vec(p, &p->SyT, Ct, "DCT matrix (inverse)", s);
+            }
+        }
     }
     // ---- state and workspace ----
     const size_t vec = (size_t)p->Ns * p->Mcol * p->esz;
@@ -1284,8 +1313,9 @@ expd_status expd_plan_footprint_bytes(const expd_grid* grid, const expd_operator
         b += (size_t)(p->NX + 1) * 16;
         if (p->ndim == 2) b += (size_t)(p->NY + 1) * 16;
     } else {
-        b += (size_t)p->NX * p->NX * 8;
-        if (p->ndim == 2) b += (size_t)p->NY * p->NY * 8;
+        const size_t mats = p->bc == EXPD_BC_NEUMANN ? 2 : 1;                // DCT: forward and inverse
+        b += mats * (size_t)p->NX * p->NX * 8;
+        if (p->ndim == 2) b += mats * (size_t)p->NY * p->NY * 8;
         if (p->tc_dst) b += dst_tc_bytes(p);                                // tensor-core DST digits
     }
     b += 2 * vec + ord * Mcol * p->esz + ord * (size_t)p->Mp * 8;            // Uh, Fh, Sh, startphys

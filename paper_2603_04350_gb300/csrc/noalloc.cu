@@ -218,6 +218,8 @@ extern "C" expd_status expd_precond_apply_noalloc(const expd_grid* grid, const e
     expd_status st = plan_init_fields(p, grid, op, dt, Nt, alpha, scheme);
     if (st != EXPD_OK) return st;
     if (p->cplx) return expd_fail(EXPD_ERR_UNSUPPORTED, "the no-allocation entry point takes real states");
+    if (p->bc == EXPD_BC_NEUMANN)
+        return expd_fail(EXPD_ERR_UNSUPPORTED, "the no-allocation entry point takes periodic and Dirichlet grids");
     if (p->adv) return expd_fail(EXPD_ERR_UNSUPPORTED, "the no-allocation entry point has no advection tables");
     p->fast_dst = 0;  // Dirichlet transforms use the dense sine matrices built below
     p->tc_dst = 0;    // (in float64: the tensor-core digits would need device memory of their own)

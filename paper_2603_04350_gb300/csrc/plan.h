@@ -101,6 +101,8 @@ struct expd_plan_s {
     void* oscdd = nullptr;     // [Ns] output scale as double-float
     double* Sx = nullptr;      // Dirichlet: [NX][NX] orthonormal DST-I matrix (dense path)
     double* Sy = nullptr;      // Dirichlet: [NY][NY]
+    double* SxT = nullptr;     // Neumann: [NX][NX] inverse-transform operand (Sx is the forward one)
+    double* SyT = nullptr;     // Neumann: [NY][NY]
     int fast_dst = 0;          // Dirichlet with n + 1 a power of two: FFT-based sine transforms
     double2* Dtx = nullptr;    // fast DST twiddles exp(-2 pi i k / (2 (NX + 1))), k <= NX
     double2* Dty = nullptr;    // the same for NY

@@ -1123,12 +1123,24 @@ expd_status transpose(expd_plan p, const double* in, double* out, int R, int C, 
     return EXPD_OK;
 }
 
+// The real eigenbasis transforms of Dirichlet and Neumann grids.
 // Orthonormal 2D DST-I: Y = Sy X Sx (S symmetric and its own inverse).  With
 // n + 1 a power of two in every direction: fast sine transforms along x, a
 // transpose, along y, and back; otherwise the dense products (on the tensor
-// cores when the plan allows, dst_tc.cu).
-expd_status dst2(expd_plan p, const double* X, double* Y, int ns, double* tmp, cudaStream_t s) {
+// cores when the plan allows, dst_tc.cu).  Neumann grids: the orthonormal
+// DCT-II by the dense products, forward (dir < 0) Y = C_y X C_x^T with the
+// operands Sx = C_x^T and Sy = C_y, inverse X = C_y^T Y C_x with SxT = C_x
+// and SyT = C_y^T.
+expd_status dst2(expd_plan p, const double* X, double* Y, int ns, double* tmp, cudaStream_t s, int dir = -1) {
     const int NX = p->NX, NY = p->NY;
+    if (p->bc == EXPD_BC_NEUMANN) {
+        const double* Bx = dir < 0 ? p->Sx : p->SxT;
+        const double* Ay = dir < 0 ? p->Sy : p->SyT;
+        if (p->ndim == 1) return dgemm(p, X, NX, (long long)NX, Bx, NX, 0, Y, NX, 0, ns, NX, NX, 1, s);
+        expd_status st = dgemm(p, X, NX, (long long)NX, Bx, NX, 0, tmp, NX, 0, ns * NY, NX, NX, 1, s);
+        if (st != EXPD_OK) return st;
+        return dgemm(p, Ay, NY, 0, tmp, NX, (long long)NY * NX, Y, NX, (long long)NY * NX, NY, NX, NY, ns, s);
+    }
     if (p->fast_dst) {
         if (p->ndim == 1) return dst_rows(p, X, Y, ns, NX, p->Dtx, s);
         double* w1 = tmp;
@@ -1253,7 +1265,7 @@ expd_status spatial_complex64(expd_plan p, const double* in, double* out, int ns
                                                         M, total);
             EXPD_CUDA_TRY(cudaGetLastError());
         }
-        expd_status st = dst2(p, P, Q, 2 * ns, tmp, s);
+        expd_status st = dst2(p, P, Q, 2 * ns, tmp, s, dir);
         if (st != EXPD_OK) return st;
         {
             KProf kp(p, s, EXPD_K_POINTWISE, 32.0 * total, 0.0);
@@ -1275,9 +1287,9 @@ expd_status spatial_forward64(expd_plan p, const double* phys, void* eig, int ns
         const int ns = std::min(chunk, nslices - b0);
         const double* x = phys + (long long)b0 * p->M;
         expd_status st;
-        if (p->bc == EXPD_BC_DIRICHLET) {
+        if (p->bc != EXPD_BC_PERIODIC) {
             double* y = static_cast<double*>(eig) + (long long)b0 * p->Mcol;
-            st = dst2(p, x, y, ns, static_cast<double*>(p->work64), s);
+            st = dst2(p, x, y, ns, static_cast<double*>(p->work64), s, -1);
         } else {
             double2* y = static_cast<double2*>(eig) + (long long)b0 * p->Mcol;
             if (p->ndim == 1) {
@@ -1300,9 +1312,9 @@ expd_status spatial_inverse64(expd_plan p, const void* eig, double* phys, int ns
         const int ns = std::min(chunk, nslices - b0);
         double* x = phys + (long long)b0 * p->M;
         expd_status st;
-        if (p->bc == EXPD_BC_DIRICHLET) {
+        if (p->bc != EXPD_BC_PERIODIC) {
             const double* y = static_cast<const double*>(eig) + (long long)b0 * p->Mcol;
-            st = dst2(p, y, x, ns, static_cast<double*>(p->work64), s);
+            st = dst2(p, y, x, ns, static_cast<double*>(p->work64), s, +1);
         } else {
             const double2* y = static_cast<const double2*>(eig) + (long long)b0 * p->Mcol;
             const double sx = 1.0 / (p->NX / 2);
@@ -1335,8 +1347,8 @@ expd_status nonlinear_eval(expd_plan p, const void* Uh, void* out, int f32, cuda
         if (st == EXPD_OK) st = launch_col<float, float2, float2>(p, w, o, Ns, -1, 1.0f, s);
         return st;
     }
-    if (p->bc == EXPD_BC_DIRICHLET) {
-        // float64 only: inverse DST, N(u), forward DST
+    if (p->bc != EXPD_BC_PERIODIC) {
+        // float64 only: inverse sine / cosine transform, N(u), forward transform
         double* phys = static_cast<double*>(p->work64) + (long long)Ns * p->M;
         expd_status st = spatial_inverse64(p, Uh, phys, Ns, s);
         if (st != EXPD_OK) return st;

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libexpd.so")
 
 (OK, ERR_INVALID_ARG, ERR_OOM, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT,
  ERR_CANCELLED) = range(9)
-BC_PERIODIC, BC_DIRICHLET = 0, 1
+BC_PERIODIC, BC_DIRICHLET, BC_NEUMANN = 0, 1, 2
 NL_NONE, NL_ALLEN_CAHN = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 STARTUP_RAMP, STARTUP_GIVEN = 0, 1
@@ -325,7 +325,8 @@ def spec_from_problem(p, precision: int = PREC_FP64, max_iter: int = 100, tol: O
                       guess: int = GUESS_LINEAR, kernel_flags: int = 0, nl_form: Optional[int] = None,
                       time_limit_ms: float = 0.0) -> PlanSpec:
     """PlanSpec from a paper_2603_04350_gb300.inputs.Problem."""
-    return PlanSpec(bc=BC_PERIODIC if p.bc == "periodic" else BC_DIRICHLET, n=tuple(p.n), length=tuple(p.length),
+    bc = {"periodic": BC_PERIODIC, "dirichlet": BC_DIRICHLET, "neumann": BC_NEUMANN}[p.bc]
+    return PlanSpec(bc=bc, n=tuple(p.n), length=tuple(p.length),
                     a=p.a, c=p.c, nonlin=NL_ALLEN_CAHN if p.nonlin == "allen_cahn" else NL_NONE, dt=p.dt,
                     Nt=p.Nt, alpha=p.alpha, order=p.order, precision=precision, max_iter=max_iter,
                     tol=p.tol if tol is None else tol, gmres_restart=gmres_restart, startup=startup,
