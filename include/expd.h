@@ -168,7 +168,9 @@ typedef struct {
  *             takes the shared-memory time kernel where the register kernel
  *             would run, EXPD_KF_FFT_RADIX4 the radix-4 shared-memory FFTs
  *             instead of the four-step register FFTs, EXPD_KF_DST_FP64 the
- *             float64 sine-transform products instead of the tensor cores.
+ *             float64 sine-transform products instead of the tensor cores,
+ *             EXPD_KF_DST_N64 tensor-core sine-transform tiles of 128 x 64
+ *             outputs instead of 128 x 128 (twice the tiles: small grids).
  *             The environment variables EXPD_TIME_KERNEL=smem,
  *             EXPD_FFT_KERNEL=radix4 and EXPD_DST_TC=0, read at plan
  *             creation, set the same flags.  0 = the default kernels.
@@ -183,7 +185,7 @@ typedef struct {
  *             iterate is returned); 0 = none.                              */
 enum { EXPD_JAC_LAGGED = 0, EXPD_JAC_MEAN_U0 = 1 };
 enum { EXPD_GUESS_LINEAR = 0, EXPD_GUESS_ZERO = 1 };
-enum { EXPD_KF_TIME_SMEM = 1, EXPD_KF_FFT_RADIX4 = 2, EXPD_KF_DST_FP64 = 4 };
+enum { EXPD_KF_TIME_SMEM = 1, EXPD_KF_FFT_RADIX4 = 2, EXPD_KF_DST_FP64 = 4, EXPD_KF_DST_N64 = 8 };
 enum { EXPD_NLF_IF = 0, EXPD_NLF_ETD1 = 1 };
 typedef struct {
     int order;

@@ -9,8 +9,10 @@ computing the same result (the GPU tests check each pair):
         on the mixed path: register kernel (default) or the shared-memory
         kernel (EXPD_KF_TIME_SMEM)
   dst   dense sine transforms on the mixed path (2D Dirichlet, sizes multiples
-        of 128 up to 1024): split-bf16 digit products on the tensor cores
-        (default) or float64 products (EXPD_KF_DST_FP64)
+        of 128 up to 1024): split-bf16 digit products on the tensor cores in
+        128 x 128 output tiles (default) or 128 x 64 tiles (EXPD_KF_DST_N64,
+        twice the tiles for grids too small to fill the SMs), or float64
+        products (EXPD_KF_DST_FP64)
 
 Which is faster depends on the grid, the window and the precision.  A Tuner
 times every applicable combination on the device (whole solves, CUDA events,
@@ -31,11 +33,11 @@ from typing import Callable, Dict, List, Optional, Tuple
 from . import expd
 from . import inputs as I
 
-ALL_FLAGS = expd.KF_TIME_SMEM | expd.KF_FFT_RADIX4 | expd.KF_DST_FP64
+ALL_FLAGS = expd.KF_TIME_SMEM | expd.KF_FFT_RADIX4 | expd.KF_DST_FP64 | expd.KF_DST_N64
 KNOBS: Dict[str, Tuple[Tuple[str, int], ...]] = {
     "fft": (("four_step", 0), ("radix4", expd.KF_FFT_RADIX4)),
     "time": (("register", 0), ("smem", expd.KF_TIME_SMEM)),
-    "dst": (("tensor", 0), ("float64", expd.KF_DST_FP64)),
+    "dst": (("tensor", 0), ("tensor_n64", expd.KF_DST_N64), ("float64", expd.KF_DST_FP64)),
 }
 
 

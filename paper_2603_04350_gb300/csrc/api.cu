@@ -575,7 +575,7 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
         return expd_fail(EXPD_ERR_INVALID_ARG, "guess must be EXPD_GUESS_LINEAR or EXPD_GUESS_ZERO");
     if (scheme->startup != EXPD_STARTUP_RAMP && scheme->startup != EXPD_STARTUP_GIVEN)
         return expd_fail(EXPD_ERR_INVALID_ARG, "unknown startup mode");
-    if (scheme->kernel_flags & ~(EXPD_KF_TIME_SMEM | EXPD_KF_FFT_RADIX4 | EXPD_KF_DST_FP64))
+    if (scheme->kernel_flags & ~(EXPD_KF_TIME_SMEM | EXPD_KF_FFT_RADIX4 | EXPD_KF_DST_FP64 | EXPD_KF_DST_N64))
         return expd_fail(EXPD_ERR_INVALID_ARG, "unknown kernel_flags bits");
     if (scheme->nl_form != EXPD_NLF_IF && scheme->nl_form != EXPD_NLF_ETD1)
         return expd_fail(EXPD_ERR_INVALID_ARG, "nl_form must be EXPD_NLF_IF or EXPD_NLF_ETD1");

@@ -53,23 +53,32 @@
 namespace {
 
 constexpr int TC_BM = 128;                          // rows per tile (TMEM lanes)
-constexpr int TC_BN = 128;                          // columns per tile
 constexpr int TC_BK = 64;                           // K per stage (bf16: 128 bytes per row)
-constexpr int TC_TILE_ELEMS = TC_BM * TC_BK;        // 8192 bf16 per operand tile
+constexpr int TC_TILE_ELEMS = TC_BM * TC_BK;        // 8192 bf16 per packed operand tile (128 rows)
 constexpr int TC_TILE_BYTES = TC_TILE_ELEMS * 2;    // 16 KB
-constexpr int TC_STAGES = 6;
-constexpr int TC_EPI_WARPS = 8;                     // two per TMEM lane quarter, 64 columns each
+constexpr int TC_EPI_WARPS = 8;                     // two per TMEM lane quarter, BN/2 columns each
 constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS); // warp 0 copies, warp 1 issues MMAs, warps 2..9 drain
-constexpr int TC_NACC = 2;                          // accumulator buffers of 128 columns
-constexpr int TC_TMEM_COLS = 512;                   // acc[0], acc[1], hi, lo: 128 columns each
+constexpr int TC_NACC = 2;                          // accumulator buffers of BN columns
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // every wait gives up after 2 s
-constexpr size_t TC_SMEM = (size_t)TC_STAGES * 2 * TC_TILE_BYTES + 256 + 1024;
 
-// kind::f16 instruction descriptor: D float32 (bits 4-5 = 1), A and B bf16
-// (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
-// M >> 4 at bit 24.
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
-                              ((uint32_t)(TC_BM >> 4) << 24);
+// Tile shapes: BN = 128 output columns per tile (the default) or 64 (twice the
+// tiles, for transforms too small to give every SM a 128-column tile; a
+// plan selects it with EXPD_KF_DST_N64).  A stage holds one 128 x 64 A tile
+// and one BN x 64 B tile; TMEM holds acc[0], acc[1], hi and lo, BN columns each.
+template <int BN>
+struct TcShape {
+    static constexpr int B_BYTES = BN * TC_BK * 2;
+    static constexpr int STAGE_BYTES = TC_TILE_BYTES + B_BYTES;
+    static constexpr int STAGES = BN == 128 ? 6 : 8;
+    static constexpr int TMEM_COLS = 4 * BN;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 256 + 1024;
+    // kind::f16 instruction descriptor: D float32 (bits 4-5 = 1), A and B bf16
+    // (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit
+    // 17, M >> 4 at bit 24.
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(TC_BM >> 4) << 24);
+};
+static_assert(TcShape<128>::SMEM <= 232448 && TcShape<64>::SMEM <= 232448, "stage ring within 227 KB");
 
 struct TcArgs {
     const uint16_t* A;        // packed digit slices of the rows: [nsl][rows/128][KB][8192]
@@ -161,13 +170,14 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-// D (TMEM, 128 lanes x 128 float32 columns) (+)= A (128 x 16) B^T (16 x 128)
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+// D (TMEM, 128 lanes x N float32 columns) (+)= A (128 x 16) B^T (16 x N)
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(acc)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
         : "memory");
 }
 
@@ -316,11 +326,14 @@ __device__ __forceinline__ double scaled_sum(float hi, float lo, int E) {
 // float32), and warps 2..9 drain the finished buffer into the double-float sum
 // in TMEM while the next group accumulates.  After a tile's last group the
 // drain warps write the float64 result.
+template <int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_constant__ TcArgs a) {
+    typedef TcShape<BN> SH;
+    constexpr int TC_STAGES = SH::STAGES;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                          ~static_cast<uintptr_t>(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (size_t)TC_STAGES * 2 * TC_TILE_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (size_t)TC_STAGES * SH::STAGE_BYTES);
     // full[s], empty[s], accf[b], acce[b], drain
     const uint32_t bar0 = smem_u32(bars);
     auto full = [&](int s) { return bar0 + 8u * (uint32_t)s; };
@@ -347,7 +360,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
-        tc_alloc(smem_u32(tmem_slot), TC_TMEM_COLS);
+        tc_alloc(smem_u32(tmem_slot), SH::TMEM_COLS);
         tc_relinquish();
     }
     tc_fence_before();
@@ -355,7 +368,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int nct = a.N / TC_BN;
+    const int nct = a.N / BN;
     const long long ntiles = (long long)(a.rows / TC_BM) * nct;
     const int KB = a.KB;
 
@@ -367,9 +380,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
             for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 const long long rt = t / nct;
                 const int ct = (int)(t - rt * nct);
+                // B: packed 128-row tiles; a 64-column tile is the lower or
+                // upper half (row groups 0-7 or 8-15: the first or second 8 KB)
+                const long long boff = (long long)(ct * BN / 128) * KB * TC_TILE_ELEMS + (long long)((ct * BN) % 128) * TC_BK;
                 for (int p = 0; p < a.npairs && ok; ++p) {
                     const uint16_t* Ab = a.A + a.pi[p] * a.a_slice + rt * KB * TC_TILE_ELEMS;
-                    const uint16_t* Bb = a.B + a.pj[p] * a.b_slice + (long long)ct * KB * TC_TILE_ELEMS;
+                    const uint16_t* Bb = a.B + a.pj[p] * a.b_slice + boff;
                     for (int kb = 0; kb < KB; ++kb, ++it) {
                         const int s = (int)(it % TC_STAGES);
                         const uint32_t ph = (it / TC_STAGES) & 1u;
@@ -377,10 +393,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
                             ok = false;
                             break;
                         }
-                        unsigned char* st = sm + (size_t)s * 2 * TC_TILE_BYTES;
-                        mbar_arrive_expect_tx(full(s), 2 * TC_TILE_BYTES);
+                        unsigned char* st = sm + (size_t)s * SH::STAGE_BYTES;
+                        mbar_arrive_expect_tx(full(s), SH::STAGE_BYTES);
                         bulk_g2s(smem_u32(st), Ab + (long long)kb * TC_TILE_ELEMS, TC_TILE_BYTES, full(s));
-                        bulk_g2s(smem_u32(st + TC_TILE_BYTES), Bb + (long long)kb * TC_TILE_ELEMS, TC_TILE_BYTES,
+                        bulk_g2s(smem_u32(st + TC_TILE_BYTES), Bb + (long long)kb * TC_TILE_ELEMS, SH::B_BYTES,
                                  full(s));
                     }
                 }
@@ -407,7 +423,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t d = tmem + (uint32_t)(b * TC_BN);
+                    const uint32_t d = tmem + (uint32_t)(b * BN);
                     for (int p = a.gstart[g]; p < a.gstart[g + 1] && ok; ++p) {
                         const bool first = p == a.gstart[g];
                         for (int kb = 0; kb < KB; ++kb, ++it) {
@@ -417,11 +433,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
                                 break;
                             }
                             tc_fence_after();
-                            const uint32_t sa = smem_u32(sm + (size_t)s * 2 * TC_TILE_BYTES);
+                            const uint32_t sa = smem_u32(sm + (size_t)s * SH::STAGE_BYTES);
                             const uint32_t sb = sa + TC_TILE_BYTES;
 #pragma unroll
                             for (int q = 0; q < TC_BK / 16; ++q)  // 16 bf16 of K = two core matrices = 256 bytes
-                                tc_mma(d, smem_desc(sa + 256u * q), smem_desc(sb + 256u * q),
+                                tc_mma(d, smem_desc(sa + 256u * q), smem_desc(sb + 256u * q), SH::IDESC,
                                        !first || (kb | q) != 0);
                             tc_commit(empty(s));
                         }
@@ -439,10 +455,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
         }
     } else {
         // ---- drain and output (warps 2..9): TMEM lane quarter warp % 4, columns
-        // 64 (warp - 2) / 4 .. +63; the double-float sums in TMEM columns 256..511 ----
+        // (BN/2) (warp - 2) / 4 .. + BN/2 - 1 in chunks of 32; the double-float
+        // sums in TMEM columns 2 BN .. 4 BN - 1 ----
+        constexpr int CHUNKS = BN / 64;
         const int lq = warp & 3, half = (warp - 2) >> 2;
-        const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(half * 64);
-        const uint32_t thi = tl + 2u * TC_BN, tlo = tl + 3u * TC_BN;
+        const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(half * (BN / 2));
+        const uint32_t thi = tl + 2u * BN, tlo = tl + 3u * BN;
         uint32_t pc = 0;
         bool ok = true;
         for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -459,16 +477,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
                 tc_fence_after();
                 // weight 2^{-7(i+j+2)} of the group's pairs (digits are 0-based)
                 const float wsc = __int_as_float((127 - 7 * (a.gw[g] + 2)) << 23);
-                const uint32_t tacc = tl + (uint32_t)(b * TC_BN);
+                const uint32_t tacc = tl + (uint32_t)(b * BN);
 #pragma unroll 1
-                for (int c = 0; c < 2; ++c) {
+                for (int c = 0; c < CHUNKS; ++c) {
                     uint32_t v[32], h[32], l[32];
                     if (g == 0) {
                         tm_ld1(tacc + 32u * c, v);
                     } else {
                         tm_ld3(tacc + 32u * c, thi + 32u * c, tlo + 32u * c, v, h, l);
                     }
-                    if (c == 1) {  // the accumulator buffer is free for the group after next
+                    if (c == CHUNKS - 1) {  // the accumulator buffer is free for the group after next
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(acce(b));
@@ -500,9 +518,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
             const long long slc = row / a.R;
             const int rin = (int)(row - slc * a.R);
             const int E = a.ea[row] + a.eb;
-            double* o = a.out + slc * (long long)a.R * a.N + (long long)(ct * TC_BN + half * 64) * a.R + rin;
+            double* o = a.out + slc * (long long)a.R * a.N + (long long)(ct * BN + half * (BN / 2)) * a.R + rin;
 #pragma unroll 1
-            for (int c = 0; c < 2; ++c) {
+            for (int c = 0; c < CHUNKS; ++c) {
                 uint32_t h[32], l[32];
                 tm_ld2(thi + 32u * c, tlo + 32u * c, h, l);
 #pragma unroll
@@ -520,7 +538,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
     tc_fence_after();
     if (warp == 1) {
         __syncwarp();
-        tc_dealloc(tmem, TC_TMEM_COLS);
+        tc_dealloc(tmem, SH::TMEM_COLS);
     }
 }
 
@@ -573,12 +591,18 @@ expd_status mma_pass(expd_plan p, const uint16_t* A, const int* ea, long long ro
     a.ngroups = ng;
     a.err = p->tc_err;
     a.cancel = p->cancel_dev;
-    const long long ntiles = (rows / TC_BM) * (N / TC_BN);
+    const int bn = (p->kernel_flags & EXPD_KF_DST_N64) ? 64 : 128;
+    const long long ntiles = (rows / TC_BM) * (N / bn);
     const int grid = (int)std::min<long long>(ntiles, (long long)p->sm_count);
-    EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel, TC_SMEM));
     KProf kp(p, s, EXPD_K_DST_TC, 2.0 * nsl * ((double)rows * K + (double)N * K) + 8.0 * rows * N,
              2.0 * np * (double)rows * N * K);
-    dst_mma_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>(a);
+    if (bn == 64) {
+        EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel<64>, TcShape<64>::SMEM));
+        dst_mma_kernel<64><<<grid, TC_THREADS, TcShape<64>::SMEM, s>>>(a);
+    } else {
+        EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel<128>, TcShape<128>::SMEM));
+        dst_mma_kernel<128><<<grid, TC_THREADS, TcShape<128>::SMEM, s>>>(a);
+    }
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }

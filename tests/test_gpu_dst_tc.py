@@ -43,8 +43,12 @@ def _counts(plan):
     return plan.timing_read(reset=True)["classes"]
 
 
+TILES = [0, 8]          # 128 x 128 output tiles, 128 x 64 tiles (EXPD_KF_DST_N64)
+
+
+@pytest.mark.parametrize("flags", TILES, ids=["n128", "n64"])
 @pytest.mark.parametrize("p", TC_CASES, ids=TC_IDS)
-def test_tc_residual_matches_oracle(expd, p):
+def test_tc_residual_matches_oracle(expd, p, flags):
     # the residual of a mixed plan is float64 arithmetic around the two
     # transforms, so its error is the transforms' error
     sp = O.spec_of(p)
@@ -56,7 +60,8 @@ def test_tc_residual_matches_oracle(expd, p):
     U_start = np.concatenate([u0[None], U[: p.order - 1]])
     ref = O.residual(sp, U[p.order - 1:], O.rhs_known(sp, U_start, f))
     R = torch.empty((p.Ns,) + p.n, dtype=torch.float64, device=DEV)
-    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-10)) as plan:
+    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-10,
+                                                 kernel_flags=flags)) as plan:
         plan.timing_enable(True)
         plan.residual(dev(u0), dev(f), dev(U), R)
         cls = _counts(plan)
@@ -64,20 +69,23 @@ def test_tc_residual_matches_oracle(expd, p):
     assert relmax(host(R), ref) < 1e-9
 
 
+@pytest.mark.parametrize("flags", TILES, ids=["n128", "n64"])
 @pytest.mark.parametrize("p", TC_CASES, ids=TC_IDS)
-def test_tc_solve_matches_sequential(expd, p):
+def test_tc_solve_matches_sequential(expd, p, flags):
     sp = O.spec_of(p)
     rng = np.random.default_rng(14)
     u0 = rng.uniform(-0.8, 0.8, p.n)
     f = rng.standard_normal((p.Nt,) + p.n) if p.nonlin == "none" else None
     ref = O.sequential_solve(sp, u0, f)[1:]
     U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
-    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-10, max_iter=200)) as plan:
+    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-10, max_iter=200,
+                                                 kernel_flags=flags)) as plan:
         info = plan.solve_fp(dev(u0), None if f is None else dev(f), U)
     assert O.rel_error(host(U), ref) < 1e-9, info
     if p.nonlin == "none":
         U2 = torch.empty_like(U)
-        with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-10)) as plan:
+        with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-10,
+                                                     kernel_flags=flags)) as plan:
             info = plan.solve_gmres(dev(u0), dev(f), U2)
         assert O.rel_error(host(U2), ref) < 1e-9, info
 
@@ -99,6 +107,22 @@ def test_tc_agrees_with_float64_products(expd, monkeypatch):
         assert (cls["dst_tc"]["count"] > 0) == (mode == "1"), cls
         out[mode] = host(U)
     assert O.rel_error(out["1"], out["0"]) < 1e-9
+
+
+def test_tc_tile_widths_agree_bit_for_bit(expd):
+    # both tile widths sum the same digit products in the same order per
+    # output element: identical results
+    p = TC_CASES[1]
+    rng = np.random.default_rng(16)
+    r = rng.standard_normal((p.Ns,) + p.n)
+    out = []
+    for flags in TILES:
+        S = torch.empty_like(dev(r))
+        with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-10,
+                                                     kernel_flags=flags)) as plan:
+            plan.precond_apply(dev(r), S)
+        out.append(host(S))
+    assert np.array_equal(out[0], out[1])
 
 
 def test_tc_deterministic(expd):
