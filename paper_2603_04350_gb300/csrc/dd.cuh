@@ -40,13 +40,25 @@ EXPD_HD float f32_from_bits(unsigned u) {
 #endif
 }
 
+// The ordinary (float64-pipe) conversions of the rare operands -- subnormal
+// results, values beyond float's range, infinities, NaN -- are out of line:
+// inlined, the compiler evaluates them for every element and selects, which
+// puts one float64-pipe instruction on every conversion.
+#ifdef __CUDA_ARCH__
+static __device__ __noinline__ float f32_of_f64_rare(double v) { return (float)v; }
+static __device__ __noinline__ double f64_of_f32_rare(float f) { return (double)f; }
+#else
+inline float f32_of_f64_rare(double v) { return (float)v; }
+inline double f64_of_f32_rare(float f) { return (double)f; }
+#endif
+
 // Round to nearest even, as the hardware conversion; values whose float is
 // subnormal, zero, infinite or NaN take the ordinary conversion.
 EXPD_HD float f32_rn_from_f64(double v) {
     const unsigned long long b = f64_bits(v);
     const int e = (int)((b >> 52) & 0x7ff);
     if ((b << 1) == 0ull) return f32_from_bits((unsigned)(b >> 63) << 31);  // signed zero
-    if (e < 897 || e > 1150) return (float)v;  // outside float's normal range
+    if (e < 897 || e > 1150) return f32_of_f64_rare(v);  // outside float's normal range
     const unsigned long long m = b & 0xfffffffffffffULL;
     unsigned u = ((unsigned)(b >> 63) << 31) | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29);
     const unsigned long long tail = m & 0x1fffffffULL;  // the 29 dropped bits
@@ -82,7 +94,7 @@ EXPD_HD double f64_from_f32(float f) {
                 ((unsigned long long)((m << (z + 1)) & 0x7fffffu) << 29);
         }
     } else if (e == 0xffu) {
-        return (double)f;  // infinity, NaN
+        return f64_of_f32_rare(f);  // infinity, NaN
     } else {
         b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
             ((unsigned long long)m << 29);
@@ -105,7 +117,7 @@ EXPD_HD float f32_ftz_from_f64(double v) {
     const unsigned long long b = f64_bits(v);
     const int e = (int)((b >> 52) & 0x7ff);
     if (e < 897) return f32_from_bits((unsigned)(b >> 63) << 31);
-    if (e > 1150) return (float)v;
+    if (e > 1150) return f32_of_f64_rare(v);
     const unsigned long long m = b & 0xfffffffffffffULL;
     unsigned u = ((unsigned)(b >> 63) << 31) | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29);
     const unsigned long long tail = m & 0x1fffffffULL;

@@ -38,6 +38,31 @@ using namespace expd_time;
 // by asynchronous copies, all of a thread's elements in flight at once.
 constexpr int TIME_REAL_COLS = 2 * EXPD_TIME_COLS;
 
+// Twiddle pairs of the radix-4 passes, one table per pass span h: entry k < h
+// holds (w4, w2) = (e^{-2 pi i k/(4h)}, e^{-2 pi i k/(2h)}), the two twiddles
+// a butterfly of that span reads, so one load fetches both and consecutive
+// lanes read consecutive entries (a strided read of the length-n table puts
+// up to 8 lanes of a half-warp on one bank in the middle passes).  The spans
+// are n/4, n/16, ... (both directions use the same set); the tables are stored
+// largest span first.
+template <typename T2>
+struct __align__(2 * sizeof(T2)) TwPair {
+    T2 w4, w2;
+};
+
+// offset of span h's table: the sizes of the larger spans before it
+__host__ __device__ constexpr int twp_offset(int n, int h) {
+    int off = 0;
+    for (int q = n >> 2; q > h; q >>= 2) off += q;
+    return off;
+}
+// entries of all the tables of length n
+__host__ __device__ constexpr int twp_entries(int n) {
+    int e = 0;
+    for (int q = n >> 2; q >= 1; q >>= 2) e += q;
+    return e;
+}
+
 // Bluestein passes of the real kernel (one warp, length 2^LOG2N, the
 // swizzled buffer map padi<2>), with the pointwise steps of precond_step_a /
 // precond_step_c folded in.  A Bluestein input is zero from Ns <= L/2 on, so
@@ -47,7 +72,7 @@ constexpr int TIME_REAL_COLS = 2 * EXPD_TIME_COLS;
 // k < Ns the solve reads.  The operations on the values kept, and their order,
 // are those of fft_dif / fft_dit and the separate sweeps.
 template <typename T2, int LOG2N, int SIGN>
-__device__ __forceinline__ void bl_dif(T2* x, const T2* tw, const T2* tab, int lane) {
+__device__ __forceinline__ void bl_dif(T2* x, const TwPair<T2>* twp, const T2* tab, int lane) {
     constexpr int n = 1 << LOG2N;
     static_assert(LOG2N >= 6, "a warp of 32 lanes covers the radix-2 passes; the first pass is not the last");
     {  // first pass: span n/4, inputs x[i + n/2], x[i + 3n/4] are zero
@@ -56,7 +81,8 @@ __device__ __forceinline__ void bl_dif(T2* x, const T2* tw, const T2* tab, int l
         for (int g0 = 0; g0 < h; g0 += 32) {
             const int i = g0 + lane;
             if (h < 32 && i >= h) break;
-            T2 w2 = tw[i * 2], w4 = tw[i];
+            const TwPair<T2> tp = twp[twp_offset(n, h) + i];
+            T2 w2 = tp.w2, w4 = tp.w4;
             if (SIGN > 0) {
                 w2.y = -w2.y;
                 w4.y = -w4.y;
@@ -74,8 +100,7 @@ __device__ __forceinline__ void bl_dif(T2* x, const T2* tw, const T2* tab, int l
 #pragma unroll
     for (int s = LOG2N - 3; s >= 1; s -= 2) {
         const int h = 1 << (s - 1);
-        const int t4 = n >> (s + 1);
-        const int t2 = n >> s;
+        const TwPair<T2>* tph = twp + twp_offset(n, h);
         const bool last = (s == 1);  // (LOG2N even: the last pass, spans 1)
 #pragma unroll 2
         for (int g0 = 0; g0 < (n >> 2); g0 += 32) {
@@ -83,7 +108,8 @@ __device__ __forceinline__ void bl_dif(T2* x, const T2* tw, const T2* tab, int l
             if ((n >> 2) < 32 && g >= (n >> 2)) break;
             const int k = g & (h - 1);
             const int i = ((g >> (s - 1)) << (s + 1)) + k;
-            T2 w2 = tw[k * t2], w4 = tw[k * t4];
+            const TwPair<T2> tp = tph[k];
+            T2 w2 = tp.w2, w4 = tp.w4;
             if (SIGN > 0) {
                 w2.y = -w2.y;
                 w4.y = -w4.y;
@@ -120,7 +146,7 @@ __device__ __forceinline__ void bl_dif(T2* x, const T2* tw, const T2* tab, int l
 }
 
 template <typename T2, int LOG2N, int SIGN>
-__device__ __forceinline__ void bl_dit(T2* x, const T2* tw, int lane) {
+__device__ __forceinline__ void bl_dit(T2* x, const TwPair<T2>* twp, int lane) {
     constexpr int n = 1 << LOG2N;
     if (LOG2N & 1) {
 #pragma unroll 2
@@ -135,8 +161,7 @@ __device__ __forceinline__ void bl_dit(T2* x, const T2* tw, int lane) {
 #pragma unroll
     for (int s = (LOG2N & 1); s < LOG2N; s += 2) {
         const int h = 1 << s;
-        const int t2 = n >> (s + 1);
-        const int t4 = n >> (s + 2);
+        const TwPair<T2>* tph = twp + twp_offset(n, h);
         const bool last = (s == LOG2N - 2);  // span n/4: only outputs below n/2 are kept
 #pragma unroll 2
         for (int g0 = 0; g0 < (n >> 2); g0 += 32) {
@@ -144,7 +169,8 @@ __device__ __forceinline__ void bl_dit(T2* x, const T2* tw, int lane) {
             if ((n >> 2) < 32 && g >= (n >> 2)) break;
             const int k = g & (h - 1);
             const int i = ((g >> s) << (s + 2)) + k;
-            T2 w2 = tw[k * t2], w4 = tw[k * t4];
+            const TwPair<T2> tp = tph[k];
+            T2 w2 = tp.w2, w4 = tp.w4;
             if (SIGN > 0) {
                 w2.y = -w2.y;
                 w4.y = -w4.y;
@@ -169,7 +195,7 @@ __device__ __forceinline__ void bl_dit(T2* x, const T2* tw, int lane) {
 // (the host sizes the launch with the same struct).
 template <typename PT, typename ST>
 struct RealSmem {
-    size_t w, tw, lam, chirp, bp, bm, acc, x, r, gam, gamf, total;
+    size_t w, tw, twp, lam, chirp, bp, bm, acc, x, r, gam, gamf, total;
     EXPD_HD static size_t up16(size_t b) { return (b + 15) & ~(size_t)15; }
     EXPD_HD RealSmem(int Ns, int L, int bluestein, int norms) {
         const size_t c = sizeof(typename cplx<PT>::t);
@@ -177,6 +203,7 @@ struct RealSmem {
         size_t o = 0;
         w = o;     o = up16(o + (size_t)EXPD_TIME_COLS * L * c);
         tw = o;    o = up16(o + (size_t)((L >> 1) + 1) * c);
+        twp = o;   o = up16(o + (size_t)twp_entries(L) * 2 * c);
         lam = o;   o = up16(o + (size_t)Ns * c);
         chirp = o; o = up16(o + (bluestein ? (size_t)Ns * c : 0));
         bp = o;    o = up16(o + (bluestein ? (size_t)L * c : 0));
@@ -201,6 +228,7 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, sizeof(PT) == 8 ? 2 : 3) 
     const RealSmem<PT, ST> lay(Ns, L, A.bluestein, A.norms);
     PT2* sW = reinterpret_cast<PT2*>(smem_raw + lay.w);          // [NW][L]
     PT2* tw = reinterpret_cast<PT2*>(smem_raw + lay.tw);         // [L/2]
+    TwPair<PT2>* twp = reinterpret_cast<TwPair<PT2>*>(smem_raw + lay.twp);  // per-pass twiddle pairs
     PT2* lam = reinterpret_cast<PT2*>(smem_raw + lay.lam);       // [Ns]
     PT2* chirp = reinterpret_cast<PT2*>(smem_raw + lay.chirp);   // [Ns]  (Bluestein)
     PT2* bp = reinterpret_cast<PT2*>(smem_raw + lay.bp);         // [L]   (Bluestein)
@@ -234,6 +262,17 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, sizeof(PT) == 8 ? 2 : 3) 
             bp[i] = static_cast<const PT2*>(A.bplus)[i];
             bm[i] = static_cast<const PT2*>(A.bminus)[i];
         }
+    __syncthreads();
+    if (LOG2L > 0 && A.bluestein) {
+        // the per-pass twiddle pairs of the folded passes, from the table above
+        for (int h = L >> 2; h >= 1; h >>= 2)
+            for (int k = tid; k < h; k += nth) {
+                TwPair<PT2> tp;
+                tp.w4 = tw[k * (L / (4 * h))];
+                tp.w2 = tw[k * (L / (2 * h))];
+                twp[twp_offset(L, h) + k] = tp;
+            }
+    }
     pdl_wait();
     __syncthreads();
 
@@ -351,8 +390,8 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, sizeof(PT) == 8 ? 2 : 3) 
                 EXPD_SYNCWARP();
                 // Step (a): chirp-z convolution; on exit w[k] c_k = L Y_k for k < Ns
                 if constexpr (LOG2L > 0) {
-                    bl_dif<PT2, LOG2L, -1>(w, tw, bp, lane);
-                    bl_dit<PT2, LOG2L, +1>(w, tw, lane);
+                    bl_dif<PT2, LOG2L, -1>(w, twp, bp, lane);
+                    bl_dit<PT2, LOG2L, +1>(w, twp, lane);
                 }
                 // Step (b) on two real columns at once (precond_column_pair), the
                 // Step (a) output chirp folded into the reads and Step (c)'s input
@@ -380,8 +419,8 @@ __global__ void __launch_bounds__(32 * EXPD_TIME_COLS, sizeof(PT) == 8 ? 2 : 3) 
                 EXPD_SYNCWARP();
                 // Step (c): the inverse DFT by chirp-z; the output chirp below
                 if constexpr (LOG2L > 0) {
-                    bl_dif<PT2, LOG2L, -1>(w, tw, bm, lane);
-                    bl_dit<PT2, LOG2L, +1>(w, tw, lane);
+                    bl_dif<PT2, LOG2L, -1>(w, twp, bm, lane);
+                    bl_dit<PT2, LOG2L, +1>(w, twp, lane);
                 }
             } else {
                 EXPD_SYNCWARP();
