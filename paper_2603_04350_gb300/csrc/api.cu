@@ -688,6 +688,10 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     p->no_graphs = gr && strcmp(gr, "0") == 0;
     const char* po = getenv("EXPD_POISON");
     p->poison = po && strcmp(po, "1") == 0;
+    // EXPD_TIME_CPLX=0: complex columns take the generic shared-memory kernel
+    // instead of the fixed-length one (both compute the same; tests)
+    const char* tc = getenv("EXPD_TIME_CPLX");
+    p->no_cplx_time = tc && strcmp(tc, "0") == 0;
     // the device-controlled loop is opt-in (EXPD_DEVICE_LOOP=1): on GB300 its
     // while-node iterations measured slower than host round trips that read
     // the norms from mapped memory (0.624 against 0.594 ms per solve on

@@ -170,6 +170,7 @@ struct expd_plan_s {
     long long fp_solves = 0;      // fixed-point solves run on this plan
     int no_graphs = 0;            // 1: launch kernel by kernel (EXPD_GRAPHS=0)
     int poison = 0;               // 1: fill every new device buffer with NaN bytes (EXPD_POISON=1)
+    int no_cplx_time = 0;         // 1: complex columns take the generic time kernel (EXPD_TIME_CPLX=0)
     int no_reg_time = 0;          // 1 forces the shared-memory time kernel (tests)
     int no_real_time = 0;         // 1: real columns take the generic kernel (EXPD_TIME_REAL=0, tests)
     int no_fft4 = 0;              // 1 forces the radix-4 shared-memory row / column FFTs (tests)

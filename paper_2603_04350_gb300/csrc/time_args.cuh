@@ -136,3 +136,9 @@ expd_status time_reg_launch(expd_plan p, expd_time::TimeArgs& a, int st, cudaStr
 // Real-column time kernel (Dirichlet grids; time_real.cu): float32 (f32 = 1)
 // or float64 preconditioner, float32 (st32 = 1) or float64 storage.
 expd_status time_real_launch(expd_plan p, expd_time::TimeArgs& a, int f32, int st32, cudaStream_t s);
+// Complex-column time kernel (periodic grids and complex states without a
+// complex symbol; time_cplx.cu): st = 1 float32 storage, 2 double-float
+// storage (both with the float32 preconditioner), 0 float64 throughout;
+// and the shared memory it needs for the plan's window.
+expd_status time_cplx_launch(expd_plan p, expd_time::TimeArgs& a, int st, cudaStream_t s);
+size_t time_cplx_smem_bytes(expd_plan p, int st);

@@ -495,6 +495,21 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s) {
         }
         return time_real_launch(p, a, op.f32 ? 1 : 0, 0, s);
     }
+    // complex columns with real coefficients: the fixed-length kernel (when its
+    // tables fit one CTA's shared memory; the generic kernel otherwise)
+    const int cst = op.stdd ? 2 : op.st32 ? 1 : 0;
+    if (!p->realcol && !p->adv && !p->no_cplx_time && time_cplx_smem_bytes(p, cst) <= 227 * 1024) {
+        if (op.stdd) {
+            if (!op.f32) return expd_fail(EXPD_ERR_INVALID_ARG, "double-float storage needs the float32 preconditioner");
+            return time_cplx_launch(p, a, 2, s);
+        }
+        if (op.st32) {
+            if (!op.f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 storage needs the float32 preconditioner");
+            if (op.NL && !op.nl_f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 storage needs float32 N");
+            return time_cplx_launch(p, a, 1, s);
+        }
+        if (!op.f32) return time_cplx_launch(p, a, 0, s);
+    }
     if (op.stdd) {
         if (!op.f32) return expd_fail(EXPD_ERR_INVALID_ARG, "double-float storage needs the float32 preconditioner");
         return p->realcol ? launch_time<float, dd, true, false>(p, a, s)

@@ -903,6 +903,57 @@ def test_real_time_kernel_matches_generic_and_oracle(expd, p, prec, monkeypatch)
                 assert O.rel_error(host(U), seq) < 1e-10, (fn.__name__, info)
 
 
+# ------------------------------------------------- complex-column kernel --
+# Periodic grids: the fixed-length complex-column time kernel (time_cplx.cu;
+# compile-time FFT lengths 64-512 here, folded Bluestein passes) against the
+# generic shared-memory kernel (EXPD_TIME_CPLX=0) and the oracle, on windows
+# covering every compiled length, a run-time length (L = 32) and a compiled
+# radix-2 window; the mixed fixed point runs its float32 and double-float
+# sweeps through it.
+CPLX_CASES = [
+    P("p2d_blue11", "periodic", (16, 32), 1, Nt=11, alpha=1e-3, dt=1e-3),      # Ns = 11: L = 32 (run time)
+    P("p2d_blue20", "periodic", (16, 32), 2, Nt=21, alpha=1e-3, dt=1e-3),      # L = 64
+    P("p2d_blue45", "periodic", (16, 16), 6, Nt=50, alpha=1e-3, dt=1e-3),      # L = 128
+    P("p2d_blue127", "periodic", (8, 16), 2, Nt=128, alpha=1e-3, dt=1e-3),     # L = 256
+    P("p2d_blue251", "periodic", (8, 8), 6, Nt=256, alpha=1e-3, dt=1e-3),      # L = 512
+    P("p2d_pow2_128", "periodic", (16, 8), 1, Nt=128, alpha=1e-3, dt=1e-3),    # radix-2, L = 128
+    P("p2d_ac_blue63", "periodic", (16, 16), 2, nonlin="allen_cahn", a=0.01, c=0.0, dt=1e-3, Nt=64,
+      alpha=1e-3),                                                              # Allen-Cahn, L = 128
+]
+
+
+@pytest.mark.parametrize("p", CPLX_CASES, ids=[p.name for p in CPLX_CASES])
+def test_complex_column_kernel_matches_generic_and_oracle(expd, p, monkeypatch):
+    sp = O.spec_of(p)
+    r = rand_field(p, (p.Ns,), 27)
+    ref = O.precond_apply(sp, r)
+    outs = {}
+    for kind in ("fixed", "generic"):
+        if kind == "generic":
+            monkeypatch.setenv("EXPD_TIME_CPLX", "0")
+        else:
+            monkeypatch.delenv("EXPD_TIME_CPLX", raising=False)
+        S = torch.empty_like(dev(r))
+        with expd.plan_create(expd.spec_from_problem(p)) as plan:
+            plan.precond_apply(dev(r), S)
+        outs[kind] = host(S)
+    assert relmax(outs["fixed"], ref) < 1e-11
+    assert relmax(outs["generic"], ref) < 1e-11
+    monkeypatch.delenv("EXPD_TIME_CPLX", raising=False)
+    rng = np.random.default_rng(28)
+    amp = 0.8 if p.nonlin != "none" else 1.0
+    u0 = amp * rng.uniform(-1, 1, p.n)
+    f = rng.standard_normal((p.Nt,) + p.n) if p.nonlin == "none" else None
+    seq = O.sequential_solve(sp, u0, f)[1:]
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    for prec in (expd.PREC_FP64, expd.PREC_MIXED):
+        with expd.plan_create(expd.spec_from_problem(p, precision=prec, tol=1e-12, max_iter=400)) as plan:
+            fns = (plan.solve_fp,) if p.nonlin != "none" else (plan.solve_fp, plan.solve_gmres)
+            for fn in fns:
+                fn(dev(u0), None if f is None else dev(f), U)
+                assert O.rel_error(host(U), seq) < 1e-10, (fn.__name__, prec)
+
+
 # ------------------------------------------------------------------- ETD1 --
 # u_n = A u_{n-1} + dt phi_1(dt L) N(u_{n-1}) (nl_form = EXPD_NLF_ETD1): the
 # phi_1 tables, the one-slice shift of the transformed N, the phi_1 N(u_0)
