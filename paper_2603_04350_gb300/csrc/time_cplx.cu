@@ -24,17 +24,18 @@ namespace {
 
 using namespace expd_time;
 
-// One warp per complex column, EXPD_TIME_COLS columns per CTA.  The tiles are
-// column-major with the odd column stride P = Ns | 1, so the coalesced
-// row-wise copies (consecutive lanes on consecutive columns) and the
-// per-column sweeps are both free of bank conflicts.
-constexpr int TC_COLS = EXPD_TIME_COLS;
-
-template <typename PT, typename ST>
+// One warp per complex column, C columns per CTA: 8, or 12 for double-float
+// storage (16-byte elements leave room for one CTA per SM only, so a wider
+// CTA is what adds resident warps).  The tiles are column-major with the odd
+// column stride P = Ns | 1, so the coalesced row-wise copies (consecutive
+// lanes on consecutive columns) and the per-column sweeps are both free of
+// bank conflicts.
+template <typename PT, typename ST, int TC_COLS>
 struct CplxSmem {
-    size_t w, tw, twp, lam, chirp, bp, bm, acc, x, r, gam, wgt, total;
+    size_t w, tw, twp, lam, chirp, bp, bm, acc, x, r, nl, gam, wgt, total;
     EXPD_HD static size_t up16(size_t b) { return (b + 15) & ~(size_t)15; }
-    EXPD_HD CplxSmem(int Ns, int L, int bluestein) {
+    // nl_async: N arrives by asynchronous copies into a tile of its own
+    EXPD_HD CplxSmem(int Ns, int L, int bluestein, int nl_async) {
         typedef typename cplx<PT>::t PT2;
         typedef typename cplx<ST>::t ST2;
         const size_t c = sizeof(PT2), sc = sizeof(ST2);
@@ -50,21 +51,33 @@ struct CplxSmem {
         acc = o;   o = up16(o + (size_t)Ns * sc);
         x = o;     o = up16(o + (size_t)TC_COLS * P * sc);
         r = o;     o = up16(o + (size_t)TC_COLS * P * sc);
+        nl = o;    o = up16(o + (nl_async ? (size_t)TC_COLS * P * sc : 0));
         gam = o;   o = up16(o + 2 * (size_t)Ns * sizeof(ST));
         wgt = o;   o = up16(o + (size_t)TC_COLS * sizeof(ST));
         total = o;
     }
 };
 
-template <typename PT, typename ST, int LOG2L>
-__global__ void __launch_bounds__(32 * TC_COLS, sizeof(ST) == 4 ? 3 : 2) time_kernel_cplx(TimeArgs A) {
+// whether N's elements have the storage type ST2 (then they are copied with the tile)
+template <typename ST>
+EXPD_HD bool nl_copyable(const TimeArgs& A) {
+    if (!A.NL) return false;
+    if (std::is_same<ST, dd>::value) return true;
+    return std::is_same<ST, float>::value ? A.nl_f32 != 0 : A.nl_f32 == 0;
+}
+
+template <typename PT, typename ST, int LOG2L, int C>
+__global__ void __launch_bounds__(32 * C, C == 8 ? (sizeof(ST) == 4 ? 3 : 2) : 1) time_kernel_cplx(TimeArgs A) {
     typedef typename cplx<PT>::t PT2;
     typedef typename cplx<ST>::t ST2;
-    constexpr int C = TC_COLS;
     const int Ns = A.Ns, L = LOG2L > 0 ? (1 << LOG2L) : A.L;
     const int P = Ns | 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const CplxSmem<PT, ST> lay(Ns, L, A.bluestein);
+    // N in the storage type (float32 N with float32 storage, double-float N
+    // with double-float storage, float64 N with float64 storage) is copied
+    // asynchronously with the tile; any other N is read element by element
+    const bool nl_async = nl_copyable<ST>(A);
+    const CplxSmem<PT, ST, C> lay(Ns, L, A.bluestein, nl_async);
     PT2* sW = reinterpret_cast<PT2*>(smem_raw + lay.w);          // [C][L]
     PT2* tw = reinterpret_cast<PT2*>(smem_raw + lay.tw);         // [L/2]
     TwPair<PT2>* twp = reinterpret_cast<TwPair<PT2>*>(smem_raw + lay.twp);
@@ -75,6 +88,7 @@ __global__ void __launch_bounds__(32 * TC_COLS, sizeof(ST) == 4 ? 3 : 2) time_ke
     ST2* sAcc = reinterpret_cast<ST2*>(smem_raw + lay.acc);      // [Ns]
     ST2* sX = reinterpret_cast<ST2*>(smem_raw + lay.x);          // [C][P]
     ST2* sR = reinterpret_cast<ST2*>(smem_raw + lay.r);          // [C][P]
+    ST2* sN = reinterpret_cast<ST2*>(smem_raw + lay.nl);         // [C][P] (nl_async)
     ST* gam = reinterpret_cast<ST*>(smem_raw + lay.gam);         // [Ns]
     ST* osc = gam + Ns;                                          // [Ns]
     ST* sWgt = reinterpret_cast<ST*>(smem_raw + lay.wgt);        // [C] norm weight of each column
@@ -112,6 +126,7 @@ __global__ void __launch_bounds__(32 * TC_COLS, sizeof(ST) == 4 ? 3 : 2) time_ke
     const ST bdt = (ST)A.bdt, sigR = (ST)A.sigR;
     const ST2* X = static_cast<const ST2*>(A.X);
     const ST2* F = static_cast<const ST2*>(A.F);
+    const ST2* NLc = static_cast<const ST2*>(A.NL);
     const PT one = (PT)(1.0 - A.dshift);
     const bool fold = LOG2L > 0 && A.bluestein;
     const int pos_shift = A.bluestein ? 0 : 1;  // radix-2 windows take bit-reversed positions
@@ -129,6 +144,7 @@ __global__ void __launch_bounds__(32 * TC_COLS, sizeof(ST) == 4 ? 3 : 2) time_ke
             else sX[c * P + n] = c2((ST)0, (ST)0);
             if (F) cp_async_elem<(int)sizeof(ST2)>(&sR[c * P + n], F + g, valid && n < A.f_slices);
             else sR[c * P + n] = c2((ST)0, (ST)0);
+            if (nl_async) cp_async_elem<(int)sizeof(ST2)>(&sN[c * P + n], NLc + g, valid);
         }
         cp_async_wait_all();
         if (A.NL) {
@@ -136,7 +152,7 @@ __global__ void __launch_bounds__(32 * TC_COLS, sizeof(ST) == 4 ? 3 : 2) time_ke
                 const int n = idx / C, c = idx - n * C;
                 const long long m = m0 + c;
                 if (m < Mcol) {
-                    const ST2 v = ldnl<ST, false>(A.NL, (long long)n * Mcol + m, A.nl_f32);
+                    const ST2 v = nl_async ? sN[c * P + n] : ldnl<ST, false>(A.NL, (long long)n * Mcol + m, A.nl_f32);
                     ST2 r = sR[c * P + n];
                     r.x = fma(bdt, v.x, r.x);
                     r.y = fma(bdt, v.y, r.y);
@@ -260,7 +276,7 @@ __global__ void __launch_bounds__(32 * TC_COLS, sizeof(ST) == 4 ? 3 : 2) time_ke
         A.partial[(size_t)n * gridDim.x + blockIdx.x] = make_double2((double)sAcc[n].x, (double)sAcc[n].y);
 }
 
-template <typename PT, typename ST, int LOG2L>
+template <typename PT, typename ST, int LOG2L, int TC_COLS>
 expd_status launch_time_cplx(expd_plan p, TimeArgs& a, cudaStream_t s) {
     const TimeTables& t = std::is_same<PT, float>::value ? p->t32 : p->t64;
     const TimeTables& ts = std::is_same<ST, float>::value ? p->t32 : p->t64;
@@ -275,8 +291,8 @@ expd_status launch_time_cplx(expd_plan p, TimeArgs& a, cudaStream_t s) {
     a.log2L = t.log2L;
     a.bluestein = t.bluestein;
     a.ntiles = (p->Mcol + TC_COLS - 1) / TC_COLS;
-    const size_t smem = CplxSmem<PT, ST>(p->Ns, t.L, t.bluestein).total;
-    auto kern = time_kernel_cplx<PT, ST, LOG2L>;
+    const size_t smem = CplxSmem<PT, ST, TC_COLS>(p->Ns, t.L, t.bluestein, nl_copyable<ST>(a)).total;
+    auto kern = time_kernel_cplx<PT, ST, LOG2L, TC_COLS>;
     EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
     int per_sm = 1;
     EXPD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * TC_COLS, smem));
@@ -300,16 +316,16 @@ expd_status launch_time_cplx(expd_plan p, TimeArgs& a, cudaStream_t s) {
     return EXPD_OK;
 }
 
-template <typename PT, typename ST>
+template <typename PT, typename ST, int C>
 expd_status launch_cplx_for_length(expd_plan p, TimeArgs& a, cudaStream_t s) {
     const TimeTables& t = std::is_same<PT, float>::value ? p->t32 : p->t64;
     switch (t.log2L) {
-        case 6: return launch_time_cplx<PT, ST, 6>(p, a, s);
-        case 7: return launch_time_cplx<PT, ST, 7>(p, a, s);
-        case 8: return launch_time_cplx<PT, ST, 8>(p, a, s);
-        case 9: return launch_time_cplx<PT, ST, 9>(p, a, s);
-        case 10: return launch_time_cplx<PT, ST, 10>(p, a, s);
-        default: return launch_time_cplx<PT, ST, 0>(p, a, s);
+        case 6: return launch_time_cplx<PT, ST, 6, C>(p, a, s);
+        case 7: return launch_time_cplx<PT, ST, 7, C>(p, a, s);
+        case 8: return launch_time_cplx<PT, ST, 8, C>(p, a, s);
+        case 9: return launch_time_cplx<PT, ST, 9, C>(p, a, s);
+        case 10: return launch_time_cplx<PT, ST, 10, C>(p, a, s);
+        default: return launch_time_cplx<PT, ST, 0, C>(p, a, s);
     }
 }
 
@@ -317,16 +333,22 @@ expd_status launch_cplx_for_length(expd_plan p, TimeArgs& a, cudaStream_t s) {
 
 size_t time_cplx_smem_bytes(expd_plan p, int st) {
     const TimeTables& t = st ? p->t32 : p->t64;
-    if (st == 1) return CplxSmem<float, float>(p->Ns, t.L, t.bluestein).total;
-    if (st == 2) return CplxSmem<float, dd>(p->Ns, t.L, t.bluestein).total;
-    return CplxSmem<double, double>(p->Ns, t.L, t.bluestein).total;
+    // (eight columns, N copied with the tile: the largest eight-column layout)
+    if (st == 1) return CplxSmem<float, float, 8>(p->Ns, t.L, t.bluestein, 1).total;
+    if (st == 2) return CplxSmem<float, dd, 8>(p->Ns, t.L, t.bluestein, 1).total;
+    return CplxSmem<double, double, 8>(p->Ns, t.L, t.bluestein, 1).total;
 }
 
 // Complex columns with real coefficient tables: st = 1 float32 storage with
 // the float32 preconditioner, st = 2 double-float storage with the float32
 // preconditioner, st = 0 float64 storage with the float64 preconditioner.
 expd_status time_cplx_launch(expd_plan p, TimeArgs& a, int st, cudaStream_t s) {
-    if (st == 1) return launch_cplx_for_length<float, float>(p, a, s);
-    if (st == 2) return launch_cplx_for_length<float, dd>(p, a, s);
-    return launch_cplx_for_length<double, double>(p, a, s);
+    if (st == 1) return launch_cplx_for_length<float, float, 8>(p, a, s);
+    if (st == 2) {
+        const TimeTables& t = p->t32;
+        if (CplxSmem<float, dd, 12>(p->Ns, t.L, t.bluestein, 1).total <= 227 * 1024)
+            return launch_cplx_for_length<float, dd, 12>(p, a, s);
+        return launch_cplx_for_length<float, dd, 8>(p, a, s);
+    }
+    return launch_cplx_for_length<double, double, 8>(p, a, s);
 }
