@@ -81,8 +81,8 @@ ORACLE_SAMPLE_N = 128
 # dominant kernel class as a fraction of its algorithmic bytes, from one ncu
 # capture of the same kernel on a 512^2 x 127 Dirichlet launch (traffic grows
 # in proportion to the unknowns, so the fraction carries to a full launch):
-# time_kernel_real's residual launch moved 775.2 MB for 799.0 MB algorithmic
-# (0.970), its operator launch 495.0 MB for 532.6 MB (0.929); the class mixes
+# time_kernel_real's residual launch moved 775.4 MB for 799.0 MB algorithmic
+# (0.970), its operator launch 495.5 MB for 532.6 MB (0.930); the class mixes
 # both kinds, so its traffic is reported as 0.95 of its algorithmic bytes per
 # launch.  An entry is removed whenever its kernel changes after the capture.
 NCU_TRAFFIC_FRACTION = {"time": 0.95}
