@@ -234,37 +234,54 @@ __device__ __forceinline__ uint32_t bf16_of_int(int d) {
     return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
 }
 
-// One warp per row of K float64 values (K a multiple of 64, rows of a 128-row
-// tile consecutive): the row exponent e (max|x| < 2^e, or fixed_e for every
-// row unless it is INT_MIN) into ex[r] (when ex is given), and the
-// nsl balanced 7-bit digits of x 2^{-e} into the packed slices, digit 0 the
-// most significant.  All arithmetic is on the binary64 encoding (integer
-// operations); a row holding a non-finite value gets NaN digits.
+// Eight rows of K float64 values per CTA of 256 threads (K a multiple of 64,
+// rows a multiple of 8): first every warp finds its row's exponent e
+// (max|x| < 2^e, or fixed_e for every row unless it is INT_MIN) into ex[r]
+// (when ex is given); then thread t splits chunk t / 8 (eight values) of row
+// t % 8 into nsl balanced 7-bit digits of x 2^{-e}, digit 0 the most
+// significant.  The eight rows of a chunk form one 128-byte row of 8x8 core
+// matrices in the packed layout and a warp covers four consecutive core
+// matrices, so every digit slice is written in contiguous 512-byte runs.  All
+// arithmetic is on the binary64 encoding (integer operations); a row holding a
+// non-finite value gets NaN digits.
 __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restrict__ in, long long rows, int K,
                                                          int nsl, uint16_t* __restrict__ out, long long slice_elems,
                                                          int* __restrict__ ex, int fixed_e) {
+    __shared__ int se[8], sbad[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long r = (long long)blockIdx.x * 8 + warp;
-    if (r >= rows) return;
-    const double2* x = reinterpret_cast<const double2*>(in + r * K);
-    const int nch = K >> 3;  // chunks of 8 values (16 bytes of bf16 per digit slice)
-    unsigned long long mx = 0;
-    for (int c = lane; c < nch; c += 32) {
+    const long long r0 = (long long)blockIdx.x * 8;
+    {
+        const long long r = r0 + warp;
+        int e = 0, bad = 0;
+        if (r < rows) {
+            const double2* x = reinterpret_cast<const double2*>(in + r * K);
+            unsigned long long mx = 0;
+            for (int c = lane; c < (K >> 1); c += 32) {
+                const double2 v = __ldg(x + c);
+                mx = max(mx, (unsigned long long)__double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFull);
+                mx = max(mx, (unsigned long long)__double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFull);
+            }
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const double2 v = __ldg(x + 4 * c + h);
-            mx = max(mx, (unsigned long long)__double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFull);
-            mx = max(mx, (unsigned long long)__double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFull);
+            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            bad = (mx >> 52) == 2047;
+            e = fixed_e != INT_MIN ? fixed_e : digit_row_exponent(mx);
+            if (lane == 0 && ex) ex[r] = bad ? 0 : e;
+        }
+        if (lane == 0) {
+            se[warp] = e;
+            sbad[warp] = bad;
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const bool bad = (mx >> 52) == 2047;
-    // max|x| < 2^e (fixed_e: one exponent given for every row, at least the row's)
-    const int e = fixed_e != INT_MIN ? fixed_e : digit_row_exponent(mx);
-    if (lane == 0 && ex) ex[r] = bad ? 0 : e;
+    __syncthreads();
+    const int rr = threadIdx.x & 7;
+    const long long r = r0 + rr;
+    if (r >= rows) return;
+    const int e = se[rr];
+    const bool bad = sbad[rr] != 0;
+    const double2* x = reinterpret_cast<const double2*>(in + r * K);
     const int KB = K >> 6;
-    for (int c = lane; c < nch; c += 32) {
+    const int nch = K >> 3;  // chunks of 8 values (16 bytes of bf16 per digit slice)
+    for (int c = threadIdx.x >> 3; c < nch; c += 32) {
         unsigned long long Y[8];
         unsigned neg = 0;
 #pragma unroll

@@ -122,6 +122,33 @@ __global__ void update_kernel(const double* __restrict__ V, long long ld, int k,
     }
 }
 
+// The same on 16-byte elements, two per thread and iteration (more loads in
+// flight per thread), for an even element count and 16-byte-aligned vectors.
+__global__ void __launch_bounds__(256) update_kernel_v(const double2* __restrict__ V, long long ld2, int k,
+                                                       const double* __restrict__ h, double2* __restrict__ x,
+                                                       long long n2) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n2; e += 2 * stride) {
+        const long long e1 = e + stride;
+        const bool two = e1 < n2;
+        double2 a = x[e];
+        double2 b = two ? x[e1] : make_double2(0.0, 0.0);
+        for (int i = 0; i < k; ++i) {
+            const double c = -h[i];
+            const double2 va = __ldg(V + (long long)i * ld2 + e);
+            a.x = fma(c, va.x, a.x);
+            a.y = fma(c, va.y, a.y);
+            if (two) {
+                const double2 vb = __ldg(V + (long long)i * ld2 + e1);
+                b.x = fma(c, vb.x, b.x);
+                b.y = fma(c, vb.y, b.y);
+            }
+        }
+        x[e] = a;
+        if (two) x[e1] = b;
+    }
+}
+
 // y = a x + b y; with b = 0, y is output only (it is not read: 0 * y would be
 // NaN where y holds a non-finite value left by an earlier use of the buffer)
 __global__ void axpby_kernel(long long n, double a, const double* x, double b, double* y) {
@@ -248,7 +275,12 @@ expd_status gm_update(expd_plan p, const double* V, long long ld, int k, const d
                       cudaStream_t s) {
     const long long n = eigen_elems(p);
     KProf kp(p, s, EXPD_K_GMRES, 8.0 * (k + 2) * (double)n, 2.0 * k * (double)n);
-    update_kernel<<<p->sm_count * 8, 256, 0, s>>>(V, ld, k, h_dev, w, n);
+    const bool vec = (n % 2 == 0) && (ld % 2 == 0) && ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
+    if (vec)
+        update_kernel_v<<<p->sm_count * 8, 256, 0, s>>>(reinterpret_cast<const double2*>(V), ld / 2, k, h_dev,
+                                                        reinterpret_cast<double2*>(w), n / 2);
+    else
+        update_kernel<<<p->sm_count * 8, 256, 0, s>>>(V, ld, k, h_dev, w, n);
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }
