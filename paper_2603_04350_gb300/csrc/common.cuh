@@ -217,6 +217,123 @@ EXPD_HD void fft_dif(T2* x, int log2n, const T2* tw, int ts, int sign, int lane,
     }
 }
 
+// Twiddle pairs of the radix-4 passes, one table per pass span h: entry k < h
+// holds (w4, w2) = (e^{-2 pi i k/(4h)}, e^{-2 pi i k/(2h)}), the two twiddles
+// a butterfly of that span reads, so one load fetches both and consecutive
+// lanes read consecutive entries (a strided read of the length-n table puts
+// up to 8 lanes of a half-warp on one bank in the middle passes).  The spans
+// are n/4, n/16, ... (both directions use the same set); the tables are stored
+// largest span first.
+template <typename T2>
+struct __align__(2 * sizeof(T2)) TwPair {
+    T2 w4, w2;
+};
+
+// offset of span h's table: the sizes of the larger spans before it
+__host__ __device__ constexpr int twp_offset(int n, int h) {
+    int off = 0;
+    for (int q = n >> 2; q > h; q >>= 2) off += q;
+    return off;
+}
+// entries of all the tables of length n
+__host__ __device__ constexpr int twp_entries(int n) {
+    int e = 0;
+    for (int q = n >> 2; q >= 1; q >>= 2) e += q;
+    return e;
+}
+
+// Fills the per-pass tables of length n (threads tid of nth) from a table
+// with tw[j * ts] = e^{-2 pi i j/n}.
+template <typename T2>
+EXPD_HD void twp_build(TwPair<T2>* twp, const T2* tw, int ts, int n, int tid, int nth) {
+    for (int h = n >> 2; h >= 1; h >>= 2)
+        for (int k = tid; k < h; k += nth) {
+            TwPair<T2> tp;
+            tp.w4 = tw[k * (n / (4 * h)) * ts];
+            tp.w2 = tw[k * (n / (2 * h)) * ts];
+            twp[twp_offset(n, h) + k] = tp;
+        }
+}
+
+// fft_dit / fft_dif reading their twiddles from the per-pass pair tables
+// (the same arithmetic in the same order)
+template <typename T2, int PAD = 0>
+EXPD_HD void fft_dit_tp(T2* x, int log2n, const TwPair<T2>* twp, int sign, int lane, int nlanes) {
+    const int n = 1 << log2n;
+    int s = 0;
+    if (log2n & 1) {
+        for (int b = lane; b < (n >> 1); b += nlanes) {
+            const T2 u = x[padi<PAD>(2 * b)], v = x[padi<PAD>(2 * b + 1)];
+            x[padi<PAD>(2 * b)] = cadd(u, v);
+            x[padi<PAD>(2 * b + 1)] = csub(u, v);
+        }
+        EXPD_SYNCWARP();
+        s = 1;
+    }
+    for (; s < log2n; s += 2) {
+        const int h = 1 << s;
+        const TwPair<T2>* tph = twp + twp_offset(n, h);
+        for (int g = lane; g < (n >> 2); g += nlanes) {
+            const int k = g & (h - 1);
+            const int i = ((g >> s) << (s + 2)) + k;
+            const TwPair<T2> tp = tph[k];
+            T2 w2 = tp.w2, w4 = tp.w4;
+            if (sign > 0) {
+                w2.y = -w2.y;
+                w4.y = -w4.y;
+            }
+            const T2 x0 = x[padi<PAD>(i)], x1 = cmul(x[padi<PAD>(i + h)], w2);
+            const T2 x2 = x[padi<PAD>(i + 2 * h)], x3 = cmul(x[padi<PAD>(i + 3 * h)], w2);
+            const T2 a0 = cadd(x0, x1), a1 = csub(x0, x1);
+            const T2 a2 = cmul(cadd(x2, x3), w4);
+            const T2 a3 = cmul_quarter(cmul(csub(x2, x3), w4), sign);
+            x[padi<PAD>(i)] = cadd(a0, a2);
+            x[padi<PAD>(i + 2 * h)] = csub(a0, a2);
+            x[padi<PAD>(i + h)] = cadd(a1, a3);
+            x[padi<PAD>(i + 3 * h)] = csub(a1, a3);
+        }
+        EXPD_SYNCWARP();
+    }
+}
+
+template <typename T2, int PAD = 0>
+EXPD_HD void fft_dif_tp(T2* x, int log2n, const TwPair<T2>* twp, int sign, int lane, int nlanes) {
+    const int n = 1 << log2n;
+    int s = log2n - 1;
+    for (; s >= 1; s -= 2) {
+        const int h = 1 << (s - 1);
+        const TwPair<T2>* tph = twp + twp_offset(n, h);
+        for (int g = lane; g < (n >> 2); g += nlanes) {
+            const int k = g & (h - 1);
+            const int i = ((g >> (s - 1)) << (s + 1)) + k;
+            const TwPair<T2> tp = tph[k];
+            T2 w2 = tp.w2, w4 = tp.w4;
+            if (sign > 0) {
+                w2.y = -w2.y;
+                w4.y = -w4.y;
+            }
+            const T2 x0 = x[padi<PAD>(i)], x1 = x[padi<PAD>(i + h)], x2 = x[padi<PAD>(i + 2 * h)],
+                     x3 = x[padi<PAD>(i + 3 * h)];
+            const T2 a0 = cadd(x0, x2), a1 = cadd(x1, x3);
+            const T2 a2 = cmul(csub(x0, x2), w4);
+            const T2 a3 = cmul_quarter(cmul(csub(x1, x3), w4), sign);
+            x[padi<PAD>(i)] = cadd(a0, a1);
+            x[padi<PAD>(i + h)] = cmul(csub(a0, a1), w2);
+            x[padi<PAD>(i + 2 * h)] = cadd(a2, a3);
+            x[padi<PAD>(i + 3 * h)] = cmul(csub(a2, a3), w2);
+        }
+        EXPD_SYNCWARP();
+    }
+    if (s == 0) {
+        for (int b = lane; b < (n >> 1); b += nlanes) {
+            const T2 u = x[padi<PAD>(2 * b)], v = x[padi<PAD>(2 * b + 1)];
+            x[padi<PAD>(2 * b)] = cadd(u, v);
+            x[padi<PAD>(2 * b + 1)] = csub(u, v);
+        }
+        EXPD_SYNCWARP();
+    }
+}
+
 // The same radix-4 passes for one warp of 32 lanes with the length known at
 // compile time (LOG2N) and the direction a template parameter: every pass and
 // lane loop unrolls and the strides, spans and twiddle steps become constants.

@@ -45,8 +45,13 @@ __global__ void row_kernel(const TIN* in, TOUT* out, long long rows, int NX,
     const int NH = NX >> 1;
     const int KX = NH + 1;
     PT2* W = reinterpret_cast<PT2*>(smem_raw);
-    PT2* buf = W + ((KX + 1) & ~1);
+    // per-pass twiddle pairs of the length-NH FFTs (consecutive lanes read
+    // consecutive entries), then the rows
+    TwPair<PT2>* twp = reinterpret_cast<TwPair<PT2>*>(W + ((KX + 1) & ~1));
+    PT2* buf = reinterpret_cast<PT2*>(twp + twp_entries(NH));
     for (int i = threadIdx.x; i < KX; i += blockDim.x) W[i] = Wg[i];
+    __syncthreads();
+    twp_build(twp, W, 2, NH, (int)threadIdx.x, (int)blockDim.x);
     pdl_wait();  // the rows come from the previous kernel
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, R = blockDim.x >> 5;
@@ -68,7 +73,7 @@ __global__ void row_kernel(const TIN* in, TOUT* out, long long rows, int NX,
             }
         }
         EXPD_SYNCWARP();
-        fft_dit<PT2, PAD>(s, log2NH, W, 2, KIND == 1 ? -1 : +1, lane, 32);  // natural order
+        fft_dit_tp<PT2, PAD>(s, log2NH, twp, KIND == 1 ? -1 : +1, lane, 32);  // natural order
         if constexpr (KIND == 0) {
             // z_n = x_{2n} + i x_{2n+1}
             TOUT* x = out + row * NX;
@@ -91,7 +96,7 @@ __global__ void row_kernel(const TIN* in, TOUT* out, long long rows, int NX,
                 s[padi<PAD>(n)] = z;
             }
             EXPD_SYNCWARP();
-            fft_dif<PT2, PAD>(s, log2NH, W, 2, -1, lane, 32);  // bit-reversed order
+            fft_dif_tp<PT2, PAD>(s, log2NH, twp, -1, lane, 32);  // bit-reversed order
         }
         // even/odd split: X_k = E_k + W^k O_k, k = 0..NH
         TOUT* X = out + row * KX;
@@ -120,8 +125,11 @@ __global__ void col_kernel(const TIN* __restrict__ in, TOUT* __restrict__ out, i
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PT2* W = reinterpret_cast<PT2*>(smem_raw);
     const int nw = NY >> 1;
-    PT2* buf = W + ((nw + 1) & ~1);
+    TwPair<PT2>* twp = reinterpret_cast<TwPair<PT2>*>(W + ((nw + 1) & ~1));  // per-pass twiddle pairs
+    PT2* buf = reinterpret_cast<PT2*>(twp + twp_entries(NY));
     for (int i = threadIdx.x; i < nw; i += blockDim.x) W[i] = Wg[i];
+    __syncthreads();
+    twp_build(twp, W, 1, NY, (int)threadIdx.x, (int)blockDim.x);
     pdl_wait();
     const long long base = (long long)blockIdx.y * NY * KX;
     const int kx0 = blockIdx.x * C;
@@ -136,7 +144,7 @@ __global__ void col_kernel(const TIN* __restrict__ in, TOUT* __restrict__ out, i
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (warp < C && kx0 + warp < KX) fft_dit(buf + warp * NYP, log2NY, W, 1, sign, lane, 32);
+    if (warp < C && kx0 + warp < KX) fft_dit_tp(buf + warp * NYP, log2NY, twp, sign, lane, 32);
     __syncthreads();
     for (int idx = threadIdx.x; idx < NY * C; idx += blockDim.x) {
         const int y = idx / C, c = idx - y * C, kx = kx0 + c;
@@ -926,7 +934,8 @@ expd_status launch_row_r4(expd_plan p, const TIN* in, TOUT* out, long long rows,
     const size_t per_row = (size_t)padded_len<(sizeof(PT2) >= 16)>(NH) * sizeof(PT2);
     int R = (int)std::max<size_t>(1, std::min<size_t>(8, (48 * 1024) / per_row));
     while (R > 1 && (rows + R - 1) / R < 2LL * p->sm_count) R >>= 1;  // small launches: more CTAs
-    const size_t smem = (size_t)((NH + 2) & ~1) * sizeof(PT2) + (size_t)R * per_row;
+    const size_t smem = (size_t)((NH + 2) & ~1) * sizeof(PT2) + (size_t)twp_entries(NH) * 2 * sizeof(PT2) +
+                        (size_t)R * per_row;
     auto kern = row_kernel<PT, TIN, TOUT, KIND>;
     if (smem > 48 * 1024)
         EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));
@@ -1019,7 +1028,8 @@ expd_status launch_col(expd_plan p, const TIN* in, TOUT* out, int nslices, int s
     int C = (int)std::max<size_t>(1, std::min<size_t>(cmax, (64 * 1024) / per_col));
     // small launches (a slice or two): fewer columns per CTA, more CTAs
     while (C > 1 && (long long)((KX + C - 1) / C) * nslices < 2LL * p->sm_count) C >>= 1;
-    const size_t smem = (size_t)(((NY >> 1) + 1) & ~1) * sizeof(PT2) + (size_t)C * per_col;
+    const size_t smem = (size_t)(((NY >> 1) + 1) & ~1) * sizeof(PT2) + (size_t)twp_entries(NY) * 2 * sizeof(PT2) +
+                        (size_t)C * per_col;
     auto kern = col_kernel<PT, TIN, TOUT>;
     if (smem > 48 * 1024)
         EXPD_CUDA_TRY(smem_allow((const void*)kern, smem));

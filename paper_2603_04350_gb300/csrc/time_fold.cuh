@@ -9,31 +9,6 @@
 
 namespace expd_time {
 
-// Twiddle pairs of the radix-4 passes, one table per pass span h: entry k < h
-// holds (w4, w2) = (e^{-2 pi i k/(4h)}, e^{-2 pi i k/(2h)}), the two twiddles
-// a butterfly of that span reads, so one load fetches both and consecutive
-// lanes read consecutive entries (a strided read of the length-n table puts
-// up to 8 lanes of a half-warp on one bank in the middle passes).  The spans
-// are n/4, n/16, ... (both directions use the same set); the tables are stored
-// largest span first.
-template <typename T2>
-struct __align__(2 * sizeof(T2)) TwPair {
-    T2 w4, w2;
-};
-
-// offset of span h's table: the sizes of the larger spans before it
-__host__ __device__ constexpr int twp_offset(int n, int h) {
-    int off = 0;
-    for (int q = n >> 2; q > h; q >>= 2) off += q;
-    return off;
-}
-// entries of all the tables of length n
-__host__ __device__ constexpr int twp_entries(int n) {
-    int e = 0;
-    for (int q = n >> 2; q >= 1; q >>= 2) e += q;
-    return e;
-}
-
 // Bluestein passes of the real kernel (one warp, length 2^LOG2N, the
 // swizzled buffer map padi<2>), with the pointwise steps of precond_step_a /
 // precond_step_c folded in.  A Bluestein input is zero from Ns <= L/2 on, so
