@@ -24,6 +24,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "plan.h"
 #include "time_column.cuh"
@@ -157,10 +159,14 @@ void pinned_release(double* q, size_t ndoubles) {
     g_pin_class[c].push_back(q);
 }
 
+// guard words after a buffer (EXPD_CANARY=1): 256 bytes of this pattern
+constexpr size_t CANARY_BYTES = 256;
+constexpr unsigned char CANARY_BYTE = 0xA5;
+
 expd_status dalloc(expd_plan p, void** ptr, size_t bytes, const char* what) {
     *ptr = nullptr;
     if (bytes == 0) return EXPD_OK;
-    cudaError_t e = plan_malloc(p, ptr, bytes);
+    cudaError_t e = plan_malloc(p, ptr, bytes + (p->canary ? CANARY_BYTES : 0));
     if (e != cudaSuccess) {
         *ptr = nullptr;
         cudaGetLastError();
@@ -168,6 +174,12 @@ expd_status dalloc(expd_plan p, void** ptr, size_t bytes, const char* what) {
                                             std::to_string(bytes) + " bytes): " + cudaGetErrorString(e));
     }
     p->bytes += bytes;
+    if (p->canary) {
+        e = cudaMemsetAsync(static_cast<char*>(*ptr) + bytes, CANARY_BYTE, CANARY_BYTES, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+        if (e != cudaSuccess) return expd_cuda_fail(e, "cudaMemsetAsync(canary)", __FILE__, __LINE__);
+        p->canaries.emplace_back(*ptr, bytes);
+    }
     // debugging aid: all-ones bytes are a NaN in every floating type, so a
     // read of a buffer before it is written turns the result non-finite
     if (p->poison) {
@@ -176,6 +188,21 @@ expd_status dalloc(expd_plan p, void** ptr, size_t bytes, const char* what) {
         if (e != cudaSuccess) return expd_cuda_fail(e, "cudaMemsetAsync(poison)", __FILE__, __LINE__);
     }
     return EXPD_OK;
+}
+
+// the kernel classes of expd_timing, for the NVTX range of each launch
+const char* kclass_name(int c) {
+    static const char* names[EXPD_NUM_KCLASS] = {"time", "fft_col", "fft_row", "dst", "gmres",
+                                                 "pointwise", "reduce", "time32", "fft_col32", "fft_row32",
+                                                 "timedd", "fft_coldd", "fft_rowdd", "dst_tc", "dst_split"};
+    return c >= 0 && c < EXPD_NUM_KCLASS ? names[c] : "expd";
+}
+
+// NVTX ranges of a solver call's phases (set-up, iterations, output): one
+// open range per plan, ended when the next phase starts or the call ends
+void nvtx_phase(expd_plan p, const char* name) {
+    if (p->nvtx_phase) nvtxRangeEnd((nvtxRangeId_t)p->nvtx_phase);
+    p->nvtx_phase = name ? (unsigned long long)nvtxRangeStartA(name) : 0ull;
 }
 
 template <typename T>
@@ -388,6 +415,7 @@ void info_reset(expd_info* info) {
 // info report); call_end waits for event 3 and reports the three intervals.
 expd_status call_begin(expd_plan p, expd_info* info, cudaStream_t s) {
     info_reset(info);
+    nvtx_phase(p, "expd: set-up");
     p->call_t0 = std::chrono::steady_clock::now();
     p->call_cancelled = 0;
     if (!info) return EXPD_OK;
@@ -398,6 +426,7 @@ expd_status call_begin(expd_plan p, expd_info* info, cudaStream_t s) {
 }
 
 expd_status call_mark(expd_plan p, expd_info* info, int k, cudaStream_t s) {
+    nvtx_phase(p, k == 1 ? "expd: iterations" : "expd: output");
     if (info) EXPD_CUDA_TRY(cudaEventRecord(p->phase_ev[k], s));
     return EXPD_OK;
 }
@@ -405,6 +434,8 @@ expd_status call_mark(expd_plan p, expd_info* info, int k, cudaStream_t s) {
 // Ends a call that returns `result`: phase times into info; a failure to read
 // them only replaces an OK result.
 expd_status call_end(expd_plan p, expd_info* info, cudaStream_t s, expd_status result) {
+    nvtx_phase(p, nullptr);
+    if (p->canary && result == EXPD_OK) result = canary_check(p, s);
     if (!info) return result;
     cudaError_t e = cudaEventRecord(p->phase_ev[3], s);
     if (e == cudaSuccess) e = cudaEventSynchronize(p->phase_ev[3]);
@@ -506,6 +537,7 @@ expd_status expd_fail(expd_status s, const std::string& msg) {
 KProf::KProf(expd_plan p_, cudaStream_t s_, int cls_, double bytes_, double flops_)
     : p(p_), s(s_), cls(cls_), bytes(bytes_), flops(flops_) {
     ++p->launches;
+    nvtxRangePushA(kclass_name(cls));
     if (!p->timing) return;
     while (p->events.size() < p->ev_used + 2) {
         cudaEvent_t e;
@@ -521,9 +553,25 @@ KProf::KProf(expd_plan p_, cudaStream_t s_, int cls_, double bytes_, double flop
 }
 
 KProf::~KProf() {
+    nvtxRangePop();
     if (e0 < 0) return;
     cudaEventRecord(p->events[e0 + 1], s);
     p->recs.push_back({cls, e0, bytes, flops});
+}
+
+expd_status canary_check(expd_plan p, cudaStream_t s) {
+    if (!p->canary) return EXPD_OK;
+    std::vector<unsigned char> tail(CANARY_BYTES);
+    for (const auto& c : p->canaries) {
+        EXPD_CUDA_TRY(cudaMemcpyAsync(tail.data(), static_cast<const char*>(c.first) + c.second, CANARY_BYTES,
+                                      cudaMemcpyDeviceToHost, s));
+        EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+        for (unsigned char b : tail)
+            if (b != CANARY_BYTE)
+                return expd_fail(EXPD_ERR_CUDA, "guard words after a workspace buffer of " +
+                                                    std::to_string(c.second) + " bytes were overwritten");
+    }
+    return EXPD_OK;
 }
 
 expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_operator* op, double dt, int Nt,
@@ -688,6 +736,8 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     p->no_graphs = gr && strcmp(gr, "0") == 0;
     const char* po = getenv("EXPD_POISON");
     p->poison = po && strcmp(po, "1") == 0;
+    const char* ca = getenv("EXPD_CANARY");
+    p->canary = ca && strcmp(ca, "1") == 0;
     // EXPD_TIME_CPLX=0: complex columns take the generic shared-memory kernel
     // instead of the fixed-length one (both compute the same; tests)
     const char* tc = getenv("EXPD_TIME_CPLX");
@@ -1760,6 +1810,11 @@ static expd_status ensure_krylov(expd_plan p, int nvec) {
     const size_t n = (size_t)eigen_elems(p);
     if (p->gm && p->gm_vecs >= nvec) return EXPD_OK;
     if (p->gm) {
+        for (size_t i = 0; i < p->canaries.size(); ++i)
+            if (p->canaries[i].first == p->gm) {
+                p->canaries.erase(p->canaries.begin() + i);
+                break;
+            }
         plan_free(p, p->gm);
         p->bytes -= ((size_t)p->gm_vecs * n + krylov_hblock(p)) * sizeof(double);
         p->gm = nullptr;

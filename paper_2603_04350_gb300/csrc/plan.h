@@ -8,6 +8,7 @@
 #include <atomic>
 #include <chrono>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "expd.h"
@@ -170,6 +171,9 @@ struct expd_plan_s {
     long long fp_solves = 0;      // fixed-point solves run on this plan
     int no_graphs = 0;            // 1: launch kernel by kernel (EXPD_GRAPHS=0)
     int poison = 0;               // 1: fill every new device buffer with NaN bytes (EXPD_POISON=1)
+    int canary = 0;               // 1: guard words after every workspace buffer, checked after each call (EXPD_CANARY=1)
+    std::vector<std::pair<void*, size_t>> canaries;  // (buffer, its usable bytes) of the guarded buffers
+    unsigned long long nvtx_phase = 0;  // the open NVTX range of a solver call's phase (0: none)
     int no_cplx_time = 0;         // 1: complex columns take the generic time kernel (EXPD_TIME_CPLX=0)
     int no_reg_time = 0;          // 1 forces the shared-memory time kernel (tests)
     int no_real_time = 0;         // 1: real columns take the generic kernel (EXPD_TIME_REAL=0, tests)
@@ -223,6 +227,10 @@ cudaError_t plan_bind_stream(expd_plan p, cudaStream_t s);
 // set by one thread would undercut another thread's launch.  Fails for
 // requests above the device maximum.
 cudaError_t smem_allow(const void* kern, size_t smem);
+
+// Debug aid (EXPD_CANARY=1): reports EXPD_ERR_CUDA when a guard word after a
+// workspace buffer was overwritten (a write past the buffer's end).
+expd_status canary_check(expd_plan p, cudaStream_t s);
 
 struct KProf {
     expd_plan p;

@@ -1,4 +1,5 @@
-"""Solves with every plan buffer filled with NaN bytes at allocation (marked gpu).
+"""Debug modes on the GPU (marked gpu): solves with every plan buffer filled
+with NaN bytes at allocation, and with guard words after every buffer.
 
 EXPD_POISON=1 makes the library fill each new device buffer with all-ones
 bytes, a NaN in every floating type.  A kernel that reads a buffer (or a part
@@ -101,3 +102,41 @@ def test_poisoned_buffers_allen_cahn(expd, monkeypatch, order, prec):
     out = U.cpu().numpy()
     assert np.isfinite(out).all()
     assert O.rel_error(out, O.sequential_solve(O.spec_of(p), u0)[1:]) < p.tol
+
+
+# EXPD_CANARY=1 puts 256 guard bytes after every workspace buffer and checks
+# them after each solver call: no kernel writes past the end of a buffer.
+@pytest.mark.parametrize("prec", ("fp64", "mixed"))
+@pytest.mark.parametrize("solver", ("gmres", "bicgstab", "fp"))
+def test_canary_guard_words_stay_intact_dirichlet(expd, monkeypatch, prec, solver):
+    monkeypatch.setenv("EXPD_CANARY", "1")
+    p = I.HEAT_DIRICHLET_1024.with_(n=(256, 256), Nt=32, dt=0.1 / 32)      # tensor-core sine transforms (mixed)
+    u0, f = I.make_inputs(p)
+    precision = expd.PREC_FP64 if prec == "fp64" else expd.PREC_MIXED
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, precision=precision, max_iter=200)) as plan:
+        fn = {"gmres": plan.solve_gmres, "bicgstab": plan.solve_bicgstab, "fp": plan.solve_fp}[solver]
+        fn(torch.from_numpy(u0).to(DEV), torch.from_numpy(f).to(DEV), U)
+    assert O.rel_error(U.cpu().numpy(), _sequential(p)) < p.tol
+
+
+@pytest.mark.parametrize("prec", ("fp64", "mixed"))
+def test_canary_guard_words_stay_intact_allen_cahn(expd, monkeypatch, prec):
+    monkeypatch.setenv("EXPD_CANARY", "1")
+    p = I.ALLEN_CAHN_512_S6.with_(n=(64, 64), Nt=40)
+    u0 = I.make_u0(p)
+    precision = expd.PREC_FP64 if prec == "fp64" else expd.PREC_MIXED
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, precision=precision, max_iter=200)) as plan:
+        plan.solve_fp(torch.from_numpy(u0).to(DEV), None, U)
+    assert O.rel_error(U.cpu().numpy(), O.sequential_solve(O.spec_of(p), u0)[1:]) < p.tol
+
+
+def test_canary_guard_words_stay_intact_complex_state(expd, monkeypatch):
+    monkeypatch.setenv("EXPD_CANARY", "1")
+    p = I.SCHRODINGER_2D.with_(Nt=20)
+    u0, f = I.make_inputs(p)
+    U = torch.empty((p.Nt,) + p.n, dtype=torch.complex128, device=DEV)
+    with expd.plan_create(expd.spec_from_problem(p, max_iter=50)) as plan:
+        plan.solve_gmres(torch.from_numpy(u0).to(DEV), None, U)
+    assert O.rel_error(U.cpu().numpy(), O.sequential_solve(O.spec_of(p), u0, f)[1:]) < 1e-10
