@@ -393,7 +393,9 @@ enum {
     EXPD_K_FFT_ROWDD = 12, /* double-float real FFT along the contiguous axis                */
     EXPD_K_DST_TC = 13,   /* Dirichlet DST-I on the tensor cores: split-BF16 digit products   */
     EXPD_K_DST_SPLIT = 14, /* Dirichlet DST-I on the tensor cores: rows cut into bf16 digits  */
-    EXPD_NUM_KCLASS = 15
+    EXPD_K_TIME_TC = 15,  /* time kernel on the tensor cores (real columns, float32           */
+                          /* preconditioner, float64 iterate; Steps (a), (c) as products)     */
+    EXPD_NUM_KCLASS = 16
 };
 
 typedef struct {

@@ -194,7 +194,7 @@ expd_status dalloc(expd_plan p, void** ptr, size_t bytes, const char* what) {
 const char* kclass_name(int c) {
     static const char* names[EXPD_NUM_KCLASS] = {"time", "fft_col", "fft_row", "dst", "gmres",
                                                  "pointwise", "reduce", "time32", "fft_col32", "fft_row32",
-                                                 "timedd", "fft_coldd", "fft_rowdd", "dst_tc", "dst_split"};
+                                                 "timedd", "fft_coldd", "fft_rowdd", "dst_tc", "dst_split", "time_tc"};
     return c >= 0 && c < EXPD_NUM_KCLASS ? names[c] : "expd";
 }
 
@@ -219,7 +219,7 @@ void free_plan(expd_plan p) {
     void* bufs[] = {p->E,    p->PHI64, p->PHI32, p->PHIdd, p->C64,  p->C32, p->Cdd, p->Wxdd, p->Wydd, p->gamdd, p->oscdd, p->Wx64, p->Wx32,   p->Wy64,    p->Wy32,    p->Sx,        p->Sy, p->SxT, p->SyT, p->Dtx, p->Dty,
                     p->Uh,   p->Fh,   p->Sh,     p->fh,      p->NL64,    p->NL32,      p->work64,
                     p->work32, p->startphys, p->partial, p->redout, p->stage, p->gm, p->U32, p->F32,
-                    p->tc_S, p->tc_pack, p->tc_ex};
+                    p->tc_S, p->tc_pack, p->tc_ex, p->tt_tab};
     for (void* b : bufs) plan_free(p, b);
     for (auto& g : p->sweep_graph)
         if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -732,6 +732,10 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
     // kernel instead of the real-column one (both compute the same; tests)
     const char* tr = getenv("EXPD_TIME_REAL");
     p->no_real_time = tr && strcmp(tr, "0") == 0;
+    // EXPD_TIME_TC=0: real columns keep the FFT time kernels instead of the
+    // tensor-core one (both compute the same preconditioner; comparisons)
+    const char* ttc = getenv("EXPD_TIME_TC");
+    p->no_tc_time = ttc && strcmp(ttc, "0") == 0;
     const char* gr = getenv("EXPD_GRAPHS");
     p->no_graphs = gr && strcmp(gr, "0") == 0;
     const char* po = getenv("EXPD_POISON");
@@ -1330,6 +1334,7 @@ expd_status expd_plan_create(const expd_grid* grid, const expd_operator* op, dou
         if (!p->redhost) st = expd_fail(EXPD_ERR_OOM, "pinned host memory for the norms");
     }
     if (st == EXPD_OK) st = time_tables_build(p, s);
+    if (st == EXPD_OK) st = time_tc_setup(p, s);
     if (st != EXPD_OK) {
         free_plan(p);
         return st;
@@ -1386,6 +1391,7 @@ expd_status expd_plan_footprint_bytes(const expd_grid* grid, const expd_operator
         b += e * (th.tw.size()) + 16 + e * Ns + 16 + 2 * g * Ns;
         if (th.bluestein) b += e * Ns + 16 + 2 * (e * th.L + 16);
     }
+    b += time_tc_bytes(p);                                                  // tensor-core time tables
     int grid_t = 0;
     st = time_grid_for(p, &grid_t);
     if (st != EXPD_OK) return st;

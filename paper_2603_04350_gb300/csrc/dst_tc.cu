@@ -48,9 +48,12 @@
 
 #include "common.cuh"
 #include "dst_digits.cuh"
+#include "tc_ptx.cuh"
 #include "plan.h"
 
 namespace {
+
+using namespace expd_tc;
 
 constexpr int TC_BM = 128;                          // rows per tile (TMEM lanes)
 constexpr int TC_BK = 64;                           // K per stage (bf16: 128 bytes per row)
@@ -96,40 +99,13 @@ struct TcArgs {
     unsigned char gstart[33], gw[32];
     int* err;                 // set to 1 when a pipeline wait gave up
     const volatile int* cancel;  // mapped host word: nonzero asks every wait to give up at once
+    // folded transforms: a second product of the same shape (A2 B2^T, the odd
+    // rows of S against the differences), and the output column map: column c
+    // of product q goes to output column c * ocs + q of Nout
+    const uint16_t* A2;
+    const uint16_t* B2;
+    int nprob, ocs, Nout;
 };
-
-// ------------------------------------------------------------ PTX helpers ----
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
 
 // Waits for the phase of the given parity; gives up after TC_WAIT_NS, when
 // another role of the CTA has given up (abort != 0) or when the host cancels
@@ -148,39 +124,6 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const vola
         }
     }
 }
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_alloc(uint32_t slot, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_relinquish() {
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-// the mbarrier arrives once every MMA this thread issued so far has completed
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-// D (TMEM, 128 lanes x N float32 columns) (+)= A (128 x 16) B^T (16 x N)
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                       uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
 
 // acc, hi and lo: three 32-column loads of this warp's 32 lanes, then the wait
 __device__ __forceinline__ void tm_ld3(uint32_t ta, uint32_t th, uint32_t tl, uint32_t (&a)[32], uint32_t (&h)[32],
@@ -234,8 +177,8 @@ __device__ __forceinline__ uint32_t bf16_of_int(int d) {
     return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
 }
 
-// Eight rows of K float64 values per CTA of 256 threads (K a multiple of 64,
-// rows a multiple of 8): first every warp finds its row's exponent e
+// Eight rows of K float64 values (row r at in + r lda) per CTA of 256 threads
+// (K a multiple of 64, rows a multiple of 8): first every warp finds its row's exponent e
 // (max|x| < 2^e, or fixed_e for every row unless it is INT_MIN) into ex[r]
 // (when ex is given); then thread t splits chunk t / 8 (eight values) of row
 // t % 8 into nsl balanced 7-bit digits of x 2^{-e}, digit 0 the most
@@ -245,8 +188,8 @@ __device__ __forceinline__ uint32_t bf16_of_int(int d) {
 // arithmetic is on the binary64 encoding (integer operations); a row holding a
 // non-finite value gets NaN digits.
 __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restrict__ in, long long rows, int K,
-                                                         int nsl, uint16_t* __restrict__ out, long long slice_elems,
-                                                         int* __restrict__ ex, int fixed_e) {
+                                                         long long lda, int nsl, uint16_t* __restrict__ out,
+                                                         long long slice_elems, int* __restrict__ ex, int fixed_e) {
     __shared__ int se[8], sbad[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long r0 = (long long)blockIdx.x * 8;
@@ -254,7 +197,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restric
         const long long r = r0 + warp;
         int e = 0, bad = 0;
         if (r < rows) {
-            const double2* x = reinterpret_cast<const double2*>(in + r * K);
+            const double2* x = reinterpret_cast<const double2*>(in + r * lda);
             unsigned long long mx = 0;
             for (int c = lane; c < (K >> 1); c += 32) {
                 const double2 v = __ldg(x + c);
@@ -278,7 +221,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restric
     if (r >= rows) return;
     const int e = se[rr];
     const bool bad = sbad[rr] != 0;
-    const double2* x = reinterpret_cast<const double2*>(in + r * K);
+    const double2* x = reinterpret_cast<const double2*>(in + r * lda);
     const int KB = K >> 6;
     const int nch = K >> 3;  // chunks of 8 values (16 bytes of bf16 per digit slice)
     for (int c = threadIdx.x >> 3; c < nch; c += 32) {
@@ -304,6 +247,93 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restric
                 w[t >> 1] |= hb << (16 * (t & 1));
             }
             *reinterpret_cast<uint4*>(o + (long long)i * slice_elems) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// Folded rows for the symmetric half of the DST-I: S[j][n-1-k] = (-1)^j S[j][k]
+// (sin(pi (j+1)(n-k)/(n+1)) = (-1)^j sin(pi (j+1)(k+1)/(n+1))), so output j of
+// a row x is sum_{k < n/2} S[j][k] (x_k + (-1)^j x_{n-1-k}) for even n.  Eight
+// rows of n float64 values per CTA: the row exponent e over all n values (as
+// split_rows_kernel), then thread t takes chunk t / 8 (eight values, k =
+// 8c..8c+7) of row t % 8 and its mirror (x_{n-1-k}), cuts both into digits with
+// the row's exponent and writes the digit sums (to u) and differences (to v):
+// integers with |d_0| <= 256 and |d_i| <= 128, exact in bf16; a product of
+// n/2 of them with S's digits sums to at most (n/2) 256 128 = 2^24 for n =
+// 1024, the bound of the unfolded product, so the same accumulator groups
+// hold them exactly.
+__global__ void __launch_bounds__(256) split_fold_kernel(const double* __restrict__ in, long long rows, int n,
+                                                         int nsl, uint16_t* __restrict__ out_u,
+                                                         uint16_t* __restrict__ out_v, long long slice_elems,
+                                                         int* __restrict__ ex) {
+    __shared__ int se[8], sbad[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long r0 = (long long)blockIdx.x * 8;
+    {
+        const long long r = r0 + warp;
+        int e = 0, bad = 0;
+        if (r < rows) {
+            const double2* x = reinterpret_cast<const double2*>(in + r * n);
+            unsigned long long mx = 0;
+            for (int c = lane; c < (n >> 1); c += 32) {
+                const double2 v = __ldg(x + c);
+                mx = max(mx, (unsigned long long)__double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFull);
+                mx = max(mx, (unsigned long long)__double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFull);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            bad = (mx >> 52) == 2047;
+            e = digit_row_exponent(mx);
+            if (lane == 0 && ex) ex[r] = bad ? 0 : e;
+        }
+        if (lane == 0) {
+            se[warp] = e;
+            sbad[warp] = bad;
+        }
+    }
+    __syncthreads();
+    const int rr = threadIdx.x & 7;
+    const long long r = r0 + rr;
+    if (r >= rows) return;
+    const int e = se[rr];
+    const bool bad = sbad[rr] != 0;
+    const double* x = in + r * n;
+    const int K = n >> 1, KB = K >> 6;
+    const int nch = K >> 3;
+    for (int c = threadIdx.x >> 3; c < nch; c += 32) {
+        unsigned long long Y[8], Z[8];
+        unsigned neg = 0, negz = 0;
+        const double2* xa = reinterpret_cast<const double2*>(x + 8 * c);
+        const double2* xb = reinterpret_cast<const double2*>(x + n - 8 * c - 8);  // x_{n-1-k} for k = 8c+7 .. 8c
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const double2 v = __ldg(xa + h), w = __ldg(xb + h);
+            unsigned n0, n1, m0, m1;
+            Y[2 * h] = digit_magnitude((unsigned long long)__double_as_longlong(v.x), e, nsl, &n0);
+            Y[2 * h + 1] = digit_magnitude((unsigned long long)__double_as_longlong(v.y), e, nsl, &n1);
+            neg |= (n0 << (2 * h)) | (n1 << (2 * h + 1));
+            // w.x = x_{n-8c-8+2h} pairs with k = 8c + 7 - 2h, w.y with k = 8c + 6 - 2h
+            Z[7 - 2 * h] = digit_magnitude((unsigned long long)__double_as_longlong(w.x), e, nsl, &m0);
+            Z[6 - 2 * h] = digit_magnitude((unsigned long long)__double_as_longlong(w.y), e, nsl, &m1);
+            negz |= (m0 << (7 - 2 * h)) | (m1 << (6 - 2 * h));
+        }
+        uint16_t* ou = out_u + packed_offset(r, 8 * c, KB);
+        uint16_t* ov = out_v + packed_offset(r, 8 * c, KB);
+        for (int i = nsl - 1; i >= 0; --i) {
+            uint32_t wu[4] = {0u, 0u, 0u, 0u}, wv[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                int d = digit_next(&Y[t], i);
+                if ((neg >> t) & 1u) d = -d;
+                int dz = digit_next(&Z[t], i);
+                if ((negz >> t) & 1u) dz = -dz;
+                const uint32_t hu = bad ? 0x7FC0u : bf16_of_int(d + dz);
+                const uint32_t hv = bad ? 0x7FC0u : bf16_of_int(d - dz);
+                wu[t >> 1] |= hu << (16 * (t & 1));
+                wv[t >> 1] |= hv << (16 * (t & 1));
+            }
+            *reinterpret_cast<uint4*>(ou + (long long)i * slice_elems) = make_uint4(wu[0], wu[1], wu[2], wu[3]);
+            *reinterpret_cast<uint4*>(ov + (long long)i * slice_elems) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
     }
 }
@@ -386,7 +416,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
     const uint32_t tmem = *tmem_slot;
 
     const int nct = a.N / BN;
-    const long long ntiles = (long long)(a.rows / TC_BM) * nct;
+    const int npc = a.nprob * nct;  // tiles per row tile: the products' column tiles
+    const long long ntiles = (long long)(a.rows / TC_BM) * npc;
     const int KB = a.KB;
 
     if (warp == 0) {
@@ -395,14 +426,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
             uint32_t it = 0;
             bool ok = true;
             for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const long long rt = t / nct;
-                const int ct = (int)(t - rt * nct);
+                const long long rt = t / npc;
+                const int pc_ = (int)(t - rt * npc), q = pc_ / nct, ct = pc_ - q * nct;
                 // B: packed 128-row tiles; a 64-column tile is the lower or
                 // upper half (row groups 0-7 or 8-15: the first or second 8 KB)
                 const long long boff = (long long)(ct * BN / 128) * KB * TC_TILE_ELEMS + (long long)((ct * BN) % 128) * TC_BK;
+                const uint16_t* Aq = q ? a.A2 : a.A;
+                const uint16_t* Bq = q ? a.B2 : a.B;
                 for (int p = 0; p < a.npairs && ok; ++p) {
-                    const uint16_t* Ab = a.A + a.pi[p] * a.a_slice + rt * KB * TC_TILE_ELEMS;
-                    const uint16_t* Bb = a.B + a.pj[p] * a.b_slice + boff;
+                    const uint16_t* Ab = Aq + a.pi[p] * a.a_slice + rt * KB * TC_TILE_ELEMS;
+                    const uint16_t* Bb = Bq + a.pj[p] * a.b_slice + boff;
                     for (int kb = 0; kb < KB; ++kb, ++it) {
                         const int s = (int)(it % TC_STAGES);
                         const uint32_t ph = (it / TC_STAGES) & 1u;
@@ -481,8 +514,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
         uint32_t pc = 0;
         bool ok = true;
         for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const long long rt = t / nct;
-            const int ct = (int)(t - rt * nct);
+            const long long rt = t / npc;
+            const int pc_ = (int)(t - rt * npc), q = pc_ / nct, ct = pc_ - q * nct;
             for (int g = 0; g < a.ngroups && ok; ++g, ++pc) {
                 const int b = (int)(pc % TC_NACC);
                 // every lane waits; the warp goes on only together (the TMEM
@@ -535,14 +568,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
             const long long slc = row / a.R;
             const int rin = (int)(row - slc * a.R);
             const int E = a.ea[row] + a.eb;
-            double* o = a.out + slc * (long long)a.R * a.N + (long long)(ct * BN + half * (BN / 2)) * a.R + rin;
+            const long long ostep = (long long)a.ocs * a.R;
+            double* o = a.out + slc * (long long)a.R * a.Nout + (long long)(ct * BN + half * (BN / 2)) * ostep +
+                        (long long)q * a.R + rin;
 #pragma unroll 1
             for (int c = 0; c < CHUNKS; ++c) {
                 uint32_t h[32], l[32];
                 tm_ld2(thi + 32u * c, tlo + 32u * c, h, l);
 #pragma unroll
                 for (int e = 0; e < 32; ++e)
-                    o[(long long)(32 * c + e) * a.R] = scaled_sum(__uint_as_float(h[e]), __uint_as_float(l[e]), E);
+                    o[(long long)(32 * c + e) * ostep] = scaled_sum(__uint_as_float(h[e]), __uint_as_float(l[e]), E);
             }
         }
         if (!ok) {
@@ -577,21 +612,40 @@ expd_status tc_dalloc(expd_plan p, void** ptr, size_t bytes, const char* what) {
     return EXPD_OK;
 }
 
-expd_status split_rows(expd_plan p, const double* in, long long rows, int K, uint16_t* out, long long slice_elems,
-                       int* ex, int fixed_e, cudaStream_t s) {
+expd_status split_rows(expd_plan p, const double* in, long long rows, int K, long long lda, uint16_t* out,
+                       long long slice_elems, int* ex, int fixed_e, cudaStream_t s) {
     const int nsl = p->tc_nsl;
     KProf kp(p, s, EXPD_K_DST_SPLIT, (double)rows * K * (8.0 + 2.0 * nsl) + 4.0 * rows, 0.0);
-    split_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(in, rows, K, nsl, out, slice_elems, ex, fixed_e);
+    split_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(in, rows, K, lda, nsl, out, slice_elems, ex, fixed_e);
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }
 
-// out (transposed within slices of R rows) = A B^T over the plan's digit pairs
+// rows of n values -> digit sums (u) and differences (v) of mirrored halves
+expd_status split_fold(expd_plan p, const double* in, long long rows, int n, uint16_t* out_u, uint16_t* out_v,
+                       long long slice_elems, int* ex, cudaStream_t s) {
+    const int nsl = p->tc_nsl;
+    KProf kp(p, s, EXPD_K_DST_SPLIT, (double)rows * n * (8.0 + 2.0 * nsl) + 4.0 * rows, 0.0);
+    split_fold_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(in, rows, n, nsl, out_u, out_v, slice_elems, ex);
+    EXPD_CUDA_TRY(cudaGetLastError());
+    return EXPD_OK;
+}
+
+// out (transposed within slices of R rows) = A B^T over the plan's digit pairs;
+// folded (A2, B2 given): out's even columns A B^T, its odd ones A2 B2^T, each
+// product N = K wide with digit sums of twice the unfolded bound (kbound = 2 K)
 expd_status mma_pass(expd_plan p, const uint16_t* A, const int* ea, long long rows, int R, const uint16_t* B,
-                     int eb, int N, int K, double* out, cudaStream_t s) {
+                     int eb, int N, int K, double* out, cudaStream_t s, const uint16_t* A2 = nullptr,
+                     const uint16_t* B2 = nullptr) {
     TcArgs a = {};
+    const bool fold = A2 != nullptr;
     a.A = A;
     a.B = B;
+    a.A2 = fold ? A2 : A;
+    a.B2 = fold ? B2 : B;
+    a.nprob = fold ? 2 : 1;
+    a.ocs = fold ? 2 : 1;
+    a.Nout = fold ? 2 * N : N;
     a.ea = ea;
     a.eb = eb;
     a.out = out;
@@ -603,16 +657,16 @@ expd_status mma_pass(expd_plan p, const uint16_t* A, const int* ea, long long ro
     a.KB = K / TC_BK;
     const int nsl = p->tc_nsl;
     int np = 0, ng = 0;
-    tc_groups(nsl, K, &np, &ng, a.pi, a.pj, a.gstart, a.gw);
+    tc_groups(nsl, fold ? 2 * K : K, &np, &ng, a.pi, a.pj, a.gstart, a.gw);
     a.npairs = np;
     a.ngroups = ng;
     a.err = p->tc_err;
     a.cancel = p->cancel_dev;
-    const int bn = (p->kernel_flags & EXPD_KF_DST_N64) ? 64 : 128;
-    const long long ntiles = (rows / TC_BM) * (N / bn);
+    const int bn = (p->kernel_flags & EXPD_KF_DST_N64) || N % 128 != 0 ? 64 : 128;
+    const long long ntiles = (rows / TC_BM) * (N / bn) * a.nprob;
     const int grid = (int)std::min<long long>(ntiles, (long long)p->sm_count);
-    KProf kp(p, s, EXPD_K_DST_TC, 2.0 * nsl * ((double)rows * K + (double)N * K) + 8.0 * rows * N,
-             2.0 * np * (double)rows * N * K);
+    KProf kp(p, s, EXPD_K_DST_TC, a.nprob * 2.0 * nsl * ((double)rows * K + (double)N * K) + 8.0 * rows * a.Nout,
+             a.nprob * 2.0 * np * (double)rows * N * K);
     if (bn == 64) {
         EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel<64>, TcShape<64>::SMEM));
         dst_mma_kernel<64><<<grid, TC_THREADS, TcShape<64>::SMEM, s>>>(a);
@@ -651,6 +705,9 @@ bool dst_tc_eligible(expd_plan p) {
 
 void dst_tc_layout(expd_plan p) {
     p->tc_nsl = tc_slices_for(p->tol);
+    // the symmetric half of S (even sizes; EXPD_DST_FOLD=0 keeps the full products)
+    const char* fo = getenv("EXPD_DST_FOLD");
+    p->tc_fold = !(fo && strcmp(fo, "0") == 0) && p->NX % 128 == 0 && p->NY % 128 == 0;
     const double per_slice = (double)p->tc_nsl * p->M * 2.0;
     p->tc_chunk = (int)std::max(1.0, std::min((double)p->Ns, std::floor(2147483648.0 / per_slice)));
 }
@@ -673,12 +730,24 @@ expd_status dst_tc_setup(expd_plan p, cudaStream_t s) {
     if (st != EXPD_OK) return st;
     p->tc_err = p->tc_ex + NX + NY + (size_t)p->tc_chunk * std::max(NX, NY);
     EXPD_CUDA_TRY(cudaMemsetAsync(p->tc_err, 0, sizeof(int), s));
-    // digits of S_x and S_y with one exponent per matrix: |S| <= sqrt(2/(n+1)) < 2^e
+    // digits of S_x and S_y with one exponent per matrix: |S| <= sqrt(2/(n+1)) < 2^e;
+    // folded: of the even rows' and the odd rows' first halves (S_e, S_o: n/2 x
+    // n/2 each, rows 2c and 2c + 1 of S at stride 2n)
     p->tc_eSx = dst_exponent(NX);
     p->tc_eSy = dst_exponent(NY);
-    st = split_rows(p, p->Sx, NX, NX, p->tc_S, (long long)NX * NX, nullptr, p->tc_eSx, s);
-    if (st == EXPD_OK)
-        st = split_rows(p, p->Sy, NY, NY, p->tc_S + (size_t)nsl * NX * NX, (long long)NY * NY, nullptr, p->tc_eSy, s);
+    for (int d = 0; d < 2 && st == EXPD_OK; ++d) {
+        const int n = d == 0 ? NX : NY;
+        const double* S = d == 0 ? p->Sx : p->Sy;
+        uint16_t* out = p->tc_S + (d == 0 ? 0 : (size_t)nsl * NX * NX);
+        const int e = d == 0 ? p->tc_eSx : p->tc_eSy;
+        if (p->tc_fold) {
+            const long long h = n / 2, sl = h * h;
+            st = split_rows(p, S, h, (int)h, 2LL * n, out, sl, nullptr, e, s);
+            if (st == EXPD_OK) st = split_rows(p, S + n, h, (int)h, 2LL * n, out + (size_t)nsl * sl, sl, nullptr, e, s);
+        } else {
+            st = split_rows(p, S, n, n, n, out, (long long)n * n, nullptr, e, s);
+        }
+    }
     if (st != EXPD_OK) return st;
     EXPD_CUDA_TRY(cudaStreamSynchronize(s));
     return EXPD_OK;
@@ -691,39 +760,51 @@ expd_status dst2_tc(expd_plan p, const double* X, double* Y, int ns, double* tmp
     const uint16_t* Sxd = p->tc_S;
     const uint16_t* Syd = p->tc_S + (size_t)nsl * NX * NX;
     int* exA = p->tc_ex + NX + NY;
+    // one pass: rows of n values (r of them, R per slice) -> out transposed within slices
+    auto pass = [&](const double* in, long long r, int R, int n, const uint16_t* Sd, int eS, double* out) {
+        if (!p->tc_fold) {
+            expd_status st = split_rows(p, in, r, n, n, p->tc_pack, r * n, exA, INT_MIN, s);
+            return st == EXPD_OK ? mma_pass(p, p->tc_pack, exA, r, R, Sd, eS, n, n, out, s) : st;
+        }
+        const int h = n / 2;
+        uint16_t* u = p->tc_pack;
+        uint16_t* v = p->tc_pack + (size_t)nsl * r * h;
+        expd_status st = split_fold(p, in, r, n, u, v, r * h, exA, s);
+        return st == EXPD_OK ? mma_pass(p, u, exA, r, R, Sd, eS, h, h, out, s, v, Sd + (size_t)nsl * h * h) : st;
+    };
     for (int b0 = 0; b0 < ns; b0 += p->tc_chunk) {
         const int cs = std::min(p->tc_chunk, ns - b0);
         const double* x = X + (long long)b0 * M;
         double* y = Y + (long long)b0 * M;
         // pass 1: rows of X (cs*NY rows of NX), T[s] = (X[s] S_x)^T, [NX][NY]
-        const long long r1 = (long long)cs * NY;
-        expd_status st = split_rows(p, x, r1, NX, p->tc_pack, r1 * NX, exA, INT_MIN, s);
-        if (st == EXPD_OK) st = mma_pass(p, p->tc_pack, exA, r1, NY, Sxd, p->tc_eSx, NX, NX, tmp, s);
+        expd_status st = pass(x, (long long)cs * NY, NY, NX, Sxd, p->tc_eSx, tmp);
         // pass 2: rows of T (cs*NX rows of NY), Y[s] = (T[s] S_y)^T, [NY][NX]
-        const long long r2 = (long long)cs * NX;
-        if (st == EXPD_OK) st = split_rows(p, tmp, r2, NY, p->tc_pack, r2 * NY, exA, INT_MIN, s);
-        if (st == EXPD_OK) st = mma_pass(p, p->tc_pack, exA, r2, NX, Syd, p->tc_eSy, NY, NY, y, s);
+        if (st == EXPD_OK) st = pass(tmp, (long long)cs * NX, NX, NY, Syd, p->tc_eSy, y);
         if (st != EXPD_OK) return st;
     }
     return EXPD_OK;
 }
 
-// Reports (and clears) a pipeline wait of the tensor-core kernel that gave up.
+// Reports (and clears) a pipeline wait of a tensor-core kernel (the DST, the
+// time kernel) that gave up.
 expd_status dst_tc_check(expd_plan p, cudaStream_t s) {
-    if (!p->tc_dst || !p->tc_err) return EXPD_OK;
-    int h = 0;
-    EXPD_CUDA_TRY(cudaMemcpyAsync(&h, p->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    EXPD_CUDA_TRY(cudaStreamSynchronize(s));
-    if (h) {
-        EXPD_CUDA_TRY(cudaMemsetAsync(p->tc_err, 0, sizeof(int), s));
+    int* words[2] = {p->tc_dst ? p->tc_err : nullptr, p->tt_err};
+    for (int w = 0; w < 2; ++w) {
+        if (!words[w]) continue;
+        int h = 0;
+        EXPD_CUDA_TRY(cudaMemcpyAsync(&h, words[w], sizeof(int), cudaMemcpyDeviceToHost, s));
+        EXPD_CUDA_TRY(cudaStreamSynchronize(s));
+        if (!h) continue;
+        EXPD_CUDA_TRY(cudaMemsetAsync(words[w], 0, sizeof(int), s));
+        const char* what = w == 0 ? "tensor-core DST" : "tensor-core time kernel";
         // a wait that gave up because the call was cancelled, or one that ran
         // out of time; the results are invalid either way
         if (p->call_cancelled || p->cancel_req.exchange(0)) {
             if (p->cancel_host) *p->cancel_host = 0;
             p->call_cancelled = 1;
-            return expd_fail(EXPD_ERR_CANCELLED, "tensor-core DST: cancelled in flight (results invalid)");
+            return expd_fail(EXPD_ERR_CANCELLED, std::string(what) + ": cancelled in flight (results invalid)");
         }
-        return expd_fail(EXPD_ERR_TIMEOUT, "tensor-core DST: a pipeline wait gave up after 2 s (results invalid)");
+        return expd_fail(EXPD_ERR_TIMEOUT, std::string(what) + ": a pipeline wait gave up after 2 s (results invalid)");
     }
     return EXPD_OK;
 }

@@ -110,6 +110,7 @@ struct expd_plan_s {
     // Dirichlet dense sizes on the mixed path: split-BF16 tensor-core products
     int tc_dst = 0;            // the dense DST runs on the tensor cores (dst_tc.cu)
     int tc_nsl = 0;            // 7-bit digits per value
+    int tc_fold = 0;           // products over the symmetric half of S (S[j][n-1-k] = (-1)^j S[j][k])
     int tc_chunk = 0;          // slices transformed per pass
     int tc_eSx = 0, tc_eSy = 0;  // exponents of the S_x and S_y digits (|S| < 2^e)
     uint16_t* tc_S = nullptr;  // packed digit slices of S_x then S_y
@@ -177,6 +178,9 @@ struct expd_plan_s {
     int no_cplx_time = 0;         // 1: complex columns take the generic time kernel (EXPD_TIME_CPLX=0)
     int no_reg_time = 0;          // 1 forces the shared-memory time kernel (tests)
     int no_real_time = 0;         // 1: real columns take the generic kernel (EXPD_TIME_REAL=0, tests)
+    int no_tc_time = 0;           // 1: real columns keep the FFT time kernels (EXPD_TIME_TC=0)
+    void* tt_tab = nullptr;       // tensor-core time kernel: DFT matrices as fp16 digits and tables (time_tc.cu)
+    int* tt_err = nullptr;        // its error word (a wait on an MMA gave up)
     int no_fft4 = 0;              // 1 forces the radix-4 shared-memory row / column FFTs (tests)
     // mixed Krylov refinement: a cycle ends once its residual fell by this factor
     double krylov_eta = 1e-3;
@@ -327,6 +331,12 @@ struct TimeOp {
                                // where the kernel taken supports them (p->dots_fused tells)
 };
 expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s);
+// Tensor-core time kernel (time_tc.cu): real columns, float32 preconditioner on
+// float64 storage, Ns <= 128.  Eligibility, the device bytes of its tables,
+// their construction (at plan creation) and the launch.
+bool time_tc_eligible(expd_plan p);
+size_t time_tc_bytes(expd_plan p);
+expd_status time_tc_setup(expd_plan p, cudaStream_t s);
 // The register time kernel serves this plan's window (Ns in {16, 32, 64}).
 bool time_reg_usable(expd_plan p);
 // per-slice totals of the time kernel's CTA partials into redout[8..]:

@@ -142,3 +142,6 @@ expd_status time_real_launch(expd_plan p, expd_time::TimeArgs& a, int f32, int s
 // and the shared memory it needs for the plan's window.
 expd_status time_cplx_launch(expd_plan p, expd_time::TimeArgs& a, int st, cudaStream_t s);
 size_t time_cplx_smem_bytes(expd_plan p, int st);
+// Tensor-core time kernel (time_tc.cu): real columns, float32 preconditioner,
+// float64 storage, Ns <= 128, no N term; the plan's tables from time_tc_setup.
+expd_status time_tc_launch(expd_plan p, expd_time::TimeArgs& a, cudaStream_t s);

@@ -487,6 +487,12 @@ expd_status time_apply(expd_plan p, const TimeOp& op, cudaStream_t s) {
         }
         if (!op.NL || !op.nl_f32) return time_reg_launch(p, a, 0, s);
     }
+    // real columns, float32 preconditioner on float64 storage, Ns <= 128:
+    // Steps (a) and (c) as tensor-core products (time_tc.cu)
+    // (sigR exact in float32: the kernel's double-float combination scales by it)
+    if (p->realcol && p->tt_tab && op.precond && op.f32 && !op.st32 && !op.stdd && !op.NL &&
+        (double)(float)op.sigR == op.sigR)
+        return time_tc_launch(p, a, s);
     if (p->realcol && !op.stdd && !p->no_real_time) {
         if (op.st32) {
             if (!op.f32) return expd_fail(EXPD_ERR_INVALID_ARG, "float32 storage needs the float32 preconditioner");

@@ -35,10 +35,10 @@ SYMBOLS = ("expd_plan_create", "expd_plan_workspace_bytes", "expd_plan_footprint
            "expd_precond_apply_noalloc",
            "expd_status_string", "expd_last_error", "expd_version")
 (K_TIME, K_FFT_COL, K_FFT_ROW, K_DST, K_GMRES, K_POINTWISE, K_REDUCE, K_TIME32, K_FFT_COL32, K_FFT_ROW32,
- K_TIMEDD, K_FFT_COLDD, K_FFT_ROWDD, K_DST_TC, K_DST_SPLIT) = range(15)
-NUM_KCLASS = 15
+ K_TIMEDD, K_FFT_COLDD, K_FFT_ROWDD, K_DST_TC, K_DST_SPLIT, K_TIME_TC) = range(16)
+NUM_KCLASS = 16
 KCLASS_NAMES = ("time", "fft_col", "fft_row", "dst", "gmres", "pointwise", "reduce", "time32", "fft_col32",
-                "fft_row32", "timedd", "fft_coldd", "fft_rowdd", "dst_tc", "dst_split")
+                "fft_row32", "timedd", "fft_coldd", "fft_rowdd", "dst_tc", "dst_split", "time_tc")
 
 
 class Grid(C.Structure):

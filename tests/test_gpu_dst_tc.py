@@ -46,11 +46,15 @@ def _counts(plan):
 TILES = [0, 8]          # 128 x 128 output tiles, 128 x 64 tiles (EXPD_KF_DST_N64)
 
 
+@pytest.mark.parametrize("fold", ["1", "0"], ids=["folded", "full"])
 @pytest.mark.parametrize("flags", TILES, ids=["n128", "n64"])
 @pytest.mark.parametrize("p", TC_CASES, ids=TC_IDS)
-def test_tc_residual_matches_oracle(expd, p, flags):
+def test_tc_residual_matches_oracle(expd, p, flags, fold, monkeypatch):
     # the residual of a mixed plan is float64 arithmetic around the two
-    # transforms, so its error is the transforms' error
+    # transforms, so its error is the transforms' error; folded: the products
+    # over the symmetric half of S (EXPD_DST_FOLD=1, the default), full: over
+    # all of S
+    monkeypatch.setenv("EXPD_DST_FOLD", fold)
     sp = O.spec_of(p)
     rng = np.random.default_rng(13)
     amp = 0.5 if p.nonlin != "none" else 1.0
@@ -107,6 +111,24 @@ def test_tc_agrees_with_float64_products(expd, monkeypatch):
         assert (cls["dst_tc"]["count"] > 0) == (mode == "1"), cls
         out[mode] = host(U)
     assert O.rel_error(out["1"], out["0"]) < 1e-9
+
+
+def test_tc_folded_products_agree_with_full_ones(expd, monkeypatch):
+    # S[j][n-1-k] = (-1)^j S[j][k]: the folded transform (half the digit
+    # products) and the full one agree to the digits' accuracy
+    p = TC_CASES[1]
+    r = np.random.default_rng(17).standard_normal((p.Ns,) + p.n)
+    out = {}
+    for fold in ("1", "0"):
+        monkeypatch.setenv("EXPD_DST_FOLD", fold)
+        S = torch.empty_like(dev(r))
+        with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-10)) as plan:
+            plan.timing_enable(True)
+            plan.precond_apply(dev(r), S)
+            cls = _counts(plan)
+        out[fold] = (host(S), cls["dst_tc"]["flops"])
+    assert relmax(out["1"][0], out["0"][0]) < 1e-9
+    assert out["1"][1] == pytest.approx(out["0"][1] / 2)
 
 
 def test_tc_tile_widths_agree_bit_for_bit(expd):
