@@ -59,8 +59,6 @@ constexpr int TC_BM = 128;                          // rows per tile (TMEM lanes
 constexpr int TC_BK = 64;                           // K per stage (bf16: 128 bytes per row)
 constexpr int TC_TILE_ELEMS = TC_BM * TC_BK;        // 8192 bf16 per packed operand tile (128 rows)
 constexpr int TC_TILE_BYTES = TC_TILE_ELEMS * 2;    // 16 KB
-constexpr int TC_EPI_WARPS = 8;                     // two per TMEM lane quarter, BN/2 columns each
-constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS); // warp 0 copies, warp 1 issues MMAs, warps 2..9 drain
 constexpr int TC_NACC = 2;                          // accumulator buffers of BN columns
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // every wait gives up after 2 s
 
@@ -74,6 +72,11 @@ struct TcShape {
     static constexpr int STAGE_BYTES = TC_TILE_BYTES + B_BYTES;
     static constexpr int STAGES = BN == 128 ? 6 : 8;
     static constexpr int TMEM_COLS = 4 * BN;
+    // drain warps: BN / 32 per TMEM lane quarter, 32 columns each (warp 0
+    // copies, warp 1 issues the MMAs, warps 2.. drain); enough warps that one's
+    // TMEM loads overlap another's double-float sums
+    static constexpr int EPI = BN / 8;
+    static constexpr int THREADS = 32 * (2 + EPI);
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 256 + 1024;
     // kind::f16 instruction descriptor: D float32 (bits 4-5 = 1), A and B bf16
     // (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit
@@ -107,6 +110,11 @@ struct TcArgs {
     int nprob, ocs, Nout;
 };
 
+// The waits of the issuing threads: one try inline (the phase is usually
+// complete already), the bounded loop of mbar_wait only when it is not.
+__device__ __forceinline__ bool mbar_wait_fast(uint32_t bar, uint32_t parity, const volatile int* abort,
+                                               const volatile int* cancel);
+
 // Waits for the phase of the given parity; gives up after TC_WAIT_NS, when
 // another role of the CTA has given up (abort != 0) or when the host cancels
 // the call (cancel != 0, read from mapped host memory every 1024 tries);
@@ -125,48 +133,47 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const vola
     }
 }
 
-// acc, hi and lo: three 32-column loads of this warp's 32 lanes, then the wait
-__device__ __forceinline__ void tm_ld3(uint32_t ta, uint32_t th, uint32_t tl, uint32_t (&a)[32], uint32_t (&h)[32],
-                                       uint32_t (&l)[32]) {
+__device__ __forceinline__ bool mbar_wait_fast(uint32_t bar, uint32_t parity, const volatile int* abort,
+                                               const volatile int* cancel) {
+    return mbar_try_wait(bar, parity) || mbar_wait(bar, parity, abort, cancel);
+}
+
+// 16-column variants for the drain (half the registers of the 32-column forms)
+__device__ __forceinline__ void tm_ld16x3(uint32_t ta, uint32_t th, uint32_t tl, uint32_t (&a)[16], uint32_t (&h)[16],
+                                          uint32_t (&l)[16]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%96];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%97];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%64, %65, %66, %67, %68, %69, %70, %71, %72, %73, %74, %75, %76, %77, %78, %79, %80, %81, %82, %83, %84, %85, %86, %87, %88, %89, %90, %91, %92, %93, %94, %95}, [%98];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%48];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%49];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%50];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(a[16]), "=r"(a[17]), "=r"(a[18]), "=r"(a[19]), "=r"(a[20]), "=r"(a[21]), "=r"(a[22]), "=r"(a[23]), "=r"(a[24]), "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), "=r"(a[28]), "=r"(a[29]), "=r"(a[30]), "=r"(a[31]), "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]), "=r"(h[7]), "=r"(h[8]), "=r"(h[9]), "=r"(h[10]), "=r"(h[11]), "=r"(h[12]), "=r"(h[13]), "=r"(h[14]), "=r"(h[15]), "=r"(h[16]), "=r"(h[17]), "=r"(h[18]), "=r"(h[19]), "=r"(h[20]), "=r"(h[21]), "=r"(h[22]), "=r"(h[23]), "=r"(h[24]), "=r"(h[25]), "=r"(h[26]), "=r"(h[27]), "=r"(h[28]), "=r"(h[29]), "=r"(h[30]), "=r"(h[31]), "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]), "=r"(l[6]), "=r"(l[7]), "=r"(l[8]), "=r"(l[9]), "=r"(l[10]), "=r"(l[11]), "=r"(l[12]), "=r"(l[13]), "=r"(l[14]), "=r"(l[15]), "=r"(l[16]), "=r"(l[17]), "=r"(l[18]), "=r"(l[19]), "=r"(l[20]), "=r"(l[21]), "=r"(l[22]), "=r"(l[23]), "=r"(l[24]), "=r"(l[25]), "=r"(l[26]), "=r"(l[27]), "=r"(l[28]), "=r"(l[29]), "=r"(l[30]), "=r"(l[31])
+        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]), "=r"(h[7]), "=r"(h[8]), "=r"(h[9]), "=r"(h[10]), "=r"(h[11]), "=r"(h[12]), "=r"(h[13]), "=r"(h[14]), "=r"(h[15]), "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]), "=r"(l[6]), "=r"(l[7]), "=r"(l[8]), "=r"(l[9]), "=r"(l[10]), "=r"(l[11]), "=r"(l[12]), "=r"(l[13]), "=r"(l[14]), "=r"(l[15])
         : "r"(ta), "r"(th), "r"(tl)
         : "memory");
 }
-
-// hi and lo only
-__device__ __forceinline__ void tm_ld2(uint32_t th, uint32_t tl, uint32_t (&h)[32], uint32_t (&l)[32]) {
+__device__ __forceinline__ void tm_ld16x2(uint32_t th, uint32_t tl, uint32_t (&h)[16], uint32_t (&l)[16]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%64];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%65];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%33];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]), "=r"(h[7]), "=r"(h[8]), "=r"(h[9]), "=r"(h[10]), "=r"(h[11]), "=r"(h[12]), "=r"(h[13]), "=r"(h[14]), "=r"(h[15]), "=r"(h[16]), "=r"(h[17]), "=r"(h[18]), "=r"(h[19]), "=r"(h[20]), "=r"(h[21]), "=r"(h[22]), "=r"(h[23]), "=r"(h[24]), "=r"(h[25]), "=r"(h[26]), "=r"(h[27]), "=r"(h[28]), "=r"(h[29]), "=r"(h[30]), "=r"(h[31]), "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]), "=r"(l[6]), "=r"(l[7]), "=r"(l[8]), "=r"(l[9]), "=r"(l[10]), "=r"(l[11]), "=r"(l[12]), "=r"(l[13]), "=r"(l[14]), "=r"(l[15]), "=r"(l[16]), "=r"(l[17]), "=r"(l[18]), "=r"(l[19]), "=r"(l[20]), "=r"(l[21]), "=r"(l[22]), "=r"(l[23]), "=r"(l[24]), "=r"(l[25]), "=r"(l[26]), "=r"(l[27]), "=r"(l[28]), "=r"(l[29]), "=r"(l[30]), "=r"(l[31])
+        : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]), "=r"(h[7]), "=r"(h[8]), "=r"(h[9]), "=r"(h[10]), "=r"(h[11]), "=r"(h[12]), "=r"(h[13]), "=r"(h[14]), "=r"(h[15]), "=r"(l[0]), "=r"(l[1]), "=r"(l[2]), "=r"(l[3]), "=r"(l[4]), "=r"(l[5]), "=r"(l[6]), "=r"(l[7]), "=r"(l[8]), "=r"(l[9]), "=r"(l[10]), "=r"(l[11]), "=r"(l[12]), "=r"(l[13]), "=r"(l[14]), "=r"(l[15])
         : "r"(th), "r"(tl)
         : "memory");
 }
-
-// one 32-column load
-__device__ __forceinline__ void tm_ld1(uint32_t ta, uint32_t (&a)[32]) {
+__device__ __forceinline__ void tm_ld16(uint32_t ta, uint32_t (&a)[16]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(a[16]), "=r"(a[17]), "=r"(a[18]), "=r"(a[19]), "=r"(a[20]), "=r"(a[21]), "=r"(a[22]), "=r"(a[23]), "=r"(a[24]), "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), "=r"(a[28]), "=r"(a[29]), "=r"(a[30]), "=r"(a[31])
+        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15])
         : "r"(ta)
         : "memory");
 }
-
-// hi and lo back to their 32 columns, then the wait
-__device__ __forceinline__ void tm_st2(uint32_t th, uint32_t tl, const uint32_t (&h)[32], const uint32_t (&l)[32]) {
+__device__ __forceinline__ void tm_st16x2(uint32_t th, uint32_t tl, const uint32_t (&h)[16], const uint32_t (&l)[16]) {
     asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33};\n\t"
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%1], {%34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63, %64, %65};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%1], {%18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33};\n\t"
         "tcgen05.wait::st.sync.aligned;"
         :
-        : "r"(th), "r"(tl), "r"(h[0]), "r"(h[1]), "r"(h[2]), "r"(h[3]), "r"(h[4]), "r"(h[5]), "r"(h[6]), "r"(h[7]), "r"(h[8]), "r"(h[9]), "r"(h[10]), "r"(h[11]), "r"(h[12]), "r"(h[13]), "r"(h[14]), "r"(h[15]), "r"(h[16]), "r"(h[17]), "r"(h[18]), "r"(h[19]), "r"(h[20]), "r"(h[21]), "r"(h[22]), "r"(h[23]), "r"(h[24]), "r"(h[25]), "r"(h[26]), "r"(h[27]), "r"(h[28]), "r"(h[29]), "r"(h[30]), "r"(h[31]), "r"(l[0]), "r"(l[1]), "r"(l[2]), "r"(l[3]), "r"(l[4]), "r"(l[5]), "r"(l[6]), "r"(l[7]), "r"(l[8]), "r"(l[9]), "r"(l[10]), "r"(l[11]), "r"(l[12]), "r"(l[13]), "r"(l[14]), "r"(l[15]), "r"(l[16]), "r"(l[17]), "r"(l[18]), "r"(l[19]), "r"(l[20]), "r"(l[21]), "r"(l[22]), "r"(l[23]), "r"(l[24]), "r"(l[25]), "r"(l[26]), "r"(l[27]), "r"(l[28]), "r"(l[29]), "r"(l[30]), "r"(l[31])
+        : "r"(th), "r"(tl), "r"(h[0]), "r"(h[1]), "r"(h[2]), "r"(h[3]), "r"(h[4]), "r"(h[5]), "r"(h[6]), "r"(h[7]), "r"(h[8]), "r"(h[9]), "r"(h[10]), "r"(h[11]), "r"(h[12]), "r"(h[13]), "r"(h[14]), "r"(h[15]), "r"(l[0]), "r"(l[1]), "r"(l[2]), "r"(l[3]), "r"(l[4]), "r"(l[5]), "r"(l[6]), "r"(l[7]), "r"(l[8]), "r"(l[9]), "r"(l[10]), "r"(l[11]), "r"(l[12]), "r"(l[13]), "r"(l[14]), "r"(l[15])
         : "memory");
 }
 
@@ -374,7 +381,7 @@ __device__ __forceinline__ double scaled_sum(float hi, float lo, int E) {
 // in TMEM while the next group accumulates.  After a tile's last group the
 // drain warps write the float64 result.
 template <int BN>
-__global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_constant__ TcArgs a) {
+__global__ void __launch_bounds__(TcShape<BN>::THREADS, 1) dst_mma_kernel(const __grid_constant__ TcArgs a) {
     typedef TcShape<BN> SH;
     constexpr int TC_STAGES = SH::STAGES;
     extern __shared__ unsigned char smem_raw[];
@@ -399,7 +406,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
         }
         for (int b = 0; b < TC_NACC; ++b) {
             mbar_init(accf(b), 1);
-            mbar_init(acce(b), TC_EPI_WARPS);
+            mbar_init(acce(b), SH::EPI);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -423,7 +430,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
     if (warp == 0) {
         if (lane == 0) {
             // ---- copies ----
-            uint32_t it = 0;
+            uint32_t it = 0, cph = 0;  // stages issued; the ring's current stage and phase
+            int cs = 0;
+            const uint32_t sm0 = smem_u32(sm);
             bool ok = true;
             for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 const long long rt = t / npc;
@@ -437,17 +446,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
                     const uint16_t* Ab = Aq + a.pi[p] * a.a_slice + rt * KB * TC_TILE_ELEMS;
                     const uint16_t* Bb = Bq + a.pj[p] * a.b_slice + boff;
                     for (int kb = 0; kb < KB; ++kb, ++it) {
-                        const int s = (int)(it % TC_STAGES);
-                        const uint32_t ph = (it / TC_STAGES) & 1u;
-                        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag, a.cancel)) {
+                        if (!mbar_wait_fast(empty(cs), cph ^ 1u, abort_flag, a.cancel)) {
                             ok = false;
                             break;
                         }
-                        unsigned char* st = sm + (size_t)s * SH::STAGE_BYTES;
-                        mbar_arrive_expect_tx(full(s), SH::STAGE_BYTES);
-                        bulk_g2s(smem_u32(st), Ab + (long long)kb * TC_TILE_ELEMS, TC_TILE_BYTES, full(s));
-                        bulk_g2s(smem_u32(st + TC_TILE_BYTES), Bb + (long long)kb * TC_TILE_ELEMS, SH::B_BYTES,
-                                 full(s));
+                        const uint32_t st = sm0 + (uint32_t)cs * SH::STAGE_BYTES, fb = full(cs);
+                        mbar_arrive_expect_tx(fb, SH::STAGE_BYTES);
+                        bulk_g2s(st, Ab + (long long)kb * TC_TILE_ELEMS, TC_TILE_BYTES, fb);
+                        bulk_g2s(st + TC_TILE_BYTES, Bb + (long long)kb * TC_TILE_ELEMS, SH::B_BYTES, fb);
+                        if (++cs == TC_STAGES) {
+                            cs = 0;
+                            cph ^= 1u;
+                        }
                     }
                 }
             }
@@ -463,7 +473,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMAs ----
-            uint32_t it = 0, pc = 0;
+            uint32_t it = 0, pc = 0, cph = 0;
+            int cs = 0;
+            const uint64_t desc0 = smem_desc(smem_u32(sm));  // stage 0's A tile; other stages by address
             bool ok = true;
             for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 for (int g = 0; g < a.ngroups && ok; ++g, ++pc) {
@@ -477,19 +489,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
                     for (int p = a.gstart[g]; p < a.gstart[g + 1] && ok; ++p) {
                         const bool first = p == a.gstart[g];
                         for (int kb = 0; kb < KB; ++kb, ++it) {
-                            const int s = (int)(it % TC_STAGES);
-                            if (!mbar_wait(full(s), (it / TC_STAGES) & 1u, abort_flag, a.cancel)) {
+                            if (!mbar_wait_fast(full(cs), cph, abort_flag, a.cancel)) {
                                 ok = false;
                                 break;
                             }
                             tc_fence_after();
-                            const uint32_t sa = smem_u32(sm + (size_t)s * SH::STAGE_BYTES);
-                            const uint32_t sb = sa + TC_TILE_BYTES;
+                            // descriptors of the stage's A and B tiles; 16 bf16 of K =
+                            // two core matrices = 256 bytes = 16 in the address field
+                            const uint64_t da = desc0 + (uint64_t)(cs * (SH::STAGE_BYTES >> 4));
+                            const uint64_t db = da + (uint64_t)(TC_TILE_BYTES >> 4);
 #pragma unroll
-                            for (int q = 0; q < TC_BK / 16; ++q)  // 16 bf16 of K = two core matrices = 256 bytes
-                                tc_mma(d, smem_desc(sa + 256u * q), smem_desc(sb + 256u * q), SH::IDESC,
-                                       !first || (kb | q) != 0);
-                            tc_commit(empty(s));
+                            for (int q = 0; q < TC_BK / 16; ++q)
+                                tc_mma(d, da + 16u * q, db + 16u * q, SH::IDESC, !first || (kb | q) != 0);
+                            tc_commit(empty(cs));
+                            if (++cs == TC_STAGES) {
+                                cs = 0;
+                                cph ^= 1u;
+                            }
                         }
                     }
                     if (ok) tc_commit(accf(b));
@@ -504,12 +520,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
             mbar_wait(drain, 0u, abort_flag, nullptr, true);
         }
     } else {
-        // ---- drain and output (warps 2..9): TMEM lane quarter warp % 4, columns
-        // (BN/2) (warp - 2) / 4 .. + BN/2 - 1 in chunks of 32; the double-float
-        // sums in TMEM columns 2 BN .. 4 BN - 1 ----
-        constexpr int CHUNKS = BN / 64;
+        // ---- drain and output (warps 2..): TMEM lane quarter warp % 4, columns
+        // 32 (warp - 2) / 4 .. + 31; the double-float sums in TMEM columns
+        // 2 BN .. 4 BN - 1 ----
         const int lq = warp & 3, half = (warp - 2) >> 2;
-        const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(half * (BN / 2));
+        const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(half * 32);
         const uint32_t thi = tl + 2u * BN, tlo = tl + 3u * BN;
         uint32_t pc = 0;
         bool ok = true;
@@ -529,20 +544,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
                 const float wsc = __int_as_float((127 - 7 * (a.gw[g] + 2)) << 23);
                 const uint32_t tacc = tl + (uint32_t)(b * BN);
 #pragma unroll 1
-                for (int c = 0; c < CHUNKS; ++c) {
-                    uint32_t v[32], h[32], l[32];
+                for (int c = 0; c < 2; ++c) {  // two 16-column halves of the warp's 32 columns
+                    uint32_t v[16], h[16], l[16];
                     if (g == 0) {
-                        tm_ld1(tacc + 32u * c, v);
+                        tm_ld16(tacc + 16u * c, v);
                     } else {
-                        tm_ld3(tacc + 32u * c, thi + 32u * c, tlo + 32u * c, v, h, l);
+                        tm_ld16x3(tacc + 16u * c, thi + 16u * c, tlo + 16u * c, v, h, l);
                     }
-                    if (c == CHUNKS - 1) {  // the accumulator buffer is free for the group after next
+                    if (c == 1) {  // the accumulator buffer is free for the group after next
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(acce(b));
                     }
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
+                    for (int e = 0; e < 16; ++e) {
                         const float w = __fmul_rn(__uint_as_float(v[e]), wsc);  // exact: a power of two
                         if (g == 0) {
                             h[e] = __float_as_uint(w);
@@ -559,7 +574,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
                             l[e] = __float_as_uint(__fsub_rn(l1, __fsub_rn(h1, sm_)));
                         }
                     }
-                    tm_st2(thi + 32u * c, tlo + 32u * c, h, l);
+                    tm_st16x2(thi + 16u * c, tlo + 16u * c, h, l);
                 }
             }
             if (!ok) break;
@@ -569,15 +584,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dst_mma_kernel(const __grid_con
             const int rin = (int)(row - slc * a.R);
             const int E = a.ea[row] + a.eb;
             const long long ostep = (long long)a.ocs * a.R;
-            double* o = a.out + slc * (long long)a.R * a.Nout + (long long)(ct * BN + half * (BN / 2)) * ostep +
+            double* o = a.out + slc * (long long)a.R * a.Nout + (long long)(ct * BN + half * 32) * ostep +
                         (long long)q * a.R + rin;
 #pragma unroll 1
-            for (int c = 0; c < CHUNKS; ++c) {
-                uint32_t h[32], l[32];
-                tm_ld2(thi + 32u * c, tlo + 32u * c, h, l);
+            for (int c = 0; c < 2; ++c) {
+                uint32_t h[16], l[16];
+                tm_ld16x2(thi + 16u * c, tlo + 16u * c, h, l);
 #pragma unroll
-                for (int e = 0; e < 32; ++e)
-                    o[(long long)(32 * c + e) * ostep] = scaled_sum(__uint_as_float(h[e]), __uint_as_float(l[e]), E);
+                for (int e = 0; e < 16; ++e)
+                    o[(long long)(16 * c + e) * ostep] = scaled_sum(__uint_as_float(h[e]), __uint_as_float(l[e]), E);
             }
         }
         if (!ok) {
@@ -669,10 +684,10 @@ expd_status mma_pass(expd_plan p, const uint16_t* A, const int* ea, long long ro
              a.nprob * 2.0 * np * (double)rows * N * K);
     if (bn == 64) {
         EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel<64>, TcShape<64>::SMEM));
-        dst_mma_kernel<64><<<grid, TC_THREADS, TcShape<64>::SMEM, s>>>(a);
+        dst_mma_kernel<64><<<grid, TcShape<64>::THREADS, TcShape<64>::SMEM, s>>>(a);
     } else {
         EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel<128>, TcShape<128>::SMEM));
-        dst_mma_kernel<128><<<grid, TC_THREADS, TcShape<128>::SMEM, s>>>(a);
+        dst_mma_kernel<128><<<grid, TcShape<128>::THREADS, TcShape<128>::SMEM, s>>>(a);
     }
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;

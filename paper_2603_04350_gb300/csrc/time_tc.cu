@@ -70,7 +70,7 @@ constexpr unsigned long long TT_WAIT_NS = 2000000000ull;
 constexpr int TT_OFF_W = 0;                                     // W: digit 0, digit 1
 constexpr int TT_OFF_WT = 2 * TT_DIG_BYTES;                     // W^T: digit 0, digit 1
 constexpr int TT_OFF_LAMP = 4 * TT_DIG_BYTES;                   // float2 [65][6]
-constexpr int TT_OFF_GAM = TT_OFF_LAMP + TT_LAMP_ROWS * 6 * 8;  // float [128] Gamma_alpha
+constexpr int TT_OFF_GAM = TT_OFF_LAMP + TT_LAMP_ROWS * 6 * 8;  // float [128] Gamma_alpha (0 past the window)
 constexpr int TT_OFF_OSC = TT_OFF_GAM + TT_KMAX * 4;            // float [128] 1 / (Ns alpha^(n/Ns))
 constexpr int TT_TAB_BYTES = TT_OFF_OSC + TT_KMAX * 4;
 // shared memory only
