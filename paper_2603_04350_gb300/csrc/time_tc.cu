@@ -72,14 +72,15 @@ constexpr int TT_OFF_WT = 2 * TT_DIG_BYTES;                     // W^T: digit 0,
 constexpr int TT_OFF_LAMP = 4 * TT_DIG_BYTES;                   // float2 [65][6]
 constexpr int TT_OFF_GAM = TT_OFF_LAMP + TT_LAMP_ROWS * 6 * 8;  // float [128] Gamma_alpha (0 past the window)
 constexpr int TT_OFF_OSC = TT_OFF_GAM + TT_KMAX * 4;            // float [128] 1 / (Ns alpha^(n/Ns))
-constexpr int TT_TAB_BYTES = TT_OFF_OSC + TT_KMAX * 4;
+constexpr int TT_OFF_TRIG = TT_OFF_OSC + TT_KMAX * 4;             // float2 [6][64] (cos, sin)(2 pi k n/Ns)
+constexpr int TT_TAB_BYTES = TT_OFF_TRIG + 6 * 64 * 8;
 // shared memory only
 constexpr int TT_OFF_MAX = TT_TAB_BYTES;                        // float [pipe][half][128] row maxima
 constexpr int TT_OFF_ACC = TT_OFF_MAX + TT_PIPES * 2 * TT_M * 4;  // double2 [pipe][lane quarter][128] partials
 constexpr int TT_OFF_BAR = TT_OFF_ACC + TT_PIPES * 4 * TT_KMAX * 16;  // mbarriers [2], TMEM slot
 constexpr int TT_SMEM_USED = TT_OFF_BAR + 32;
 constexpr size_t TT_SMEM = (size_t)TT_SMEM_USED + 1024;         // + alignment of the dynamic base
-static_assert(TT_TAB_BYTES % 16 == 0 && TT_OFF_LAMP % 16 == 0 && TT_OFF_ACC % 16 == 0,
+static_assert(TT_TAB_BYTES % 16 == 0 && TT_OFF_LAMP % 16 == 0 && TT_OFF_ACC % 16 == 0 && TT_OFF_TRIG % 16 == 0,
               "16-byte regions");
 static_assert(TT_SMEM <= 232448, "one CTA per SM within 227 KB");
 
@@ -88,6 +89,7 @@ struct TtArgs {
     const unsigned char* tab;  // the table image (TT_TAB_BYTES)
     int* err;                  // set to 1 when a wait on an MMA gave up
     int NF, KT;                // columns of Step (a)'s product; the window rounded up to 16
+    float alpha;               // the identity form's factor (IDENT)
 };
 
 // byte offset of element (r, k) of digit d of a 128 x 128 K-major operand image
@@ -195,7 +197,16 @@ __device__ __forceinline__ float f32_of_f64_fast(double v) {
 // float32 from the iterate rounded to float32; otherwise the combination
 // F + sigR R_s X in float64, rounded to float32 before Step (a).  ORDER: the
 // BDF order s (the lookback of R_s and the degree of d_k).
-template <bool LOWQ, int ORDER>
+//
+// IDENT (with LOWQ, an unshifted Step (b) and s < Ns): R_s differs from the
+// alpha-circulant matrix P of Eq. (3.3) only in the wrap-around terms, R_s =
+// P + alpha W with (W X)_n = sum_{j > n} c_j X_{n-j+Ns} nonzero in the first s
+// slices, so P^{-1} R_s X = X + alpha P^{-1} (W X).  Step (a) of the s-slice
+// vector W X is s terms per frequency (a table of the first s rows of the
+// DFT), the first product is skipped, X is read once (by the output pass, which
+// reads it for the Krylov dot anyway), and the rounding of the preconditioner
+// enters the output scaled by alpha.
+template <bool LOWQ, bool IDENT, int ORDER>
 __global__ void __launch_bounds__(TT_THREADS, 1) time_kernel_tc(const __grid_constant__ TtArgs ta) {
     const TimeArgs& A = ta.a;
     extern __shared__ unsigned char smem_raw[];
@@ -204,6 +215,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1) time_kernel_tc(const __grid_con
     const float2* lamp = reinterpret_cast<const float2*>(sm + TT_OFF_LAMP);
     float* gamf = reinterpret_cast<float*>(sm + TT_OFF_GAM);
     const float* oscp = reinterpret_cast<const float*>(sm + TT_OFF_OSC);
+    const float2* trig = reinterpret_cast<const float2*>(sm + TT_OFF_TRIG);
     float* smax = reinterpret_cast<float*>(sm + TT_OFF_MAX);
     double2* sacc = reinterpret_cast<double2*>(sm + TT_OFF_ACC);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + TT_OFF_BAR);
@@ -264,7 +276,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1) time_kernel_tc(const __grid_con
     const double* F = static_cast<const double*>(A.F);
     double* out = static_cast<double*>(A.out);
     float* sout = static_cast<float*>(A.sout);
-    const bool xload = A.accum || (LOWQ && A.norms == 2);  // the output pass reads X again
+    const bool xload = IDENT || A.accum || (LOWQ && A.norms == 2);  // the output pass reads X
     uint32_t ph = 0;
     bool pending = false, ok = true;
 
@@ -281,6 +293,24 @@ __global__ void __launch_bounds__(TT_THREADS, 1) time_kernel_tc(const __grid_con
 
         const bool xr = X && mv, fr = !LOWQ && F && mv;
 
+        // ---- IDENT: the wrap-around vector y_n = sum_{j=n+1..s} c_j X_{n-j+Ns}
+        // (n < s) times sigR Gamma_n, from the window's last s slices ----
+        float yv[ORDER];
+        if constexpr (IDENT) {
+            float xw[ORDER];  // X_{Ns-s} .. X_{Ns-1} rounded to float32
+#pragma unroll
+            for (int j = 0; j < ORDER; ++j)
+                xw[j] = X && mv ? f32_of_f64_fast(X[(long long)(Ns - ORDER + j) * Mcol + mg]) : 0.0f;
+#pragma unroll
+            for (int n = 0; n < ORDER; ++n) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int j = n + 1; j <= ORDER; ++j) acc = fmaf(cp[j], xw[ORDER + n - j], acc);
+                yv[n] = acc * gamf[n];
+            }
+        }
+        float s1 = 1.0f;
+        if constexpr (!IDENT) {
         // ---- Step (a) input: the combination of Eq. (3.2) times Gamma_alpha,
         // slice by slice (this thread: groups gn0..gn1-1), raw floats into the
         // accumulator columns; a warp reads 32 consecutive modes of a slice, the
@@ -367,7 +397,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1) time_kernel_tc(const __grid_con
         tc_fence_before();
         pipe_sync(bid);
         tc_fence_after();
-        const float s1 = digit_scale(fmaxf(vmax, smax[(pipe * 2 + (half ^ 1)) * TT_M + m]));
+        s1 = digit_scale(fmaxf(vmax, smax[(pipe * 2 + (half ^ 1)) * TT_M + m]));
 #pragma unroll 1
         for (int g = gn0; g < gn1; ++g) {
             uint32_t v[8], hi[4], lo[4];
@@ -393,17 +423,42 @@ __global__ void __launch_bounds__(TT_THREADS, 1) time_kernel_tc(const __grid_con
         if (!ok) break;
         tc_fence_after();
 
+        }  // !IDENT
+
         // ---- Step (b), in place in the accumulator columns: Z_f = w_f Y_f / d_k ----
         const float k1 = (1.0f / 16384.0f) / s1;  // a power of two: 2^-14 / s1 (s1 <= 2^113)
         float zmax = 0.0f;
 #pragma unroll 1
         for (int g = gf0; g < gf1; ++g) {
             uint32_t v[8];
-            tm_ld8(wD + 8u * g, v);
+            if constexpr (!IDENT) tm_ld8(wD + 8u * g, v);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int k = 4 * g + i;
-                const float yr = __uint_as_float(v[2 * i]) * k1, yi = __uint_as_float(v[2 * i + 1]) * k1;
+                float yr, yi;
+                if constexpr (IDENT) {
+                    // Step (a) of the s-slice vector: the mean, the alternating
+                    // frequency and the pairs as s-term sums
+                    yr = 0.0f;
+                    yi = 0.0f;
+                    if (k == 0) {
+#pragma unroll
+                        for (int n = 0; n < ORDER; ++n) {
+                            yr += yv[n];
+                            yi += (n & 1) ? -yv[n] : yv[n];
+                        }
+                    } else if (2 * k < Ns) {
+#pragma unroll
+                        for (int n = 0; n < ORDER; ++n) {
+                            const float2 tr = trig[n * 64 + k];
+                            yr = fmaf(yv[n], tr.x, yr);
+                            yi = fmaf(yv[n], tr.y, yi);
+                        }
+                    }
+                } else {
+                    yr = __uint_as_float(v[2 * i]) * k1;
+                    yi = __uint_as_float(v[2 * i + 1]) * k1;
+                }
                 float zr = 0.0f, zi = 0.0f;
                 if (k == 0) {
                     // the mean (real d_0) and, for even Ns, the alternating frequency (row 64)
@@ -491,9 +546,11 @@ __global__ void __launch_bounds__(TT_THREADS, 1) time_kernel_tc(const __grid_con
             for (int i = 0; i < 8; ++i) {
                 const int n = n0 + i;
                 const bool in = n < Ns && mv;
-                const float sa = (__uint_as_float(v[i]) * k2) * oscp[n];
+                float sa = (__uint_as_float(v[i]) * k2) * oscp[n];
+                const float xf = LOWQ && (IDENT || A.norms == 2) ? f32_of_f64_fast(xo[i]) : 0.0f;
+                if constexpr (IDENT) sa = fmaf(ta.alpha, sa, sgR * xf);  // sigR X + alpha P^{-1} (sigR W X)
                 a8[i] = in ? sa * sa : 0.0f;
-                b8[i] = LOWQ && A.norms == 2 && in ? f32_of_f64_fast(xo[i]) * sa : 0.0f;
+                b8[i] = LOWQ && A.norms == 2 && in ? xf * sa : 0.0f;
                 r8[i] = 0.0;
                 if (in) {
                     const double res = f64_from_f32(sa);
@@ -608,6 +665,13 @@ expd_status time_tc_setup(expd_plan p, cudaStream_t s) {
         g[n] = (float)gm;
         o[n] = (float)(1.0 / ((double)Ns * gm));
     }
+    std::vector<float2> tr((size_t)6 * 64, make_float2(0.f, 0.f));
+    for (int n = 0; n < 6; ++n)
+        for (int k = 1; k < 64 && 2 * k < Ns; ++k) {
+            const double th = 2.0 * M_PI * (double)(((long long)k * n) % Ns) / Ns;
+            tr[(size_t)n * 64 + k] = make_float2((float)cos(th), (float)sin(th));
+        }
+    memcpy(&img[TT_OFF_TRIG], tr.data(), tr.size() * sizeof(float2));
     memcpy(&img[TT_OFF_GAM], g.data(), g.size() * 4);
     memcpy(&img[TT_OFF_OSC], o.data(), o.size() * 4);
     void* d = nullptr;
@@ -622,6 +686,12 @@ expd_status time_tc_setup(expd_plan p, cudaStream_t s) {
     return EXPD_OK;
 }
 
+template <int ORDER>
+static void (*pick_tc_kernel(bool lowq, bool ident))(TtArgs) {
+    if (!lowq) return time_kernel_tc<false, false, ORDER>;
+    return ident ? time_kernel_tc<true, true, ORDER> : time_kernel_tc<true, false, ORDER>;
+}
+
 expd_status time_tc_launch(expd_plan p, TimeArgs& a, cudaStream_t s) {
     TtArgs t;
     t.a = a;
@@ -634,14 +704,17 @@ expd_status time_tc_launch(expd_plan p, TimeArgs& a, cudaStream_t s) {
     long long grid = std::min<long long>(p->sm_count, (ntiles + TT_PIPES - 1) / TT_PIPES);
     if (a.norms) grid = std::min<long long>(grid, p->partial_cap);
     grid = std::max<long long>(grid, 1);
+    // the identity form for the unshifted Krylov operator (s < Ns)
+    const bool ident = lowq && a.dshift == 0.0 && p->order < p->Ns;
+    t.alpha = (float)p->alpha;
     void (*kern)(TtArgs) = nullptr;
     switch (p->order) {
-        case 1: kern = lowq ? time_kernel_tc<true, 1> : time_kernel_tc<false, 1>; break;
-        case 2: kern = lowq ? time_kernel_tc<true, 2> : time_kernel_tc<false, 2>; break;
-        case 3: kern = lowq ? time_kernel_tc<true, 3> : time_kernel_tc<false, 3>; break;
-        case 4: kern = lowq ? time_kernel_tc<true, 4> : time_kernel_tc<false, 4>; break;
-        case 5: kern = lowq ? time_kernel_tc<true, 5> : time_kernel_tc<false, 5>; break;
-        case 6: kern = lowq ? time_kernel_tc<true, 6> : time_kernel_tc<false, 6>; break;
+        case 1: kern = pick_tc_kernel<1>(lowq, ident); break;
+        case 2: kern = pick_tc_kernel<2>(lowq, ident); break;
+        case 3: kern = pick_tc_kernel<3>(lowq, ident); break;
+        case 4: kern = pick_tc_kernel<4>(lowq, ident); break;
+        case 5: kern = pick_tc_kernel<5>(lowq, ident); break;
+        case 6: kern = pick_tc_kernel<6>(lowq, ident); break;
         default: return expd_fail(EXPD_ERR_UNSUPPORTED, "tensor-core time kernel: BDF order outside 1..6");
     }
     EXPD_CUDA_TRY(smem_allow((const void*)kern, TT_SMEM));

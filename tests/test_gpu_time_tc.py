@@ -64,6 +64,7 @@ CASES = [
     P("d1_ns128_s1", "dirichlet", (300,), 1, Nt=128),
     P("n2_ns45_s2", "neumann", (12, 14), 2, Nt=46),
     P("n1_ns122_s6", "neumann", (50,), 6, Nt=127, alpha=1e-3, dt=1e-3),
+    P("d2_ns2_s3", "dirichlet", (13, 11), 3, Nt=4),    # s >= N_s: the Krylov operator without the identity form
 ]
 IDS = [p.name for p in CASES]
 
@@ -113,9 +114,11 @@ def test_tc_precond_many_tiles_per_pipeline(expd):
     assert relmax(S, ref) < bound(p)
 
 
-@pytest.mark.parametrize("p", [CASES[i] for i in (1, 3, 5, 7, 8, 10)], ids=[IDS[i] for i in (1, 3, 5, 7, 8, 10)])
+@pytest.mark.parametrize("p", [CASES[i] for i in (1, 3, 5, 7, 8, 10, 12)], ids=[IDS[i] for i in (1, 3, 5, 7, 8, 10, 12)])
 @pytest.mark.parametrize("solver", ("gmres", "bicgstab", "fp"))
 def test_tc_solvers_match_sequential(expd, p, solver):
+    # the Krylov solvers' operator launches take the identity form
+    # P^{-1} R_s X = X + alpha P^{-1} (W X) where s < N_s, the general one otherwise
     sp = O.spec_of(p)
     rng = np.random.default_rng(4)
     u0 = rng.standard_normal(p.n)
