@@ -77,15 +77,18 @@ FP64_PEAK_TFLOPS = 1.248
 FP64_CLASSES = ("time", "fft_col", "fft_row", "dst")
 # the sample of the headline workload the CPU oracle solves per replica
 ORACLE_SAMPLE_N = 128
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel class as a fraction of its algorithmic bytes, from one ncu
-# capture of the same kernel on a 512^2 x 127 Dirichlet launch (traffic grows
-# in proportion to the unknowns, so the fraction carries to a full launch):
-# time_kernel_real's residual launch moved 775.4 MB for 799.0 MB algorithmic
-# (0.970), its operator launch 495.5 MB for 532.6 MB (0.930); the class mixes
-# both kinds, so its traffic is reported as 0.95 of its algorithmic bytes per
-# launch.  An entry is removed whenever its kernel changes after the capture.
-NCU_TRAFFIC_FRACTION = {"time": 0.95}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel
+# class as a fraction of its algorithmic bytes, from one ncu capture of the
+# same kernel on a 512^2 x 127 Dirichlet launch (traffic grows in proportion to
+# the unknowns, so the fraction carries to a full launch).  time_kernel_tc:
+# the refinement residual moved 765.3 MB for 799.0 MB algorithmic (0.958), the
+# identity-form operator 490.2 MB for 532.6 MB (0.920); a solve runs four of
+# each kind (the right-hand side launch with the residuals), so the class is
+# reported at 0.94 of its algorithmic bytes per launch.  time_kernel_real
+# (the FFT-based real-column kernel, on plans without the tensor-core one):
+# 775.4 / 799.0 MB and 495.5 / 532.6 MB, 0.95.  An entry is removed whenever
+# its kernel changes after the capture.
+NCU_TRAFFIC_FRACTION = {"time": 0.95, "time_tc": 0.94}
 
 
 def parse_args():

@@ -371,18 +371,19 @@ __global__ void __launch_bounds__(TT_THREADS, 1) time_kernel_tc(const __grid_con
                         // the float32 pipe (GB300's float64 rate is 1/64 of it):
                         // the terms to 2^-48 relative, so the cancellation of a
                         // small residual keeps its float32 rounding
-                        dd q = dd_from_f64(cf[i]);
-                        const dd xd = dd_from_f64(cx[i]);
                         if (X) {
+                            const dd xd = dd_from_f64(cx[i]);
                             dd rx = xd;
 #pragma unroll
                             for (int j = 1; j <= ORDER; ++j) rx = rx - cs[j] * wd[j - 1];
-                            q = q + rx * sgR;
-                        }
+                            const dd q = dd_from_f64(cf[i]) + rx * sgR;
 #pragma unroll
-                        for (int j = ORDER - 1; j > 0; --j) wd[j] = wd[j - 1];
-                        wd[0] = xd;
-                        val = (q.hi + q.lo) * gamf[n0 + i];
+                            for (int j = ORDER - 1; j > 0; --j) wd[j] = wd[j - 1];
+                            wd[0] = xd;
+                            val = (q.hi + q.lo) * gamf[n0 + i];
+                        } else {
+                            val = f32_of_f64_fast(cf[i]) * gamf[n0 + i];  // the right-hand side alone
+                        }
                     }
                     // slices past the window and modes past the grid give zero
                     // (their loads are zero, Gamma beyond Ns is zero)
