@@ -627,3 +627,49 @@ def neumann_allen_cahn_errors(order, n=256, T=0.1, steps=(25, 50, 100, 200), eps
         ex = np.array([ue(k * dt) for k in range(Nt + 1)])
         out.append(O.rel_error(U[1:], ex[1:]))
     return out
+
+
+def check_wraparound_identity(bc="dirichlet", n=(9,), order=2, Nt=12, alpha=1e-2, seed=0):
+    """R_s and the alpha-circulant preconditioner P_alpha = R_s^alpha differ only
+    in the wrap-around entries: R_s - R_s^alpha = alpha W_s with
+    (W_s v)_n = sum_{j = n+1..s} a_j A^j v_{n-j+Ns}, nonzero in the first s slices
+    (C_{j-1}^alpha - C_{j-1} is alpha in the top-right corner, Eq. (2.4) and
+    reading 1).  Hence P_alpha^{-1} R_s v = v + alpha P_alpha^{-1} (W_s v) for
+    s < Ns: checked through the oracle's three-step preconditioner, and W_s
+    against the dense R_s - R_s^alpha.  Returns the larger relative error."""
+    sp = O.Spec(bc, tuple(n), tuple(1.0 for _ in n), 0.02, 0.1, "none", 0.01, Nt, alpha, order)
+    Ns = sp.Ns
+    rng = np.random.default_rng(seed)
+    V = rng.standard_normal((Ns,) + sp.n)
+    a, _ = O.bdf_float(order)
+    W = np.zeros_like(V)
+    for i in range(min(order, Ns)):
+        for j in range(i + 1, order + 1):
+            if i - j + Ns >= 0:
+                W[i] += a[j - 1] * O.apply_A_power(sp, V[i - j + Ns], j)
+    lhs = O.precond_apply(sp, O.apply_R(sp, V))
+    rhs = V + alpha * O.precond_apply(sp, W)
+    e1 = np.abs(lhs - rhs).max() / np.abs(lhs).max()
+    D = (O.dense_R(sp, 0.0) - O.dense_R(sp, alpha)) @ V.reshape(-1)
+    e2 = np.abs(D - alpha * W.reshape(-1)).max() / np.abs(alpha * W).max()
+    return max(e1, e2)
+
+
+def check_dst_mirror_fold(n=12, seed=0):
+    """The orthonormal DST-I S (L_h's Dirichlet eigenvectors, Sec. 3.1) satisfies
+    S[j][n-1-k] = (-1)^j S[j][k], so for even n output j of a row x is
+    sum_{k < n/2} S[j][k] (x_k + (-1)^j x_{n-1-k}).  S is taken from the oracle's
+    eigenbasis transform applied to unit vectors; returns the larger of the
+    symmetry's and the folded product's errors."""
+    sp = O.Spec("dirichlet", (n,), (1.0,), 0.02, 0.1, "none", 0.01, 4, 0.01, 1)
+    S = np.array([O.to_eigen(sp, e) for e in np.eye(n)]).T  # column k = transform of e_k
+    j = np.arange(n)[:, None]
+    e1 = np.abs(S[:, ::-1] - ((-1.0) ** j) * S).max()
+    x = np.random.default_rng(seed).standard_normal(n)
+    h = n // 2
+    u, v = x[:h] + x[::-1][:h], x[:h] - x[::-1][:h]
+    y = np.empty(n)
+    y[0::2] = S[0::2, :h] @ u
+    y[1::2] = S[1::2, :h] @ v
+    e2 = np.abs(y - S @ x).max() / np.abs(S @ x).max()
+    return max(e1, e2)

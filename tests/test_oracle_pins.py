@@ -471,3 +471,16 @@ def test_neumann_gmres_and_richardson_reach_dense():
     ref = O.dense_solve(sp, u0, f)[1:]
     assert O.rel_error(O.gmres(sp, u0, f, tol=1e-13).U[1:], ref) < 1e-11
     assert O.rel_error(O.richardson(sp, u0, f, max_iter=60, tol=1e-14).U[1:], ref) < 1e-11
+
+@pytest.mark.parametrize("bc,n,order,Nt", [("dirichlet", (9,), 1, 6), ("dirichlet", (7, 5), 2, 12),
+                                           ("dirichlet", (9,), 6, 13), ("neumann", (8,), 3, 10),
+                                           ("periodic", (8,), 2, 9)])
+def test_wraparound_identity_of_the_krylov_operator(bc, n, order, Nt):
+    # the form the tensor-core time kernel applies the Krylov operator in
+    assert C.check_wraparound_identity(bc, n, order, Nt) < 1e-12
+
+
+@pytest.mark.parametrize("n", [8, 12, 64])
+def test_dst_mirror_symmetry_and_fold(n):
+    # the symmetry the folded tensor-core sine transform relies on
+    assert C.check_dst_mirror_fold(n) < 1e-13
