@@ -44,6 +44,23 @@ EXPD_HD int digit_next(unsigned long long* Y, int i) {
     return d;
 }
 
+// The offset that turns the balanced lower digits into standard base-128
+// digits: adding 64 at every lower digit position makes digit i (i > 0) of
+// Y + offset equal d_i + 64 in [0, 127] with no carries, and leaves the top
+// digit d_0 as the quotient by 128^(nsl-1).
+EXPD_HD unsigned long long digit_offset(int nsl) {
+    unsigned long long off = 0;
+    for (int p = 0; p < nsl - 1; ++p) off |= 64ull << (7 * p);
+    return off;
+}
+
+// Digit i of Yo = Y + digit_offset(nsl): the same value repeated digit_next
+// calls give for digit i, without their carry chain.
+EXPD_HD int digit_at(unsigned long long Yo, int i, int nsl) {
+    const int sh = 7 * (nsl - 1 - i);
+    return i == 0 ? (int)(Yo >> sh) : (int)((Yo >> sh) & 127ull) - 64;
+}
+
 // Element offset of (row r, column k) of a packed operand with KB tiles of
 // 64 K per 128-row tile: tile (r / 128, k / 64) of 8192 elements, inside it
 // the 8x8 core matrix of row group (r % 128) / 8 and K group (k % 64) / 8 at

@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restric
     const bool bad = sbad[rr] != 0;
     const double2* x = reinterpret_cast<const double2*>(in + r * lda);
     const int KB = K >> 6;
+    const unsigned long long off = digit_offset(nsl);
     const int nch = K >> 3;  // chunks of 8 values (16 bytes of bf16 per digit slice)
     for (int c = threadIdx.x >> 3; c < nch; c += 32) {
         unsigned long long Y[8];
@@ -244,11 +245,13 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restric
         }
         // the 8 values' 16 bytes of each digit slice (same 8x8 core matrix row)
         uint16_t* o = out + packed_offset(r, 8 * c, KB);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) Y[t] += off;
         for (int i = nsl - 1; i >= 0; --i) {
             uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                int d = digit_next(&Y[t], i);
+                int d = digit_at(Y[t], i, nsl);
                 if ((neg >> t) & 1u) d = -d;
                 const uint32_t hb = bad ? 0x7FC0u : bf16_of_int(d);
                 w[t >> 1] |= hb << (16 * (t & 1));
@@ -306,6 +309,7 @@ __global__ void __launch_bounds__(256) split_fold_kernel(const double* __restric
     const bool bad = sbad[rr] != 0;
     const double* x = in + r * n;
     const int K = n >> 1, KB = K >> 6;
+    const unsigned long long off = digit_offset(nsl);
     const int nch = K >> 3;
     for (int c = threadIdx.x >> 3; c < nch; c += 32) {
         unsigned long long Y[8], Z[8];
@@ -326,13 +330,18 @@ __global__ void __launch_bounds__(256) split_fold_kernel(const double* __restric
         }
         uint16_t* ou = out_u + packed_offset(r, 8 * c, KB);
         uint16_t* ov = out_v + packed_offset(r, 8 * c, KB);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            Y[t] += off;
+            Z[t] += off;
+        }
         for (int i = nsl - 1; i >= 0; --i) {
             uint32_t wu[4] = {0u, 0u, 0u, 0u}, wv[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                int d = digit_next(&Y[t], i);
+                int d = digit_at(Y[t], i, nsl);
                 if ((neg >> t) & 1u) d = -d;
-                int dz = digit_next(&Z[t], i);
+                int dz = digit_at(Z[t], i, nsl);
                 if ((negz >> t) & 1u) dz = -dz;
                 const uint32_t hu = bad ? 0x7FC0u : bf16_of_int(d + dz);
                 const uint32_t hv = bad ? 0x7FC0u : bf16_of_int(d - dz);

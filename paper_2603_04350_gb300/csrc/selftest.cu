@@ -388,8 +388,10 @@ static void split_host(const std::vector<double>& x, long long rows, int K, int 
         for (int k = 0; k < K; ++k) {
             unsigned neg;
             unsigned long long Y = digit_magnitude(bits_of(x[r * K + k]), e, nsl, &neg);
+            const unsigned long long Yo = Y + digit_offset(nsl);
             for (int i = nsl - 1; i >= 0; --i) {
                 int d = digit_next(&Y, i);
+                if (d != digit_at(Yo, i, nsl)) ++failures;  // the kernels' carry-free extraction
                 if (i == 0 && (d < 0 || d > 128)) ++failures;
                 if (i > 0 && (d < -64 || d > 63)) ++failures;
                 if (neg) d = -d;

@@ -122,6 +122,25 @@ __device__ __noinline__ bool tt_wait(uint32_t bar, uint32_t parity) {
     }
 }
 
+// 1/x to the hardware approximation (within one ulp): the divisions of
+// Step (b) at the float32 preconditioner's accuracy
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Exact float -> double by integer operations on the encodings for normal
+// floats (the exponent rebiased, the fraction widened); zeros, subnormals,
+// infinities and NaN through f64_from_f32
+__device__ __forceinline__ double f64_of_f32_fast(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    if (e - 1u < 254u)
+        return __hiloint2double((int)((u & 0x80000000u) | (((u & 0x7FFFFFFFu) >> 3) + (896u << 20))), (int)(u << 29));
+    return f64_from_f32(f);
+}
+
 // 2^(15 - e) for a row whose largest magnitude mx satisfies 2^(e-1) <= mx < 2^e:
 // the scaled row lies within 2^15; zero and non-finite maxima take 1 (the
 // non-finite values themselves reach the output)
@@ -469,8 +488,8 @@ __global__ void __launch_bounds__(TT_THREADS, 1) time_kernel_tc(const __grid_con
                         d0 = fmaf(-cp[j], lamp[j - 1].x, d0);
                         dn = fmaf(-cp[j], lamp[64 * 6 + j - 1].x, dn);
                     }
-                    zr = yr * __frcp_rn(d0);
-                    zi = (Ns & 1) ? 0.0f : yi * __frcp_rn(dn);
+                    zr = yr * rcp_approx(d0);
+                    zi = (Ns & 1) ? 0.0f : yi * rcp_approx(dn);
                 } else if (2 * k < Ns) {
                     float dr = one, di = 0.0f;
 #pragma unroll
@@ -480,7 +499,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1) time_kernel_tc(const __grid_con
                         di = fmaf(-cp[j], l.y, di);
                     }
                     // 2 y / d = 2 y conj(d) / |d|^2
-                    const float inv = 2.0f * __frcp_rn(fmaf(dr, dr, di * di));
+                    const float inv = 2.0f * rcp_approx(fmaf(dr, dr, di * di));
                     zr = fmaf(yr, dr, yi * di) * inv;
                     zi = fmaf(yi, dr, -yr * di) * inv;
                 }
@@ -554,7 +573,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1) time_kernel_tc(const __grid_con
                 b8[i] = LOWQ && A.norms == 2 && in ? xf * sa : 0.0f;
                 r8[i] = 0.0;
                 if (in) {
-                    const double res = f64_from_f32(sa);
+                    const double res = f64_of_f32_fast(sa);
                     const long long idx = gb + (long long)i * Mcol;
                     r8[i] = res;
                     if (A.accum) {
