@@ -162,7 +162,15 @@ typedef struct {
  *             alpha perturbation, so the iteration needs one sweep fewer.
  *             EXPD_GUESS_ZERO (1): u_n = 0.  The paper runs several initial
  *             guesses (Sec. 7) without fixing one.  GMRES and BiCGStab start
- *             from zero.
+ *             from zero under both.  EXPD_GUESS_GIVEN (2, every solver but the
+ *             sequential one): the initial iterate is read from slices
+ *             s-1..Nt-1 of the U argument (u_s..u_Nt) -- resuming from a
+ *             checkpoint, e.g. the last iterate a call that returned
+ *             EXPD_ERR_NOT_CONVERGED, EXPD_ERR_TIMEOUT or EXPD_ERR_CANCELLED
+ *             left in U (copied to host memory and back in between, or not).
+ *             The stopping tests are the fresh solve's: GMRES and BiCGStab
+ *             measure residuals against the zero start's P^{-1} f_s.  No
+ *             counterpart in the paper.
  *  kernel_flags  interchangeable kernel variants (each pair computes the same
  *             result; the autotuner chooses among them): EXPD_KF_TIME_SMEM
  *             takes the shared-memory time kernel where the register kernel
@@ -184,7 +192,7 @@ typedef struct {
  *             between iterations (EXPD_ERR_TIMEOUT when exceeded; the last
  *             iterate is returned); 0 = none.                              */
 enum { EXPD_JAC_LAGGED = 0, EXPD_JAC_MEAN_U0 = 1 };
-enum { EXPD_GUESS_LINEAR = 0, EXPD_GUESS_ZERO = 1 };
+enum { EXPD_GUESS_LINEAR = 0, EXPD_GUESS_ZERO = 1, EXPD_GUESS_GIVEN = 2 };
 enum { EXPD_KF_TIME_SMEM = 1, EXPD_KF_FFT_RADIX4 = 2, EXPD_KF_DST_FP64 = 4, EXPD_KF_DST_N64 = 8 };
 enum { EXPD_NLF_IF = 0, EXPD_NLF_ETD1 = 1 };
 typedef struct {
@@ -277,9 +285,10 @@ expd_status expd_precond_apply(expd_plan plan, const double* R, double* S, void*
  * (R_s^alpha)^{-1}(f_s + beta_s dt N(v^k) - R_s v^k) (Eq. (3.2), Eq. (4.4);
  * lagged N as in Eqs. (7.3)-(7.4)) from the initial iterate the scheme's
  * `guess` selects: by default (EXPD_GUESS_LINEAR) v^0_n = A^(n-s+1) u_{s-1},
- * with EXPD_GUESS_ZERO v^0 = 0.
+ * with EXPD_GUESS_ZERO v^0 = 0, with EXPD_GUESS_GIVEN the iterate in U.
  *   u0 [1 slice]; f [Nt slices] or NULL; U [Nt slices] output u_1..u_Nt
- *   (input for its first s-1 slices when startup = EXPD_STARTUP_GIVEN)
+ *   (input for its first s-1 slices when startup = EXPD_STARTUP_GIVEN, for
+ *   the others when guess = EXPD_GUESS_GIVEN)
  *   info may be NULL.
  * Returns EXPD_ERR_NOT_CONVERGED (U holds the last iterate) when max_iter
  * sweeps do not reach tol, EXPD_ERR_DIVERGED when an update is non-finite or

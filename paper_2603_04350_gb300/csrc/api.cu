@@ -287,6 +287,15 @@ expd_status stage_out(expd_plan p, const Staging& st, cudaStream_t s) {
     return EXPD_OK;
 }
 
+// The solvers read U when it carries start-up values or the initial iterate.
+bool u_is_input(expd_plan p) { return p->startup == EXPD_STARTUP_GIVEN || p->guess == EXPD_GUESS_GIVEN; }
+
+// EXPD_GUESS_GIVEN: the caller's iterate (U's unknown slices u_s..u_Nt,
+// physical) in the eigenbasis, float64, into dst
+expd_status load_guess(expd_plan p, const double* U, void* dst, cudaStream_t s) {
+    return spatial_forward64(p, U + (size_t)(p->order - 1) * p->Mp, dst, p->Ns, s);
+}
+
 void* eig_slice(expd_plan p, void* base, long long n) {
     return static_cast<char*>(base) + (size_t)n * p->Mcol * p->esz;
 }
@@ -619,8 +628,8 @@ expd_status plan_init_fields(expd_plan p, const expd_grid* grid, const expd_oper
         return expd_fail(EXPD_ERR_INVALID_ARG, "gmres_restart must be in [1, 64]");
     if (scheme->jacobian != EXPD_JAC_LAGGED && scheme->jacobian != EXPD_JAC_MEAN_U0)
         return expd_fail(EXPD_ERR_INVALID_ARG, "jacobian must be EXPD_JAC_LAGGED or EXPD_JAC_MEAN_U0");
-    if (scheme->guess != EXPD_GUESS_LINEAR && scheme->guess != EXPD_GUESS_ZERO)
-        return expd_fail(EXPD_ERR_INVALID_ARG, "guess must be EXPD_GUESS_LINEAR or EXPD_GUESS_ZERO");
+    if (scheme->guess != EXPD_GUESS_LINEAR && scheme->guess != EXPD_GUESS_ZERO && scheme->guess != EXPD_GUESS_GIVEN)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "guess must be EXPD_GUESS_LINEAR, EXPD_GUESS_ZERO or EXPD_GUESS_GIVEN");
     if (scheme->startup != EXPD_STARTUP_RAMP && scheme->startup != EXPD_STARTUP_GIVEN)
         return expd_fail(EXPD_ERR_INVALID_ARG, "unknown startup mode");
     if (scheme->kernel_flags & ~(EXPD_KF_TIME_SMEM | EXPD_KF_FFT_RADIX4 | EXPD_KF_DST_FP64 | EXPD_KF_DST_N64))
@@ -1546,7 +1555,7 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     expd_status st = call_begin(p, info, s);
     if (st != EXPD_OK) return st;
     Staging sg;
-    st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
+    st = stage_in(p, u0, f, U, p->Nt, u_is_input(p), sg, s);
     if (st != EXPD_OK) return st;
     const bool nl = p->nonlin != EXPD_NL_NONE;
     const bool etd = nl && p->nl_form == EXPD_NLF_ETD1;
@@ -1568,9 +1577,15 @@ expd_status expd_solve_fp(expd_plan p, const double* u0, const double* f, double
     enum { PH32, PHDD, PH64 };
     const bool use_dd = mixed && p->bc == EXPD_BC_PERIODIC && p->Cdd != nullptr;
     int phase = (mixed && p->U32 != nullptr) ? PH32 : PH64;
-    // the initial iterate: the last start-up slice propagated by A, or zero
+    // the initial iterate: the last start-up slice propagated by A, the
+    // caller's (a checkpoint), or zero
     if (p->guess == EXPD_GUESS_LINEAR) {
         st = linear_guess(p, phase == PH32 ? p->U32 : p->Uh, phase == PH32, s);
+        if (st != EXPD_OK) return st;
+    } else if (p->guess == EXPD_GUESS_GIVEN) {
+        st = load_guess(p, sg.U, p->Uh, s);
+        if (st == EXPD_OK && phase == PH32)
+            st = convert_f64_to_f32(p, static_cast<const double*>(p->Uh), static_cast<float*>(p->U32), nvec, s);
         if (st != EXPD_OK) return st;
     } else if (phase == PH32) {
         EXPD_CUDA_TRY(cudaMemsetAsync(p->U32, 0, (size_t)nvec * sizeof(float), s));
@@ -1837,7 +1852,7 @@ expd_status expd_solve_sequential(expd_plan p, const double* u0, const double* f
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     EXPD_CUDA_TRY(plan_bind_stream(p, s));
     Staging sg;
-    expd_status st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
+    expd_status st = stage_in(p, u0, f, U, p->Nt, u_is_input(p), sg, s);
     if (st != EXPD_OK) return st;
     // u_0 .. u_{s-1} (the ramp or the given values) exactly as the all-at-once solve takes them
     st = setup_start(p, sg.u0, sg.f, sg.U, s);
@@ -1912,14 +1927,19 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
     double* w = c + n;
     double* h = w + n;  // [128] results + partials
     Staging sg;
-    st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
+    st = stage_in(p, u0, f, U, p->Nt, u_is_input(p), sg, s);
     if (st != EXPD_OK) return st;
     st = setup_start(p, sg.u0, sg.f, sg.U, s);
     if (st != EXPD_OK) return st;
     st = call_mark(p, info, 1, s);
     if (st != EXPD_OK) return st;
     double* x = static_cast<double*>(p->Uh);
-    EXPD_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    if (p->guess == EXPD_GUESS_GIVEN) {
+        st = load_guess(p, sg.U, x, s);  // resume from the caller's iterate
+        if (st != EXPD_OK) return st;
+    } else {
+        EXPD_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    }
 
     // out = P^{-1} R v  (the preconditioned operator of Theorem 3.3)
     auto apply_op = [&](const double* v, double* out) -> expd_status {
@@ -2007,7 +2027,7 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
         if (st != EXPD_OK) return st;
         cn = sqrt(cn2);
         double beta = cn;
-        bool first = true;
+        bool first = p->guess != EXPD_GUESS_GIVEN;  // x = 0: the first residual is c
         while (cn > 0) {
             if (!first) {
                 // r = P^{-1}(f_s - R x): the residual in float64, then preconditioned
@@ -2157,7 +2177,7 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
         cn = sqrt(cn2);
         std::vector<cd> Hc((size_t)(m + 1) * m), csc(m), gc(m + 1), h1(m + 1), h2(m + 1), yc(m);
         std::vector<double> snc(m);
-        bool first = true;
+        bool first = p->guess != EXPD_GUESS_GIVEN;  // x = 0: the first residual is c
         while (cn > 0) {
             if (first) {
                 EXPD_CUDA_TRY(cudaMemcpyAsync(V, c, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -2266,7 +2286,7 @@ expd_status expd_solve_gmres(expd_plan p, const double* u0, const double* f, dou
     st = dots(c, 1, c, &cn2);
     if (st != EXPD_OK) return st;
     cn = sqrt(cn2);
-    bool first = true;
+    bool first = p->guess != EXPD_GUESS_GIVEN;  // x = 0: the first residual is c
     while (cn > 0) {
         // r = P^{-1}(f_s - R x)   (= c on the first cycle, x = 0)
         if (first) {
@@ -2403,14 +2423,19 @@ expd_status expd_solve_bicgstab(expd_plan p, const double* u0, const double* f, 
     double* c = v + n;
     double* h = c + n;
     Staging sg;
-    st = stage_in(p, u0, f, U, p->Nt, p->startup == EXPD_STARTUP_GIVEN, sg, s);
+    st = stage_in(p, u0, f, U, p->Nt, u_is_input(p), sg, s);
     if (st != EXPD_OK) return st;
     st = setup_start(p, sg.u0, sg.f, sg.U, s);
     if (st != EXPD_OK) return st;
     st = call_mark(p, info, 1, s);
     if (st != EXPD_OK) return st;
     double* x = static_cast<double*>(p->Uh);
-    EXPD_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    if (p->guess == EXPD_GUESS_GIVEN) {
+        st = load_guess(p, sg.U, x, s);  // resume from the caller's iterate
+        if (st != EXPD_OK) return st;
+    } else {
+        EXPD_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    }
     auto apply_op = [&](const double* in, double* out) -> expd_status {  // out = P^{-1} R in
         TimeOp op;
         op.X = in;
@@ -2452,8 +2477,9 @@ expd_status expd_solve_bicgstab(expd_plan p, const double* u0, const double* f, 
         op.out = c;
         st = time_apply(p, op, s);
     }
-    if (st == EXPD_OK) st = copy(c, r);
-    if (st == EXPD_OK) st = copy(c, rhat);
+    // r = P^{-1}(f_s - R x): c from x = 0, recomputed from a given iterate
+    if (st == EXPD_OK) st = p->guess == EXPD_GUESS_GIVEN ? residual_op(r) : copy(c, r);
+    if (st == EXPD_OK) st = copy(r, rhat);
     if (st == EXPD_OK) EXPD_CUDA_TRY(cudaMemsetAsync(pv, 0, 2 * n * sizeof(double), s));  // p, v
     if (st != EXPD_OK) return st;
     double cc = 0;

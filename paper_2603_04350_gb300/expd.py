@@ -24,7 +24,7 @@ NL_NONE, NL_ALLEN_CAHN = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 STARTUP_RAMP, STARTUP_GIVEN = 0, 1
 JAC_LAGGED, JAC_MEAN_U0 = 0, 1
-GUESS_LINEAR, GUESS_ZERO = 0, 1
+GUESS_LINEAR, GUESS_ZERO, GUESS_GIVEN = 0, 1, 2
 KF_TIME_SMEM, KF_FFT_RADIX4, KF_DST_FP64, KF_DST_N64 = 1, 2, 4, 8
 NLF_IF, NLF_ETD1 = 0, 1
 MAX_HISTORY = 128

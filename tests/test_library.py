@@ -83,7 +83,7 @@ def test_plan_create_rejects_too_long_windows_without_touching_the_gpu(expd):
     (dict(n=(8, 8, 8)), "ndim"),
     (dict(bc=1, n=(7, 7), b=(0.5, 0.0)), "advection needs a periodic grid"),
     (dict(jacobian=5), "jacobian"),
-    (dict(guess=2), "guess"),
+    (dict(guess=3), "guess"),
     (dict(a=0.01 + 1j), "complex_state"),
     (dict(c=2j), "complex_state"),
 ])
