@@ -66,11 +66,15 @@ constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // every wait gives up
 // tiles, for transforms too small to give every SM a 128-column tile; a
 // plan selects it with EXPD_KF_DST_N64).  A stage holds one 128 x 64 A tile
 // and one BN x 64 B tile; TMEM holds acc[0], acc[1], hi and lo, BN columns each.
-template <int BN>
+// SK: 64-K tile pairs per stage -- 2 (one 32 KB A image and one 32 KB B image
+// of 128 K, eight MMAs per stage: half the stage hand-offs of the copy and
+// MMA threads per MMA) where the 128-column B tiles are contiguous along K and
+// the K-tile count is even, else 1.
+template <int BN, int SK = 1>
 struct TcShape {
     static constexpr int B_BYTES = BN * TC_BK * 2;
-    static constexpr int STAGE_BYTES = TC_TILE_BYTES + B_BYTES;
-    static constexpr int STAGES = BN == 128 ? 6 : 8;
+    static constexpr int STAGE_BYTES = SK * (TC_TILE_BYTES + B_BYTES);
+    static constexpr int STAGES = SK == 2 ? 3 : (BN == 128 ? 6 : 8);
     static constexpr int TMEM_COLS = 4 * BN;
     // drain warps: BN / 32 per TMEM lane quarter, 32 columns each (warp 0
     // copies, warp 1 issues the MMAs, warps 2.. drain); enough warps that one's
@@ -84,7 +88,8 @@ struct TcShape {
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                       ((uint32_t)(TC_BM >> 4) << 24);
 };
-static_assert(TcShape<128>::SMEM <= 232448 && TcShape<64>::SMEM <= 232448, "stage ring within 227 KB");
+static_assert(TcShape<128>::SMEM <= 232448 && TcShape<64>::SMEM <= 232448 && TcShape<128, 2>::SMEM <= 232448,
+              "stage ring within 227 KB");
 
 struct TcArgs {
     const uint16_t* A;        // packed digit slices of the rows: [nsl][rows/128][KB][8192]
@@ -389,9 +394,9 @@ __device__ __forceinline__ double scaled_sum(float hi, float lo, int E) {
 // float32), and warps 2..9 drain the finished buffer into the double-float sum
 // in TMEM while the next group accumulates.  After a tile's last group the
 // drain warps write the float64 result.
-template <int BN>
-__global__ void __launch_bounds__(TcShape<BN>::THREADS, 1) dst_mma_kernel(const __grid_constant__ TcArgs a) {
-    typedef TcShape<BN> SH;
+template <int BN, int SK>
+__global__ void __launch_bounds__(TcShape<BN, SK>::THREADS, 1) dst_mma_kernel(const __grid_constant__ TcArgs a) {
+    typedef TcShape<BN, SK> SH;
     constexpr int TC_STAGES = SH::STAGES;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -454,15 +459,16 @@ __global__ void __launch_bounds__(TcShape<BN>::THREADS, 1) dst_mma_kernel(const 
                 for (int p = 0; p < a.npairs && ok; ++p) {
                     const uint16_t* Ab = Aq + a.pi[p] * a.a_slice + rt * KB * TC_TILE_ELEMS;
                     const uint16_t* Bb = Bq + a.pj[p] * a.b_slice + boff;
-                    for (int kb = 0; kb < KB; ++kb, ++it) {
+                    for (int kb = 0; kb < KB; kb += SK, ++it) {
                         if (!mbar_wait_fast(empty(cs), cph ^ 1u, abort_flag, a.cancel)) {
                             ok = false;
                             break;
                         }
+                        // SK consecutive K tiles: contiguous in the packed images
                         const uint32_t st = sm0 + (uint32_t)cs * SH::STAGE_BYTES, fb = full(cs);
                         mbar_arrive_expect_tx(fb, SH::STAGE_BYTES);
-                        bulk_g2s(st, Ab + (long long)kb * TC_TILE_ELEMS, TC_TILE_BYTES, fb);
-                        bulk_g2s(st + TC_TILE_BYTES, Bb + (long long)kb * TC_TILE_ELEMS, SH::B_BYTES, fb);
+                        bulk_g2s(st, Ab + (long long)kb * TC_TILE_ELEMS, SK * TC_TILE_BYTES, fb);
+                        bulk_g2s(st + SK * TC_TILE_BYTES, Bb + (long long)kb * TC_TILE_ELEMS, SK * SH::B_BYTES, fb);
                         if (++cs == TC_STAGES) {
                             cs = 0;
                             cph ^= 1u;
@@ -497,7 +503,7 @@ __global__ void __launch_bounds__(TcShape<BN>::THREADS, 1) dst_mma_kernel(const 
                     const uint32_t d = tmem + (uint32_t)(b * BN);
                     for (int p = a.gstart[g]; p < a.gstart[g + 1] && ok; ++p) {
                         const bool first = p == a.gstart[g];
-                        for (int kb = 0; kb < KB; ++kb, ++it) {
+                        for (int kb = 0; kb < KB; kb += SK, ++it) {
                             if (!mbar_wait_fast(full(cs), cph, abort_flag, a.cancel)) {
                                 ok = false;
                                 break;
@@ -506,10 +512,14 @@ __global__ void __launch_bounds__(TcShape<BN>::THREADS, 1) dst_mma_kernel(const 
                             // descriptors of the stage's A and B tiles; 16 bf16 of K =
                             // two core matrices = 256 bytes = 16 in the address field
                             const uint64_t da = desc0 + (uint64_t)(cs * (SH::STAGE_BYTES >> 4));
-                            const uint64_t db = da + (uint64_t)(TC_TILE_BYTES >> 4);
+                            const uint64_t db = da + (uint64_t)((SK * TC_TILE_BYTES) >> 4);
 #pragma unroll
-                            for (int q = 0; q < TC_BK / 16; ++q)
-                                tc_mma(d, da + 16u * q, db + 16u * q, SH::IDESC, !first || (kb | q) != 0);
+                            for (int j = 0; j < SK; ++j)
+#pragma unroll
+                                for (int q = 0; q < TC_BK / 16; ++q)
+                                    tc_mma(d, da + (uint64_t)(j * (TC_TILE_BYTES >> 4)) + 16u * q,
+                                           db + (uint64_t)(j * (SH::B_BYTES >> 4)) + 16u * q, SH::IDESC,
+                                           !first || (kb | j | q) != 0);
                             tc_commit(empty(cs));
                             if (++cs == TC_STAGES) {
                                 cs = 0;
@@ -692,11 +702,14 @@ expd_status mma_pass(expd_plan p, const uint16_t* A, const int* ea, long long ro
     KProf kp(p, s, EXPD_K_DST_TC, a.nprob * 2.0 * nsl * ((double)rows * K + (double)N * K) + 8.0 * rows * a.Nout,
              a.nprob * 2.0 * np * (double)rows * N * K);
     if (bn == 64) {
-        EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel<64>, TcShape<64>::SMEM));
-        dst_mma_kernel<64><<<grid, TcShape<64>::THREADS, TcShape<64>::SMEM, s>>>(a);
+        EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel<64, 1>, TcShape<64>::SMEM));
+        dst_mma_kernel<64, 1><<<grid, TcShape<64>::THREADS, TcShape<64>::SMEM, s>>>(a);
+    } else if (a.KB % 2 == 0) {
+        EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel<128, 2>, TcShape<128, 2>::SMEM));
+        dst_mma_kernel<128, 2><<<grid, TcShape<128, 2>::THREADS, TcShape<128, 2>::SMEM, s>>>(a);
     } else {
-        EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel<128>, TcShape<128>::SMEM));
-        dst_mma_kernel<128><<<grid, TcShape<128>::THREADS, TcShape<128>::SMEM, s>>>(a);
+        EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel<128, 1>, TcShape<128>::SMEM));
+        dst_mma_kernel<128, 1><<<grid, TcShape<128>::THREADS, TcShape<128>::SMEM, s>>>(a);
     }
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;

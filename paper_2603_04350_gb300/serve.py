@@ -132,7 +132,11 @@ class Engine:
         self.dev = torch.device("cuda", device)
         torch.cuda.set_device(self.dev)
         free, _ = torch.cuda.mem_get_info(self.dev)
-        self.budget = int(budget_bytes if budget_bytes is not None else 0.7 * free)
+        # 60 % of the free memory: the rest absorbs blocks that freed requests
+        # leave in the allocators' pools (not yet reusable by another worker's
+        # stream), which at 70 % made the largest requests' plan creation fail
+        # and retry alone
+        self.budget = int(budget_bytes if budget_bytes is not None else 0.6 * free)
         self.workers = workers
         self.precision = precision
         self.max_iter = max_iter
