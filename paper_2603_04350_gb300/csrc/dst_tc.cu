@@ -277,21 +277,57 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restric
 // n/2 of them with S's digits sums to at most (n/2) 256 128 = 2^24 for n =
 // 1024, the bound of the unfolded product, so the same accumulator groups
 // hold them exactly.
+//
+// STAGED: the CTA's rows come into shared memory by one bulk copy each (row
+// stride n + 2 values, so that the eight rows a warp reads in the digit pass
+// fall on distinct banks) and both passes read them there: every value leaves
+// HBM once, with the CTA's whole 64 KB (n = 1024) in flight at a time.
+// Otherwise both passes read global memory (inputs not 16-byte aligned).
+template <bool STAGED>
 __global__ void __launch_bounds__(256) split_fold_kernel(const double* __restrict__ in, long long rows, int n,
                                                          int nsl, uint16_t* __restrict__ out_u,
                                                          uint16_t* __restrict__ out_v, long long slice_elems,
-                                                         int* __restrict__ ex) {
+                                                         int* __restrict__ ex, int* __restrict__ err) {
     __shared__ int se[8], sbad[8];
+    __shared__ __align__(8) uint64_t sbar;
+    extern __shared__ __align__(16) double srows[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long r0 = (long long)blockIdx.x * 8;
+    const int stride = n + 2;
+    auto row = [&](int rr) -> const double* { return STAGED ? srows + (size_t)rr * stride : in + (r0 + rr) * n; };
+    if constexpr (STAGED) {
+        const uint32_t bar = smem_u32(&sbar);
+        const int nr = (int)min(8LL, rows - r0);
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive_expect_tx(bar, (uint32_t)(nr * n * 8));
+            for (int i = 0; i < nr; ++i) bulk_g2s(smem_u32(srows + (size_t)i * stride), in + (r0 + i) * n, (uint32_t)n * 8u, bar);
+        }
+        __syncthreads();
+        // a copy that has not landed after 2 s: flagged, the CTA leaves
+        bool done = mbar_try_wait(bar, 0);
+        if (!done) {
+            const uint64_t t0 = globaltimer();
+            for (uint32_t it = 1; !done; ++it) {
+                done = mbar_try_wait(bar, 0);
+                if (!done && (it & 63) == 0 && globaltimer() - t0 > TC_WAIT_NS) break;
+            }
+        }
+        if (!__syncthreads_and(done)) {
+            if (threadIdx.x == 0) atomicExch(err, 1);
+            return;
+        }
+    }
     {
         const long long r = r0 + warp;
         int e = 0, bad = 0;
         if (r < rows) {
-            const double2* x = reinterpret_cast<const double2*>(in + r * n);
+            const double2* x = reinterpret_cast<const double2*>(row(warp));
             unsigned long long mx = 0;
             for (int c = lane; c < (n >> 1); c += 32) {
-                const double2 v = __ldg(x + c);
+                const double2 v = x[c];
                 mx = max(mx, (unsigned long long)__double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFull);
                 mx = max(mx, (unsigned long long)__double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFull);
             }
@@ -312,7 +348,7 @@ __global__ void __launch_bounds__(256) split_fold_kernel(const double* __restric
     if (r >= rows) return;
     const int e = se[rr];
     const bool bad = sbad[rr] != 0;
-    const double* x = in + r * n;
+    const double* x = row(rr);
     const int K = n >> 1, KB = K >> 6;
     const unsigned long long off = digit_offset(nsl);
     const int nch = K >> 3;
@@ -323,7 +359,7 @@ __global__ void __launch_bounds__(256) split_fold_kernel(const double* __restric
         const double2* xb = reinterpret_cast<const double2*>(x + n - 8 * c - 8);  // x_{n-1-k} for k = 8c+7 .. 8c
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-            const double2 v = __ldg(xa + h), w = __ldg(xb + h);
+            const double2 v = xa[h], w = xb[h];
             unsigned n0, n1, m0, m1;
             Y[2 * h] = digit_magnitude((unsigned long long)__double_as_longlong(v.x), e, nsl, &n0);
             Y[2 * h + 1] = digit_magnitude((unsigned long long)__double_as_longlong(v.y), e, nsl, &n1);
@@ -660,7 +696,14 @@ expd_status split_fold(expd_plan p, const double* in, long long rows, int n, uin
                        long long slice_elems, int* ex, cudaStream_t s) {
     const int nsl = p->tc_nsl;
     KProf kp(p, s, EXPD_K_DST_SPLIT, (double)rows * n * (8.0 + 2.0 * nsl) + 4.0 * rows, 0.0);
-    split_fold_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(in, rows, n, nsl, out_u, out_v, slice_elems, ex);
+    const unsigned grid = (unsigned)((rows + 7) / 8);
+    const size_t staged = (size_t)8 * (n + 2) * sizeof(double);
+    if (reinterpret_cast<uintptr_t>(in) % 16 == 0 && n % 2 == 0 && staged <= 232448 - 1024) {
+        EXPD_CUDA_TRY(smem_allow((const void*)split_fold_kernel<true>, staged));
+        split_fold_kernel<true><<<grid, 256, staged, s>>>(in, rows, n, nsl, out_u, out_v, slice_elems, ex, p->tc_err);
+    } else {
+        split_fold_kernel<false><<<grid, 256, 0, s>>>(in, rows, n, nsl, out_u, out_v, slice_elems, ex, p->tc_err);
+    }
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
 }
