@@ -399,36 +399,49 @@ __global__ void linear_guess_kernel(const double* __restrict__ E, const double* 
     }
 }
 
-// grid: x over a slice's elements, y over the Ns slices
+// grid: x over a slice's elements, y over the Ns slices; a thread takes four
+// elements a grid stride apart per iteration, their source loads issued
+// together (four loads in flight per thread)
 __global__ void rhs_kernel(RhsArgs r) {
     const int i = blockIdx.y;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < r.nelem;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long idx = (long long)i * r.nelem + e;
-        const int n = r.s + i;
-        double acc = r.fh ? r.bdt * r.fh[(long long)(n - 1) * r.nelem + e] : 0.0;
-        if (i < r.s && !r.adv) {
-            const double Em = r.E[e >> r.eshift];
-            double Ej = 1.0;
-            for (int j = 1; j <= r.s; ++j) {
-                Ej *= Em;
-                if (n - j < r.s) acc = fma(r.a[j] * Ej, r.Sh[(long long)(n - j) * r.nelem + e], acc);
-            }
-        } else if (i < r.s) {
-            const long long m = e >> 1;
-            const double er = r.E[2 * m], ei = r.E[2 * m + 1];
-            double pr = 1.0, pi = 0.0;
-            for (int j = 1; j <= r.s; ++j) {
-                const double t = pr * er - pi * ei;
-                pi = pr * ei + pi * er;
-                pr = t;
-                if (n - j < r.s) acc += cmul_elem(r.a[j] * pr, r.a[j] * pi, r.Sh + (long long)(n - j) * r.nelem, e);
-            }
+    const int n = r.s + i;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; e0 < r.nelem; e0 += 4 * stride) {
+        double fv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long e = e0 + u * stride;
+            fv[u] = r.fh && e < r.nelem ? r.fh[(long long)(n - 1) * r.nelem + e] : 0.0;
         }
-        if (i == 0 && r.nl0) acc = fma(r.phi[e >> r.eshift], r.nl0[e], acc);
-        if (r.F32) r.F32[idx] = f32_rn_from_f64(acc);
-        if (r.fh_dd) reinterpret_cast<dd*>(r.Fh)[idx] = dd_from_f64(acc);
-        else r.Fh[idx] = acc;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long e = e0 + u * stride;
+            if (e >= r.nelem) break;
+            const long long idx = (long long)i * r.nelem + e;
+            double acc = r.fh ? r.bdt * fv[u] : 0.0;
+            if (i < r.s && !r.adv) {
+                const double Em = r.E[e >> r.eshift];
+                double Ej = 1.0;
+                for (int j = 1; j <= r.s; ++j) {
+                    Ej *= Em;
+                    if (n - j < r.s) acc = fma(r.a[j] * Ej, r.Sh[(long long)(n - j) * r.nelem + e], acc);
+                }
+            } else if (i < r.s) {
+                const long long m = e >> 1;
+                const double er = r.E[2 * m], ei = r.E[2 * m + 1];
+                double pr = 1.0, pi = 0.0;
+                for (int j = 1; j <= r.s; ++j) {
+                    const double t = pr * er - pi * ei;
+                    pi = pr * ei + pi * er;
+                    pr = t;
+                    if (n - j < r.s) acc += cmul_elem(r.a[j] * pr, r.a[j] * pi, r.Sh + (long long)(n - j) * r.nelem, e);
+                }
+            }
+            if (i == 0 && r.nl0) acc = fma(r.phi[e >> r.eshift], r.nl0[e], acc);
+            if (r.F32) r.F32[idx] = f32_rn_from_f64(acc);
+            if (r.fh_dd) reinterpret_cast<dd*>(r.Fh)[idx] = dd_from_f64(acc);
+            else r.Fh[idx] = acc;
+        }
     }
 }
 
