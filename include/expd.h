@@ -30,7 +30,10 @@
  *    host pointers; the library detects which with cudaPointerGetAttributes.
  *    Host buffers are staged through plan-owned device buffers with the
  *    copies enqueued on the call's stream, so a call with host buffers
- *    includes its own host<->device traffic.  The caller owns every buffer it
+ *    includes its own host<->device traffic.  Device buffers that are not
+ *    16-byte aligned (a view starting at an odd element) are staged the same
+ *    way, by device-to-device copies, and such a call returns once its
+ *    results are in the caller's buffer, as a host-pointer call does.  The caller owns every buffer it
  *    passes; the library never keeps a pointer past the call.
  *  - Streams.  `stream` is a cudaStream_t (NULL = the legacy default
  *    stream).  Device-pointer calls are asynchronous except that solvers
@@ -255,7 +258,8 @@ expd_status expd_plan_workspace_bytes(expd_plan plan, size_t* bytes);
 /* Device bytes expd_plan_create would allocate for these arguments, computed
  * without allocating anything (admission control before creating a plan).
  * flags adds the buffers a plan allocates on first use: EXPD_FOOTPRINT_SOURCE
- * (a source f is passed), EXPD_FOOTPRINT_HOST (host pointers are passed),
+ * (a source f is passed), EXPD_FOOTPRINT_HOST (host pointers, or device
+ * pointers that are not 16-byte aligned, are passed),
  * EXPD_FOOTPRINT_GMRES (expd_solve_gmres or expd_solve_bicgstab is called). */
 enum { EXPD_FOOTPRINT_SOURCE = 1, EXPD_FOOTPRINT_HOST = 2, EXPD_FOOTPRINT_GMRES = 4 };
 expd_status expd_plan_footprint_bytes(const expd_grid* grid, const expd_operator* op, double dt, int Nt,
@@ -361,7 +365,9 @@ expd_status expd_plan_cancel(expd_plan plan);
  * fixed device array of EXPD_NOALLOC_SCRATCH_BYTES bytes that each GPU loading
  * the library holds until the process exits.  It calls no cudaMalloc, no
  * cudaFree and no allocating library routine.
- *   R, S   device pointers, [Ns slices] as for expd_precond_apply (may alias)
+ *   R, S   16-byte-aligned device pointers, [Ns slices] as for
+ *          expd_precond_apply (may alias); other pointers get
+ *          EXPD_ERR_INVALID_ARG (staging them would need memory)
  * Limits: at most 512 unknown slices, and the tables, the eigen-space copy of
  * R, the spatial scratch and the norm partials must fit the array (about
  * 2 Ns M complex values plus the DST matrices on Dirichlet grids); larger

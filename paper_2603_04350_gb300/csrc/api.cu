@@ -92,6 +92,14 @@ bool is_device_ptr(const void* ptr) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Whether a caller's buffer goes through the plan's staging buffers: host
+// memory, and device memory that is not 16-byte aligned (a view starting at
+// an odd element: the kernels read 16-byte vectors and copy 16-byte-aligned
+// rows in bulk, so they see only aligned buffers)
+bool needs_stage(const void* ptr) {
+    return !is_device_ptr(ptr) || (reinterpret_cast<uintptr_t>(ptr) & 15u) != 0;
+}
+
 // Pinned host words for the per-sweep norm read-back, handed out from one
 // process-wide arena (freeing pinned memory would synchronise the device).
 std::mutex g_pin_mu;
@@ -250,9 +258,9 @@ expd_status ensure_stage(expd_plan p) {
 // Resolve u0/f (inputs, [1]/[Nt] slices) and U ([U_slices], in/out) to device memory.
 expd_status stage_in(expd_plan p, const double* u0, const double* f, double* U, size_t U_slices, bool U_is_input,
                      Staging& st, cudaStream_t s) {
-    const bool hu0 = u0 && !is_device_ptr(u0);
-    const bool hf = f && !is_device_ptr(f);
-    const bool hU = U && !is_device_ptr(U);
+    const bool hu0 = u0 && needs_stage(u0);
+    const bool hf = f && needs_stage(f);
+    const bool hU = U && needs_stage(U);
     if (hu0 || hf || hU) {
         expd_status r = ensure_stage(p);
         if (r != EXPD_OK) return r;
@@ -263,18 +271,18 @@ expd_status stage_in(expd_plan p, const double* u0, const double* f, double* U, 
     st.U = U;
     st.U_slices = U_slices;
     if (hu0) {
-        EXPD_CUDA_TRY(cudaMemcpyAsync(p->stage, u0, M * sizeof(double), cudaMemcpyHostToDevice, s));
+        EXPD_CUDA_TRY(cudaMemcpyAsync(p->stage, u0, M * sizeof(double), cudaMemcpyDefault, s));
         st.u0 = p->stage;
     }
     if (hf) {
-        EXPD_CUDA_TRY(cudaMemcpyAsync(p->stage + M, f, (size_t)p->Nt * M * sizeof(double), cudaMemcpyHostToDevice, s));
+        EXPD_CUDA_TRY(cudaMemcpyAsync(p->stage + M, f, (size_t)p->Nt * M * sizeof(double), cudaMemcpyDefault, s));
         st.f = p->stage + M;
     }
     if (hU) {
         st.U_host = U;
         st.U = p->stage + (size_t)(p->Nt + 1) * M;
         if (U_is_input)
-            EXPD_CUDA_TRY(cudaMemcpyAsync(st.U, U, U_slices * M * sizeof(double), cudaMemcpyHostToDevice, s));
+            EXPD_CUDA_TRY(cudaMemcpyAsync(st.U, U, U_slices * M * sizeof(double), cudaMemcpyDefault, s));
     }
     return EXPD_OK;
 }
@@ -282,7 +290,7 @@ expd_status stage_in(expd_plan p, const double* u0, const double* f, double* U, 
 expd_status stage_out(expd_plan p, const Staging& st, cudaStream_t s) {
     if (st.U_host)
         EXPD_CUDA_TRY(cudaMemcpyAsync(st.U_host, st.U, st.U_slices * (size_t)p->Mp * sizeof(double),
-                                      cudaMemcpyDeviceToHost, s));
+                                      cudaMemcpyDefault, s));
     if (st.U_host) EXPD_CUDA_TRY(cudaStreamSynchronize(s));
     return EXPD_OK;
 }
@@ -1467,8 +1475,9 @@ expd_status expd_residual(expd_plan p, const double* u0, const double* f, const 
     Staging sg;
     expd_status st = stage_in(p, u0, f, const_cast<double*>(U), p->Nt, true, sg, s);
     if (st != EXPD_OK) return st;
-    // R may be host memory: compute into the staging area or the caller's buffer
-    const bool hR = !is_device_ptr(R);
+    // R may be host (or unaligned device) memory: compute into the staging
+    // area or the caller's buffer
+    const bool hR = needs_stage(R);
     double* Rd = R;
     if (hR) {
         st = ensure_stage(p);
@@ -1503,7 +1512,7 @@ expd_status expd_residual(expd_plan p, const double* u0, const double* f, const 
     if (st == EXPD_OK) st = dst_tc_check(p, s);
     if (st != EXPD_OK) return st;
     if (hR) {
-        EXPD_CUDA_TRY(cudaMemcpyAsync(R, Rd, (size_t)p->Ns * M * sizeof(double), cudaMemcpyDeviceToHost, s));
+        EXPD_CUDA_TRY(cudaMemcpyAsync(R, Rd, (size_t)p->Ns * M * sizeof(double), cudaMemcpyDefault, s));
         EXPD_CUDA_TRY(cudaStreamSynchronize(s));
     }
     return EXPD_OK;
@@ -1517,13 +1526,13 @@ expd_status expd_precond_apply(expd_plan p, const double* R, double* S, void* st
     const size_t bytes = (size_t)p->Ns * M * sizeof(double);
     const double* Rd = R;
     double* Sd = S;
-    const bool hR = !is_device_ptr(R), hS = !is_device_ptr(S);
+    const bool hR = needs_stage(R), hS = needs_stage(S);
     if (hR || hS) {
         expd_status st = ensure_stage(p);
         if (st != EXPD_OK) return st;
     }
     if (hR) {
-        EXPD_CUDA_TRY(cudaMemcpyAsync(p->stage, R, bytes, cudaMemcpyHostToDevice, s));
+        EXPD_CUDA_TRY(cudaMemcpyAsync(p->stage, R, bytes, cudaMemcpyDefault, s));
         Rd = p->stage;
     }
     if (hS) Sd = p->stage + (size_t)p->Nt * M;
@@ -1540,7 +1549,7 @@ expd_status expd_precond_apply(expd_plan p, const double* R, double* S, void* st
     if (st == EXPD_OK) st = dst_tc_check(p, s);
     if (st != EXPD_OK) return st;
     if (hS) {
-        EXPD_CUDA_TRY(cudaMemcpyAsync(S, Sd, bytes, cudaMemcpyDeviceToHost, s));
+        EXPD_CUDA_TRY(cudaMemcpyAsync(S, Sd, bytes, cudaMemcpyDefault, s));
         EXPD_CUDA_TRY(cudaStreamSynchronize(s));
     }
     return EXPD_OK;

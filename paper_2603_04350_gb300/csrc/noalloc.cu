@@ -212,6 +212,8 @@ extern "C" expd_status expd_precond_apply_noalloc(const expd_grid* grid, const e
     if (!R || !S) return expd_fail(EXPD_ERR_INVALID_ARG, "R and S are required");
     if (!expd_is_device_ptr(R) || !expd_is_device_ptr(S))
         return expd_fail(EXPD_ERR_INVALID_ARG, "R and S must be device pointers (host buffers would need staging)");
+    if (((reinterpret_cast<uintptr_t>(R) | reinterpret_cast<uintptr_t>(S)) & 15u) != 0)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "R and S must be 16-byte aligned (unaligned buffers would need staging)");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     expd_plan_s pl;  // plan fields on the stack; every buffer below points into the scratch array
     expd_plan p = &pl;
