@@ -282,7 +282,8 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const double* __restric
 // stride n + 2 values, so that the eight rows a warp reads in the digit pass
 // fall on distinct banks) and both passes read them there: every value leaves
 // HBM once, with the CTA's whole 64 KB (n = 1024) in flight at a time.
-// Otherwise both passes read global memory (inputs not 16-byte aligned).
+// Otherwise (rows too long to stage) both passes read global memory.  Both
+// read 16-byte vectors: the rows start 16-byte aligned (the caller checks).
 template <bool STAGED>
 __global__ void __launch_bounds__(256) split_fold_kernel(const double* __restrict__ in, long long rows, int n,
                                                          int nsl, uint16_t* __restrict__ out_u,
@@ -685,6 +686,9 @@ expd_status tc_dalloc(expd_plan p, void** ptr, size_t bytes, const char* what) {
 expd_status split_rows(expd_plan p, const double* in, long long rows, int K, long long lda, uint16_t* out,
                        long long slice_elems, int* ex, int fixed_e, cudaStream_t s) {
     const int nsl = p->tc_nsl;
+    // the kernel reads 16-byte vectors: every row starts 16-byte aligned
+    if (reinterpret_cast<uintptr_t>(in) % 16 != 0 || lda % 2 != 0 || K % 2 != 0)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "digit split: rows must start 16-byte aligned");
     KProf kp(p, s, EXPD_K_DST_SPLIT, (double)rows * K * (8.0 + 2.0 * nsl) + 4.0 * rows, 0.0);
     split_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(in, rows, K, lda, nsl, out, slice_elems, ex, fixed_e);
     EXPD_CUDA_TRY(cudaGetLastError());
@@ -696,9 +700,11 @@ expd_status split_fold(expd_plan p, const double* in, long long rows, int n, uin
                        long long slice_elems, int* ex, cudaStream_t s) {
     const int nsl = p->tc_nsl;
     KProf kp(p, s, EXPD_K_DST_SPLIT, (double)rows * n * (8.0 + 2.0 * nsl) + 4.0 * rows, 0.0);
+    if (reinterpret_cast<uintptr_t>(in) % 16 != 0 || n % 2 != 0)
+        return expd_fail(EXPD_ERR_INVALID_ARG, "folded digit split: rows must start 16-byte aligned");
     const unsigned grid = (unsigned)((rows + 7) / 8);
     const size_t staged = (size_t)8 * (n + 2) * sizeof(double);
-    if (reinterpret_cast<uintptr_t>(in) % 16 == 0 && n % 2 == 0 && staged <= 232448 - 1024) {
+    if (staged <= 232448 - 1024) {
         EXPD_CUDA_TRY(smem_allow((const void*)split_fold_kernel<true>, staged));
         split_fold_kernel<true><<<grid, 256, staged, s>>>(in, rows, n, nsl, out_u, out_v, slice_elems, ex, p->tc_err);
     } else {
