@@ -64,12 +64,12 @@ constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // every wait gives up
 
 // Tile shapes: BN = 128 output columns per tile (the default) or 64 (twice the
 // tiles, for transforms too small to give every SM a 128-column tile; a
-// plan selects it with EXPD_KF_DST_N64).  A stage holds one 128 x 64 A tile
-// and one BN x 64 B tile; TMEM holds acc[0], acc[1], hi and lo, BN columns each.
-// SK: 64-K tile pairs per stage -- 2 (one 32 KB A image and one 32 KB B image
-// of 128 K, eight MMAs per stage: half the stage hand-offs of the copy and
-// MMA threads per MMA) where the 128-column B tiles are contiguous along K and
-// the K-tile count is even, else 1.
+// plan selects it with EXPD_KF_DST_N64).  A stage holds SK 128 x 64 A tiles
+// and SK BN x 64 B tiles; TMEM holds acc[0], acc[1], hi and lo, BN columns each.
+// SK: 64-K tile pairs per stage -- 2 for the 128-column tiles (one 32 KB A
+// image and one 32 KB B image of 128 K, eight MMAs per stage: half the stage
+// hand-offs of the copy and MMA threads per MMA; their B tiles are contiguous
+// along K and their K-tile count is even), 1 for the 64-column tiles.
 template <int BN, int SK = 1>
 struct TcShape {
     static constexpr int B_BYTES = BN * TC_BK * 2;
@@ -88,8 +88,7 @@ struct TcShape {
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                       ((uint32_t)(TC_BM >> 4) << 24);
 };
-static_assert(TcShape<128>::SMEM <= 232448 && TcShape<64>::SMEM <= 232448 && TcShape<128, 2>::SMEM <= 232448,
-              "stage ring within 227 KB");
+static_assert(TcShape<64>::SMEM <= 232448 && TcShape<128, 2>::SMEM <= 232448, "stage ring within 227 KB");
 
 struct TcArgs {
     const uint16_t* A;        // packed digit slices of the rows: [nsl][rows/128][KB][8192]
@@ -753,12 +752,12 @@ expd_status mma_pass(expd_plan p, const uint16_t* A, const int* ea, long long ro
     if (bn == 64) {
         EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel<64, 1>, TcShape<64>::SMEM));
         dst_mma_kernel<64, 1><<<grid, TcShape<64>::THREADS, TcShape<64>::SMEM, s>>>(a);
-    } else if (a.KB % 2 == 0) {
+    } else {
+        // N = K in every pass (the products are square), so a 128-column tile
+        // means K a multiple of 128: an even K-tile count, two per stage
+        if (a.KB % 2 != 0) return expd_fail(EXPD_ERR_INVALID_ARG, "tensor-core DST: odd K-tile count for 128-column tiles");
         EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel<128, 2>, TcShape<128, 2>::SMEM));
         dst_mma_kernel<128, 2><<<grid, TcShape<128, 2>::THREADS, TcShape<128, 2>::SMEM, s>>>(a);
-    } else {
-        EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel<128, 1>, TcShape<128>::SMEM));
-        dst_mma_kernel<128, 1><<<grid, TcShape<128>::THREADS, TcShape<128>::SMEM, s>>>(a);
     }
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
