@@ -86,9 +86,12 @@ ORACLE_SAMPLE_N = 128
 # each kind (the right-hand side launch with the residuals), so the class is
 # reported at 0.94 of its algorithmic bytes per launch.  time_kernel_real
 # (the FFT-based real-column kernel, on plans without the tensor-core one):
-# 775.4 / 799.0 MB and 495.5 / 532.6 MB, 0.95.  An entry is removed whenever
-# its kernel changes after the capture.
-NCU_TRAFFIC_FRACTION = {"time": 0.95, "time_tc": 0.94}
+# 775.4 / 799.0 MB and 495.5 / 532.6 MB, 0.95.  dst_mma_kernel<128, 2> (the
+# tensor-core DST, first pass of the source's transform): 335.2 + 222.9 MB
+# for 605.2 MB algorithmic (the digits read once, the float64 result written
+# once), 0.92.  An entry is removed whenever its kernel changes after the
+# capture.
+NCU_TRAFFIC_FRACTION = {"time": 0.95, "time_tc": 0.94, "dst_tc": 0.92}
 
 
 def parse_args():
@@ -283,8 +286,11 @@ def roofline_of(classes, k, fp64_plan: bool, unknowns=None):
         # launch is timed alone by its own event pair, so the burst figure
         peak, src = bf16_peak(sustained=False)
         ach = (c["flops"] / n) / sec / 1e12
+        frac_t = NCU_TRAFFIC_FRACTION.get(k)
         return {"bound": "tensor", "kernel": k, "achieved": ach, "peak": peak, "peak_source": src,
-                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": frac_t * c["bytes"] / n if frac_t is not None else None,
+                "algorithmic_bytes_per_launch": c["bytes"] / n,
                 "flops_per_launch": c["flops"] / n,
                 "note": "bf16 digit products executed per launch (pairs x 2 rows N K)"}
     if fp64_plan and k in FP64_CLASSES:
