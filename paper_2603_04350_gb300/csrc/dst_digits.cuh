@@ -113,113 +113,3 @@ inline void tc_groups(int nsl, int K, int* np, int* ng, unsigned char* pi, unsig
     *np = n;
     *ng = q;
 }
-
-// ---- the operand-reuse schedule (four accumulators, stages of digit tiles) ----
-//
-// The groups of tc_groups run in rounds of up to TC_R_ACC groups, one TMEM
-// accumulator each.  Within a round every 64-K step streams the digit tiles
-// of A and B that the round's pairs need, as a sequence of stage sets of at
-// most TC_R_SLOTS tiles; a set carries the pairs whose two tiles it holds,
-// so one tile feeds several pairs.  Sets are chosen by greedy set cover: a
-// candidate is a set of A digits and a set of B digits (at most TC_R_SLOTS
-// tiles together) covering the uncovered pairs (i, j) with i and j in them;
-// the candidate with the most pairs per tile is taken (ties: more pairs,
-// then fewer tiles), until every pair of the round is covered.
-constexpr int TC_R_ACC = 4;     // accumulators (128 TMEM columns each)
-constexpr int TC_R_SLOTS = 6;   // digit tiles per stage set
-constexpr int TC_R_MAXR = 8;    // rounds
-constexpr int TC_R_MAXS = 32;   // stage sets
-constexpr int TC_R_MAXP = 32;   // pairs
-
-struct TcRounds {
-    int nr, ns;
-    // round r: groups rg0[r] .. rg0[r] + rgn[r] - 1 (group g in accumulator
-    // g - rg0[r]); stage sets rs0[r] .. rs0[r] + rsn[r] - 1
-    unsigned char rg0[TC_R_MAXR], rgn[TC_R_MAXR], rs0[TC_R_MAXR], rsn[TC_R_MAXR];
-    // set s: st_n[s] tiles, tile u = st_tile[s][u] (bit 7: a B tile; low bits:
-    // the digit); pairs sp0[s] .. sp0[s] + spn[s] - 1
-    unsigned char st_n[TC_R_MAXS], st_tile[TC_R_MAXS][TC_R_SLOTS], sp0[TC_R_MAXS], spn[TC_R_MAXS];
-    // pair k: the set slots of its A and B tiles, its accumulator, and whether
-    // it takes the accumulator's first MMA of the round (at the first 64-K step)
-    unsigned char pa[TC_R_MAXP], pb[TC_R_MAXP], pacc[TC_R_MAXP], pfirst[TC_R_MAXP];
-};
-
-// false when the schedule does not fit the arrays above
-inline bool tc_rounds(int nsl, int np, int ng, const unsigned char* pi, const unsigned char* pj,
-                      const unsigned char* gstart, TcRounds* R) {
-    *R = TcRounds{};
-    if (np > TC_R_MAXP || nsl > 7) return false;
-    int k = 0;
-    for (int g0 = 0; g0 < ng; g0 += TC_R_ACC) {
-        const int r = R->nr++;
-        if (r >= TC_R_MAXR) return false;
-        const int g1 = g0 + TC_R_ACC < ng ? g0 + TC_R_ACC : ng;
-        R->rg0[r] = (unsigned char)g0;
-        R->rgn[r] = (unsigned char)(g1 - g0);
-        R->rs0[r] = (unsigned char)R->ns;
-        // the round's pairs and their accumulators
-        int rp[TC_R_MAXP], racc[TC_R_MAXP], nrp = 0;
-        for (int g = g0; g < g1; ++g)
-            for (int q = gstart[g]; q < gstart[g + 1]; ++q) {
-                rp[nrp] = q;
-                racc[nrp] = g - g0;
-                ++nrp;
-            }
-        bool covered[TC_R_MAXP] = {};
-        bool started[TC_R_ACC] = {};
-        int left = nrp;
-        while (left > 0) {
-            int best_a = 0, best_b = 0, best_c = 0, best_t = 1;
-            for (int ma = 1; ma < (1 << nsl); ++ma)
-                for (int mb = 1; mb < (1 << nsl); ++mb) {
-                    const int t = __builtin_popcount((unsigned)ma) + __builtin_popcount((unsigned)mb);
-                    if (t > TC_R_SLOTS) continue;
-                    int c = 0;
-                    for (int u = 0; u < nrp; ++u)
-                        if (!covered[u] && ((ma >> pi[rp[u]]) & 1) && ((mb >> pj[rp[u]]) & 1)) ++c;
-                    if (c == 0) continue;
-                    // more pairs per tile; then more pairs; then fewer tiles
-                    const long long lhs = (long long)c * best_t, rhs = (long long)best_c * t;
-                    if (best_c == 0 || lhs > rhs || (lhs == rhs && (c > best_c || (c == best_c && t < best_t)))) {
-                        best_a = ma;
-                        best_b = mb;
-                        best_c = c;
-                        best_t = t;
-                    }
-                }
-            if (best_c == 0) return false;
-            const int s = R->ns++;
-            if (s >= TC_R_MAXS) return false;
-            unsigned char slot_a[8], slot_b[8];
-            int n = 0;
-            for (int d = 0; d < nsl; ++d)
-                if ((best_a >> d) & 1) {
-                    slot_a[d] = (unsigned char)n;
-                    R->st_tile[s][n++] = (unsigned char)d;
-                }
-            for (int d = 0; d < nsl; ++d)
-                if ((best_b >> d) & 1) {
-                    slot_b[d] = (unsigned char)n;
-                    R->st_tile[s][n++] = (unsigned char)(0x80 | d);
-                }
-            R->st_n[s] = (unsigned char)n;
-            R->sp0[s] = (unsigned char)k;
-            for (int u = 0; u < nrp; ++u) {
-                const int q = rp[u];
-                if (covered[u] || !((best_a >> pi[q]) & 1) || !((best_b >> pj[q]) & 1)) continue;
-                covered[u] = true;
-                --left;
-                if (k >= TC_R_MAXP) return false;
-                R->pa[k] = slot_a[pi[q]];
-                R->pb[k] = slot_b[pj[q]];
-                R->pacc[k] = (unsigned char)racc[u];
-                R->pfirst[k] = started[racc[u]] ? 0 : 1;
-                started[racc[u]] = true;
-                ++k;
-            }
-            R->spn[s] = (unsigned char)(k - R->sp0[s]);
-        }
-        R->rsn[r] = (unsigned char)(R->ns - R->rs0[r]);
-    }
-    return k == np;
-}

@@ -112,7 +112,6 @@ struct TcArgs {
     const uint16_t* A2;
     const uint16_t* B2;
     int nprob, ocs, Nout;
-    TcRounds rs;              // the operand-reuse schedule (dst_mma_rounds_kernel)
 };
 
 // The waits of the issuing threads: one try inline (the phase is usually
@@ -665,240 +664,6 @@ __global__ void __launch_bounds__(TcShape<BN, SK>::THREADS, 1) dst_mma_kernel(co
     }
 }
 
-// ------------------------------------------- MMA kernel, operand reuse ----
-// The same products, tiles (128 x 128) and output as dst_mma_kernel<128, 2>,
-// scheduled so that one digit tile in shared memory feeds several MMAs: the
-// groups run in rounds of up to four (TC_R_ACC accumulators fill the 512 TMEM
-// columns), and each 64-K step of a round streams the stage sets of
-// a.rs (up to six 16 KB digit tiles each, both of A and of B) through a
-// two-stage ring; the MMA thread issues, per set, the four K = 16 MMAs of
-// every pair the set holds into the pair's accumulator.  The double-float
-// sums live in the drain warps' registers (lane = tile row, 32 columns per
-// warp: 64 registers), so TMEM holds only accumulators; after a round's last
-// step the drain warps add its groups in group order (the same additions as
-// dst_mma_kernel, so the same bits) and free the accumulators for the next
-// round.  Per 64-K step the stream is 18 instead of 30 tiles for five digits.
-constexpr int TR_STAGES = 2;
-constexpr int TR_STAGE_BYTES = TC_R_SLOTS * TC_TILE_BYTES;  // 96 KB
-constexpr int TR_EPI = 16;                                  // drain warps
-constexpr int TR_THREADS = 32 * (2 + TR_EPI);
-constexpr size_t TR_SMEM = (size_t)TR_STAGES * TR_STAGE_BYTES + 256 + 1024;
-static_assert(TR_SMEM <= 232448, "stage ring within 227 KB");
-static_assert(TC_R_ACC * 128 <= 512, "accumulators within TMEM");
-
-__global__ void __launch_bounds__(TR_THREADS, 1) dst_mma_rounds_kernel(const __grid_constant__ TcArgs a) {
-    constexpr int BN = 128;
-    constexpr uint32_t IDESC = TcShape<128, 2>::IDESC;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                                         ~static_cast<uintptr_t>(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (size_t)TR_STAGES * TR_STAGE_BYTES);
-    // full[s], empty[s], accf (a round's MMAs done), acce (its drain done), drain
-    const uint32_t bar0 = smem_u32(bars);
-    auto full = [&](int st) { return bar0 + 8u * (uint32_t)st; };
-    auto empty = [&](int st) { return bar0 + 8u * (uint32_t)(TR_STAGES + st); };
-    const uint32_t accf = bar0 + 8u * (uint32_t)(2 * TR_STAGES), acce = accf + 8u, drain = accf + 16u;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TR_STAGES + 3);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    const TcRounds& rs = a.rs;
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < TR_STAGES; ++st) {
-            mbar_init(full(st), 1);
-            mbar_init(empty(st), 1);
-        }
-        mbar_init(accf, 1);
-        mbar_init(acce, TR_EPI);
-        mbar_init(drain, 1);
-        *abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    if (warp == 1) {
-        tc_alloc(smem_u32(tmem_slot), 512);
-        tc_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-
-    const int nct = a.N / BN;
-    const int npc = a.nprob * nct;
-    const long long ntiles = (long long)(a.rows / TC_BM) * npc;
-    const int KB = a.KB;
-
-    if (warp == 0) {
-        if (lane == 0) {
-            // ---- copies: per round, 64-K step and stage set, the set's digit tiles ----
-            uint32_t it = 0, cph = 0;
-            int cs = 0;
-            const uint32_t sm0 = smem_u32(sm);
-            bool ok = true;
-            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const long long rt = t / npc;
-                const int pc_ = (int)(t - rt * npc), q = pc_ / nct, ct = pc_ - q * nct;
-                const uint16_t* Aq = (q ? a.A2 : a.A) + rt * KB * TC_TILE_ELEMS;
-                const uint16_t* Bq = (q ? a.B2 : a.B) + (long long)ct * KB * TC_TILE_ELEMS;
-                for (int r = 0; r < rs.nr && ok; ++r)
-                    for (int kb = 0; kb < KB && ok; ++kb)
-                        for (int st = rs.rs0[r]; st < rs.rs0[r] + rs.rsn[r]; ++st, ++it) {
-                            if (!mbar_wait_fast(empty(cs), cph ^ 1u, abort_flag, a.cancel)) {
-                                ok = false;
-                                break;
-                            }
-                            const uint32_t dst = sm0 + (uint32_t)cs * TR_STAGE_BYTES, fb = full(cs);
-                            const int n = rs.st_n[st];
-                            mbar_arrive_expect_tx(fb, (uint32_t)n * TC_TILE_BYTES);
-                            for (int u = 0; u < n; ++u) {
-                                const int code = rs.st_tile[st][u], d = code & 0x7F;
-                                const uint16_t* src = (code & 0x80) ? Bq + d * a.b_slice : Aq + d * a.a_slice;
-                                bulk_g2s(dst + (uint32_t)u * TC_TILE_BYTES, src + (long long)kb * TC_TILE_ELEMS,
-                                         TC_TILE_BYTES, fb);
-                            }
-                            if (++cs == TR_STAGES) {
-                                cs = 0;
-                                cph ^= 1u;
-                            }
-                        }
-            }
-            if (!ok) {
-                *abort_flag = 1;
-                atomicExch(a.err, 1);
-            }
-            for (uint32_t u = it > (uint32_t)TR_STAGES ? it - TR_STAGES : 0u; u < it; ++u)
-                mbar_wait(full((int)(u % TR_STAGES)), (u / TR_STAGES) & 1u, abort_flag, nullptr, true);
-        }
-    } else if (warp == 1) {
-        if (lane == 0) {
-            // ---- MMAs: per stage set, four per pair it holds, into the pair's accumulator ----
-            uint32_t it = 0, cph = 0, rc = 0;
-            int cs = 0;
-            const uint64_t desc0 = smem_desc(smem_u32(sm));
-            bool ok = true;
-            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                for (int r = 0; r < rs.nr && ok; ++r, ++rc) {
-                    // the previous round's accumulators are drained
-                    if (rc > 0 && !mbar_wait(acce, (rc - 1) & 1u, abort_flag, a.cancel)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    for (int kb = 0; kb < KB && ok; ++kb)
-                        for (int st = rs.rs0[r]; st < rs.rs0[r] + rs.rsn[r]; ++st, ++it) {
-                            if (!mbar_wait_fast(full(cs), cph, abort_flag, a.cancel)) {
-                                ok = false;
-                                break;
-                            }
-                            tc_fence_after();
-                            const uint64_t ds = desc0 + (uint64_t)(((uint32_t)cs * TR_STAGE_BYTES) >> 4);
-                            for (int k = rs.sp0[st]; k < rs.sp0[st] + rs.spn[st]; ++k) {
-                                const uint64_t da = ds + (uint64_t)(rs.pa[k] * (TC_TILE_BYTES >> 4));
-                                const uint64_t db = ds + (uint64_t)(rs.pb[k] * (TC_TILE_BYTES >> 4));
-                                const uint32_t d = tmem + (uint32_t)(rs.pacc[k] * BN);
-                                const bool fresh = kb == 0 && rs.pfirst[k];
-#pragma unroll
-                                for (int qq = 0; qq < TC_BK / 16; ++qq)
-                                    tc_mma(d, da + 16u * qq, db + 16u * qq, IDESC, !(fresh && qq == 0));
-                            }
-                            tc_commit(empty(cs));
-                            if (++cs == TR_STAGES) {
-                                cs = 0;
-                                cph ^= 1u;
-                            }
-                        }
-                    if (ok) tc_commit(accf);
-                }
-            }
-            if (!ok) {
-                *abort_flag = 1;
-                atomicExch(a.err, 1);
-            }
-            tc_commit(drain);
-            mbar_wait(drain, 0u, abort_flag, nullptr, true);
-        }
-    } else {
-        // ---- drain and output (warps 2..17): TMEM lane quarter warp % 4,
-        // columns 32 (warp - 2) / 4 .. + 31 of each accumulator; the
-        // double-float sums of those 32 outputs in registers ----
-        const int lq = warp & 3, cq = (warp - 2) >> 2;
-        const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(cq * 32);
-        uint32_t rc = 0;
-        bool ok = true;
-        for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const long long rt = t / npc;
-            const int pc_ = (int)(t - rt * npc), q = pc_ / nct, ct = pc_ - q * nct;
-            float hs[32], ls[32];
-            for (int r = 0; r < rs.nr && ok; ++r, ++rc) {
-                if (!__all_sync(0xffffffffu, mbar_wait(accf, rc & 1u, abort_flag, a.cancel))) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-#pragma unroll 1
-                for (int gg = 0; gg < rs.rgn[r]; ++gg) {
-                    const int g = rs.rg0[r] + gg;
-                    // weight 2^{-7(i+j+2)} of the group's pairs (digits are 0-based)
-                    const float wsc = __int_as_float((127 - 7 * (a.gw[g] + 2)) << 23);
-                    const uint32_t tacc = tl + (uint32_t)(gg * BN);
-                    // eight columns at a time (the 64 registers of the sums
-                    // leave little room: 18 warps give 96 registers a thread)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        uint32_t v[8];
-                        tm_ld8(tacc + 8u * c, v);
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const float w = __fmul_rn(__uint_as_float(v[e]), wsc);  // exact: a power of two
-                            if (g == 0) {
-                                hs[8 * c + e] = w;
-                                ls[8 * c + e] = 0.0f;
-                            } else {
-                                // (hi, lo) += w: two-sum, error into lo, renormalise
-                                const float hi = hs[8 * c + e], lo = ls[8 * c + e];
-                                const float sm_ = __fadd_rn(hi, w);
-                                const float bb = __fsub_rn(sm_, hi);
-                                const float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(sm_, bb)), __fsub_rn(w, bb));
-                                const float l1 = __fadd_rn(lo, er);
-                                const float h1 = __fadd_rn(sm_, l1);
-                                hs[8 * c + e] = h1;
-                                ls[8 * c + e] = __fsub_rn(l1, __fsub_rn(h1, sm_));
-                            }
-                        }
-                    }
-                }
-                // the round's accumulators are free for the next round
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(acce);
-            }
-            if (!ok) break;
-            // ---- output: C[row][col] = (hi + lo) 2^{ea[row] + eb}, transposed within the slice ----
-            const long long row = rt * TC_BM + lq * 32 + lane;
-            const long long slc = row / a.R;
-            const int rin = (int)(row - slc * a.R);
-            const int E = a.ea[row] + a.eb;
-            const long long ostep = (long long)a.ocs * a.R;
-            double* o = a.out + slc * (long long)a.R * a.Nout + (long long)(ct * BN + cq * 32) * ostep +
-                        (long long)q * a.R + rin;
-#pragma unroll
-            for (int e = 0; e < 32; ++e) o[(long long)e * ostep] = scaled_sum(hs[e], ls[e], E);
-        }
-        if (!ok) {
-            *abort_flag = 1;
-            atomicExch(a.err, 1);
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (warp == 1) {
-        __syncwarp();
-        tc_dealloc(tmem, 512);
-    }
-}
-
 }  // namespace
 
 // ------------------------------------------------------------------ host ----
@@ -991,14 +756,8 @@ expd_status mma_pass(expd_plan p, const uint16_t* A, const int* ea, long long ro
         // N = K in every pass (the products are square), so a 128-column tile
         // means K a multiple of 128: an even K-tile count, two per stage
         if (a.KB % 2 != 0) return expd_fail(EXPD_ERR_INVALID_ARG, "tensor-core DST: odd K-tile count for 128-column tiles");
-        if (p->tc_rounds && tc_rounds(nsl, np, ng, a.pi, a.pj, a.gstart, &a.rs)) {
-            // the operand-reuse schedule (EXPD_DST_ROUNDS=1)
-            EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_rounds_kernel, TR_SMEM));
-            dst_mma_rounds_kernel<<<grid, TR_THREADS, TR_SMEM, s>>>(a);
-        } else {
-            EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel<128, 2>, TcShape<128, 2>::SMEM));
-            dst_mma_kernel<128, 2><<<grid, TcShape<128, 2>::THREADS, TcShape<128, 2>::SMEM, s>>>(a);
-        }
+        EXPD_CUDA_TRY(smem_allow((const void*)dst_mma_kernel<128, 2>, TcShape<128, 2>::SMEM));
+        dst_mma_kernel<128, 2><<<grid, TcShape<128, 2>::THREADS, TcShape<128, 2>::SMEM, s>>>(a);
     }
     EXPD_CUDA_TRY(cudaGetLastError());
     return EXPD_OK;
@@ -1034,10 +793,6 @@ void dst_tc_layout(expd_plan p) {
     // the symmetric half of S (even sizes; EXPD_DST_FOLD=0 keeps the full products)
     const char* fo = getenv("EXPD_DST_FOLD");
     p->tc_fold = !(fo && strcmp(fo, "0") == 0) && p->NX % 128 == 0 && p->NY % 128 == 0;
-    // the operand-reuse schedule of the 128-column products: off unless
-    // EXPD_DST_ROUNDS=1 (it has not yet run on a GPU)
-    const char* ro = getenv("EXPD_DST_ROUNDS");
-    p->tc_rounds = ro && strcmp(ro, "1") == 0;
     const double per_slice = (double)p->tc_nsl * p->M * 2.0;
     p->tc_chunk = (int)std::max(1.0, std::min((double)p->Ns, std::floor(2147483648.0 / per_slice)));
 }

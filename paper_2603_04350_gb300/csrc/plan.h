@@ -111,7 +111,6 @@ struct expd_plan_s {
     int tc_dst = 0;            // the dense DST runs on the tensor cores (dst_tc.cu)
     int tc_nsl = 0;            // 7-bit digits per value
     int tc_fold = 0;           // products over the symmetric half of S (S[j][n-1-k] = (-1)^j S[j][k])
-    int tc_rounds = 0;         // 128-column products with the operand-reuse schedule (dst_mma_rounds_kernel)
     int tc_chunk = 0;          // slices transformed per pass
     int tc_eSx = 0, tc_eSy = 0;  // exponents of the S_x and S_y digits (|S| < 2^e)
     uint16_t* tc_S = nullptr;  // packed digit slices of S_x then S_y

@@ -468,93 +468,6 @@ static void tc_pass_host(const std::vector<double>& A, long long rows, int R, co
         }
 }
 
-// The same pass with the operand-reuse schedule (tc_rounds), replaying what
-// dst_mma_rounds_kernel does: per tile, round, 64-K step and stage set, the
-// set's digit tiles copied into slots of one of two 96 KB stages (the copy
-// sources checked against the operands' extents), the four MMAs of each of
-// its pairs read through the slot descriptors into the pair's accumulator
-// (the first of each accumulator per round overwriting), and after each
-// round its groups added in group order.  Returns false if the schedule
-// breaks a rule of the kernel.
-static bool tc_pass_rounds_host(const std::vector<double>& A, long long rows, int R, const std::vector<double>& B,
-                                int N, int K, int nsl, int eB, std::vector<double>& out) {
-    std::vector<uint16_t> pa, pb;
-    std::vector<int> ea, eb;
-    split_host(A, rows, K, nsl, pa, ea, INT_MIN);
-    split_host(B, N, K, nsl, pb, eb, eB);
-    int np = 0, ng = 0;
-    unsigned char pi[32], pj[32], gstart[33], gw[32];
-    tc_groups(nsl, K, &np, &ng, pi, pj, gstart, gw);
-    TcRounds rs;
-    if (!tc_rounds(nsl, np, ng, pi, pj, gstart, &rs)) return false;
-    // each pair of a round appears once per 64-K step, in the round of its
-    // group, with tiles of its own digits; sets hold at most TC_R_SLOTS tiles
-    std::vector<int> seen(np, 0);
-    for (int r = 0; r < rs.nr; ++r) {
-        if (rs.rgn[r] < 1 || rs.rgn[r] > TC_R_ACC) return false;
-        for (int st = rs.rs0[r]; st < rs.rs0[r] + rs.rsn[r]; ++st) {
-            if (rs.st_n[st] < 2 || rs.st_n[st] > TC_R_SLOTS) return false;
-            for (int k = rs.sp0[st]; k < rs.sp0[st] + rs.spn[st]; ++k)
-                if (rs.pa[k] >= rs.st_n[st] || rs.pb[k] >= rs.st_n[st] || (rs.st_tile[st][rs.pa[k]] & 0x80) ||
-                    !(rs.st_tile[st][rs.pb[k]] & 0x80) || rs.pacc[k] >= rs.rgn[r])
-                    return false;
-        }
-    }
-    const int KB = K / 64;
-    const size_t a_slice = (size_t)rows * K, b_slice = (size_t)N * K;
-    const size_t stage_bytes = (size_t)TC_R_SLOTS * 16384;
-    std::vector<uint8_t> smem(2 * stage_bytes);
-    std::vector<double> D[TC_R_ACC], hi(128 * 128);
-    for (auto& d : D) d.assign(128 * 128, 0.0);
-    out.assign((size_t)rows * N, 0.0);
-    int cs = 0;
-    for (long long rt = 0; rt < rows / 128; ++rt)
-        for (int ct = 0; ct < N / 128; ++ct) {
-            int pairs_done = 0;
-            for (int r = 0; r < rs.nr; ++r) {
-                for (int kb = 0; kb < KB; ++kb)
-                    for (int st = rs.rs0[r]; st < rs.rs0[r] + rs.rsn[r]; ++st) {
-                        uint8_t* stage = smem.data() + (size_t)cs * stage_bytes;
-                        for (int u = 0; u < rs.st_n[st]; ++u) {
-                            const int code = rs.st_tile[st][u], d = code & 0x7F;
-                            if (d >= nsl) return false;
-                            const bool isb = code & 0x80;
-                            const size_t off = isb ? (size_t)d * b_slice + ((size_t)ct * KB + kb) * 8192
-                                                   : (size_t)d * a_slice + ((size_t)rt * KB + kb) * 8192;
-                            const std::vector<uint16_t>& src = isb ? pb : pa;
-                            if (off + 8192 > src.size()) return false;
-                            memcpy(stage + (size_t)u * 16384, src.data() + off, 16384);
-                        }
-                        for (int k = rs.sp0[st]; k < rs.sp0[st] + rs.spn[st]; ++k) {
-                            const uint32_t base = (uint32_t)(cs * stage_bytes);
-                            for (int c = 0; c < 4; ++c)
-                                mma_emulate(smem.data(), smem_desc(base + 16384u * rs.pa[k] + 256u * c),
-                                            smem_desc(base + 16384u * rs.pb[k] + 256u * c), D[rs.pacc[k]],
-                                            !(kb == 0 && rs.pfirst[k] && c == 0));
-                            if (kb == 0) ++pairs_done;
-                        }
-                        cs ^= 1;
-                    }
-                for (int gg = 0; gg < rs.rgn[r]; ++gg) {
-                    const int g = rs.rg0[r] + gg;
-                    for (int t = 0; t < 128 * 128; ++t) {
-                        if (std::fabs(D[gg][t]) > 16777216.0) ++failures;
-                        const double w = ldexp(D[gg][t], -7 * (gw[g] + 2));
-                        hi[t] = g == 0 ? w : hi[t] + w;
-                    }
-                }
-            }
-            if (pairs_done != np) return false;
-            for (int m = 0; m < 128; ++m)
-                for (int n = 0; n < 128; ++n) {
-                    const long long row = rt * 128 + m, col = (long long)ct * 128 + n;
-                    const long long sl = row / R, rin = row % R;
-                    out[(size_t)(sl * R * N + col * R + rin)] = ldexp(hi[m * 128 + n], ea[row] + eB);
-                }
-        }
-    return true;
-}
-
 // every digit pair once, most significant weight first, each group of one
 // weight and its worst-case float32 sum within 2^24
 static void test_tc_groups() {
@@ -617,36 +530,6 @@ static void test_tc_dst(std::mt19937_64& rng) {
                 r2 += ref * ref;
             }
     check("tensor-core DST (digits, packing, descriptors)", sqrt(e2 / r2), 1e-9, NY, NX);
-    // the operand-reuse schedule gives the same bits, pass by pass
-    std::vector<double> T2, Y2;
-    const bool ok1 = tc_pass_rounds_host(X, (long long)ns * NY, NY, Sx, NX, NX, nsl, ebound(NX), T2);
-    const bool ok2 = tc_pass_rounds_host(T, (long long)ns * NX, NX, Sy, NY, NY, nsl, ebound(NY), Y2);
-    check("tensor-core DST, operand-reuse schedule (same bits)",
-          ok1 && ok2 && T2 == T && Y2 == Y ? 0.0 : 1.0, 0.5, NY, NX);
-}
-
-// the operand-reuse schedule for every digit count and depth the plans use
-static void test_tc_rounds() {
-    for (int nsl = 3; nsl <= 7; ++nsl)
-        for (int K = 128; K <= 2048; K += 128) {
-            int np = 0, ng = 0;
-            unsigned char pi[32], pj[32], gstart[33], gw[32];
-            tc_groups(nsl, K, &np, &ng, pi, pj, gstart, gw);
-            TcRounds rs;
-            bool ok = tc_rounds(nsl, np, ng, pi, pj, gstart, &rs);
-            int tiles = 0, pairs = 0;
-            for (int st = 0; ok && st < rs.ns; ++st) {
-                tiles += rs.st_n[st];
-                pairs += rs.spn[st];
-                ok = rs.st_n[st] <= TC_R_SLOTS;
-            }
-            // every pair once; fewer tiles per 64-K step than two per pair
-            ok = ok && pairs == np && tiles < 2 * np && rs.nr == (ng + TC_R_ACC - 1) / TC_R_ACC;
-            if (!ok) {
-                ++failures;
-                printf("FAIL tc_rounds nsl %d K %d\n", nsl, K);
-            }
-        }
 }
 
 int main() {
@@ -654,7 +537,6 @@ int main() {
     test_conversions(rng);
     test_dd_complex(rng);
     test_tc_groups();
-    test_tc_rounds();
     test_tc_dst(rng);
     for (int l = 1; l <= 12; ++l)
         for (int sign = -1; sign <= 1; sign += 2) {

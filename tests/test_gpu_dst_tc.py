@@ -199,45 +199,3 @@ def test_tc_cancel_in_flight_gives_up_waits_and_gpu_stays_usable(expd):
         plan.solve_gmres(dev(u0), dev(f), U)
         assert _counts(plan)["dst_tc"]["count"] > 0
     assert O.rel_error(host(U), ref) < 1e-9
-
-
-# The operand-reuse schedule of the 128-column products (dst_mma_rounds_kernel,
-# EXPD_DST_ROUNDS=1): the same digit products summed into the same
-# accumulator groups and added in the same order, so the same bits as the
-# default kernel.  It runs only when EXPD_TEST_DST_ROUNDS=1: the kernel is
-# checked by the host emulation of its schedule (csrc/selftest.cu) and has
-# not yet run on a GPU.
-ROUNDS = pytest.mark.skipif(__import__("os").environ.get("EXPD_TEST_DST_ROUNDS") != "1",
-                            reason="operand-reuse DST kernel: not yet run on a GPU (EXPD_TEST_DST_ROUNDS=1 runs it)")
-
-
-@ROUNDS
-@pytest.mark.parametrize("fold", ["1", "0"], ids=["folded", "full"])
-@pytest.mark.parametrize("p", TC_CASES[:3], ids=TC_IDS[:3])
-def test_tc_rounds_schedule_same_bits(expd, p, fold, monkeypatch):
-    monkeypatch.setenv("EXPD_DST_FOLD", fold)
-    r = np.random.default_rng(18).standard_normal((p.Ns,) + p.n)
-    out = {}
-    for rounds in ("0", "1"):
-        monkeypatch.setenv("EXPD_DST_ROUNDS", rounds)
-        S = torch.empty_like(dev(r))
-        with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-10)) as plan:
-            plan.timing_enable(True)
-            plan.precond_apply(dev(r), S)
-            cls = _counts(plan)
-        assert cls["dst_tc"]["count"] > 0, cls
-        out[rounds] = host(S)
-    assert np.array_equal(out["0"], out["1"])
-
-
-@ROUNDS
-def test_tc_rounds_headline_solve(expd, monkeypatch):
-    # the 1024^2 x 128 GMRES solve with the operand-reuse products
-    monkeypatch.setenv("EXPD_DST_ROUNDS", "1")
-    p = I.HEAT_DIRICHLET_1024
-    u0, f = I.make_inputs(p)
-    U = torch.empty((p.Nt,) + p.n, dtype=torch.float64, device=DEV)
-    with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, max_iter=200)) as plan:
-        info = plan.solve_gmres(dev(u0), dev(f), U)
-    ref = O.sequential_solve(O.spec_of(p), u0, f)[1:]
-    assert O.rel_error(host(U), ref) < p.tol, info
