@@ -69,6 +69,11 @@ EXPD_HD long long packed_offset(long long r, int k, int KB) {
     return ((r >> 7) * KB + (k >> 6)) * 8192 + ((((r & 127) >> 3) * 8 + ((k & 63) >> 3)) * 64) + (r & 7) * 8 + (k & 7);
 }
 
+// Rows of a packed operand rounded up to whole 128-row tiles: the extent of
+// one digit slice (a last, partly filled tile still takes its full 16 KB per
+// 64-K step, so slices of fewer rows would overlap the next digit's tiles)
+EXPD_HD long long digit_rows(long long n) { return (n + 127) / 128 * 128; }
+
 // Shared-memory matrix descriptor of a K-major operand without swizzle
 // (tcgen05): start address >> 4 (bits 0-13), leading-dimension byte offset
 // >> 4 = the next core matrix along K, 128 B (bits 16-29), stride-dimension

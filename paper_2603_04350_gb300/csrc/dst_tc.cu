@@ -97,7 +97,7 @@ struct TcArgs {
     int eb;                   // exponent of S: max|S| < 2^eb (one for all its rows)
     double* out;              // [rows / R][N][R]: C transposed within each slice
     long long a_slice;        // elements per digit slice of A (rows * K)
-    long long b_slice;        // elements per digit slice of B (N * K)
+    long long b_slice;        // elements per digit slice of B (N padded to whole 128-row tiles, times K)
     int rows, R, N, KB;       // rows (multiple of 128), rows per slice, columns, K / 64
     int npairs, ngroups;
     unsigned char pi[32], pj[32];  // digit pair (i, j), 0-based, most significant first
@@ -732,7 +732,7 @@ expd_status mma_pass(expd_plan p, const uint16_t* A, const int* ea, long long ro
     a.eb = eb;
     a.out = out;
     a.a_slice = rows * K;
-    a.b_slice = (long long)N * K;
+    a.b_slice = digit_rows(N) * K;
     a.rows = (int)rows;
     a.R = R;
     a.N = N;
@@ -826,7 +826,12 @@ expd_status dst_tc_setup(expd_plan p, cudaStream_t s) {
         uint16_t* out = p->tc_S + (d == 0 ? 0 : (size_t)nsl * NX * NX);
         const int e = d == 0 ? p->tc_eSx : p->tc_eSy;
         if (p->tc_fold) {
-            const long long h = n / 2, sl = h * h;
+            // a digit slice of S_e or S_o holds whole 128-row tiles: h rows
+            // padded to a multiple of 128 (h = 192, 320, 448 leave a half
+            // tile), so that one digit's last tile does not reach into the
+            // next digit's slice; 2 nsl padded slices fit the n^2 nsl of
+            // the unfolded layout
+            const long long h = n / 2, sl = digit_rows(h) * h;
             st = split_rows(p, S, h, (int)h, 2LL * n, out, sl, nullptr, e, s);
             if (st == EXPD_OK) st = split_rows(p, S + n, h, (int)h, 2LL * n, out + (size_t)nsl * sl, sl, nullptr, e, s);
         } else {
@@ -855,7 +860,8 @@ expd_status dst2_tc(expd_plan p, const double* X, double* Y, int ns, double* tmp
         uint16_t* u = p->tc_pack;
         uint16_t* v = p->tc_pack + (size_t)nsl * r * h;
         expd_status st = split_fold(p, in, r, n, u, v, r * h, exA, s);
-        return st == EXPD_OK ? mma_pass(p, u, exA, r, R, Sd, eS, h, h, out, s, v, Sd + (size_t)nsl * h * h) : st;
+        return st == EXPD_OK ? mma_pass(p, u, exA, r, R, Sd, eS, h, h, out, s, v, Sd + (size_t)nsl * digit_rows(h) * h)
+                             : st;
     };
     for (int b0 = 0; b0 < ns; b0 += p->tc_chunk) {
         const int cs = std::min(p->tc_chunk, ns - b0);

@@ -468,6 +468,50 @@ static void tc_pass_host(const std::vector<double>& A, long long rows, int R, co
         }
 }
 
+// The packed digit slices of S's folded halves (h = n/2 rows of h values,
+// digit slices digit_rows(h) * h apart, S_e's then S_o's) for every size the
+// tensor-core DST takes: no element written twice, every B tile the MMA
+// kernel reads (128- or 64-row tiles, per 64-K step) lies on written elements
+// of its own digit and half, and all of it within the n * n * nsl elements
+// allocated per axis.
+static void test_tc_s_layout() {
+    for (int n = 128; n <= 1024; n += 128)
+        for (int nsl = 3; nsl <= 7; ++nsl) {
+            const long long h = n / 2, K = h, KB = K / 64, sl = digit_rows(h) * h;
+            const long long total = (long long)nsl * n * n;
+            std::vector<int> owner((size_t)total / 8, -1);  // 8-element groups: (half, digit) + 1
+            bool ok = 2 * nsl * sl <= total;
+            for (int half = 0; half < 2 && ok; ++half)
+                for (int d = 0; d < nsl && ok; ++d)
+                    for (long long r = 0; r < h && ok; ++r)
+                        for (long long k = 0; k < K; k += 8) {
+                            const long long e = half * nsl * sl + d * sl + packed_offset(r, (int)k, (int)KB);
+                            if (e + 8 > total || owner[(size_t)(e / 8)] != -1) {
+                                ok = false;
+                                break;
+                            }
+                            owner[(size_t)(e / 8)] = half * 8 + d;
+                        }
+            const int BN = h % 128 ? 64 : 128;
+            for (int half = 0; half < 2 && ok; ++half)
+                for (int d = 0; d < nsl && ok; ++d)
+                    for (long long ct = 0; ct < h / BN && ok; ++ct)
+                        for (long long kb = 0; kb < KB && ok; ++kb) {
+                            const long long boff = (ct * BN / 128) * KB * 8192 + ((ct * BN) % 128) * 64;
+                            const long long start = half * nsl * sl + d * sl + boff + kb * 8192;
+                            for (long long e = start; e < start + BN * 64; e += 8)
+                                if (e + 8 > total || owner[(size_t)(e / 8)] != half * 8 + d) {
+                                    ok = false;
+                                    break;
+                                }
+                        }
+            if (!ok) {
+                ++failures;
+                printf("FAIL tensor-core DST operand layout n %d nsl %d\n", n, nsl);
+            }
+        }
+}
+
 // every digit pair once, most significant weight first, each group of one
 // weight and its worst-case float32 sum within 2^24
 static void test_tc_groups() {
@@ -537,6 +581,7 @@ int main() {
     test_conversions(rng);
     test_dd_complex(rng);
     test_tc_groups();
+    test_tc_s_layout();
     test_tc_dst(rng);
     for (int l = 1; l <= 12; ++l)
         for (int sign = -1; sign <= 1; sign += 2) {

@@ -35,6 +35,9 @@ TC_CASES = [
     P("tc_d2d_s2", "dirichlet", (128, 256), 2, Nt=10),
     P("tc_d2d_s6", "dirichlet", (128, 128), 6, Nt=13),
     P("tc_d2d_ac_s1", "dirichlet", (128, 256), 1, nonlin="allen_cahn", a=0.01, c=0.0, dt=1e-3, Nt=12, alpha=1e-3),
+    # 384 points: folded, S's halves have 192 rows, one and a half 128-row
+    # tiles (64-column products over three 64-K steps)
+    P("tc_d2d_384_s2", "dirichlet", (384, 256), 2, Nt=7),
 ]
 TC_IDS = [p.name for p in TC_CASES]
 
@@ -199,3 +202,20 @@ def test_tc_cancel_in_flight_gives_up_waits_and_gpu_stays_usable(expd):
         plan.solve_gmres(dev(u0), dev(f), U)
         assert _counts(plan)["dst_tc"]["count"] > 0
     assert O.rel_error(host(U), ref) < 1e-9
+
+
+def test_tc_half_tile_operand_rows_same_bits_every_run(expd):
+    # S's folded halves of 192 rows end in a half-filled 128-row tile; each
+    # digit slice spans whole tiles, so no digit's tiles overlap the next
+    # one's and repeated transforms give the same bits (and the oracle's values)
+    p = TC_CASES[-1]
+    r = np.random.default_rng(19).standard_normal((p.Ns,) + p.n)
+    ref = O.precond_apply(O.spec_of(p), r)
+    outs = []
+    for _ in range(3):
+        S = torch.empty_like(dev(r))
+        with expd.plan_create(expd.spec_from_problem(p, precision=expd.PREC_MIXED, tol=1e-10)) as plan:
+            plan.precond_apply(dev(r), S)
+        outs.append(host(S))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    assert relmax(outs[0], ref) < 6e-8 * 16 / p.alpha
