@@ -35,8 +35,10 @@ TC_CASES = [
     P("tc_d2d_s2", "dirichlet", (128, 256), 2, Nt=10),
     P("tc_d2d_s6", "dirichlet", (128, 128), 6, Nt=13),
     P("tc_d2d_ac_s1", "dirichlet", (128, 256), 1, nonlin="allen_cahn", a=0.01, c=0.0, dt=1e-3, Nt=12, alpha=1e-3),
-    # 384 points: folded, S's halves have 192 rows, one and a half 128-row
-    # tiles (64-column products over three 64-K steps)
+    # 384 and 640 points: folded, S's halves have 192 or 320 rows, ending in
+    # a half-filled 128-row tile (64-column products over three or five
+    # 64-K steps)
+    P("tc_d2d_640_s1", "dirichlet", (640, 128), 1, Nt=5),
     P("tc_d2d_384_s2", "dirichlet", (384, 256), 2, Nt=7),
 ]
 TC_IDS = [p.name for p in TC_CASES]
